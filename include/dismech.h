@@ -1,0 +1,180 @@
+/*
+ * dismech.h -- C ABI of the GB300 implicit Discrete Elastic Rods step.
+ *
+ * The library advances batches of independent rod systems (single rods and
+ * rods joined at elastic joints) by the fully implicit backward-Euler step of
+ * the DisMech paper (arXiv 2311.18126):
+ *
+ *   Sec. III, Eq. 1    DOF vector q = [q_0, theta^0, q_1, ..., q_{N-1}] per rod
+ *                      (node positions, edge twist angles), 4N-1 entries.
+ *   Sec. III-A, Eq. 2-9  stretching, bending and twisting energies over edges
+ *                      and node stencils, with time-parallel reference frames,
+ *                      reference twist and material curvatures kappa1, kappa2.
+ *   Sec. III-B, Eq. 10-13  IMC ground / edge-edge contact, smooth Coulomb
+ *                      friction, gravity and viscous damping.
+ *   Sec. III-C, Eq. 14-16  residual M/dt((q_{n+1}-q_n)/dt - qdot_n) - F = 0
+ *                      solved by Newton's method with J = M/dt^2 - dF/dq,
+ *                      then qdot_{n+1} = (q_{n+1}-q_n)/dt.
+ *   Sec. III-D         elastic joints: bending and twisting for every pair of
+ *                      edges meeting at a joint node.
+ *   Sec. III-E         natural curvature kappabar as the control input.
+ *
+ * Everything on the step runs in hand-written sm_103a CUDA kernels in FP64.
+ *
+ * Conventions
+ *  - Every call returns dm_status; no C++ exception crosses the ABI.  On an
+ *    error, dm_last_error() returns a message for the calling thread.
+ *  - A dm_system handle is not thread-safe: one host thread at a time.
+ *  - The caller owns every buffer it passes; the library copies what it
+ *    needs before returning (device-side copies are ordered on the system's
+ *    stream).  The library owns all device memory behind the handle.
+ *  - Units are SI.  Arrays are row-major, FP64 unless stated.
+ *  - A "system" is a connected component of rods under the joints.  Systems
+ *    are numbered in the order of their lowest rod index.
+ */
+#ifndef DISMECH_H
+#define DISMECH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dm_system dm_system; /* opaque */
+
+typedef enum dm_status {
+  DM_OK = 0,
+  DM_ERR_INVALID_ARG = 1,   /* bad descriptor, size or pointer               */
+  DM_ERR_NOT_CONVERGED = 2, /* Newton hit max_iter; state kept at last step  */
+  DM_ERR_NONFINITE = 3,     /* NaN/Inf in the residual or the update         */
+  DM_ERR_DEGENERATE = 4,    /* zero-length edge, antiparallel edges at a
+                               stencil (kappa b singular, Eq. 4), an edge
+                               reversed within one step, or a zero pivot     */
+  DM_ERR_PENETRATION = 5,   /* edge-edge distance D <= 0 (Eq. 10 undefined)  */
+  DM_ERR_CUDA = 6,          /* a CUDA runtime call failed                    */
+  DM_ERR_OOM = 7            /* device allocation failed                      */
+} dm_status;
+
+/* Rod geometry, materials and boundary conditions (Sec. III, III-D).
+ * All arrays are host memory and are copied by dm_create_system. */
+typedef struct dm_system_desc {
+  int32_t n_rods;
+  const int32_t *nodes_per_rod; /* [n_rods], N_r >= 2                          */
+  const double *x0;             /* [sum N_r][3] rest = initial node positions   */
+  const double *v0;             /* [sum N_r][3] initial velocities, or NULL (0) */
+  const double *theta0;         /* [sum (N_r-1)] initial twist angles, or NULL  */
+  const double *theta_dot0;     /* [sum (N_r-1)] or NULL                        */
+  const double *E;              /* [n_rods] Young's modulus                     */
+  const double *nu;             /* [n_rods] Poisson ratio (G = E/(2(1+nu)))     */
+  const double *rho;            /* [n_rods] density                             */
+  const double *radius;         /* [n_rods] rod radius h                        */
+  /* Elastic joints: joint j merges the nodes joint_members[k] = (rod, node)
+   * for k in [joint_offsets[j], joint_offsets[j+1]) into one shared node. */
+  int32_t n_joints;
+  const int32_t *joint_offsets; /* [n_joints+1] or NULL when n_joints == 0      */
+  const int32_t *joint_members; /* [joint_offsets[n_joints]][2]                 */
+  /* Fixed DOFs in the per-rod layout of Eq. 1 (nonzero = fixed), or NULL. */
+  const uint8_t *fixed;         /* [sum (4 N_r - 1)]                            */
+  /* Ground friction coefficient and contact stiffness per rod (a shared
+   * joint node takes the values of its lowest-numbered rod), or NULL (0). */
+  const double *ground_mu;      /* [n_rods]                                     */
+  const double *ground_kc;      /* [n_rods] k_c multiplying Eq. 10, N/m         */
+} dm_system_desc;
+
+/* Step parameters (Sec. III-B, III-C). */
+typedef struct dm_params {
+  double dt;            /* time step                                           */
+  double newton_tol;    /* convergence: max_i |f_i| / (D_i l_i) <= newton_tol,
+                           D_i = M_i/dt^2 + rest stretch (position DOFs) or
+                           twist (angle DOFs) stiffness, l_i = total rest
+                           length of the system (positions) or 1 (angles)     */
+  int32_t max_iter;     /* Newton iterations per step before giving up         */
+  double gravity[3];    /* m/s^2                                               */
+  double damping;       /* viscous damping eta: F_i = -eta V_i (x_i - x_i^n)/dt */
+  int32_t ground;       /* nonzero: ground plane z = ground_z with IMC contact  */
+  double ground_z;
+  double delta;         /* contact distance tolerance delta (K1 = 15/delta)    */
+  double slip_nu;       /* slipping tolerance nu (K2 = 15/nu), m/s             */
+  int32_t self_contact; /* nonzero: edge-edge IMC contact within each system   */
+  double pair_kc;       /* k_c of edge-edge contact                            */
+  double pair_mu;       /* edge-edge friction coefficient                      */
+  void *stream;         /* cudaStream_t for all work, NULL = default stream    */
+} dm_params;
+
+/* Optional per-call statistics (caller-owned arrays may be NULL). */
+typedef struct dm_step_stats {
+  int32_t capacity;          /* entries available in iterations[]/residual[]  */
+  int32_t *iterations;       /* [n_systems] Newton iterations of the last step */
+  double *residual;          /* [n_systems] final scaled residual              */
+  int32_t first_failed;      /* out: -1, or the first failing system           */
+  int32_t steps_done;        /* out: steps completed                           */
+  int64_t sum_iterations;    /* out: sum over steps and systems of iterations  */
+  int32_t max_iterations;    /* out: max over steps and systems                */
+} dm_step_stats;
+
+/* Builds the systems of `desc` on the current CUDA device (Sec. III, III-D):
+ * merges joint nodes, numbers the DOFs, computes rest lengths, masses
+ * (node: sum over incident edges of rho A l/2; twist: rho A h^2 l/2),
+ * initial reference frames (z projected off the first tangent of each rod,
+ * then space-parallel transport along the rod), initial reference twist,
+ * natural strains (kappabar, taubar = initial values), and uploads it all.
+ * `out` receives the handle; on error *out is NULL.  Bend-twist stencils
+ * are numbered by node (nodes in order of their lowest (rod, node) entry),
+ * then by the pair of incident edges (edges in descriptor order). */
+dm_status dm_create_system(const dm_system_desc *desc, const dm_params *params,
+                           dm_system **out);
+
+/* Frees all device and host memory of the handle.  NULL-safe. */
+void dm_destroy(dm_system *sys);
+
+/* Natural curvature control (Sec. III-E, Eq. 6): kbar holds
+ * (kappabar1, kappabar2) -- integrated curvature, dimensionless as in Eq. 5 --
+ * for every interior node of rods [rod_begin, rod_end), rods in order,
+ * nodes 1..N_r-2 in order: 2 * sum (N_r - 2) doubles.  Joint stencils keep
+ * their initial natural curvature.  `kbar` is host memory, or device memory
+ * when is_device != 0.  Takes effect at the next dm_step, in stream order. */
+dm_status dm_set_natural_curvature(dm_system *sys, int32_t rod_begin,
+                                   int32_t rod_end, const double *kbar,
+                                   int32_t is_device);
+
+/* Advances every system by `nsteps` backward-Euler steps (Eq. 15-16).
+ * Each step is all-or-nothing: if any system fails (status != DM_OK) the
+ * step is not committed, the state stays at the last completed step and the
+ * call returns that status.  `stats` may be NULL. */
+dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats);
+
+/* Copies q and qdot out in the per-rod layout of Eq. 1, rods concatenated
+ * (a shared joint node appears in every rod that contains it).  q and qdot
+ * are host buffers (or device buffers when is_device != 0) of at least
+ * dm_state_size() doubles each; qdot may be NULL.  Synchronises the stream
+ * for host buffers. */
+dm_status dm_get_state(dm_system *sys, double *q, double *qdot, size_t cap,
+                       int32_t is_device);
+
+/* Sets q and qdot (same layout as dm_get_state; joint-node copies must
+ * agree, the lowest rod's copy wins).  Reference frames are kept; the
+ * committed tangents are recomputed from the new q. */
+dm_status dm_set_state(dm_system *sys, const double *q, const double *qdot,
+                       size_t cap, int32_t is_device);
+
+/* History a bitwise resume needs: reference director d1 per edge
+ * ([sum (N_r-1)][3], descriptor edge order) and reference twist beta per
+ * bend-twist stencil ([dm_num_stencils]).  Host buffers.  Either may be NULL. */
+dm_status dm_get_frames(dm_system *sys, double *d1, double *beta);
+dm_status dm_set_frames(dm_system *sys, const double *d1, const double *beta);
+
+/* Sizes. */
+int64_t dm_state_size(const dm_system *sys);  /* sum (4 N_r - 1) */
+int32_t dm_num_systems(const dm_system *sys);
+int64_t dm_num_stencils(const dm_system *sys);
+int64_t dm_num_edges(const dm_system *sys);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *dm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DISMECH_H */

@@ -1,0 +1,492 @@
+"""Pins of the CPU oracle against closed forms, invariances, finite
+differences and textbook results (DisMech, arXiv 2311.18126, Sec. III-IV).
+
+These run on the CPU only.  Each test is chosen so that a plausible mistake
+in the oracle (a dropped term, a wrong sign or index, a transposed operand)
+fails at least one of them."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+from torch.func import grad, hessian, vmap
+
+from oracle import OracleSystems, der
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+DT = torch.float64
+
+
+def rod_desc(x, E=1e7, nu=0.5, rho=1000.0, h=1e-3, fixed=None, v0=None, theta0=None):
+    x = np.asarray(x, dtype=np.float64)
+    N = len(x)
+    d = dict(nodes_per_rod=[N], x0=x, E=[E], nu=[nu], rho=[rho], radius=[h],
+             fixed=np.zeros(4 * N - 1, np.uint8) if fixed is None else fixed)
+    if v0 is not None:
+        d["v0"] = v0
+    if theta0 is not None:
+        d["theta0"] = theta0
+    return d
+
+
+def clamp(N):
+    m = np.zeros(4 * N - 1, np.uint8)
+    m[0:8] = 1
+    return m
+
+
+def straight(N, L=1.0):
+    x = np.zeros((N, 3))
+    x[:, 0] = np.linspace(0, L, N)
+    return x
+
+
+def random_rod(N, seed, amp=0.2):
+    rng = np.random.default_rng(seed)
+    x = straight(N) + amp * rng.standard_normal((N, 3)) / N
+    return x
+
+
+# ---------------------------------------------------------------------------
+# Eq. 4-5: kappa = 2 tan(phi/2) for a kink of turning angle phi
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("phi", [0.1, 0.7, 1.5, 2.5, 3.0])
+def test_kink_curvature_closed_form(phi):
+    # kink in the x-y plane: d1 = z stays normal to the plane
+    x = np.array([[-1.0, 0, 0], [0, 0, 0], [math.cos(phi), math.sin(phi), 0]])
+    o = OracleSystems(rod_desc(x))
+    s = o.systems[0]
+    k1, k2 = float(s.kbar1[0]), float(s.kbar2[0])
+    assert abs(k1) < 1e-14
+    # material frame m1 = d1 = z, m2 = t x z: in-plane bending is kappa2
+    assert k2 == pytest.approx(-2.0 * math.tan(phi / 2.0), rel=1e-13)
+    # kink in the x-z plane: bending about the d2 axis is kappa1
+    x = np.array([[-1.0, 0, 0], [0, 0, 0], [math.cos(phi), 0, math.sin(phi)]])
+    s = OracleSystems(rod_desc(x)).systems[0]
+    assert abs(float(s.kbar2[0])) < 1e-13
+    assert abs(float(s.kbar1[0])) == pytest.approx(2.0 * math.tan(phi / 2.0), rel=1e-13)
+
+
+def test_arc_bending_energy_closed_form():
+    # straight rest shape bent into an arc of turning angle phi per node:
+    # E_b = sum 1/2 EI/V (2 tan(phi/2))^2 with V the rest Voronoi length
+    N, phi, h, E = 9, 0.2, 1e-3, 1e7
+    L = 1.0
+    desc = rod_desc(straight(N, L), E=E, h=h)
+    o = OracleSystems(desc)
+    s = o.systems[0]
+    ell = L / (N - 1)
+    ang = phi * np.arange(N - 1)
+    pts = np.concatenate([[[0, 0, 0]], np.cumsum(ell * np.stack(
+        [np.cos(ang), np.sin(ang), np.zeros(N - 1)], 1), 0)])
+    q = s.q.clone()
+    for i in range(N):
+        q[4 * i:4 * i + 3] = torch.as_tensor(pts[i])
+    _, t = o._stencil_geometry(s, q)
+    d1 = o._time_parallel_frames(s, t)
+    sa, sb, ta, d1a, tb, d1b = o._oriented(s, t, d1)
+    beta = der.reference_twist(ta, d1a, tb, d1b, s.beta)
+    q11 = q[torch.as_tensor(s.st_dofs)]
+    Eb = der.bend_energy_only(q11, sa, sb, ta, d1a, tb, d1b, beta,
+                              torch.as_tensor(s.st_kb), s.kbar1, s.kbar2).sum()
+    EI = E * math.pi * h ** 4 / 4
+    expect = (N - 2) * 0.5 * EI / ell * (2 * math.tan(phi / 2)) ** 2
+    assert float(Eb) == pytest.approx(expect, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 7-8: uniform twist of a straight rod
+# ---------------------------------------------------------------------------
+
+def test_uniform_twist_end_moments():
+    N, c, E, nu, h = 7, 0.3, 2e6, 0.25, 2e-3
+    L = 0.6
+    o = OracleSystems(rod_desc(straight(N, L), E=E, nu=nu, h=h))
+    s = o.systems[0]
+    q = s.q.clone()
+    th = c * np.arange(N - 1)
+    q[torch.as_tensor(s.edge_dof)] = torch.as_tensor(th)
+    F, _, _ = o.forces(s, q, s.v, s.q, need_jac=False)
+    G = E / (2 * (1 + nu))
+    GJ = G * math.pi * h ** 4 / 2
+    V = L / (N - 1)
+    Mth = F[torch.as_tensor(s.edge_dof)].numpy()
+    expect = np.zeros(N - 1)
+    expect[0] = GJ * c / V          # -dE/dtheta^0 = +GJ tau / V
+    expect[-1] = -GJ * c / V
+    np.testing.assert_allclose(Mth, expect, rtol=1e-12, atol=1e-12 * GJ * c / V)
+    # straight rod: twist exerts no force on the nodes, gravity aside
+    Fx = F[torch.as_tensor(s.node_dof)[:, None] + torch.arange(3)].numpy()
+    grav = s.mnode[:, None] * np.array([0, 0, -9.81])
+    np.testing.assert_allclose(Fx, grav, atol=1e-12 * GJ * c / V)
+
+
+# ---------------------------------------------------------------------------
+# Forces are the negative gradients (Eq. 9): central finite differences
+# ---------------------------------------------------------------------------
+
+def _stencil_setup(seed):
+    N = 6
+    rng = np.random.default_rng(seed)
+    x = random_rod(N, seed, amp=0.6)
+    o = OracleSystems(rod_desc(x, theta0=0.3 * rng.standard_normal(N - 1)))
+    s = o.systems[0]
+    s.kbar1 = torch.as_tensor(rng.uniform(-0.3, 0.3, len(s.st)))
+    s.kbar2 = torch.as_tensor(rng.uniform(-0.3, 0.3, len(s.st)))
+    # move the rod away from its committed state
+    q = s.q + torch.as_tensor(0.05 * rng.standard_normal(s.n) / N)
+    return o, s, q
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_forces_match_central_differences(seed):
+    o, s, q = _stencil_setup(seed)
+    F, _, _ = o.forces(s, q, s.v, s.q, need_jac=False)
+    # energy with the reference frames held at those of q (at-point gauge)
+    _, t = o._stencil_geometry(s, q)
+    d1 = o._time_parallel_frames(s, t)
+    sa, sb, ta, d1a, tb, d1b = o._oriented(s, t, d1)
+    bref = der.reference_twist(ta, d1a, tb, d1b, s.beta)
+    kb, kt = torch.as_tensor(s.st_kb), torch.as_tensor(s.st_kt)
+    idx = torch.as_tensor(s.st_dofs)
+    e6 = torch.as_tensor(s.edge_dofs6)
+
+    def energy(qq):
+        Eb = der.bend_twist_energy(qq[idx], sa, sb, ta, d1a, tb, d1b, bref, kb, kt,
+                                   s.kbar1, s.kbar2, s.taubar).sum()
+        Es = der.stretch_energy(qq[e6], torch.as_tensor(s.EA), torch.as_tensor(s.lbar)).sum()
+        return Eb + Es - (torch.as_tensor(s.mnode)[:, None] * torch.tensor([0, 0, -9.81], dtype=DT)
+                          * qq[torch.as_tensor(s.node_dof)[:, None] + torch.arange(3)]).sum()
+
+    hstep = 1e-6
+    fd = np.zeros(s.n)
+    for i in range(s.n):
+        dq = torch.zeros(s.n, dtype=DT)
+        dq[i] = hstep
+        fd[i] = -(float(energy(q + dq)) - float(energy(q - dq))) / (2 * hstep)
+    scale = np.max(np.abs(fd))
+    np.testing.assert_allclose(F.numpy(), fd, atol=1e-7 * scale)
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_jacobians_match_central_differences(seed):
+    o, s, q = _stencil_setup(seed)
+    # (1) at-point Hessian = derivative of the gradient with frames held
+    F0, _, J = o.forces(s, q, s.v, s.q, need_jac=True)
+    _, t = o._stencil_geometry(s, q)
+    d1 = o._time_parallel_frames(s, t)
+    sa, sb, ta, d1a, tb, d1b = o._oriented(s, t, d1)
+    bref = der.reference_twist(ta, d1a, tb, d1b, s.beta)
+    kb, kt = torch.as_tensor(s.st_kb), torch.as_tensor(s.st_kt)
+    idx = torch.as_tensor(s.st_dofs)
+    e6 = torch.as_tensor(s.edge_dofs6)
+
+    def held_force(qq):
+        def en(z):
+            return (der.bend_twist_energy(z[idx], sa, sb, ta, d1a, tb, d1b, bref, kb, kt,
+                                          s.kbar1, s.kbar2, s.taubar).sum()
+                    + der.stretch_energy(z[e6], torch.as_tensor(s.EA),
+                                         torch.as_tensor(s.lbar)).sum())
+        return -grad(en)(qq)
+
+    hstep = 1e-6
+    fd = np.zeros((s.n, s.n))
+    for j in range(s.n):
+        dq = torch.zeros(s.n, dtype=DT)
+        dq[j] = hstep
+        fd[:, j] = -(held_force(q + dq) - held_force(q - dq)).numpy() / (2 * hstep)
+    sc = np.max(np.abs(fd))
+    np.testing.assert_allclose(J.numpy(), fd, atol=1e-6 * sc)
+    # (2) exact mode = derivative of the at-point force with frames carried
+    #     by time-parallel transport (no frames held)
+    _, _, Jx = o.forces(s, q, s.v, s.q, need_jac=True, mode="exact")
+    fd2 = np.zeros((s.n, s.n))
+    for j in range(s.n):
+        dq = torch.zeros(s.n, dtype=DT)
+        dq[j] = hstep
+        Fp, _, _ = o.forces(s, q + dq, s.v, s.q, need_jac=False)
+        Fm, _, _ = o.forces(s, q - dq, s.v, s.q, need_jac=False)
+        fd2[:, j] = -(Fp - Fm).numpy() / (2 * hstep)
+    np.testing.assert_allclose(Jx.numpy(), fd2, atol=1e-6 * sc)
+    # the two Jacobians differ (the at-point one is symmetric, the exact one
+    # carries the holonomy of the transported frames)
+    assert np.allclose(J.numpy(), J.numpy().T, atol=1e-12 * sc)
+
+
+# ---------------------------------------------------------------------------
+# Invariances: rigid motions
+# ---------------------------------------------------------------------------
+
+def _rotation(seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((3, 3))
+    Q, R = np.linalg.qr(A)
+    Q = Q * np.sign(np.diag(R))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] = -Q[:, 0]
+    return Q
+
+
+def test_rigid_motion_invariance():
+    o, s, q = _stencil_setup(7)
+    o.p["g"] = (0.0, 0.0, 0.0)
+    F, _, _ = o.forces(s, q, s.v, s.q, need_jac=False)
+    nd = torch.as_tensor(s.node_dof)[:, None] + torch.arange(3)
+    x = q[nd].numpy()
+    Fx = F[nd].numpy()
+    M = F[torch.as_tensor(s.edge_dof)].numpy()
+    _, t = o._stencil_geometry(s, q)
+    # total force and total torque (nodes plus twisting moments about t) vanish
+    assert np.allclose(Fx.sum(0), 0, atol=1e-10 * np.abs(Fx).max())
+    tau = np.cross(x, Fx).sum(0) + (M[:, None] * t.numpy()).sum(0)
+    assert np.allclose(tau, 0, atol=1e-10 * np.abs(Fx).max())
+    # rotate everything (state, committed frames): forces rotate with it
+    Rm = _rotation(1)
+    R = torch.as_tensor(Rm)
+    q2 = q.clone()
+    q2[nd] = q[nd] @ R.T + torch.tensor([0.3, -1.0, 2.0], dtype=DT)
+    s.d1 = s.d1 @ R.T
+    s.tn = s.tn @ R.T
+    F2, _, _ = o.forces(s, q2, s.v, s.q, need_jac=False)
+    np.testing.assert_allclose(F2[nd].numpy(), Fx @ Rm.T, atol=1e-10 * np.abs(Fx).max())
+    np.testing.assert_allclose(F2[torch.as_tensor(s.edge_dof)].numpy(), M,
+                               atol=1e-10 * np.abs(Fx).max())
+
+
+def test_linear_momentum_conserved():
+    # no gravity, damping, contact or fixed DOFs: backward Euler keeps
+    # sum m v exactly, because internal forces sum to zero
+    N = 8
+    rng = np.random.default_rng(11)
+    x = random_rod(N, 11, amp=0.5)
+    v0 = rng.standard_normal((N, 3))
+    o = OracleSystems(rod_desc(x, v0=v0), dict(g=(0, 0, 0), dt=1e-3, eta=0.0))
+    s = o.systems[0]
+    nd = torch.as_tensor(s.node_dof)[:, None] + torch.arange(3)
+
+    def mom():
+        return (torch.as_tensor(s.mnode)[:, None] * s.v[nd]).sum(0).numpy()
+
+    p0 = mom()
+    for _ in range(5):
+        st = o.step_system(s)
+        assert st[0] == 0
+    np.testing.assert_allclose(mom(), p0, atol=1e-12 * np.abs(p0).max())
+
+
+# ---------------------------------------------------------------------------
+# Time-parallel transport and reference twist: holonomy of a closed loop
+# ---------------------------------------------------------------------------
+
+def _ode_transport(d, path):
+    """Parallel transport along a sampled unit-vector path by integrating
+    dd/ds = -(d . dt/ds) t with RK4 on a fine reparametrisation."""
+    for k in range(len(path) - 1):
+        a, b = path[k], path[k + 1]
+        for sub in range(2):
+            def tt(u):
+                v = a + u * (b - a)
+                return v / np.linalg.norm(v)
+
+            def rhs(u, dv):
+                t = tt(u)
+                h = 1e-6
+                tdot = (tt(u + h) - tt(u - h)) / (2 * h)
+                return -np.dot(dv, tdot) * t
+            u0, du = sub / 2, 0.5
+            k1 = rhs(u0, d)
+            k2 = rhs(u0 + du / 2, d + du / 2 * k1)
+            k3 = rhs(u0 + du / 2, d + du / 2 * k2)
+            k4 = rhs(u0 + du, d + du * k3)
+            d = d + du / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return d
+
+
+def test_reference_twist_holonomy():
+    # edge a fixed along x; edge b's tangent goes once around a cone about z
+    # (half-angle alpha).  Time-parallel transport carries d1^b around the
+    # loop; the continued reference twist must change by exactly the angle
+    # that the transported director has turned, which is the enclosed solid
+    # angle 2 pi (1 - cos alpha) (mod 2 pi) of the traced loop.
+    alpha = 0.6
+    n = 2000
+    ph = np.linspace(0, 2 * math.pi, n + 1)
+    path = np.stack([np.sin(alpha) * np.cos(ph), np.sin(alpha) * np.sin(ph),
+                     np.full_like(ph, math.cos(alpha))], 1)
+    ta = torch.tensor([1.0, 0, 0], dtype=DT)
+    d1a = torch.tensor([0, 0, 1.0], dtype=DT)
+    tb = torch.as_tensor(path[0])
+    d1b = torch.as_tensor(np.cross(path[0], [0, 1.0, 0]))
+    d1b = d1b / torch.linalg.vector_norm(d1b)
+    beta = der.reference_twist(ta, d1a, tb, d1b, torch.tensor(0.0, dtype=DT))
+    beta0 = float(beta)
+    d1b_start = d1b.clone()
+    for k in range(1, n + 1):
+        tnew = torch.as_tensor(path[k])
+        d1b = der.parallel_transport(d1b, tb, tnew)
+        tb = tnew
+        beta = der.reference_twist(ta, d1a, tb, d1b, beta)
+    # independent ODE transport agrees with the minimal-rotation steps
+    d_ode = _ode_transport(d1b_start.numpy(), path)
+    assert np.allclose(d_ode, d1b.numpy(), atol=1e-7)
+    turned = math.atan2(np.dot(path[0], np.cross(d1b_start.numpy(), d1b.numpy())),
+                        np.dot(d1b_start.numpy(), d1b.numpy()))
+    assert float(beta) - beta0 == pytest.approx(turned, abs=1e-9)
+    solid = 2 * math.pi * (1 - math.cos(alpha))
+    wrapped = (abs(turned) - solid + math.pi) % (2 * math.pi) - math.pi
+    assert abs(wrapped) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Newton: quadratic convergence with the exact Jacobian; banded == dense LU
+# ---------------------------------------------------------------------------
+
+def test_newton_quadratic_convergence():
+    # one Newton step from q* + eps w has error O(eps^2) with the exact
+    # Jacobian (Eq. 16 in full): the ratio err/eps^2 stays constant as eps
+    # shrinks.  A dropped or wrong Jacobian term makes it grow like 1/eps.
+    N = 10
+    rng = np.random.default_rng(5)
+    desc = rod_desc(straight(N, 0.5), E=1e6, h=2e-3, fixed=clamp(N),
+                    v0=np.c_[np.zeros(N), 0.5 * rng.standard_normal(N), rng.standard_normal(N)])
+    p = dict(dt=0.01, tol=1e-15, max_iter=40, eta=0.0, jacobian="exact")
+    o = OracleSystems(desc, p)
+    s = o.systems[0]
+    s.kbar1 = torch.full((N - 2,), 0.05, dtype=DT)
+    q_n, v_n = s.q.clone(), s.v.clone()
+    assert o.step_system(s)[0] == 0
+    qstar = s.q.clone()
+    w = torch.as_tensor(rng.standard_normal(s.n))
+    w = torch.where(s.fixed, torch.zeros_like(w), w)
+    w = w / torch.linalg.vector_norm(w)
+    ratios = []
+    for eps in (1e-3, 1e-4, 1e-5):
+        q0 = qstar + eps * w
+        f, _, J = o.residual(s, q0, q_n, v_n, need_jac=True, mode="exact")
+        q1 = q0 + o.solve(s, J, -f)
+        ratios.append(float(torch.linalg.vector_norm(q1 - qstar)) / eps ** 2)
+    assert ratios[2] < 2.0 * ratios[1] and ratios[1] < 2.0 * ratios[0]
+    # the at-point Jacobian reaches the same root
+    o2 = OracleSystems(desc, dict(p, jacobian="atpoint"))
+    o2.systems[0].kbar1 = s.kbar1.clone()
+    st = o2.step_system(o2.systems[0])
+    assert st[0] == 0
+    np.testing.assert_allclose(o2.systems[0].q.numpy(), qstar.numpy(), atol=1e-12)
+
+
+def test_banded_and_dense_solves_agree():
+    o, s, q = _stencil_setup(9)
+    f, _, J = o.residual(s, q, s.q, s.v, need_jac=True)
+    x_band = o.solve(s, J, -f).numpy()
+    x_dense = np.linalg.solve(J.numpy(), -f.numpy())
+    np.testing.assert_allclose(x_band, x_dense, rtol=1e-10, atol=1e-14 * np.abs(x_dense).max())
+
+
+# ---------------------------------------------------------------------------
+# Euler-Bernoulli statics and the first cantilever mode (Sec. IV-A)
+# ---------------------------------------------------------------------------
+
+def _static_tip(N, E=1e11, h=1e-2, L=1.0, rho=1000.0):
+    desc = rod_desc(straight(N, L), E=E, h=h, rho=rho, fixed=clamp(N))
+    o = OracleSystems(desc, dict(dt=1e3, g=(0, 0, -9.81), eta=0.0, tol=1e-12))
+    s = o.systems[0]
+    for _ in range(3):
+        st = o.step_system(s)
+        assert st[0] == 0
+        s.v.zero_()
+    return -float(s.q[4 * (N - 1) + 2])
+
+
+def test_euler_bernoulli_static_cantilever():
+    E, h, L, rho, g = 1e11, 1e-2, 1.0, 1000.0, 9.81
+    A, I = math.pi * h * h, math.pi * h ** 4 / 4
+    errs = []
+    for N in (11, 21):
+        # nodes 0 and 1 clamped: the beam is built in at the middle of the
+        # clamped edge, where the first free stencil's Voronoi cell begins
+        Leff = L - 0.5 * L / (N - 1)
+        w = rho * A * g * Leff ** 4 / (8 * E * I)
+        errs.append(abs(_static_tip(N) - w) / w)
+    assert errs[1] < 0.003
+    assert errs[1] < errs[0]
+
+
+def test_cantilever_first_mode_frequency():
+    gold = json.load(open(os.path.join(GOLD, "table2_cantilever.json")))
+    h, rho, L, E = gold["radius"], gold["rho"], gold["length"], gold["a1"]["E"]
+    N = 21
+    ell = L / (N - 1)
+    Leff = L - 0.5 * ell                     # built in mid clamped edge
+    A, I = math.pi * h * h, math.pi * h ** 4 / 4
+    omega = (gold["beta1_L"] / Leff) ** 2 * math.sqrt(E * I / (rho * A))
+    # initial velocity in the first mode shape, tip speed from the paper
+    bl = gold["beta1_L"]
+    sig = (math.sinh(bl) - math.sin(bl)) / (math.cosh(bl) + math.cos(bl))
+    s_ = np.clip(np.linspace(0, L, N) - 0.5 * ell, 0, None) * bl / Leff
+
+    def phi(u):
+        return np.cosh(u) - np.cos(u) - sig * (np.sinh(u) - np.sin(u))
+    v0 = np.zeros((N, 3))
+    v0[:, 2] = gold["tip_velocity"] * phi(s_) / phi(bl)
+    v0[:2] = 0
+    desc = rod_desc(straight(N, L), E=E, h=h, rho=rho, fixed=clamp(N), v0=v0)
+    dt = 0.05
+    o = OracleSystems(desc, dict(dt=dt, g=(0, 0, 0), eta=0.0))
+    s = o.systems[0]
+    zs = [0.0]
+    half = math.pi / omega
+    for _ in range(int(1.3 * half / dt)):
+        assert o.step_system(s)[0] == 0
+        zs.append(float(s.q[4 * (N - 1) + 2]))
+    zs = np.array(zs)
+    k = np.nonzero((zs[1:-1] > 0) & (zs[2:] <= 0))[0][0] + 1
+    tz = dt * (k + zs[k] / (zs[k] - zs[k + 1]))
+    assert tz == pytest.approx(half, rel=0.02)
+
+
+# ---------------------------------------------------------------------------
+# Ground contact with friction: the closed form of Sec. IV-C
+# ---------------------------------------------------------------------------
+
+def _sliding_energy(push, T):
+    gold = json.load(open(os.path.join(GOLD, "friction_validation.json")))
+    h, rho, L, E, mu = gold["radius"], gold["rho"], gold["length"], gold["E"], gold["mu"]
+    g = gold["g"]
+    N = 11                                   # rigid sliding: N does not matter
+    x = straight(N, L)
+    x[:, 2] = h
+    m = rho * math.pi * h * h * L
+    mnode = m / (N - 1)
+    kc = 50.0 * mnode * g / gold["delta"]    # reading C11
+    desc = rod_desc(x, E=E, h=h, rho=rho, nu=gold["nu"])
+    desc["ground_mu"] = [mu]
+    desc["ground_kc"] = [kc]
+    p = dict(dt=gold["dt"], g=(0.0, 0.0, -g), eta=0.0, ground=True, ground_z=0.0,
+             delta=gold["delta"], nu_slip=gold["slip_nu"])
+    o = OracleSystems(desc, p)
+    s = o.systems[0]
+    for _ in range(40):                      # settle onto the floor at rest
+        assert o.step_system(s)[0] == 0
+        s.v.zero_()
+    # the push is a uniform body force: gravity gains an x component
+    o.p["g"] = (push / m, 0.0, -g)
+    for _ in range(int(round(T / gold["dt"]))):
+        assert o.step_system(s)[0] == 0
+    nd = torch.as_tensor(s.node_dof)[:, None] + torch.arange(3)
+    v = s.v[nd].numpy()
+    Ek = 0.5 * float(np.sum(s.mnode[:, None] * v * v))
+    return Ek, m, mu, g
+
+
+@pytest.mark.parametrize("push", [10.5, 3.0])
+def test_friction_kinetic_energy_closed_form(push):
+    T = 0.5
+    Ek, m, mu, g = _sliding_energy(push, T)
+    if push <= mu * m * g:
+        assert Ek < 1e-6
+    else:
+        expect = T * T / (2 * m) * (push - mu * m * g) ** 2
+        assert Ek == pytest.approx(expect, rel=0.03)
