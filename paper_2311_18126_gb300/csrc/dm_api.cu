@@ -1,0 +1,488 @@
+// C ABI of the GB300 implicit DER library (include/dismech.h).
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "dm_internal.h"
+#include "dm_kernels.cuh"
+
+namespace dm {
+
+static thread_local std::string g_err;
+void set_error(const std::string &m) { g_err = m; }
+
+}  // namespace dm
+
+using namespace dm;
+
+namespace {
+
+#define DM_CK(call)                                                             \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess) {                                                    \
+      set_error(std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #call); \
+      return e_ == cudaErrorMemoryAllocation ? DM_ERR_OOM : DM_ERR_CUDA;        \
+    }                                                                           \
+  } while (0)
+
+template <class T>
+dm_status dalloc(dm_system *s, T **p, size_t n) {
+  void *v = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc(&v, n * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return DM_ERR_OOM;
+  }
+  s->allocations.push_back(v);
+  *p = (T *)v;
+  return DM_OK;
+}
+
+template <class T>
+dm_status upload(dm_system *s, T **p, const std::vector<T> &h) {
+  dm_status st = dalloc(s, p, h.size());
+  if (st != DM_OK) return st;
+  if (!h.empty()) DM_CK(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return DM_OK;
+}
+
+#define DM_TRY(x)                 \
+  do {                            \
+    dm_status st_ = (x);          \
+    if (st_ != DM_OK) return st_; \
+  } while (0)
+
+inline int blocks(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+__global__ void k_gather_layout(int n, const int32_t *map, const double *src, double *dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[map[i]];
+}
+__global__ void k_scatter_layout(int n, const int32_t *map, const double *src, double *dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[map[i]] = src[i];
+}
+__global__ void k_scatter_kbar(int n, const int32_t *slot2st, int slot0, int ns,
+                               const double *in, double *kbar) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int st = slot2st[slot0 + i];
+  kbar[st] = in[2 * i];
+  kbar[ns + st] = in[2 * i + 1];
+}
+
+struct Extra {
+  std::vector<int32_t> slot2st;
+  int32_t *d_slot2st = nullptr;
+  int32_t *d_dof_sys = nullptr;
+  double *d_damp = nullptr;
+  double *d_scratch = nullptr;  // layout-sized staging for state copies
+  size_t scratch_n = 0;
+};
+
+}  // namespace
+
+// Extra per-handle data lives next to the handle.
+struct dm_system_ext : dm_system {
+  Extra x;
+};
+
+static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
+                             dm_system_ext *s) {
+  HostTopology &T = s->T;
+  if (!build_topology(desc, prm, T)) return DM_ERR_INVALID_ARG;
+  if (prm->ground || prm->self_contact) {
+    set_error("ground and edge-edge contact are not supported by this build");
+    return DM_ERR_INVALID_ARG;
+  }
+  s->prm = *prm;
+  s->stream = (cudaStream_t)prm->stream;
+  s->p.dt = prm->dt;
+  s->p.tol = prm->newton_tol;
+  s->p.max_iter = prm->max_iter;
+  for (int c = 0; c < 3; ++c) s->p.g[c] = prm->gravity[c];
+  s->p.eta = prm->damping;
+
+  const int64_t nd = T.n_dofs, ne = T.n_edges, ns = T.n_stencils;
+  const int S = T.n_systems;
+  DevArrays &d = s->d;
+  // DOF vectors
+  DM_TRY(upload(s, &d.q, T.q0));
+  DM_TRY(upload(s, &d.qn, T.q0));
+  DM_TRY(upload(s, &d.vn, T.v0));
+  DM_TRY(dalloc(s, &d.f, nd));
+  DM_TRY(upload(s, &d.mass, T.dof_mass));
+  DM_TRY(upload(s, &d.rscale, T.dof_rscale));
+  DM_TRY(upload(s, &d.fixed, T.dof_fixed));
+  std::vector<int32_t> dof_sys(nd);
+  for (int k = 0; k < S; ++k)
+    for (int i = 0; i < T.sys_ndof[k]; ++i) dof_sys[T.sys_dof0[k] + i] = k;
+  DM_TRY(upload(s, &s->x.d_dof_sys, dof_sys));
+  std::vector<double> damp(nd, 0.0);
+  for (int64_t v = 0; v < T.n_nodes; ++v)
+    for (int c = 0; c < 3; ++c) damp[T.node_dof[v] + c] = prm->damping * T.node_vor[v] / prm->dt;
+  DM_TRY(upload(s, &s->x.d_damp, damp));
+  // edges
+  std::vector<int32_t> ea(ne), eb(ne);
+  for (int64_t e = 0; e < ne; ++e) {
+    ea[e] = T.node_dof[T.edge_a[e]];
+    eb[e] = T.node_dof[T.edge_b[e]];
+  }
+  DM_TRY(upload(s, &d.edge_a, ea));
+  DM_TRY(upload(s, &d.edge_b, eb));
+  DM_TRY(upload(s, &d.edge_th, T.edge_thdof));
+  DM_TRY(upload(s, &d.edge_sys, T.edge_sys));
+  DM_TRY(upload(s, &d.edge_lbar, T.edge_lbar));
+  DM_TRY(upload(s, &d.edge_EA, T.edge_EA));
+  std::vector<double> soa(3 * ne);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int c = 0; c < 3; ++c) soa[c * ne + e] = T.d1_init[3 * e + c];
+  DM_TRY(upload(s, &d.d1n, soa));
+  for (int64_t e = 0; e < ne; ++e)
+    for (int c = 0; c < 3; ++c) soa[c * ne + e] = T.t_init[3 * e + c];
+  DM_TRY(upload(s, &d.tn, soa));
+  DM_TRY(dalloc(s, &d.ef, 13 * ne));
+  DM_TRY(dalloc(s, &d.es, 9 * ne));
+  // stencils
+  std::vector<int32_t> sted(2 * ns), stth(2 * ns), stsg(ns);
+  for (int64_t k = 0; k < ns; ++k) {
+    sted[k] = T.st_edge[0][k];
+    sted[ns + k] = T.st_edge[1][k];
+    stth[k] = T.edge_thdof[T.st_edge[0][k]];
+    stth[ns + k] = T.edge_thdof[T.st_edge[1][k]];
+    stsg[k] = (T.st_sign[0][k] < 0 ? 1 : 0) | (T.st_sign[1][k] < 0 ? 2 : 0);
+  }
+  DM_TRY(upload(s, &d.st_ed, sted));
+  DM_TRY(upload(s, &d.st_th, stth));
+  DM_TRY(upload(s, &d.st_sg, stsg));
+  DM_TRY(upload(s, &d.st_sys, T.st_sys));
+  DM_TRY(upload(s, &d.st_kb, T.st_kb));
+  DM_TRY(upload(s, &d.st_kt, T.st_kt));
+  std::vector<double> kb2(2 * ns);
+  for (int64_t k = 0; k < ns; ++k) {
+    kb2[k] = T.st_kbar1[k];
+    kb2[ns + k] = T.st_kbar2[k];
+  }
+  DM_TRY(upload(s, &d.kbar, kb2));
+  DM_TRY(upload(s, &d.taubar, T.st_taubar));
+  DM_TRY(upload(s, &d.beta_n, T.st_beta0));
+  DM_TRY(dalloc(s, &d.beta_it, ns));
+  DM_TRY(dalloc(s, &d.sg, 11 * ns));
+  DM_TRY(dalloc(s, &d.sh, 66 * ns));
+  // systems
+  DM_TRY(upload(s, &d.sys_dof0, T.sys_dof0));
+  DM_TRY(upload(s, &d.sys_ndof, T.sys_ndof));
+  DM_TRY(upload(s, &d.sys_st0, T.sys_st0));
+  DM_TRY(upload(s, &d.sys_edge0, T.sys_edge0));
+  DM_TRY(dalloc(s, &d.sys_active, S));
+  DM_TRY(dalloc(s, &d.sys_iters, S));
+  DM_TRY(dalloc(s, &d.sys_status, S));
+  DM_TRY(dalloc(s, &d.sys_res, S));
+  DM_TRY(dalloc(s, &d.ctrl, 4));
+  DM_TRY(dalloc(s, &d.band, 11 * nd));
+  DM_TRY(dalloc(s, &d.dq, nd));
+  std::vector<int32_t> order(S);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return T.sys_ndof[a] > T.sys_ndof[b]; });
+  DM_TRY(upload(s, &d.solve_order, order));
+  DM_TRY(upload(s, &d.layout2dof, T.layout2dof));
+  // natural-curvature slots -> stencils
+  int64_t nslots = 0;
+  for (int r = 0; r < T.n_rods; ++r) nslots += T.npr[r] - 2;
+  s->x.slot2st.assign(std::max<int64_t>(nslots, 1), 0);
+  for (int64_t k = 0; k < ns; ++k)
+    if (T.st_rod_slot[k] >= 0) s->x.slot2st[T.st_rod_slot[k]] = (int32_t)k;
+  DM_TRY(upload(s, &s->x.d_slot2st, s->x.slot2st));
+  s->x.scratch_n = std::max<size_t>({(size_t)T.layout2dof.size(), (size_t)(2 * nslots), (size_t)1});
+  DM_TRY(dalloc(s, &s->x.d_scratch, s->x.scratch_n));
+  DM_CK(cudaMallocHost(&s->h_ctrl, 4 * sizeof(int32_t)));
+  DM_CK(cudaDeviceSynchronize());
+  return DM_OK;
+}
+
+extern "C" {
+
+const char *dm_last_error(void) { return dm::g_err.c_str(); }
+
+dm_status dm_create_system(const dm_system_desc *desc, const dm_params *params,
+                           dm_system **out) {
+  if (!out) {
+    set_error("out is NULL");
+    return DM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  set_error("");
+  dm_system_ext *s = new (std::nothrow) dm_system_ext();
+  if (!s) {
+    set_error("host allocation failed");
+    return DM_ERR_OOM;
+  }
+  dm_status st;
+  try {
+    st = create_impl(desc, params, s);
+  } catch (const std::exception &ex) {
+    set_error(std::string("host exception: ") + ex.what());
+    st = DM_ERR_OOM;
+  }
+  if (st != DM_OK) {
+    std::string keep = dm::g_err;
+    dm_destroy(s);
+    set_error(keep);
+    return st;
+  }
+  *out = s;
+  return DM_OK;
+}
+
+void dm_destroy(dm_system *sys) {
+  if (!sys) return;
+  for (void *p : sys->allocations) cudaFree(p);
+  if (sys->h_ctrl) cudaFreeHost(sys->h_ctrl);
+  delete static_cast<dm_system_ext *>(sys);
+}
+
+int64_t dm_state_size(const dm_system *s) { return s ? (int64_t)s->T.layout2dof.size() : 0; }
+int32_t dm_num_systems(const dm_system *s) { return s ? s->T.n_systems : 0; }
+int64_t dm_num_stencils(const dm_system *s) { return s ? s->T.n_stencils : 0; }
+int64_t dm_num_edges(const dm_system *s) { return s ? s->T.n_edges : 0; }
+
+dm_status dm_set_natural_curvature(dm_system *sys, int32_t rod_begin, int32_t rod_end,
+                                   const double *kbar, int32_t is_device) {
+  if (!sys || !kbar || rod_begin < 0 || rod_end > sys->T.n_rods || rod_begin > rod_end) {
+    set_error("dm_set_natural_curvature: bad arguments");
+    return DM_ERR_INVALID_ARG;
+  }
+  auto *s = static_cast<dm_system_ext *>(sys);
+  const HostTopology &T = s->T;
+  int64_t slot0 = 0, n = 0;
+  for (int r = 0; r < rod_begin; ++r) slot0 += T.npr[r] - 2;
+  for (int r = rod_begin; r < rod_end; ++r) n += T.npr[r] - 2;
+  if (n == 0) return DM_OK;
+  const double *src = kbar;
+  if (!is_device) {
+    DM_CK(cudaMemcpyAsync(s->x.d_scratch, kbar, 2 * n * sizeof(double),
+                          cudaMemcpyHostToDevice, s->stream));
+    src = s->x.d_scratch;
+  }
+  k_scatter_kbar<<<blocks(n, 256), 256, 0, s->stream>>>((int)n, s->x.d_slot2st, (int)slot0,
+                                                        (int)T.n_stencils, src, s->d.kbar);
+  DM_CK(cudaGetLastError());
+  if (!is_device) DM_CK(cudaStreamSynchronize(s->stream));  // host buffer reusable
+  return DM_OK;
+}
+
+dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
+  if (!sys || nsteps < 0) {
+    set_error("dm_step: bad arguments");
+    return DM_ERR_INVALID_ARG;
+  }
+  auto *s = static_cast<dm_system_ext *>(sys);
+  const HostTopology &T = s->T;
+  DevArrays &d = s->d;
+  cudaStream_t st = s->stream;
+  const int nd = (int)T.n_dofs, ne = (int)T.n_edges, ns = (int)T.n_stencils, S = T.n_systems;
+  StepArgs sa{nd, ne, ns, S, s->p.dt, d.q, d.qn, d.vn, d.d1n, d.tn, d.beta_n, d.ef, d.beta_it,
+              d.fixed, d.sys_active, d.sys_iters, d.sys_status, d.sys_res};
+  EdgeArgs ea{ne, d.q, d.edge_a, d.edge_b, d.edge_th, d.edge_sys, d.edge_EA, d.edge_lbar,
+              d.tn, d.d1n, d.sys_active, d.sys_status, d.ef, d.es};
+  StencilArgs ka{ns, ne, d.q, d.ef, d.st_ed, d.st_th, d.st_sg, d.st_sys, d.st_kb, d.st_kt,
+                 d.kbar, d.taubar, d.beta_n, d.sys_active, d.sys_status, d.beta_it, d.sg, d.sh};
+  RowArgs ra{};
+  ra.nd = nd; ra.ns = ns; ra.ne = ne; ra.dt = s->p.dt;
+  for (int c = 0; c < 3; ++c) ra.g[c] = s->p.g[c];
+  ra.eta = s->p.eta;
+  ra.q = d.q; ra.qn = d.qn; ra.vn = d.vn; ra.mass = d.mass; ra.rscale = d.rscale;
+  ra.damp = s->x.d_damp; ra.fixed = d.fixed; ra.dof_sys = s->x.d_dof_sys;
+  ra.sys_dof0 = d.sys_dof0; ra.sys_ndof = d.sys_ndof; ra.sys_st0 = d.sys_st0;
+  ra.sys_edge0 = d.sys_edge0; ra.sys_active = d.sys_active;
+  ra.sg = d.sg; ra.sh = d.sh; ra.es = d.es; ra.f = d.f; ra.band = d.band; ra.sys_res = d.sys_res;
+  SolveArgs va{S, nd, s->p.tol, s->p.max_iter, d.solve_order, d.sys_dof0, d.sys_ndof, d.fixed, d.f,
+               d.band, d.q, d.dq, d.sys_active, d.sys_iters, d.sys_status, d.sys_res, d.ctrl};
+  if (stats) {
+    stats->first_failed = -1;
+    stats->steps_done = 0;
+    stats->sum_iterations = 0;
+    stats->max_iterations = 0;
+  }
+  std::vector<int32_t> iters;
+  for (int step = 0; step < nsteps; ++step) {
+    int32_t init[4] = {0, 0, INT_MAX, 0};
+    DM_CK(cudaMemcpyAsync(d.ctrl, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    k_begin_step<<<blocks(std::max(nd, S), 256), 256, 0, st>>>(sa);
+    for (int it = 0; it <= s->p.max_iter; ++it) {
+      DM_CK(cudaMemsetAsync(d.sys_res, 0, S * sizeof(unsigned long long), st));
+      DM_CK(cudaMemsetAsync(d.ctrl, 0, sizeof(int32_t), st));
+      k_edge<<<blocks(ne, 256), 256, 0, st>>>(ea);
+      k_stencil<<<blocks(ns, 128), 128, 0, st>>>(ka);
+      k_rows_rod<<<blocks(nd, 256), 256, 0, st>>>(ra);
+      k_solve_rod<<<blocks(S, 32), 32, 0, st>>>(va);
+      DM_CK(cudaGetLastError());
+      DM_CK(cudaMemcpyAsync(s->h_ctrl, d.ctrl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      DM_CK(cudaStreamSynchronize(st));
+      if (s->h_ctrl[0] == 0) break;
+    }
+    if (stats || s->h_ctrl[1] > 0) {
+      iters.resize(S);
+      DM_CK(cudaMemcpyAsync(iters.data(), d.sys_iters, S * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      DM_CK(cudaStreamSynchronize(st));
+    }
+    if (s->h_ctrl[1] > 0) {
+      k_restore<<<blocks(nd, 256), 256, 0, st>>>(sa);
+      int32_t first = s->h_ctrl[2], code = 0;
+      DM_CK(cudaMemcpyAsync(&code, d.sys_status + first, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      DM_CK(cudaStreamSynchronize(st));
+      if (stats) stats->first_failed = first;
+      set_error("step " + std::to_string(step) + ": system " + std::to_string(first) +
+                " failed with status " + std::to_string(code));
+      return (dm_status)code;
+    }
+    k_commit<<<blocks(std::max({nd, ne, ns}), 256), 256, 0, st>>>(sa);
+    DM_CK(cudaGetLastError());
+    if (stats) {
+      stats->steps_done = step + 1;
+      for (int k = 0; k < S; ++k) {
+        stats->sum_iterations += iters[k];
+        stats->max_iterations = std::max(stats->max_iterations, iters[k]);
+      }
+    }
+  }
+  if (stats) {
+    int n = std::min(stats->capacity, S);
+    if (stats->iterations && n > 0) std::copy(iters.begin(), iters.begin() + n, stats->iterations);
+    if (stats->residual && n > 0) {
+      std::vector<unsigned long long> rb(S);
+      DM_CK(cudaMemcpyAsync(rb.data(), d.sys_res, S * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, st));
+      DM_CK(cudaStreamSynchronize(st));
+      for (int k = 0; k < n; ++k) {
+        double v;
+        std::memcpy(&v, &rb[k], sizeof(double));
+        stats->residual[k] = v;
+      }
+    }
+  }
+  return DM_OK;
+}
+
+dm_status dm_get_state(dm_system *sys, double *q, double *qdot, size_t cap, int32_t is_device) {
+  if (!sys || !q) {
+    set_error("dm_get_state: bad arguments");
+    return DM_ERR_INVALID_ARG;
+  }
+  auto *s = static_cast<dm_system_ext *>(sys);
+  const size_t n = s->T.layout2dof.size();
+  if (cap < n) {
+    set_error("dm_get_state: capacity " + std::to_string(cap) + " < " + std::to_string(n));
+    return DM_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = s->stream;
+  for (int k = 0; k < 2; ++k) {
+    double *dst = k == 0 ? q : qdot;
+    if (!dst) continue;
+    double *stage = is_device ? dst : s->x.d_scratch;
+    k_gather_layout<<<blocks(n, 256), 256, 0, st>>>((int)n, s->d.layout2dof,
+                                                    k == 0 ? s->d.qn : s->d.vn, stage);
+    DM_CK(cudaGetLastError());
+    if (!is_device) {
+      DM_CK(cudaMemcpyAsync(dst, stage, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+      DM_CK(cudaStreamSynchronize(st));
+    }
+  }
+  return DM_OK;
+}
+
+dm_status dm_set_state(dm_system *sys, const double *q, const double *qdot, size_t cap,
+                       int32_t is_device) {
+  if (!sys || !q || !qdot) {
+    set_error("dm_set_state: bad arguments");
+    return DM_ERR_INVALID_ARG;
+  }
+  auto *s = static_cast<dm_system_ext *>(sys);
+  const size_t n = s->T.layout2dof.size();
+  if (cap < n) {
+    set_error("dm_set_state: capacity too small");
+    return DM_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = s->stream;
+  // scatter in reverse rod order so that the lowest rod's joint copy wins
+  for (int k = 0; k < 2; ++k) {
+    const double *src = k == 0 ? q : qdot;
+    const double *stage = src;
+    if (!is_device) {
+      DM_CK(cudaMemcpyAsync(s->x.d_scratch, src, n * sizeof(double), cudaMemcpyHostToDevice, st));
+      stage = s->x.d_scratch;
+    }
+    k_scatter_layout<<<blocks(n, 256), 256, 0, st>>>((int)n, s->d.layout2dof, stage,
+                                                     k == 0 ? s->d.qn : s->d.vn);
+    DM_CK(cudaGetLastError());
+    if (!is_device) DM_CK(cudaStreamSynchronize(st));
+  }
+  DM_CK(cudaMemcpyAsync(s->d.q, s->d.qn, s->T.n_dofs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // committed tangents from the new positions
+  const HostTopology &T = s->T;
+  std::vector<double> qh(T.n_dofs), tn(3 * T.n_edges);
+  DM_CK(cudaMemcpyAsync(qh.data(), s->d.qn, T.n_dofs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DM_CK(cudaStreamSynchronize(st));
+  for (int64_t e = 0; e < T.n_edges; ++e) {
+    const int a = T.node_dof[T.edge_a[e]], b = T.node_dof[T.edge_b[e]];
+    double v[3] = {qh[b] - qh[a], qh[b + 1] - qh[a + 1], qh[b + 2] - qh[a + 2]};
+    double l = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(l > 0)) {
+      set_error("dm_set_state: zero-length edge");
+      return DM_ERR_DEGENERATE;
+    }
+    for (int c = 0; c < 3; ++c) tn[c * T.n_edges + e] = v[c] / l;
+  }
+  DM_CK(cudaMemcpy(s->d.tn, tn.data(), tn.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return DM_OK;
+}
+
+dm_status dm_get_frames(dm_system *sys, double *d1, double *beta) {
+  if (!sys) {
+    set_error("dm_get_frames: NULL handle");
+    return DM_ERR_INVALID_ARG;
+  }
+  const HostTopology &T = sys->T;
+  cudaStream_t st = sys->stream;
+  if (d1) {
+    std::vector<double> soa(3 * T.n_edges);
+    DM_CK(cudaMemcpyAsync(soa.data(), sys->d.d1n, soa.size() * sizeof(double),
+                          cudaMemcpyDeviceToHost, st));
+    DM_CK(cudaStreamSynchronize(st));
+    for (int64_t e = 0; e < T.n_edges; ++e)
+      for (int c = 0; c < 3; ++c) d1[3 * e + c] = soa[c * T.n_edges + e];
+  }
+  if (beta) {
+    DM_CK(cudaMemcpyAsync(beta, sys->d.beta_n, T.n_stencils * sizeof(double),
+                          cudaMemcpyDeviceToHost, st));
+    DM_CK(cudaStreamSynchronize(st));
+  }
+  return DM_OK;
+}
+
+dm_status dm_set_frames(dm_system *sys, const double *d1, const double *beta) {
+  if (!sys) {
+    set_error("dm_set_frames: NULL handle");
+    return DM_ERR_INVALID_ARG;
+  }
+  const HostTopology &T = sys->T;
+  cudaStream_t st = sys->stream;
+  DM_CK(cudaStreamSynchronize(st));
+  if (d1) {
+    std::vector<double> soa(3 * T.n_edges);
+    for (int64_t e = 0; e < T.n_edges; ++e)
+      for (int c = 0; c < 3; ++c) soa[c * T.n_edges + e] = d1[3 * e + c];
+    DM_CK(cudaMemcpy(sys->d.d1n, soa.data(), soa.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if (beta)
+    DM_CK(cudaMemcpy(sys->d.beta_n, beta, T.n_stencils * sizeof(double), cudaMemcpyHostToDevice));
+  return DM_OK;
+}
+
+}  // extern "C"

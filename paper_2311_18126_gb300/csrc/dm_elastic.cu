@@ -1,0 +1,344 @@
+// Elastic forces and Hessians of the implicit DER step, FP64, sm_103a.
+//
+//  k_edge     -- one thread per edge: tangent, time-parallel reference frame
+//                (Sec. III), material frame, stretching force and Hessian
+//                (Sec. III-A, Eq. 2-3).
+//  k_stencil  -- one thread per bend-twist stencil: curvature binormal
+//                (Eq. 4), material curvatures (Eq. 5), reference twist and
+//                twist (Eq. 7), and the gradient and Hessian of
+//                1/2 EI/V |kappa - kappabar|^2 + 1/2 GJ/V (tau - taubar)^2
+//                (Eq. 6, 8) in closed form, in the at-point gauge: the
+//                derivatives are taken with the reference frames carried by
+//                parallel transport from the current iterate.
+//
+// The GB300 FP64 pipe is narrow (about 1 TFLOP/s) and charges a full warp
+// slot for every FP64 instruction whatever its active mask, so each thread
+// owns one whole edge or stencil and all 32 lanes do useful FP64 work.
+#include "dm_internal.h"
+#include "dm_kernels.cuh"
+
+namespace dm {
+
+__global__ void k_edge(EdgeArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.ne) return;
+  const int s = a.edge_sys[e];
+  if (!a.sys_active[s]) return;
+  const int ia = a.edge_a[e], ib = a.edge_b[e];
+  const double ex = a.q[ib] - a.q[ia];
+  const double ey = a.q[ib + 1] - a.q[ia + 1];
+  const double ez = a.q[ib + 2] - a.q[ia + 2];
+  const double l2 = ex * ex + ey * ey + ez * ez;
+  if (!(l2 > 0.0)) {
+    atomicMax(&a.sys_status[s], (int)DM_ERR_DEGENERATE);
+    return;
+  }
+  const double il = rsqrt(l2);
+  const double l = l2 * il;
+  const double tx = ex * il, ty = ey * il, tz = ez * il;
+  const int NE = a.ne;
+  const double nx = a.tn[e], ny = a.tn[NE + e], nz = a.tn[2 * NE + e];
+  const double c = 1.0 + nx * tx + ny * ty + nz * tz;
+  if (!(c > 1e-12)) {  // edge reversed within one step: transport undefined
+    atomicMax(&a.sys_status[s], (int)DM_ERR_DEGENERATE);
+    return;
+  }
+  // time-parallel transport of d1 from t_n to t (d1 normal to t_n)
+  const double px = a.d1n[e], py = a.d1n[NE + e], pz = a.d1n[2 * NE + e];
+  const double k = (px * tx + py * ty + pz * tz) / c;
+  const double d1x = px - k * (nx + tx), d1y = py - k * (ny + ty), d1z = pz - k * (nz + tz);
+  const double d2x = ty * d1z - tz * d1y, d2y = tz * d1x - tx * d1z, d2z = tx * d1y - ty * d1x;
+  double sn, cs;
+  sincos(a.q[a.edge_th[e]], &sn, &cs);
+  double *o = a.ef;
+  o[0 * NE + e] = tx;
+  o[1 * NE + e] = ty;
+  o[2 * NE + e] = tz;
+  o[3 * NE + e] = il;
+  o[4 * NE + e] = d1x;
+  o[5 * NE + e] = d1y;
+  o[6 * NE + e] = d1z;
+  o[7 * NE + e] = cs * d1x + sn * d2x;   // m1
+  o[8 * NE + e] = cs * d1y + sn * d2y;
+  o[9 * NE + e] = cs * d1z + sn * d2z;
+  o[10 * NE + e] = -sn * d1x + cs * d2x; // m2
+  o[11 * NE + e] = -sn * d1y + cs * d2y;
+  o[12 * NE + e] = -sn * d1z + cs * d2z;
+  // stretching: dE/dx_b = EA (l/lbar - 1) t,
+  // Hessian block K = EA/l t t^T + EA (1/lbar - 1/l) I
+  const double EA = a.edge_EA[e], ilb = 1.0 / a.edge_lbar[e];
+  const double fm = EA * (l * ilb - 1.0);
+  const double al = EA * (ilb - il), be = EA * il;
+  double *w = a.es;
+  w[0 * NE + e] = fm * tx;
+  w[1 * NE + e] = fm * ty;
+  w[2 * NE + e] = fm * tz;
+  w[3 * NE + e] = fma(be * tx, tx, al);
+  w[4 * NE + e] = be * tx * ty;
+  w[5 * NE + e] = be * tx * tz;
+  w[6 * NE + e] = fma(be * ty, ty, al);
+  w[7 * NE + e] = be * ty * tz;
+  w[8 * NE + e] = fma(be * tz, tz, al);
+}
+
+// ---------------------------------------------------------------------------
+// small vector helpers (FP64)
+// ---------------------------------------------------------------------------
+struct v3 {
+  double x, y, z;
+};
+__device__ __forceinline__ v3 mk(double x, double y, double z) { return {x, y, z}; }
+__device__ __forceinline__ v3 operator+(v3 a, v3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ v3 operator-(v3 a, v3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ v3 operator*(double s, v3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double dot(v3 a, v3 b) { return fma(a.x, b.x, fma(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ v3 cross(v3 a, v3 b) {
+  return {fma(a.y, b.z, -a.z * b.y), fma(a.z, b.x, -a.x * b.z), fma(a.x, b.y, -a.y * b.x)};
+}
+__device__ __forceinline__ v3 axpy(double s, v3 x, v3 y) {  // s x + y
+  return {fma(s, x.x, y.x), fma(s, x.y, y.y), fma(s, x.z, y.z)};
+}
+// component access by compile-time index
+__device__ __forceinline__ double cmp(const v3 &a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
+// P_perp(t) v = v - (t.v) t
+__device__ __forceinline__ v3 perp(v3 t, v3 v) { return axpy(-dot(t, v), t, v); }
+
+// packed upper-triangle index of an n x n symmetric matrix (i <= j)
+template <int n>
+__host__ __device__ constexpr int up(int i, int j) {
+  return i * n - i * (i - 1) / 2 + (j - i);
+}
+
+// H8[blk] += s * (x y^T + y x^T) on a 3x3 diagonal block starting at o
+__device__ __forceinline__ void add_sym(double *h, int o, double s, v3 x, v3 y) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j)
+      h[up<8>(o + i, o + j)] += s * fma(cmp(x, i), cmp(y, j), cmp(y, i) * cmp(x, j));
+}
+
+__device__ __forceinline__ void load_edge(const double *ef, int NE, int e, int sgn,
+                                          v3 &t, double &il, v3 &d1, v3 &m1, v3 &m2) {
+  const double s = (double)sgn;
+  t = mk(s * ef[e], s * ef[NE + e], s * ef[2 * NE + e]);
+  il = ef[3 * NE + e];
+  d1 = mk(ef[4 * NE + e], ef[5 * NE + e], ef[6 * NE + e]);
+  m1 = mk(ef[7 * NE + e], ef[8 * NE + e], ef[9 * NE + e]);
+  m2 = mk(s * ef[10 * NE + e], s * ef[11 * NE + e], s * ef[12 * NE + e]);
+}
+
+__global__ void __launch_bounds__(128) k_stencil(StencilArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.ns) return;
+  const int sys = a.st_sys[k];
+  if (!a.sys_active[sys]) return;
+  const int NS = a.ns, NE = a.ne;
+  const int sg = a.st_sg[k];
+  const int sa = (sg & 1) ? -1 : 1, sb = (sg & 2) ? -1 : 1;
+  v3 ta, d1a, m1a, m2a, tb, d1b, m1b, m2b;
+  double ila, ilb;
+  load_edge(a.ef, NE, a.st_ed[k], sa, ta, ila, d1a, m1a, m2a);
+  load_edge(a.ef, NE, a.st_ed[NS + k], sb, tb, ilb, d1b, m1b, m2b);
+
+  // Eq. 4: curvature binormal
+  const double chi = 1.0 + dot(ta, tb);
+  if (!(chi > 1e-12)) {
+    atomicMax(&a.sys_status[sys], (int)DM_ERR_DEGENERATE);
+    return;
+  }
+  const double ichi = 1.0 / chi;
+  const v3 kb = (2.0 * ichi) * cross(ta, tb);
+  const v3 M1 = m1a + m1b, M2 = m2a + m2b;
+  // Eq. 5: material curvatures
+  const double k1 = 0.5 * dot(kb, M2);
+  const double k2 = -0.5 * dot(kb, M1);
+  // Eq. 7: reference twist, continued from the committed value
+  const v3 s_ab = ta + tb;
+  const v3 u = axpy(-dot(d1a, tb) * ichi, s_ab, d1a);
+  const double ang = atan2(dot(tb, cross(u, d1b)), dot(u, d1b));
+  const double bn = a.beta_n[k];
+  double dd = ang - bn;
+  dd -= 6.283185307179586 * rint(dd * 0.15915494309189535);
+  const double beta = bn + dd;
+  a.beta_it[k] = beta;
+  const double tha = a.q[a.st_th[k]], thb = a.q[a.st_th[NS + k]];
+  const double tau = sb * thb - sa * tha + beta;
+  const double kbs = a.st_kb[k], kts = a.st_kt[k];
+  const double c1 = kbs * (k1 - a.kbar[k]);
+  const double c2 = kbs * (k2 - a.kbar[NS + k]);
+  const double c3 = kts * (tau - a.taubar[k]);
+
+  // gradients of kappa1, kappa2, tau in (e_a, e_b, theta_a, theta_b)
+  const v3 tt = ichi * s_ab, mt1 = ichi * M1, mt2 = ichi * M2;
+  double g1[8], g2[8], g3[8];
+  {
+    v3 x;
+    x = ila * (cross(tb, mt2) - k1 * tt);
+    g1[0] = x.x; g1[1] = x.y; g1[2] = x.z;
+    x = ilb * ((-k1) * tt - cross(ta, mt2));
+    g1[3] = x.x; g1[4] = x.y; g1[5] = x.z;
+    g1[6] = -0.5 * dot(kb, m1a);
+    g1[7] = -0.5 * dot(kb, m1b);
+    x = ila * ((-k2) * tt - cross(tb, mt1));
+    g2[0] = x.x; g2[1] = x.y; g2[2] = x.z;
+    x = ilb * (cross(ta, mt1) - k2 * tt);
+    g2[3] = x.x; g2[4] = x.y; g2[5] = x.z;
+    g2[6] = -0.5 * dot(kb, m2a);
+    g2[7] = -0.5 * dot(kb, m2b);
+    g3[0] = 0.5 * ila * kb.x; g3[1] = 0.5 * ila * kb.y; g3[2] = 0.5 * ila * kb.z;
+    g3[3] = 0.5 * ilb * kb.x; g3[4] = 0.5 * ilb * kb.y; g3[5] = 0.5 * ilb * kb.z;
+    g3[6] = -1.0;
+    g3[7] = 1.0;
+  }
+  // energy gradient (8-space) and its outer-product Hessian part
+  double g8[8];
+  double h[36];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) g8[i] = fma(c1, g1[i], fma(c2, g2[i], c3 * g3[i]));
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = i; j < 8; ++j)
+      h[up<8>(i, j)] = kbs * fma(g1[i], g1[j], g2[i] * g2[j]) + kts * g3[i] * g3[j];
+
+  // second-derivative part, first in tangent space then projected
+  const v3 w = c1 * M2 - c2 * M1;
+  const double kw = dot(kb, w);
+  const double ichi2 = ichi * ichi;
+  const v3 pb = perp(ta, tb);   // P_a t_b
+  const v3 pa = perp(tb, ta);   // P_b t_a
+  // t-space gradient of E (the extension of the energy off the sphere)
+  const v3 tbxw = cross(tb, w), wxta = cross(w, ta);
+  const v3 gta = axpy(ichi, tbxw, axpy(-0.5 * kw * ichi, tb, (0.5 * c3) * kb));
+  const v3 gtb = axpy(ichi, wxta, axpy(-0.5 * kw * ichi, ta, (0.5 * c3) * kb));
+  const double tga = 0.5 * kw * ichi;  // t_a . g_ta == t_b . g_tb
+  const v3 hga = perp(ta, gta), hgb = perp(tb, gtb);
+  const v3 Pa = c1 * m2a - c2 * m1a, Pb = c1 * m2b - c2 * m1b;
+  const v3 Ra = c1 * m1a + c2 * m2a, Rb = c1 * m1b + c2 * m2b;
+  // aa block
+  {
+    const double s2 = ila * ila;
+    const v3 Xa = axpy(-ichi2, perp(ta, tbxw), axpy(0.5 * kw * ichi2, pb, (-0.25 * c3 * ichi) * kb));
+    add_sym(h, 0, s2, Xa, pb);
+    add_sym(h, 0, 0.25 * s2, perp(ta, Pa), kb);
+    add_sym(h, 0, -s2, ta, hga);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j)
+        h[up<8>(i, j)] -= s2 * tga * ((i == j ? 1.0 : 0.0) - cmp(ta, i) * cmp(ta, j));
+  }
+  // bb block
+  {
+    const double s2 = ilb * ilb;
+    const v3 Xb = axpy(-ichi2, perp(tb, wxta), axpy(0.5 * kw * ichi2, pa, (-0.25 * c3 * ichi) * kb));
+    add_sym(h, 3, s2, Xb, pa);
+    add_sym(h, 3, 0.25 * s2, perp(tb, Pb), kb);
+    add_sym(h, 3, -s2, tb, hgb);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j)
+        h[up<8>(3 + i, 3 + j)] -= s2 * tga * ((i == j ? 1.0 : 0.0) - cmp(tb, i) * cmp(tb, j));
+  }
+  // ab block: M = -ichi [w]x - ichi^2 (alpha_a t_a^T + t_b alpha_b^T)
+  //               + (kw ichi^2) t_b t_a^T - kw ichi/2 I
+  //               + c3 ichi [t_a]x - c3 ichi/2 kb t_a^T,  then P_a M P_b
+  {
+    double Mab[3][3];
+    const double ca = -0.5 * kw * ichi;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        double v = -ichi2 * fma(cmp(tbxw, i), cmp(ta, j), cmp(tb, i) * cmp(wxta, j));
+        v = fma(kw * ichi2, cmp(tb, i) * cmp(ta, j), v);
+        v = fma(-0.5 * c3 * ichi, cmp(kb, i) * cmp(ta, j), v);
+        if (i == j) v += ca;
+        Mab[i][j] = v;
+      }
+    // skew parts: -ichi [w]x + c3 ichi [t_a]x = [z]x with z = ichi (c3 t_a - w)
+    const v3 z = ichi * axpy(c3, ta, (-1.0) * w);
+    Mab[0][1] -= z.z; Mab[0][2] += z.y;
+    Mab[1][0] += z.z; Mab[1][2] -= z.x;
+    Mab[2][0] -= z.y; Mab[2][1] += z.x;
+    // P_a M P_b
+    double r[3], cc[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) r[j] = ta.x * Mab[0][j] + ta.y * Mab[1][j] + ta.z * Mab[2][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) cc[i] = Mab[i][0] * tb.x + Mab[i][1] * tb.y + Mab[i][2] * tb.z;
+    const double sc = r[0] * tb.x + r[1] * tb.y + r[2] * tb.z;
+    const double s2 = ila * ilb;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        double v = Mab[i][j] - cmp(ta, i) * r[j] - cc[i] * cmp(tb, j) + sc * cmp(ta, i) * cmp(tb, j);
+        h[up<8>(i, 3 + j)] += s2 * v;
+      }
+  }
+  // theta cross blocks: -1/2 P ga(R), ga(v) = 2 ichi (t_b x v) - (kb.v) ichi t_b,
+  //                                     gb(v) = 2 ichi (v x t_a) - (kb.v) ichi t_a
+  {
+    const double kRa = dot(kb, Ra), kRb = dot(kb, Rb);
+    v3 x;
+    x = (-0.5 * ila) * axpy(2.0 * ichi, perp(ta, cross(tb, Ra)), (-kRa * ichi) * pb);
+    h[up<8>(0, 6)] += x.x; h[up<8>(1, 6)] += x.y; h[up<8>(2, 6)] += x.z;
+    x = (-0.5 * ilb) * axpy(2.0 * ichi, perp(tb, cross(Ra, ta)), (-kRa * ichi) * pa);
+    h[up<8>(3, 6)] += x.x; h[up<8>(4, 6)] += x.y; h[up<8>(5, 6)] += x.z;
+    x = (-0.5 * ila) * axpy(2.0 * ichi, perp(ta, cross(tb, Rb)), (-kRb * ichi) * pb);
+    h[up<8>(0, 7)] += x.x; h[up<8>(1, 7)] += x.y; h[up<8>(2, 7)] += x.z;
+    x = (-0.5 * ilb) * axpy(2.0 * ichi, perp(tb, cross(Rb, ta)), (-kRb * ichi) * pa);
+    h[up<8>(3, 7)] += x.x; h[up<8>(4, 7)] += x.y; h[up<8>(5, 7)] += x.z;
+    h[up<8>(6, 6)] += -0.5 * dot(kb, Pa);
+    h[up<8>(7, 7)] += -0.5 * dot(kb, Pb);
+  }
+
+  // map (e_a, e_b, A, B) -> 11 stencil DOFs [x0, th_a, x1, th_b, x2]:
+  // x0 = -e_a, x1 = e_a - e_b, x2 = e_b, A = sa th_a, B = sb th_b
+  double *G = a.sg;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    G[(0 + c) * NS + k] = -g8[c];
+    G[(4 + c) * NS + k] = g8[c] - g8[3 + c];
+    G[(8 + c) * NS + k] = g8[3 + c];
+  }
+  G[3 * NS + k] = sa * g8[6];
+  G[7 * NS + k] = sb * g8[7];
+
+  // H11 = T^T H8 T written as packed upper triangle
+  auto H8 = [&](int i, int j) -> double { return i <= j ? h[up<8>(i, j)] : h[up<8>(j, i)]; };
+  // coefficient rows: slot -> list of (8-space index, weight)
+  double *Ho = a.sh;
+#pragma unroll
+  for (int p = 0; p < 11; ++p)
+#pragma unroll
+    for (int q = p; q < 11; ++q) {
+      // slot p combination
+      double v = 0.0;
+#pragma unroll
+      for (int tp = 0; tp < 2; ++tp)
+#pragma unroll
+        for (int tq = 0; tq < 2; ++tq) {
+          int ip, iq;
+          double wp, wq;
+          // decode slot -> (index, weight) pairs
+          if (p == 3) { ip = (tp == 0) ? 6 : -1; wp = sa; }
+          else if (p == 7) { ip = (tp == 0) ? 7 : -1; wp = sb; }
+          else if (p < 3) { ip = (tp == 0) ? p : -1; wp = -1.0; }
+          else if (p < 7) { ip = (tp == 0) ? (p - 4) : (p - 4 + 3); wp = (tp == 0) ? 1.0 : -1.0; }
+          else { ip = (tp == 0) ? (p - 8 + 3) : -1; wp = 1.0; }
+          if (q == 3) { iq = (tq == 0) ? 6 : -1; wq = sa; }
+          else if (q == 7) { iq = (tq == 0) ? 7 : -1; wq = sb; }
+          else if (q < 3) { iq = (tq == 0) ? q : -1; wq = -1.0; }
+          else if (q < 7) { iq = (tq == 0) ? (q - 4) : (q - 4 + 3); wq = (tq == 0) ? 1.0 : -1.0; }
+          else { iq = (tq == 0) ? (q - 8 + 3) : -1; wq = 1.0; }
+          if (ip >= 0 && iq >= 0) v += wp * wq * H8(ip, iq);
+        }
+      Ho[up<11>(p, q) * NS + k] = v;
+    }
+}
+
+}  // namespace dm

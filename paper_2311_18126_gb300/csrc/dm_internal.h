@@ -1,0 +1,126 @@
+// Internal declarations of the GB300 implicit DER library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dismech.h"
+
+namespace dm {
+
+// Per-thread last error message (dm_last_error).
+void set_error(const std::string &msg);
+
+// ---------------------------------------------------------------------------
+// Host-side topology (built once by dm_create_system from the descriptor)
+// ---------------------------------------------------------------------------
+enum SolverKind : int32_t {
+  SOLVE_ROD_BAND = 0, // one rod, Eq. 1 layout, half bandwidth 10
+};
+
+struct HostTopology {
+  int32_t n_rods = 0;
+  std::vector<int32_t> npr;      // nodes per rod
+  std::vector<int64_t> rod_node0, rod_edge0, rod_layout0; // flat offsets
+  // global nodes (joint members merged)
+  int64_t n_nodes = 0, n_edges = 0, n_stencils = 0, n_dofs = 0;
+  std::vector<int64_t> flat2node;      // (rod,node) flat -> node
+  std::vector<int32_t> node_dof;       // DOF index of x of each node
+  std::vector<int32_t> node_sys;
+  std::vector<double> node_mass, node_vor, node_h, node_mu, node_kc;
+  // edges (descriptor order)
+  std::vector<int32_t> edge_a, edge_b, edge_rod, edge_sys, edge_thdof;
+  std::vector<double> edge_lbar, edge_EA, edge_EI, edge_GJ, edge_rhoA, edge_h;
+  std::vector<double> d1_init, t_init;  // [Ne][3]
+  // stencils (node order, then incident edge pairs)
+  std::vector<int32_t> st_node[3], st_edge[2], st_sign[2], st_sys;
+  std::vector<int32_t> st_rod_slot; // -1 for joint stencils, else flat index
+                                     // into the per-rod interior-node list
+  std::vector<double> st_kb, st_kt, st_beta0, st_kbar1, st_kbar2, st_taubar;
+  // systems
+  int32_t n_systems = 0;
+  std::vector<int32_t> sys_kind, sys_dof0, sys_ndof;
+  std::vector<int32_t> sys_rod0, sys_nrods;
+  std::vector<int32_t> sys_st0, sys_nst, sys_edge0, sys_nedge;
+  // per-DOF data
+  std::vector<double> dof_mass, dof_rscale, q0, v0;
+  std::vector<uint8_t> dof_fixed;
+  // per-rod layout (Eq. 1) -> DOF index
+  std::vector<int32_t> layout2dof;
+  // force gather CSR: for each DOF, entries (element, local slot)
+  std::vector<int32_t> gat_ptr, gat_ent;
+};
+
+// Builds the topology; returns false with set_error() on invalid input.
+bool build_topology(const dm_system_desc *desc, const dm_params *prm,
+                    HostTopology &T);
+
+// ---------------------------------------------------------------------------
+// Device-side state
+// ---------------------------------------------------------------------------
+struct DevArrays {
+  // DOF vectors
+  double *q = nullptr, *qn = nullptr, *vn = nullptr, *f = nullptr;
+  double *mass = nullptr, *rscale = nullptr;
+  uint8_t *fixed = nullptr;
+  // nodes
+  int32_t *node_dof = nullptr;
+  double *node_mass = nullptr, *node_vor = nullptr;
+  // edges
+  int32_t *edge_a = nullptr, *edge_b = nullptr, *edge_th = nullptr,
+          *edge_sys = nullptr;
+  double *edge_lbar = nullptr, *edge_EA = nullptr;
+  double *d1n = nullptr, *tn = nullptr;  // committed frames, SoA [3][Ne]
+  // per-iteration edge outputs (SoA): t[3], len, d1[3], m1[3], m2[3]
+  double *ef = nullptr;                  // [13][Ne]
+  double *es = nullptr;                  // stretch: f[3], K[6]  [9][Ne]
+  // stencils
+  int32_t *st_nd = nullptr;   // [3][Ns] node DOF bases
+  int32_t *st_ed = nullptr;   // [2][Ns] edge ids
+  int32_t *st_th = nullptr;   // [2][Ns] theta DOF
+  int32_t *st_sg = nullptr;   // [Ns] sign bits: bit0 = a reversed, bit1 = b
+  int32_t *st_sys = nullptr;
+  double *st_kb = nullptr, *st_kt = nullptr, *kbar = nullptr /*[2][Ns]*/,
+         *taubar = nullptr, *beta_n = nullptr, *beta_it = nullptr;
+  double *sg = nullptr;       // stencil gradient [11][Ns]
+  double *sh = nullptr;       // stencil Hessian, packed upper [66][Ns]
+  // systems
+  int32_t *sys_dof0 = nullptr, *sys_ndof = nullptr, *sys_st0 = nullptr,
+          *sys_edge0 = nullptr;
+  int32_t *sys_active = nullptr;   // 1 while Newton runs on the system
+  int32_t *sys_iters = nullptr;
+  int32_t *sys_status = nullptr;
+  unsigned long long *sys_res = nullptr; // max scaled residual (double bits)
+  int32_t *ctrl = nullptr;         // [0] = number of active systems
+  // gather CSR
+  int32_t *gat_ptr = nullptr, *gat_ent = nullptr;
+  // band workspace for the rod solver: L factors [11][n_dofs]
+  double *band = nullptr;
+  double *dq = nullptr;
+  int32_t *layout2dof = nullptr;
+  // rod-solver ordering (systems sorted by size)
+  int32_t *solve_order = nullptr;
+};
+
+struct Params {
+  double dt, tol;
+  int32_t max_iter;
+  double g[3];
+  double eta;
+};
+
+}  // namespace dm
+
+struct dm_system {
+  dm::HostTopology T;
+  dm::DevArrays d;
+  dm::Params p;
+  dm_params prm;
+  cudaStream_t stream = nullptr;
+  std::vector<void *> allocations;
+  int32_t *h_ctrl = nullptr;  // pinned
+};
+

@@ -1,0 +1,72 @@
+// Kernel argument blocks and declarations (internal).
+#pragma once
+#include "dm_internal.h"
+
+namespace dm {
+
+struct EdgeArgs {
+  int ne;
+  const double *q;
+  const int32_t *edge_a, *edge_b, *edge_th, *edge_sys;
+  const double *edge_EA, *edge_lbar, *tn, *d1n;
+  const int32_t *sys_active;
+  int32_t *sys_status;
+  double *ef, *es;
+};
+
+struct StencilArgs {
+  int ns, ne;
+  const double *q, *ef;
+  const int32_t *st_ed, *st_th, *st_sg, *st_sys;
+  const double *st_kb, *st_kt, *kbar, *taubar, *beta_n;
+  const int32_t *sys_active;
+  int32_t *sys_status;
+  double *beta_it, *sg, *sh;
+};
+
+struct RowArgs {
+  int nd, ns, ne;
+  double dt, g[3], eta;
+  const double *q, *qn, *vn, *mass, *rscale, *damp;
+  const uint8_t *fixed;
+  const int32_t *dof_sys;
+  const int32_t *sys_dof0, *sys_ndof, *sys_st0, *sys_edge0;
+  const int32_t *sys_active;
+  const double *sg, *sh, *es;
+  double *f, *band;
+  unsigned long long *sys_res;
+};
+
+struct SolveArgs {
+  int nsys, nd;
+  double tol;
+  int max_iter;
+  const int32_t *order;
+  const int32_t *sys_dof0, *sys_ndof;
+  const uint8_t *fixed;
+  const double *f;
+  double *band, *q, *dq;
+  int32_t *sys_active, *sys_iters, *sys_status;
+  const unsigned long long *sys_res;
+  int32_t *ctrl;
+};
+
+__global__ void k_edge(EdgeArgs a);
+__global__ void k_stencil(StencilArgs a);
+__global__ void k_rows_rod(RowArgs a);
+__global__ void k_solve_rod(SolveArgs a);
+
+struct StepArgs {
+  int nd, ne, ns, nsys;
+  double dt;
+  double *q, *qn, *vn, *d1n, *tn, *beta_n;
+  const double *ef, *beta_it;
+  const uint8_t *fixed;
+  int32_t *sys_active, *sys_iters, *sys_status;
+  unsigned long long *sys_res;
+};
+__global__ void k_begin_step(StepArgs a);
+__global__ void k_commit(StepArgs a);
+__global__ void k_restore(StepArgs a);
+
+}  // namespace dm

@@ -1,0 +1,50 @@
+// Step bookkeeping kernels: predictor, commit and rollback (DisMech,
+// arXiv 2311.18126, Sec. III-C: q_dot_{n+1} = (q_{n+1} - q_n)/dt; Sec. III:
+// reference frames carried between steps by time-parallel transport).
+#include "dm_internal.h"
+#include "dm_kernels.cuh"
+
+namespace dm {
+
+// Start of a step: every system active, Newton guess q = q_n + dt qdot_n
+// (reading C23), fixed DOFs keep q_n.
+__global__ void k_begin_step(StepArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.nsys) {
+    a.sys_active[i] = 1;
+    a.sys_iters[i] = 0;
+    a.sys_status[i] = 0;
+    a.sys_res[i] = 0ull;
+  }
+  if (i < a.nd) a.q[i] = a.fixed[i] ? a.qn[i] : fma(a.dt, a.vn[i], a.qn[i]);
+}
+
+// Commit the converged step: velocities, then q_n, the transported reference
+// directors and tangents of every edge, and the reference twist of every
+// stencil (all computed at the converged iterate).
+__global__ void k_commit(StepArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double idt = 1.0 / a.dt;
+  if (i < a.nd) {
+    const double q = a.q[i];
+    a.vn[i] = (q - a.qn[i]) * idt;
+    a.qn[i] = q;
+  }
+  if (i < a.ne) {
+    const int NE = a.ne;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      a.tn[c * NE + i] = a.ef[c * NE + i];
+      a.d1n[c * NE + i] = a.ef[(4 + c) * NE + i];
+    }
+  }
+  if (i < a.ns) a.beta_n[i] = a.beta_it[i];
+}
+
+// Failed step: drop the iterate, the committed state is untouched.
+__global__ void k_restore(StepArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.nd) a.q[i] = a.qn[i];
+}
+
+}  // namespace dm

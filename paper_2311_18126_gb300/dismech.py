@@ -1,0 +1,270 @@
+"""Thin ctypes binding of the C ABI in ``include/dismech.h``.
+
+Argument marshalling only: every step of the implicit DER solve runs in the
+CUDA kernels of ``libdismech.so``.  Host arrays are numpy; device buffers
+are torch CUDA tensors (their data pointers are passed with is_device=1).
+The binding refuses to work without the compiled library: there is no CPU
+fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdismech.so")
+
+DM_OK = 0
+STATUS = {0: "DM_OK", 1: "DM_ERR_INVALID_ARG", 2: "DM_ERR_NOT_CONVERGED",
+          3: "DM_ERR_NONFINITE", 4: "DM_ERR_DEGENERATE", 5: "DM_ERR_PENETRATION",
+          6: "DM_ERR_CUDA", 7: "DM_ERR_OOM"}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_up = C.POINTER(C.c_uint8)
+
+
+class SystemDesc(C.Structure):
+    _fields_ = [("n_rods", C.c_int32), ("nodes_per_rod", _ip), ("x0", _dp), ("v0", _dp),
+                ("theta0", _dp), ("theta_dot0", _dp), ("E", _dp), ("nu", _dp), ("rho", _dp),
+                ("radius", _dp), ("n_joints", C.c_int32), ("joint_offsets", _ip),
+                ("joint_members", _ip), ("fixed", _up), ("ground_mu", _dp), ("ground_kc", _dp)]
+
+
+class Params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("newton_tol", C.c_double), ("max_iter", C.c_int32),
+                ("gravity", C.c_double * 3), ("damping", C.c_double), ("ground", C.c_int32),
+                ("ground_z", C.c_double), ("delta", C.c_double), ("slip_nu", C.c_double),
+                ("self_contact", C.c_int32), ("pair_kc", C.c_double), ("pair_mu", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("capacity", C.c_int32), ("iterations", _ip), ("residual", _dp),
+                ("first_failed", C.c_int32), ("steps_done", C.c_int32),
+                ("sum_iterations", C.c_int64), ("max_iterations", C.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Loads ``libdismech.so``; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libdismech.so is missing: run __graft_entry__.build() "
+                           "(no CPU fallback exists)")
+    lib = C.CDLL(path)
+    H = C.c_void_p
+    lib.dm_create_system.argtypes = [C.POINTER(SystemDesc), C.POINTER(Params), C.POINTER(H)]
+    lib.dm_create_system.restype = C.c_int
+    lib.dm_destroy.argtypes = [H]
+    lib.dm_destroy.restype = None
+    lib.dm_set_natural_curvature.argtypes = [H, C.c_int32, C.c_int32, C.c_void_p, C.c_int32]
+    lib.dm_set_natural_curvature.restype = C.c_int
+    lib.dm_step.argtypes = [H, C.c_int32, C.POINTER(StepStats)]
+    lib.dm_step.restype = C.c_int
+    lib.dm_get_state.argtypes = [H, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32]
+    lib.dm_get_state.restype = C.c_int
+    lib.dm_set_state.argtypes = [H, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32]
+    lib.dm_set_state.restype = C.c_int
+    lib.dm_get_frames.argtypes = [H, _dp, _dp]
+    lib.dm_get_frames.restype = C.c_int
+    lib.dm_set_frames.argtypes = [H, _dp, _dp]
+    lib.dm_set_frames.restype = C.c_int
+    lib.dm_state_size.argtypes = [H]
+    lib.dm_state_size.restype = C.c_int64
+    lib.dm_num_systems.argtypes = [H]
+    lib.dm_num_systems.restype = C.c_int32
+    lib.dm_num_stencils.argtypes = [H]
+    lib.dm_num_stencils.restype = C.c_int64
+    lib.dm_num_edges.argtypes = [H]
+    lib.dm_num_edges.restype = C.c_int64
+    lib.dm_last_error.argtypes = []
+    lib.dm_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+class DismechError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+def _check(code):
+    if code != DM_OK:
+        raise DismechError(code, _lib.dm_last_error().decode())
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+def _dev_ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class System:
+    """Batch of rod systems advanced by the GPU implicit DER step.
+
+    ``desc``: dict with nodes_per_rod, x0, E, nu, rho, radius and optional
+    v0, theta0, theta_dot0, joints (list of [(rod, node), ...]), fixed,
+    ground_mu, ground_kc.  ``params``: dt, tol, max_iter, g, eta, ground,
+    ground_z, delta, nu_slip, self_contact, pair_kc, pair_mu, stream.
+    """
+
+    def __init__(self, desc, params):
+        lib = load_library()
+        self._keep = []
+
+        def arr(key, dtype, shape=None):
+            v = desc.get(key)
+            if v is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(v, dtype=dtype))
+            if shape is not None:
+                a = a.reshape(shape)
+            self._keep.append(a)
+            return a
+
+        npr = arr("nodes_per_rod", np.int32)
+        d = SystemDesc()
+        d.n_rods = len(npr)
+        d.nodes_per_rod = _ptr(npr, C.c_int32)
+        d.x0 = _ptr(arr("x0", np.float64, (-1,)), C.c_double)
+        d.v0 = _ptr(arr("v0", np.float64, (-1,)), C.c_double)
+        d.theta0 = _ptr(arr("theta0", np.float64), C.c_double)
+        d.theta_dot0 = _ptr(arr("theta_dot0", np.float64), C.c_double)
+        for k in ("E", "nu", "rho", "radius"):
+            setattr(d, k, _ptr(arr(k, np.float64), C.c_double))
+        joints = desc.get("joints") or []
+        if joints:
+            off = np.zeros(len(joints) + 1, np.int32)
+            mem = []
+            for j, grp in enumerate(joints):
+                off[j + 1] = off[j] + len(grp)
+                for (r, i) in grp:
+                    mem += [r, i]
+            mem = np.asarray(mem, np.int32)
+            self._keep += [off, mem]
+            d.n_joints = len(joints)
+            d.joint_offsets = _ptr(off, C.c_int32)
+            d.joint_members = _ptr(mem, C.c_int32)
+        d.fixed = _ptr(arr("fixed", np.uint8), C.c_uint8)
+        d.ground_mu = _ptr(arr("ground_mu", np.float64), C.c_double)
+        d.ground_kc = _ptr(arr("ground_kc", np.float64), C.c_double)
+        p = Params()
+        p.dt = params.get("dt", 1e-3)
+        p.newton_tol = params.get("tol", 1e-10)
+        p.max_iter = params.get("max_iter", 100)
+        g = params.get("g", (0.0, 0.0, -9.81))
+        for c in range(3):
+            p.gravity[c] = g[c]
+        p.damping = params.get("eta", 0.0)
+        p.ground = int(bool(params.get("ground", False)))
+        p.ground_z = params.get("ground_z", 0.0)
+        p.delta = params.get("delta", 5e-4)
+        p.slip_nu = params.get("nu_slip", 1e-3)
+        p.self_contact = int(bool(params.get("self_contact", False)))
+        p.pair_kc = params.get("pair_kc", 0.0)
+        p.pair_mu = params.get("pair_mu", 0.0)
+        p.stream = params.get("stream", None)
+        h = C.c_void_p()
+        _check(lib.dm_create_system(C.byref(d), C.byref(p), C.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.n_state = lib.dm_state_size(h)
+        self.n_systems = lib.dm_num_systems(h)
+        self.n_stencils = lib.dm_num_stencils(h)
+        self.n_edges = lib.dm_num_edges(h)
+        self.n_rods = d.n_rods
+        self.stats = StepStats()
+        self._iters = np.zeros(self.n_systems, np.int32)
+        self._res = np.zeros(self.n_systems, np.float64)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps=1, stats=True):
+        st = self.stats
+        if stats:
+            st.capacity = self.n_systems
+            st.iterations = _ptr(self._iters, C.c_int32)
+            st.residual = _ptr(self._res, C.c_double)
+        else:
+            st.capacity = 0
+            st.iterations = None
+            st.residual = None
+        _check(self._lib.dm_step(self._h, nsteps, C.byref(st)))
+        return st
+
+    @property
+    def iterations(self):
+        return self._iters.copy()
+
+    @property
+    def residual(self):
+        return self._res.copy()
+
+    def set_natural_curvature(self, rod_begin, rod_end, kbar):
+        if hasattr(kbar, "data_ptr"):
+            _check(self._lib.dm_set_natural_curvature(self._h, rod_begin, rod_end,
+                                                      _dev_ptr(kbar), 1))
+        else:
+            k = np.ascontiguousarray(np.asarray(kbar, np.float64).reshape(-1))
+            _check(self._lib.dm_set_natural_curvature(self._h, rod_begin, rod_end,
+                                                      k.ctypes.data_as(C.c_void_p), 0))
+
+    def get_state(self, q=None, qdot=None):
+        """Host copy (numpy) unless torch CUDA tensors are given."""
+        if q is not None and hasattr(q, "data_ptr"):
+            _check(self._lib.dm_get_state(self._h, _dev_ptr(q),
+                                          _dev_ptr(qdot) if qdot is not None else None,
+                                          self.n_state, 1))
+            return q, qdot
+        q = np.zeros(self.n_state)
+        v = np.zeros(self.n_state)
+        _check(self._lib.dm_get_state(self._h, q.ctypes.data_as(C.c_void_p),
+                                      v.ctypes.data_as(C.c_void_p), self.n_state, 0))
+        return q, v
+
+    def set_state(self, q, qdot):
+        if hasattr(q, "data_ptr"):
+            _check(self._lib.dm_set_state(self._h, _dev_ptr(q), _dev_ptr(qdot),
+                                          self.n_state, 1))
+            return
+        q = np.ascontiguousarray(np.asarray(q, np.float64))
+        v = np.ascontiguousarray(np.asarray(qdot, np.float64))
+        _check(self._lib.dm_set_state(self._h, q.ctypes.data_as(C.c_void_p),
+                                      v.ctypes.data_as(C.c_void_p), len(q), 0))
+
+    def get_frames(self):
+        d1 = np.zeros((self.n_edges, 3))
+        beta = np.zeros(self.n_stencils)
+        _check(self._lib.dm_get_frames(self._h, _ptr(d1, C.c_double), _ptr(beta, C.c_double)))
+        return d1, beta
+
+    def set_frames(self, d1, beta):
+        d1 = np.ascontiguousarray(np.asarray(d1, np.float64))
+        beta = np.ascontiguousarray(np.asarray(beta, np.float64))
+        _check(self._lib.dm_set_frames(self._h, _ptr(d1, C.c_double), _ptr(beta, C.c_double)))
+
+
+def ensure_built():
+    """Compiles the library if it is missing (used by tests and tools)."""
+    if not os.path.exists(LIB_PATH):
+        _build.build()
+    return load_library()
