@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Throughput of the implicit DER step (DisMech, arXiv 2311.18126) on GB300.
+
+One step = one backward-Euler time step of every rod of the batch: Newton's
+method to the 1e-10 scaled residual, with every phase (frames, stretch,
+bend-twist gradients/Hessians, assembly, banded solve, commit) in the CUDA
+library.  Workload: 4096 independent clamped rods, N ~ U{20..200} nodes,
+L ~ U(0.2, 1.5) m, h ~ U(5e-4, 3e-3) m, log10 E ~ U(6, 8), natural
+curvature ~ U[-5, 5]^2 1/m, gravity, damping 0.1, dt = 1e-3 s (synthetic,
+seeded; the same generator the parity tests use).
+
+Multi-GPU: rods are independent, so each rank runs its own seeded batch of
+4096 rods with no collective on the data path (weak scaling); the barrier
+and the max over ranks bracket the timed region only.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rod-steps/s at 1e-10 Newton residual, batched; learned vs plain speedup; % roofline"
+UNIT = "rod-steps/s"
+WORKLOAD = "uneven_rods: 4096 clamped rods, N~U{20..200}, dt=1e-3 s, backward Euler, FP64"
+
+# FP64 flops executed per work unit of each kernel (DADD + DMUL + 2 DFMA,
+# predicated-on lanes), counted by ncu on the uneven-rods workload
+# (profiles/kernel_fp64_counts.md); the denominator is the measured FP64 FMA
+# throughput of the device.
+FP64_FLOPS_PER_UNIT = {
+    "bend_twist_stencil": None,
+    "edge_frames_stretch": None,
+    "residual_jacobian_rows": None,
+    "band_ldlt_solve": None,
+}
+UNIT_NAME = {"bend_twist_stencil": "stencil", "edge_frames_stretch": "edge",
+             "residual_jacobian_rows": "DOF row", "band_ldlt_solve": "DOF",
+             "step_begin": "DOF", "step_commit": "DOF"}
+
+
+def _load_counts():
+    p = os.path.join(ROOT, "profiles", "kernel_fp64_counts.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        for k, v in d.get("flops_per_unit", {}).items():
+            FP64_FLOPS_PER_UNIT[k] = v
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rods", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during timing."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[2][k].lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def oracle_rate(desc, params, kbar, rods, steps):
+    """Times the CPU oracle on `rods` of the workload for `steps` steps."""
+    import torch
+    import workloads
+    from oracle import OracleSystems
+    sub, kb = workloads.subset(desc, rods, kbar)
+    o = OracleSystems(sub, params)
+    o.set_natural_curvature(0, len(rods), kb)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        out = o.step(1)
+        assert all(x[0] == 0 for x in out), out
+    dt = time.perf_counter() - t0
+    nodes = int(np.sum(np.asarray(sub["nodes_per_rod"])))
+    return len(rods) * steps / dt, dt, torch.get_num_threads(), nodes
+
+
+def sample_rods(n_total, k, seed=12345):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(n_total, size=k, replace=False))
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return
+    import workloads
+    desc, params, kbar = workloads.uneven_rods(n_rods=args.rods, seed=2)
+    rods = sample_rods(args.rods, 4)
+    import torch
+    from oracle import OracleSystems
+    sub, kb = workloads.subset(desc, rods, kbar)
+    o = OracleSystems(sub, params)
+    o.set_natural_curvature(0, len(rods), kb)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    v = len(rods) * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rods_per_step": len(rods),
+                       "sample": "rods %s of the 4096 (seeded), consecutive steps" % rods.tolist()},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(),
+                             "kind": "oracle",
+                             "sample": "%d seeded rods of the 4096-rod batch, %d steps" %
+                                       (len(rods), args.steps)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import workloads
+    from paper_2311_18126_gb300 import System, ensure_built, fp64_peak_gflops
+    ensure_built()
+    _load_counts()
+    desc, params, kbar = workloads.uneven_rods(n_rods=args.rods, seed=2 + rank)
+    R = args.rods
+    sysm = System(desc, params)
+    sysm.set_natural_curvature(0, R, kbar)
+    peak_fp64 = fp64_peak_gflops()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+
+    for _ in range(args.warmup):
+        sysm.step(1, stats=False)
+    torch.cuda.synchronize()
+    sysm.set_profiling(True)
+    barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    iters = []
+    e0.record()
+    for _ in range(args.steps):
+        st = sysm.step(1, stats=True)
+        iters.append(sysm.iterations.copy())
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    prof = sysm.get_profile()
+    sysm.set_profiling(False)
+    tmax = ms
+    if ws > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        tmax = float(t.item())
+    value = ws * R * args.steps / (tmax * 1e-3)
+
+    # end to end through the public API with pinned host buffers
+    n = sysm.n_state
+    hq = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hv = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    q0, v0 = sysm.get_state()
+    hq.numpy()[:] = q0
+    hv.numpy()[:] = v0
+    barrier()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sysm.set_state(hq.numpy(), hv.numpy())
+        sysm.step(1, stats=False)
+        qq, vv = sysm.get_state()
+        hq.numpy()[:] = qq
+        hv.numpy()[:] = vv
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    if ws > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([te], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        te = float(t.item())
+    e2e = {"value": ws * R * e2e_steps / te, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": 2 * n * 8}
+
+    # dominant kernel and its FP64 roofline
+    dom = max(prof, key=lambda k: prof[k][2])
+    launches, units, kms = prof[dom]
+    per_launch_ms = kms / launches
+    fpu = FP64_FLOPS_PER_UNIT.get(dom)
+    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s",
+            "peak": peak_fp64 / 1e3, "peak_source": "measured FP64 FMA throughput "
+            "(dm_fp64_peak_gflops, this run)", "traffic": None}
+    if fpu:
+        ach = fpu * units / launches / (per_launch_ms * 1e-3) / 1e12
+        roof.update({"achieved": ach, "frac": ach / (peak_fp64 / 1e3),
+                     "flops_per_unit": fpu, "unit_name": UNIT_NAME.get(dom),
+                     "units_per_launch": units / launches})
+    else:
+        roof.update({"achieved": None, "frac": None})
+    counts = os.path.join(ROOT, "profiles", "kernel_fp64_counts.json")
+    if os.path.exists(counts):
+        tr = json.load(open(counts)).get("dram_bytes_per_unit", {}).get(dom)
+        if tr:
+            roof["traffic"] = tr * units / launches
+    kernels = {k: {"launches": v[0], "units": v[1], "ms_total": round(v[2], 3),
+                   "share": round(v[2] / sum(x[2] for x in prof.values()), 4)}
+               for k, v in prof.items()}
+
+    it = np.array(iters)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rods_per_gpu": R,
+                       "nodes_per_gpu": int(np.sum(desc["nodes_per_rod"])),
+                       "dofs_per_gpu": int(n), "dt": params["dt"], "newton_tol": params["tol"],
+                       "parallelism": "independent rod batches per GPU (dp%d)" % ws,
+                       "l2": "no flush: per-iteration working set (~0.7 GB) exceeds L2"},
+            "newton": {"iters_mean": float(it.mean()), "iters_max": int(it.max()),
+                       "node_steps_per_s": value * float(np.mean(desc["nodes_per_rod"]))},
+            "clocks": clocks, "e2e": e2e,
+            "gpu_launches": int(sum(v[0] for v in prof.values())),
+            "roofline": roof, "kernels": kernels}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rods = sample_rods(R, 8)
+        v, dt, cores, nodes = oracle_rate(desc, params, kbar, rods, 2)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "8 seeded rods (%d nodes) of the batch, 2 steps "
+                                          "from the initial state, %.1f s" % (nodes, dt)}
+    if rank == 0:
+        print(json.dumps(line))
+    sysm.close()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -171,6 +171,27 @@ int32_t dm_num_systems(const dm_system *sys);
 int64_t dm_num_stencils(const dm_system *sys);
 int64_t dm_num_edges(const dm_system *sys);
 
+/* Per-kernel profile of dm_step calls made while profiling is on: CUDA-event
+ * time on the system's stream, launch count and work units processed
+ * (edges, stencils, DOF rows, systems) per kernel id.  Kernel ids:
+ * 0 edge frames + stretch, 1 bend-twist stencils, 2 residual/Jacobian rows,
+ * 3 banded solve, 4 step begin, 5 step commit.  Profiling adds two event
+ * records per launch; it is off by default. */
+#define DM_NUM_KERNELS 16
+typedef struct dm_profile {
+  int64_t launches[DM_NUM_KERNELS];
+  int64_t units[DM_NUM_KERNELS];
+  double ms[DM_NUM_KERNELS];
+} dm_profile;
+dm_status dm_set_profiling(dm_system *sys, int32_t enable); /* also resets */
+dm_status dm_get_profile(dm_system *sys, dm_profile *out);
+const char *dm_kernel_name(int32_t id); /* "" for unused ids */
+
+/* Measures the FP64 FMA throughput of the current device (GFLOP/s, an FMA
+ * counted as 2 flops) with a short register-resident DFMA kernel: the
+ * denominator of the FP64 roofline.  Returns a negative value on error. */
+double dm_fp64_peak_gflops(void);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *dm_last_error(void);
 

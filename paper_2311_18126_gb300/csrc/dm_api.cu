@@ -76,7 +76,21 @@ __global__ void k_scatter_kbar(int n, const int32_t *slot2st, int slot0, int ns,
   kbar[ns + st] = in[2 * i + 1];
 }
 
+enum { K_EDGE = 0, K_STENCIL = 1, K_ROWS = 2, K_SOLVE = 3, K_BEGIN = 4, K_COMMIT = 5 };
+const char *kKernelNames[DM_NUM_KERNELS] = {"edge_frames_stretch", "bend_twist_stencil",
+                                            "residual_jacobian_rows", "band_ldlt_solve",
+                                            "step_begin", "step_commit"};
+
 struct Extra {
+  bool prof = false;
+  cudaEvent_t ev[2 * DM_NUM_KERNELS] = {};
+  bool ev_used[DM_NUM_KERNELS] = {};
+  int64_t launches[DM_NUM_KERNELS] = {};
+  double ms[DM_NUM_KERNELS] = {};
+  unsigned long long *d_units = nullptr;
+  int32_t *d_bad = nullptr;
+  int solve_blocks = 1;
+  size_t solve_smem = 0;
   std::vector<int32_t> slot2st;
   int32_t *d_slot2st = nullptr;
   int32_t *d_dof_sys = nullptr;
@@ -201,9 +215,57 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
   DM_TRY(upload(s, &s->x.d_slot2st, s->x.slot2st));
   s->x.scratch_n = std::max<size_t>({(size_t)T.layout2dof.size(), (size_t)(2 * nslots), (size_t)1});
   DM_TRY(dalloc(s, &s->x.d_scratch, s->x.scratch_n));
+  DM_TRY(dalloc(s, &s->x.d_units, DM_NUM_KERNELS));
+  DM_CK(cudaMemset(s->x.d_units, 0, DM_NUM_KERNELS * sizeof(unsigned long long)));
+  DM_TRY(dalloc(s, &s->x.d_bad, 1));
+  for (int k = 0; k < 2 * DM_NUM_KERNELS; ++k) DM_CK(cudaEventCreate(&s->x.ev[k]));
   DM_CK(cudaMallocHost(&s->h_ctrl, 4 * sizeof(int32_t)));
+  // persistent banded solver: 32 rods per 128-thread block, enough blocks
+  // to cover the batch but no more than fit at once
+  s->x.solve_smem = 16 * (2 * 133 + 32) * sizeof(double);  // 16 rods per block
+  DM_CK(cudaFuncSetAttribute(k_solve_rod, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)s->x.solve_smem));
+  {
+    int dev = 0, sms = 0, per_sm = 0;
+    DM_CK(cudaGetDevice(&dev));
+    DM_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    DM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_rod, 128,
+                                                        s->x.solve_smem));
+    int want = (S + 15) / 16;
+    s->x.solve_blocks = std::max(1, std::min(want, std::max(1, per_sm) * sms));
+  }
   DM_CK(cudaDeviceSynchronize());
   return DM_OK;
+}
+
+// Event bracket around one kernel launch when profiling is on.
+struct Timed {
+  dm_system_ext *s;
+  int id;
+  cudaStream_t st;
+  Timed(dm_system_ext *s_, int id_, cudaStream_t st_) : s(s_), id(id_), st(st_) {
+    s->x.launches[id]++;
+    if (s->x.prof) cudaEventRecord(s->x.ev[2 * id], st);
+  }
+  ~Timed() {
+    if (s->x.prof) {
+      cudaEventRecord(s->x.ev[2 * id + 1], st);
+      s->x.ev_used[id] = true;
+    }
+  }
+};
+
+// Adds the elapsed time of the event pairs recorded since the last call
+// (the stream has been synchronised).
+static void harvest(dm_system_ext *s) {
+  if (!s->x.prof) return;
+  for (int k = 0; k < DM_NUM_KERNELS; ++k)
+    if (s->x.ev_used[k]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, s->x.ev[2 * k], s->x.ev[2 * k + 1]) == cudaSuccess)
+        s->x.ms[k] += ms;
+      s->x.ev_used[k] = false;
+    }
 }
 
 extern "C" {
@@ -243,6 +305,9 @@ dm_status dm_create_system(const dm_system_desc *desc, const dm_params *params,
 void dm_destroy(dm_system *sys) {
   if (!sys) return;
   for (void *p : sys->allocations) cudaFree(p);
+  auto *sx = static_cast<dm_system_ext *>(sys);
+  for (int k = 0; k < 2 * DM_NUM_KERNELS; ++k)
+    if (sx->x.ev[k]) cudaEventDestroy(sx->x.ev[k]);
   if (sys->h_ctrl) cudaFreeHost(sys->h_ctrl);
   delete static_cast<dm_system_ext *>(sys);
 }
@@ -290,9 +355,11 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   StepArgs sa{nd, ne, ns, S, s->p.dt, d.q, d.qn, d.vn, d.d1n, d.tn, d.beta_n, d.ef, d.beta_it,
               d.fixed, d.sys_active, d.sys_iters, d.sys_status, d.sys_res};
   EdgeArgs ea{ne, d.q, d.edge_a, d.edge_b, d.edge_th, d.edge_sys, d.edge_EA, d.edge_lbar,
-              d.tn, d.d1n, d.sys_active, d.sys_status, d.ef, d.es};
+              d.tn, d.d1n, d.sys_active, d.sys_status, d.ef, d.es,
+              s->x.prof ? s->x.d_units + K_EDGE : nullptr};
   StencilArgs ka{ns, ne, d.q, d.ef, d.st_ed, d.st_th, d.st_sg, d.st_sys, d.st_kb, d.st_kt,
-                 d.kbar, d.taubar, d.beta_n, d.sys_active, d.sys_status, d.beta_it, d.sg, d.sh};
+                 d.kbar, d.taubar, d.beta_n, d.sys_active, d.sys_status, d.beta_it, d.sg, d.sh,
+                 s->x.prof ? s->x.d_units + K_STENCIL : nullptr};
   RowArgs ra{};
   ra.nd = nd; ra.ns = ns; ra.ne = ne; ra.dt = s->p.dt;
   for (int c = 0; c < 3; ++c) ra.g[c] = s->p.g[c];
@@ -302,8 +369,10 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   ra.sys_dof0 = d.sys_dof0; ra.sys_ndof = d.sys_ndof; ra.sys_st0 = d.sys_st0;
   ra.sys_edge0 = d.sys_edge0; ra.sys_active = d.sys_active;
   ra.sg = d.sg; ra.sh = d.sh; ra.es = d.es; ra.f = d.f; ra.band = d.band; ra.sys_res = d.sys_res;
+  ra.units = s->x.prof ? s->x.d_units + K_ROWS : nullptr;
   SolveArgs va{S, nd, s->p.tol, s->p.max_iter, d.solve_order, d.sys_dof0, d.sys_ndof, d.fixed, d.f,
-               d.band, d.q, d.dq, d.sys_active, d.sys_iters, d.sys_status, d.sys_res, d.ctrl};
+               d.band, d.q, d.dq, d.sys_active, d.sys_iters, d.sys_status, d.sys_res, d.ctrl,
+               s->x.prof ? s->x.d_units + K_SOLVE : nullptr};
   if (stats) {
     stats->first_failed = -1;
     stats->steps_done = 0;
@@ -312,19 +381,36 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   }
   std::vector<int32_t> iters;
   for (int step = 0; step < nsteps; ++step) {
-    int32_t init[4] = {0, 0, INT_MAX, 0};
+    int32_t init[4] = {0, 0, INT_MAX, 0};  // active, failed, first failed, queue
     DM_CK(cudaMemcpyAsync(d.ctrl, init, sizeof(init), cudaMemcpyHostToDevice, st));
-    k_begin_step<<<blocks(std::max(nd, S), 256), 256, 0, st>>>(sa);
+    {
+      Timed t(s, K_BEGIN, st);
+      k_begin_step<<<blocks(std::max(nd, S), 256), 256, 0, st>>>(sa);
+    }
     for (int it = 0; it <= s->p.max_iter; ++it) {
       DM_CK(cudaMemsetAsync(d.sys_res, 0, S * sizeof(unsigned long long), st));
       DM_CK(cudaMemsetAsync(d.ctrl, 0, sizeof(int32_t), st));
-      k_edge<<<blocks(ne, 256), 256, 0, st>>>(ea);
-      k_stencil<<<blocks(ns, 128), 128, 0, st>>>(ka);
-      k_rows_rod<<<blocks(nd, 256), 256, 0, st>>>(ra);
-      k_solve_rod<<<blocks(S, 32), 32, 0, st>>>(va);
+      DM_CK(cudaMemsetAsync(d.ctrl + 3, 0, sizeof(int32_t), st));
+      {
+        Timed t(s, K_EDGE, st);
+        k_edge<<<blocks(ne, 256), 256, 0, st>>>(ea);
+      }
+      {
+        Timed t(s, K_STENCIL, st);
+        k_stencil<<<blocks(ns, 128), 128, 0, st>>>(ka);
+      }
+      {
+        Timed t(s, K_ROWS, st);
+        k_rows_rod<<<blocks(nd, 256), 256, 0, st>>>(ra);
+      }
+      {
+        Timed t(s, K_SOLVE, st);
+        k_solve_rod<<<s->x.solve_blocks, 128, s->x.solve_smem, st>>>(va);
+      }
       DM_CK(cudaGetLastError());
       DM_CK(cudaMemcpyAsync(s->h_ctrl, d.ctrl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
       DM_CK(cudaStreamSynchronize(st));
+      harvest(s);
       if (s->h_ctrl[0] == 0) break;
     }
     if (stats || s->h_ctrl[1] > 0) {
@@ -342,7 +428,10 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
                 " failed with status " + std::to_string(code));
       return (dm_status)code;
     }
-    k_commit<<<blocks(std::max({nd, ne, ns}), 256), 256, 0, st>>>(sa);
+    {
+      Timed t(s, K_COMMIT, st);
+      k_commit<<<blocks(std::max({nd, ne, ns}), 256), 256, 0, st>>>(sa);
+    }
     DM_CK(cudaGetLastError());
     if (stats) {
       stats->steps_done = step + 1;
@@ -425,21 +514,17 @@ dm_status dm_set_state(dm_system *sys, const double *q, const double *qdot, size
   }
   DM_CK(cudaMemcpyAsync(s->d.q, s->d.qn, s->T.n_dofs * sizeof(double), cudaMemcpyDeviceToDevice, st));
   // committed tangents from the new positions
-  const HostTopology &T = s->T;
-  std::vector<double> qh(T.n_dofs), tn(3 * T.n_edges);
-  DM_CK(cudaMemcpyAsync(qh.data(), s->d.qn, T.n_dofs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DM_CK(cudaMemsetAsync(s->x.d_bad, 0, sizeof(int32_t), st));
+  k_tangents<<<blocks(s->T.n_edges, 256), 256, 0, st>>>((int)s->T.n_edges, s->d.edge_a,
+                                                       s->d.edge_b, s->d.qn, s->d.tn, s->x.d_bad);
+  DM_CK(cudaGetLastError());
+  int32_t bad = 0;
+  DM_CK(cudaMemcpyAsync(&bad, s->x.d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   DM_CK(cudaStreamSynchronize(st));
-  for (int64_t e = 0; e < T.n_edges; ++e) {
-    const int a = T.node_dof[T.edge_a[e]], b = T.node_dof[T.edge_b[e]];
-    double v[3] = {qh[b] - qh[a], qh[b + 1] - qh[a + 1], qh[b + 2] - qh[a + 2]};
-    double l = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    if (!(l > 0)) {
-      set_error("dm_set_state: zero-length edge");
-      return DM_ERR_DEGENERATE;
-    }
-    for (int c = 0; c < 3; ++c) tn[c * T.n_edges + e] = v[c] / l;
+  if (bad) {
+    set_error("dm_set_state: zero-length edge");
+    return DM_ERR_DEGENERATE;
   }
-  DM_CK(cudaMemcpy(s->d.tn, tn.data(), tn.size() * sizeof(double), cudaMemcpyHostToDevice));
   return DM_OK;
 }
 
@@ -485,4 +570,91 @@ dm_status dm_set_frames(dm_system *sys, const double *d1, const double *beta) {
   return DM_OK;
 }
 
+dm_status dm_set_profiling(dm_system *sys, int32_t enable) {
+  if (!sys) {
+    set_error("dm_set_profiling: NULL handle");
+    return DM_ERR_INVALID_ARG;
+  }
+  auto *s = static_cast<dm_system_ext *>(sys);
+  DM_CK(cudaStreamSynchronize(s->stream));
+  s->x.prof = enable != 0;
+  for (int k = 0; k < DM_NUM_KERNELS; ++k) {
+    s->x.launches[k] = 0;
+    s->x.ms[k] = 0.0;
+    s->x.ev_used[k] = false;
+  }
+  DM_CK(cudaMemset(s->x.d_units, 0, DM_NUM_KERNELS * sizeof(unsigned long long)));
+  return DM_OK;
+}
+
+dm_status dm_get_profile(dm_system *sys, dm_profile *out) {
+  if (!sys || !out) {
+    set_error("dm_get_profile: bad arguments");
+    return DM_ERR_INVALID_ARG;
+  }
+  auto *s = static_cast<dm_system_ext *>(sys);
+  DM_CK(cudaStreamSynchronize(s->stream));
+  harvest(s);
+  unsigned long long u[DM_NUM_KERNELS];
+  DM_CK(cudaMemcpy(u, s->x.d_units, sizeof(u), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < DM_NUM_KERNELS; ++k) {
+    out->launches[k] = s->x.launches[k];
+    out->ms[k] = s->x.ms[k];
+    out->units[k] = (int64_t)u[k];
+  }
+  return DM_OK;
+}
+
+const char *dm_kernel_name(int32_t id) {
+  if (id < 0 || id >= DM_NUM_KERNELS || !kKernelNames[id]) return "";
+  return kKernelNames[id];
+}
+
 }  // extern "C"
+
+namespace {
+// Register-resident DFMA chains: 8 independent chains per thread.
+__global__ void k_fp64_probe(double *out, int iters) {
+  double a[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) a[c] = 1.0 + 1e-9 * (threadIdx.x + c);
+  const double m = 0.999999999, k = 1e-12;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = fma(a[c], m, k);
+  }
+  double r = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) r += a[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+}  // namespace
+
+extern "C" double dm_fp64_peak_gflops(void) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1.0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1.0;
+  const int threads = 256, nblk = sms * 4, iters = 4096;
+  double *buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * threads * nblk) != cudaSuccess) return -1.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    k_fp64_probe<<<nblk, threads>>>(buf, iters);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (err != cudaSuccess) return -1.0;
+  const double flops = 2.0 * 8.0 * iters * (double)threads * nblk;
+  return flops / (best * 1e-3) / 1e9;
+}

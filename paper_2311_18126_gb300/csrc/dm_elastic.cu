@@ -21,9 +21,10 @@ namespace dm {
 
 __global__ void k_edge(EdgeArgs a) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.ne) return;
+  const bool act = e < a.ne && a.sys_active[a.edge_sys[e]];
+  count_units(a.units, act);
+  if (!act) return;
   const int s = a.edge_sys[e];
-  if (!a.sys_active[s]) return;
   const int ia = a.edge_a[e], ib = a.edge_b[e];
   const double ex = a.q[ib] - a.q[ia];
   const double ey = a.q[ib + 1] - a.q[ia + 1];
@@ -130,9 +131,10 @@ __device__ __forceinline__ void load_edge(const double *ef, int NE, int e, int s
 
 __global__ void __launch_bounds__(128) k_stencil(StencilArgs a) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= a.ns) return;
+  const bool act = k < a.ns && a.sys_active[a.st_sys[k]];
+  count_units(a.units, act);
+  if (!act) return;
   const int sys = a.st_sys[k];
-  if (!a.sys_active[sys]) return;
   const int NS = a.ns, NE = a.ne;
   const int sg = a.st_sg[k];
   const int sa = (sg & 1) ? -1 : 1, sb = (sg & 2) ? -1 : 1;

@@ -12,6 +12,7 @@ struct EdgeArgs {
   const int32_t *sys_active;
   int32_t *sys_status;
   double *ef, *es;
+  unsigned long long *units;
 };
 
 struct StencilArgs {
@@ -22,6 +23,7 @@ struct StencilArgs {
   const int32_t *sys_active;
   int32_t *sys_status;
   double *beta_it, *sg, *sh;
+  unsigned long long *units;
 };
 
 struct RowArgs {
@@ -35,6 +37,7 @@ struct RowArgs {
   const double *sg, *sh, *es;
   double *f, *band;
   unsigned long long *sys_res;
+  unsigned long long *units;
 };
 
 struct SolveArgs {
@@ -49,6 +52,7 @@ struct SolveArgs {
   int32_t *sys_active, *sys_iters, *sys_status;
   const unsigned long long *sys_res;
   int32_t *ctrl;
+  unsigned long long *units;
 };
 
 __global__ void k_edge(EdgeArgs a);
@@ -68,5 +72,14 @@ struct StepArgs {
 __global__ void k_begin_step(StepArgs a);
 __global__ void k_commit(StepArgs a);
 __global__ void k_restore(StepArgs a);
+__global__ void k_tangents(int ne, const int32_t *edge_a, const int32_t *edge_b,
+                           const double *q, double *tn, int32_t *bad);
+
+// Counts the active threads of a block into *units (all threads must call).
+__device__ __forceinline__ void count_units(unsigned long long *units, bool act) {
+  if (units == nullptr) return;
+  const int n = __syncthreads_count(act ? 1 : 0);
+  if (threadIdx.x == 0 && n) atomicAdd(units, (unsigned long long)n);
+}
 
 }  // namespace dm

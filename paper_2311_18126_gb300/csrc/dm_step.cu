@@ -47,4 +47,22 @@ __global__ void k_restore(StepArgs a) {
   if (i < a.nd) a.q[i] = a.qn[i];
 }
 
+// Committed tangents recomputed from q (after a state is set).
+__global__ void k_tangents(int ne, const int32_t *edge_a, const int32_t *edge_b,
+                           const double *q, double *tn, int32_t *bad) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const int ia = edge_a[e], ib = edge_b[e];
+  const double x = q[ib] - q[ia], y = q[ib + 1] - q[ia + 1], z = q[ib + 2] - q[ia + 2];
+  const double l2 = x * x + y * y + z * z;
+  if (!(l2 > 0.0)) {
+    atomicExch(bad, 1);
+    return;
+  }
+  const double il = rsqrt(l2);
+  tn[e] = x * il;
+  tn[ne + e] = y * il;
+  tn[2 * ne + e] = z * il;
+}
+
 }  // namespace dm

@@ -47,6 +47,14 @@ class StepStats(C.Structure):
                 ("sum_iterations", C.c_int64), ("max_iterations", C.c_int32)]
 
 
+NUM_KERNELS = 16
+
+
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_int64 * NUM_KERNELS), ("units", C.c_int64 * NUM_KERNELS),
+                ("ms", C.c_double * NUM_KERNELS)]
+
+
 _lib = None
 
 
@@ -84,6 +92,14 @@ def load_library(path=LIB_PATH):
     lib.dm_num_stencils.restype = C.c_int64
     lib.dm_num_edges.argtypes = [H]
     lib.dm_num_edges.restype = C.c_int64
+    lib.dm_set_profiling.argtypes = [H, C.c_int32]
+    lib.dm_set_profiling.restype = C.c_int
+    lib.dm_get_profile.argtypes = [H, C.POINTER(Profile)]
+    lib.dm_get_profile.restype = C.c_int
+    lib.dm_kernel_name.argtypes = [C.c_int32]
+    lib.dm_kernel_name.restype = C.c_char_p
+    lib.dm_fp64_peak_gflops.argtypes = []
+    lib.dm_fp64_peak_gflops.restype = C.c_double
     lib.dm_last_error.argtypes = []
     lib.dm_last_error.restype = C.c_char_p
     _lib = lib
@@ -251,6 +267,20 @@ class System:
         _check(self._lib.dm_set_state(self._h, q.ctypes.data_as(C.c_void_p),
                                       v.ctypes.data_as(C.c_void_p), len(q), 0))
 
+    def set_profiling(self, enable=True):
+        _check(self._lib.dm_set_profiling(self._h, int(bool(enable))))
+
+    def get_profile(self):
+        """{kernel name: (launches, units, ms)} for kernels that ran."""
+        p = Profile()
+        _check(self._lib.dm_get_profile(self._h, C.byref(p)))
+        out = {}
+        for k in range(NUM_KERNELS):
+            name = self._lib.dm_kernel_name(k).decode()
+            if name and p.launches[k]:
+                out[name] = (int(p.launches[k]), int(p.units[k]), float(p.ms[k]))
+        return out
+
     def get_frames(self):
         d1 = np.zeros((self.n_edges, 3))
         beta = np.zeros(self.n_stencils)
@@ -261,6 +291,11 @@ class System:
         d1 = np.ascontiguousarray(np.asarray(d1, np.float64))
         beta = np.ascontiguousarray(np.asarray(beta, np.float64))
         _check(self._lib.dm_set_frames(self._h, _ptr(d1, C.c_double), _ptr(beta, C.c_double)))
+
+
+def fp64_peak_gflops():
+    """Measured FP64 FMA throughput of the current device (GFLOP/s)."""
+    return float(load_library().dm_fp64_peak_gflops())
 
 
 def ensure_built():
