@@ -171,6 +171,23 @@ int32_t dm_num_systems(const dm_system *sys);
 int64_t dm_num_stencils(const dm_system *sys);
 int64_t dm_num_edges(const dm_system *sys);
 
+/* Solves J x = rhs for a batch of independent symmetric banded systems of
+ * half bandwidth 10 -- the Jacobian layout of a single rod in the order of
+ * Eq. 1 (Sec. III-C, Eq. 16 is solved with this kernel inside dm_step) --
+ * with the library's twisted banded LDL^T kernel (no pivoting).
+ *   nsys, sys_dof0[nsys], sys_ndof[nsys]: host arrays; system k occupies
+ *     entries [sys_dof0[k], sys_dof0[k] + sys_ndof[k]) of the vectors.
+ *   ntot: length of the vectors.
+ *   band: device, [11][ntot], band[d * ntot + i] = J[i][i - d] (the lower
+ *     band; entries reaching outside a system are ignored).  Not modified.
+ *   rhs: device [ntot]; x: device [ntot] output.  x may not alias band/rhs.
+ * Work is ordered on `stream` (NULL = default stream); the call allocates
+ * device scratch and returns after the solve has finished.  Returns
+ * DM_ERR_DEGENERATE if a pivot is zero or not finite. */
+dm_status dm_solve_band(int32_t nsys, const int32_t *sys_dof0, const int32_t *sys_ndof,
+                        int64_t ntot, const double *band, const double *rhs, double *x,
+                        void *stream);
+
 /* Per-kernel profile of dm_step calls made while profiling is on: CUDA-event
  * time on the system's stream, launch count and work units processed
  * (edges, stencils, DOF rows, systems) per kernel id.  Kernel ids:

@@ -100,6 +100,9 @@ def load_library(path=LIB_PATH):
     lib.dm_kernel_name.restype = C.c_char_p
     lib.dm_fp64_peak_gflops.argtypes = []
     lib.dm_fp64_peak_gflops.restype = C.c_double
+    lib.dm_solve_band.argtypes = [C.c_int32, _ip, _ip, C.c_int64, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]
+    lib.dm_solve_band.restype = C.c_int
     lib.dm_last_error.argtypes = []
     lib.dm_last_error.restype = C.c_char_p
     _lib = lib
@@ -291,6 +294,18 @@ class System:
         d1 = np.ascontiguousarray(np.asarray(d1, np.float64))
         beta = np.ascontiguousarray(np.asarray(beta, np.float64))
         _check(self._lib.dm_set_frames(self._h, _ptr(d1, C.c_double), _ptr(beta, C.c_double)))
+
+
+def solve_band(sys_dof0, sys_ndof, band, rhs, x, stream=None):
+    """J x = rhs for a batch of symmetric banded rod systems (half bandwidth
+    10) on the GPU.  band [11, ntot], rhs and x [ntot]: torch CUDA float64
+    tensors; sys_dof0/sys_ndof: host integer sequences."""
+    lib = load_library()
+    d0 = np.ascontiguousarray(np.asarray(sys_dof0, np.int32))
+    nd = np.ascontiguousarray(np.asarray(sys_ndof, np.int32))
+    _check(lib.dm_solve_band(len(d0), _ptr(d0, C.c_int32), _ptr(nd, C.c_int32), x.numel(),
+                             _dev_ptr(band), _dev_ptr(rhs), _dev_ptr(x), stream))
+    return x
 
 
 def fp64_peak_gflops():
