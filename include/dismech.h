@@ -188,6 +188,35 @@ dm_status dm_solve_band(int32_t nsys, const int32_t *sys_dof0, const int32_t *sy
                         int64_t ntot, const double *band, const double *rhs, double *x,
                         void *stream);
 
+/* dm_solve_band without any device allocation.
+ *
+ * Some callers cannot allocate device memory at the point where they need a
+ * solve: a real-time control loop cannot afford the device-wide
+ * synchronisation that cudaMalloc/cudaFree imply, and a process whose device
+ * memory is already reserved by another allocator (a framework's caching
+ * pool, a fixed arena) may have none left to give.  This entry point takes
+ * the same arguments and returns the same result as dm_solve_band, but keeps
+ * all of its scratch in one fixed device array inside the library, sized for
+ * DM_NOALLOC_MAX_SYSTEMS systems and DM_NOALLOC_MAX_DOFS DOFs in total
+ * (about 3.3 MiB, held on every GPU that loads the library until the process
+ * exits).  Larger batches are rejected with DM_ERR_INVALID_ARG and a message
+ * naming the limit; it calls no allocating CUDA routine.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture.
+ *  - Every call reuses the same array and leaves its contents behind; each
+ *    call re-initialises what it reads.  Calls whose work overlaps on the
+ *    GPU (other streams, other host threads) race on the array: serialise
+ *    them.
+ *  - It returns after the solve has finished, like dm_solve_band.
+ * The paper has no counterpart to this entry point. */
+#define DM_NOALLOC_MAX_SYSTEMS 2048
+#define DM_NOALLOC_MAX_DOFS 32768
+dm_status dm_solve_band_noalloc(int32_t nsys, const int32_t *sys_dof0,
+                                const int32_t *sys_ndof, int64_t ntot,
+                                const double *band, const double *rhs, double *x,
+                                void *stream);
+
 /* Per-kernel profile of dm_step calls made while profiling is on: CUDA-event
  * time on the system's stream, launch count and work units processed
  * (edges, stencils, DOF rows, systems) per kernel id.  Kernel ids:

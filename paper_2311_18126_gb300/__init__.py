@@ -4,4 +4,4 @@ The compute path is the CUDA library ``libdismech.so`` (C ABI in
 ``include/dismech.h``); ``dismech.System`` is its Python binding.
 """
 from .dismech import (System, DismechError, load_library, ensure_built,  # noqa: F401
-                      fp64_peak_gflops, solve_band)
+                      fp64_peak_gflops, solve_band, solve_band_noalloc)

@@ -103,6 +103,8 @@ def load_library(path=LIB_PATH):
     lib.dm_solve_band.argtypes = [C.c_int32, _ip, _ip, C.c_int64, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]
     lib.dm_solve_band.restype = C.c_int
+    lib.dm_solve_band_noalloc.argtypes = lib.dm_solve_band.argtypes
+    lib.dm_solve_band_noalloc.restype = C.c_int
     lib.dm_last_error.argtypes = []
     lib.dm_last_error.restype = C.c_char_p
     _lib = lib
@@ -305,6 +307,26 @@ def solve_band(sys_dof0, sys_ndof, band, rhs, x, stream=None):
     nd = np.ascontiguousarray(np.asarray(sys_ndof, np.int32))
     _check(lib.dm_solve_band(len(d0), _ptr(d0, C.c_int32), _ptr(nd, C.c_int32), x.numel(),
                              _dev_ptr(band), _dev_ptr(rhs), _dev_ptr(x), stream))
+    return x
+
+
+NOALLOC_MAX_SYSTEMS = 2048
+NOALLOC_MAX_DOFS = 32768
+
+
+def solve_band_noalloc(sys_dof0, sys_ndof, band, rhs, x, stream=None):
+    """solve_band without device allocation, for callers that cannot allocate
+    (real-time loops that cannot take cudaMalloc's device-wide
+    synchronisation, processes whose device memory belongs to another
+    allocator).  The scratch is one fixed library array of at most
+    NOALLOC_MAX_SYSTEMS systems / NOALLOC_MAX_DOFS DOFs; calls that overlap
+    on the GPU race on it."""
+    lib = load_library()
+    d0 = np.ascontiguousarray(np.asarray(sys_dof0, np.int32))
+    nd = np.ascontiguousarray(np.asarray(sys_ndof, np.int32))
+    _check(lib.dm_solve_band_noalloc(len(d0), _ptr(d0, C.c_int32), _ptr(nd, C.c_int32),
+                                     x.numel(), _dev_ptr(band), _dev_ptr(rhs), _dev_ptr(x),
+                                     stream))
     return x
 
 
