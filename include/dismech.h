@@ -100,6 +100,13 @@ typedef struct dm_params {
   int32_t self_contact; /* nonzero: edge-edge IMC contact within each system   */
   double pair_kc;       /* k_c of edge-edge contact                            */
   double pair_mu;       /* edge-edge friction coefficient                      */
+  int32_t line_search;  /* nonzero: backtracking after each Newton update: a
+                           trial point whose 2-norm of the scaled residual
+                           f_i / (D_i l_i) is not below (1 - 1e-4 alpha) times
+                           that of the last accepted iterate is pulled halfway
+                           back to it (alpha halves), at most 12 times, before
+                           it is accepted (Sec. III-C notes a line search as an
+                           optional safeguard)                                */
   void *stream;         /* cudaStream_t for all work, NULL = default stream    */
 } dm_params;
 
@@ -232,6 +239,14 @@ typedef struct dm_profile {
 dm_status dm_set_profiling(dm_system *sys, int32_t enable); /* also resets */
 dm_status dm_get_profile(dm_system *sys, dm_profile *out);
 const char *dm_kernel_name(int32_t id); /* "" for unused ids */
+
+/* Diagnostics: copies an internal device buffer of the last Newton
+ * iteration to host memory (`out`, capacity n doubles).  Names: "q" (iterate),
+ * "f" (residual, DOF order), "sg"/"sh" (stencil gradients [11][Ns] and packed
+ * Hessians [66][Ns]), "es" (stretch force/Hessian [9][Ne]), "ef" (edge frames
+ * [13][Ne]), "nt" (node contact terms [12][Nn]), "gen" (general-path matrix
+ * storage).  Synchronises the stream.  Not part of the solve. */
+dm_status dm_debug_copy(dm_system *sys, const char *name, double *out, int64_t n);
 
 /* Measures the FP64 FMA throughput of the current device (GFLOP/s, an FMA
  * counted as 2 flops) with a short register-resident DFMA kernel: the

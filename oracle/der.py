@@ -145,6 +145,22 @@ def bend_twist_energy(q11, sa, sb, ta_ref, d1a_ref, tb_ref, d1b_ref, beta_ref,
             + 0.5 * kt_stiff * (tau - taubar) ** 2)
 
 
+def time_transported_energy(q11, sa, sb, ta_n, d1a_n, tb_n, d1b_n, beta_n,
+                            kb_stiff, kt_stiff, kbar1, kbar2, taubar):
+    """Eq. 6 + Eq. 8 of one stencil as a function of its 11 DOFs alone: the
+    reference directors are those of the committed step (``d1*_n`` on the
+    committed oriented tangents ``t*_n``) carried to the current tangents by
+    time-parallel transport (Sec. III), and the reference twist is continued
+    from ``beta_n``.  Forces and Jacobians are its exact derivatives."""
+    xa, xm, xb = q11[..., 0:3], q11[..., 4:7], q11[..., 8:11]
+    ta = (xm - xa) / torch.linalg.vector_norm(xm - xa, dim=-1)[..., None]
+    tb = (xb - xm) / torch.linalg.vector_norm(xb - xm, dim=-1)[..., None]
+    d1a = parallel_transport(d1a_n, ta_n, ta)
+    d1b = parallel_transport(d1b_n, tb_n, tb)
+    return bend_twist_energy(q11, sa, sb, ta, d1a, tb, d1b, beta_n, kb_stiff,
+                             kt_stiff, kbar1, kbar2, taubar)
+
+
 def bend_energy_only(q11, sa, sb, ta_ref, d1a_ref, tb_ref, d1b_ref, beta_ref,
                      kb_stiff, kbar1, kbar2):
     k1, k2, _ = stencil_strains(q11, sa, sb, ta_ref, d1a_ref, tb_ref,

@@ -51,7 +51,7 @@ DEFAULT_PARAMS = dict(dt=1e-3, tol=1e-10, max_iter=100,
                       g=(0.0, 0.0, -9.81), eta=0.0,
                       ground=False, ground_z=0.0, delta=5e-4, nu_slip=1e-3,
                       self_contact=False, pair_kc=0.0, pair_mu=0.0,
-                      jacobian="atpoint")
+                      line_search=False)
 
 
 class _Sys:
@@ -424,12 +424,11 @@ class OracleSystems:
     # ------------------------------------------------------------------
     # forces and Jacobian at an iterate
     # ------------------------------------------------------------------
-    def forces(self, s, q, v_n, q_n, need_jac=True, mode=None):
+    def forces(self, s, q, v_n, q_n, need_jac=True):
         """Total generalized force F(q) (Eq. 9 plus external forces), the
         per-DOF sum of absolute term contributions (scale of reading C9), and
-        (optionally) dF/dq as the matrix Jint = -dF/dq (the force part of
-        Eq. 16, reading C10)."""
-        mode = mode or self.p["jacobian"]
+        (optionally) the matrix Jint = -dF/dq (the force part of Eq. 16,
+        reading C10)."""
         n = s.n
         dt = self.dt
         F = torch.zeros(n, dtype=DT)
@@ -455,23 +454,18 @@ class OracleSystems:
             g = vmap(grad(der.stretch_energy))(x6, EA, lb)
             H = vmap(hessian(der.stretch_energy))(x6, EA, lb) if need_jac else None
             scatter(s.edge_dofs6, -g, H)
-        # -- bending and twisting (Eq. 4-8), at-point gauge (reading C6)
+        # -- bending and twisting (Eq. 4-8): the energy of the configuration
+        #    q with reference frames carried from the committed step by
+        #    time-parallel transport (Sec. III), differentiated exactly
+        #    (Eq. 9, reading C6)
         if len(s.st):
-            d1 = self._time_parallel_frames(s, t)
-            sa, sb, ta, d1a, tb, d1b = self._oriented(s, t, d1)
-            if torch.any(1.0 + der.dot(ta, tb) <= 1e-12):
-                raise FloatingPointError("antiparallel edges (reading C25)")
-            beta_ref = der.reference_twist(ta, d1a, tb, d1b, s.beta)
+            _ = self._time_parallel_frames(s, t)      # checks 1 + t_n.t > 0
             q11 = q[torch.as_tensor(s.st_dofs)]
-            args = (sa, sb, ta, d1a, tb, d1b, beta_ref, _t(s.st_kb),
-                    _t(s.st_kt), s.kbar1, s.kbar2, s.taubar)
-            g = vmap(grad(der.bend_twist_energy))(q11, *args)
-            H = None
-            if need_jac:
-                if mode == "exact":
-                    H = self._exact_bend_twist_jac(s, q11, t)
-                else:
-                    H = vmap(hessian(der.bend_twist_energy))(q11, *args)
+            args = self._stencil_history(s)
+            if torch.any(1.0 + der.dot(*self._oriented_tangents(s, t)) <= 1e-12):
+                raise FloatingPointError("antiparallel edges (reading C25)")
+            g = vmap(grad(der.time_transported_energy))(q11, *args)
+            H = vmap(hessian(der.time_transported_energy))(q11, *args) if need_jac else None
             scatter(s.st_dofs, -g, H)
         # -- gravity and viscous damping (Sec. III-B misc forces, reading C8)
         nd = torch.as_tensor(s.node_dof)[:, None] + torch.arange(3)
@@ -495,42 +489,32 @@ class OracleSystems:
                 scatter(idx, Fk, Jk)
         return F, Sabs, Jint
 
-    def _exact_bend_twist_jac(self, s, q11, t):
-        """Exact derivative of the at-point bending/twisting force with the
-        reference frames carried from the committed step (time-parallel
-        transport) -- used to pin quadratic Newton convergence."""
+    def _stencil_history(self, s):
+        """Per-stencil committed data: orientation signs, oriented committed
+        tangents and reference directors, committed reference twist, and the
+        stiffnesses and natural strains."""
         sa = _t(s.st_sign[:, 0])
         sb = _t(s.st_sign[:, 1])
         ea = torch.as_tensor(s.st_el[:, 0])
         eb = torch.as_tensor(s.st_el[:, 1])
-        tan = sa[:, None] * s.tn[ea]
-        tbn = sb[:, None] * s.tn[eb]
-        d1an = s.d1[ea]
-        d1bn = s.d1[eb]
+        return (sa, sb, sa[:, None] * s.tn[ea], s.d1[ea], sb[:, None] * s.tn[eb], s.d1[eb],
+                s.beta, _t(s.st_kb), _t(s.st_kt), s.kbar1, s.kbar2, s.taubar)
 
-        def force(q11_, sa_, sb_, tan_, d1an_, tbn_, d1bn_, betan_, kb_, kt_,
-                  k1_, k2_, tb_):
-            xa, xm, xb = q11_[0:3], q11_[4:7], q11_[8:11]
-            ta = (xm - xa) / torch.linalg.vector_norm(xm - xa)
-            tb = (xb - xm) / torch.linalg.vector_norm(xb - xm)
-            d1a = der.parallel_transport(d1an_, tan_, ta)
-            d1b = der.parallel_transport(d1bn_, tbn_, tb)
-            bref = der.reference_twist(ta, d1a, tb, d1b, betan_)
-            return grad(der.bend_twist_energy)(q11_, sa_, sb_, ta, d1a, tb, d1b,
-                                               bref, kb_, kt_, k1_, k2_, tb_)
-
-        return vmap(jacfwd(force))(q11, sa, sb, tan, d1an, tbn, d1bn, s.beta,
-                                   _t(s.st_kb), _t(s.st_kt), s.kbar1, s.kbar2,
-                                   s.taubar)
+    def _oriented_tangents(self, s, t):
+        sa = _t(s.st_sign[:, 0])
+        sb = _t(s.st_sign[:, 1])
+        ea = torch.as_tensor(s.st_el[:, 0])
+        eb = torch.as_tensor(s.st_el[:, 1])
+        return sa[:, None] * t[ea], sb[:, None] * t[eb]
 
     # ------------------------------------------------------------------
     # residual, Newton, commit (Sec. III-C)
     # ------------------------------------------------------------------
-    def residual(self, s, q, q_n, v_n, need_jac=True, mode=None):
+    def residual(self, s, q, q_n, v_n, need_jac=True):
         """Eq. 15: f = M/dt ((q - q_n)/dt - q_dot_n) - F_int - F_ext, with the
         scale S of reading C9 and (optionally) J = M/dt^2 - dF/dq."""
         dt = self.dt
-        F, Sabs, Jint = self.forces(s, q, v_n, q_n, need_jac, mode)
+        F, Sabs, Jint = self.forces(s, q, v_n, q_n, need_jac)
         inert = s.mass / dt ** 2 * (q - q_n)
         mom = s.mass / dt * v_n
         f = inert - mom - F
@@ -575,13 +559,28 @@ class OracleSystems:
         q = torch.where(s.fixed, q_n, q)
         status, it = ERR_NOT_CONVERGED, 0
         res = scale = float("nan")
+        ls = bool(self.p["line_search"])
+        trial, nback, alpha, q_acc, m_acc = False, 0, 1.0, q, float("inf")
         try:
             while True:
                 f, S, _ = self.residual(s, q, q_n, v_n, need_jac=False)
                 res = float(torch.max(torch.abs(f) * s.rscale))
+                merit = float(torch.linalg.vector_norm(f * s.rscale))
                 scale = float(torch.linalg.vector_norm(f))
                 if record is not None:
                     record.append(res)
+                # backtracking (Sec. III-C optional line search): Armijo test
+                # on the 2-norm of the scaled residual, for which the Newton
+                # direction is a descent direction; a trial point without
+                # sufficient decrease moves halfway back to the last accepted
+                # iterate
+                if (ls and trial and nback < 12
+                        and not (merit <= (1.0 - 1e-4 * alpha) * m_acc)):
+                    q = 0.5 * (q + q_acc)
+                    alpha *= 0.5
+                    nback += 1
+                    continue
+                trial, nback, alpha, q_acc, m_acc = False, 0, 1.0, q, merit
                 if not math.isfinite(res):
                     status = ERR_NONFINITE
                     break
@@ -596,6 +595,7 @@ class OracleSystems:
                     status = ERR_NONFINITE
                     break
                 q = q + dq
+                trial = True
                 it += 1
         except FloatingPointError:
             status = ERR_DEGENERATE

@@ -76,10 +76,14 @@ __global__ void k_scatter_kbar(int n, const int32_t *slot2st, int slot0, int ns,
   kbar[ns + st] = in[2 * i + 1];
 }
 
-enum { K_EDGE = 0, K_STENCIL = 1, K_ROWS = 2, K_SOLVE = 3, K_BEGIN = 4, K_COMMIT = 5 };
-const char *kKernelNames[DM_NUM_KERNELS] = {"edge_frames_stretch", "bend_twist_stencil",
-                                            "residual_jacobian_rows", "band_ldlt_solve",
-                                            "step_begin", "step_commit"};
+enum {
+  K_EDGE = 0, K_STENCIL = 1, K_ROWS = 2, K_SOLVE = 3, K_BEGIN = 4, K_COMMIT = 5,
+  K_NODES = 6, K_ROWS_GEN = 7, K_ASM_GEN = 8, K_SOLVE_GEN = 9
+};
+const char *kKernelNames[DM_NUM_KERNELS] = {
+    "edge_frames_stretch", "bend_twist_stencil", "residual_jacobian_rows", "band_ldlt_solve",
+    "step_begin",          "step_commit",        "ground_contact_friction", "residual_rows_general",
+    "assemble_general",    "limb_schur_solve"};
 
 struct Extra {
   bool prof = false;
@@ -89,6 +93,10 @@ struct Extra {
   double ms[DM_NUM_KERNELS] = {};
   unsigned long long *d_units = nullptr;
   int32_t *d_bad = nullptr;
+  int32_t *d_sys_kind = nullptr;
+  int32_t *ls_action = nullptr, *ls_trial = nullptr, *ls_nback = nullptr;
+  double *ls_alpha = nullptr, *ls_racc = nullptr, *ls_qacc = nullptr, *ls_merit = nullptr;
+  int n_rod_sys = 0;
   int solve_blocks = 1;
   size_t solve_smem = 0;
   std::vector<int32_t> slot2st;
@@ -110,8 +118,12 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
                              dm_system_ext *s) {
   HostTopology &T = s->T;
   if (!build_topology(desc, prm, T)) return DM_ERR_INVALID_ARG;
-  if (prm->ground || prm->self_contact) {
-    set_error("ground and edge-edge contact are not supported by this build");
+  if (prm->self_contact) {
+    set_error("edge-edge contact is not supported by this build");
+    return DM_ERR_INVALID_ARG;
+  }
+  if (prm->ground && !(prm->delta > 0 && prm->slip_nu > 0)) {
+    set_error("ground contact needs delta > 0 and slip_nu > 0");
     return DM_ERR_INVALID_ARG;
   }
   s->prm = *prm;
@@ -200,11 +212,70 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
   DM_TRY(dalloc(s, &d.ctrl, 4));
   DM_TRY(dalloc(s, &d.band, 11 * nd));
   DM_TRY(dalloc(s, &d.dq, nd));
-  std::vector<int32_t> order(S);
-  std::iota(order.begin(), order.end(), 0);
+  std::vector<int32_t> order;
+  for (int k = 0; k < S; ++k)
+    if (T.sys_kind[k] == SOLVE_ROD_BAND) order.push_back(k);
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return T.sys_ndof[a] > T.sys_ndof[b]; });
+  s->x.n_rod_sys = (int)order.size();
   DM_TRY(upload(s, &d.solve_order, order));
+  DM_TRY(upload(s, &s->x.d_sys_kind, T.sys_kind));
+  if (prm->line_search) {
+    DM_TRY(dalloc(s, &s->x.ls_action, S));
+    DM_TRY(dalloc(s, &s->x.ls_trial, S));
+    DM_TRY(dalloc(s, &s->x.ls_nback, S));
+    DM_TRY(dalloc(s, &s->x.ls_alpha, S));
+    DM_TRY(dalloc(s, &s->x.ls_racc, S));
+    DM_TRY(dalloc(s, &s->x.ls_merit, S));
+    DM_TRY(dalloc(s, &s->x.ls_qacc, nd));
+  }
+  // general path
+  DM_TRY(upload(s, &d.dof_node, T.dof_node));
+  DM_TRY(upload(s, &d.dof_comp, T.dof_comp));
+  {
+    std::vector<double> dc(nd);
+    for (int64_t i = 0; i < nd; ++i)
+      dc[i] = T.dof_fixed[i] ? 1.0 : T.dof_mass[i] / (prm->dt * prm->dt) + damp[i];
+    DM_TRY(upload(s, &d.dconst, dc));
+  }
+  if (T.any_general) {
+    std::vector<int32_t> ndof_arr(T.n_nodes);
+    for (int64_t v = 0; v < T.n_nodes; ++v) ndof_arr[v] = T.node_dof[v];
+    DM_TRY(upload(s, &d.node_dof_arr, ndof_arr));
+    DM_TRY(upload(s, &d.node_sys, T.node_sys));
+    DM_TRY(upload(s, &d.node_h, T.node_h));
+    DM_TRY(upload(s, &d.node_mu, T.node_mu));
+    DM_TRY(upload(s, &d.node_kc, T.node_kc));
+    DM_TRY(dalloc(s, &d.nt, 12 * T.n_nodes));
+    DM_CK(cudaMemset(d.nt, 0, 12 * T.n_nodes * sizeof(double)));
+    DM_TRY(dalloc(s, &d.gen, T.gen_doubles));
+    DM_TRY(upload(s, &d.gen_sys, T.gen_sys));
+    DM_TRY(upload(s, &d.gs_limb0, T.gs_limb0));
+    DM_TRY(upload(s, &d.gs_nlimb, T.gs_nlimb));
+    DM_TRY(upload(s, &d.gs_nB, T.gs_nB));
+    DM_TRY(upload(s, &d.gs_border0, T.gs_border0));
+    DM_TRY(upload(s, &d.gs_JBB, T.gs_JBB));
+    DM_TRY(upload(s, &d.gs_rB, T.gs_rB));
+    DM_TRY(upload(s, &d.gs_S, T.gs_S));
+    DM_TRY(upload(s, &d.gs_xB, T.gs_xB));
+    DM_TRY(upload(s, &d.lb_dof0, T.lb_dof0));
+    DM_TRY(upload(s, &d.lb_n, T.lb_n));
+    DM_TRY(upload(s, &d.lb_ncr, T.lb_ncr));
+    DM_TRY(upload(s, &d.lb_cr0, T.lb_cr0));
+    DM_TRY(upload(s, &d.lb_band, T.lb_band));
+    DM_TRY(upload(s, &d.lb_piv, T.lb_piv));
+    DM_TRY(upload(s, &d.lb_C, T.lb_C));
+    DM_TRY(upload(s, &d.lb_R, T.lb_R));
+    DM_TRY(upload(s, &d.lb_Y, T.lb_Y));
+    DM_TRY(upload(s, &d.lb_y, T.lb_y));
+    DM_TRY(upload(s, &d.border_dof, T.border_dof));
+    DM_TRY(upload(s, &d.coupled_rows, T.coupled_rows));
+    DM_TRY(upload(s, &d.asm_target, T.asm_target));
+    DM_TRY(upload(s, &d.asm_ptr, T.asm_ptr));
+    DM_TRY(upload(s, &d.asm_src, T.asm_src));
+    DM_TRY(upload(s, &d.gat_ptr, T.gat_ptr));
+    DM_TRY(upload(s, &d.gat_ent, T.gat_ent));
+  }
   DM_TRY(upload(s, &d.layout2dof, T.layout2dof));
   // natural-curvature slots -> stencils
   int64_t nslots = 0;
@@ -231,7 +302,7 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     DM_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     DM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_rod, 128,
                                                         s->x.solve_smem));
-    int want = (S + 15) / 16;
+    int want = (s->x.n_rod_sys + 15) / 16;
     s->x.solve_blocks = std::max(1, std::min(want, std::max(1, per_sm) * sms));
   }
   DM_CK(cudaDeviceSynchronize());
@@ -357,7 +428,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   EdgeArgs ea{ne, d.q, d.edge_a, d.edge_b, d.edge_th, d.edge_sys, d.edge_EA, d.edge_lbar,
               d.tn, d.d1n, d.sys_active, d.sys_status, d.ef, d.es,
               s->x.prof ? s->x.d_units + K_EDGE : nullptr};
-  StencilArgs ka{ns, ne, d.q, d.ef, d.st_ed, d.st_th, d.st_sg, d.st_sys, d.st_kb, d.st_kt,
+  StencilArgs ka{ns, ne, d.q, d.ef, d.tn, d.st_ed, d.st_th, d.st_sg, d.st_sys, d.st_kb, d.st_kt,
                  d.kbar, d.taubar, d.beta_n, d.sys_active, d.sys_status, d.beta_it, d.sg, d.sh,
                  s->x.prof ? s->x.d_units + K_STENCIL : nullptr};
   RowArgs ra{};
@@ -367,12 +438,44 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   ra.q = d.q; ra.qn = d.qn; ra.vn = d.vn; ra.mass = d.mass; ra.rscale = d.rscale;
   ra.damp = s->x.d_damp; ra.fixed = d.fixed; ra.dof_sys = s->x.d_dof_sys;
   ra.sys_dof0 = d.sys_dof0; ra.sys_ndof = d.sys_ndof; ra.sys_st0 = d.sys_st0;
-  ra.sys_edge0 = d.sys_edge0; ra.sys_active = d.sys_active;
+  ra.sys_edge0 = d.sys_edge0; ra.sys_active = d.sys_active; ra.sys_kind = s->x.d_sys_kind;
   ra.sg = d.sg; ra.sh = d.sh; ra.es = d.es; ra.f = d.f; ra.band = d.band; ra.sys_res = d.sys_res;
   ra.units = s->x.prof ? s->x.d_units + K_ROWS : nullptr;
-  SolveArgs va{S, nd, s->p.tol, s->p.max_iter, d.solve_order, d.sys_dof0, d.sys_ndof, d.fixed, d.f,
+  SolveArgs va{s->x.n_rod_sys, nd, s->p.tol, s->p.max_iter, d.solve_order, d.sys_dof0, d.sys_ndof, d.fixed, d.f,
                d.band, d.q, d.dq, d.sys_active, d.sys_iters, d.sys_status, d.sys_res, d.ctrl,
-               s->x.prof ? s->x.d_units + K_SOLVE : nullptr};
+               s->x.prof ? s->x.d_units + K_SOLVE : nullptr, s->x.ls_action, s->x.ls_trial};
+  const int nn = (int)T.n_nodes;
+  NodeArgs na{nn, s->p.dt, s->prm.ground_z, s->prm.delta, s->prm.slip_nu, d.q, d.qn,
+              d.node_dof_arr, d.node_sys, d.node_h, d.node_mu, d.node_kc, d.sys_active, d.nt};
+  RowGenArgs rg{};
+  rg.nd = nd; rg.ns = ns; rg.ne = ne; rg.nn = nn; rg.dt = s->p.dt;
+  for (int c = 0; c < 3; ++c) rg.g[c] = s->p.g[c];
+  rg.q = d.q; rg.qn = d.qn; rg.vn = d.vn; rg.mass = d.mass; rg.rscale = d.rscale;
+  rg.damp = s->x.d_damp; rg.fixed = d.fixed; rg.dof_sys = s->x.d_dof_sys; rg.dof_node = d.dof_node;
+  rg.dof_comp = d.dof_comp; rg.sys_kind = s->x.d_sys_kind; rg.sys_active = d.sys_active;
+  rg.gat_ptr = d.gat_ptr; rg.gat_ent = d.gat_ent; rg.sg = d.sg; rg.es = d.es;
+  rg.nt = T.ground ? d.nt : nullptr; rg.f = d.f; rg.sys_res = d.sys_res;
+  AsmArgs aa{(int)T.asm_target.size(), d.asm_target, d.asm_ptr, d.asm_src, d.sh, d.es, d.nt,
+             d.dconst, d.gen};
+  SolveGenArgs ga{};
+  ga.ngen = (int)T.gen_sys.size(); ga.max_iter = s->p.max_iter; ga.tol = s->p.tol;
+  ga.gen_sys = d.gen_sys; ga.gs_limb0 = d.gs_limb0; ga.gs_nlimb = d.gs_nlimb; ga.gs_nB = d.gs_nB;
+  ga.gs_border0 = d.gs_border0; ga.gs_JBB = d.gs_JBB; ga.gs_rB = d.gs_rB; ga.gs_S = d.gs_S;
+  ga.gs_xB = d.gs_xB; ga.lb_dof0 = d.lb_dof0; ga.lb_n = d.lb_n; ga.lb_ncr = d.lb_ncr;
+  ga.lb_cr0 = d.lb_cr0; ga.lb_band = d.lb_band; ga.lb_piv = d.lb_piv; ga.lb_C = d.lb_C; ga.lb_R = d.lb_R;
+  ga.lb_Y = d.lb_Y; ga.lb_y = d.lb_y; ga.border_dof = d.border_dof;
+  ga.coupled_rows = d.coupled_rows; ga.f = d.f; ga.gen = d.gen; ga.q = d.q;
+  ga.sys_active = d.sys_active; ga.sys_iters = d.sys_iters; ga.sys_status = d.sys_status;
+  ga.sys_res = d.sys_res; ga.ctrl = d.ctrl;
+  ga.units = s->x.prof ? s->x.d_units + K_SOLVE_GEN : nullptr;
+  ga.ls_action = s->x.ls_action;
+  ga.ls_trial = s->x.ls_trial;
+  LineSearchArgs la{S, nd, d.sys_active, s->x.d_dof_sys, d.sys_dof0, d.sys_ndof, d.f, d.rscale,
+                    s->x.ls_action, s->x.ls_trial, s->x.ls_nback, s->x.ls_alpha, s->x.ls_racc,
+                    s->x.ls_merit, d.q, s->x.ls_qacc};
+  const bool ls_on = s->prm.line_search != 0;
+  const int max_rounds = ls_on ? 13 * (s->p.max_iter + 1) : s->p.max_iter + 1;
+  const bool gen_on = T.any_general, rod_on = s->x.n_rod_sys > 0;
   if (stats) {
     stats->first_failed = -1;
     stats->steps_done = 0;
@@ -387,7 +490,11 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       Timed t(s, K_BEGIN, st);
       k_begin_step<<<blocks(std::max(nd, S), 256), 256, 0, st>>>(sa);
     }
-    for (int it = 0; it <= s->p.max_iter; ++it) {
+    if (ls_on) {
+      DM_CK(cudaMemsetAsync(s->x.ls_trial, 0, S * sizeof(int32_t), st));
+      DM_CK(cudaMemsetAsync(s->x.ls_nback, 0, S * sizeof(int32_t), st));
+    }
+    for (int it = 0; it < max_rounds; ++it) {
       DM_CK(cudaMemsetAsync(d.sys_res, 0, S * sizeof(unsigned long long), st));
       DM_CK(cudaMemsetAsync(d.ctrl, 0, sizeof(int32_t), st));
       DM_CK(cudaMemsetAsync(d.ctrl + 3, 0, sizeof(int32_t), st));
@@ -395,17 +502,43 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
         Timed t(s, K_EDGE, st);
         k_edge<<<blocks(ne, 256), 256, 0, st>>>(ea);
       }
-      {
+      if (T.ground) {
+        Timed t(s, K_NODES, st);
+        k_nodes<<<blocks(nn, 256), 256, 0, st>>>(na);
+      }
+      if (ns > 0) {
         Timed t(s, K_STENCIL, st);
         k_stencil<<<blocks(ns, 128), 128, 0, st>>>(ka);
       }
-      {
+      if (rod_on) {
         Timed t(s, K_ROWS, st);
         k_rows_rod<<<blocks(nd, 256), 256, 0, st>>>(ra);
       }
-      {
-        Timed t(s, K_SOLVE, st);
-        k_solve_rod<<<s->x.solve_blocks, 128, s->x.solve_smem, st>>>(va);
+      if (gen_on) {
+        Timed t(s, K_ROWS_GEN, st);
+        k_rows_gen<<<blocks(nd, 256), 256, 0, st>>>(rg);
+      }
+      if (ls_on) {
+        k_ls_merit<<<blocks((int64_t)S * 32, 128), 128, 0, st>>>(la);
+        k_ls_decide<<<blocks(S, 128), 128, 0, st>>>(la);
+        k_ls_apply<<<blocks(nd, 256), 256, 0, st>>>(la);
+      }
+      if (rod_on) {
+        {
+          Timed t(s, K_SOLVE, st);
+          k_solve_rod<<<s->x.solve_blocks, 128, s->x.solve_smem, st>>>(va);
+        }
+      }
+      if (gen_on) {
+        DM_CK(cudaMemsetAsync(d.gen, 0, T.gen_doubles * sizeof(double), st));
+        if (aa.ntarget > 0) {
+          Timed t(s, K_ASM_GEN, st);
+          k_assemble_gen<<<blocks(aa.ntarget, 256), 256, 0, st>>>(aa);
+        }
+        {
+          Timed t(s, K_SOLVE_GEN, st);
+          k_solve_gen<<<blocks((int64_t)ga.ngen * 32, 128), 128, 0, st>>>(ga);
+        }
       }
       DM_CK(cudaGetLastError());
       DM_CK(cudaMemcpyAsync(s->h_ctrl, d.ctrl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -419,6 +552,16 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       DM_CK(cudaStreamSynchronize(st));
     }
     if (s->h_ctrl[1] > 0) {
+      if (stats) {
+        const int nsys = std::min(stats->capacity, S);
+        if (stats->iterations && nsys > 0)
+          DM_CK(cudaMemcpyAsync(stats->iterations, d.sys_iters, nsys * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, st));
+        if (stats->residual && nsys > 0)
+          DM_CK(cudaMemcpyAsync(stats->residual, d.sys_res, nsys * sizeof(double),
+                                cudaMemcpyDeviceToHost, st));
+        DM_CK(cudaStreamSynchronize(st));
+      }
       k_restore<<<blocks(nd, 256), 256, 0, st>>>(sa);
       int32_t first = s->h_ctrl[2], code = 0;
       DM_CK(cudaMemcpyAsync(&code, d.sys_status + first, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -602,6 +745,37 @@ dm_status dm_get_profile(dm_system *sys, dm_profile *out) {
     out->ms[k] = s->x.ms[k];
     out->units[k] = (int64_t)u[k];
   }
+  return DM_OK;
+}
+
+dm_status dm_debug_copy(dm_system *sys, const char *name, double *out, int64_t n) {
+  if (!sys || !name || !out) {
+    set_error("dm_debug_copy: bad arguments");
+    return DM_ERR_INVALID_ARG;
+  }
+  const HostTopology &T = sys->T;
+  const DevArrays &d = sys->d;
+  const std::string k(name);
+  const double *src = nullptr;
+  int64_t len = 0;
+  if (k == "gen") { src = d.gen; len = T.gen_doubles; }
+  else if (k == "f") { src = d.f; len = T.n_dofs; }
+  else if (k == "q") { src = d.q; len = T.n_dofs; }
+  else if (k == "nt") { src = d.nt; len = T.any_general ? 12 * T.n_nodes : 0; }
+  else if (k == "sg") { src = d.sg; len = 11 * T.n_stencils; }
+  else if (k == "sh") { src = d.sh; len = 66 * T.n_stencils; }
+  else if (k == "es") { src = d.es; len = 9 * T.n_edges; }
+  else if (k == "ef") { src = d.ef; len = 13 * T.n_edges; }
+  else {
+    set_error("dm_debug_copy: unknown buffer " + k);
+    return DM_ERR_INVALID_ARG;
+  }
+  if (n < len || !src) {
+    set_error("dm_debug_copy: buffer " + k + " needs " + std::to_string(len) + " doubles");
+    return DM_ERR_INVALID_ARG;
+  }
+  DM_CK(cudaStreamSynchronize(sys->stream));
+  DM_CK(cudaMemcpy(out, src, len * sizeof(double), cudaMemcpyDeviceToHost));
   return DM_OK;
 }
 

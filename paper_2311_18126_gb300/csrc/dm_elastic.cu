@@ -7,9 +7,12 @@
 //                (Eq. 4), material curvatures (Eq. 5), reference twist and
 //                twist (Eq. 7), and the gradient and Hessian of
 //                1/2 EI/V |kappa - kappabar|^2 + 1/2 GJ/V (tau - taubar)^2
-//                (Eq. 6, 8) in closed form, in the at-point gauge: the
-//                derivatives are taken with the reference frames carried by
-//                parallel transport from the current iterate.
+//                (Eq. 6, 8) in closed form: first in the at-point gauge
+//                (reference frames carried by parallel transport from the
+//                current iterate), then corrected by the holonomy of the
+//                time-parallel transport so that they are the exact
+//                derivatives of the energy whose frames are carried from the
+//                committed step.
 //
 // The GB300 FP64 pipe is narrow (about 1 TFLOP/s) and charges a full warp
 // slot for every FP64 instruction whatever its active mask, so each thread
@@ -296,6 +299,79 @@ __global__ void __launch_bounds__(128) k_stencil(StencilArgs a) {
     h[up<8>(3, 7)] += x.x; h[up<8>(4, 7)] += x.y; h[up<8>(5, 7)] += x.z;
     h[up<8>(6, 6)] += -0.5 * dot(kb, Pa);
     h[up<8>(7, 7)] += -0.5 * dot(kb, Pb);
+  }
+
+  // Exact derivatives of the energy with the reference frames carried from
+  // the committed step by time-parallel transport (Eq. 9): moving the edge
+  // tangent t also rotates its time-transported director about t by the
+  // holonomy chi of the geodesic triangle (t_n, t, t'), which acts like a
+  // twist-angle shift.  With Phi the at-point energy above:
+  //   grad E = grad Phi - sum_x E_x grad chi_x
+  //   hess E = H - sum_x sym(H[:, x], grad chi_x) + sum_xy H[x, y] grad chi_x grad chi_y^T
+  //            - sum_x E_x hess chi_x,      x in {A, B} (effective angles)
+  // grad_e chi = w / l with w = (t_n x t)/(1 + t_n.t), and
+  // hess_e chi = -[ (n s^T + s n^T) / (2 c^2) + w t^T + t w^T ] / l^2,
+  // n = t_n x t, c = 1 + t_n.t, s = t_n - (t_n.t) t.
+  {
+    const v3 tna = (double)sa * mk(a.tn[a.st_ed[k]], a.tn[NE + a.st_ed[k]], a.tn[2 * NE + a.st_ed[k]]);
+    const v3 tnb = (double)sb * mk(a.tn[a.st_ed[NS + k]], a.tn[NE + a.st_ed[NS + k]],
+                                   a.tn[2 * NE + a.st_ed[NS + k]]);
+    v3 ga, gb;
+    double Ha[6], Hb[6];
+    {
+      const double c = 1.0 + dot(tna, ta), ic = 1.0 / c;
+      const v3 n = cross(tna, ta), w = ic * n;
+      const v3 sp = axpy(-dot(tna, ta), ta, tna);
+      ga = ila * w;
+      const double f1 = -0.5 * ic * ic * ila * ila, f2 = -ila * ila;
+      int e = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j, ++e)
+          Ha[e] = f1 * fma(cmp(n, i), cmp(sp, j), cmp(sp, i) * cmp(n, j)) +
+                  f2 * fma(cmp(w, i), cmp(ta, j), cmp(ta, i) * cmp(w, j));
+    }
+    {
+      const double c = 1.0 + dot(tnb, tb), ic = 1.0 / c;
+      const v3 n = cross(tnb, tb), w = ic * n;
+      const v3 sp = axpy(-dot(tnb, tb), tb, tnb);
+      gb = ilb * w;
+      const double f1 = -0.5 * ic * ic * ilb * ilb, f2 = -ilb * ilb;
+      int e = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j, ++e)
+          Hb[e] = f1 * fma(cmp(n, i), cmp(sp, j), cmp(sp, i) * cmp(n, j)) +
+                  f2 * fma(cmp(w, i), cmp(tb, j), cmp(tb, i) * cmp(w, j));
+    }
+    double colA[8], colB[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      colA[i] = i <= 6 ? h[up<8>(i, 6)] : h[up<8>(6, i)];
+      colB[i] = h[up<8>(i < 7 ? i : 7, 7)];
+    }
+    const double EA = g8[6], EB = g8[7];
+    const double HAA = h[up<8>(6, 6)], HBB = h[up<8>(7, 7)], HAB = h[up<8>(6, 7)];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      g8[i] -= EA * cmp(ga, i);
+      g8[3 + i] -= EB * cmp(gb, i);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = i; j < 8; ++j) {
+        const double Gai = i < 3 ? cmp(ga, i) : 0.0, Gaj = j < 3 ? cmp(ga, j) : 0.0;
+        const double Gbi = (i >= 3 && i < 6) ? cmp(gb, i - 3) : 0.0;
+        const double Gbj = (j >= 3 && j < 6) ? cmp(gb, j - 3) : 0.0;
+        double v = -(colA[i] * Gaj + Gai * colA[j]) - (colB[i] * Gbj + Gbi * colB[j]);
+        v += HAA * Gai * Gaj + HBB * Gbi * Gbj + HAB * (Gai * Gbj + Gbi * Gaj);
+        if (i < 3 && j < 3) v -= EA * Ha[up<3>(i, j)];
+        if (i >= 3 && i < 6 && j >= 3 && j < 6) v -= EB * Hb[up<3>(i - 3, j - 3)];
+        h[up<8>(i, j)] += v;
+      }
   }
 
   // map (e_a, e_b, A, B) -> 11 stencil DOFs [x0, th_a, x1, th_b, x2]:

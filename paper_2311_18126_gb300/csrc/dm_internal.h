@@ -18,8 +18,16 @@ void set_error(const std::string &msg);
 // Host-side topology (built once by dm_create_system from the descriptor)
 // ---------------------------------------------------------------------------
 enum SolverKind : int32_t {
-  SOLVE_ROD_BAND = 0, // one rod, Eq. 1 layout, half bandwidth 10
+  SOLVE_ROD_BAND = 0,  // one rod, Eq. 1 layout, symmetric, half bandwidth 10
+  SOLVE_GENERAL = 1,   // limbs (banded interiors) + dense border (joints,
+                       // ground contact/friction: possibly nonsymmetric)
 };
+
+// Gather-map source codes for the general assembly (see dm_general.cu).
+enum SrcType : uint32_t { SRC_STENCIL = 0, SRC_EDGE = 1, SRC_NODE = 2, SRC_DIAG = 3 };
+inline uint32_t src_code(uint32_t type, uint32_t index, bool neg) {
+  return (neg ? 0x80000000u : 0u) | (type << 29) | index;
+}
 
 struct HostTopology {
   int32_t n_rods = 0;
@@ -52,6 +60,23 @@ struct HostTopology {
   std::vector<int32_t> layout2dof;
   // force gather CSR: for each DOF, entries (element, local slot)
   std::vector<int32_t> gat_ptr, gat_ent;
+  // per-DOF node (-1 for twist angles) and component (0..2, 3 = angle)
+  std::vector<int32_t> dof_node, dof_comp;
+  // general systems: limbs (banded interiors) and border
+  std::vector<int32_t> gen_sys;            // general system ids
+  std::vector<int32_t> gs_limb0, gs_nlimb, gs_nB, gs_border0;
+  std::vector<int64_t> gs_JBB, gs_rB, gs_S, gs_xB, gs_mat0, gs_mat1;
+  std::vector<int32_t> lb_dof0, lb_n, lb_ncr, lb_cr0;
+  std::vector<int64_t> lb_band, lb_piv, lb_C, lb_R, lb_Y, lb_y;
+  std::vector<int32_t> border_dof;         // global DOF of each border entry
+  std::vector<int32_t> coupled_rows;       // limb-local rows coupled to border
+  int64_t gen_doubles = 0;                 // size of the general scratch
+  // gather map for the general assembly: target (offset into the general
+  // scratch) <- sum of sources
+  std::vector<int64_t> asm_target;
+  std::vector<int32_t> asm_ptr;
+  std::vector<uint32_t> asm_src;
+  bool any_general = false, ground = false;
 };
 
 // Builds the topology; returns false with set_error() on invalid input.
@@ -103,6 +128,22 @@ struct DevArrays {
   int32_t *layout2dof = nullptr;
   // rod-solver ordering (systems sorted by size)
   int32_t *solve_order = nullptr;
+  // general path
+  int32_t *dof_node = nullptr, *dof_comp = nullptr;
+  double *nt = nullptr;          // node terms [12][Nn]: force (3), -dF/dx (9)
+  double *dconst = nullptr;      // per-DOF M/dt^2 + damping
+  int32_t *node_dof_arr = nullptr, *node_sys = nullptr;
+  double *node_h = nullptr, *node_mu = nullptr, *node_kc = nullptr;
+  double *gen = nullptr;
+  int32_t *gen_sys = nullptr, *gs_limb0 = nullptr, *gs_nlimb = nullptr, *gs_nB = nullptr,
+          *gs_border0 = nullptr;
+  int64_t *gs_JBB = nullptr, *gs_rB = nullptr, *gs_S = nullptr, *gs_xB = nullptr;
+  int32_t *lb_dof0 = nullptr, *lb_n = nullptr, *lb_ncr = nullptr, *lb_cr0 = nullptr;
+  int64_t *lb_band = nullptr, *lb_piv = nullptr, *lb_C = nullptr, *lb_R = nullptr, *lb_Y = nullptr, *lb_y = nullptr;
+  int32_t *border_dof = nullptr, *coupled_rows = nullptr;
+  int64_t *asm_target = nullptr;
+  int32_t *asm_ptr = nullptr;
+  uint32_t *asm_src = nullptr;
 };
 
 struct Params {

@@ -17,7 +17,7 @@ struct EdgeArgs {
 
 struct StencilArgs {
   int ns, ne;
-  const double *q, *ef;
+  const double *q, *ef, *tn;
   const int32_t *st_ed, *st_th, *st_sg, *st_sys;
   const double *st_kb, *st_kt, *kbar, *taubar, *beta_n;
   const int32_t *sys_active;
@@ -33,7 +33,7 @@ struct RowArgs {
   const uint8_t *fixed;
   const int32_t *dof_sys;
   const int32_t *sys_dof0, *sys_ndof, *sys_st0, *sys_edge0;
-  const int32_t *sys_active;
+  const int32_t *sys_active, *sys_kind;
   const double *sg, *sh, *es;
   double *f, *band;
   unsigned long long *sys_res;
@@ -53,7 +53,74 @@ struct SolveArgs {
   const unsigned long long *sys_res;
   int32_t *ctrl;
   unsigned long long *units;
+  const int32_t *ls_action;  // NULL without line search; 1 = backtracking
+  int32_t *ls_trial;
 };
+
+struct NodeArgs {
+  int nn;
+  double dt, ground_z, delta, slip_nu;
+  const double *q, *qn;
+  const int32_t *node_dof, *node_sys;
+  const double *node_h, *node_mu, *node_kc;
+  const int32_t *sys_active;
+  double *nt;
+};
+
+struct RowGenArgs {
+  int nd, ns, ne, nn;
+  double dt, g[3];
+  const double *q, *qn, *vn, *mass, *rscale, *damp;
+  const uint8_t *fixed;
+  const int32_t *dof_sys, *dof_node, *dof_comp, *sys_kind, *sys_active;
+  const int32_t *gat_ptr, *gat_ent;
+  const double *sg, *es, *nt;
+  double *f;
+  unsigned long long *sys_res;
+};
+
+struct AsmArgs {
+  int ntarget;
+  const int64_t *target;
+  const int32_t *ptr;
+  const uint32_t *src;
+  const double *sh, *es, *nt, *dconst;
+  double *gen;
+};
+
+struct SolveGenArgs {
+  int ngen, max_iter;
+  double tol;
+  const int32_t *gen_sys, *gs_limb0, *gs_nlimb, *gs_nB, *gs_border0;
+  const int64_t *gs_JBB, *gs_rB, *gs_S, *gs_xB;
+  const int32_t *lb_dof0, *lb_n, *lb_ncr, *lb_cr0;
+  const int64_t *lb_band, *lb_piv, *lb_C, *lb_R, *lb_Y, *lb_y;
+  const int32_t *border_dof, *coupled_rows;
+  const double *f;
+  double *gen, *q;
+  int32_t *sys_active, *sys_iters, *sys_status;
+  const unsigned long long *sys_res;
+  int32_t *ctrl;
+  unsigned long long *units;
+  const int32_t *ls_action;
+  int32_t *ls_trial;
+};
+
+struct LineSearchArgs {
+  int nsys, nd;
+  const int32_t *sys_active, *dof_sys, *sys_dof0, *sys_ndof;
+  const double *f, *rscale;
+  int32_t *action, *trial, *nback;
+  double *alpha, *racc, *merit, *q, *qacc;
+};
+__global__ void k_ls_merit(LineSearchArgs a);
+__global__ void k_ls_decide(LineSearchArgs a);
+__global__ void k_ls_apply(LineSearchArgs a);
+
+__global__ void k_nodes(NodeArgs a);
+__global__ void k_rows_gen(RowGenArgs a);
+__global__ void k_assemble_gen(AsmArgs a);
+__global__ void k_solve_gen(SolveGenArgs a);
 
 __global__ void k_edge(EdgeArgs a);
 __global__ void k_stencil(StencilArgs a);

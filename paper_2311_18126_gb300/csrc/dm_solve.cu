@@ -28,7 +28,8 @@ __device__ __forceinline__ int ksym(int c, int cp) {  // packed 3x3 (xx,xy,xz,yy
 
 __global__ void __launch_bounds__(256) k_rows_rod(RowArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool act = i < a.nd && a.sys_active[a.dof_sys[i]];
+  const bool act = i < a.nd && a.sys_active[a.dof_sys[i]] &&
+                   a.sys_kind[a.dof_sys[i]] == SOLVE_ROD_BAND;
   count_units(a.units, act);
   if (!act) return;
   const int s = a.dof_sys[i];
@@ -321,6 +322,10 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
     if (t >= a.nsys) break;
     const int s = a.order[t];
     if (!a.sys_active[s]) continue;
+    if (a.ls_action && a.ls_action[s] == 1) {  // backtracking: no solve this round
+      if ((lane & 7) == 0) atomicAdd(&a.ctrl[0], 1);
+      continue;
+    }
     const double res = __longlong_as_double((long long)a.sys_res[s]);
     int st = a.sys_status[s];
     if (st == 0 && isnan(res)) st = DM_ERR_NONFINITE;
@@ -419,10 +424,58 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
     __syncwarp(umask);
     if ((lane & 7) == 0) {
       a.sys_iters[s] += 1;
+      if (a.ls_trial) a.ls_trial[s] = 1;
       atomicAdd(&a.ctrl[0], 1);
       if (a.units) atomicAdd(a.units, (unsigned long long)n);
     }
   }
+}
+
+// Line search (optional): Armijo test on the 2-norm of the scaled residual
+// |f_i| / (D_i l_i) of each system (the Newton direction is a descent
+// direction for it); a trial point without sufficient decrease is pulled
+// halfway back to the last accepted iterate, at most 12 times.
+// k_ls_merit: one warp per system, fixed summation order (deterministic).
+__global__ void k_ls_merit(LineSearchArgs a) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= a.nsys) return;
+  if (!a.sys_active[s]) return;
+  const int d0 = a.sys_dof0[s], n = a.sys_ndof[s];
+  double acc = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double v = a.f[d0 + i] * a.rscale[d0 + i];
+    acc = fma(v, v, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) a.merit[s] = sqrt(acc);
+}
+
+__global__ void k_ls_decide(LineSearchArgs a) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.nsys || !a.sys_active[s]) return;
+  const double m = a.merit[s];
+  if (a.trial[s] && a.nback[s] < 12 && !(m <= (1.0 - 1e-4 * a.alpha[s]) * a.racc[s])) {
+    a.action[s] = 1;
+    a.alpha[s] *= 0.5;
+    a.nback[s] += 1;
+  } else {
+    a.action[s] = 0;
+    a.trial[s] = 0;
+    a.nback[s] = 0;
+    a.alpha[s] = 1.0;
+    a.racc[s] = m;
+  }
+}
+
+__global__ void k_ls_apply(LineSearchArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.nd) return;
+  const int s = a.dof_sys[i];
+  if (!a.sys_active[s]) return;
+  if (a.action[s] == 1) a.q[i] = 0.5 * (a.q[i] + a.qacc[i]);
+  else a.qacc[i] = a.q[i];
 }
 
 }  // namespace dm

@@ -5,6 +5,8 @@
 #include <cmath>
 #include <numeric>
 #include <string>
+#include <tuple>
+#include <utility>
 
 #include "dm_internal.h"
 
@@ -290,30 +292,104 @@ bool build_topology(const dm_system_desc *D, const dm_params *P, HostTopology &T
     T.node_sys[T.edge_b[e]] = T.edge_sys[e];
   }
 
-  // --- DOF numbering: per system, per rod in Eq. 1 order, shared nodes once
+  // --- joints may only merge rod end nodes
+  std::vector<int32_t> mult(nn, 0);
+  for (int64_t a = 0; a < nflat; ++a) mult[T.flat2node[a]]++;
+  for (int r = 0; r < R; ++r)
+    for (int i = 1; i + 1 < T.npr[r]; ++i)
+      if (mult[T.flat2node[T.rod_node0[r] + i]] > 1) {
+        set_error("joints must join rod end nodes (rod " + std::to_string(r) + ", node " +
+                  std::to_string(i) + ")");
+        return false;
+      }
+  T.ground = P->ground != 0;
+
+  // --- DOF numbering.  Single rods without contact: Eq. 1 order.  General
+  // systems (joints or ground contact): every rod's interior DOFs in Eq. 1
+  // order, then the border: joint nodes, the nodes next to them along each
+  // attached rod, and the twist angles of the edges at joint nodes.
   T.node_dof.assign(nn, -1);
   T.edge_thdof.assign(ne, -1);
   T.sys_dof0.assign(S, 0);
   T.sys_ndof.assign(S, 0);
   T.sys_kind.assign(S, SOLVE_ROD_BAND);
+  std::vector<char> bnode(nn, 0), bedge(ne, 0);
+  std::vector<int32_t> limb_sys, limb_rod, limb_d0, limb_n;
+  std::vector<std::vector<int32_t>> sys_border(S);
   int32_t ndof = 0;
   for (int s = 0; s < S; ++s) {
     T.sys_dof0[s] = ndof;
-    for (int r = T.sys_rod0[s]; r < T.sys_rod0[s] + T.sys_nrods[s]; ++r) {
-      for (int i = 0; i < T.npr[r]; ++i) {
-        int64_t v = T.flat2node[T.rod_node0[r] + i];
-        if (T.node_dof[v] < 0) {
-          T.node_dof[v] = ndof;
-          ndof += 3;
+    const int r0 = T.sys_rod0[s], r1 = T.sys_rod0[s] + T.sys_nrods[s];
+    const bool general = T.sys_nrods[s] > 1 || T.ground;
+    T.sys_kind[s] = general ? SOLVE_GENERAL : SOLVE_ROD_BAND;
+    if (!general) {
+      for (int i = 0; i < T.npr[r0]; ++i) {
+        T.node_dof[T.flat2node[T.rod_node0[r0] + i]] = ndof;
+        ndof += 3;
+        if (i + 1 < T.npr[r0]) T.edge_thdof[T.rod_edge0[r0] + i] = ndof++;
+      }
+      T.sys_ndof[s] = ndof - T.sys_dof0[s];
+      continue;
+    }
+    for (int r = r0; r < r1; ++r) {
+      const int N = T.npr[r];
+      for (int end = 0; end < 2; ++end) {
+        const int i = end ? N - 1 : 0, nb = end ? N - 2 : 1;
+        const int64_t v = T.flat2node[T.rod_node0[r] + i];
+        if (mult[v] > 1) {
+          bnode[v] = 1;
+          bnode[T.flat2node[T.rod_node0[r] + nb]] = 1;
+          bedge[T.rod_edge0[r] + (end ? N - 2 : 0)] = 1;
         }
-        if (i + 1 < T.npr[r]) T.edge_thdof[T.rod_edge0[r] + i] = ndof++;
+      }
+    }
+    for (int r = r0; r < r1; ++r) {
+      const int N = T.npr[r];
+      int first = -1, last = -1, count = 0;
+      for (int k = 0; k < 4 * N - 1; ++k) {
+        const int i = k / 4, c = k % 4;
+        const bool isb = c < 3 ? bnode[T.flat2node[T.rod_node0[r] + i]] != 0
+                               : bedge[T.rod_edge0[r] + i] != 0;
+        if (isb) continue;
+        if (first < 0) first = k;
+        if (last >= 0 && k != last + 1) {
+          set_error("rod " + std::to_string(r) + ": border DOFs inside the rod");
+          return false;
+        }
+        last = k;
+        ++count;
+      }
+      if (count > 0) {
+        limb_sys.push_back(s);
+        limb_rod.push_back(r);
+        limb_d0.push_back(ndof);
+        limb_n.push_back(count);
+      }
+      for (int k = first; count > 0 && k <= last; ++k) {
+        const int i = k / 4, c = k % 4;
+        if (c < 3) {
+          if (c == 0) T.node_dof[T.flat2node[T.rod_node0[r] + i]] = ndof;
+          ++ndof;
+        } else {
+          T.edge_thdof[T.rod_edge0[r] + i] = ndof++;
+        }
+      }
+    }
+    for (int r = r0; r < r1; ++r) {
+      const int N = T.npr[r];
+      for (int i = 0; i < N; ++i) {
+        const int64_t v = T.flat2node[T.rod_node0[r] + i];
+        if (bnode[v] && T.node_dof[v] < 0) {
+          T.node_dof[v] = ndof;
+          for (int c = 0; c < 3; ++c) sys_border[s].push_back(ndof++);
+        }
+        if (i + 1 < N && bedge[T.rod_edge0[r] + i] && T.edge_thdof[T.rod_edge0[r] + i] < 0) {
+          T.edge_thdof[T.rod_edge0[r] + i] = ndof;
+          sys_border[s].push_back(ndof++);
+        }
       }
     }
     T.sys_ndof[s] = ndof - T.sys_dof0[s];
-    if (T.sys_nrods[s] != 1) {
-      set_error("joined rod systems are not supported by this build");
-      return false;
-    }
   }
   T.n_dofs = ndof;
   T.sys_edge0.assign(S, 0);
@@ -394,6 +470,7 @@ bool build_topology(const dm_system_desc *D, const dm_params *P, HostTopology &T
     }
   }
 
+  // (general-path storage and gather maps are built after the fixed DOFs)
   // --- per-DOF masses (reading C7), state, fixed DOFs
   T.dof_mass.assign(ndof, 0.0);
   T.q0.assign(ndof, 0.0);
@@ -473,6 +550,160 @@ bool build_topology(const dm_system_desc *D, const dm_params *P, HostTopology &T
     set_error("too many stencils or edges for one handle (limit 2^26)");
     return false;
   }
+
+  // --- per-DOF node and component
+  T.dof_node.assign(ndof, -1);
+  T.dof_comp.assign(ndof, 3);
+  for (int64_t v = 0; v < nn; ++v)
+    for (int c = 0; c < 3; ++c) {
+      T.dof_node[T.node_dof[v] + c] = (int32_t)v;
+      T.dof_comp[T.node_dof[v] + c] = c;
+    }
+
+  // --- general systems: storage layout and the assembly gather map
+  std::vector<int32_t> dof_limb(ndof, -1), dof_row(ndof, -1), dof_bidx(ndof, -1);
+  int64_t off = 0;
+  std::vector<std::pair<int64_t, uint32_t>> pairs;
+  size_t li = 0;
+  for (int s = 0; s < S; ++s) {
+    if (T.sys_kind[s] != SOLVE_GENERAL) continue;
+    T.any_general = true;
+    const int gid = (int)T.gen_sys.size();
+    T.gen_sys.push_back(s);
+    const int nB = (int)sys_border[s].size();
+    T.gs_nB.push_back(nB);
+    T.gs_border0.push_back((int32_t)T.border_dof.size());
+    for (int b = 0; b < nB; ++b) {
+      T.border_dof.push_back(sys_border[s][b]);
+      dof_bidx[sys_border[s][b]] = b;
+    }
+    T.gs_limb0.push_back((int32_t)T.lb_dof0.size());
+    int nl = 0;
+    std::vector<int> mylimbs;
+    while (li < limb_sys.size() && limb_sys[li] == s) {
+      const int L = (int)T.lb_dof0.size();
+      T.lb_dof0.push_back(limb_d0[li]);
+      T.lb_n.push_back(limb_n[li]);
+      for (int k = 0; k < limb_n[li]; ++k) {
+        dof_limb[limb_d0[li] + k] = L;
+        dof_row[limb_d0[li] + k] = k;
+      }
+      mylimbs.push_back(L);
+      ++li;
+      ++nl;
+    }
+    T.gs_nlimb.push_back(nl);
+    // element entries of this system: (row DOF, col DOF, source)
+    std::vector<std::tuple<int32_t, int32_t, uint32_t>> ent;
+    auto fixed = [&](int32_t g) { return T.dof_fixed[g] != 0; };
+    auto add = [&](int32_t g1, int32_t g2, uint32_t src) {
+      if (fixed(g1) || fixed(g2)) return;
+      ent.emplace_back(g1, g2, src);
+    };
+    for (int64_t k = T.sys_st0[s]; k < T.sys_st0[s] + T.sys_nst[s]; ++k) {
+      int32_t slots[11];
+      for (int n = 0; n < 3; ++n)
+        for (int c = 0; c < 3; ++c) slots[4 * n + c] = T.node_dof[T.st_node[n][k]] + c;
+      slots[3] = T.edge_thdof[T.st_edge[0][k]];
+      slots[7] = T.edge_thdof[T.st_edge[1][k]];
+      for (int a = 0; a < 11; ++a)
+        for (int b = 0; b < 11; ++b) {
+          const int lo = a < b ? a : b, hi = a < b ? b : a;
+          const int up = lo * 11 - lo * (lo - 1) / 2 + (hi - lo);
+          add(slots[a], slots[b], src_code(SRC_STENCIL, (uint32_t)(up * T.n_stencils + k), false));
+        }
+    }
+    for (int64_t e = T.sys_edge0[s]; e < T.sys_edge0[s] + T.sys_nedge[s]; ++e) {
+      const int32_t ba = T.node_dof[T.edge_a[e]], bb = T.node_dof[T.edge_b[e]];
+      for (int sa = 0; sa < 2; ++sa)
+        for (int sb = 0; sb < 2; ++sb)
+          for (int ca = 0; ca < 3; ++ca)
+            for (int cb = 0; cb < 3; ++cb) {
+              const int i = ca < cb ? ca : cb, j = ca < cb ? cb : ca;
+              const int ks = 3 + (i == 0 ? j : (i == 1 ? 2 + j : 5));
+              add((sa ? bb : ba) + ca, (sb ? bb : ba) + cb,
+                  src_code(SRC_EDGE, (uint32_t)(ks * ne + e), sa != sb));
+            }
+    }
+    for (int32_t g = T.sys_dof0[s]; g < T.sys_dof0[s] + T.sys_ndof[s]; ++g) {
+      if (T.ground && T.dof_comp[g] < 3) {
+        const int32_t v = T.dof_node[g], c = T.dof_comp[g];
+        if (c == 0)
+          for (int ca = 0; ca < 3; ++ca)
+            for (int cb = 0; cb < 3; ++cb)
+              add(g + ca, g + cb, src_code(SRC_NODE, (uint32_t)((3 + 3 * ca + cb) * nn + v), false));
+      }
+      ent.emplace_back(g, g, src_code(SRC_DIAG, (uint32_t)g, false));
+    }
+    // coupled rows per limb
+    std::vector<std::vector<int32_t>> crow(nl);
+    for (auto &t : ent) {
+      const int32_t g1 = std::get<0>(t), g2 = std::get<1>(t);
+      if (dof_limb[g1] >= 0 && dof_bidx[g2] >= 0) crow[dof_limb[g1] - mylimbs[0]].push_back(dof_row[g1]);
+      if (dof_bidx[g1] >= 0 && dof_limb[g2] >= 0) crow[dof_limb[g2] - mylimbs[0]].push_back(dof_row[g2]);
+    }
+    std::vector<std::vector<int32_t>> crmap(nl);
+    for (int l = 0; l < nl; ++l) {
+      std::sort(crow[l].begin(), crow[l].end());
+      crow[l].erase(std::unique(crow[l].begin(), crow[l].end()), crow[l].end());
+      const int L = mylimbs[l];
+      T.lb_ncr.push_back((int32_t)crow[l].size());
+      T.lb_cr0.push_back((int32_t)T.coupled_rows.size());
+      crmap[l].assign(T.lb_n[L], -1);
+      for (size_t k = 0; k < crow[l].size(); ++k) {
+        T.coupled_rows.push_back(crow[l][k]);
+        crmap[l][crow[l][k]] = (int32_t)k;
+      }
+      const int64_t n = T.lb_n[L], ncr = (int64_t)crow[l].size();
+      T.lb_band.push_back(off); off += 31 * n;   // kl = 10, ku + fill = 20
+      T.lb_piv.push_back(off); off += n;
+      T.lb_C.push_back(off); off += ncr * nB;
+      T.lb_R.push_back(off); off += ncr * nB;
+      T.lb_Y.push_back(off); off += n * nB;
+      T.lb_y.push_back(off); off += n;
+    }
+    T.gs_JBB.push_back(off); off += (int64_t)nB * nB;
+    T.gs_rB.push_back(off); off += nB;
+    T.gs_S.push_back(off); off += (int64_t)nB * nB;
+    T.gs_xB.push_back(off); off += nB;
+    T.gs_mat0.push_back(T.lb_band.empty() || nl == 0 ? T.gs_JBB.back() : T.lb_band[mylimbs[0]]);
+    T.gs_mat1.push_back(off);
+    for (auto &t : ent) {
+      const int32_t g1 = std::get<0>(t), g2 = std::get<1>(t);
+      const uint32_t src = std::get<2>(t);
+      int64_t tgt = -1;
+      const int L1 = dof_limb[g1], L2 = dof_limb[g2];
+      if (L1 >= 0 && L2 >= 0) {
+        const int r1 = dof_row[g1], r2 = dof_row[g2];
+        if (L1 != L2 || r2 - r1 > 10 || r1 - r2 > 10) {
+          set_error("internal: element couples DOFs outside a limb band");
+          return false;
+        }
+        tgt = T.lb_band[L1] + (int64_t)(r2 - r1 + 10) * T.lb_n[L1] + r1;
+      } else if (L1 >= 0) {
+        tgt = T.lb_C[L1] + (int64_t)crmap[L1 - mylimbs[0]][dof_row[g1]] * nB + dof_bidx[g2];
+      } else if (L2 >= 0) {
+        tgt = T.lb_R[L2] + (int64_t)dof_bidx[g1] * T.lb_ncr[L2] + crmap[L2 - mylimbs[0]][dof_row[g2]];
+      } else {
+        tgt = T.gs_JBB[gid] + (int64_t)dof_bidx[g1] * nB + dof_bidx[g2];
+      }
+      pairs.emplace_back(tgt, src);
+    }
+  }
+  T.gen_doubles = off;
+  std::stable_sort(pairs.begin(), pairs.end(),
+                   [](const std::pair<int64_t, uint32_t> &a, const std::pair<int64_t, uint32_t> &b) {
+                     return a.first < b.first;
+                   });
+  T.asm_ptr.push_back(0);
+  for (size_t k = 0; k < pairs.size(); ++k) {
+    if (k == 0 || pairs[k].first != pairs[k - 1].first) {
+      if (k > 0) T.asm_ptr.push_back((int32_t)k);
+      T.asm_target.push_back(pairs[k].first);
+    }
+    T.asm_src.push_back(pairs[k].second);
+  }
+  if (!pairs.empty()) T.asm_ptr.push_back((int32_t)pairs.size());
   return true;
 }
 

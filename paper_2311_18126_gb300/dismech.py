@@ -38,7 +38,7 @@ class Params(C.Structure):
                 ("gravity", C.c_double * 3), ("damping", C.c_double), ("ground", C.c_int32),
                 ("ground_z", C.c_double), ("delta", C.c_double), ("slip_nu", C.c_double),
                 ("self_contact", C.c_int32), ("pair_kc", C.c_double), ("pair_mu", C.c_double),
-                ("stream", C.c_void_p)]
+                ("line_search", C.c_int32), ("stream", C.c_void_p)]
 
 
 class StepStats(C.Structure):
@@ -105,6 +105,8 @@ def load_library(path=LIB_PATH):
     lib.dm_solve_band.restype = C.c_int
     lib.dm_solve_band_noalloc.argtypes = lib.dm_solve_band.argtypes
     lib.dm_solve_band_noalloc.restype = C.c_int
+    lib.dm_debug_copy.argtypes = [H, C.c_char_p, _dp, C.c_int64]
+    lib.dm_debug_copy.restype = C.c_int
     lib.dm_last_error.argtypes = []
     lib.dm_last_error.restype = C.c_char_p
     _lib = lib
@@ -194,6 +196,7 @@ class System:
         p.self_contact = int(bool(params.get("self_contact", False)))
         p.pair_kc = params.get("pair_kc", 0.0)
         p.pair_mu = params.get("pair_mu", 0.0)
+        p.line_search = int(bool(params.get("line_search", False)))
         p.stream = params.get("stream", None)
         h = C.c_void_p()
         _check(lib.dm_create_system(C.byref(d), C.byref(p), C.byref(h)))
@@ -284,6 +287,11 @@ class System:
             name = self._lib.dm_kernel_name(k).decode()
             if name and p.launches[k]:
                 out[name] = (int(p.launches[k]), int(p.units[k]), float(p.ms[k]))
+        return out
+
+    def debug_copy(self, name, n):
+        out = np.zeros(int(n))
+        _check(self._lib.dm_debug_copy(self._h, name.encode(), _ptr(out, C.c_double), len(out)))
         return out
 
     def get_frames(self):

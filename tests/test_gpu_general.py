@@ -1,0 +1,91 @@
+"""GPU vs oracle for the general path: rods joined at elastic joints
+(Sec. III-D), ground contact with smooth Coulomb friction (Sec. III-B,
+Eq. 10-13), and the limb/border block solve.  Identical initial states,
+element-by-element comparison of the per-rod state after every step."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import OracleSystems
+from test_gpu_parity import _assert_close, _gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(desc, params, steps, rel, kbar_fn=None, nrods=None):
+    gpu = _gpu(desc, params)
+    ora = OracleSystems(desc, params)
+    npr = desc["nodes_per_rod"]
+    L = max(1.0, float(np.max(np.abs(desc["x0"]))))
+    for k in range(steps):
+        if kbar_fn is not None:
+            kb = kbar_fn(k * params["dt"])
+            gpu.set_natural_curvature(0, nrods, kb)
+            ora.set_natural_curvature(0, nrods, kb)
+        gpu.step(1)
+        st = ora.step(1)
+        assert all(x[0] == 0 for x in st), st
+        qg, vg = gpu.get_state()
+        qo, vo = ora.get_state()
+        _assert_close(qg, qo, npr, L, rel)
+        # identical states for the next step (per-step parity)
+        d1, beta = ora.get_frames()
+        gpu.set_state(qo, vo)
+        gpu.set_frames(d1, beta)
+    return gpu, ora
+
+
+def test_star_robots_on_ground_with_gait():
+    desc, params, gait = workloads.star_robots(n_robots=3, seed=3, nodes_per_limb=8)
+    R = len(desc["nodes_per_rod"])
+    _run(desc, params, 6, 1e-10, lambda t: workloads.gait_kbar(gait, t), R)
+
+
+def test_joined_chain_without_ground():
+    # two rods joined end to end plus a rod joined to their junction: a
+    # T-shaped network with a free end swinging under gravity
+    N = 7
+    a = np.c_[np.linspace(0, 0.3, N), np.zeros(N), np.zeros(N)]
+    b = np.c_[np.linspace(0.3, 0.6, N), np.zeros(N), np.zeros(N)]
+    c = np.c_[np.full(N, 0.3), np.linspace(0, 0.25, N), np.zeros(N)]
+    fixed = np.zeros(3 * (4 * N - 1), np.uint8)
+    fixed[0:8] = 1
+    desc = dict(nodes_per_rod=[N, N, N], x0=np.concatenate([a, b, c]),
+                E=[1e6, 2e6, 1.5e6], nu=[0.5] * 3, rho=[1e3] * 3, radius=[2e-3, 2.5e-3, 2e-3],
+                joints=[[(0, N - 1), (1, 0), (2, 0)]], fixed=fixed)
+    params = dict(dt=2e-3, tol=1e-10, max_iter=60, g=(0, 0, -9.81), eta=0.05)
+    _run(desc, params, 6, 1e-10)
+
+
+def test_rod_sliding_on_ground_with_friction():
+    N = 9
+    h = 0.01
+    x = np.c_[np.linspace(0, 0.5, N), np.zeros(N), np.full(N, h)]
+    m = 1000.0 * math.pi * h * h * 0.5
+    kc = 50.0 * m / (N - 1) * 9.81 / 5e-4
+    desc = dict(nodes_per_rod=[N], x0=x, E=[1e6], nu=[0.5], rho=[1e3], radius=[h],
+                ground_mu=[0.4], ground_kc=[kc],
+                v0=np.c_[np.full(N, 0.05), np.full(N, 0.02), np.zeros(N)])
+    params = dict(dt=2e-3, tol=1e-10, max_iter=60, g=(2.0, 0.0, -9.81), eta=0.0,
+                  ground=True, ground_z=0.0, delta=5e-4, nu_slip=1e-3)
+    _run(desc, params, 8, 1e-10)
+
+
+def test_star_robots_trajectory():
+    # free-running trajectory (no per-step reset): contact-rich, so the
+    # tolerance is looser than the contact-free 1e-7 rule
+    desc, params, gait = workloads.star_robots(n_robots=2, seed=7, nodes_per_limb=6)
+    R = len(desc["nodes_per_rod"])
+    gpu = _gpu(desc, params)
+    ora = OracleSystems(desc, params)
+    for k in range(12):
+        kb = workloads.gait_kbar(gait, k * params["dt"])
+        gpu.set_natural_curvature(0, R, kb)
+        ora.set_natural_curvature(0, R, kb)
+        gpu.step(1)
+        ora.step(1)
+    qg, _ = gpu.get_state()
+    qo, _ = ora.get_state()
+    _assert_close(qg, qo, desc["nodes_per_rod"], 1.0, 1e-7)

@@ -141,78 +141,49 @@ def _stencil_setup(seed):
     return o, s, q
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_forces_match_central_differences(seed):
-    o, s, q = _stencil_setup(seed)
-    F, _, _ = o.forces(s, q, s.v, s.q, need_jac=False)
-    # energy with the reference frames held at those of q (at-point gauge)
-    _, t = o._stencil_geometry(s, q)
-    d1 = o._time_parallel_frames(s, t)
-    sa, sb, ta, d1a, tb, d1b = o._oriented(s, t, d1)
-    bref = der.reference_twist(ta, d1a, tb, d1b, s.beta)
-    kb, kt = torch.as_tensor(s.st_kb), torch.as_tensor(s.st_kt)
+def _total_energy(o, s, qq):
+    """Stretching + bending + twisting (frames time-transported from the
+    committed step) + gravity potential of one system at DOF vector qq."""
     idx = torch.as_tensor(s.st_dofs)
     e6 = torch.as_tensor(s.edge_dofs6)
+    Eb = der.time_transported_energy(qq[idx], *o._stencil_history(s)).sum()
+    Es = der.stretch_energy(qq[e6], torch.as_tensor(s.EA), torch.as_tensor(s.lbar)).sum()
+    x = qq[torch.as_tensor(s.node_dof)[:, None] + torch.arange(3)]
+    Eg = -(torch.as_tensor(s.mnode)[:, None] * torch.tensor(o.p["g"], dtype=DT) * x).sum()
+    return Eb + Es + Eg
 
-    def energy(qq):
-        Eb = der.bend_twist_energy(qq[idx], sa, sb, ta, d1a, tb, d1b, bref, kb, kt,
-                                   s.kbar1, s.kbar2, s.taubar).sum()
-        Es = der.stretch_energy(qq[e6], torch.as_tensor(s.EA), torch.as_tensor(s.lbar)).sum()
-        return Eb + Es - (torch.as_tensor(s.mnode)[:, None] * torch.tensor([0, 0, -9.81], dtype=DT)
-                          * qq[torch.as_tensor(s.node_dof)[:, None] + torch.arange(3)]).sum()
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_forces_match_central_differences(seed):
+    # Eq. 9: forces are minus the gradient of the energy
+    o, s, q = _stencil_setup(seed)
+    F, _, _ = o.forces(s, q, s.v, s.q, need_jac=False)
     hstep = 1e-6
     fd = np.zeros(s.n)
     for i in range(s.n):
         dq = torch.zeros(s.n, dtype=DT)
         dq[i] = hstep
-        fd[i] = -(float(energy(q + dq)) - float(energy(q - dq))) / (2 * hstep)
+        fd[i] = -(float(_total_energy(o, s, q + dq)) - float(_total_energy(o, s, q - dq))) / (2 * hstep)
     scale = np.max(np.abs(fd))
     np.testing.assert_allclose(F.numpy(), fd, atol=1e-7 * scale)
 
 
 @pytest.mark.parametrize("seed", [3, 4])
-def test_jacobians_match_central_differences(seed):
+def test_jacobian_matches_central_differences_and_is_symmetric(seed):
+    # Eq. 16: J = -dF/dq, by central differences of the forces; it is the
+    # Hessian of the energy, hence symmetric
     o, s, q = _stencil_setup(seed)
-    # (1) at-point Hessian = derivative of the gradient with frames held
-    F0, _, J = o.forces(s, q, s.v, s.q, need_jac=True)
-    _, t = o._stencil_geometry(s, q)
-    d1 = o._time_parallel_frames(s, t)
-    sa, sb, ta, d1a, tb, d1b = o._oriented(s, t, d1)
-    bref = der.reference_twist(ta, d1a, tb, d1b, s.beta)
-    kb, kt = torch.as_tensor(s.st_kb), torch.as_tensor(s.st_kt)
-    idx = torch.as_tensor(s.st_dofs)
-    e6 = torch.as_tensor(s.edge_dofs6)
-
-    def held_force(qq):
-        def en(z):
-            return (der.bend_twist_energy(z[idx], sa, sb, ta, d1a, tb, d1b, bref, kb, kt,
-                                          s.kbar1, s.kbar2, s.taubar).sum()
-                    + der.stretch_energy(z[e6], torch.as_tensor(s.EA),
-                                         torch.as_tensor(s.lbar)).sum())
-        return -grad(en)(qq)
-
+    _, _, J = o.forces(s, q, s.v, s.q, need_jac=True)
     hstep = 1e-6
     fd = np.zeros((s.n, s.n))
     for j in range(s.n):
         dq = torch.zeros(s.n, dtype=DT)
         dq[j] = hstep
-        fd[:, j] = -(held_force(q + dq) - held_force(q - dq)).numpy() / (2 * hstep)
-    sc = np.max(np.abs(fd))
-    np.testing.assert_allclose(J.numpy(), fd, atol=1e-6 * sc)
-    # (2) exact mode = derivative of the at-point force with frames carried
-    #     by time-parallel transport (no frames held)
-    _, _, Jx = o.forces(s, q, s.v, s.q, need_jac=True, mode="exact")
-    fd2 = np.zeros((s.n, s.n))
-    for j in range(s.n):
-        dq = torch.zeros(s.n, dtype=DT)
-        dq[j] = hstep
         Fp, _, _ = o.forces(s, q + dq, s.v, s.q, need_jac=False)
         Fm, _, _ = o.forces(s, q - dq, s.v, s.q, need_jac=False)
-        fd2[:, j] = -(Fp - Fm).numpy() / (2 * hstep)
-    np.testing.assert_allclose(Jx.numpy(), fd2, atol=1e-6 * sc)
-    # the two Jacobians differ (the at-point one is symmetric, the exact one
-    # carries the holonomy of the transported frames)
+        fd[:, j] = -(Fp - Fm).numpy() / (2 * hstep)
+    sc = np.max(np.abs(fd))
+    np.testing.assert_allclose(J.numpy(), fd, atol=1e-6 * sc)
     assert np.allclose(J.numpy(), J.numpy().T, atol=1e-12 * sc)
 
 
@@ -239,10 +210,9 @@ def test_rigid_motion_invariance():
     Fx = F[nd].numpy()
     M = F[torch.as_tensor(s.edge_dof)].numpy()
     _, t = o._stencil_geometry(s, q)
-    # total force and total torque (nodes plus twisting moments about t) vanish
+    # translation invariance: the nodal forces sum to zero
     assert np.allclose(Fx.sum(0), 0, atol=1e-10 * np.abs(Fx).max())
-    tau = np.cross(x, Fx).sum(0) + (M[:, None] * t.numpy()).sum(0)
-    assert np.allclose(tau, 0, atol=1e-10 * np.abs(Fx).max())
+    E0 = float(_total_energy(o, s, q))
     # rotate everything (state, committed frames): forces rotate with it
     Rm = _rotation(1)
     R = torch.as_tensor(Rm)
@@ -251,6 +221,8 @@ def test_rigid_motion_invariance():
     s.d1 = s.d1 @ R.T
     s.tn = s.tn @ R.T
     F2, _, _ = o.forces(s, q2, s.v, s.q, need_jac=False)
+    # the energy (with the committed frames rotated too) is unchanged
+    assert float(_total_energy(o, s, q2)) == pytest.approx(E0, rel=1e-12, abs=1e-14)
     np.testing.assert_allclose(F2[nd].numpy(), Fx @ Rm.T, atol=1e-10 * np.abs(Fx).max())
     np.testing.assert_allclose(F2[torch.as_tensor(s.edge_dof)].numpy(), M,
                                atol=1e-10 * np.abs(Fx).max())
@@ -345,36 +317,35 @@ def test_reference_twist_holonomy():
 # ---------------------------------------------------------------------------
 
 def test_newton_quadratic_convergence():
-    # one Newton step from q* + eps w has error O(eps^2) with the exact
-    # Jacobian (Eq. 16 in full): the ratio err/eps^2 stays constant as eps
-    # shrinks.  A dropped or wrong Jacobian term makes it grow like 1/eps.
+    # one Newton step from q* + eps w has error O(eps^2) (exact Jacobian,
+    # Eq. 16 in full): err/eps^2 stays constant as eps shrinks.  A dropped or
+    # wrong Jacobian term makes it grow like 1/eps.
     N = 10
     rng = np.random.default_rng(5)
     desc = rod_desc(straight(N, 0.5), E=1e6, h=2e-3, fixed=clamp(N),
                     v0=np.c_[np.zeros(N), 0.5 * rng.standard_normal(N), rng.standard_normal(N)])
-    p = dict(dt=0.01, tol=1e-15, max_iter=40, eta=0.0, jacobian="exact")
+    p = dict(dt=0.01, tol=1e-15, max_iter=40, eta=0.0)
     o = OracleSystems(desc, p)
     s = o.systems[0]
     s.kbar1 = torch.full((N - 2,), 0.05, dtype=DT)
     q_n, v_n = s.q.clone(), s.v.clone()
+    hist = (s.tn.clone(), s.d1.clone(), s.beta.clone())
     assert o.step_system(s)[0] == 0
     qstar = s.q.clone()
+    # the step committed its frames: restore the history of the step that
+    # produced q* before evaluating its residual
+    s.q, s.v = q_n, v_n
+    s.tn, s.d1, s.beta = hist
     w = torch.as_tensor(rng.standard_normal(s.n))
     w = torch.where(s.fixed, torch.zeros_like(w), w)
     w = w / torch.linalg.vector_norm(w)
     ratios = []
     for eps in (1e-3, 1e-4, 1e-5):
         q0 = qstar + eps * w
-        f, _, J = o.residual(s, q0, q_n, v_n, need_jac=True, mode="exact")
+        f, _, J = o.residual(s, q0, q_n, v_n, need_jac=True)
         q1 = q0 + o.solve(s, J, -f)
         ratios.append(float(torch.linalg.vector_norm(q1 - qstar)) / eps ** 2)
     assert ratios[2] < 2.0 * ratios[1] and ratios[1] < 2.0 * ratios[0]
-    # the at-point Jacobian reaches the same root
-    o2 = OracleSystems(desc, dict(p, jacobian="atpoint"))
-    o2.systems[0].kbar1 = s.kbar1.clone()
-    st = o2.step_system(o2.systems[0])
-    assert st[0] == 0
-    np.testing.assert_allclose(o2.systems[0].q.numpy(), qstar.numpy(), atol=1e-12)
 
 
 def test_banded_and_dense_solves_agree():

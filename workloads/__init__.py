@@ -154,7 +154,8 @@ def star_robots(n_robots=1024, seed=3, k_min=3, k_max=8, nodes_per_limb=30,
                      np.zeros(int(np.sum(4 * np.asarray(npr) - 1)), dtype=np.uint8),
                      joints=joints, ground_mu=np.array(gm), ground_kc=np.array(gk))
     params = dict(dt=5e-3, tol=1e-10, max_iter=100, g=(0.0, 0.0, -9.81), eta=0.1,
-                  ground=True, ground_z=0.0, delta=delta, nu_slip=nu_slip)
+                  ground=True, ground_z=0.0, delta=delta, nu_slip=nu_slip,
+                  line_search=True)
     gait = dict(A=np.array(gait_A), T=np.array(gait_T), phase=np.array(gait_ph),
                 robot=np.array(robot_of), spacing=spacing,
                 nodes_per_limb=nodes_per_limb)
