@@ -224,6 +224,39 @@ dm_status dm_solve_band_noalloc(int32_t nsys, const int32_t *sys_dof0,
                                 const double *band, const double *rhs, double *x,
                                 void *stream);
 
+/* BF16 tensor-core GEMM used by the learned warm start (no counterpart in
+ * the paper): C = act(A B^T + bias) with A [M][K], B [N][K] bf16 row-major
+ * device arrays, bias [N] fp32 device array or NULL, C [M][N] row-major bf16
+ * (out_f32 = 0) or fp32 (out_f32 != 0), act = ReLU when relu != 0.
+ * Accumulation is fp32 in tensor memory (tcgen05).  Requires M % 128 == 0,
+ * K % 64 == 0, 16 <= N <= 256, N % 16 == 0.  Synchronises `stream`. */
+dm_status dm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A, const void *B,
+                       const float *bias, void *C, int32_t relu, int32_t out_f32,
+                       void *stream);
+
+/* Warm-start network (no counterpart in the paper): a 4-layer MLP
+ * in_dim (<= 64) -> 256 -> 256 -> 256 -> out_dim (<= 64), ReLU, BF16 operands
+ * with FP32 accumulation on the tensor cores, FP32 master weights, Adam.
+ * Inputs are [M][64] bf16 device arrays (columns >= in_dim zero), outputs
+ * and targets fp32 device arrays, M a multiple of 128.  All work is ordered
+ * on `stream`; the calls synchronise it.  Parameters travel as one fp32 host
+ * array: per layer W [out][in] then b [out] on the padded shapes 256x64,
+ * 256x256, 256x256, 64x256 (dm_mlp_num_params entries). */
+typedef struct dm_mlp dm_mlp;
+dm_status dm_mlp_create(int32_t in_dim, int32_t out_dim, uint64_t seed, void *stream,
+                        dm_mlp **out);
+void dm_mlp_destroy(dm_mlp *m);
+int64_t dm_mlp_num_params(void);
+dm_status dm_mlp_get_params(dm_mlp *m, float *host);
+dm_status dm_mlp_set_params(dm_mlp *m, const float *host);
+/* Y [M][64] = network(X) (fp32, columns >= out_dim are zero). */
+dm_status dm_mlp_forward(dm_mlp *m, const void *X, float *Y, int32_t M);
+/* One Adam step (learning rate lr; lr = 0 computes gradients only) on the
+ * mean squared error against Y [M][out_dim]; grads (device, optional) gets
+ * the gradient in the parameter layout, loss the loss before the update. */
+dm_status dm_mlp_train_step(dm_mlp *m, const void *X, const float *Y, int32_t M, float lr,
+                            float *grads, double *loss);
+
 /* Per-kernel profile of dm_step calls made while profiling is on: CUDA-event
  * time on the system's stream, launch count and work units processed
  * (edges, stencils, DOF rows, systems) per kernel id.  Kernel ids:

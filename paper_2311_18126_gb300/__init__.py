@@ -4,4 +4,5 @@ The compute path is the CUDA library ``libdismech.so`` (C ABI in
 ``include/dismech.h``); ``dismech.System`` is its Python binding.
 """
 from .dismech import (System, DismechError, load_library, ensure_built,  # noqa: F401
-                      fp64_peak_gflops, solve_band, solve_band_noalloc)
+                      fp64_peak_gflops, solve_band, solve_band_noalloc,
+                      gemm_bf16, MLP)

@@ -1,0 +1,272 @@
+// BF16 tensor-core GEMM for the learned warm start, written for sm_103a's
+// fifth-generation tensor cores (tcgen05): C = act(A B^T + bias).
+//
+//   A: [M][K] bf16 row-major (K contiguous), B: [N][K] bf16 row-major,
+//   bias: [N] fp32 (or NULL), C: [M][N] bf16 or fp32 row-major.
+//   M % 128 == 0, K % 64 == 0, 16 <= N <= 256, N % 16 == 0.
+//
+// One CTA of 128 threads computes a 128 x N tile.  Operand tiles (128 x 64
+// and N x 64) are staged in shared memory in the tensor core's canonical
+// K-major layout without swizzle (8-row x 16-byte core matrices), a single
+// elected thread issues tcgen05.mma (M = 128, K = 16 per instruction) with
+// the fp32 accumulator in tensor memory, tcgen05.commit signals an mbarrier,
+// and the four warps read their 32 accumulator lanes back with tcgen05.ld
+// for the epilogue (bias, ReLU, conversion).  Two shared-memory stages let
+// the next tile load while the tensor core works on the current one.
+// Every mbarrier wait is bounded: on timeout the kernel records an error
+// flag, skips the rest and frees its tensor memory.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "dm_internal.h"
+
+namespace dm {
+
+namespace {
+
+constexpr int kBM = 128, kBK = 64, kThreads = 128;
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading-byte
+// offset (between core matrices along K), stride-byte offset (between 8-row
+// groups), version 1, no swizzle.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;                // base offset 0, swizzle none
+}
+
+// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4)                      // D format: f32
+         | (1u << 7)                    // A format: bf16
+         | (1u << 10)                   // B format: bf16
+         | ((uint32_t)(N >> 3) << 17)   // N / 8
+         | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait on an mbarrier phase; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// Stores a rows x 64 bf16 tile (row-major source with leading dimension ld
+// elements) into the canonical no-swizzle K-major layout: core matrix
+// (r/8, k/8) at ((r/8) * 8 + k/8) * 128 bytes, row r%8 at 16-byte stride.
+__device__ __forceinline__ void stage_tile(char *dst, const uint16_t *src, int rows, int ld,
+                                           int k0, int tid) {
+  const int chunks = rows * (kBK / 8);  // 16-byte chunks
+  for (int c = tid; c < chunks; c += kThreads) {
+    const int r = c >> 3, kc = c & 7;
+    const uint4 v = *reinterpret_cast<const uint4 *>(src + (size_t)r * ld + k0 + kc * 8);
+    *reinterpret_cast<uint4 *>(dst + ((r >> 3) * 8 + kc) * 128 + (r & 7) * 16) = v;
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads) k_gemm_bf16(const uint16_t *__restrict__ A,
+                                                        const uint16_t *__restrict__ B,
+                                                        const float *__restrict__ bias, void *C,
+                                                        int M, int N, int K, int relu,
+                                                        int out_f32, int *err) {
+  extern __shared__ __align__(1024) char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kBM;
+  const int a_bytes = kBM * kBK * 2, b_bytes = N * kBK * 2;
+  char *sA[2] = {smem, smem + a_bytes + b_bytes};
+  char *sB[2] = {smem + a_bytes, smem + 2 * a_bytes + b_bytes};
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * (a_bytes + b_bytes));
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2);
+  uint32_t ncols = 32;
+  while ((int)ncols < N) ncols <<= 1;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = make_idesc(kBM, N);
+  const int nk = K / kBK;
+  bool ok = true;
+  uint32_t phase[2] = {0, 0};
+
+  for (int kb = 0; kb < nk && ok; ++kb) {
+    const int s = kb & 1;
+    // the stage was last read by the MMAs of block kb - 2
+    if (kb >= 2) {
+      const bool w = mbar_wait(&bar[s], phase[s]);
+      phase[s] ^= 1u;
+      ok = __syncthreads_and(w) != 0;  // uniform decision: no thread is left behind
+      if (!ok) break;
+    }
+    stage_tile(sA[s], A + (size_t)m0 * K, kBM, K, kb * kBK, tid);
+    stage_tile(sB[s], B, N, K, kb * kBK, tid);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a0 = smem_u32(sA[s]), b0 = smem_u32(sB[s]);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        // K = 16 per instruction = two 8-element core matrices (256 bytes)
+        const uint64_t ad = make_desc(a0 + kk * 256, 128, 1024);
+        const uint64_t bd = make_desc(b0 + kk * 256, 128, 1024);
+        mma_bf16(tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(&bar[s]);
+    }
+    __syncthreads();
+  }
+  // the last commit covers every MMA issued before it
+  {
+    const int sl = (nk - 1) & 1;
+    const bool w = ok ? mbar_wait(&bar[sl], phase[sl]) : false;
+    ok = __syncthreads_and(w) != 0;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (!ok) {
+    if (lane == 0) atomicExch(err, 1);
+  } else {
+    // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
+    const int row = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < N; c0 += 8) {
+      uint32_t r[8];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+            "=r"(r[6]), "=r"(r[7])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        v[j] = __uint_as_float(r[j]) + (bias ? bias[c0 + j] : 0.0f);
+        if (relu) v[j] = fmaxf(v[j], 0.0f);
+      }
+      if (row < M) {
+        if (out_f32) {
+          float *o = reinterpret_cast<float *>(C) + (size_t)row * N + c0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) o[j] = v[j];
+        } else {
+          uint16_t *o = reinterpret_cast<uint16_t *>(C) + (size_t)row * N + c0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(v[j]);
+            o[j] = *reinterpret_cast<const uint16_t *>(&b);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+size_t gemm_smem_bytes(int N) { return 2 * (size_t)(kBM * kBK * 2 + N * kBK * 2) + 64; }
+
+// Launches k_gemm_bf16; err: device int (set to 1 on a barrier timeout).
+cudaError_t launch_gemm_bf16(int M, int N, int K, const void *A, const void *B, const float *bias,
+                             void *C, int relu, int out_f32, int *err, cudaStream_t st) {
+  static bool attr_set = false;
+  const size_t smem = gemm_smem_bytes(256);
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_gemm_bf16<<<M / kBM, kThreads, gemm_smem_bytes(N), st>>>(
+      (const uint16_t *)A, (const uint16_t *)B, bias, C, M, N, K, relu, out_f32, err);
+  return cudaGetLastError();
+}
+
+bool check_gemm_shape(int M, int N, int K) {
+  return M > 0 && M % kBM == 0 && K > 0 && K % kBK == 0 && N >= 16 && N <= 256 && N % 16 == 0;
+}
+
+}  // namespace dm
+
+extern "C" dm_status dm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A, const void *B,
+                                  const float *bias, void *C, int32_t relu, int32_t out_f32,
+                                  void *stream) {
+  using namespace dm;
+  if (!A || !B || !C || !check_gemm_shape(M, N, K)) {
+    set_error("dm_gemm_bf16: need M % 128 == 0, K % 64 == 0, N in [16, 256] with N % 16 == 0");
+    return DM_ERR_INVALID_ARG;
+  }
+  int *err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    set_error("dm_gemm_bf16: cudaMalloc");
+    return DM_ERR_OOM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = launch_gemm_bf16(M, N, K, A, B, bias, C, relu, out_f32, err, st);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(err);
+  if (e != cudaSuccess) {
+    set_error(std::string("dm_gemm_bf16: ") + cudaGetErrorString(e));
+    return DM_ERR_CUDA;
+  }
+  if (h) {
+    set_error("dm_gemm_bf16: tensor-core completion barrier timed out");
+    return DM_ERR_CUDA;
+  }
+  return DM_OK;
+}

@@ -107,6 +107,25 @@ def load_library(path=LIB_PATH):
     lib.dm_solve_band_noalloc.restype = C.c_int
     lib.dm_debug_copy.argtypes = [H, C.c_char_p, _dp, C.c_int64]
     lib.dm_debug_copy.restype = C.c_int
+    lib.dm_gemm_bf16.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
+    lib.dm_gemm_bf16.restype = C.c_int
+    lib.dm_mlp_create.argtypes = [C.c_int32, C.c_int32, C.c_uint64, C.c_void_p,
+                                  C.POINTER(C.c_void_p)]
+    lib.dm_mlp_create.restype = C.c_int
+    lib.dm_mlp_destroy.argtypes = [C.c_void_p]
+    lib.dm_mlp_destroy.restype = None
+    lib.dm_mlp_num_params.argtypes = []
+    lib.dm_mlp_num_params.restype = C.c_int64
+    lib.dm_mlp_get_params.argtypes = [C.c_void_p, C.POINTER(C.c_float)]
+    lib.dm_mlp_get_params.restype = C.c_int
+    lib.dm_mlp_set_params.argtypes = [C.c_void_p, C.POINTER(C.c_float)]
+    lib.dm_mlp_set_params.restype = C.c_int
+    lib.dm_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+    lib.dm_mlp_forward.restype = C.c_int
+    lib.dm_mlp_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
+                                      C.c_void_p, C.POINTER(C.c_double)]
+    lib.dm_mlp_train_step.restype = C.c_int
     lib.dm_last_error.argtypes = []
     lib.dm_last_error.restype = C.c_char_p
     _lib = lib
@@ -336,6 +355,64 @@ def solve_band_noalloc(sys_dof0, sys_ndof, band, rhs, x, stream=None):
                                      x.numel(), _dev_ptr(band), _dev_ptr(rhs), _dev_ptr(x),
                                      stream))
     return x
+
+
+def gemm_bf16(A, B, bias, C, relu=False, stream=None):
+    """C = act(A B^T + bias) on the tcgen05 tensor cores (torch CUDA tensors:
+    A [M, K] and B [N, K] bfloat16, bias [N] float32 or None, C [M, N]
+    bfloat16 or float32)."""
+    lib = load_library()
+    M, K = A.shape
+    N = B.shape[0]
+    out_f32 = 1 if C.dtype.itemsize == 4 else 0
+    _check(lib.dm_gemm_bf16(M, N, K, _dev_ptr(A), _dev_ptr(B),
+                            _dev_ptr(bias) if bias is not None else None, _dev_ptr(C),
+                            int(bool(relu)), out_f32, stream))
+    return C
+
+
+class MLP:
+    """The warm-start network of the library (tensor-core training and
+    inference).  Device buffers are torch CUDA tensors."""
+
+    def __init__(self, in_dim, out_dim, seed=0, stream=None):
+        self._lib = load_library()
+        h = C.c_void_p()
+        _check(self._lib.dm_mlp_create(in_dim, out_dim, seed, stream, C.byref(h)))
+        self._h = h
+        self.in_dim, self.out_dim = in_dim, out_dim
+        self.n_params = int(self._lib.dm_mlp_num_params())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dm_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        p = np.zeros(self.n_params, np.float32)
+        _check(self._lib.dm_mlp_get_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float))))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, np.float32))
+        _check(self._lib.dm_mlp_set_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def forward(self, X, Y):
+        _check(self._lib.dm_mlp_forward(self._h, _dev_ptr(X), _dev_ptr(Y), X.shape[0]))
+        return Y
+
+    def train_step(self, X, Y, lr, grads=None):
+        loss = C.c_double()
+        _check(self._lib.dm_mlp_train_step(self._h, _dev_ptr(X), _dev_ptr(Y), X.shape[0],
+                                           float(lr), _dev_ptr(grads) if grads is not None
+                                           else None, C.byref(loss)))
+        return loss.value
 
 
 def fp64_peak_gflops():

@@ -461,3 +461,27 @@ def test_friction_kinetic_energy_closed_form(push):
     else:
         expect = T * T / (2 * m) * (push - mu * m * g) ** 2
         assert Ek == pytest.approx(expect, rel=0.03)
+
+
+# ---------------------------------------------------------------------------
+# Warm-start network reference: backward pass = finite differences of the loss
+# ---------------------------------------------------------------------------
+
+def test_mlp_reference_gradient_matches_central_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    n = sum(fo * fi + fo for fi, fo in zip(mlp.DIN, mlp.DOUT))
+    params = rng.standard_normal(n) * 0.05
+    X = np.zeros((6, 64))
+    X[:, :20] = rng.standard_normal((6, 20))
+    Y = rng.standard_normal((6, 4))
+    loss, g = mlp.loss_and_grad(params, X, Y, 4)
+    idx = rng.choice(n, size=40, replace=False)
+    h = 1e-6
+    for i in idx:
+        p1 = params.copy()
+        p1[i] += h
+        p2 = params.copy()
+        p2[i] -= h
+        fd = (mlp.loss_and_grad(p1, X, Y, 4)[0] - mlp.loss_and_grad(p2, X, Y, 4)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-9
