@@ -257,11 +257,47 @@ dm_status dm_mlp_forward(dm_mlp *m, const void *X, float *Y, int32_t M);
 dm_status dm_mlp_train_step(dm_mlp *m, const void *X, const float *Y, int32_t M, float lr,
                             float *grads, double *loss);
 
+/* Learned warm start of the Newton iteration (no counterpart in the paper;
+ * the paper starts each step from the previous state).  One segment per rod
+ * node i >= 1: the network maps 64 features of the committed step, in the
+ * local frame of edge i-1, to a correction (3 position components in units
+ * of the edge rest length, 1 twist angle) of the guess q_n + dt qdot_n for
+ * node i and edge i-1.  Newton then runs to the same tolerance from the
+ * corrected guess, so only the iteration count changes.
+ *
+ * dm_ws_enable builds the segment tables (idempotent).  dm_ws_num_segments
+ * returns their number S (0 before enabling).  dm_ws_capture_features writes
+ * the raw fp32 features [S][64] of the committed state to device memory and
+ * remembers the extrapolated guess; after dm_step, dm_ws_capture_targets
+ * writes the fp32 targets [S][4] (converged q minus that guess, local frame)
+ * to device memory.  Both are asynchronous on the system's stream.
+ * dm_ws_set_model attaches a network (dm_mlp with out_dim 4; NULL detaches)
+ * and its normalisation, 132 host floats: input mean [64], input std [64],
+ * output scale [4]; the system does not own the network, which must outlive
+ * its use.  While attached, every dm_step evaluates it on the tensor cores
+ * before the first Newton iteration.
+ * dm_ws_prepare_batch gathers rows idx[M] of device feature/target arrays
+ * into a normalised bf16 input [M][64] and fp32 target [M][4] (all device
+ * pointers, norm included).  dm_ws_column_stats writes the mean and standard
+ * deviation of each column of a device fp32 [rows][cols] array to stats
+ * [2][cols] (device).  Errors: DM_ERR_INVALID_ARG on NULL or unenabled. */
+dm_status dm_ws_enable(dm_system *sys);
+int64_t dm_ws_num_segments(const dm_system *sys);
+dm_status dm_ws_capture_features(dm_system *sys, float *features);
+dm_status dm_ws_capture_targets(dm_system *sys, float *targets);
+dm_status dm_ws_set_model(dm_system *sys, dm_mlp *net, const float *norm);
+dm_status dm_ws_prepare_batch(const float *features, const float *targets, const int64_t *idx,
+                              int32_t M, const float *norm, void *X, float *Y, void *stream);
+dm_status dm_ws_column_stats(const float *data, int64_t rows, int32_t cols, float *stats,
+                             void *stream);
+
 /* Per-kernel profile of dm_step calls made while profiling is on: CUDA-event
  * time on the system's stream, launch count and work units processed
  * (edges, stencils, DOF rows, systems) per kernel id.  Kernel ids:
  * 0 edge frames + stretch, 1 bend-twist stencils, 2 residual/Jacobian rows,
- * 3 banded solve, 4 step begin, 5 step commit.  Profiling adds two event
+ * 3 banded solve, 4 step begin, 5 step commit, 6 ground contact/friction,
+ * 7 general residual rows, 8 general assembly, 9 limb/Schur solve,
+ * 10 learned warm start (features + network + apply).  Profiling adds two event
  * records per launch; it is off by default. */
 #define DM_NUM_KERNELS 16
 typedef struct dm_profile {

@@ -78,12 +78,12 @@ __global__ void k_scatter_kbar(int n, const int32_t *slot2st, int slot0, int ns,
 
 enum {
   K_EDGE = 0, K_STENCIL = 1, K_ROWS = 2, K_SOLVE = 3, K_BEGIN = 4, K_COMMIT = 5,
-  K_NODES = 6, K_ROWS_GEN = 7, K_ASM_GEN = 8, K_SOLVE_GEN = 9
+  K_NODES = 6, K_ROWS_GEN = 7, K_ASM_GEN = 8, K_SOLVE_GEN = 9, K_WARM = 10
 };
 const char *kKernelNames[DM_NUM_KERNELS] = {
     "edge_frames_stretch", "bend_twist_stencil", "residual_jacobian_rows", "band_ldlt_solve",
     "step_begin",          "step_commit",        "ground_contact_friction", "residual_rows_general",
-    "assemble_general",    "limb_schur_solve"};
+    "assemble_general",    "limb_schur_solve",   "learned_warm_start"};
 
 struct Extra {
   bool prof = false;
@@ -97,6 +97,10 @@ struct Extra {
   int32_t *ls_action = nullptr, *ls_trial = nullptr, *ls_nback = nullptr;
   double *ls_alpha = nullptr, *ls_racc = nullptr, *ls_qacc = nullptr, *ls_merit = nullptr;
   int n_rod_sys = 0;
+  int n_fast = 0, n_slow = 0;   // general systems on the condensation / Schur path
+  size_t border_smem = 0;
+  int limb_nmax = 0, wpb_factor = 1, wpb_back = 1;  // limb kernels: rows, warps per block
+  size_t smem_factor = 0, smem_back = 0;
   int solve_blocks = 1;
   size_t solve_smem = 0;
   std::vector<int32_t> slot2st;
@@ -270,7 +274,45 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     DM_TRY(upload(s, &d.lb_y, T.lb_y));
     DM_TRY(upload(s, &d.border_dof, T.border_dof));
     DM_TRY(upload(s, &d.coupled_rows, T.coupled_rows));
+    DM_TRY(upload(s, &d.gs_fast, T.gs_fast));
+    DM_TRY(upload(s, &d.lb_gsys, T.lb_gsys));
+    DM_TRY(upload(s, &d.lb_dir, T.lb_dir));
+    DM_TRY(upload(s, &d.lb_m, T.lb_m));
+    DM_TRY(upload(s, &d.lb_nbc, T.lb_nbc));
+    DM_TRY(upload(s, &d.lb_bc0, T.lb_bc0));
+    DM_TRY(upload(s, &d.lb_bcols, T.lb_bcols));
+    DM_TRY(dalloc(s, &d.gen_go, T.gen_sys.size()));
+    DM_TRY(dalloc(s, &d.gen_bad, T.gen_sys.size()));
+    DM_CK(cudaMemset(d.gen_bad, 0, T.gen_sys.size() * sizeof(int32_t)));
+    for (size_t w = 0; w < T.gen_sys.size(); ++w) {
+      if (T.gs_fast[w]) {
+        s->x.n_fast++;
+        s->x.border_smem = std::max<size_t>(
+            s->x.border_smem, (size_t)(T.gs_nB[w] * T.gs_nB[w] + T.gs_nB[w]) * sizeof(double));
+      } else {
+        s->x.n_slow++;
+      }
+    }
+    if (s->x.border_smem > 48 * 1024)
+      DM_CK(cudaFuncSetAttribute(k_gen_border, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)s->x.border_smem));
+    for (size_t L = 0; L < T.lb_n.size(); ++L)
+      if (T.gs_fast[T.lb_gsys[L]]) s->x.limb_nmax = std::max(s->x.limb_nmax, T.lb_n[L]);
+    {
+      // warps per block: up to 4, within 200 KB of shared memory per block
+      const size_t pf = gen_factor_smem(s->x.limb_nmax) * sizeof(double);
+      const size_t pb = gen_back_smem(s->x.limb_nmax) * sizeof(double);
+      s->x.wpb_factor = (int)std::max<size_t>(1, std::min<size_t>(4, (200 << 10) / pf));
+      s->x.wpb_back = (int)std::max<size_t>(1, std::min<size_t>(4, (200 << 10) / pb));
+      s->x.smem_factor = pf * s->x.wpb_factor;
+      s->x.smem_back = pb * s->x.wpb_back;
+      DM_CK(cudaFuncSetAttribute(k_gen_limb_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)s->x.smem_factor));
+      DM_CK(cudaFuncSetAttribute(k_gen_limb_back, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)s->x.smem_back));
+    }
     DM_TRY(upload(s, &d.asm_target, T.asm_target));
+    DM_TRY(upload(s, &d.asm_sys, T.asm_sys));
     DM_TRY(upload(s, &d.asm_ptr, T.asm_ptr));
     DM_TRY(upload(s, &d.asm_src, T.asm_src));
     DM_TRY(upload(s, &d.gat_ptr, T.gat_ptr));
@@ -380,6 +422,7 @@ void dm_destroy(dm_system *sys) {
   for (int k = 0; k < 2 * DM_NUM_KERNELS; ++k)
     if (sx->x.ev[k]) cudaEventDestroy(sx->x.ev[k]);
   if (sys->h_ctrl) cudaFreeHost(sys->h_ctrl);
+  dm::ws_free(sys->ws);
   delete static_cast<dm_system_ext *>(sys);
 }
 
@@ -455,8 +498,9 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   rg.dof_comp = d.dof_comp; rg.sys_kind = s->x.d_sys_kind; rg.sys_active = d.sys_active;
   rg.gat_ptr = d.gat_ptr; rg.gat_ent = d.gat_ent; rg.sg = d.sg; rg.es = d.es;
   rg.nt = T.ground ? d.nt : nullptr; rg.f = d.f; rg.sys_res = d.sys_res;
+  const bool ls_on = s->prm.line_search != 0;
   AsmArgs aa{(int)T.asm_target.size(), d.asm_target, d.asm_ptr, d.asm_src, d.sh, d.es, d.nt,
-             d.dconst, d.gen};
+             d.dconst, d.gen, d.asm_sys, d.sys_active, ls_on ? s->x.ls_action : nullptr};
   SolveGenArgs ga{};
   ga.ngen = (int)T.gen_sys.size(); ga.max_iter = s->p.max_iter; ga.tol = s->p.tol;
   ga.gen_sys = d.gen_sys; ga.gs_limb0 = d.gs_limb0; ga.gs_nlimb = d.gs_nlimb; ga.gs_nB = d.gs_nB;
@@ -470,10 +514,20 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   ga.units = s->x.prof ? s->x.d_units + K_SOLVE_GEN : nullptr;
   ga.ls_action = s->x.ls_action;
   ga.ls_trial = s->x.ls_trial;
+  ga.nlimb = (int)T.lb_n.size();
+  ga.limb_nmax = s->x.limb_nmax;
+  ga.gs_fast = d.gs_fast; ga.lb_gsys = d.lb_gsys; ga.lb_dir = d.lb_dir; ga.lb_m = d.lb_m;
+  ga.lb_nbc = d.lb_nbc; ga.lb_bc0 = d.lb_bc0; ga.lb_bcols = d.lb_bcols;
+  ga.gen_go = d.gen_go; ga.gen_bad = d.gen_bad;
   LineSearchArgs la{S, nd, d.sys_active, s->x.d_dof_sys, d.sys_dof0, d.sys_ndof, d.f, d.rscale,
                     s->x.ls_action, s->x.ls_trial, s->x.ls_nback, s->x.ls_alpha, s->x.ls_racc,
-                    s->x.ls_merit, d.q, s->x.ls_qacc};
-  const bool ls_on = s->prm.line_search != 0;
+                    s->x.ls_merit, d.q, s->x.ls_qacc, nullptr};
+  // learned initial guess: with the line search it is tried against the
+  // extrapolation (first round evaluates the extrapolation, the second the
+  // learned guess, which is kept only if it lowers the merit)
+  const bool ws_on = ws_active(s);
+  const bool ws_trial = ws_on && ls_on;
+  if (ws_trial) la.wstry = ws_trial_flags(s);
   const int max_rounds = ls_on ? 13 * (s->p.max_iter + 1) : s->p.max_iter + 1;
   const bool gen_on = T.any_general, rod_on = s->x.n_rod_sys > 0;
   if (stats) {
@@ -490,9 +544,14 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       Timed t(s, K_BEGIN, st);
       k_begin_step<<<blocks(std::max(nd, S), 256), 256, 0, st>>>(sa);
     }
+    if (ws_on) {
+      Timed t(s, K_WARM, st);
+      DM_CK(ws_predict(s, st, ws_trial));
+    }
     if (ls_on) {
       DM_CK(cudaMemsetAsync(s->x.ls_trial, 0, S * sizeof(int32_t), st));
       DM_CK(cudaMemsetAsync(s->x.ls_nback, 0, S * sizeof(int32_t), st));
+      if (ws_trial) DM_CK(cudaMemsetAsync(la.wstry, 0, S * sizeof(int32_t), st));
     }
     for (int it = 0; it < max_rounds; ++it) {
       DM_CK(cudaMemsetAsync(d.sys_res, 0, S * sizeof(unsigned long long), st));
@@ -522,6 +581,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
         k_ls_merit<<<blocks((int64_t)S * 32, 128), 128, 0, st>>>(la);
         k_ls_decide<<<blocks(S, 128), 128, 0, st>>>(la);
         k_ls_apply<<<blocks(nd, 256), 256, 0, st>>>(la);
+        if (ws_trial && it == 0) DM_CK(ws_inject(s, st, s->x.ls_action, s->x.ls_trial));
       }
       if (rod_on) {
         {
@@ -537,7 +597,16 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
         }
         {
           Timed t(s, K_SOLVE_GEN, st);
-          k_solve_gen<<<blocks((int64_t)ga.ngen * 32, 128), 128, 0, st>>>(ga);
+          if (s->x.n_fast) {
+            const int wf = s->x.wpb_factor, wb = s->x.wpb_back;
+            if (ga.nlimb)
+              k_gen_limb_factor<<<(ga.nlimb + wf - 1) / wf, 32 * wf, s->x.smem_factor, st>>>(ga);
+            k_gen_border<<<ga.ngen, 32, s->x.border_smem, st>>>(ga);
+            if (ga.nlimb)
+              k_gen_limb_back<<<(ga.nlimb + wb - 1) / wb, 32 * wb, s->x.smem_back, st>>>(ga);
+          }
+          if (s->x.n_slow)
+            k_solve_gen<<<blocks((int64_t)ga.ngen * 32, 128), 128, 0, st>>>(ga);
         }
       }
       DM_CK(cudaGetLastError());

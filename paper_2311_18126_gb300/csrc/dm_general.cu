@@ -117,6 +117,8 @@ __global__ void __launch_bounds__(256) k_rows_gen(RowGenArgs a) {
 __global__ void k_assemble_gen(AsmArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.ntarget) return;
+  const int sy = a.tsys[t];
+  if (!a.sys_active[sy] || (a.ls_action && a.ls_action[sy] == 1)) return;  // no solve
   double v = 0.0;
   for (int k = a.ptr[t]; k < a.ptr[t + 1]; ++k) {
     const uint32_t code = a.src[k];
@@ -134,7 +136,7 @@ __global__ void k_assemble_gen(AsmArgs a) {
 __global__ void k_solve_gen(SolveGenArgs a) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= a.ngen) return;
+  if (w >= a.ngen || a.gs_fast[w]) return;  // condensation path systems
   const int s = a.gen_sys[w];
   int st = 0;
   int go = 0;

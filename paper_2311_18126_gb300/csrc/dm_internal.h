@@ -24,6 +24,12 @@ enum SolverKind : int32_t {
 };
 
 // Gather-map source codes for the general assembly (see dm_general.cu).
+// Limits of the condensation path of general systems.
+constexpr int kFastMaxM = 10;        // coupled rows at one limb end
+constexpr int kFastMaxBC = 16;       // border columns one limb couples to
+constexpr int kFastMaxBorder = 96;   // border DOFs of one system
+constexpr int kFastMaxRows = 1200;   // rows of one limb (shared-memory staging)
+
 enum SrcType : uint32_t { SRC_STENCIL = 0, SRC_EDGE = 1, SRC_NODE = 2, SRC_DIAG = 3 };
 inline uint32_t src_code(uint32_t type, uint32_t index, bool neg) {
   return (neg ? 0x80000000u : 0u) | (type << 29) | index;
@@ -68,12 +74,17 @@ struct HostTopology {
   std::vector<int64_t> gs_JBB, gs_rB, gs_S, gs_xB, gs_mat0, gs_mat1;
   std::vector<int32_t> lb_dof0, lb_n, lb_ncr, lb_cr0;
   std::vector<int64_t> lb_band, lb_piv, lb_C, lb_R, lb_Y, lb_y;
+  // condensation path (systems whose limbs attach at one end): per system
+  // flag; per limb its system, elimination direction (1 = from the last
+  // row), trailing block size m and coupled border columns
+  std::vector<int32_t> gs_fast, lb_gsys, lb_dir, lb_m, lb_nbc, lb_bc0, lb_bcols;
   std::vector<int32_t> border_dof;         // global DOF of each border entry
   std::vector<int32_t> coupled_rows;       // limb-local rows coupled to border
   int64_t gen_doubles = 0;                 // size of the general scratch
   // gather map for the general assembly: target (offset into the general
   // scratch) <- sum of sources
   std::vector<int64_t> asm_target;
+  std::vector<int32_t> asm_sys;            // system of each target
   std::vector<int32_t> asm_ptr;
   std::vector<uint32_t> asm_src;
   bool any_general = false, ground = false;
@@ -141,7 +152,11 @@ struct DevArrays {
   int32_t *lb_dof0 = nullptr, *lb_n = nullptr, *lb_ncr = nullptr, *lb_cr0 = nullptr;
   int64_t *lb_band = nullptr, *lb_piv = nullptr, *lb_C = nullptr, *lb_R = nullptr, *lb_Y = nullptr, *lb_y = nullptr;
   int32_t *border_dof = nullptr, *coupled_rows = nullptr;
+  int32_t *gs_fast = nullptr, *lb_gsys = nullptr, *lb_dir = nullptr, *lb_m = nullptr,
+          *lb_nbc = nullptr, *lb_bc0 = nullptr, *lb_bcols = nullptr;
+  int32_t *gen_go = nullptr, *gen_bad = nullptr;  // per general system
   int64_t *asm_target = nullptr;
+  int32_t *asm_sys = nullptr;
   int32_t *asm_ptr = nullptr;
   uint32_t *asm_src = nullptr;
 };
@@ -153,6 +168,18 @@ struct Params {
   double eta;
 };
 
+// Learned warm start (dm_warmstart.cu).
+struct WarmStart;
+void ws_free(WarmStart *w);
+bool ws_active(const dm_system *s);  // a network is attached
+// Evaluates the network on the committed state.  defer = false: the guess
+// replaces the extrapolation in q; defer = true: it is kept for ws_inject.
+cudaError_t ws_predict(dm_system *s, cudaStream_t st, bool defer);
+// After the first line-search round: q <- learned guess for every active
+// system, marked as a trial (no solve this round).
+cudaError_t ws_inject(dm_system *s, cudaStream_t st, int32_t *ls_action, int32_t *ls_trial);
+int32_t *ws_trial_flags(dm_system *s);
+
 }  // namespace dm
 
 struct dm_system {
@@ -163,5 +190,6 @@ struct dm_system {
   cudaStream_t stream = nullptr;
   std::vector<void *> allocations;
   int32_t *h_ctrl = nullptr;  // pinned
+  dm::WarmStart *ws = nullptr;
 };
 

@@ -86,6 +86,8 @@ struct AsmArgs {
   const uint32_t *src;
   const double *sh, *es, *nt, *dconst;
   double *gen;
+  const int32_t *tsys;       // system of each target
+  const int32_t *sys_active, *ls_action;
 };
 
 struct SolveGenArgs {
@@ -104,7 +106,17 @@ struct SolveGenArgs {
   unsigned long long *units;
   const int32_t *ls_action;
   int32_t *ls_trial;
+  // condensation path
+  int nlimb, limb_nmax;  // limbs; most rows of a condensation-path limb
+  const int32_t *gs_fast, *lb_gsys, *lb_dir, *lb_m, *lb_nbc, *lb_bc0, *lb_bcols;
+  int32_t *gen_go, *gen_bad;
 };
+
+// shared memory (doubles) per warp of the condensation-path limb kernels
+__host__ __device__ constexpr size_t gen_factor_smem(int nmax) {
+  return (size_t)nmax * 22 + kFastMaxM * (kFastMaxM + kFastMaxBC + 1);
+}
+__host__ __device__ constexpr size_t gen_back_smem(int nmax) { return (size_t)nmax * 12 + 16; }
 
 struct LineSearchArgs {
   int nsys, nd;
@@ -112,6 +124,7 @@ struct LineSearchArgs {
   const double *f, *rscale;
   int32_t *action, *trial, *nback;
   double *alpha, *racc, *merit, *q, *qacc;
+  int32_t *wstry;  // NULL, or 1 while the trial is the learned initial guess
 };
 __global__ void k_ls_merit(LineSearchArgs a);
 __global__ void k_ls_decide(LineSearchArgs a);
@@ -121,6 +134,9 @@ __global__ void k_nodes(NodeArgs a);
 __global__ void k_rows_gen(RowGenArgs a);
 __global__ void k_assemble_gen(AsmArgs a);
 __global__ void k_solve_gen(SolveGenArgs a);
+__global__ void k_gen_limb_factor(SolveGenArgs a);
+__global__ void k_gen_border(SolveGenArgs a);
+__global__ void k_gen_limb_back(SolveGenArgs a);
 
 __global__ void k_edge(EdgeArgs a);
 __global__ void k_stencil(StencilArgs a);

@@ -201,6 +201,23 @@ cudaError_t forward(dm_mlp *m, const uint16_t *X, int M) {
 
 }  // namespace
 
+namespace dm {
+// Forward pass on `st` without synchronisation (used inside dm_step);
+// returns the fp32 output [M][64] (owned by the network) or nullptr.
+float *mlp_forward_async(dm_mlp *m, const void *X, int M, cudaStream_t st, int *err) {
+  if (!m || M <= 0 || M % 128) return nullptr;
+  if (ensure_batch(m, M) != DM_OK) return nullptr;
+  cudaStream_t keep = m->stream;
+  int *keep_err = m->err;
+  m->stream = st;
+  m->err = err;
+  const cudaError_t e = forward(m, (const uint16_t *)X, M);
+  m->stream = keep;
+  m->err = keep_err;
+  return e == cudaSuccess ? m->out32 : nullptr;
+}
+}  // namespace dm
+
 extern "C" {
 
 dm_status dm_mlp_create(int32_t in_dim, int32_t out_dim, uint64_t seed, void *stream,

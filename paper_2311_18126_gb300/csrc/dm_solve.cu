@@ -456,6 +456,18 @@ __global__ void k_ls_decide(LineSearchArgs a) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.nsys || !a.sys_active[s]) return;
   const double m = a.merit[s];
+  if (a.wstry && a.wstry[s]) {
+    // the learned guess is kept only if it lowers the merit below that of
+    // the extrapolation; otherwise the iterate returns to the extrapolation
+    a.wstry[s] = 0;
+    if (!(m <= (1.0 - 1e-4) * a.racc[s])) {
+      a.action[s] = 1;
+      a.alpha[s] = 0.0;
+      a.trial[s] = 0;
+      a.nback[s] = 0;
+      return;
+    }
+  }
   if (a.trial[s] && a.nback[s] < 12 && !(m <= (1.0 - 1e-4 * a.alpha[s]) * a.racc[s])) {
     a.action[s] = 1;
     a.alpha[s] *= 0.5;
@@ -474,7 +486,7 @@ __global__ void k_ls_apply(LineSearchArgs a) {
   if (i >= a.nd) return;
   const int s = a.dof_sys[i];
   if (!a.sys_active[s]) return;
-  if (a.action[s] == 1) a.q[i] = 0.5 * (a.q[i] + a.qacc[i]);
+  if (a.action[s] == 1) a.q[i] = a.alpha[s] == 0.0 ? a.qacc[i] : 0.5 * (a.q[i] + a.qacc[i]);
   else a.qacc[i] = a.q[i];
 }
 

@@ -635,18 +635,49 @@ bool build_topology(const dm_system_desc *D, const dm_params *P, HostTopology &T
       }
       ent.emplace_back(g, g, src_code(SRC_DIAG, (uint32_t)g, false));
     }
-    // coupled rows per limb
-    std::vector<std::vector<int32_t>> crow(nl);
+    // coupled rows (limb-local, natural order) and coupled border columns
+    std::vector<std::vector<int32_t>> crow(nl), bcl(nl);
     for (auto &t : ent) {
       const int32_t g1 = std::get<0>(t), g2 = std::get<1>(t);
-      if (dof_limb[g1] >= 0 && dof_bidx[g2] >= 0) crow[dof_limb[g1] - mylimbs[0]].push_back(dof_row[g1]);
-      if (dof_bidx[g1] >= 0 && dof_limb[g2] >= 0) crow[dof_limb[g2] - mylimbs[0]].push_back(dof_row[g2]);
+      if (dof_limb[g1] >= 0 && dof_bidx[g2] >= 0) {
+        crow[dof_limb[g1] - mylimbs[0]].push_back(dof_row[g1]);
+        bcl[dof_limb[g1] - mylimbs[0]].push_back(dof_bidx[g2]);
+      }
+      if (dof_bidx[g1] >= 0 && dof_limb[g2] >= 0) {
+        crow[dof_limb[g2] - mylimbs[0]].push_back(dof_row[g2]);
+        bcl[dof_limb[g2] - mylimbs[0]].push_back(dof_bidx[g1]);
+      }
     }
-    std::vector<std::vector<int32_t>> crmap(nl);
+    // Condensation path: every limb couples to the border only through its
+    // first or its last kFastMaxM rows (a rod attached at one end).  The
+    // limb is then eliminated from its free end, leaving an m x m block.
+    bool fast = nB <= kFastMaxBorder;
+    std::vector<int32_t> ldir(nl, 0), lm(nl, 0);
     for (int l = 0; l < nl; ++l) {
-      std::sort(crow[l].begin(), crow[l].end());
-      crow[l].erase(std::unique(crow[l].begin(), crow[l].end()), crow[l].end());
+      auto &c = crow[l];
+      std::sort(c.begin(), c.end());
+      c.erase(std::unique(c.begin(), c.end()), c.end());
+      auto &b = bcl[l];
+      std::sort(b.begin(), b.end());
+      b.erase(std::unique(b.begin(), b.end()), b.end());
+      const int n = T.lb_n[mylimbs[l]];
+      if (n > kFastMaxRows) fast = false;
+      if (c.empty()) continue;
+      if (c.back() < kFastMaxM) {
+        ldir[l] = 1;
+        lm[l] = c.back() + 1;
+      } else if (c.front() >= n - kFastMaxM) {
+        lm[l] = n - c.front();
+      } else {
+        fast = false;
+      }
+      if ((int)b.size() > kFastMaxBC) fast = false;
+    }
+    T.gs_fast.push_back(fast ? 1 : 0);
+    std::vector<std::vector<int32_t>> crmap(nl), bcmap(nl);
+    for (int l = 0; l < nl; ++l) {
       const int L = mylimbs[l];
+      T.lb_gsys.push_back(gid);
       T.lb_ncr.push_back((int32_t)crow[l].size());
       T.lb_cr0.push_back((int32_t)T.coupled_rows.size());
       crmap[l].assign(T.lb_n[L], -1);
@@ -655,12 +686,32 @@ bool build_topology(const dm_system_desc *D, const dm_params *P, HostTopology &T
         crmap[l][crow[l][k]] = (int32_t)k;
       }
       const int64_t n = T.lb_n[L], ncr = (int64_t)crow[l].size();
-      T.lb_band.push_back(off); off += 31 * n;   // kl = 10, ku + fill = 20
-      T.lb_piv.push_back(off); off += n;
-      T.lb_C.push_back(off); off += ncr * nB;
-      T.lb_R.push_back(off); off += ncr * nB;
-      T.lb_Y.push_back(off); off += n * nB;
-      T.lb_y.push_back(off); off += n;
+      const int64_t nbc = (int64_t)bcl[l].size(), m = lm[l];
+      T.lb_dir.push_back(fast ? ldir[l] : 0);
+      T.lb_m.push_back(fast ? (int32_t)m : 0);
+      T.lb_nbc.push_back(fast ? (int32_t)nbc : 0);
+      T.lb_bc0.push_back((int32_t)T.lb_bcols.size());
+      bcmap[l].assign(nB, -1);
+      if (fast)
+        for (int64_t k = 0; k < nbc; ++k) {
+          T.lb_bcols.push_back(bcl[l][k]);
+          bcmap[l][bcl[l][k]] = (int32_t)k;
+        }
+      if (fast) {
+        T.lb_band.push_back(off); off += 21 * n;   // row-major [n][21]
+        T.lb_piv.push_back(off); off += n;         // reciprocal pivots
+        T.lb_C.push_back(off); off += m * nbc;
+        T.lb_R.push_back(off); off += nbc * m;
+        T.lb_Y.push_back(off); off += m * (nbc + 1);
+        T.lb_y.push_back(off); off += n;
+      } else {
+        T.lb_band.push_back(off); off += 31 * n;   // kl = 10, ku + fill = 20
+        T.lb_piv.push_back(off); off += n;
+        T.lb_C.push_back(off); off += ncr * nB;
+        T.lb_R.push_back(off); off += ncr * nB;
+        T.lb_Y.push_back(off); off += n * nB;
+        T.lb_y.push_back(off); off += n;
+      }
     }
     T.gs_JBB.push_back(off); off += (int64_t)nB * nB;
     T.gs_rB.push_back(off); off += nB;
@@ -673,17 +724,34 @@ bool build_topology(const dm_system_desc *D, const dm_params *P, HostTopology &T
       const uint32_t src = std::get<2>(t);
       int64_t tgt = -1;
       const int L1 = dof_limb[g1], L2 = dof_limb[g2];
+      // row of limb L in the elimination order of the condensation path
+      auto mapped = [&](int L, int r) { return T.lb_dir[L] ? T.lb_n[L] - 1 - r : r; };
       if (L1 >= 0 && L2 >= 0) {
         const int r1 = dof_row[g1], r2 = dof_row[g2];
         if (L1 != L2 || r2 - r1 > 10 || r1 - r2 > 10) {
           set_error("internal: element couples DOFs outside a limb band");
           return false;
         }
-        tgt = T.lb_band[L1] + (int64_t)(r2 - r1 + 10) * T.lb_n[L1] + r1;
+        if (fast) {
+          const int p1 = mapped(L1, r1), p2 = mapped(L1, r2);
+          tgt = T.lb_band[L1] + (int64_t)p1 * 21 + (p2 - p1 + 10);
+        } else {
+          tgt = T.lb_band[L1] + (int64_t)(r2 - r1 + 10) * T.lb_n[L1] + r1;
+        }
       } else if (L1 >= 0) {
-        tgt = T.lb_C[L1] + (int64_t)crmap[L1 - mylimbs[0]][dof_row[g1]] * nB + dof_bidx[g2];
+        if (fast) {
+          const int a = mapped(L1, dof_row[g1]) - (T.lb_n[L1] - T.lb_m[L1]);
+          tgt = T.lb_C[L1] + (int64_t)a * T.lb_nbc[L1] + bcmap[L1 - mylimbs[0]][dof_bidx[g2]];
+        } else {
+          tgt = T.lb_C[L1] + (int64_t)crmap[L1 - mylimbs[0]][dof_row[g1]] * nB + dof_bidx[g2];
+        }
       } else if (L2 >= 0) {
-        tgt = T.lb_R[L2] + (int64_t)dof_bidx[g1] * T.lb_ncr[L2] + crmap[L2 - mylimbs[0]][dof_row[g2]];
+        if (fast) {
+          const int a = mapped(L2, dof_row[g2]) - (T.lb_n[L2] - T.lb_m[L2]);
+          tgt = T.lb_R[L2] + (int64_t)bcmap[L2 - mylimbs[0]][dof_bidx[g1]] * T.lb_m[L2] + a;
+        } else {
+          tgt = T.lb_R[L2] + (int64_t)dof_bidx[g1] * T.lb_ncr[L2] + crmap[L2 - mylimbs[0]][dof_row[g2]];
+        }
       } else {
         tgt = T.gs_JBB[gid] + (int64_t)dof_bidx[g1] * nB + dof_bidx[g2];
       }
@@ -704,6 +772,13 @@ bool build_topology(const dm_system_desc *D, const dm_params *P, HostTopology &T
     T.asm_src.push_back(pairs[k].second);
   }
   if (!pairs.empty()) T.asm_ptr.push_back((int32_t)pairs.size());
+  // system of each target (storage regions are contiguous and ascending)
+  T.asm_sys.resize(T.asm_target.size());
+  for (size_t k = 0; k < T.asm_target.size(); ++k) {
+    const int64_t o = T.asm_target[k];
+    const size_t w = std::upper_bound(T.gs_mat0.begin(), T.gs_mat0.end(), o) - T.gs_mat0.begin() - 1;
+    T.asm_sys[k] = T.gen_sys[w];
+  }
   return true;
 }
 

@@ -126,6 +126,21 @@ def load_library(path=LIB_PATH):
     lib.dm_mlp_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
                                       C.c_void_p, C.POINTER(C.c_double)]
     lib.dm_mlp_train_step.restype = C.c_int
+    lib.dm_ws_enable.argtypes = [H]
+    lib.dm_ws_enable.restype = C.c_int
+    lib.dm_ws_num_segments.argtypes = [H]
+    lib.dm_ws_num_segments.restype = C.c_int64
+    lib.dm_ws_capture_features.argtypes = [H, C.c_void_p]
+    lib.dm_ws_capture_features.restype = C.c_int
+    lib.dm_ws_capture_targets.argtypes = [H, C.c_void_p]
+    lib.dm_ws_capture_targets.restype = C.c_int
+    lib.dm_ws_set_model.argtypes = [H, C.c_void_p, C.POINTER(C.c_float)]
+    lib.dm_ws_set_model.restype = C.c_int
+    lib.dm_ws_prepare_batch.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.dm_ws_prepare_batch.restype = C.c_int
+    lib.dm_ws_column_stats.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]
+    lib.dm_ws_column_stats.restype = C.c_int
     lib.dm_last_error.argtypes = []
     lib.dm_last_error.restype = C.c_char_p
     _lib = lib
@@ -323,6 +338,56 @@ class System:
         d1 = np.ascontiguousarray(np.asarray(d1, np.float64))
         beta = np.ascontiguousarray(np.asarray(beta, np.float64))
         _check(self._lib.dm_set_frames(self._h, _ptr(d1, C.c_double), _ptr(beta, C.c_double)))
+
+
+    # ----- learned warm start -------------------------------------------
+    def ws_enable(self):
+        """Builds the warm-start segment tables; returns their number."""
+        _check(self._lib.dm_ws_enable(self._h))
+        return int(self._lib.dm_ws_num_segments(self._h))
+
+    def ws_capture_features(self, feat):
+        """Raw features [S, 64] (torch CUDA float32) of the committed state;
+        asynchronous on the system's stream."""
+        _check(self._lib.dm_ws_capture_features(self._h, _dev_ptr(feat)))
+        return feat
+
+    def ws_capture_targets(self, tgt):
+        """Targets [S, 4] (torch CUDA float32) of the step just taken,
+        relative to the guess remembered by ws_capture_features."""
+        _check(self._lib.dm_ws_capture_targets(self._h, _dev_ptr(tgt)))
+        return tgt
+
+    def ws_set_model(self, mlp, norm=None):
+        """Attaches a trained MLP (out_dim 4) with its normalisation (132
+        floats: input mean, input std, output scale); None detaches."""
+        if mlp is None:
+            _check(self._lib.dm_ws_set_model(self._h, None, None))
+            self._ws_model = None
+            return
+        n = np.ascontiguousarray(np.asarray(norm, np.float32))
+        if n.size != 132:
+            raise ValueError("norm must hold 132 floats")
+        _check(self._lib.dm_ws_set_model(self._h, mlp._h, n.ctypes.data_as(C.POINTER(C.c_float))))
+        self._ws_model = mlp  # keeps the network alive while attached
+
+
+def ws_prepare_batch(feat, tgt, idx, norm, X, Y, stream=None):
+    """X [M, 64] bf16 = normalised feat[idx], Y [M, 4] f32 = tgt[idx] /
+    output scale (torch CUDA tensors; norm a float32 CUDA tensor [132])."""
+    lib = load_library()
+    _check(lib.dm_ws_prepare_batch(_dev_ptr(feat), _dev_ptr(tgt), _dev_ptr(idx), idx.numel(),
+                                   _dev_ptr(norm), _dev_ptr(X), _dev_ptr(Y), stream))
+    return X, Y
+
+
+def ws_column_stats(data, stats, stream=None):
+    """stats [2, cols] = column means and standard deviations of data
+    [rows, cols] (torch CUDA float32)."""
+    lib = load_library()
+    rows, cols = data.shape
+    _check(lib.dm_ws_column_stats(_dev_ptr(data), rows, cols, _dev_ptr(stats), stream))
+    return stats
 
 
 def solve_band(sys_dof0, sys_ndof, band, rhs, x, stream=None):

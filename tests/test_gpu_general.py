@@ -89,3 +89,28 @@ def test_star_robots_trajectory():
     qg, _ = gpu.get_state()
     qo, _ = ora.get_state()
     _assert_close(qg, qo, desc["nodes_per_rod"], 1.0, 1e-7)
+
+
+def test_chain_with_two_jointed_ends_and_mixed_batch():
+    # a chain of three rods (the middle rod is jointed at both ends, which
+    # takes the limb/Schur path) batched with a T of three rods attached at
+    # one end each (the condensation path)
+    N = 9
+    xs, npr, joints = [], [], []
+    for k in range(3):
+        xs.append(np.c_[np.linspace(0.3 * k, 0.3 * (k + 1), N), np.zeros(N), np.zeros(N)])
+    joints += [[(0, N - 1), (1, 0)], [(1, N - 1), (2, 0)]]
+    y0 = 1.0
+    xs.append(np.c_[np.linspace(0, 0.3, N), np.full(N, y0), np.zeros(N)])
+    xs.append(np.c_[np.linspace(0.3, 0.6, N), np.full(N, y0), np.zeros(N)])
+    xs.append(np.c_[np.full(N, 0.3), y0 + np.linspace(0, 0.25, N), np.zeros(N)])
+    joints += [[(3, N - 1), (4, 0), (5, 0)]]
+    nd = 4 * N - 1
+    fixed = np.zeros(6 * nd, np.uint8)
+    fixed[0:8] = 1            # chain clamped at its first rod's start
+    fixed[3 * nd:3 * nd + 8] = 1
+    desc = dict(nodes_per_rod=[N] * 6, x0=np.concatenate(xs),
+                E=[1e6, 2e6, 1.5e6, 1e6, 2e6, 1.5e6], nu=[0.5] * 6, rho=[1e3] * 6,
+                radius=[2e-3, 2.5e-3, 2e-3] * 2, joints=joints, fixed=fixed)
+    params = dict(dt=2e-3, tol=1e-10, max_iter=60, g=(0, 0, -9.81), eta=0.05)
+    _run(desc, params, 6, 1e-10)
