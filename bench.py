@@ -48,6 +48,16 @@ UNIT_NAME = {"bend_twist_stencil": "stencil", "edge_frames_stretch": "edge",
              "step_begin": "DOF", "step_commit": "DOF"}
 
 
+def _hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p)).get("hbm_gbs", 6800.0))
+    return 6800.0  # fallback figure of an earlier GB300 measurement
+
+
+HBM_PEAK = _hbm_peak()
+
+
 def _load_counts():
     p = os.path.join(ROOT, "profiles", "kernel_fp64_counts.json")
     if os.path.exists(p):
@@ -282,6 +292,21 @@ def run_ours(args):
     kernels = {k: {"launches": v[0], "units": v[1], "ms_total": round(v[2], 3),
                    "share": round(v[2] / sum(x[2] for x in prof.values()), 4)}
                for k, v in prof.items()}
+    # every kernel with counted FP64 work: achieved FP64 rate and fraction of
+    # the measured FP64 peak, and DRAM rate from the counted bytes per unit
+    bpu = {}
+    if os.path.exists(counts):
+        bpu = json.load(open(counts)).get("dram_bytes_per_unit", {})
+    for k, v in prof.items():
+        f = FP64_FLOPS_PER_UNIT.get(k)
+        if f and v[2] > 0:
+            rate = f * v[1] / (v[2] * 1e-3) / 1e12
+            kernels[k]["fp64_tflops"] = round(rate, 4)
+            kernels[k]["fp64_frac"] = round(rate / (peak_fp64 / 1e3), 4)
+        if bpu.get(k) and v[2] > 0:
+            gbs = bpu[k] * v[1] / (v[2] * 1e-3) / 1e9
+            kernels[k]["dram_gbs"] = round(gbs, 1)
+            kernels[k]["hbm_frac"] = round(gbs / HBM_PEAK, 4) if HBM_PEAK else None
 
     it = np.array(iters)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,

@@ -291,13 +291,22 @@ dm_status dm_ws_prepare_batch(const float *features, const float *targets, const
 dm_status dm_ws_column_stats(const float *data, int64_t rows, int32_t cols, float *stats,
                              void *stream);
 
+/* Edge-edge contact (Sec. III-B, Eq. 10-11; params.self_contact != 0):
+ * number of edge pairs closer than C + delta at the last evaluated Newton
+ * iterate, summed over the systems (0 without edge-edge contact, -1 on a
+ * CUDA error).  Synchronises the stream.  Contact acts within single rods
+ * (no joints, no ground contact) and without friction (pair_mu = 0);
+ * dm_create_system rejects other combinations with DM_ERR_INVALID_ARG. */
+int64_t dm_contact_pairs(dm_system *sys);
+
 /* Per-kernel profile of dm_step calls made while profiling is on: CUDA-event
  * time on the system's stream, launch count and work units processed
  * (edges, stencils, DOF rows, systems) per kernel id.  Kernel ids:
  * 0 edge frames + stretch, 1 bend-twist stencils, 2 residual/Jacobian rows,
  * 3 banded solve, 4 step begin, 5 step commit, 6 ground contact/friction,
  * 7 general residual rows, 8 general assembly, 9 limb/Schur solve,
- * 10 learned warm start (features + network + apply).  Profiling adds two event
+ * 10 learned warm start (features + network + apply), 11 edge-edge contact
+ * (broadphase, pairs, derivatives), 12 contact-system LU.  Profiling adds two event
  * records per launch; it is off by default. */
 #define DM_NUM_KERNELS 16
 typedef struct dm_profile {

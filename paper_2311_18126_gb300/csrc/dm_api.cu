@@ -78,12 +78,14 @@ __global__ void k_scatter_kbar(int n, const int32_t *slot2st, int slot0, int ns,
 
 enum {
   K_EDGE = 0, K_STENCIL = 1, K_ROWS = 2, K_SOLVE = 3, K_BEGIN = 4, K_COMMIT = 5,
-  K_NODES = 6, K_ROWS_GEN = 7, K_ASM_GEN = 8, K_SOLVE_GEN = 9, K_WARM = 10
+  K_NODES = 6, K_ROWS_GEN = 7, K_ASM_GEN = 8, K_SOLVE_GEN = 9, K_WARM = 10,
+  K_CONTACT = 11, K_SOLVE_CONTACT = 12
 };
 const char *kKernelNames[DM_NUM_KERNELS] = {
     "edge_frames_stretch", "bend_twist_stencil", "residual_jacobian_rows", "band_ldlt_solve",
     "step_begin",          "step_commit",        "ground_contact_friction", "residual_rows_general",
-    "assemble_general",    "limb_schur_solve",   "learned_warm_start"};
+    "assemble_general",    "limb_schur_solve",   "learned_warm_start",
+    "edge_contact_pairs",  "contact_band_lu"};
 
 struct Extra {
   bool prof = false;
@@ -97,6 +99,16 @@ struct Extra {
   int32_t *ls_action = nullptr, *ls_trial = nullptr, *ls_nback = nullptr;
   double *ls_alpha = nullptr, *ls_racc = nullptr, *ls_qacc = nullptr, *ls_merit = nullptr;
   int n_rod_sys = 0;
+  struct {
+    int table = 0, pair_cap = 0, n_contact = 0;
+    double inv_cell = 0.0;
+    double *edge_h = nullptr, *fc = nullptr, *dense = nullptr;
+    int32_t *edge_idx = nullptr, *contact_sys = nullptr, *sys_bw = nullptr;
+    int32_t *bucket_count = nullptr, *bucket_start = nullptr, *bucket_fill = nullptr,
+            *bucket_edges = nullptr, *pairs = nullptr, *npairs = nullptr;
+    int64_t *sys_dense0 = nullptr;
+    unsigned long long *edge_key = nullptr;
+  } cc;  // edge-edge contact
   int n_fast = 0, n_slow = 0;   // general systems on the condensation / Schur path
   size_t border_smem = 0;
   int limb_nmax = 0, wpb_factor = 1, wpb_back = 1;  // limb kernels: rows, warps per block
@@ -123,8 +135,33 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
   HostTopology &T = s->T;
   if (!build_topology(desc, prm, T)) return DM_ERR_INVALID_ARG;
   if (prm->self_contact) {
-    set_error("edge-edge contact is not supported by this build");
-    return DM_ERR_INVALID_ARG;
+    // edge-edge contact within single rods (no joints, no ground)
+    if (prm->ground) {
+      set_error("edge-edge contact together with ground contact is not supported");
+      return DM_ERR_INVALID_ARG;
+    }
+    if (prm->pair_mu != 0.0) {
+      set_error("edge-edge friction (pair_mu != 0) is not supported");
+      return DM_ERR_INVALID_ARG;
+    }
+    if (!(prm->pair_kc > 0 && prm->delta > 0)) {
+      set_error("edge-edge contact needs pair_kc > 0 and delta > 0");
+      return DM_ERR_INVALID_ARG;
+    }
+    double dense = 0.0;
+    for (int k = 0; k < T.n_systems; ++k) {
+      if (T.sys_kind[k] != SOLVE_ROD_BAND) {
+        set_error("edge-edge contact is supported on single rods only (system " +
+                  std::to_string(k) + " has joints)");
+        return DM_ERR_INVALID_ARG;
+      }
+      T.sys_kind[k] = SOLVE_CONTACT;
+      dense += (double)T.sys_ndof[k] * T.sys_ndof[k];
+    }
+    if (dense * 8.0 > 8e9) {
+      set_error("edge-edge contact: the per-system matrices would exceed 8 GB");
+      return DM_ERR_INVALID_ARG;
+    }
   }
   if (prm->ground && !(prm->delta > 0 && prm->slip_nu > 0)) {
     set_error("ground contact needs delta > 0 and slip_nu > 0");
@@ -224,6 +261,48 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
   s->x.n_rod_sys = (int)order.size();
   DM_TRY(upload(s, &d.solve_order, order));
   DM_TRY(upload(s, &s->x.d_sys_kind, T.sys_kind));
+  if (prm->self_contact) {
+    auto &c = s->x.cc;
+    std::vector<int32_t> eidx(ne), csys;
+    for (int r = 0; r < T.n_rods; ++r)
+      for (int64_t e = T.rod_edge0[r]; e < T.rod_edge0[r + 1]; ++e) eidx[e] = (int32_t)(e - T.rod_edge0[r]);
+    std::vector<int64_t> dense0(S, 0);
+    int64_t tot = 0;
+    for (int k = 0; k < S; ++k) {
+      dense0[k] = tot;
+      tot += (int64_t)T.sys_ndof[k] * T.sys_ndof[k];
+      csys.push_back(k);
+    }
+    double lmax = 0.0, hmax = 0.0;
+    for (int64_t e = 0; e < ne; ++e) {
+      lmax = std::max(lmax, T.edge_lbar[e]);
+      hmax = std::max(hmax, T.edge_h[e]);
+    }
+    int tsize = 1024;
+    while (tsize < 2 * ne && tsize < (1 << 22)) tsize <<= 1;
+    c.table = tsize;
+    c.pair_cap = (int)std::min<int64_t>(64 * std::max<int64_t>(ne, 16), 1 << 24);
+    c.inv_cell = 1.0 / (1.5 * lmax + 2.0 * hmax + prm->delta);
+    c.n_contact = S;
+    DM_TRY(upload(s, &c.edge_h, T.edge_h));
+    DM_TRY(upload(s, &c.edge_idx, eidx));
+    DM_TRY(upload(s, &c.contact_sys, csys));
+    DM_TRY(upload(s, &c.sys_dense0, dense0));
+    DM_TRY(dalloc(s, &c.edge_key, ne));
+    DM_TRY(dalloc(s, &c.bucket_count, tsize));
+    DM_TRY(dalloc(s, &c.bucket_start, tsize + 1));
+    DM_TRY(dalloc(s, &c.bucket_fill, tsize));
+    DM_TRY(dalloc(s, &c.bucket_edges, ne));
+    DM_TRY(dalloc(s, &c.pairs, 2 * (int64_t)c.pair_cap));
+    DM_TRY(dalloc(s, &c.npairs, 1));
+    DM_TRY(dalloc(s, &c.fc, nd));
+    DM_TRY(dalloc(s, &c.dense, tot));
+    DM_TRY(dalloc(s, &c.sys_bw, S));
+    DM_CK(cudaMemset(c.dense, 0, tot * sizeof(double)));
+    DM_CK(cudaMemset(c.npairs, 0, sizeof(int32_t)));
+    std::vector<int32_t> bw10(S, 10);
+    DM_CK(cudaMemcpy(c.sys_bw, bw10.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
   if (prm->line_search) {
     DM_TRY(dalloc(s, &s->x.ls_action, S));
     DM_TRY(dalloc(s, &s->x.ls_trial, S));
@@ -474,7 +553,25 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   StencilArgs ka{ns, ne, d.q, d.ef, d.tn, d.st_ed, d.st_th, d.st_sg, d.st_sys, d.st_kb, d.st_kt,
                  d.kbar, d.taubar, d.beta_n, d.sys_active, d.sys_status, d.beta_it, d.sg, d.sh,
                  s->x.prof ? s->x.d_units + K_STENCIL : nullptr};
+  const bool contact_on = s->x.cc.n_contact > 0;
+  ContactArgs ca{};
+  if (contact_on) {
+    auto &c = s->x.cc;
+    ca.ne = ne; ca.nd = nd; ca.nsys = S; ca.table_mask = c.table - 1; ca.pair_cap = c.pair_cap;
+    ca.inv_cell = c.inv_cell; ca.delta = s->prm.delta; ca.kc = s->prm.pair_kc;
+    ca.q = d.q; ca.edge_h = c.edge_h; ca.band = d.band;
+    ca.edge_a = d.edge_a; ca.edge_b = d.edge_b; ca.edge_sys = d.edge_sys; ca.edge_idx = c.edge_idx;
+    ca.sys_kind = s->x.d_sys_kind; ca.sys_active = d.sys_active; ca.dof_sys = s->x.d_dof_sys;
+    ca.sys_dof0 = d.sys_dof0; ca.sys_ndof = d.sys_ndof; ca.contact_sys = c.contact_sys;
+    ca.ls_action = s->prm.line_search ? s->x.ls_action : nullptr;
+    ca.fixed = d.fixed; ca.sys_dense0 = c.sys_dense0; ca.sys_status = d.sys_status;
+    ca.sys_bw = c.sys_bw; ca.edge_key = c.edge_key; ca.bucket_count = c.bucket_count;
+    ca.bucket_start = c.bucket_start; ca.bucket_fill = c.bucket_fill;
+    ca.bucket_edges = c.bucket_edges; ca.pairs = c.pairs; ca.npairs = c.npairs;
+    ca.fc = c.fc; ca.dense = c.dense;
+  }
   RowArgs ra{};
+  ra.fc = contact_on ? s->x.cc.fc : nullptr;
   ra.nd = nd; ra.ns = ns; ra.ne = ne; ra.dt = s->p.dt;
   for (int c = 0; c < 3; ++c) ra.g[c] = s->p.g[c];
   ra.eta = s->p.eta;
@@ -569,7 +666,21 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
         Timed t(s, K_STENCIL, st);
         k_stencil<<<blocks(ns, 128), 128, 0, st>>>(ka);
       }
-      if (rod_on) {
+      if (contact_on) {
+        Timed t(s, K_CONTACT, st);
+        const auto &c = s->x.cc;
+        DM_CK(cudaMemsetAsync(c.fc, 0, nd * sizeof(double), st));
+        DM_CK(cudaMemsetAsync(c.npairs, 0, sizeof(int32_t), st));
+        DM_CK(cudaMemsetAsync(c.bucket_count, 0, c.table * sizeof(int32_t), st));
+        k_cc_clear<<<blocks(nd, 256), 256, 0, st>>>(ca);
+        k_cc_reset_bw<<<blocks(S, 256), 256, 0, st>>>(ca);
+        k_cc_cells<<<blocks(ne, 256), 256, 0, st>>>(ca);
+        k_cc_scan<<<1, 1024, 0, st>>>(ca);
+        k_cc_fill<<<blocks(ne, 256), 256, 0, st>>>(ca);
+        k_cc_pairs<<<blocks(ne, 128), 128, 0, st>>>(ca);
+        k_cc_terms<<<blocks(c.pair_cap, 64), 64, 0, st>>>(ca);
+      }
+      if (rod_on || contact_on) {
         Timed t(s, K_ROWS, st);
         k_rows_rod<<<blocks(nd, 256), 256, 0, st>>>(ra);
       }
@@ -588,6 +699,11 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
           Timed t(s, K_SOLVE, st);
           k_solve_rod<<<s->x.solve_blocks, 128, s->x.solve_smem, st>>>(va);
         }
+      }
+      if (contact_on) {
+        Timed t(s, K_SOLVE_CONTACT, st);
+        k_cc_band<<<blocks(nd, 256), 256, 0, st>>>(ca);
+        k_solve_contact<<<s->x.cc.n_contact, 1024, 0, st>>>(ca, va);
       }
       if (gen_on) {
         DM_CK(cudaMemsetAsync(d.gen, 0, T.gen_doubles * sizeof(double), st));
@@ -846,6 +962,16 @@ dm_status dm_debug_copy(dm_system *sys, const char *name, double *out, int64_t n
   DM_CK(cudaStreamSynchronize(sys->stream));
   DM_CK(cudaMemcpy(out, src, len * sizeof(double), cudaMemcpyDeviceToHost));
   return DM_OK;
+}
+
+int64_t dm_contact_pairs(dm_system *sys) {
+  auto *s = static_cast<dm_system_ext *>(sys);
+  if (!s || !s->x.cc.npairs) return 0;
+  int32_t n = 0;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return -1;
+  if (cudaMemcpy(&n, s->x.cc.npairs, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return -1;
+  return n;
 }
 
 const char *dm_kernel_name(int32_t id) {

@@ -21,6 +21,8 @@ enum SolverKind : int32_t {
   SOLVE_ROD_BAND = 0,  // one rod, Eq. 1 layout, symmetric, half bandwidth 10
   SOLVE_GENERAL = 1,   // limbs (banded interiors) + dense border (joints,
                        // ground contact/friction: possibly nonsymmetric)
+  SOLVE_CONTACT = 2,   // one rod with edge-edge contact: band widened by the
+                       // contact blocks, LU in a dense per-system matrix
 };
 
 // Gather-map source codes for the general assembly (see dm_general.cu).

@@ -27,6 +27,7 @@ struct StencilArgs {
 };
 
 struct RowArgs {
+  const double *fc;  // edge-edge contact force per DOF (NULL without contact)
   int nd, ns, ne;
   double dt, g[3], eta;
   const double *q, *qn, *vn, *mass, *rscale, *damp;
@@ -126,6 +127,30 @@ struct LineSearchArgs {
   double *alpha, *racc, *merit, *q, *qacc;
   int32_t *wstry;  // NULL, or 1 while the trial is the learned initial guess
 };
+struct ContactArgs {
+  int ne, nd, nsys, table_mask, pair_cap;
+  double inv_cell, delta, kc;
+  const double *q, *edge_h, *band;
+  const int32_t *edge_a, *edge_b, *edge_sys, *edge_idx, *sys_kind, *sys_active, *dof_sys;
+  const int32_t *sys_dof0, *sys_ndof, *contact_sys, *ls_action;
+  const uint8_t *fixed;
+  const int64_t *sys_dense0;
+  int32_t *sys_status, *sys_bw;
+  unsigned long long *edge_key;
+  int32_t *bucket_count, *bucket_start, *bucket_fill, *bucket_edges;
+  int32_t *pairs, *npairs;
+  double *fc, *dense;
+};
+__global__ void k_cc_cells(ContactArgs a);
+__global__ void k_cc_scan(ContactArgs a);
+__global__ void k_cc_fill(ContactArgs a);
+__global__ void k_cc_pairs(ContactArgs a);
+__global__ void k_cc_terms(ContactArgs a);
+__global__ void k_cc_band(ContactArgs a);
+__global__ void k_cc_clear(ContactArgs a);
+__global__ void k_cc_reset_bw(ContactArgs a);
+__global__ void k_solve_contact(ContactArgs a, SolveArgs v);
+
 __global__ void k_ls_merit(LineSearchArgs a);
 __global__ void k_ls_decide(LineSearchArgs a);
 __global__ void k_ls_apply(LineSearchArgs a);

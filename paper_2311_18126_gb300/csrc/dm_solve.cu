@@ -29,7 +29,7 @@ __device__ __forceinline__ int ksym(int c, int cp) {  // packed 3x3 (xx,xy,xz,yy
 __global__ void __launch_bounds__(256) k_rows_rod(RowArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = i < a.nd && a.sys_active[a.dof_sys[i]] &&
-                   a.sys_kind[a.dof_sys[i]] == SOLVE_ROD_BAND;
+                   a.sys_kind[a.dof_sys[i]] != SOLVE_GENERAL;
   count_units(a.units, act);
   if (!act) return;
   const int s = a.dof_sys[i];
@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) k_rows_rod(RowArgs a) {
     F -= cd * (a.q[i] - a.qn[i]);
     brow[0] += cd;
   }
+  if (a.fc) F += a.fc[i];
   brow[0] += m_i * idt * idt;
   double f = m_i * idt * idt * (a.q[i] - a.qn[i]) - m_i * idt * a.vn[i] - F;
   if (a.fixed[i]) {

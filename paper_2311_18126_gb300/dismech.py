@@ -141,6 +141,8 @@ def load_library(path=LIB_PATH):
     lib.dm_ws_prepare_batch.restype = C.c_int
     lib.dm_ws_column_stats.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]
     lib.dm_ws_column_stats.restype = C.c_int
+    lib.dm_contact_pairs.argtypes = [H]
+    lib.dm_contact_pairs.restype = C.c_int64
     lib.dm_last_error.argtypes = []
     lib.dm_last_error.restype = C.c_char_p
     _lib = lib
@@ -339,6 +341,10 @@ class System:
         beta = np.ascontiguousarray(np.asarray(beta, np.float64))
         _check(self._lib.dm_set_frames(self._h, _ptr(d1, C.c_double), _ptr(beta, C.c_double)))
 
+
+    def contact_pairs(self):
+        """Edge pairs in contact at the last evaluated Newton iterate."""
+        return int(self._lib.dm_contact_pairs(self._h))
 
     # ----- learned warm start -------------------------------------------
     def ws_enable(self):

@@ -1,0 +1,74 @@
+"""GPU vs oracle for edge-edge contact (Sec. III-B, Eq. 10-11): a helical rod
+collapsing under gravity until its turns touch.  Per step from identical
+states (1e-10 relative) with the active pair counts of both sides compared,
+and a free trajectory through the first contacts."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import OracleSystems
+from oracle.contact import segment_distance
+from test_gpu_parity import _assert_close, _gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_active_pairs(ora, params):
+    s = ora.systems[0]
+    cand = s.pair_cand
+    nd = torch.as_tensor(s.node_dof)
+    nl = torch.as_tensor(s.edge_nl)
+    i, j = torch.as_tensor(cand[:, 0]), torch.as_tensor(cand[:, 1])
+    idx = torch.stack([nd[nl[i, 0]], nd[nl[i, 1]], nd[nl[j, 0]], nd[nl[j, 1]]], 1)
+    x = s.q[(idx[:, :, None] + torch.arange(3)).reshape(-1, 12)]
+    D, _, _ = segment_distance(x[:, 0:3], x[:, 3:6], x[:, 6:9], x[:, 9:12])
+    C = torch.as_tensor(s.h_edge[cand[:, 0]] + s.h_edge[cand[:, 1]])
+    return int((D < C + params["delta"]).sum())
+
+
+def test_coil_contact_per_step():
+    desc, params, _ = workloads.coil(N=60)
+    gpu = _gpu(desc, params)
+    ora = OracleSystems(desc, params)
+    npr = desc["nodes_per_rod"]
+    touched = 0
+    for k in range(44):
+        gpu.step(1)
+        st = ora.step(1)
+        assert all(x[0] == 0 for x in st), st
+        qg, vg = gpu.get_state()
+        qo, vo = ora.get_state()
+        _assert_close(qg, qo, npr, 1.0, 1e-10)
+        # pairs in contact at the converged state: the GPU counts them at
+        # its last evaluated iterate, which is the converged one
+        ng = gpu.contact_pairs()
+        no = _oracle_active_pairs(ora, params)
+        assert ng == no, (k, ng, no)
+        touched += no > 0
+        d1, beta = ora.get_frames()
+        gpu.set_state(qo, vo)
+        gpu.set_frames(d1, beta)
+    assert touched >= 5
+
+
+def test_coil_contact_trajectory():
+    desc, params, _ = workloads.coil(N=60)
+    gpu = _gpu(desc, params)
+    ora = OracleSystems(desc, params)
+    for k in range(40):
+        gpu.step(1)
+        ora.step(1)
+    assert gpu.contact_pairs() > 0
+    qg, _ = gpu.get_state()
+    qo, _ = ora.get_state()
+    _assert_close(qg, qo, desc["nodes_per_rod"], 1.0, 1e-7)
+
+
+def test_contact_options_rejected():
+    from paper_2311_18126_gb300 import System, DismechError
+    desc, params, _ = workloads.coil(N=20)
+    with pytest.raises(DismechError):
+        System(desc, dict(params, pair_mu=0.3))
+    with pytest.raises(DismechError):
+        System(desc, dict(params, ground=True))

@@ -173,9 +173,11 @@ def gait_kbar(gait, t):
 
 
 def coil(N=500, h=1e-3, radius=0.02, pitch_factor=2.2, E=1e7, rho=1000.0,
-         delta=1e-4):
-    """Helical rod whose natural curvature is 1.5x the helix's, with
-    self-contact.  Returns (desc, params, kbar)."""
+         delta=1e-4, mu=0.0):
+    """Helical rod standing on its clamped lower end, stress-free at rest
+    (natural strains = initial), collapsing under gravity so that its turns
+    come into contact (edge-edge self-contact).  The turns start a gap of
+    (pitch_factor - 2) h apart.  Returns (desc, params, None)."""
     pitch = pitch_factor * h
     turn_len = math.sqrt((2.0 * math.pi * radius) ** 2 + pitch ** 2)
     spacing = 2.5e-3
@@ -185,13 +187,7 @@ def coil(N=500, h=1e-3, radius=0.02, pitch_factor=2.2, E=1e7, rho=1000.0,
                   pitch * phi / (2.0 * math.pi)], 1)
     mask = _clamp_mask(N)
     desc = _rod_desc([N], x, [E], [0.5], [rho], [h], mask)
-    # helix curvature radius/(radius^2 + (pitch/2pi)^2), times 1.5, about the
-    # helix axis direction of the material frame: all of it in kappa1
-    b = pitch / (2.0 * math.pi)
-    curv = radius / (radius ** 2 + b ** 2)
-    kbar = np.zeros((N - 2, 2))
-    kbar[:, 0] = 1.5 * curv * spacing
     kc = E * h                                           # reading C11 (~E h)
-    params = dict(dt=1e-3, tol=1e-10, max_iter=100, g=(0.0, 0.0, 0.0), eta=0.1,
-                  self_contact=True, delta=delta, pair_kc=kc, pair_mu=0.0)
-    return desc, params, kbar
+    params = dict(dt=1e-3, tol=1e-10, max_iter=100, g=(0.0, 0.0, -9.81), eta=0.1,
+                  self_contact=True, delta=delta, pair_kc=kc, pair_mu=mu)
+    return desc, params, None
