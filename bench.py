@@ -84,6 +84,29 @@ def dist():
     return ws, rank, local
 
 
+def rank_seed(rank):
+    """Seed of a rank's own batch (weak scaling: independent rods per rank)."""
+    return 2 + rank
+
+
+def max_over_ranks(x, ws, device=None):
+    """Largest value of x over the ranks (the timed region ends when the
+    slowest rank ends); x unchanged on one rank."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, rods_per_rank, steps, seconds):
+    """Whole-job rod-steps per second: every rank's rods over the slowest
+    rank's time."""
+    return ws * rods_per_rank * steps / seconds
+
+
 class Clocks:
     """nvidia-smi samples of SM clock and throttle reasons during timing."""
 
@@ -201,7 +224,7 @@ def run_ours(args):
     from paper_2311_18126_gb300 import System, ensure_built, fp64_peak_gflops
     ensure_built()
     _load_counts()
-    desc, params, kbar = workloads.uneven_rods(n_rods=args.rods, seed=2 + rank)
+    desc, params, kbar = workloads.uneven_rods(n_rods=args.rods, seed=rank_seed(rank))
     R = args.rods
     sysm = System(desc, params)
     sysm.set_natural_curvature(0, R, kbar)
@@ -234,13 +257,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     prof = sysm.get_profile()
     sysm.set_profiling(False)
-    tmax = ms
-    if ws > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        tmax = float(t.item())
-    value = ws * R * args.steps / (tmax * 1e-3)
+    tmax = max_over_ranks(ms, ws, "cuda")
+    value = job_rate(ws, R, args.steps, tmax * 1e-3)
 
     # end to end through the public API with pinned host buffers
     n = sysm.n_state
@@ -260,13 +278,8 @@ def run_ours(args):
         hq.numpy()[:] = qq
         hv.numpy()[:] = vv
     torch.cuda.synchronize()
-    te = time.perf_counter() - t0
-    if ws > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([te], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        te = float(t.item())
-    e2e = {"value": ws * R * e2e_steps / te, "unit": UNIT,
+    te = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
+    e2e = {"value": job_rate(ws, R, e2e_steps, te), "unit": UNIT,
            "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": 2 * n * 8}
 
     # dominant kernel and its FP64 roofline

@@ -27,8 +27,14 @@ def _oracle_active_pairs(ora, params):
     return int((D < C + params["delta"]).sum())
 
 
-def test_coil_contact_per_step():
+def _short_coil():
+    # 60 nodes at dt = 1 ms without line search: the turns touch from step 30
     desc, params, _ = workloads.coil(N=60)
+    return desc, dict(params, dt=1e-3, line_search=False)
+
+
+def test_coil_contact_per_step():
+    desc, params = _short_coil()
     gpu = _gpu(desc, params)
     ora = OracleSystems(desc, params)
     npr = desc["nodes_per_rod"]
@@ -53,7 +59,7 @@ def test_coil_contact_per_step():
 
 
 def test_coil_contact_trajectory():
-    desc, params, _ = workloads.coil(N=60)
+    desc, params = _short_coil()
     gpu = _gpu(desc, params)
     ora = OracleSystems(desc, params)
     for k in range(40):

@@ -485,3 +485,39 @@ def test_mlp_reference_gradient_matches_central_differences():
         p2[i] -= h
         fd = (mlp.loss_and_grad(p1, X, Y, 4)[0] - mlp.loss_and_grad(p2, X, Y, 4)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-9
+
+
+def test_segment_distance_matches_brute_force():
+    """Eq. 10's D: the clamped closest-point rule against a brute-force
+    minimum over the two segment parameters (grid, then local refinement)."""
+    from scipy.optimize import minimize
+    from oracle.contact import segment_distance
+    rng = np.random.default_rng(11)
+    for _ in range(40):
+        p = rng.normal(size=(4, 3))
+        if rng.random() < 0.3:  # nearly parallel pairs too
+            p[3] = p[2] + (p[1] - p[0]) * rng.uniform(0.5, 2) + 1e-3 * rng.normal(size=3)
+        P = torch.as_tensor(p)
+        D, s, t = segment_distance(P[0], P[1], P[2], P[3])
+        f = lambda st: np.linalg.norm(p[0] + st[0] * (p[1] - p[0]) - p[2] - st[1] * (p[3] - p[2]))
+        g = np.linspace(0, 1, 101)
+        best = min(((f((a, b)), a, b) for a in g for b in g))
+        r = minimize(f, x0=[best[1], best[2]], bounds=[(0, 1), (0, 1)], method="L-BFGS-B",
+                     options=dict(ftol=1e-15, gtol=1e-12))
+        ref = min(best[0], r.fun)
+        assert float(D) <= ref + 1e-9
+        assert float(D) >= ref - 1e-6 * max(1.0, ref)
+
+
+def test_imc_energy_branches():
+    """Eq. 10: zero beyond C + delta, (C - D)^2 below C - delta, and the
+    smooth branch joining both (to the accuracy K1 = 15/delta allows)."""
+    from oracle.der import imc_energy
+    C, delta = 2e-3, 1e-4
+    D = torch.tensor([C + 1.01 * delta, C - 1.5 * delta, C - delta * (1 + 1e-9),
+                      C - delta * (1 - 1e-9), C + delta * (1 - 1e-9)], dtype=torch.float64)
+    E = imc_energy(D, torch.full_like(D, C), delta)
+    assert float(E[0]) == 0.0
+    assert abs(float(E[1]) - (1.5 * delta) ** 2) < 1e-20
+    assert abs(float(E[2]) - float(E[3])) <= 1e-6 * float(E[2])
+    assert float(E[4]) <= 1e-12 * delta ** 2

@@ -188,6 +188,9 @@ def coil(N=500, h=1e-3, radius=0.02, pitch_factor=2.2, E=1e7, rho=1000.0,
     mask = _clamp_mask(N)
     desc = _rod_desc([N], x, [E], [0.5], [rho], [h], mask)
     kc = E * h                                           # reading C11 (~E h)
-    params = dict(dt=1e-3, tol=1e-10, max_iter=100, g=(0.0, 0.0, -9.81), eta=0.1,
-                  self_contact=True, delta=delta, pair_kc=kc, pair_mu=mu)
+    # dt = 0.25 ms and the line search keep Newton at 2-3 iterations through
+    # the collapse of the 500-node coil (at 1 ms it stalls once the turns pile up)
+    params = dict(dt=2.5e-4, tol=1e-10, max_iter=100, g=(0.0, 0.0, -9.81), eta=0.1,
+                  self_contact=True, delta=delta, pair_kc=kc, pair_mu=mu,
+                  line_search=True)
     return desc, params, None
