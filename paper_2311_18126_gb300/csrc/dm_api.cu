@@ -414,7 +414,7 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
   DM_CK(cudaMallocHost(&s->h_ctrl, 4 * sizeof(int32_t)));
   // persistent banded solver: 32 rods per 128-thread block, enough blocks
   // to cover the batch but no more than fit at once
-  s->x.solve_smem = 16 * (2 * 133 + 32) * sizeof(double);  // 16 rods per block
+  s->x.solve_smem = 16 * kSolveRodDoubles * sizeof(double);  // 16 rods per block
   DM_CK(cudaFuncSetAttribute(k_solve_rod, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)s->x.solve_smem));
   {
@@ -423,8 +423,11 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     DM_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     DM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_rod, 128,
                                                         s->x.solve_smem));
-    int want = (s->x.n_rod_sys + 15) / 16;
-    s->x.solve_blocks = std::max(1, std::min(want, std::max(1, per_sm) * sms));
+    // persistent: one block of four warps per SM, so that each SM partition
+    // runs one warp; the warps take rod quads from the size-sorted queue
+    // (largest first), which balances the FP64 work across partitions
+    const int want = (s->x.n_rod_sys + 15) / 16;
+    s->x.solve_blocks = std::max(1, std::min({want, sms, std::max(1, per_sm) * sms}));
   }
   DM_CK(cudaDeviceSynchronize());
   return DM_OK;

@@ -113,13 +113,15 @@ dm_status run_band_solve(int32_t nsys, const int32_t *dof0, const int32_t *ndof,
   va.sys_res = res;
   va.ctrl = ctrl;
   va.units = nullptr;
-  const size_t smem = 16 * (2 * 133 + 32) * sizeof(double);  // 16 rods per block
+  const size_t smem = 16 * kSolveRodDoubles * sizeof(double);  // 16 rods per block
   int dev = 0, sms = 1, per_sm = 1;
   BS_CK(cudaGetDevice(&dev));
   BS_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  BS_CK(cudaFuncSetAttribute(k_solve_rod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   BS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_rod, 128, smem));
   int nblk = (nsys + 15) / 16;
   if (nblk > per_sm * sms) nblk = per_sm * sms;
+  if (nblk > sms) nblk = sms;  // one block of four warps per SM, as in dm_step
   if (nblk < 1) nblk = 1;
   k_solve_rod<<<nblk, 128, smem, st>>>(va);
   BS_CK(cudaGetLastError());

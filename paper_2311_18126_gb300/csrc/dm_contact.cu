@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(1024) k_solve_contact(ContactArgs a, SolveArgs
       y[i] = fma(-M[(size_t)i * n + j], xj, y[i]);
     if (threadIdx.x == 0) {
       y[j] = xj;
-      v.q[d0 + j] += xj;
+      atomicAdd(v.q + d0 + j, xj);
     }
     __syncthreads();
   }

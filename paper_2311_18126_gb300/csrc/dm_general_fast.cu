@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(128) k_gen_limb_back(SolveGenArgs a) {
     double v = Z[nbc];
     for (int b = 0; b < nbc; ++b) v = fma(-Z[b], xB[bc[b]], v);
     xr[(ne + lane) & 15] = v;
-    a.q[dof(ne + lane)] += v;
+    atomicAdd(a.q + dof(ne + lane), v);
   }
   __syncwarp();
   for (int p = ne - 1; p >= 0; --p) {
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(128) k_gen_limb_back(SolveGenArgs a) {
     if (lane == 0) {
       const double x = (u[10] - t) * u[11];
       xr[p & 15] = x;
-      a.q[dof(p)] += x;
+      atomicAdd(a.q + dof(p), x);  // a reduction: no load on the recurrence
     }
     __syncwarp();
   }

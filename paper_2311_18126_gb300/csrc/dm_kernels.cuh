@@ -58,6 +58,10 @@ struct SolveArgs {
   int32_t *ls_trial;
 };
 
+// shared memory (doubles) per rod of k_solve_rod: two chain windows and the
+// separator scratch
+constexpr int kSolveRodDoubles = 2 * (22 * 12 + 2) + 32;
+
 struct NodeArgs {
   int nn;
   double dt, ground_z, delta, slip_nu;

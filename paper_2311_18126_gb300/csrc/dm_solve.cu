@@ -127,9 +127,13 @@ __global__ void __launch_bounds__(256) k_rows_rod(RowArgs a) {
 // Rods are taken from a queue in order of decreasing size, four per warp.
 #define SOLVE_WARPS 4
 #define SOLVE_RODS_PER_WARP 4
-#define SOLVE_CHAIN_STRIDE 133  // doubles per chain: W 121, z 11, spare 1
-
-__device__ __forceinline__ int wrap11(int x) { return x >= 11 ? x - 11 : x; }
+// Window of a chain in shared memory: matrix rows in order, 12 doubles per
+// row (the 11 lower-band diagonals J[r][r-d], d = 0..10, then the
+// right-hand side), SOLVE_WROWS rows; the pivot row walks down the buffer
+// and the last 11 rows are moved back to the top every 11 columns.
+#define SOLVE_WROWS 22
+#define SOLVE_CHAIN_STRIDE (SOLVE_WROWS * 12 + 2)  // window + final base + spare
+static_assert(SOLVE_CHAIN_STRIDE * 2 + 32 == kSolveRodDoubles, "rod smem layout");
 
 // 1/d from an FP32 seed and two Newton steps in FP64 (|d| within FP32 range).
 __device__ __forceinline__ double rcp64(double d) {
@@ -178,126 +182,208 @@ struct Chain {
   __device__ __forceinline__ double *zstore(int idx) const { return dq + base + orig(idx); }
 };
 
-// Eliminates `ncol` columns of a chain.  On return W/Z hold rows
-// ncol..ncol+10 of the partially reduced matrix and right-hand side.
-__device__ __forceinline__ bool eliminate(const Chain &c, int ncol, double *W, double *Z,
-                                          int p, unsigned cmask, int leader) {
+// Eliminates `ncol` columns of a chain.  On return the window rows
+// W[(b + i) * 12 + .] (b = the final base, also stored at W[SOLVE_WROWS * 12])
+// hold rows ncol..ncol+10 of the partially reduced matrix and right-hand side.
+//
+// The window stores each matrix row by absolute diagonal, so the slide from
+// column j to j+1 moves no data: the update of window entry (i, q) (row
+// j+i, column j+q) is always at offset 12 i + (i - q) from the pivot row,
+// its column entry a_q at 13 q, the multiplier source at 13 i, and the
+// right-hand side at 12 i + 11; every lane holds its 17 offsets in
+// registers.  Rows beyond the end are zero, so no update needs a bound test.
+//
+// All eight chains of a warp run the same number of iterations (`nwarp`,
+// the warp's largest ncol); a chain past its own ncol changes nothing, so
+// every synchronisation is warp-wide and the warp never diverges.
+__device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, double *W, int p,
+                                          int leader) {
   const int n = c.n;
   int rows[3];
   rows[0] = p == 0 ? 10 : (p == 1 ? 9 : (p == 2 ? 8 : 7));
   rows[1] = p == 0 ? 3 : (p == 1 ? 5 : (p == 2 ? 6 : 4));
   rows[2] = p == 0 ? 1 : (p == 3 ? 2 : 0);
-  int code[17];
+  int toff[17], uoff[17], rsel[17];
 #pragma unroll
-  for (int k = 0; k < 17; ++k)
-    code[k] = p == 0 ? task_code(0, k) : (p == 1 ? task_code(1, k) : (p == 2 ? task_code(2, k) : task_code(3, k)));
-  for (int e = p; e < 121; e += 4) {
-    const int r = e / 11, d = e - 11 * r;
-    W[e] = (r < n && d <= r) ? *c.entry(r, d) : 0.0;
+  for (int k = 0; k < 17; ++k) {
+    const int code = p == 0 ? task_code(0, k) : (p == 1 ? task_code(1, k) : (p == 2 ? task_code(2, k) : task_code(3, k)));
+    const int i = code & 15, q = (code >> 4) & 15;
+    rsel[k] = q == 15 ? 3 : (code >> 8);
+    toff[k] = q == 15 ? 0 : (q == 0 ? 12 * i + 11 : 12 * i + (i - q));
+    uoff[k] = q == 15 ? 0 : (q == 0 ? 11 : 13 * q);
   }
-  for (int r = p; r < 11; r += 4) Z[r] = (r < n) ? c.rhs(r) : 0.0;
-  __syncwarp(cmask);
-  double rj = rcp64(W[0]);
+  int loff[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) loff[r] = 13 * rows[r];
+  // rows 0..10 of the chain; diagonals reaching before row 0 are zero
+  if (ncol > 0)
+    for (int e = p; e < 11 * 12; e += 4) {
+      const int r = e / 12, d = e - 12 * r;
+      double v = 0.0;
+      if (r < n) v = d == 11 ? c.rhs(r) : (d <= r ? *c.entry(r, d) : 0.0);
+      W[e] = v;
+    }
+  __syncwarp();
+  double rj = ncol > 0 ? rcp64(W[0]) : 1.0;
   bool bad = false;
-  int s0 = 0;
-  for (int j = 0; j < ncol; ++j) {
-    const bool more = j + 11 < n;
-    double pre0 = 0.0, pre1 = 0.0, pre2 = 0.0;
+  int b = 0;
+  for (int j = 0; j < nwarp; ++j) {
+    const bool act = j < ncol;
+    // prefetch of row j + 11 (diagonals p, p+4, p+8; the right-hand side)
+    const bool more = act && j + 11 < n;
+    double pre0 = 0.0, pre1 = 0.0, pre2 = 0.0, prz = 0.0;
     if (more) {
       pre0 = *c.entry(j + 11, p);
       pre1 = *c.entry(j + 11, p + 4);
       if (p + 8 < 11) pre2 = *c.entry(j + 11, p + 8);
+      if (p == 3) prz = c.rhs(j + 11);
     }
-    const double zj = Z[s0];
-    if (p == 0) {
+    double *Wb = W + 12 * b;
+    const double zj = Wb[11];
+    if (act && p == 0) {
       if (!isfinite(rj) || rj == 0.0) bad = true;
       *c.zstore(j) = zj * rj;  // z_j = y_j / D_j for the backward pass
     }
-    double l[3], uq[17];
+    double l[4];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const int i = rows[r];
-      const bool ok = i > 0 && j + i < n;
-      l[r] = (ok ? W[wrap11(s0 + i) * 11 + i] : 0.0) * rj;
-    }
+    for (int r = 0; r < 3; ++r) l[r] = rows[r] > 0 ? Wb[loff[r]] * rj : 0.0;
+    l[3] = 0.0;
+    double uq[17], dv[17];
 #pragma unroll
     for (int k = 0; k < 17; ++k) {
-      const int q = (code[k] >> 4) & 15;
-      uq[k] = (q > 0 && q < 15 && j + q < n) ? W[wrap11(s0 + q) * 11 + q] : (q == 0 ? zj : 0.0);
+      uq[k] = Wb[uoff[k]];
+      dv[k] = Wb[toff[k]];
     }
     // next pivot first (lane 0 owns window row 1), broadcast, reciprocal
-    double piv = 0.0;
-    if (p == 0) piv = (j + 1 < n) ? fma(-l[2], uq[0], W[wrap11(s0 + 1) * 11]) : 1.0;
-    piv = __shfl_sync(cmask, piv, leader);
-    const double rnext = rcp64(piv);
-    __syncwarp(cmask);
+    double piv = 1.0;
+    if (p == 0 && act && j + 1 < n) piv = fma(-l[2], Wb[13], Wb[12]);
+    piv = __shfl_sync(0xffffffffu, piv, leader);
+    const double rnext = act ? rcp64(piv) : rj;
+    __syncwarp();
+    if (act) {
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const int i = rows[r];
-      if (i > 0 && j + i < n) *c.lstore(j, i) = l[r];
+      for (int r = 0; r < 3; ++r) {
+        const int i = rows[r];
+        if (i > 0 && j + i < n) *c.lstore(j, i) = l[r];
+      }
+#pragma unroll
+      for (int k = 0; k < 17; ++k) {
+        const double lk = rsel[k] == 0 ? l[0] : (rsel[k] == 1 ? l[1] : (rsel[k] == 2 ? l[2] : l[3]));
+        if (rsel[k] < 3) Wb[toff[k]] = fma(-lk, uq[k], dv[k]);
+      }
+      // the new row j + 11 (zeros past the end)
+      double *Wn = Wb + 12 * 11;
+      Wn[p] = pre0;
+      Wn[p + 4] = pre1;
+      if (p + 8 < 11) Wn[p + 8] = pre2;
+      if (p == 3) Wn[11] = prz;
     }
+    __syncwarp();
+    const bool wrap = act && b + 1 == SOLVE_WROWS - 11;
+    // move rows b+1..b+11 (the next window) to the top of the buffer
+    double t[33];
+    if (wrap) {
 #pragma unroll
-    for (int k = 0; k < 17; ++k) {
-      const int i = code[k] & 15, q = (code[k] >> 4) & 15, r = code[k] >> 8;
-      const double lk = r == 0 ? l[0] : (r == 1 ? l[1] : l[2]);
-      if (q < 15 && j + i < n) {
-        double *dst = (q == 0) ? (Z + wrap11(s0 + i)) : (W + wrap11(s0 + i) * 11 + (i - q));
-        *dst = fma(-lk, uq[k], *dst);
+      for (int u = 0; u < 33; ++u) t[u] = Wb[12 + p + 4 * u];
+    }
+    __syncwarp();
+    if (wrap) {
+#pragma unroll
+      for (int u = 0; u < 33; ++u) W[p + 4 * u] = t[u];
+    }
+    __syncwarp();
+    if (act) {
+      b = wrap ? 0 : b + 1;
+      rj = rnext;
+    }
+  }
+  if (p == 0) W[SOLVE_WROWS * 12] = (double)b;
+  __syncwarp();
+  return bad;
+}
+
+__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Copies, for rows k0, k0-1, .., k0-10 of a chain, the multipliers
+// L(k, d) (d = 1..10) and the z value of row k - 11 (slot d = 0) into
+// buf[u * 11 + d] (u = k0 - k) with asynchronous copies; entries that do not
+// exist are zero.
+__device__ __forceinline__ void stage_rows(const Chain &c, bool on, int k0, int kstart,
+                                           double *buf, int p) {
+  for (int e = p; e < 121; e += 4) {
+    const int u = e / 11, d = e - 11 * u;
+    const int kk = k0 - u;
+    bool ok = on && kk >= 0 && kk < c.n && kk <= kstart + 9;
+    const double *src = nullptr;
+    if (ok) {
+      if (d == 0) {
+        ok = kk < kstart && kk - 11 >= 0;
+        if (ok) src = c.zstore(kk - 11);
+      } else {
+        ok = kk - d >= 0 && kk - d < kstart;
+        if (ok) src = c.entry(kk, d);
       }
     }
-    __syncwarp(cmask);
-    if (more) {
-      W[s0 * 11 + p] = pre0;
-      W[s0 * 11 + p + 4] = pre1;
-      if (p + 8 < 11) W[s0 * 11 + p + 8] = pre2;
-      if (p == 0) Z[s0] = c.rhs(j + 11);
-    } else {
-#pragma unroll
-      for (int d = 0; d < 11; d += 4) if (d + p < 11) W[s0 * 11 + d + p] = 0.0;
-      if (p == 0) Z[s0] = 0.0;
-    }
-    s0 = wrap11(s0 + 1);
-    rj = rnext;
-    __syncwarp(cmask);
+    if (ok) cp_async8(buf + e, src);
+    else buf[e] = 0.0;
   }
-  return bad;
 }
 
 // Right-looking backward substitution x_i = z_i - sum_d L[i+d][i] x_{i+d}
 // for chain rows kstart-1 .. 0, given x of rows kstart..kstart+9 in xs[].
-__device__ __forceinline__ void back_substitute(const Chain &c, int kstart, const double *xs,
-                                                double *Z, double *q, int p, unsigned cmask) {
-  // Z slot m % 11 holds the running z of chain row m (m < kstart)
-  for (int m = kstart - 1 - p; m >= 0 && m >= kstart - 11; m -= 4) Z[m % 11] = *c.zstore(m);
-  __syncwarp(cmask);
-  for (int k = kstart + 9; k >= 0; --k) {
-    if (k >= c.n) continue;
-    double xk;
-    if (k >= kstart) {
-      xk = xs[k - kstart];
-    } else {
-      xk = Z[k % 11];
-      if (p == 0) q[c.base + c.orig(k)] += xk;
-    }
-    double Lv[3];
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      const int d = 1 + p + 4 * t;
-      Lv[t] = (d <= 10 && k - d >= 0 && k - d < kstart) ? *c.entry(k, d) : 0.0;
-    }
-    const double znew = (p == 1 && k < kstart && k - 11 >= 0) ? *c.zstore(k - 11) : 0.0;
-    __syncwarp(cmask);
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      const int d = 1 + p + 4 * t;
-      if (d <= 10 && k - d >= 0 && k - d < kstart) {
-        const int slot = (k - d) % 11;
-        Z[slot] = fma(-Lv[t], xk, Z[slot]);
+// The chain's window buffer W (free by now) holds two staging buffers of
+// 11 rows (W[0..120], W[121..241]), filled by asynchronous copies one block
+// of rows ahead, and the running z values in an 11-slot ring (W[242..252]).
+// `on` = this chain solves; `ktop` = the warp's largest kstart + 9 (uniform
+// trip count, warp-wide synchronisation).
+__device__ __forceinline__ void back_substitute(const Chain &c, bool on, int kstart, int ktop,
+                                                const double *xs, double *W, double *q, int p) {
+  double *Z = W + 242;
+  if (on)
+    for (int m = kstart - 1 - p; m >= 0 && m >= kstart - 11; m -= 4) Z[m % 11] = *c.zstore(m);
+  stage_rows(c, on, ktop, kstart, W, p);
+  cp_async_commit();
+  for (int g = 0; ktop - 11 * g >= 0; ++g) {
+    const int k0 = ktop - 11 * g;
+    double *cur = W + 121 * (g & 1);
+    if (k0 - 11 >= 0) stage_rows(c, on, k0 - 11, kstart, W + 121 * ((g + 1) & 1), p);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncwarp();
+    for (int u = 0; u < 11; ++u) {
+      const int k = k0 - u;
+      const bool act = on && k >= 0 && k <= kstart + 9 && k < c.n;
+      double xk = 0.0;
+      if (act) {
+        if (k >= kstart) {
+          xk = xs[k - kstart];
+        } else {
+          xk = Z[k % 11];
+          if (p == 0) atomicAdd(q + c.base + c.orig(k), xk);  // no read on the chain
+        }
       }
+      __syncwarp();
+      if (act) {
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const int d = 1 + p + 4 * t;
+          if (d <= 10 && k - d >= 0 && k - d < kstart) {
+            const int slot = (k - d) % 11;
+            Z[slot] = fma(-cur[u * 11 + d], xk, Z[slot]);
+          }
+        }
+        if (p == 1 && k < kstart && k - 11 >= 0) Z[k % 11] = cur[u * 11];
+      }
+      __syncwarp();
     }
-    if (p == 1 && k < kstart && k - 11 >= 0) Z[k % 11] = znew;
-    __syncwarp(cmask);
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncwarp();
 }
 
 __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
@@ -311,124 +397,179 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
   double *Wb = Wt + SOLVE_CHAIN_STRIDE;
   double *XS = Wb + SOLVE_CHAIN_STRIDE;  // separator solution (10) + scratch
   double *W = half ? Wb : Wt;
-  double *Z = W + 121;
-  const unsigned umask = 0xFFu << (unit * 8);
-  const unsigned cmask = 0xFu << (unit * 8 + half * 4);
+  const unsigned full = 0xffffffffu;
   const int leader = unit * 8 + half * 4;
+  const bool head = (lane & 7) == 0;     // bookkeeping lane of the rod
 
+  // The warp takes four consecutive rods of the size-sorted queue at a time
+  // and factors them in lockstep.
   while (true) {
     int t = 0;
-    if ((lane & 7) == 0) t = atomicAdd(&a.ctrl[3], 1);
-    t = __shfl_sync(umask, t, unit * 8);
+    if (lane == 0) t = atomicAdd(&a.ctrl[3], SOLVE_RODS_PER_WARP);
+    t = __shfl_sync(full, t, 0);
     if (t >= a.nsys) break;
-    const int s = a.order[t];
-    if (!a.sys_active[s]) continue;
-    if (a.ls_action && a.ls_action[s] == 1) {  // backtracking: no solve this round
-      if ((lane & 7) == 0) atomicAdd(&a.ctrl[0], 1);
-      continue;
-    }
-    const double res = __longlong_as_double((long long)a.sys_res[s]);
-    int st = a.sys_status[s];
-    if (st == 0 && isnan(res)) st = DM_ERR_NONFINITE;
-    if (st == 0 && res <= a.tol) {  // converged at this iterate
-      if ((lane & 7) == 0) a.sys_active[s] = 0;
-      continue;
-    }
-    if (st == 0 && a.sys_iters[s] >= a.max_iter) st = DM_ERR_NOT_CONVERGED;
-    if (st != 0) {
-      if ((lane & 7) == 0) {
-        a.sys_status[s] = st;
-        a.sys_active[s] = 0;
-        atomicAdd(&a.ctrl[1], 1);
-        atomicMin(&a.ctrl[2], s);
+    const int my = t + unit;
+    const int s = my < a.nsys ? a.order[my] : -1;
+    // Newton bookkeeping of this rod: go = a solve is due this round
+    bool go = false;
+    if (s >= 0 && a.sys_active[s]) {
+      if (a.ls_action && a.ls_action[s] == 1) {  // backtracking: no solve this round
+        if (head) atomicAdd(&a.ctrl[0], 1);
+      } else {
+        const double res = __longlong_as_double((long long)a.sys_res[s]);
+        int st = a.sys_status[s];
+        if (st == 0 && isnan(res)) st = DM_ERR_NONFINITE;
+        if (st == 0 && res <= a.tol) {  // converged at this iterate
+          if (head) a.sys_active[s] = 0;
+        } else {
+          if (st == 0 && a.sys_iters[s] >= a.max_iter) st = DM_ERR_NOT_CONVERGED;
+          if (st != 0) {
+            if (head) {
+              a.sys_status[s] = st;
+              a.sys_active[s] = 0;
+              atomicAdd(&a.ctrl[1], 1);
+              atomicMin(&a.ctrl[2], s);
+            }
+          } else {
+            go = true;
+          }
+        }
       }
-      continue;
     }
-    const int n = a.sys_ndof[s];
-    Chain c{a.band, a.f, a.dq, (size_t)a.nd, (size_t)a.sys_dof0[s], n, half ? -1 : 1};
+    __syncwarp();
+    const int n = go ? a.sys_ndof[s] : 0;
+    Chain c{a.band, a.f, a.dq, (size_t)a.nd, go ? (size_t)a.sys_dof0[s] : 0, n, half ? -1 : 1};
     // split: top eliminates [0, m), bottom [m + 10, n), separator [m, m + 10)
     const bool twist = n >= 32;
     const int m = twist ? (n - 10) / 2 : n;
-    const int ncol = half ? (twist ? n - m - 10 : 0) : m;
-    bool bad = false;
-    if (!half || twist) bad = eliminate(c, ncol, W, Z, p, cmask, leader);
-    bad = __any_sync(umask, bad);
-    __syncwarp(umask);
-    if (bad) {
-      if ((lane & 7) == 0) {
+    const int ncol = !go ? 0 : (half ? (twist ? n - m - 10 : 0) : m);
+    const int nwarp = __reduce_max_sync(full, ncol);
+    bool bad = eliminate(c, ncol, nwarp, W, p, leader);
+    // a rod is bad if either of its chains met a zero pivot
+    const unsigned bm = __ballot_sync(full, bad);
+    bad = ((bm >> (unit * 8)) & 0xFFu) != 0;
+    if (bad && go) {
+      if (head) {
         a.sys_status[s] = DM_ERR_DEGENERATE;
         a.sys_active[s] = 0;
         atomicAdd(&a.ctrl[1], 1);
         atomicMin(&a.ctrl[2], s);
       }
-      continue;
+      go = false;
     }
-    if (twist) {
-      // separator: S = top window + bottom window - original, same for the
-      // right-hand side; dense LDL^T by one lane (10 x 10)
-      if ((lane & 7) == 0) {
-        const int nb = n - m - 10;
-        double S[10][10], r[10];
-        for (int i = 0; i < 10; ++i) {
-          for (int j2 = 0; j2 <= i; ++j2) {
-            const int d = i - j2;
-            const double top = Wt[((m + i) % 11) * 11 + d];
-            const double bot = Wb[((nb + 9 - j2) % 11) * 11 + d];
-            const double org = a.band[d * (size_t)a.nd + c.base + m + i];
-            S[i][j2] = top + bot - org;
-          }
-          r[i] = Wt[121 + (m + i) % 11] + Wb[121 + (nb + 9 - i) % 11] + a.f[c.base + m + i];
+    // separator: S = top window + bottom window - original (10 x 10, lower),
+    // right-hand side likewise; dense LDL^T by the rod's 8 lanes (one row of
+    // the trailing update each, rows 8 and 9 by lanes 0 and 1), staged in the
+    // top window after it has been read
+    const bool sep = go && twist;
+    const int r8 = lane & 7;
+    double sv[14];
+    if (sep) {
+      const int bt = (int)Wt[SOLVE_WROWS * 12], bb = (int)Wb[SOLVE_WROWS * 12];
+#pragma unroll
+      for (int u = 0; u < 14; ++u) {
+        const int e = r8 + 8 * u;  // 0..54 lower entries, 55..64 right-hand side
+        double v = 0.0;
+        if (e < 55) {
+          int i = 0;
+          while ((i + 1) * (i + 2) / 2 <= e) ++i;
+          const int j2 = e - i * (i + 1) / 2, d = i - j2;
+          v = Wt[(bt + i) * 12 + d] + Wb[(bb + 9 - j2) * 12 + d] -
+              a.band[d * (size_t)a.nd + c.base + m + i];
+        } else if (e < 65) {
+          const int i = e - 55;
+          v = Wt[(bt + i) * 12 + 11] + Wb[(bb + 9 - i) * 12 + 11] + a.f[c.base + m + i];
         }
-        for (int j2 = 0; j2 < 10; ++j2) {
-          const double dinv = 1.0 / S[j2][j2];
-          if (!isfinite(dinv)) bad = true;
-          // rows in decreasing order: S[k][j2] (k < i) is still unscaled
-          for (int i = 9; i > j2; --i) {
-            const double li = S[i][j2] * dinv;
-            for (int k = j2 + 1; k <= i; ++k) S[i][k] = fma(-li, S[k][j2], S[i][k]);
-            r[i] = fma(-li, r[j2], r[i]);
-            S[i][j2] = li;
-          }
-          S[j2][j2] = dinv;
-        }
-        for (int i = 9; i >= 0; --i) {
-          double x = r[i] * S[i][i];
-          for (int k = i + 1; k < 10; ++k) x = fma(-S[k][i], XS[k], x);
-          XS[i] = x;
-          a.q[c.base + m + i] += x;
+        sv[u] = v;
+      }
+    }
+    __syncwarp();
+    double *S = Wt;          // S[i * 10 + k], k <= i
+    double *rs = Wt + 100;   // right-hand side
+    if (sep) {
+#pragma unroll
+      for (int u = 0; u < 14; ++u) {
+        const int e = r8 + 8 * u;
+        if (e < 55) {
+          int i = 0;
+          while ((i + 1) * (i + 2) / 2 <= e) ++i;
+          S[i * 10 + (e - i * (i + 1) / 2)] = sv[u];
+        } else if (e < 65) {
+          rs[e - 55] = sv[u];
         }
       }
-      bad = __any_sync(umask, bad);
-      __syncwarp(umask);
-      if (bad) {
-        if ((lane & 7) == 0) {
-          a.sys_status[s] = DM_ERR_DEGENERATE;
-          a.sys_active[s] = 0;
-          atomicAdd(&a.ctrl[1], 1);
-          atomicMin(&a.ctrl[2], s);
-        }
-        continue;
-      }
-      // separator x in chain order for each half (the bottom chain sees the
-      // separator rows reversed)
-      double xs[10];
-#pragma unroll
-      for (int i = 0; i < 10; ++i) xs[i] = half ? XS[9 - i] : XS[i];
-      const int kstart = half ? n - m - 10 : m;
-      back_substitute(c, kstart, xs, Z, a.q, p, cmask);
-    } else if (!half) {
-      double xs[10];
-#pragma unroll
-      for (int i = 0; i < 10; ++i) xs[i] = 0.0;
-      back_substitute(c, n, xs, Z, a.q, p, cmask);
     }
-    __syncwarp(umask);
-    if ((lane & 7) == 0) {
+    __syncwarp();
+    bool sbad = false;
+    for (int j2 = 0; j2 < 10; ++j2) {
+      double dinv = 1.0, li[2] = {0.0, 0.0};
+      int ri[2] = {-1, -1};
+      if (sep) {
+        dinv = 1.0 / S[j2 * 10 + j2];
+        if (!isfinite(dinv)) sbad = true;
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int i = j2 + 1 + r8 + 8 * h2;
+          if (i < 10) {
+            ri[h2] = i;
+            li[h2] = S[i * 10 + j2] * dinv;
+          }
+        }
+      }
+      __syncwarp();
+      if (sep) {
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int i = ri[h2];
+          if (i < 0) continue;
+          for (int k = j2 + 1; k <= i; ++k) S[i * 10 + k] = fma(-li[h2], S[k * 10 + j2], S[i * 10 + k]);
+          rs[i] = fma(-li[h2], rs[j2], rs[i]);
+        }
+      }
+      __syncwarp();
+      if (sep) {
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2)
+          if (ri[h2] >= 0) S[ri[h2] * 10 + j2] = li[h2];
+        if (r8 == 0) S[j2 * 10 + j2] = dinv;
+      }
+      __syncwarp();
+    }
+    if (sep && head) {
+      for (int i = 9; i >= 0; --i) {
+        double x = rs[i] * S[i * 10 + i];
+        for (int k = i + 1; k < 10; ++k) x = fma(-S[k * 10 + i], XS[k], x);
+        XS[i] = x;
+        atomicAdd(a.q + c.base + m + i, x);
+      }
+    }
+    const unsigned sm = __ballot_sync(full, sbad);
+    if (((sm >> (unit * 8)) & 0xFFu) != 0 && go) {
+      if (head) {
+        a.sys_status[s] = DM_ERR_DEGENERATE;
+        a.sys_active[s] = 0;
+        atomicAdd(&a.ctrl[1], 1);
+        atomicMin(&a.ctrl[2], s);
+      }
+      go = false;
+    }
+    __syncwarp();
+    // separator x in chain order for each half (the bottom chain sees the
+    // separator rows reversed); a short rod is one top chain with no separator
+    double xs[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) xs[i] = (go && twist) ? (half ? XS[9 - i] : XS[i]) : 0.0;
+    const bool on = go && (twist || !half);
+    const int kstart = !on ? 0 : (twist ? (half ? n - m - 10 : m) : n);
+    const int ktop = __reduce_max_sync(full, on ? kstart + 9 : -1);
+    back_substitute(c, on, kstart, ktop, xs, W, a.q, p);
+    if (go && head) {
       a.sys_iters[s] += 1;
       if (a.ls_trial) a.ls_trial[s] = 1;
       atomicAdd(&a.ctrl[0], 1);
       if (a.units) atomicAdd(a.units, (unsigned long long)n);
     }
+    __syncwarp();
   }
 }
 
