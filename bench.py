@@ -74,6 +74,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rods", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="uneven_rods",
+                    choices=["uneven_rods", "star_robots", "coil", "warm_start"],
+                    help="uneven_rods: the headline batch (default); star_robots: limbed "
+                         "robots on the ground with a gait; coil: edge-edge self-contact; "
+                         "warm_start: learned vs extrapolated Newton guess on star robots")
+    ap.add_argument("--robots", type=int, default=1024)
     return ap.parse_args()
 
 
@@ -350,10 +356,168 @@ def run_ours(args):
         tdist.destroy_process_group()
 
 
+def _timed_steps(sysm, steps, controls, k0, local):
+    """Runs `steps` steps (controls(k) applied before step k0 + i) between CUDA
+    events with nvidia-smi sampling; returns (ms, per-step iterations, clocks)."""
+    import torch
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    its = []
+    e0.record()
+    for i in range(steps):
+        if controls is not None:
+            sysm.set_natural_curvature(0, sysm.n_rods, controls(k0 + i))
+        sysm.step(1, stats=True)
+        its.append(sysm.iterations.copy())
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), np.array(its), clk.stop()
+
+
+def _kernel_table(prof):
+    tot = sum(x[2] for x in prof.values()) or 1.0
+    return {k: {"launches": v[0], "units": v[1], "ms_total": round(v[2], 3),
+                "share": round(v[2] / tot, 4)} for k, v in prof.items()}
+
+
+def run_other(args):
+    """Star robots (scope config 3), the self-contacting coil (config 4's
+    contact part) and the learned warm start (config 5): one JSON line each,
+    same keys as the headline line; rod-steps/s counts every rod (limb) of
+    the batch."""
+    import torch
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import workloads
+    from paper_2311_18126_gb300 import System, ensure_built, fp64_peak_gflops
+    ensure_built()
+    peak_fp64 = fp64_peak_gflops()
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic"}
+    if args.workload in ("star_robots", "warm_start"):
+        desc, params, gait = workloads.star_robots(n_robots=args.robots, seed=777 + rank)
+        dt = params["dt"]
+        controls = lambda k: workloads.gait_kbar(gait, k * dt)
+        line["config"] = {"workload": "star_robots: %d robots of 3-8 limbs x 30 nodes on the "
+                          "ground, gait kappabar, dt=5e-3 s, line search" % args.robots,
+                          "rods_per_gpu": len(desc["nodes_per_rod"]), "seed": 777 + rank,
+                          "l2": "no flush: per-iteration working set exceeds L2 at 1024 robots"}
+    else:
+        desc, params, _ = workloads.coil(N=500)
+        controls = None
+        line["config"] = {"workload": "coil: one 500-node helix collapsing under gravity into "
+                          "edge-edge self-contact, dt=2.5e-4 s, line search", "rods_per_gpu": 1,
+                          "l2": "working set in L2 (one system)"}
+    R = len(desc["nodes_per_rod"])
+    warm = args.warmup if args.workload != "coil" else max(args.warmup, 400)
+    line["warmup"] = warm
+    if args.workload == "warm_start":
+        from paper_2311_18126_gb300 import warmstart as wsm
+        tdesc, tparams, tgait = workloads.star_robots(n_robots=max(args.robots // 4, 64),
+                                                      seed=101 + rank)
+        tsys = System(tdesc, tparams)
+        feats, tgts = wsm.collect(tsys, 400, controls=lambda k: workloads.gait_kbar(tgait, k * dt),
+                                  every=2)
+        tsys.close()
+        mlp, norm, losses = wsm.train(feats, tgts, iters=4000, batch=16384, seed=1)
+        del feats, tgts
+        arms = {}
+        for label, model in (("extrapolation", None), ("learned", mlp)):
+            sysm = System(desc, params)
+            if model is not None:
+                sysm.ws_enable()
+                sysm.ws_set_model(model, norm)
+            for k in range(warm):
+                sysm.set_natural_curvature(0, R, controls(k))
+                sysm.step(1, stats=False)
+            sysm.set_profiling(True)
+            ms, its, clocks = _timed_steps(sysm, args.steps, controls, warm, local)
+            ms = max_over_ranks(ms, ws, "cuda")
+            arms[label] = {"value": job_rate(ws, R, args.steps, ms * 1e-3),
+                           "ms_per_step": ms / args.steps,
+                           "iters_per_rod_step": float(its.mean()),
+                           "slowest_per_step": float(its.max(1).mean()),
+                           "kernels": _kernel_table(sysm.get_profile()), "clocks": clocks}
+            sysm.close()
+        line.update({"value": arms["learned"]["value"],
+                     "ms_per_step": arms["learned"]["ms_per_step"],
+                     "learned": {"speedup_vs_extrapolation":
+                                 arms["learned"]["value"] / arms["extrapolation"]["value"],
+                                 "train_loss": [losses[0], losses[-1]], "arms": arms},
+                     "clocks": arms["learned"]["clocks"],
+                     "gpu_launches": int(sum(v["launches"] for v in
+                                             arms["learned"]["kernels"].values())),
+                     "e2e": None, "roofline": None})
+        line["config"]["training"] = "%d robots x 400 steps (every 2nd step sampled), 4000 Adam " \
+                                     "steps of 16384 segments" % max(args.robots // 4, 64)
+    else:
+        sysm = System(desc, params)
+        for k in range(warm):
+            if controls is not None:
+                sysm.set_natural_curvature(0, R, controls(k))
+            sysm.step(1, stats=False)
+        sysm.set_profiling(True)
+        ms, its, clocks = _timed_steps(sysm, args.steps, controls, warm, local)
+        prof = sysm.get_profile()
+        ms = max_over_ranks(ms, ws, "cuda")
+        value = job_rate(ws, R, args.steps, ms * 1e-3)
+        # end to end through the C ABI: pinned host state in and out every step
+        n = sysm.n_state
+        hq = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        hv = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        q0, v0 = sysm.get_state()
+        hq.numpy()[:] = q0
+        hv.numpy()[:] = v0
+        e2e_steps = max(3, args.steps // 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            if controls is not None:
+                sysm.set_natural_curvature(0, R, controls(warm + args.steps + i))
+            sysm.set_state(hq.numpy(), hv.numpy())
+            sysm.step(1, stats=False)
+            qq, vv = sysm.get_state()
+            hq.numpy()[:] = qq
+            hv.numpy()[:] = vv
+        torch.cuda.synchronize()
+        te = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
+        dom = max(prof, key=lambda k: prof[k][2])
+        line.update({"value": value, "ms_per_step": ms / args.steps,
+                     "newton": {"iters_mean": float(its.mean()), "iters_max": int(its.max()),
+                                "slowest_per_step_mean": float(its.max(1).mean())},
+                     "clocks": clocks,
+                     "e2e": {"value": job_rate(ws, R, e2e_steps, te), "unit": UNIT,
+                             "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": 2 * n * 8},
+                     "gpu_launches": int(sum(v[0] for v in prof.values())),
+                     "roofline": {"bound": "alu", "kernel": dom, "unit": "TFLOP/s",
+                                  "peak": peak_fp64 / 1e3, "achieved": None, "frac": None,
+                                  "traffic": None,
+                                  "note": "no per-unit counts for this kernel: latency bound "
+                                          "(few systems active in most Newton rounds)"},
+                     "kernels": _kernel_table(prof)})
+        if args.workload == "coil":
+            line["contact_pairs"] = sysm.contact_pairs()
+        sysm.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "uneven_rods":
+        run_other(args)
     else:
         run_ours(args)
 

@@ -106,6 +106,7 @@ struct Extra {
     int32_t *edge_idx = nullptr, *contact_sys = nullptr, *sys_bw = nullptr;
     int32_t *bucket_count = nullptr, *bucket_start = nullptr, *bucket_fill = nullptr,
             *bucket_edges = nullptr, *pairs = nullptr, *npairs = nullptr;
+    int32_t *cgo = nullptr, *cbad = nullptr;
     int64_t *sys_dense0 = nullptr;
     unsigned long long *edge_key = nullptr;
   } cc;  // edge-edge contact
@@ -298,6 +299,8 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     DM_TRY(dalloc(s, &c.fc, nd));
     DM_TRY(dalloc(s, &c.dense, tot));
     DM_TRY(dalloc(s, &c.sys_bw, S));
+    DM_TRY(dalloc(s, &c.cgo, S));
+    DM_TRY(dalloc(s, &c.cbad, S));
     DM_CK(cudaMemset(c.dense, 0, tot * sizeof(double)));
     DM_CK(cudaMemset(c.npairs, 0, sizeof(int32_t)));
     std::vector<int32_t> bw10(S, 10);
@@ -572,6 +575,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     ca.bucket_start = c.bucket_start; ca.bucket_fill = c.bucket_fill;
     ca.bucket_edges = c.bucket_edges; ca.pairs = c.pairs; ca.npairs = c.npairs;
     ca.fc = c.fc; ca.dense = c.dense;
+    ca.n_contact = c.n_contact; ca.cgo = c.cgo; ca.cbad = c.cbad;
   }
   RowArgs ra{};
   ra.fc = contact_on ? s->x.cc.fc : nullptr;
@@ -706,7 +710,21 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       if (contact_on) {
         Timed t(s, K_SOLVE_CONTACT, st);
         k_cc_band<<<blocks(nd, 256), 256, 0, st>>>(ca);
-        k_solve_contact<<<s->x.cc.n_contact, 1024, 0, st>>>(ca, va);
+        const int nc = s->x.cc.n_contact;
+        k_cc_decide<<<blocks(nc, 128), 128, 0, st>>>(ca, va);
+        for (int c = 0; c < nc; ++c) {
+          const int n = T.sys_ndof[c];  // contact systems are systems 0..nc-1 in order
+          for (int k = 0; k < n; k += kNB) {
+            const int rest = n - k - std::min(kNB, n - k);
+            k_lu_diag<<<1, 256, 0, st>>>(ca, c, k);
+            if (rest > 0) {
+              k_lu_trsm<<<blocks(2 * rest, 128), 128, 0, st>>>(ca, c, k);
+              const int t = (rest + 63) / 64;
+              k_lu_gemm<<<dim3(t, t), 256, 0, st>>>(ca, c, k);
+            }
+          }
+        }
+        k_cc_subst<<<nc, 1024, 0, st>>>(ca, va);
       }
       if (gen_on) {
         DM_CK(cudaMemsetAsync(d.gen, 0, T.gen_doubles * sizeof(double), st));

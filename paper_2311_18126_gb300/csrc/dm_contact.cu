@@ -19,9 +19,9 @@
 //                             the Hessian into the system's dense matrix.
 //  k_cc_band               -- adds the rod's own band (11 lower diagonals of
 //                             the symmetric Jacobian) to the dense matrix.
-//  k_solve_contact         -- one block per system: LU without pivoting
-//                             restricted to the current bandwidth (the rod
-//                             band widened by the contacts), solve, q += dq.
+//  k_lu_* / k_cc_subst     -- blocked LU without pivoting restricted to the
+//                             current bandwidth (the rod band widened by the
+//                             contacts) over all SMs, then the solve, q += dq.
 #include <cmath>
 
 #include "dm_internal.h"
@@ -438,64 +438,183 @@ __global__ void k_cc_reset_bw(ContactArgs a) {
   if (s < a.nsys) a.sys_bw[s] = 10;
 }
 
-// LU without pivoting of the dense matrix restricted to the bandwidth,
-// forward elimination of -f alongside, back substitution, q += dq.
-__global__ void __launch_bounds__(1024) k_solve_contact(ContactArgs a, SolveArgs v) {
-  const int s = a.contact_sys[blockIdx.x];
-  __shared__ int go;
-  __shared__ int bad;
-  if (threadIdx.x == 0) {
-    go = 0;
-    bad = 0;
-    if (v.sys_active[s] && v.ls_action && v.ls_action[s] == 1) {
-      atomicAdd(&v.ctrl[0], 1);
-    } else if (v.sys_active[s]) {
-      const double res = __longlong_as_double((long long)v.sys_res[s]);
-      int st = v.sys_status[s];
-      if (st == 0 && isnan(res)) st = DM_ERR_NONFINITE;
-      if (st == 0 && res <= v.tol) {
+// --- blocked LU of a contact system (no pivoting), spread over the GPU ---
+//
+// The rod's Jacobian widened by the contact blocks, within its current
+// bandwidth bw, is factored in panels of kNB columns: the kNB x kNB
+// diagonal block by one block (k_lu_diag), the panel's L (rows below) and
+// U (columns right) by triangular solves with one thread per row or column
+// (k_lu_trsm), and the trailing update A22 -= L21 U12 by 64 x 64 FP64 tiles
+// over all SMs (k_lu_gemm).  Nothing outside |i - j| <= bw is touched: the
+// LU of a band matrix without pivoting has no fill outside the band.
+// k_cc_decide takes the Newton decision of each contact system first;
+// k_cc_subst solves with the factors (blocked forward and backward
+// substitution) and updates q.
+
+__global__ void k_cc_decide(ContactArgs a, SolveArgs v) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.n_contact) return;
+  const int s = a.contact_sys[c];
+  int go = 0;
+  if (v.sys_active[s] && v.ls_action && v.ls_action[s] == 1) {
+    atomicAdd(&v.ctrl[0], 1);  // backtracking: no solve this round
+  } else if (v.sys_active[s]) {
+    const double res = __longlong_as_double((long long)v.sys_res[s]);
+    int st = v.sys_status[s];
+    if (st == 0 && isnan(res)) st = DM_ERR_NONFINITE;
+    if (st == 0 && res <= v.tol) {
+      v.sys_active[s] = 0;
+    } else {
+      if (st == 0 && v.sys_iters[s] >= v.max_iter) st = DM_ERR_NOT_CONVERGED;
+      if (st != 0) {
+        v.sys_status[s] = st;
         v.sys_active[s] = 0;
+        atomicAdd(&v.ctrl[1], 1);
+        atomicMin(&v.ctrl[2], s);
       } else {
-        if (st == 0 && v.sys_iters[s] >= v.max_iter) st = DM_ERR_NOT_CONVERGED;
-        if (st != 0) {
-          v.sys_status[s] = st;
-          v.sys_active[s] = 0;
-          atomicAdd(&v.ctrl[1], 1);
-          atomicMin(&v.ctrl[2], s);
-        } else {
-          go = 1;
-        }
+        go = 1;
       }
     }
   }
+  a.cgo[c] = go;
+  a.cbad[c] = 0;
+}
+
+__global__ void __launch_bounds__(256) k_lu_diag(ContactArgs a, int c, int k) {
+  if (!a.cgo[c] || a.cbad[c]) return;
+  const int s = a.contact_sys[c];
+  const int n = a.sys_ndof[s];
+  const int nb = min(kNB, n - k);
+  double *A = a.dense + a.sys_dense0[s];
+  __shared__ double D[kNB][kNB + 1];
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, j = t - i * nb;
+    D[i][j] = A[(size_t)(k + i) * n + k + j];
+  }
   __syncthreads();
-  if (!go) return;
-  const int d0 = v.sys_dof0[s], n = v.sys_ndof[s];
-  const int bw = max(10, a.sys_bw[s]);
-  double *M = a.dense + a.sys_dense0[s];
-  double *y = v.dq + d0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = -v.f[d0 + i];
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    const double piv = M[(size_t)j * n + j];
+  for (int j = 0; j < nb; ++j) {
+    const double piv = D[j][j];
     if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
-      if (threadIdx.x == 0) bad = 1;
-      break;
+      if (threadIdx.x == 0) a.cbad[c] = 1;
+      return;  // uniform: every thread read the same pivot
     }
     const double rp = 1.0 / piv;
-    const int m = min(bw, n - 1 - j);  // rows/columns below/right within the band
-    const double *Uj = M + (size_t)j * n;
-    for (int t = threadIdx.x; t < m * (m + 1); t += blockDim.x) {
-      const int i = t / (m + 1) + 1, k = t - (i - 1) * (m + 1);
-      double *Ri = M + (size_t)(j + i) * n;
-      const double l = Ri[j] * rp;
-      if (k == 0) y[j + i] = fma(-l, y[j], y[j + i]);
-      else Ri[j + k] = fma(-l, Uj[j + k], Ri[j + k]);
+    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) D[i][j] *= rp;
+    __syncthreads();
+    const int m = nb - 1 - j;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int i = j + 1 + t / m, cc = j + 1 + t % m;
+      D[i][cc] = fma(-D[i][j], D[j][cc], D[i][cc]);
     }
     __syncthreads();
   }
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, j = t - i * nb;
+    A[(size_t)(k + i) * n + k + j] = D[i][j];
+  }
+}
+
+// Rows [k+nb, rend): L21 = A21 U11^{-1}; columns [k+nb, cend): U12 = L11^{-1} A12.
+__global__ void __launch_bounds__(128) k_lu_trsm(ContactArgs a, int c, int k) {
+  if (!a.cgo[c] || a.cbad[c]) return;
+  const int s = a.contact_sys[c];
+  const int n = a.sys_ndof[s];
+  const int nb = min(kNB, n - k);
+  const int bw = max(10, a.sys_bw[s]);
+  const int lo = k + nb, hi = min(n, k + nb + bw);
+  const int cnt = hi - lo;
+  if (cnt <= 0) return;
+  double *A = a.dense + a.sys_dense0[s];
+  __shared__ double D[kNB][kNB + 1];
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, j = t - i * nb;
+    D[i][j] = A[(size_t)(k + i) * n + k + j];
+  }
   __syncthreads();
-  if (bad) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  double x[kNB];
+  if (g < cnt) {  // a row of L21: x U11 = a
+    double *row = A + (size_t)(lo + g) * n + k;
+#pragma unroll
+    for (int j = 0; j < kNB; ++j) {
+      if (j < nb) {
+        double v = row[j];
+        for (int m = 0; m < j; ++m) v = fma(-x[m], D[m][j], v);
+        x[j] = v / D[j][j];
+        row[j] = x[j];
+      }
+    }
+  } else if (g < 2 * cnt) {  // a column of U12: L11 x = a (unit lower)
+    const int col = lo + (g - cnt);
+#pragma unroll
+    for (int j = 0; j < kNB; ++j) {
+      if (j < nb) {
+        double v = A[(size_t)(k + j) * n + col];
+        for (int m = 0; m < j; ++m) v = fma(-D[j][m], x[m], v);
+        x[j] = v;
+        A[(size_t)(k + j) * n + col] = v;
+      }
+    }
+  }
+}
+
+// A22 -= L21 U12 over [k+nb, k+nb+bw)^2 in 64 x 64 tiles, 4 x 4 per thread.
+__global__ void __launch_bounds__(256) k_lu_gemm(ContactArgs a, int c, int k) {
+  if (!a.cgo[c] || a.cbad[c]) return;
+  const int s = a.contact_sys[c];
+  const int n = a.sys_ndof[s];
+  const int nb = min(kNB, n - k);
+  const int bw = max(10, a.sys_bw[s]);
+  const int lo = k + nb, hi = min(n, k + nb + bw);
+  const int r0 = lo + blockIdx.y * 64, c0 = lo + blockIdx.x * 64;
+  if (r0 >= hi || c0 >= hi) return;
+  double *A = a.dense + a.sys_dense0[s];
+  __shared__ double Ls[64][kNB + 1];
+  __shared__ double Us[kNB][64 + 1];
+  for (int t = threadIdx.x; t < 64 * kNB; t += blockDim.x) {
+    const int i = t / kNB, m = t - i * kNB;
+    Ls[i][m] = (r0 + i < hi && m < nb) ? A[(size_t)(r0 + i) * n + k + m] : 0.0;
+  }
+  for (int t = threadIdx.x; t < kNB * 64; t += blockDim.x) {
+    const int m = t / 64, j = t - m * 64;
+    Us[m][j] = (c0 + j < hi && m < nb) ? A[(size_t)(k + m) * n + c0 + j] : 0.0;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) acc[u][w] = 0.0;
+  for (int m = 0; m < nb; ++m) {
+    double lv[4], uv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) lv[u] = Ls[ty + 16 * u][m];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) uv[w] = Us[m][tx + 16 * w];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) acc[u][w] = fma(lv[u], uv[w], acc[u][w]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = r0 + ty + 16 * u;
+    if (i >= hi) continue;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int j = c0 + tx + 16 * w;
+      if (j < hi) A[(size_t)i * n + j] -= acc[u][w];
+    }
+  }
+}
+
+// Blocked substitution with the factors (L unit lower, U upper), q += x.
+__global__ void __launch_bounds__(1024) k_cc_subst(ContactArgs a, SolveArgs v) {
+  const int c = blockIdx.x;
+  const int s = a.contact_sys[c];
+  if (!a.cgo[c]) return;
+  if (a.cbad[c]) {
     if (threadIdx.x == 0) {
       v.sys_status[s] = DM_ERR_DEGENERATE;
       v.sys_active[s] = 0;
@@ -504,16 +623,53 @@ __global__ void __launch_bounds__(1024) k_solve_contact(ContactArgs a, SolveArgs
     }
     return;
   }
-  // back substitution, column oriented: x_j = y_j / U_jj, then the rows
-  // above within the band lose U_ij x_j
-  for (int j = n - 1; j >= 0; --j) {
-    const double xj = y[j] / M[(size_t)j * n + j];
+  const int d0 = v.sys_dof0[s], n = v.sys_ndof[s];
+  const int bw = max(10, a.sys_bw[s]);
+  const double *A = a.dense + a.sys_dense0[s];
+  double *y = v.dq + d0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = -v.f[d0 + i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // forward: L y = -f
+  for (int k = 0; k < n; k += kNB) {
+    const int nb = min(kNB, n - k);
+    if (warp == 0) {
+      double yv = lane < nb ? y[k + lane] : 0.0;
+      for (int j = 0; j < nb; ++j) {
+        const double yj = __shfl_sync(0xffffffffu, yv, j);
+        if (lane > j && lane < nb) yv = fma(-A[(size_t)(k + lane) * n + k + j], yj, yv);
+      }
+      if (lane < nb) y[k + lane] = yv;
+    }
     __syncthreads();
-    for (int i = max(0, j - bw) + threadIdx.x; i < j; i += blockDim.x)
-      y[i] = fma(-M[(size_t)i * n + j], xj, y[i]);
-    if (threadIdx.x == 0) {
-      y[j] = xj;
-      atomicAdd(v.q + d0 + j, xj);
+    for (int i = k + nb + threadIdx.x; i < min(n, k + nb + bw); i += blockDim.x) {
+      double v2 = y[i];
+      for (int m = 0; m < nb; ++m) v2 = fma(-A[(size_t)i * n + k + m], y[k + m], v2);
+      y[i] = v2;
+    }
+    __syncthreads();
+  }
+  // backward: U x = y
+  for (int k = ((n - 1) / kNB) * kNB; k >= 0; k -= kNB) {
+    const int nb = min(kNB, n - k);
+    if (warp == 0) {
+      double xv = lane < nb ? y[k + lane] : 0.0;
+      for (int j = nb - 1; j >= 0; --j) {
+        double xj = __shfl_sync(0xffffffffu, xv, j);
+        xj = xj / A[(size_t)(k + j) * n + k + j];
+        if (lane == j) xv = xj;
+        if (lane < j) xv = fma(-A[(size_t)(k + lane) * n + k + j], xj, xv);
+      }
+      if (lane < nb) {
+        y[k + lane] = xv;
+        atomicAdd(v.q + d0 + k + lane, xv);
+      }
+    }
+    __syncthreads();
+    for (int i = max(0, k - bw) + threadIdx.x; i < k; i += blockDim.x) {
+      double v2 = y[i];
+      for (int m = 0; m < nb; ++m) v2 = fma(-A[(size_t)i * n + k + m], y[k + m], v2);
+      y[i] = v2;
     }
     __syncthreads();
   }

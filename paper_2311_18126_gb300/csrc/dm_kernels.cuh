@@ -144,7 +144,10 @@ struct ContactArgs {
   int32_t *bucket_count, *bucket_start, *bucket_fill, *bucket_edges;
   int32_t *pairs, *npairs;
   double *fc, *dense;
+  int n_contact;
+  int32_t *cgo, *cbad;  // per contact system: solve this round, zero pivot met
 };
+constexpr int kNB = 32;  // panel width of the contact-system LU
 __global__ void k_cc_cells(ContactArgs a);
 __global__ void k_cc_scan(ContactArgs a);
 __global__ void k_cc_fill(ContactArgs a);
@@ -153,7 +156,11 @@ __global__ void k_cc_terms(ContactArgs a);
 __global__ void k_cc_band(ContactArgs a);
 __global__ void k_cc_clear(ContactArgs a);
 __global__ void k_cc_reset_bw(ContactArgs a);
-__global__ void k_solve_contact(ContactArgs a, SolveArgs v);
+__global__ void k_cc_decide(ContactArgs a, SolveArgs v);
+__global__ void k_lu_diag(ContactArgs a, int c, int k);
+__global__ void k_lu_trsm(ContactArgs a, int c, int k);
+__global__ void k_lu_gemm(ContactArgs a, int c, int k);
+__global__ void k_cc_subst(ContactArgs a, SolveArgs v);
 
 __global__ void k_ls_merit(LineSearchArgs a);
 __global__ void k_ls_decide(LineSearchArgs a);
