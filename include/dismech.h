@@ -295,8 +295,9 @@ dm_status dm_ws_column_stats(const float *data, int64_t rows, int32_t cols, floa
  * number of edge pairs closer than C + delta at the last evaluated Newton
  * iterate, summed over the systems (0 without edge-edge contact, -1 on a
  * CUDA error).  Synchronises the stream.  Contact acts within single rods
- * (no joints, no ground contact) and without friction (pair_mu = 0);
- * dm_create_system rejects other combinations with DM_ERR_INVALID_ARG. */
+ * (no joints, no ground contact); friction at the closest points (Eq. 12-13)
+ * when pair_mu > 0, with the slip tolerance slip_nu.  dm_create_system
+ * rejects other combinations with DM_ERR_INVALID_ARG. */
 int64_t dm_contact_pairs(dm_system *sys);
 
 /* Per-kernel profile of dm_step calls made while profiling is on: CUDA-event

@@ -5,7 +5,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 Sec. III-B of the DisMech paper (arXiv 2311.18126):
 * Eq. 10: IMC contact energy of the minimum distance D, with K1 = 15/delta.
 * Eq. 11: contact force = -(dE/dD) (dD/dq).
-* Eq. 12-13: friction gamma(|u|) with K2 = 15/nu, F_fr = -mu gamma u_hat |F_con|.
+* Eq. 12-13: friction gamma(|u|) with K2 = 15/nu, F_fr = -mu gamma u_hat |F_con|,
+  on the ground and at the closest points of touching edge pairs.
 
 Readings (design notes): the energy is multiplied by a stiffness k_c (C11);
 the quadratic branch extends to D <= 0 for the ground (C12); the tangential
@@ -166,3 +167,65 @@ def pair_terms(osys, s, q, q_n, need_jac):
     g = vmap(grad(_pair_energy))(xa, Ca, dl, kk)
     H = vmap(jacfwd(grad(_pair_energy)))(xa, Ca, dl, kk) if need_jac else None
     yield dofs[act].numpy(), -g, H
+    mu = float(p.get("pair_mu", 0.0))
+    if mu == 0.0:
+        return
+    # friction at the closest points (Eq. 12-13, reading C28)
+    xn = q_n[dofs[act]]
+    nu = float(p["nu_slip"])
+    mm = torch.full_like(Ca, mu)
+    nn = torch.full_like(Ca, nu)
+    dtt = torch.full_like(Ca, float(osys.dt))
+    sig = torch.linalg.vector_norm(vmap(_pair_slip)(xa, xn, dtt), dim=-1)
+    moving = torch.nonzero(sig > 0).reshape(-1)
+    still = torch.nonzero(sig == 0).reshape(-1)
+    for idx, fn in ((moving, _pair_friction), (still, _pair_friction_limit)):
+        if len(idx) == 0:
+            continue
+        args = (xa[idx], xn[idx], Ca[idx], dl[idx], kk[idx], mm[idx], nn[idx], dtt[idx])
+        F = vmap(fn)(*args)
+        J = -vmap(jacfwd(fn))(*args) if need_jac else None
+        yield dofs[act][idx].numpy(), F, J
+
+
+def _pair_slip(x12, xn12, dt):
+    """Tangential relative velocity of the closest points of a pair, with
+    the implicit velocities (x - x_n)/dt (reading C26 for the ground)."""
+    D, s, t = segment_distance(x12[0:3], x12[3:6], x12[6:9], x12[9:12])
+    d = (x12[0:3] + s * (x12[3:6] - x12[0:3])) - (x12[6:9] + t * (x12[9:12] - x12[6:9]))
+    n = d / D
+    v = (x12 - xn12) / dt
+    va = (1.0 - s) * v[0:3] + s * v[3:6]
+    vb = (1.0 - t) * v[6:9] + t * v[9:12]
+    vr = va - vb
+    return vr - der.dot(vr, n) * n
+
+
+def _pair_normal_force(x12, C, delta, kc):
+    """|F_con| of the pair: the net contact force on either edge,
+    k_c |dE/dD| (Eq. 11 with |dD/dx| summed over an edge's nodes = 1)."""
+    D, _, _ = segment_distance(x12[0:3], x12[3:6], x12[6:9], x12[9:12])
+    return torch.abs(kc * grad(der.imc_energy)(D, C, delta))
+
+
+def _distribute(x12, Fa):
+    _, s, t = segment_distance(x12[0:3], x12[3:6], x12[6:9], x12[9:12])
+    return torch.cat([(1.0 - s) * Fa, s * Fa, -(1.0 - t) * Fa, -t * Fa])
+
+
+def _pair_friction(x12, xn12, C, delta, kc, mu, nu, dt):
+    """Eq. 13 on edge a (and its opposite on edge b), spread to the nodes
+    by the closest-point weights."""
+    u = _pair_slip(x12, xn12, dt)
+    sp = torch.linalg.vector_norm(u)
+    gam = der.friction_gamma(sp, nu)
+    Fa = -mu * gam * u / sp * _pair_normal_force(x12, C, delta, kc)
+    return _distribute(x12, Fa)
+
+
+def _pair_friction_limit(x12, xn12, C, delta, kc, mu, nu, dt):
+    """The u -> 0 limit of the friction law, -mu |F_con| (K2 / 2) u, whose
+    value is 0 at u = 0 and whose Jacobian is the limit of the smooth one."""
+    u = _pair_slip(x12, xn12, dt)
+    Fa = -mu * (7.5 / nu) * u * _pair_normal_force(x12, C, delta, kc)
+    return _distribute(x12, Fa)

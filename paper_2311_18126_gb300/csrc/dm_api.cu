@@ -141,8 +141,8 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
       set_error("edge-edge contact together with ground contact is not supported");
       return DM_ERR_INVALID_ARG;
     }
-    if (prm->pair_mu != 0.0) {
-      set_error("edge-edge friction (pair_mu != 0) is not supported");
+    if (prm->pair_mu < 0.0 || (prm->pair_mu > 0.0 && !(prm->slip_nu > 0.0))) {
+      set_error("edge-edge friction needs pair_mu >= 0 and slip_nu > 0");
       return DM_ERR_INVALID_ARG;
     }
     if (!(prm->pair_kc > 0 && prm->delta > 0)) {
@@ -565,7 +565,9 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     auto &c = s->x.cc;
     ca.ne = ne; ca.nd = nd; ca.nsys = S; ca.table_mask = c.table - 1; ca.pair_cap = c.pair_cap;
     ca.inv_cell = c.inv_cell; ca.delta = s->prm.delta; ca.kc = s->prm.pair_kc;
-    ca.q = d.q; ca.edge_h = c.edge_h; ca.band = d.band;
+    ca.mu = s->prm.pair_mu; ca.K2 = s->prm.pair_mu > 0 ? 15.0 / s->prm.slip_nu : 0.0;
+    ca.dt = s->p.dt;
+    ca.q = d.q; ca.qn = d.qn; ca.edge_h = c.edge_h; ca.band = d.band;
     ca.edge_a = d.edge_a; ca.edge_b = d.edge_b; ca.edge_sys = d.edge_sys; ca.edge_idx = c.edge_idx;
     ca.sys_kind = s->x.d_sys_kind; ca.sys_active = d.sys_active; ca.dof_sys = s->x.d_dof_sys;
     ca.sys_dof0 = d.sys_dof0; ca.sys_ndof = d.sys_ndof; ca.contact_sys = c.contact_sys;

@@ -90,6 +90,68 @@ __device__ void hd_div(const HD &a, const HD &b, HD &tmp, HD &o) {
   hd_mul(a, tmp, o);
 }
 
+// First-order dual number in the 12 coordinates of a pair (value and
+// gradient), for the friction force whose Jacobian is not a Hessian.
+struct D1 {
+  double v;
+  double g[12];
+};
+__device__ __forceinline__ D1 d1_of(const HD &a) {
+  D1 o;
+  o.v = a.v;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) o.g[i] = a.g[i];
+  return o;
+}
+__device__ __forceinline__ D1 d1_const(double v) {
+  D1 o;
+  o.v = v;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) o.g[i] = 0.0;
+  return o;
+}
+__device__ __forceinline__ D1 d1_var(double v, int k) {
+  D1 o = d1_const(v);
+  o.g[k] = 1.0;
+  return o;
+}
+__device__ __forceinline__ D1 operator+(const D1 &a, const D1 &b) {
+  D1 o;
+  o.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) o.g[i] = a.g[i] + b.g[i];
+  return o;
+}
+__device__ __forceinline__ D1 operator-(const D1 &a, const D1 &b) {
+  D1 o;
+  o.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) o.g[i] = a.g[i] - b.g[i];
+  return o;
+}
+__device__ __forceinline__ D1 operator*(const D1 &a, const D1 &b) {
+  D1 o;
+  o.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) o.g[i] = fma(a.v, b.g[i], b.v * a.g[i]);
+  return o;
+}
+__device__ __forceinline__ D1 operator*(double c, const D1 &a) {
+  D1 o;
+  o.v = c * a.v;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) o.g[i] = c * a.g[i];
+  return o;
+}
+// f(a) with f(a.v) = f0, f'(a.v) = f1
+__device__ __forceinline__ D1 d1_apply(const D1 &a, double f0, double f1) {
+  D1 o;
+  o.v = f0;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) o.g[i] = f1 * a.g[i];
+  return o;
+}
+
 // Coordinates of a pair: x[0..2] = p0, x[3..5] = p1, x[6..8] = q0,
 // x[9..11] = q1.  The vectors a = p1 - p0, b = q1 - q0, r = p0 - q0 are
 // linear in x: component c is +1 at variable P + c and -1 at N + c.
@@ -402,6 +464,68 @@ __global__ void __launch_bounds__(64) k_cc_terms(ContactArgs a) {
     }
   }
   atomicMax(a.sys_bw + s, bw);
+  if (a.mu == 0.0) return;
+  // Friction at the closest points (Eq. 12-13): u = tangential relative
+  // velocity of the closest points with the implicit velocities
+  // (x - x_n)/dt; F_a = -mu gamma(|u|) u/|u| |F_con| on edge a, -F_a on
+  // edge b, spread by the closest-point weights; |F_con| = k_c |dE/dD|.
+  // Derivatives by first-order dual numbers; at |u| = 0 the limit
+  // gamma/|u| -> K2/2 of the smooth law.
+  const D1 sD = d1_of(W.s), tD = d1_of(W.t), Dd = d1_of(D);
+  D1 nrm[3];
+  const D1 iD = d1_apply(Dd, 1.0 / Dd.v, -1.0 / (Dd.v * Dd.v));
+#pragma unroll
+  for (int c = 0; c < 3; ++c) nrm[c] = d1_of(W.d[c]) * iD;
+  const double idt = 1.0 / a.dt;
+  D1 ur[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const D1 v0 = idt * (d1_var(x[c], c) - d1_const(a.qn[dof[c]]));
+    const D1 v1 = idt * (d1_var(x[3 + c], 3 + c) - d1_const(a.qn[dof[3 + c]]));
+    const D1 v2 = idt * (d1_var(x[6 + c], 6 + c) - d1_const(a.qn[dof[6 + c]]));
+    const D1 v3 = idt * (d1_var(x[9 + c], 9 + c) - d1_const(a.qn[dof[9 + c]]));
+    const D1 one = d1_const(1.0);
+    ur[c] = ((one - sD) * v0 + sD * v1) - ((one - tD) * v2 + tD * v3);
+  }
+  const D1 vn = ur[0] * nrm[0] + ur[1] * nrm[1] + ur[2] * nrm[2];
+  D1 u[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) u[c] = ur[c] - vn * nrm[c];
+  const D1 s2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  // |F_con| = -k_c e1 (e1 <= 0 in contact), derivative -k_c e2 grad D
+  const D1 fn = d1_apply(Dd, -kc * e1, -kc * e2);
+  D1 coef;
+  if (s2.v > 0.0) {
+    const double sg = sqrt(s2.v);
+    const D1 sig = d1_apply(s2, sg, 0.5 / sg);
+    const double ex = exp(-a.K2 * sg);
+    const double gam = 2.0 / (1.0 + ex) - 1.0;
+    const double dgam = 2.0 * a.K2 * ex / ((1.0 + ex) * (1.0 + ex));
+    // gamma(sigma) / sigma
+    const D1 gs = d1_apply(sig, gam / sg, (dgam * sg - gam) / (sg * sg));
+    coef = (-a.mu) * (fn * gs);
+  } else {
+    coef = (-0.5 * a.mu * a.K2) * fn;
+  }
+  D1 Fa[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) Fa[c] = coef * u[c];
+  const D1 one = d1_const(1.0);
+  const D1 wgt[4] = {one - sD, sD, tD - one, d1_const(0.0) - tD};
+#pragma unroll
+  for (int nd = 0; nd < 4; ++nd)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int i = 3 * nd + c;
+      if (a.fixed[dof[i]]) continue;
+      const D1 F = wgt[nd] * Fa[c];
+      atomicAdd(a.fc + dof[i], F.v);
+      for (int j = 0; j < 12; ++j) {
+        if (a.fixed[dof[j]] || F.g[j] == 0.0) continue;
+        const int r = dof[i] - d0, cc = dof[j] - d0;
+        atomicAdd(M + (size_t)r * n + cc, -F.g[j]);  // J = -dF/dq
+      }
+    }
 }
 
 // The rod's band (lower, symmetric) into the dense matrix of each contact

@@ -134,7 +134,8 @@ struct LineSearchArgs {
 struct ContactArgs {
   int ne, nd, nsys, table_mask, pair_cap;
   double inv_cell, delta, kc;
-  const double *q, *edge_h, *band;
+  double mu, K2, dt;  // edge-edge friction (mu = 0: none)
+  const double *q, *qn, *edge_h, *band;
   const int32_t *edge_a, *edge_b, *edge_sys, *edge_idx, *sys_kind, *sys_active, *dof_sys;
   const int32_t *sys_dof0, *sys_ndof, *contact_sys, *ls_action;
   const uint8_t *fixed;

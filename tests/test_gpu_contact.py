@@ -75,6 +75,29 @@ def test_contact_options_rejected():
     from paper_2311_18126_gb300 import System, DismechError
     desc, params, _ = workloads.coil(N=20)
     with pytest.raises(DismechError):
-        System(desc, dict(params, pair_mu=0.3))
+        System(desc, dict(params, pair_mu=-0.3))
     with pytest.raises(DismechError):
         System(desc, dict(params, ground=True))
+
+
+def test_coil_contact_with_friction_per_step():
+    """Friction at the closest points of touching edges (Eq. 12-13, pair_mu
+    > 0): per-step parity through the first contacts, line search on."""
+    desc, params = _short_coil()
+    params = dict(params, pair_mu=0.3, line_search=True)
+    gpu = _gpu(desc, params)
+    ora = OracleSystems(desc, params)
+    npr = desc["nodes_per_rod"]
+    touched = 0
+    for k in range(40):
+        gpu.step(1)
+        st = ora.step(1)
+        assert all(x[0] == 0 for x in st), st
+        qg, vg = gpu.get_state()
+        qo, vo = ora.get_state()
+        _assert_close(qg, qo, npr, 1.0, 1e-10)
+        touched += _oracle_active_pairs(ora, params) > 0
+        d1, beta = ora.get_frames()
+        gpu.set_state(qo, vo)
+        gpu.set_frames(d1, beta)
+    assert touched >= 5

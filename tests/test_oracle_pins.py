@@ -521,3 +521,31 @@ def test_imc_energy_branches():
     assert abs(float(E[1]) - (1.5 * delta) ** 2) < 1e-20
     assert abs(float(E[2]) - float(E[3])) <= 1e-6 * float(E[2])
     assert float(E[4]) <= 1e-12 * delta ** 2
+
+
+def test_edge_pair_friction_closed_form():
+    """Eq. 12-13 at touching edges: two crossing segments (a along x at
+    z = 0, b along y at height D < C - delta), b sliding fast along x.  The
+    net friction on b is -mu |F_con| x (gamma -> 1), +mu |F_con| x on a, split
+    equally between the nodes of each edge at a midpoint crossing, with
+    |F_con| = k_c 2 (C - D) on the quadratic branch of Eq. 10."""
+    from oracle.contact import _pair_friction
+    C, delta, kc, mu, nu, dt = 2e-3, 1e-4, 1e4, 0.3, 1e-3, 1e-3
+    D = 1.5e-3
+    x = torch.tensor([-1.0, 0, 0, 1.0, 0, 0, 0, -1.0, D, 0, 1.0, D], dtype=torch.float64) * \
+        torch.tensor([1e-2, 1, 1, 1e-2, 1, 1, 1, 1e-2, 1, 1, 1e-2, 1], dtype=torch.float64)
+    v = 0.5  # m/s along x for edge b: K2 |u| = 7500, gamma = 1 to rounding
+    xn = x.clone()
+    xn[6] -= v * dt
+    xn[9] -= v * dt
+    T = lambda z: torch.tensor(z, dtype=torch.float64)
+    F = _pair_friction(x, xn, T(C), T(delta), T(kc), T(mu), T(nu), T(dt))
+    Fn = kc * 2.0 * (C - D)
+    Fa = F[0:3] + F[3:6]
+    Fb = F[6:9] + F[9:12]
+    np.testing.assert_allclose(Fb.numpy(), [-mu * Fn, 0, 0], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(Fa.numpy(), [mu * Fn, 0, 0], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(F[0:3].numpy(), F[3:6].numpy(), rtol=1e-12, atol=1e-15)
+    # no friction without relative motion
+    F0 = _pair_friction(x, x + 1e-30, T(C), T(delta), T(kc), T(mu), T(nu), T(dt))
+    assert float(torch.abs(F0).max()) < 1e-20
