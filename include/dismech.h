@@ -291,6 +291,27 @@ dm_status dm_ws_prepare_batch(const float *features, const float *targets, const
 dm_status dm_ws_column_stats(const float *data, int64_t rows, int32_t cols, float *stats,
                              void *stream);
 
+/* Adjoint of one implicit step (no counterpart in the paper, whose
+ * calibration uses finite differences): gradients of a loss L(q_{n+1},
+ * qdot_{n+1}) with respect to the step's natural curvatures and its initial
+ * state, by J^T lambda = dL/dq_{n+1} + dL/dqdot_{n+1} / dt with the
+ * Jacobian of Eq. 16 at q_{n+1} (banded LDL^T, J symmetric), then
+ * dL/dkappabar = -lambda . df/dkappabar, dL/dq_n = -lambda . df/dq_n -
+ * dL/dqdot_{n+1}/dt, dL/dqdot_n = -lambda . df/dqdot_n.  The committed
+ * reference frames (d1, beta, tangents) of step n are held fixed.
+ * Precondition: the system holds the state of step n (dm_set_state and
+ * dm_set_frames to the values before the step) and q_next is the converged
+ * q_{n+1} of that step.  q_next, gq, gv (inputs) and gq0, gv0 (outputs) are
+ * in the dm_get_state layout; gkbar (output) holds 2 values per interior node
+ * in the dm_set_natural_curvature layout (all rods).  is_device: the
+ * pointers are device (1) or host (0) memory.  Single rods without contact
+ * only (DM_ERR_INVALID_ARG otherwise); fixed DOFs pass dL/dq_{n+1} through
+ * and get no velocity gradient.  Synchronises the stream; the state of step
+ * n is left in place. */
+dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq,
+                          const double *gv, double *gkbar, double *gq0, double *gv0,
+                          int32_t is_device);
+
 /* Edge-edge contact (Sec. III-B, Eq. 10-11; params.self_contact != 0):
  * number of edge pairs closer than C + delta at the last evaluated Newton
  * iterate, summed over the systems (0 without edge-edge contact, -1 on a

@@ -1,0 +1,74 @@
+"""Adjoint of one implicit step for the oracle (TEST INFRASTRUCTURE ONLY,
+see ``oracle/__init__.py``).
+
+The step solves f(q_{n+1}; q_n, qdot_n, kappabar) = 0 (Sec. III-C, Eq. 15)
+and sets qdot_{n+1} = (q_{n+1} - q_n)/dt.  For a loss L(q_{n+1}, qdot_{n+1}),
+by the implicit function theorem with J = df/dq_{n+1}:
+    J^T lambda = dL/dq_{n+1} + dL/dqdot_{n+1} / dt,
+    dL/dp = -lambda . df/dp  for p in (kappabar, q_n, qdot_n),
+plus -dL/dqdot_{n+1} / dt on q_n from the velocity update.  The committed
+reference frames are held fixed.  J is the oracle's autograd Jacobian;
+lambda . df/dp is a vector-Jacobian product of the oracle's residual.
+Fixed DOFs keep q_{n+1} = q_n: they pass dL/dq_{n+1} through and get no
+velocity gradient.
+"""
+import numpy as np
+import torch
+
+DT = torch.float64
+
+
+def step_adjoint(osys, q_next, gq, gv):
+    """osys holds step n (state and frames); q_next, gq, gv in the
+    get_state layout.  Returns (dL/dkappabar [slots, 2], dL/dq_n, dL/dqdot_n)
+    with the kappabar slots in the set_natural_curvature layout."""
+    dt = osys.dt
+    maps = osys._rod_maps()
+    n_slots = int(np.sum(osys.npr - 2))
+    gk = np.zeros((n_slots, 2))
+    gq0 = np.zeros(len(q_next))
+    gv0 = np.zeros(len(q_next))
+    slot0 = np.concatenate([[0], np.cumsum(osys.npr - 2)])
+    off = 0
+    for (r, si, idx) in maps:
+        s = osys.systems[si]
+        k = len(idx)
+        sl = slice(off, off + k)
+        off += k
+        ti = torch.as_tensor(idx)
+        q = s.q.clone()
+        q[ti] = torch.as_tensor(q_next[sl], dtype=DT)
+        g_q = torch.zeros(s.n, dtype=DT)
+        g_v = torch.zeros(s.n, dtype=DT)
+        g_q[ti] = torch.as_tensor(gq[sl], dtype=DT)
+        g_v[ti] = torch.as_tensor(gv[sl], dtype=DT)
+        _, _, J = osys.residual(s, q, s.q, s.v, need_jac=True)
+        gbar = torch.where(s.fixed, torch.zeros_like(g_q), g_q + g_v / dt)
+        lam = torch.as_tensor(np.linalg.solve(J.numpy().T, gbar.numpy()))
+        keep = (s.kbar1, s.kbar2)
+        kb1 = s.kbar1.clone().requires_grad_(True)
+        kb2 = s.kbar2.clone().requires_grad_(True)
+        qn = s.q.clone().requires_grad_(True)
+        vn = s.v.clone().requires_grad_(True)
+        s.kbar1, s.kbar2 = kb1, kb2
+        try:
+            f, _, _ = osys.residual(s, q, qn, vn, need_jac=False)
+            d1, d2, dqn, dvn = torch.autograd.grad(f, [kb1, kb2, qn, vn], grad_outputs=lam,
+                                                   allow_unused=True)
+        finally:
+            s.kbar1, s.kbar2 = keep
+        z = torch.zeros(s.n, dtype=DT)
+        dqn = z if dqn is None else dqn
+        dvn = z if dvn is None else dvn
+        a_q0 = torch.where(s.fixed, g_q, -dqn - g_v / dt)
+        a_v0 = torch.where(s.fixed, torch.zeros_like(g_v), -dvn)
+        gq0[sl] = a_q0[ti].numpy()
+        gv0[sl] = a_v0[ti].numpy()
+        for kk, gst in enumerate(s.st):
+            slot = osys.st_rodslot[gst]
+            if slot == -1:
+                continue
+            rr, j = slot
+            gk[slot0[rr] + j, 0] = -float(d1[kk]) if d1 is not None else 0.0
+            gk[slot0[rr] + j, 1] = -float(d2[kk]) if d2 is not None else 0.0
+    return gk, gq0, gv0

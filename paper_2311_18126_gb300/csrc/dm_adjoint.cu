@@ -1,0 +1,58 @@
+// Adjoint of one backward-Euler step of single rods (Sec. III-C, Eq. 15),
+// for gradients of a loss L(q_{n+1}, qdot_{n+1}) with respect to the
+// natural curvatures of the step and the state (q_n, qdot_n), the committed
+// reference frames held fixed.  With f(q_{n+1}; q_n, qdot_n, kappabar) = 0,
+// qdot_{n+1} = (q_{n+1} - q_n)/dt and J = df/dq_{n+1} (symmetric for rods):
+//   J lambda = gbar,  gbar = dL/dq_{n+1} + dL/dqdot_{n+1} / dt   (free DOFs)
+//   dL/dkappabar_c = -lambda . df/dkappabar_c =  EI/V lambda . grad kappa_c
+//   dL/dq_n        = -lambda . df/dq_n - dL/dqdot_{n+1} / dt
+//                  =  lambda (M/dt^2 + c_damp) - dL/dqdot_{n+1} / dt
+//   dL/dqdot_n     = -lambda . df/dqdot_n = lambda M / dt
+// Fixed DOFs keep q_{n+1} = q_n: dL/dq_n = dL/dq_{n+1} there, no velocity
+// gradient, and they do not enter the solve.
+#include "dm_internal.h"
+#include "dm_kernels.cuh"
+
+namespace dm {
+
+__global__ void k_adj_rhs(AdjArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.nd) return;
+  a.rhs[i] = a.fixed[i] ? 0.0 : a.gq[i] + a.gv[i] / a.dt;
+}
+
+__global__ void k_adj_state(AdjArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.nd) return;
+  if (a.fixed[i]) {
+    a.gq0[i] = a.gq[i];
+    a.gv0[i] = 0.0;
+    return;
+  }
+  const double m = a.mass[i], idt = 1.0 / a.dt;
+  a.gq0[i] = a.lam[i] * (m * idt * idt + a.damp[i]) - a.gv[i] * idt;
+  a.gv0[i] = a.lam[i] * m * idt;
+}
+
+__global__ void k_adj_kbar(AdjArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.nslots) return;
+  const int k = a.slot2st[t];
+  const int NS = a.ns;
+  int dof[11];
+#pragma unroll
+  for (int n = 0; n < 3; ++n)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dof[4 * n + c] = a.st_nd[n * NS + k] + c;
+  dof[3] = a.st_th[k];
+  dof[7] = a.st_th[NS + k];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    double v = 0.0;
+#pragma unroll
+    for (int p = 0; p < 11; ++p) v = fma(a.lam[dof[p]], a.dk[(size_t)(11 * c + p) * NS + k], v);
+    a.gkbar[2 * t + c] = a.st_kb[k] * v;
+  }
+}
+
+}  // namespace dm

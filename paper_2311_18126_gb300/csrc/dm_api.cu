@@ -110,6 +110,13 @@ struct Extra {
     int64_t *sys_dense0 = nullptr;
     unsigned long long *edge_key = nullptr;
   } cc;  // edge-edge contact
+  struct {
+    double *buf = nullptr;   // [6][nd]: lambda, rhs, gq, gv, gq0, gv0 (DOF order)
+    double *dk = nullptr;    // [22][Ns] curvature gradients
+    double *gk = nullptr;    // [2][slots]
+    double *stage = nullptr; // [n] layout staging
+    char *scratch = nullptr; // banded-solve scratch
+  } adj;  // step adjoint (allocated on first use)
   int n_fast = 0, n_slow = 0;   // general systems on the condensation / Schur path
   size_t border_smem = 0;
   int limb_nmax = 0, wpb_factor = 1, wpb_back = 1;  // limb kernels: rows, warps per block
@@ -224,6 +231,12 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     stth[k] = T.edge_thdof[T.st_edge[0][k]];
     stth[ns + k] = T.edge_thdof[T.st_edge[1][k]];
     stsg[k] = (T.st_sign[0][k] < 0 ? 1 : 0) | (T.st_sign[1][k] < 0 ? 2 : 0);
+  }
+  {
+    std::vector<int32_t> stnd(3 * ns);
+    for (int64_t k = 0; k < ns; ++k)
+      for (int n3 = 0; n3 < 3; ++n3) stnd[n3 * ns + k] = T.node_dof[T.st_node[n3][k]];
+    DM_TRY(upload(s, &d.st_nd, stnd));
   }
   DM_TRY(upload(s, &d.st_ed, sted));
   DM_TRY(upload(s, &d.st_th, stth));
@@ -984,6 +997,100 @@ dm_status dm_debug_copy(dm_system *sys, const char *name, double *out, int64_t n
   }
   DM_CK(cudaStreamSynchronize(sys->stream));
   DM_CK(cudaMemcpy(out, src, len * sizeof(double), cudaMemcpyDeviceToHost));
+  return DM_OK;
+}
+
+dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq,
+                          const double *gv, double *gkbar, double *gq0, double *gv0,
+                          int32_t is_device) {
+  auto *s = static_cast<dm_system_ext *>(sys);
+  if (!s || !q_next || !gq || !gv || !gkbar || !gq0 || !gv0) {
+    set_error("dm_step_adjoint: NULL argument");
+    return DM_ERR_INVALID_ARG;
+  }
+  const HostTopology &T = s->T;
+  for (int k = 0; k < T.n_systems; ++k)
+    if (T.sys_kind[k] != SOLVE_ROD_BAND) {
+      set_error("dm_step_adjoint: single rods without contact only (system " +
+                std::to_string(k) + ")");
+      return DM_ERR_INVALID_ARG;
+    }
+  DevArrays &d = s->d;
+  cudaStream_t st = s->stream;
+  const int nd = (int)T.n_dofs, ne = (int)T.n_edges, ns = (int)T.n_stencils, S = T.n_systems;
+  const int n = (int)T.layout2dof.size();
+  int nslots = 0;
+  for (int r = 0; r < T.n_rods; ++r) nslots += T.npr[r] - 2;
+  auto &A = s->x.adj;
+  if (!A.buf) {
+    DM_TRY(dalloc(s, &A.buf, 6 * (size_t)nd));
+    DM_TRY(dalloc(s, &A.dk, 22 * (size_t)std::max(ns, 1)));
+    DM_TRY(dalloc(s, &A.gk, 2 * (size_t)std::max(nslots, 1)));
+    DM_TRY(dalloc(s, &A.stage, 3 * (size_t)n));
+    DM_TRY(dalloc(s, &A.scratch, band_scratch_bytes(S, nd)));
+  }
+  double *lam = A.buf, *rhs = A.buf + nd, *bgq = A.buf + 2 * nd, *bgv = A.buf + 3 * nd;
+  double *bgq0 = A.buf + 4 * nd, *bgv0 = A.buf + 5 * nd;
+  // inputs in layout order -> DOF order
+  const double *src[3] = {q_next, gq, gv};
+  double *dst[3] = {d.q, bgq, bgv};
+  for (int k = 0; k < 3; ++k) {
+    const double *in = src[k];
+    if (!is_device) {
+      DM_CK(cudaMemcpyAsync(A.stage + (size_t)k * n, in, n * sizeof(double),
+                            cudaMemcpyHostToDevice, st));
+      in = A.stage + (size_t)k * n;
+    }
+    k_scatter_layout<<<blocks(n, 256), 256, 0, st>>>(n, d.layout2dof, in, dst[k]);
+  }
+  // every system active, evaluate J and the curvature gradients at q_next
+  std::vector<int32_t> ones(S, 1);
+  DM_CK(cudaMemcpyAsync(d.sys_active, ones.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  DM_CK(cudaMemsetAsync(d.sys_status, 0, S * sizeof(int32_t), st));
+  DM_CK(cudaMemsetAsync(d.sys_res, 0, S * sizeof(unsigned long long), st));
+  EdgeArgs ea{ne, d.q, d.edge_a, d.edge_b, d.edge_th, d.edge_sys, d.edge_EA, d.edge_lbar,
+              d.tn, d.d1n, d.sys_active, d.sys_status, d.ef, d.es, nullptr};
+  StencilArgs ka{ns, ne, d.q, d.ef, d.tn, d.st_ed, d.st_th, d.st_sg, d.st_sys, d.st_kb, d.st_kt,
+                 d.kbar, d.taubar, d.beta_n, d.sys_active, d.sys_status, d.beta_it, d.sg, d.sh,
+                 nullptr, A.dk};
+  RowArgs ra{};
+  ra.nd = nd; ra.ns = ns; ra.ne = ne; ra.dt = s->p.dt;
+  for (int c = 0; c < 3; ++c) ra.g[c] = s->p.g[c];
+  ra.eta = s->p.eta;
+  ra.q = d.q; ra.qn = d.qn; ra.vn = d.vn; ra.mass = d.mass; ra.rscale = d.rscale;
+  ra.damp = s->x.d_damp; ra.fixed = d.fixed; ra.dof_sys = s->x.d_dof_sys;
+  ra.sys_dof0 = d.sys_dof0; ra.sys_ndof = d.sys_ndof; ra.sys_st0 = d.sys_st0;
+  ra.sys_edge0 = d.sys_edge0; ra.sys_active = d.sys_active; ra.sys_kind = s->x.d_sys_kind;
+  ra.sg = d.sg; ra.sh = d.sh; ra.es = d.es; ra.f = d.f; ra.band = d.band; ra.sys_res = d.sys_res;
+  k_edge<<<blocks(ne, 256), 256, 0, st>>>(ea);
+  if (ns > 0) k_stencil<<<blocks(ns, 128), 128, 0, st>>>(ka);
+  k_rows_rod<<<blocks(nd, 256), 256, 0, st>>>(ra);
+  AdjArgs aa{nd, ns, nslots, s->p.dt, lam, bgq, bgv, d.mass, s->x.d_damp, A.dk, d.st_kb,
+             d.fixed, d.st_nd, d.st_th, s->x.d_slot2st, rhs, bgq0, bgv0, A.gk};
+  k_adj_rhs<<<blocks(nd, 256), 256, 0, st>>>(aa);
+  DM_CK(cudaGetLastError());
+  // J lambda = gbar with the step's banded LDL^T (J is symmetric for rods)
+  dm_status bs = run_band_solve(S, T.sys_dof0.data(), T.sys_ndof.data(), nd, d.band, rhs, lam,
+                                A.scratch, st);
+  // the system stays at step n whatever happened
+  DM_CK(cudaMemcpyAsync(d.q, d.qn, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (bs != DM_OK) return bs;
+  k_adj_state<<<blocks(nd, 256), 256, 0, st>>>(aa);
+  if (nslots > 0) k_adj_kbar<<<blocks(nslots, 128), 128, 0, st>>>(aa);
+  // outputs: state gradients in layout order, curvature gradients by slot
+  double *outs[2] = {gq0, gv0};
+  const double *ins[2] = {bgq0, bgv0};
+  for (int k = 0; k < 2; ++k) {
+    double *o = is_device ? outs[k] : A.stage + (size_t)k * n;
+    k_gather_layout<<<blocks(n, 256), 256, 0, st>>>(n, d.layout2dof, ins[k], o);
+    if (!is_device)
+      DM_CK(cudaMemcpyAsync(outs[k], o, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  if (nslots > 0)
+    DM_CK(cudaMemcpyAsync(gkbar, A.gk, 2 * (size_t)nslots * sizeof(double),
+                          is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  DM_CK(cudaGetLastError());
+  DM_CK(cudaStreamSynchronize(st));
   return DM_OK;
 }
 

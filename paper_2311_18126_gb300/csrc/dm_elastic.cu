@@ -372,6 +372,32 @@ __global__ void __launch_bounds__(128) k_stencil(StencilArgs a) {
         if (i >= 3 && i < 6 && j >= 3 && j < 6) v -= EB * Hb[up<3>(i - 3, j - 3)];
         h[up<8>(i, j)] += v;
       }
+    if (a.dk) {
+      // gradients of kappa1 and kappa2 as functions of the 11 DOFs (the
+      // same holonomy correction as the energy gradient), for the adjoint:
+      // d(grad E)/d(kappabar_c) = -EI/V grad kappa_c
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const double *gc = c == 0 ? g1 : g2;
+        double e8[8];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          e8[i] = gc[i] - gc[6] * cmp(ga, i);
+          e8[3 + i] = gc[3 + i] - gc[7] * cmp(gb, i);
+        }
+        e8[6] = gc[6];
+        e8[7] = gc[7];
+        double *o = a.dk + (size_t)(11 * c) * NS + k;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          o[(size_t)i * NS] = -e8[i];
+          o[(size_t)(4 + i) * NS] = e8[i] - e8[3 + i];
+          o[(size_t)(8 + i) * NS] = e8[3 + i];
+        }
+        o[(size_t)3 * NS] = sa * e8[6];
+        o[(size_t)7 * NS] = sb * e8[7];
+      }
+    }
   }
 
   // map (e_a, e_b, A, B) -> 11 stencil DOFs [x0, th_a, x1, th_b, x2]:

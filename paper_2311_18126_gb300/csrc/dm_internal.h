@@ -173,6 +173,13 @@ struct Params {
 // Learned warm start (dm_warmstart.cu).
 struct WarmStart;
 void ws_free(WarmStart *w);
+// Batched banded solve (dm_band_solve.cu): scratch size and the solve with
+// host arrays of system offsets/sizes.
+size_t band_scratch_bytes(int32_t nsys, int64_t ntot);
+dm_status run_band_solve(int32_t nsys, const int32_t *dof0, const int32_t *ndof, int64_t ntot,
+                         const double *band, const double *rhs, double *x, char *scr,
+                         cudaStream_t st);
+
 bool ws_active(const dm_system *s);  // a network is attached
 // Evaluates the network on the committed state.  defer = false: the guess
 // replaces the extrapolation in q; defer = true: it is kept for ws_inject.

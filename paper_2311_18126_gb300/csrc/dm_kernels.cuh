@@ -24,6 +24,7 @@ struct StencilArgs {
   int32_t *sys_status;
   double *beta_it, *sg, *sh;
   unsigned long long *units;
+  double *dk;  // NULL, or [22][Ns]: gradients of kappa1, kappa2 (11 stencil DOFs each)
 };
 
 struct RowArgs {
@@ -162,6 +163,20 @@ __global__ void k_lu_diag(ContactArgs a, int c, int k);
 __global__ void k_lu_trsm(ContactArgs a, int c, int k);
 __global__ void k_lu_gemm(ContactArgs a, int c, int k);
 __global__ void k_cc_subst(ContactArgs a, SolveArgs v);
+
+// Adjoint of one implicit step (single rods): right-hand side, state and
+// natural-curvature gradients.
+struct AdjArgs {
+  int nd, ns, nslots;
+  double dt;
+  const double *lam, *gq, *gv, *mass, *damp, *dk, *st_kb;
+  const uint8_t *fixed;
+  const int32_t *st_nd, *st_th, *slot2st;
+  double *rhs, *gq0, *gv0, *gkbar;
+};
+__global__ void k_adj_rhs(AdjArgs a);
+__global__ void k_adj_state(AdjArgs a);
+__global__ void k_adj_kbar(AdjArgs a);
 
 __global__ void k_ls_merit(LineSearchArgs a);
 __global__ void k_ls_decide(LineSearchArgs a);

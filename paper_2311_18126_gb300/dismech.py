@@ -141,6 +141,8 @@ def load_library(path=LIB_PATH):
     lib.dm_ws_prepare_batch.restype = C.c_int
     lib.dm_ws_column_stats.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]
     lib.dm_ws_column_stats.restype = C.c_int
+    lib.dm_step_adjoint.argtypes = [H] + [C.c_void_p] * 6 + [C.c_int32]
+    lib.dm_step_adjoint.restype = C.c_int
     lib.dm_contact_pairs.argtypes = [H]
     lib.dm_contact_pairs.restype = C.c_int64
     lib.dm_last_error.argtypes = []
@@ -243,6 +245,7 @@ class System:
         self.n_stencils = lib.dm_num_stencils(h)
         self.n_edges = lib.dm_num_edges(h)
         self.n_rods = d.n_rods
+        self._npr = np.asarray(npr, np.int64)
         self.stats = StepStats()
         self._iters = np.zeros(self.n_systems, np.int32)
         self._res = np.zeros(self.n_systems, np.float64)
@@ -341,6 +344,21 @@ class System:
         beta = np.ascontiguousarray(np.asarray(beta, np.float64))
         _check(self._lib.dm_set_frames(self._h, _ptr(d1, C.c_double), _ptr(beta, C.c_double)))
 
+
+    def step_adjoint(self, q_next, gq, gv):
+        """Adjoint of the step from the current state (step n) to q_next:
+        returns (dL/dkappabar [slots, 2], dL/dq_n, dL/dqdot_n) for the loss
+        gradients gq = dL/dq_{n+1}, gv = dL/dqdot_{n+1} (host numpy)."""
+        f = lambda a: np.ascontiguousarray(np.asarray(a, np.float64))
+        q_next, gq, gv = f(q_next), f(gq), f(gv)
+        nslots = int(np.sum(self._npr - 2))
+        gk = np.zeros((max(nslots, 1), 2))
+        gq0 = np.zeros(self.n_state)
+        gv0 = np.zeros(self.n_state)
+        ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+        _check(self._lib.dm_step_adjoint(self._h, ptr(q_next), ptr(gq), ptr(gv), ptr(gk),
+                                         ptr(gq0), ptr(gv0), 0))
+        return gk[:nslots], gq0, gv0
 
     def contact_pairs(self):
         """Edge pairs in contact at the last evaluated Newton iterate."""

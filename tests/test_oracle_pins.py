@@ -549,3 +549,60 @@ def test_edge_pair_friction_closed_form():
     # no friction without relative motion
     F0 = _pair_friction(x, x + 1e-30, T(C), T(delta), T(kc), T(mu), T(nu), T(dt))
     assert float(torch.abs(F0).max()) < 1e-20
+
+
+def test_step_adjoint_matches_central_differences():
+    """The oracle's one-step adjoint (implicit function theorem) against
+    central differences of the oracle's own step, for natural curvatures and
+    the initial state, the committed frames (directors, reference twist and
+    tangents) held fixed: every evaluation restarts from the same step-n
+    frames."""
+    import workloads
+    from oracle import OracleSystems
+    from oracle.adjoint import step_adjoint
+    desc, params = workloads.cantilever(N=10)
+    o = OracleSystems(desc, params)
+    rng = np.random.default_rng(4)
+    kb0 = rng.uniform(-0.02, 0.02, size=(8, 2))
+    o.set_natural_curvature(0, 1, kb0)
+    for _ in range(3):
+        o.step(1)
+    q0, v0 = o.get_state()
+    d1, beta = o.get_frames()
+    tn = [s.tn.clone() for s in o.systems]  # committed tangents, held fixed too
+    wq = rng.normal(size=len(q0))
+    wv = rng.normal(size=len(q0))
+
+    def loss(kb, q, v):
+        o.set_state(q, v)
+        o.set_frames(d1, beta)
+        for s, t in zip(o.systems, tn):
+            s.tn = t.clone()
+        o.set_natural_curvature(0, 1, kb)
+        out = o.step(1)
+        assert out[0][0] == 0
+        q1, v1 = o.get_state()
+        return float(wq @ q1 + wv @ v1), q1
+
+    _, q1 = loss(kb0, q0, v0)
+    o.set_state(q0, v0)
+    o.set_frames(d1, beta)
+    o.set_natural_curvature(0, 1, kb0)
+    gk, gq0, gv0 = step_adjoint(o, q1, wq, wv)
+    h = 1e-6
+    for (i, c) in [(0, 0), (3, 1), (7, 0)]:
+        kp = kb0.copy(); kp[i, c] += h
+        km = kb0.copy(); km[i, c] -= h
+        fd = (loss(kp, q0, v0)[0] - loss(km, q0, v0)[0]) / (2 * h)
+        assert abs(fd - gk[i, c]) <= 1e-5 * max(1.0, abs(fd)), (i, c, fd, gk[i, c])
+    for j in [9, 14, 30]:  # free DOFs (positions and a twist angle)
+        for vec, g in ((0, gq0), (1, gv0)):
+            qp, vp = q0.copy(), v0.copy()
+            qm, vm = q0.copy(), v0.copy()
+            hh = 1e-7
+            if vec == 0:
+                qp[j] += hh; qm[j] -= hh
+            else:
+                vp[j] += hh; vm[j] -= hh
+            fd = (loss(kb0, qp, vp)[0] - loss(kb0, qm, vm)[0]) / (2 * hh)
+            assert abs(fd - g[j]) <= 1e-4 * max(1.0, abs(fd)), (vec, j, fd, g[j])
