@@ -246,6 +246,10 @@ class System:
         self.n_edges = lib.dm_num_edges(h)
         self.n_rods = d.n_rods
         self._npr = np.asarray(npr, np.int64)
+        self.dt = float(p.dt)
+        fx = desc.get("fixed")
+        self._fixed = (np.zeros(int(np.sum(4 * self._npr - 1)), bool) if fx is None
+                       else np.asarray(fx).astype(bool).reshape(-1))
         self.stats = StepStats()
         self._iters = np.zeros(self.n_systems, np.int32)
         self._res = np.zeros(self.n_systems, np.float64)
@@ -359,6 +363,10 @@ class System:
         _check(self._lib.dm_step_adjoint(self._h, ptr(q_next), ptr(gq), ptr(gv), ptr(gk),
                                          ptr(gq0), ptr(gv0), 0))
         return gk[:nslots], gq0, gv0
+
+    def fixed_mask(self):
+        """Fixed-DOF mask in the dm_get_state layout (from the descriptor)."""
+        return self._fixed.copy()
 
     def contact_pairs(self):
         """Edge pairs in contact at the last evaluated Newton iterate."""
