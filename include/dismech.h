@@ -295,7 +295,9 @@ dm_status dm_ws_column_stats(const float *data, int64_t rows, int32_t cols, floa
  * calibration uses finite differences): gradients of a loss L(q_{n+1},
  * qdot_{n+1}) with respect to the step's natural curvatures and its initial
  * state, by J^T lambda = dL/dq_{n+1} + dL/dqdot_{n+1} / dt with the
- * Jacobian of Eq. 16 at q_{n+1} (banded LDL^T, J symmetric), then
+ * Jacobian of Eq. 16 at q_{n+1} (single rods: banded LDL^T, J symmetric;
+ * rod networks and rods on the ground: the condensation solve applied to
+ * J^T, which friction makes nonsymmetric), then
  * dL/dkappabar = -lambda . df/dkappabar, dL/dq_n = -lambda . df/dq_n -
  * dL/dqdot_{n+1}/dt, dL/dqdot_n = -lambda . df/dqdot_n.  The committed
  * reference frames (d1, beta, tangents) of step n are held fixed.
@@ -303,11 +305,16 @@ dm_status dm_ws_column_stats(const float *data, int64_t rows, int32_t cols, floa
  * dm_set_frames to the values before the step) and q_next is the converged
  * q_{n+1} of that step.  q_next, gq, gv (inputs) and gq0, gv0 (outputs) are
  * in the dm_get_state layout; gkbar (output) holds 2 values per interior node
- * in the dm_set_natural_curvature layout (all rods).  is_device: the
- * pointers are device (1) or host (0) memory.  Single rods without contact
- * only (DM_ERR_INVALID_ARG otherwise); fixed DOFs pass dL/dq_{n+1} through
- * and get no velocity gradient.  Synchronises the stream; the state of step
- * n is left in place. */
+ * in the dm_set_natural_curvature layout (all rods).  A joint node appears
+ * once per rod in the layout: its loss gradients are summed over the copies
+ * and its output gradients are written to its first copy (zeros in the
+ * others), so that outputs can be fed back as inputs.  is_device: the
+ * pointers are device (1) or host (0) memory.  Systems with edge-edge
+ * contact, and networks with a limb jointed at both ends, are rejected
+ * (DM_ERR_INVALID_ARG); the friction force's dependence on x_n enters
+ * dL/dq_n; fixed DOFs pass dL/dq_{n+1} through and get no velocity
+ * gradient.  Synchronises the stream; the state of step n is left in
+ * place. */
 dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq,
                           const double *gv, double *gkbar, double *gq0, double *gv0,
                           int32_t is_device);

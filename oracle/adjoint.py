@@ -21,7 +21,10 @@ DT = torch.float64
 def step_adjoint(osys, q_next, gq, gv):
     """osys holds step n (state and frames); q_next, gq, gv in the
     get_state layout.  Returns (dL/dkappabar [slots, 2], dL/dq_n, dL/dqdot_n)
-    with the kappabar slots in the set_natural_curvature layout."""
+    with the kappabar slots in the set_natural_curvature layout.  A joint
+    node appears once per rod in the layout: its loss gradients are summed
+    over the copies and its output gradients go to its first copy (zeros in
+    the others)."""
     dt = osys.dt
     maps = osys._rod_maps()
     n_slots = int(np.sum(osys.npr - 2))
@@ -29,19 +32,27 @@ def step_adjoint(osys, q_next, gq, gv):
     gq0 = np.zeros(len(q_next))
     gv0 = np.zeros(len(q_next))
     slot0 = np.concatenate([[0], np.cumsum(osys.npr - 2)])
+    # layout slices per system
+    offs = {}
     off = 0
     for (r, si, idx) in maps:
+        offs.setdefault(si, []).append((off, idx))
+        off += len(idx)
+    for si, parts in offs.items():
         s = osys.systems[si]
-        k = len(idx)
-        sl = slice(off, off + k)
-        off += k
-        ti = torch.as_tensor(idx)
         q = s.q.clone()
-        q[ti] = torch.as_tensor(q_next[sl], dtype=DT)
         g_q = torch.zeros(s.n, dtype=DT)
         g_v = torch.zeros(s.n, dtype=DT)
-        g_q[ti] = torch.as_tensor(gq[sl], dtype=DT)
-        g_v[ti] = torch.as_tensor(gv[sl], dtype=DT)
+        seen = np.zeros(s.n, bool)
+        for (o, idx) in parts:
+            k = len(idx)
+            new = ~seen[idx]
+            ti = torch.as_tensor(idx[new])
+            q[ti] = torch.as_tensor(q_next[o:o + k][new], dtype=DT)
+            # a loss on a shared node counts once per copy in the layout
+            g_q.index_add_(0, torch.as_tensor(idx), torch.as_tensor(gq[o:o + k], dtype=DT))
+            g_v.index_add_(0, torch.as_tensor(idx), torch.as_tensor(gv[o:o + k], dtype=DT))
+            seen[idx] = True
         _, _, J = osys.residual(s, q, s.q, s.v, need_jac=True)
         gbar = torch.where(s.fixed, torch.zeros_like(g_q), g_q + g_v / dt)
         lam = torch.as_tensor(np.linalg.solve(J.numpy().T, gbar.numpy()))
@@ -62,8 +73,14 @@ def step_adjoint(osys, q_next, gq, gv):
         dvn = z if dvn is None else dvn
         a_q0 = torch.where(s.fixed, g_q, -dqn - g_v / dt)
         a_v0 = torch.where(s.fixed, torch.zeros_like(g_v), -dvn)
-        gq0[sl] = a_q0[ti].numpy()
-        gv0[sl] = a_v0[ti].numpy()
+        done = np.zeros(s.n, bool)
+        for (o, idx) in parts:
+            k = len(idx)
+            ti = torch.as_tensor(idx)
+            firstc = ~done[idx]
+            gq0[o:o + k] = np.where(firstc, a_q0[ti].numpy(), 0.0)
+            gv0[o:o + k] = np.where(firstc, a_v0[ti].numpy(), 0.0)
+            done[idx] = True
         for kk, gst in enumerate(s.st):
             slot = osys.st_rodslot[gst]
             if slot == -1:

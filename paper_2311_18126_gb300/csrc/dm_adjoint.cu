@@ -18,7 +18,7 @@ namespace dm {
 __global__ void k_adj_rhs(AdjArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.nd) return;
-  a.rhs[i] = a.fixed[i] ? 0.0 : a.gq[i] + a.gv[i] / a.dt;
+  a.rhs[i] = a.fixed[i] ? 0.0 : a.rhs_sign * (a.gq[i] + a.gv[i] / a.dt);
 }
 
 __global__ void k_adj_state(AdjArgs a) {
@@ -30,8 +30,54 @@ __global__ void k_adj_state(AdjArgs a) {
     return;
   }
   const double m = a.mass[i], idt = 1.0 / a.dt;
-  a.gq0[i] = a.lam[i] * (m * idt * idt + a.damp[i]) - a.gv[i] * idt;
+  double g = a.lam[i] * (m * idt * idt + a.damp[i]) - a.gv[i] * idt;
+  if (a.nt) {
+    // ground friction depends on x - x_n: dL/dx_n += lambda^T J_plane
+    // (the in-plane block of -dF/dx, node terms rows 0-1, column c)
+    const int c = a.dof_comp[i];
+    if (c < 2) {
+      const int v = a.dof_node[i], d = a.node_dof[v], NN = a.nn;
+      g = fma(a.lam[d], a.nt[(3 + c) * NN + v], g);
+      g = fma(a.lam[d + 1], a.nt[(6 + c) * NN + v], g);
+    }
+  }
+  a.gq0[i] = g;
   a.gv0[i] = a.lam[i] * m * idt;
+}
+
+// dst = transposed condensation-path storage: per limb the band
+// B'[p][k + 10] = B[p + k][10 - k], C' = R^T, R' = C^T (one thread per entry)
+__global__ void k_gen_transpose(SolveGenArgs a, const double *src, double *dst) {
+  const int L = blockIdx.y;
+  if (L >= a.nlimb || !a.gs_fast[a.lb_gsys[L]]) return;
+  const int n = a.lb_n[L], m = a.lb_m[L], nbc = a.lb_nbc[L];
+  const double *B = src + a.lb_band[L];
+  double *Bt = dst + a.lb_band[L];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * 21; e += gridDim.x * blockDim.x) {
+    const int p = e / 21, k = e - p * 21 - 10;
+    Bt[e] = (p + k >= 0 && p + k < n) ? B[(size_t)(p + k) * 21 + (10 - k)] : 0.0;
+  }
+  if (blockIdx.x == 0) {
+    const double *C = src + a.lb_C[L], *R = src + a.lb_R[L];
+    double *Ct = dst + a.lb_C[L], *Rt = dst + a.lb_R[L];
+    for (int e = threadIdx.x; e < m * nbc; e += blockDim.x) {
+      const int r = e / nbc, b = e - r * nbc;
+      Ct[e] = R[(size_t)b * m + r];
+      Rt[(size_t)b * m + r] = C[e];
+    }
+  }
+}
+
+__global__ void k_gen_transpose_border(SolveGenArgs a, const double *src, double *dst) {
+  const int w = blockIdx.x;
+  if (w >= a.ngen || !a.gs_fast[w]) return;
+  const int nB = a.gs_nB[w];
+  const double *J = src + a.gs_JBB[w];
+  double *Jt = dst + a.gs_JBB[w];
+  for (int e = threadIdx.x; e < nB * nB; e += blockDim.x) {
+    const int i = e / nB, j = e - i * nB;
+    Jt[(size_t)j * nB + i] = J[e];
+  }
 }
 
 __global__ void k_adj_kbar(AdjArgs a) {

@@ -67,6 +67,17 @@ __global__ void k_scatter_layout(int n, const int32_t *map, const double *src, d
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[map[i]] = src[i];
 }
+// layout -> DOF order summing the copies of a shared (joint) node
+__global__ void k_scatter_add_layout(int n, const int32_t *map, const double *src, double *dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(dst + map[i], src[i]);
+}
+// DOF -> layout order with a shared node's value in its first copy only
+__global__ void k_gather_layout_first(int n, const int32_t *map, const uint8_t *first,
+                                      const double *src, double *dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = first[i] ? src[map[i]] : 0.0;
+}
 __global__ void k_scatter_kbar(int n, const int32_t *slot2st, int slot0, int ns,
                                const double *in, double *kbar) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -116,6 +127,10 @@ struct Extra {
     double *gk = nullptr;    // [2][slots]
     double *stage = nullptr; // [n] layout staging
     char *scratch = nullptr; // banded-solve scratch
+    double *gen2 = nullptr;  // transposed general-path storage
+    uint8_t *first = nullptr; // first copy of each DOF in the layout
+    int32_t *ints = nullptr; // bookkeeping of the transposed solve
+    unsigned long long *res = nullptr;
   } adj;  // step adjoint (allocated on first use)
   int n_fast = 0, n_slow = 0;   // general systems on the condensation / Schur path
   size_t border_smem = 0;
@@ -1009,31 +1024,59 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
     return DM_ERR_INVALID_ARG;
   }
   const HostTopology &T = s->T;
-  for (int k = 0; k < T.n_systems; ++k)
-    if (T.sys_kind[k] != SOLVE_ROD_BAND) {
-      set_error("dm_step_adjoint: single rods without contact only (system " +
-                std::to_string(k) + ")");
+  std::vector<int32_t> rod_d0, rod_n;
+  for (int k = 0; k < T.n_systems; ++k) {
+    if (T.sys_kind[k] == SOLVE_ROD_BAND) {
+      rod_d0.push_back(T.sys_dof0[k]);
+      rod_n.push_back(T.sys_ndof[k]);
+    } else if (T.sys_kind[k] != SOLVE_GENERAL) {
+      set_error("dm_step_adjoint: systems with edge-edge contact are not supported");
+      return DM_ERR_INVALID_ARG;
+    }
+  }
+  for (size_t w = 0; w < T.gen_sys.size(); ++w)
+    if (!T.gs_fast[w]) {
+      set_error("dm_step_adjoint: general system " + std::to_string(T.gen_sys[w]) +
+                " is not on the condensation path (a limb jointed at both ends)");
       return DM_ERR_INVALID_ARG;
     }
   DevArrays &d = s->d;
   cudaStream_t st = s->stream;
   const int nd = (int)T.n_dofs, ne = (int)T.n_edges, ns = (int)T.n_stencils, S = T.n_systems;
+  const int nn = (int)T.n_nodes, ngen = (int)T.gen_sys.size();
   const int n = (int)T.layout2dof.size();
   int nslots = 0;
   for (int r = 0; r < T.n_rods; ++r) nslots += T.npr[r] - 2;
   auto &A = s->x.adj;
   if (!A.buf) {
-    DM_TRY(dalloc(s, &A.buf, 6 * (size_t)nd));
+    DM_TRY(dalloc(s, &A.buf, 7 * (size_t)nd));
     DM_TRY(dalloc(s, &A.dk, 22 * (size_t)std::max(ns, 1)));
     DM_TRY(dalloc(s, &A.gk, 2 * (size_t)std::max(nslots, 1)));
     DM_TRY(dalloc(s, &A.stage, 3 * (size_t)n));
-    DM_TRY(dalloc(s, &A.scratch, band_scratch_bytes(S, nd)));
+    if (!rod_d0.empty())
+      DM_TRY(dalloc(s, &A.scratch, band_scratch_bytes((int32_t)rod_d0.size(), nd)));
+    if (ngen > 0) {
+      DM_TRY(dalloc(s, &A.gen2, (size_t)T.gen_doubles));
+      DM_TRY(dalloc(s, &A.ints, 6 * (size_t)S + 2 * (size_t)ngen + 8));
+      DM_TRY(dalloc(s, &A.res, (size_t)S));
+    }
   }
   double *lam = A.buf, *rhs = A.buf + nd, *bgq = A.buf + 2 * nd, *bgv = A.buf + 3 * nd;
-  double *bgq0 = A.buf + 4 * nd, *bgv0 = A.buf + 5 * nd;
-  // inputs in layout order -> DOF order
+  double *bgq0 = A.buf + 4 * nd, *bgv0 = A.buf + 5 * nd, *nrhs = A.buf + 6 * nd;
+  if (!A.first) {
+    std::vector<uint8_t> first(n, 0), seen(nd, 0);
+    for (int i = 0; i < n; ++i)
+      if (!seen[T.layout2dof[i]]) {
+        first[i] = 1;
+        seen[T.layout2dof[i]] = 1;
+      }
+    DM_TRY(upload(s, &A.first, first));
+  }
+  // inputs in layout order -> DOF order (loss gradients summed over the
+  // copies of a shared node)
   const double *src[3] = {q_next, gq, gv};
   double *dst[3] = {d.q, bgq, bgv};
+  DM_CK(cudaMemsetAsync(bgq, 0, 2 * (size_t)nd * sizeof(double), st));
   for (int k = 0; k < 3; ++k) {
     const double *in = src[k];
     if (!is_device) {
@@ -1041,9 +1084,12 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
                             cudaMemcpyHostToDevice, st));
       in = A.stage + (size_t)k * n;
     }
-    k_scatter_layout<<<blocks(n, 256), 256, 0, st>>>(n, d.layout2dof, in, dst[k]);
+    if (k == 0)
+      k_scatter_layout<<<blocks(n, 256), 256, 0, st>>>(n, d.layout2dof, in, dst[k]);
+    else
+      k_scatter_add_layout<<<blocks(n, 256), 256, 0, st>>>(n, d.layout2dof, in, dst[k]);
   }
-  // every system active, evaluate J and the curvature gradients at q_next
+  // every system active; J and the curvature gradients at q_next
   std::vector<int32_t> ones(S, 1);
   DM_CK(cudaMemcpyAsync(d.sys_active, ones.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   DM_CK(cudaMemsetAsync(d.sys_status, 0, S * sizeof(int32_t), st));
@@ -1053,25 +1099,94 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
   StencilArgs ka{ns, ne, d.q, d.ef, d.tn, d.st_ed, d.st_th, d.st_sg, d.st_sys, d.st_kb, d.st_kt,
                  d.kbar, d.taubar, d.beta_n, d.sys_active, d.sys_status, d.beta_it, d.sg, d.sh,
                  nullptr, A.dk};
-  RowArgs ra{};
-  ra.nd = nd; ra.ns = ns; ra.ne = ne; ra.dt = s->p.dt;
-  for (int c = 0; c < 3; ++c) ra.g[c] = s->p.g[c];
-  ra.eta = s->p.eta;
-  ra.q = d.q; ra.qn = d.qn; ra.vn = d.vn; ra.mass = d.mass; ra.rscale = d.rscale;
-  ra.damp = s->x.d_damp; ra.fixed = d.fixed; ra.dof_sys = s->x.d_dof_sys;
-  ra.sys_dof0 = d.sys_dof0; ra.sys_ndof = d.sys_ndof; ra.sys_st0 = d.sys_st0;
-  ra.sys_edge0 = d.sys_edge0; ra.sys_active = d.sys_active; ra.sys_kind = s->x.d_sys_kind;
-  ra.sg = d.sg; ra.sh = d.sh; ra.es = d.es; ra.f = d.f; ra.band = d.band; ra.sys_res = d.sys_res;
   k_edge<<<blocks(ne, 256), 256, 0, st>>>(ea);
+  if (T.ground) {
+    NodeArgs na{nn, s->p.dt, s->prm.ground_z, s->prm.delta, s->prm.slip_nu, d.q, d.qn,
+                d.node_dof_arr, d.node_sys, d.node_h, d.node_mu, d.node_kc, d.sys_active, d.nt};
+    k_nodes<<<blocks(nn, 256), 256, 0, st>>>(na);
+  }
   if (ns > 0) k_stencil<<<blocks(ns, 128), 128, 0, st>>>(ka);
-  k_rows_rod<<<blocks(nd, 256), 256, 0, st>>>(ra);
+  if (!rod_d0.empty()) {
+    RowArgs ra{};
+    ra.nd = nd; ra.ns = ns; ra.ne = ne; ra.dt = s->p.dt;
+    for (int c = 0; c < 3; ++c) ra.g[c] = s->p.g[c];
+    ra.eta = s->p.eta;
+    ra.q = d.q; ra.qn = d.qn; ra.vn = d.vn; ra.mass = d.mass; ra.rscale = d.rscale;
+    ra.damp = s->x.d_damp; ra.fixed = d.fixed; ra.dof_sys = s->x.d_dof_sys;
+    ra.sys_dof0 = d.sys_dof0; ra.sys_ndof = d.sys_ndof; ra.sys_st0 = d.sys_st0;
+    ra.sys_edge0 = d.sys_edge0; ra.sys_active = d.sys_active; ra.sys_kind = s->x.d_sys_kind;
+    ra.sg = d.sg; ra.sh = d.sh; ra.es = d.es; ra.f = d.f; ra.band = d.band; ra.sys_res = d.sys_res;
+    k_rows_rod<<<blocks(nd, 256), 256, 0, st>>>(ra);
+  }
+  if (ngen > 0) {
+    DM_CK(cudaMemsetAsync(d.gen, 0, T.gen_doubles * sizeof(double), st));
+    AsmArgs aa{(int)T.asm_target.size(), d.asm_target, d.asm_ptr, d.asm_src, d.sh, d.es, d.nt,
+               d.dconst, d.gen, d.asm_sys, d.sys_active, nullptr};
+    if (aa.ntarget > 0) k_assemble_gen<<<blocks(aa.ntarget, 256), 256, 0, st>>>(aa);
+  }
   AdjArgs aa{nd, ns, nslots, s->p.dt, lam, bgq, bgv, d.mass, s->x.d_damp, A.dk, d.st_kb,
-             d.fixed, d.st_nd, d.st_th, s->x.d_slot2st, rhs, bgq0, bgv0, A.gk};
+             d.fixed, d.st_nd, d.st_th, s->x.d_slot2st, rhs, bgq0, bgv0, A.gk,
+             nn, T.ground ? d.nt : nullptr, d.dof_node, d.dof_comp, d.node_dof_arr, 1.0};
   k_adj_rhs<<<blocks(nd, 256), 256, 0, st>>>(aa);
   DM_CK(cudaGetLastError());
-  // J lambda = gbar with the step's banded LDL^T (J is symmetric for rods)
-  dm_status bs = run_band_solve(S, T.sys_dof0.data(), T.sys_ndof.data(), nd, d.band, rhs, lam,
-                                A.scratch, st);
+  dm_status bs = DM_OK;
+  if (!rod_d0.empty()) {
+    // rods: J lambda = gbar by the banded LDL^T (J symmetric); zeroes lambda
+    bs = run_band_solve((int32_t)rod_d0.size(), rod_d0.data(), rod_n.data(), nd, d.band, rhs,
+                        lam, A.scratch, st);
+  } else {
+    DM_CK(cudaMemsetAsync(lam, 0, nd * sizeof(double), st));
+  }
+  if (bs == DM_OK && ngen > 0) {
+    // networks: J^T lambda = gbar by the condensation kernels on the
+    // transposed storage (they solve J dq = -f and add dq to q)
+    AdjArgs an = aa;
+    an.rhs = nrhs;
+    an.rhs_sign = -1.0;
+    k_adj_rhs<<<blocks(nd, 256), 256, 0, st>>>(an);
+    int32_t *act = A.ints, *its = act + S, *sts = its + S, *ctl = sts + S;
+    int32_t *go = ctl + 8, *bad = go + ngen;
+    DM_CK(cudaMemcpyAsync(act, ones.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    DM_CK(cudaMemsetAsync(its, 0, 2 * S * sizeof(int32_t), st));
+    const int32_t c0[4] = {0, 0, INT_MAX, 0};
+    DM_CK(cudaMemcpyAsync(ctl, c0, sizeof(c0), cudaMemcpyHostToDevice, st));
+    DM_CK(cudaMemsetAsync(go, 0, 2 * ngen * sizeof(int32_t), st));
+    DM_CK(cudaMemsetAsync(A.res, 0x7f, S * sizeof(unsigned long long), st));  // huge: never converged
+    DM_CK(cudaMemsetAsync(A.gen2, 0, T.gen_doubles * sizeof(double), st));
+    SolveGenArgs ga{};
+    ga.ngen = ngen; ga.max_iter = 1; ga.tol = 0.0;
+    ga.gen_sys = d.gen_sys; ga.gs_limb0 = d.gs_limb0; ga.gs_nlimb = d.gs_nlimb; ga.gs_nB = d.gs_nB;
+    ga.gs_border0 = d.gs_border0; ga.gs_JBB = d.gs_JBB; ga.gs_rB = d.gs_rB; ga.gs_S = d.gs_S;
+    ga.gs_xB = d.gs_xB; ga.lb_dof0 = d.lb_dof0; ga.lb_n = d.lb_n; ga.lb_ncr = d.lb_ncr;
+    ga.lb_cr0 = d.lb_cr0; ga.lb_band = d.lb_band; ga.lb_piv = d.lb_piv; ga.lb_C = d.lb_C;
+    ga.lb_R = d.lb_R; ga.lb_Y = d.lb_Y; ga.lb_y = d.lb_y; ga.border_dof = d.border_dof;
+    ga.coupled_rows = d.coupled_rows; ga.f = nrhs; ga.gen = A.gen2; ga.q = lam;
+    ga.sys_active = act; ga.sys_iters = its; ga.sys_status = sts;
+    ga.sys_res = A.res; ga.ctrl = ctl; ga.units = nullptr; ga.ls_action = nullptr;
+    ga.ls_trial = nullptr;
+    ga.nlimb = (int)T.lb_n.size();
+    ga.limb_nmax = s->x.limb_nmax;
+    ga.gs_fast = d.gs_fast; ga.lb_gsys = d.lb_gsys; ga.lb_dir = d.lb_dir; ga.lb_m = d.lb_m;
+    ga.lb_nbc = d.lb_nbc; ga.lb_bc0 = d.lb_bc0; ga.lb_bcols = d.lb_bcols;
+    ga.gen_go = go; ga.gen_bad = bad;
+    if (ga.nlimb > 0)
+      k_gen_transpose<<<dim3(4, ga.nlimb), 256, 0, st>>>(ga, d.gen, A.gen2);
+    k_gen_transpose_border<<<ngen, 256, 0, st>>>(ga, d.gen, A.gen2);
+    const int wf = s->x.wpb_factor, wb = s->x.wpb_back;
+    if (ga.nlimb)
+      k_gen_limb_factor<<<(ga.nlimb + wf - 1) / wf, 32 * wf, s->x.smem_factor, st>>>(ga);
+    k_gen_border<<<ngen, 32, s->x.border_smem, st>>>(ga);
+    if (ga.nlimb)
+      k_gen_limb_back<<<(ga.nlimb + wb - 1) / wb, 32 * wb, s->x.smem_back, st>>>(ga);
+    DM_CK(cudaGetLastError());
+    int32_t h[4] = {0, 0, 0, 0};
+    DM_CK(cudaMemcpyAsync(h, ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
+    DM_CK(cudaStreamSynchronize(st));
+    if (h[1] > 0) {
+      set_error("dm_step_adjoint: zero or non-finite pivot in the transposed solve");
+      bs = DM_ERR_DEGENERATE;
+    }
+  }
   // the system stays at step n whatever happened
   DM_CK(cudaMemcpyAsync(d.q, d.qn, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (bs != DM_OK) return bs;
@@ -1082,7 +1197,7 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
   const double *ins[2] = {bgq0, bgv0};
   for (int k = 0; k < 2; ++k) {
     double *o = is_device ? outs[k] : A.stage + (size_t)k * n;
-    k_gather_layout<<<blocks(n, 256), 256, 0, st>>>(n, d.layout2dof, ins[k], o);
+    k_gather_layout_first<<<blocks(n, 256), 256, 0, st>>>(n, d.layout2dof, A.first, ins[k], o);
     if (!is_device)
       DM_CK(cudaMemcpyAsync(outs[k], o, n * sizeof(double), cudaMemcpyDeviceToHost, st));
   }

@@ -173,7 +173,16 @@ struct AdjArgs {
   const uint8_t *fixed;
   const int32_t *st_nd, *st_th, *slot2st;
   double *rhs, *gq0, *gv0, *gkbar;
+  // ground friction (general systems): node terms [12][nn] and DOF maps
+  int nn;
+  const double *nt;
+  const int32_t *dof_node, *dof_comp, *node_dof;
+  double rhs_sign;  // +1: rhs = gbar; -1: rhs = -gbar (the solve kernels take -f)
 };
+// Transposed copy of the condensation-path storage of general systems
+// (limb bands, couplings swapped, border block transposed).
+__global__ void k_gen_transpose(SolveGenArgs a, const double *src, double *dst);
+__global__ void k_gen_transpose_border(SolveGenArgs a, const double *src, double *dst);
 __global__ void k_adj_rhs(AdjArgs a);
 __global__ void k_adj_state(AdjArgs a);
 __global__ void k_adj_kbar(AdjArgs a);

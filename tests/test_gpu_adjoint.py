@@ -146,3 +146,81 @@ def test_calibration_reduces_trajectory_loss():
                              checkpoint_every=4)
     print("calibration losses:", ["%.3e" % l for l in losses])
     assert losses[-1] < 0.1 * losses[0]
+
+
+def _stars():
+    desc, params, gait = workloads.star_robots(n_robots=3, seed=3, nodes_per_limb=8)
+    return desc, params, gait
+
+
+def test_step_adjoint_star_robots_matches_oracle_adjoint():
+    """Limbed robots on the ground (joints, contact, friction: J not
+    symmetric, solved transposed by the condensation kernels)."""
+    desc, params, gait = _stars()
+    R = len(desc["nodes_per_rod"])
+    gpu = _gpu(desc, params)
+    ora = OracleSystems(desc, params)
+    for k in range(4):
+        kb = workloads.gait_kbar(gait, k * params["dt"])
+        ora.set_natural_curvature(0, R, kb)
+        ora.step(1)
+    kb = workloads.gait_kbar(gait, 4 * params["dt"])
+    ora.set_natural_curvature(0, R, kb)
+    gpu.set_natural_curvature(0, R, kb)
+    q0, v0 = ora.get_state()
+    d1, beta = ora.get_frames()
+    ora.step(1)
+    q1, _ = ora.get_state()
+    rng = np.random.default_rng(5)
+    wq, wv = rng.normal(size=len(q0)), rng.normal(size=len(q0))
+    ora.set_state(q0, v0)
+    ora.set_frames(d1, beta)
+    ok, oq, ov = step_adjoint(ora, q1, wq, wv)
+    gpu.set_state(q0, v0)
+    gpu.set_frames(d1, beta)
+    gk, gq, gv = gpu.step_adjoint(q1, wq, wv)
+    for a, b in ((gk, ok), (gq, oq), (gv, ov)):
+        scale = max(1.0, float(np.abs(b).max()))
+        assert np.abs(a - b).max() <= 1e-8 * scale, np.abs(a - b).max() / scale
+
+
+def test_star_robot_rollout_gradient_against_central_differences():
+    """Six steps of star robots on the ground with the gait as controls:
+    rollout gradient (frame chain, friction, joints) against central
+    differences of the GPU rollout."""
+    import torch
+    from paper_2311_18126_gb300 import dismech as dmx
+    from paper_2311_18126_gb300.adjoint import rollout
+    desc, params, gait = _stars()
+    R = len(desc["nodes_per_rod"])
+    gpu = dmx.System(desc, params)
+    dt = params["dt"]
+    for k in range(3):
+        gpu.set_natural_curvature(0, R, workloads.gait_kbar(gait, k * dt))
+        gpu.step(1)
+    q0, v0 = gpu.get_state()
+    frames = gpu.get_frames()
+    T = 6
+    kseq = np.stack([workloads.gait_kbar(gait, (3 + t) * dt) for t in range(T)])
+    rng = np.random.default_rng(6)
+    w = rng.normal(size=(T, len(q0)))
+    kt = torch.tensor(kseq, requires_grad=True)
+    x = rollout(gpu, kt, torch.from_numpy(q0), torch.from_numpy(v0), frames, 4)
+    (x * torch.from_numpy(w)).sum().backward()
+    gk = kt.grad.numpy()
+
+    def loss_np(k):
+        x = rollout(gpu, torch.from_numpy(k), torch.from_numpy(q0), torch.from_numpy(v0),
+                    frames, 4)
+        return float((x.numpy() * w).sum())
+
+    errs = []
+    h = 1e-6
+    for (t, i, c) in [(0, 2, 0), (2, 20, 1), (4, 40, 0), (5, 9, 0)]:
+        kp, km = kseq.copy(), kseq.copy()
+        kp[t, i, c] += h
+        km[t, i, c] -= h
+        fd = (loss_np(kp) - loss_np(km)) / (2 * h)
+        errs.append(abs(fd - gk[t, i, c]) / max(abs(fd), 1e-3 * np.abs(gk).max()))
+    print("star-robot rollout gradient relative errors:", ["%.2e" % e for e in errs])
+    assert max(errs) < 1e-3
