@@ -75,10 +75,11 @@ def parse():
     ap.add_argument("--rods", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="uneven_rods",
-                    choices=["uneven_rods", "star_robots", "coil", "warm_start"],
+                    choices=["uneven_rods", "star_robots", "coil", "warm_start", "calibration"],
                     help="uneven_rods: the headline batch (default); star_robots: limbed "
                          "robots on the ground with a gait; coil: edge-edge self-contact; "
-                         "warm_start: learned vs extrapolated Newton guess on star robots")
+                         "warm_start: learned vs extrapolated Newton guess on star robots; "
+                         "calibration: adjoint gradient of a 500-step star-robot rollout")
     ap.add_argument("--robots", type=int, default=1024)
     return ap.parse_args()
 
@@ -515,10 +516,91 @@ def run_other(args):
         tdist.destroy_process_group()
 
 
+def run_calibration(args):
+    """Scope config 4: 64 star robots of 4 limbs on the ground, per-step
+    per-limb natural curvatures (kappabar1, kappabar2) as parameters, L2 loss
+    on all node positions against a trajectory the solver makes from seeded
+    sinusoids, 500 steps with checkpoints every 50.  Times one loss+gradient
+    evaluation (forward rollout, re-simulation of each segment, step
+    adjoints with the frame chain) and reports rod-steps/s of that pass,
+    then takes calibration iterations."""
+    import torch
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    import workloads
+    from paper_2311_18126_gb300 import System, ensure_built, DismechError
+    from paper_2311_18126_gb300.adjoint import rollout, _layout_positions
+    ensure_built()
+    T, K = 500, 50
+    desc, params, gait = workloads.star_robots(n_robots=64, seed=4 + rank, fixed_limbs=4)
+    dt = params["dt"]
+    R = len(desc["nodes_per_rod"])
+    sysm = System(desc, params)
+    q0, v0 = sysm.get_state()
+    frames = sysm.get_frames()
+    nint = gait["nodes_per_limb"] - 2
+    spacing = gait["spacing"]
+    # per-step per-limb controls c[t, limb, 2] (1/m) -> integrated kappabar per node
+    tt = np.arange(T) * dt
+    c1 = gait["A"][None, :] * np.sin(2 * np.pi * tt[:, None] / gait["T"][None, :] +
+                                     gait["phase"][None, :])
+    c_true = np.stack([c1, np.zeros_like(c1)], axis=-1)
+    expand = lambda c: (c[:, :, None, :] * spacing).expand(-1, -1, nint, -1).reshape(T, R * nint, 2)
+    with torch.no_grad():
+        target = rollout(sysm, expand(torch.from_numpy(c_true)), torch.from_numpy(q0),
+                         torch.from_numpy(v0), frames, K)
+    pos = torch.from_numpy(_layout_positions(np.asarray(desc["nodes_per_rod"])).astype(np.float64))
+    c = torch.zeros_like(torch.from_numpy(c_true), requires_grad=True)
+
+    def loss_grad(cc):
+        x = rollout(sysm, expand(cc), torch.from_numpy(q0), torch.from_numpy(v0), frames, K)
+        loss = (((x - target) ** 2) * pos).sum()
+        g, = torch.autograd.grad(loss, [cc])
+        return float(loss.detach()), g
+
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    t0 = time.perf_counter()
+    l0, g = loss_grad(c)
+    torch.cuda.synchronize()
+    tg = time.perf_counter() - t0
+    clocks = clk.stop()
+    # calibration iterations with a backtracking step
+    losses = [l0]
+    step = l0 / float((g * g).sum())
+    for _ in range(max(1, args.steps // 10)):
+        for _ in range(12):
+            trial = (c.detach() - step * g).requires_grad_(True)
+            try:
+                lt, gt = loss_grad(trial)
+            except DismechError:  # a step too long for Newton: shorter
+                lt = float("inf")
+            if lt < losses[-1]:
+                c, g = trial, gt
+                losses.append(lt)
+                step *= 1.5
+                break
+            step *= 0.5
+    line = {"metric": METRIC, "value": R * T / tg, "unit": "rod-steps/s (loss+gradient pass)",
+            "n_gpus": ws, "steps": T, "warmup": 0, "ms_per_step": 1e3 * tg / T,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "calibration: 64 star robots x 4 limbs on the ground, "
+                       "500 steps, per-step per-limb natural curvature, checkpoints every 50",
+                       "rods": R, "params": int(np.prod(c_true.shape)), "seed": 4 + rank},
+            "calibration": {"gradient_seconds": tg, "losses": losses}, "clocks": clocks,
+            "e2e": None, "roofline": None}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "calibration":
+        run_calibration(args)
     elif args.workload != "uneven_rods":
         run_other(args)
     else:

@@ -24,6 +24,8 @@ taken as transported along with its tangents.
 import numpy as np
 import torch
 
+from . import dismech as dmx
+
 
 def _edge_tangents(q, npr):
     """Unit tangents [E, 3] and inverse lengths [E] of every edge, from a
@@ -209,7 +211,11 @@ def calibrate(system, target, kbar_init, q0, v0, frames0, iters=20, lr=None,
         with torch.no_grad():
             for _ in range(20):
                 trial = kb - step * g
-                if float(evaluate(trial)) < losses[-1]:
+                try:
+                    lt = float(evaluate(trial))
+                except dmx.DismechError:  # too long a step for Newton: shorter
+                    lt = float("inf")
+                if lt < losses[-1]:
                     kb.copy_(trial)
                     step *= 1.5
                     break
