@@ -309,9 +309,11 @@ dm_status dm_ws_column_stats(const float *data, int64_t rows, int32_t cols, floa
  * once per rod in the layout: its loss gradients are summed over the copies
  * and its output gradients are written to its first copy (zeros in the
  * others), so that outputs can be fed back as inputs.  is_device: the
- * pointers are device (1) or host (0) memory.  Systems with edge-edge
- * contact, and networks with a limb jointed at both ends, are rejected
- * (DM_ERR_INVALID_ARG); the friction force's dependence on x_n enters
+ * pointers are device (1) or host (0) memory.  Rods with edge-edge contact
+ * solve J^T lambda with the transposed dense-band LU of the contact path;
+ * edge-edge friction (pair_mu != 0), and networks with a limb jointed at
+ * both ends, are rejected (DM_ERR_INVALID_ARG); the ground friction
+ * force's dependence on x_n enters
  * dL/dq_n; fixed DOFs pass dL/dq_{n+1} through and get no velocity
  * gradient.  Synchronises the stream; the state of step n is left in
  * place. */

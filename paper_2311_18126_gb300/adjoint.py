@@ -5,7 +5,9 @@ gradient by the library's step adjoint (dm_step_adjoint) and checkpoints.
 The forward pass stores the state and frames every ``checkpoint_every``
 steps; the backward pass re-simulates each segment from its checkpoint,
 keeping the per-step states of that segment only, and runs the step adjoint
-backwards through it.  Single rods without contact.
+backwards through it.  Any system the step adjoint accepts: single rods,
+rods in edge-edge contact without pair friction, rod networks and rods on
+the ground.
 
 The frame chain: the step adjoint holds the committed reference frames
 fixed, but each step's frames come from the earlier tangents by

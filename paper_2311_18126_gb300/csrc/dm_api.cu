@@ -1029,11 +1029,12 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
     if (T.sys_kind[k] == SOLVE_ROD_BAND) {
       rod_d0.push_back(T.sys_dof0[k]);
       rod_n.push_back(T.sys_ndof[k]);
-    } else if (T.sys_kind[k] != SOLVE_GENERAL) {
-      set_error("dm_step_adjoint: systems with edge-edge contact are not supported");
+    } else if (T.sys_kind[k] == SOLVE_CONTACT && s->prm.pair_mu != 0.0) {
+      set_error("dm_step_adjoint: edge-edge friction (pair_mu != 0) is not supported");
       return DM_ERR_INVALID_ARG;
     }
   }
+  const bool contact_on = s->x.cc.n_contact > 0;
   for (size_t w = 0; w < T.gen_sys.size(); ++w)
     if (!T.gs_fast[w]) {
       set_error("dm_step_adjoint: general system " + std::to_string(T.gen_sys[w]) +
@@ -1106,8 +1107,36 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
     k_nodes<<<blocks(nn, 256), 256, 0, st>>>(na);
   }
   if (ns > 0) k_stencil<<<blocks(ns, 128), 128, 0, st>>>(ka);
-  if (!rod_d0.empty()) {
+  ContactArgs ca{};
+  if (contact_on) {
+    auto &c = s->x.cc;
+    ca.ne = ne; ca.nd = nd; ca.nsys = S; ca.table_mask = c.table - 1; ca.pair_cap = c.pair_cap;
+    ca.inv_cell = c.inv_cell; ca.delta = s->prm.delta; ca.kc = s->prm.pair_kc;
+    ca.mu = 0.0; ca.K2 = 0.0; ca.dt = s->p.dt;
+    ca.q = d.q; ca.qn = d.qn; ca.edge_h = c.edge_h; ca.band = d.band;
+    ca.edge_a = d.edge_a; ca.edge_b = d.edge_b; ca.edge_sys = d.edge_sys; ca.edge_idx = c.edge_idx;
+    ca.sys_kind = s->x.d_sys_kind; ca.sys_active = d.sys_active; ca.dof_sys = s->x.d_dof_sys;
+    ca.sys_dof0 = d.sys_dof0; ca.sys_ndof = d.sys_ndof; ca.contact_sys = c.contact_sys;
+    ca.ls_action = nullptr; ca.fixed = d.fixed; ca.sys_dense0 = c.sys_dense0;
+    ca.sys_status = d.sys_status; ca.sys_bw = c.sys_bw; ca.edge_key = c.edge_key;
+    ca.bucket_count = c.bucket_count; ca.bucket_start = c.bucket_start;
+    ca.bucket_fill = c.bucket_fill; ca.bucket_edges = c.bucket_edges; ca.pairs = c.pairs;
+    ca.npairs = c.npairs; ca.fc = c.fc; ca.dense = c.dense;
+    ca.n_contact = c.n_contact; ca.cgo = c.cgo; ca.cbad = c.cbad;
+    DM_CK(cudaMemsetAsync(c.fc, 0, nd * sizeof(double), st));
+    DM_CK(cudaMemsetAsync(c.npairs, 0, sizeof(int32_t), st));
+    DM_CK(cudaMemsetAsync(c.bucket_count, 0, c.table * sizeof(int32_t), st));
+    k_cc_clear<<<blocks(nd, 256), 256, 0, st>>>(ca);
+    k_cc_reset_bw<<<blocks(S, 256), 256, 0, st>>>(ca);
+    k_cc_cells<<<blocks(ne, 256), 256, 0, st>>>(ca);
+    k_cc_scan<<<1, 1024, 0, st>>>(ca);
+    k_cc_fill<<<blocks(ne, 256), 256, 0, st>>>(ca);
+    k_cc_pairs<<<blocks(ne, 128), 128, 0, st>>>(ca);
+    k_cc_terms<<<blocks(c.pair_cap, 64), 64, 0, st>>>(ca);
+  }
+  if (!rod_d0.empty() || contact_on) {
     RowArgs ra{};
+    ra.fc = contact_on ? s->x.cc.fc : nullptr;
     ra.nd = nd; ra.ns = ns; ra.ne = ne; ra.dt = s->p.dt;
     for (int c = 0; c < 3; ++c) ra.g[c] = s->p.g[c];
     ra.eta = s->p.eta;
@@ -1184,6 +1213,51 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
     DM_CK(cudaStreamSynchronize(st));
     if (h[1] > 0) {
       set_error("dm_step_adjoint: zero or non-finite pivot in the transposed solve");
+      bs = DM_ERR_DEGENERATE;
+    }
+  }
+  if (bs == DM_OK && contact_on) {
+    // contact rods: J^T lambda = gbar with the blocked LU of the transposed
+    // dense matrix (the contact kernels solve J dq = -f and add dq to q)
+    const int nc = s->x.cc.n_contact;
+    k_cc_band<<<blocks(nd, 256), 256, 0, st>>>(ca);
+    AdjArgs an = aa;
+    an.rhs = nrhs;
+    an.rhs_sign = -1.0;
+    k_adj_rhs<<<blocks(nd, 256), 256, 0, st>>>(an);
+    if (rod_d0.empty() && ngen == 0) DM_CK(cudaMemsetAsync(lam, 0, nd * sizeof(double), st));
+    std::vector<int32_t> onec(nc, 1);
+    DM_CK(cudaMemcpyAsync(ca.cgo, onec.data(), nc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    DM_CK(cudaMemsetAsync(ca.cbad, 0, nc * sizeof(int32_t), st));
+    for (int c = 0; c < nc; ++c) {
+      const int nc_n = T.sys_ndof[c];
+      k_cc_transpose<<<blocks((int64_t)nc_n * std::max(10, nc_n), 256), 256, 0, st>>>(ca, c);
+      for (int k = 0; k < nc_n; k += kNB) {
+        const int rest = nc_n - k - std::min(kNB, nc_n - k);
+        k_lu_diag<<<1, 256, 0, st>>>(ca, c, k);
+        if (rest > 0) {
+          k_lu_trsm<<<blocks(2 * rest, 128), 128, 0, st>>>(ca, c, k);
+          const int t = (rest + 63) / 64;
+          k_lu_gemm<<<dim3(t, t), 256, 0, st>>>(ca, c, k);
+        }
+      }
+    }
+    if (!A.ints) DM_TRY(dalloc(s, &A.ints, 6 * (size_t)S + 2 * (size_t)std::max(ngen, 1) + 8));
+    int32_t *its = A.ints, *sts = its + S, *ctl = sts + S;
+    DM_CK(cudaMemsetAsync(its, 0, 2 * S * sizeof(int32_t), st));
+    const int32_t c0[4] = {0, 0, INT_MAX, 0};
+    DM_CK(cudaMemcpyAsync(ctl, c0, sizeof(c0), cudaMemcpyHostToDevice, st));
+    SolveArgs vs{};
+    vs.nd = nd; vs.sys_dof0 = d.sys_dof0; vs.sys_ndof = d.sys_ndof; vs.f = nrhs;
+    vs.q = lam; vs.dq = d.dq; vs.sys_active = d.sys_active; vs.sys_iters = its;
+    vs.sys_status = sts; vs.ctrl = ctl;
+    k_cc_subst<<<nc, 1024, 0, st>>>(ca, vs);
+    DM_CK(cudaGetLastError());
+    int32_t h[4] = {0, 0, 0, 0};
+    DM_CK(cudaMemcpyAsync(h, ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
+    DM_CK(cudaStreamSynchronize(st));
+    if (h[1] > 0) {
+      set_error("dm_step_adjoint: zero or non-finite pivot in the transposed contact solve");
       bs = DM_ERR_DEGENERATE;
     }
   }

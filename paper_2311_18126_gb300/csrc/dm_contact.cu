@@ -733,6 +733,22 @@ __global__ void __launch_bounds__(256) k_lu_gemm(ContactArgs a, int c, int k) {
   }
 }
 
+// In-place transpose of a contact system's matrix within its bandwidth
+// (for the adjoint's J^T solve): one thread per (row, offset) pair.
+__global__ void k_cc_transpose(ContactArgs a, int c) {
+  const int s = a.contact_sys[c];
+  const int n = a.sys_ndof[s];
+  const int bw = max(10, a.sys_bw[s]);
+  double *A = a.dense + a.sys_dense0[s];
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * bw) return;
+  const int i = (int)(t / bw), j = i + 1 + (int)(t - (int64_t)i * bw);
+  if (j >= n) return;
+  const double x = A[(size_t)i * n + j];
+  A[(size_t)i * n + j] = A[(size_t)j * n + i];
+  A[(size_t)j * n + i] = x;
+}
+
 // Blocked substitution with the factors (L unit lower, U upper), q += x.
 __global__ void __launch_bounds__(1024) k_cc_subst(ContactArgs a, SolveArgs v) {
   const int c = blockIdx.x;

@@ -163,6 +163,7 @@ __global__ void k_lu_diag(ContactArgs a, int c, int k);
 __global__ void k_lu_trsm(ContactArgs a, int c, int k);
 __global__ void k_lu_gemm(ContactArgs a, int c, int k);
 __global__ void k_cc_subst(ContactArgs a, SolveArgs v);
+__global__ void k_cc_transpose(ContactArgs a, int c);
 
 // Adjoint of one implicit step (single rods): right-hand side, state and
 // natural-curvature gradients.

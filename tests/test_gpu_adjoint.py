@@ -224,3 +224,31 @@ def test_star_robot_rollout_gradient_against_central_differences():
         errs.append(abs(fd - gk[t, i, c]) / max(abs(fd), 1e-3 * np.abs(gk).max()))
     print("star-robot rollout gradient relative errors:", ["%.2e" % e for e in errs])
     assert max(errs) < 1e-3
+
+
+def test_step_adjoint_coil_with_contact_matches_oracle_adjoint():
+    """A self-contacting coil (edge-edge IMC contact, no friction): the
+    transposed dense-band LU on the GPU against the oracle's adjoint, at a
+    step where turns touch."""
+    from test_gpu_contact import _short_coil, _oracle_active_pairs
+    desc, params = _short_coil()
+    gpu = _gpu(desc, params)
+    ora = OracleSystems(desc, params)
+    for _ in range(36):
+        ora.step(1)
+    q0, v0 = ora.get_state()
+    d1, beta = ora.get_frames()
+    ora.step(1)
+    assert _oracle_active_pairs(ora, params) > 0
+    q1, _ = ora.get_state()
+    rng = np.random.default_rng(7)
+    wq, wv = rng.normal(size=len(q0)), rng.normal(size=len(q0))
+    ora.set_state(q0, v0)
+    ora.set_frames(d1, beta)
+    ok, oq, ov = step_adjoint(ora, q1, wq, wv)
+    gpu.set_state(q0, v0)
+    gpu.set_frames(d1, beta)
+    gk, gq, gv = gpu.step_adjoint(q1, wq, wv)
+    for a, b in ((gk, ok), (gq, oq), (gv, ov)):
+        scale = max(1.0, float(np.abs(b).max()))
+        assert np.abs(a - b).max() <= 1e-8 * scale, np.abs(a - b).max() / scale
