@@ -242,10 +242,12 @@ def run_ours(args):
             import torch.distributed as tdist
             tdist.barrier()
 
+    tuning = sysm.autotune(steps=2)
     for _ in range(args.warmup):
         sysm.step(1, stats=False)
     torch.cuda.synchronize()
-    sysm.set_profiling(True)
+    snap = _snapshot(sysm)
+    sysm.set_profiling(False)  # counters reset; Newton rounds run as CUDA graphs
     barrier()
     torch.cuda.synchronize()
     clk = Clocks(local)
@@ -262,10 +264,19 @@ def run_ours(args):
     barrier()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
-    prof = sysm.get_profile()
-    sysm.set_profiling(False)
+    n_launch = sum(v[0] for v in sysm.get_profile().values())
     tmax = max_over_ranks(ms, ws, "cuda")
     value = job_rate(ws, R, args.steps, tmax * 1e-3)
+    # the same steps again from the same state with the host driving the
+    # rounds, then a profiled pass (per-kernel CUDA events, host-driven) for
+    # the kernel table
+    _restore(sysm, snap)
+    host_ms, _, _ = _timed_steps(sysm, args.steps, None, 0, local, graphs=False, clocks=False)
+    _restore(sysm, snap)
+    sysm.set_profiling(True)
+    _timed_steps(sysm, args.steps, None, 0, local, clocks=False)
+    prof = sysm.get_profile()
+    sysm.set_profiling(False)
 
     # end to end through the public API with pinned host buffers
     n = sysm.n_state
@@ -341,7 +352,14 @@ def run_ours(args):
             "newton": {"iters_mean": float(it.mean()), "iters_max": int(it.max()),
                        "node_steps_per_s": value * float(np.mean(desc["nodes_per_rod"]))},
             "clocks": clocks, "e2e": e2e,
-            "gpu_launches": int(sum(v[0] for v in prof.values())),
+            "gpu_launches": int(n_launch),
+            "rounds": {"mode": "one CUDA graph per step (device-side while loop over Newton "
+                               "rounds)", "host_loop_ms_per_step": host_ms / args.steps,
+                       "note": "host loop timed on the same steps from the same state"},
+            "autotune": tuning,
+            "kernel_timing": "per-kernel CUDA events in a separate pass of the same number "
+                             "of steps right after the timed region (host-driven rounds, "
+                             "same kernels and launch shapes)",
             "roofline": roof, "kernels": kernels}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rods = sample_rods(R, 8)
@@ -357,13 +375,28 @@ def run_ours(args):
         tdist.destroy_process_group()
 
 
-def _timed_steps(sysm, steps, controls, k0, local):
+def _snapshot(sysm):
+    q, v = sysm.get_state()
+    d1, beta = sysm.get_frames()
+    return q, v, d1, beta
+
+
+def _restore(sysm, snap):
+    q, v, d1, beta = snap
+    sysm.set_state(q, v)
+    sysm.set_frames(d1, beta)
+
+
+def _timed_steps(sysm, steps, controls, k0, local, graphs=True, clocks=True):
     """Runs `steps` steps (controls(k) applied before step k0 + i) between CUDA
-    events with nvidia-smi sampling; returns (ms, per-step iterations, clocks)."""
+    events with nvidia-smi sampling; returns (ms, per-step iterations, clocks).
+    graphs=False: the host drives the Newton rounds."""
     import torch
+    sysm.set_graphs(graphs)
     torch.cuda.synchronize()
-    clk = Clocks(local)
-    clk.start()
+    clk = Clocks(local) if clocks else None
+    if clk:
+        clk.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     its = []
@@ -375,7 +408,8 @@ def _timed_steps(sysm, steps, controls, k0, local):
         its.append(sysm.iterations.copy())
     e1.record()
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1), np.array(its), clk.stop()
+    sysm.set_graphs(True)
+    return e0.elapsed_time(e1), np.array(its), clk.stop() if clk else None
 
 
 def _kernel_table(prof):
@@ -441,14 +475,21 @@ def run_other(args):
             for k in range(warm):
                 sysm.set_natural_curvature(0, R, controls(k))
                 sysm.step(1, stats=False)
-            sysm.set_profiling(True)
+            snap = _snapshot(sysm)
+            sysm.set_profiling(False)
             ms, its, clocks = _timed_steps(sysm, args.steps, controls, warm, local)
+            n_launch = sum(v[0] for v in sysm.get_profile().values())
             ms = max_over_ranks(ms, ws, "cuda")
+            _restore(sysm, snap)
+            sysm.set_profiling(True)
+            _timed_steps(sysm, args.steps, controls, warm, local, clocks=False)
             arms[label] = {"value": job_rate(ws, R, args.steps, ms * 1e-3),
                            "ms_per_step": ms / args.steps,
                            "iters_per_rod_step": float(its.mean()),
                            "slowest_per_step": float(its.max(1).mean()),
+                           "gpu_launches": int(n_launch),
                            "kernels": _kernel_table(sysm.get_profile()), "clocks": clocks}
+            sysm.set_profiling(False)
             sysm.close()
         line.update({"value": arms["learned"]["value"],
                      "ms_per_step": arms["learned"]["ms_per_step"],
@@ -456,22 +497,35 @@ def run_other(args):
                                  arms["learned"]["value"] / arms["extrapolation"]["value"],
                                  "train_loss": [losses[0], losses[-1]], "arms": arms},
                      "clocks": arms["learned"]["clocks"],
-                     "gpu_launches": int(sum(v["launches"] for v in
-                                             arms["learned"]["kernels"].values())),
+                     "gpu_launches": arms["learned"]["gpu_launches"],
                      "e2e": None, "roofline": None})
         line["config"]["training"] = "%d robots x 400 steps (every 2nd step sampled), 4000 Adam " \
                                      "steps of 16384 segments" % max(args.robots // 4, 64)
     else:
         sysm = System(desc, params)
+        if controls is not None:
+            sysm.set_natural_curvature(0, R, controls(0))
+        tuning = sysm.autotune(steps=2)
         for k in range(warm):
             if controls is not None:
                 sysm.set_natural_curvature(0, R, controls(k))
             sysm.step(1, stats=False)
-        sysm.set_profiling(True)
+        snap = _snapshot(sysm)
+        sysm.set_profiling(False)
         ms, its, clocks = _timed_steps(sysm, args.steps, controls, warm, local)
-        prof = sysm.get_profile()
+        n_launch = sum(v[0] for v in sysm.get_profile().values())
         ms = max_over_ranks(ms, ws, "cuda")
         value = job_rate(ws, R, args.steps, ms * 1e-3)
+        # the same steps from the same state: host-driven rounds, then profiled
+        _restore(sysm, snap)
+        host_ms, _, _ = _timed_steps(sysm, args.steps, controls, warm, local, graphs=False,
+                                     clocks=False)
+        _restore(sysm, snap)
+        sysm.set_profiling(True)
+        _timed_steps(sysm, args.steps, controls, warm, local, clocks=False)
+        prof = sysm.get_profile()
+        sysm.set_profiling(False)
+        k1 = warm + args.steps
         # end to end through the C ABI: pinned host state in and out every step
         n = sysm.n_state
         hq = torch.empty(n, dtype=torch.float64, pin_memory=True)
@@ -484,7 +538,7 @@ def run_other(args):
         t0 = time.perf_counter()
         for i in range(e2e_steps):
             if controls is not None:
-                sysm.set_natural_curvature(0, R, controls(warm + args.steps + i))
+                sysm.set_natural_curvature(0, R, controls(k1 + i))
             sysm.set_state(hq.numpy(), hv.numpy())
             sysm.step(1, stats=False)
             qq, vv = sysm.get_state()
@@ -499,7 +553,13 @@ def run_other(args):
                      "clocks": clocks,
                      "e2e": {"value": job_rate(ws, R, e2e_steps, te), "unit": UNIT,
                              "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": 2 * n * 8},
-                     "gpu_launches": int(sum(v[0] for v in prof.values())),
+                     "gpu_launches": int(n_launch),
+                     "rounds": {"mode": "one CUDA graph per step (device-side while loop "
+                                        "over Newton rounds)",
+                                "host_loop_ms_per_step": host_ms / args.steps,
+                                "note": "host loop timed on the same steps from the same "
+                                        "state"},
+                     "autotune": tuning,
                      "roofline": {"bound": "alu", "kernel": dom, "unit": "TFLOP/s",
                                   "peak": peak_fp64 / 1e3, "achieved": None, "frac": None,
                                   "traffic": None,

@@ -346,6 +346,43 @@ typedef struct dm_profile {
   double ms[DM_NUM_KERNELS];
 } dm_profile;
 dm_status dm_set_profiling(dm_system *sys, int32_t enable); /* also resets */
+/* Newton rounds as a CUDA graph (default on): dm_step launches, per step,
+ * one graph whose while node runs a round (every phase's kernels) and then a
+ * one-thread kernel that keeps the loop going while a system is active, at
+ * most the host loop's round limit; the host reads the control words once
+ * per step instead of once per round.  The results are the same kernels in
+ * the same order, so they are identical.  Off (0): the host drives the
+ * rounds.  With a learned guess tried against the extrapolation, the trial
+ * round runs before the graph.  Steps with profiling on use the host loop
+ * (per-launch events). */
+dm_status dm_set_graphs(dm_system *sys, int32_t enable);
+
+/* Launch shapes chosen by dm_autotune. */
+typedef struct dm_tuning {
+  int32_t edge_threads;        /* threads per block, edge frames + stretch        */
+  int32_t stencil_threads;     /* threads per block, bend-twist stencils          */
+  int32_t stencil_per_thread;  /* stencils per thread (stencils per warp / 32)    */
+  int32_t rows_threads;        /* threads per block, residual/Jacobian rows       */
+  int32_t solve_warps;         /* rod solver: warps per block (4 rods per warp)   */
+  int32_t solve_blocks_per_sm; /* rod solver: resident blocks per SM              */
+  int32_t limb_factor_warps;   /* condensation: limbs (warps) per factor block    */
+  int32_t limb_back_warps;     /* condensation: limbs (warps) per back-subst block */
+  double us_per_launch[8];     /* measured time per launch of the chosen shapes:
+                                  edge, stencil, rows, rod solve, limb solve with
+                                  the chosen factor shape, with both chosen (us) */
+} dm_tuning;
+/* Autotuner: from the current committed state, runs `steps` steps per
+ * candidate launch shape with per-kernel CUDA events and keeps, kernel by
+ * kernel, the fastest shape (the default unless another is faster by more
+ * than 2 %): threads per block and stencils per thread of the stencil
+ * kernel, threads per block of the edge and row kernels, warps per block
+ * (systems per block = 4 x warps) and blocks per SM of the persistent rod
+ * solver, limbs per block of the condensation kernels.  Every shape computes
+ * the same arithmetic per system.  The committed state, the profiling
+ * switch and the counters are restored before returning; `out` (optional,
+ * caller-owned) receives the choice.  Rejects a system with a learned warm
+ * start attached (DM_ERR_INVALID_ARG).  Synchronises the stream. */
+dm_status dm_autotune(dm_system *sys, int32_t steps, dm_tuning *out);
 dm_status dm_get_profile(dm_system *sys, dm_profile *out);
 const char *dm_kernel_name(int32_t id); /* "" for unused ids */
 

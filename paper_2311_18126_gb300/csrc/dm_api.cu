@@ -1,5 +1,6 @@
 // C ABI of the GB300 implicit DER library (include/dismech.h).
 #include <algorithm>
+#include <cmath>
 #include <climits>
 #include <cstring>
 #include <numeric>
@@ -138,6 +139,20 @@ struct Extra {
   size_t smem_factor = 0, smem_back = 0;
   int solve_blocks = 1;
   size_t solve_smem = 0;
+  int sms = 1;
+  int wpb_factor_max = 1, wpb_back_max = 1;
+  // launch shapes (dm_autotune): threads per block and work per thread of
+  // the edge, stencil and row kernels; warps per block and blocks per SM of
+  // the persistent rod solver
+  struct {
+    int edge_threads = 256, stencil_threads = 128, stencil_per_thread = 1, rows_threads = 256;
+    int solve_warps = 4, solve_bps = 1;
+  } tune;
+  // Newton rounds as one CUDA graph: a device-side while loop over rounds
+  bool graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t round_graph = nullptr;
+  int64_t round_launches[DM_NUM_KERNELS] = {};  // launches of one captured round
   std::vector<int32_t> slot2st;
   int32_t *d_slot2st = nullptr;
   int32_t *d_dof_sys = nullptr;
@@ -152,6 +167,17 @@ struct Extra {
 struct dm_system_ext : dm_system {
   Extra x;
 };
+
+// Persistent rod solver shape: `warps` warps of four rods each per block,
+// `bps` blocks per SM, no more blocks than the batch needs.
+static void set_solve_shape(dm_system_ext *s, int warps, int bps) {
+  s->x.tune.solve_warps = warps;
+  s->x.tune.solve_bps = bps;
+  s->x.solve_smem = (size_t)warps * 4 * kSolveRodDoubles * sizeof(double);
+  const int rods_per_block = 4 * warps;
+  const int want = (s->x.n_rod_sys + rods_per_block - 1) / rods_per_block;
+  s->x.solve_blocks = std::max(1, std::min(want, bps * s->x.sms));
+}
 
 static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
                              dm_system_ext *s) {
@@ -279,7 +305,7 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
   DM_TRY(dalloc(s, &d.sys_iters, S));
   DM_TRY(dalloc(s, &d.sys_status, S));
   DM_TRY(dalloc(s, &d.sys_res, S));
-  DM_TRY(dalloc(s, &d.ctrl, 4));
+  DM_TRY(dalloc(s, &d.ctrl, 8));  // [4] = Newton rounds of the step
   DM_TRY(dalloc(s, &d.band, 11 * nd));
   DM_TRY(dalloc(s, &d.dq, nd));
   std::vector<int32_t> order;
@@ -414,6 +440,8 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
       const size_t pb = gen_back_smem(s->x.limb_nmax) * sizeof(double);
       s->x.wpb_factor = (int)std::max<size_t>(1, std::min<size_t>(4, (200 << 10) / pf));
       s->x.wpb_back = (int)std::max<size_t>(1, std::min<size_t>(4, (200 << 10) / pb));
+      s->x.wpb_factor_max = s->x.wpb_factor;
+      s->x.wpb_back_max = s->x.wpb_back;
       s->x.smem_factor = pf * s->x.wpb_factor;
       s->x.smem_back = pb * s->x.wpb_back;
       DM_CK(cudaFuncSetAttribute(k_gen_limb_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -442,7 +470,7 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
   DM_CK(cudaMemset(s->x.d_units, 0, DM_NUM_KERNELS * sizeof(unsigned long long)));
   DM_TRY(dalloc(s, &s->x.d_bad, 1));
   for (int k = 0; k < 2 * DM_NUM_KERNELS; ++k) DM_CK(cudaEventCreate(&s->x.ev[k]));
-  DM_CK(cudaMallocHost(&s->h_ctrl, 4 * sizeof(int32_t)));
+  DM_CK(cudaMallocHost(&s->h_ctrl, 8 * sizeof(int32_t)));
   // persistent banded solver: 32 rods per 128-thread block, enough blocks
   // to cover the batch but no more than fit at once
   s->x.solve_smem = 16 * kSolveRodDoubles * sizeof(double);  // 16 rods per block
@@ -457,8 +485,8 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     // persistent: one block of four warps per SM, so that each SM partition
     // runs one warp; the warps take rod quads from the size-sorted queue
     // (largest first), which balances the FP64 work across partitions
-    const int want = (s->x.n_rod_sys + 15) / 16;
-    s->x.solve_blocks = std::max(1, std::min({want, sms, std::max(1, per_sm) * sms}));
+    s->x.sms = sms;
+    set_solve_shape(s, 4, 1);
   }
   DM_CK(cudaDeviceSynchronize());
   return DM_OK;
@@ -535,6 +563,8 @@ void dm_destroy(dm_system *sys) {
   for (int k = 0; k < 2 * DM_NUM_KERNELS; ++k)
     if (sx->x.ev[k]) cudaEventDestroy(sx->x.ev[k]);
   if (sys->h_ctrl) cudaFreeHost(sys->h_ctrl);
+  if (sx->x.round_graph) cudaGraphExecDestroy(sx->x.round_graph);
+  if (sx->x.cap_stream) cudaStreamDestroy(sx->x.cap_stream);
   dm::ws_free(sys->ws);
   delete static_cast<dm_system_ext *>(sys);
 }
@@ -671,8 +701,154 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     stats->max_iterations = 0;
   }
   std::vector<int32_t> iters;
+  // One Newton round: every phase's launches, in stream order on rs.
+  auto round = [&](cudaStream_t rs, int it) -> dm_status {
+    DM_CK(cudaMemsetAsync(d.sys_res, 0, S * sizeof(unsigned long long), rs));
+    DM_CK(cudaMemsetAsync(d.ctrl, 0, sizeof(int32_t), rs));
+    DM_CK(cudaMemsetAsync(d.ctrl + 3, 0, sizeof(int32_t), rs));
+    {
+      Timed t(s, K_EDGE, rs);
+      const int tb = s->x.tune.edge_threads;
+      k_edge<<<blocks(ne, tb), tb, 0, rs>>>(ea);
+    }
+    if (T.ground) {
+      Timed t(s, K_NODES, rs);
+      k_nodes<<<blocks(nn, 256), 256, 0, rs>>>(na);
+    }
+    if (ns > 0) {
+      Timed t(s, K_STENCIL, rs);
+      const int tb = s->x.tune.stencil_threads;
+      k_stencil<<<blocks(ns, (int64_t)tb * s->x.tune.stencil_per_thread), tb, 0, rs>>>(ka);
+    }
+    if (contact_on) {
+      Timed t(s, K_CONTACT, rs);
+      const auto &c = s->x.cc;
+      DM_CK(cudaMemsetAsync(c.fc, 0, nd * sizeof(double), rs));
+      DM_CK(cudaMemsetAsync(c.npairs, 0, sizeof(int32_t), rs));
+      DM_CK(cudaMemsetAsync(c.bucket_count, 0, c.table * sizeof(int32_t), rs));
+      k_cc_clear<<<blocks(nd, 256), 256, 0, rs>>>(ca);
+      k_cc_reset_bw<<<blocks(S, 256), 256, 0, rs>>>(ca);
+      k_cc_cells<<<blocks(ne, 256), 256, 0, rs>>>(ca);
+      k_cc_scan<<<1, 1024, 0, rs>>>(ca);
+      k_cc_fill<<<blocks(ne, 256), 256, 0, rs>>>(ca);
+      k_cc_pairs<<<blocks(ne, 128), 128, 0, rs>>>(ca);
+      k_cc_terms<<<blocks(c.pair_cap, 64), 64, 0, rs>>>(ca);
+    }
+    if (rod_on || contact_on) {
+      Timed t(s, K_ROWS, rs);
+      const int tb = s->x.tune.rows_threads;
+      k_rows_rod<<<blocks(nd, tb), tb, 0, rs>>>(ra);
+    }
+    if (gen_on) {
+      Timed t(s, K_ROWS_GEN, rs);
+      k_rows_gen<<<blocks(nd, 256), 256, 0, rs>>>(rg);
+    }
+    if (ls_on) {
+      k_ls_merit<<<blocks((int64_t)S * 32, 128), 128, 0, rs>>>(la);
+      k_ls_decide<<<blocks(S, 128), 128, 0, rs>>>(la);
+      k_ls_apply<<<blocks(nd, 256), 256, 0, rs>>>(la);
+      if (ws_trial && it == 0) DM_CK(ws_inject(s, rs, s->x.ls_action, s->x.ls_trial));
+    }
+    if (rod_on) {
+      {
+        Timed t(s, K_SOLVE, rs);
+        k_solve_rod<<<s->x.solve_blocks, 32 * s->x.tune.solve_warps, s->x.solve_smem, rs>>>(va);
+      }
+    }
+    if (contact_on) {
+      Timed t(s, K_SOLVE_CONTACT, rs);
+      k_cc_band<<<blocks(nd, 256), 256, 0, rs>>>(ca);
+      const int nc = s->x.cc.n_contact;
+      k_cc_decide<<<blocks(nc, 128), 128, 0, rs>>>(ca, va);
+      for (int c = 0; c < nc; ++c) {
+        const int n = T.sys_ndof[c];  // contact systems are systems 0..nc-1 in order
+        for (int k = 0; k < n; k += kNB) {
+          const int rest = n - k - std::min(kNB, n - k);
+          k_lu_diag<<<1, 256, 0, rs>>>(ca, c, k);
+          if (rest > 0) {
+            k_lu_trsm<<<blocks(2 * rest, 128), 128, 0, rs>>>(ca, c, k);
+            const int t = (rest + 63) / 64;
+            k_lu_gemm<<<dim3(t, t), 256, 0, rs>>>(ca, c, k);
+          }
+        }
+      }
+      k_cc_subst<<<nc, 1024, 0, rs>>>(ca, va);
+    }
+    if (gen_on) {
+      DM_CK(cudaMemsetAsync(d.gen, 0, T.gen_doubles * sizeof(double), rs));
+      if (aa.ntarget > 0) {
+        Timed t(s, K_ASM_GEN, rs);
+        k_assemble_gen<<<blocks(aa.ntarget, 256), 256, 0, rs>>>(aa);
+      }
+      {
+        Timed t(s, K_SOLVE_GEN, rs);
+        if (s->x.n_fast) {
+          const int wf = s->x.wpb_factor, wb = s->x.wpb_back;
+          const size_t sf = s->x.smem_factor / s->x.wpb_factor_max * wf;
+          const size_t sb = s->x.smem_back / s->x.wpb_back_max * wb;
+          if (ga.nlimb)
+            k_gen_limb_factor<<<(ga.nlimb + wf - 1) / wf, 32 * wf, sf, rs>>>(ga);
+          k_gen_border<<<ga.ngen, 32, s->x.border_smem, rs>>>(ga);
+          if (ga.nlimb)
+            k_gen_limb_back<<<(ga.nlimb + wb - 1) / wb, 32 * wb, sb, rs>>>(ga);
+        }
+        if (s->x.n_slow)
+          k_solve_gen<<<blocks((int64_t)ga.ngen * 32, 128), 128, 0, rs>>>(ga);
+      }
+    }
+    DM_CK(cudaGetLastError());
+    return DM_OK;
+  };
+  // Rounds as a CUDA graph (no host round trip between rounds): one while
+  // node whose body is a round followed by k_round_continue.  The learned
+  // guess's trial round (the first, with the injection) runs before the
+  // graph; per-kernel profiling uses the host-driven loop.
+  const bool graph_mode = s->x.graphs && !s->x.prof;
+  if (graph_mode && !s->x.round_graph) {
+    if (!s->x.cap_stream) DM_CK(cudaStreamCreateWithFlags(&s->x.cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    DM_CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    }
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(s->x.cap_stream, cp.conditional.phGraph_out[0], nullptr,
+                                        nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      set_error(std::string("CUDA: round graph: ") + cudaGetErrorString(e));
+      return DM_ERR_CUDA;
+    }
+    int64_t before[DM_NUM_KERNELS];
+    std::copy(s->x.launches, s->x.launches + DM_NUM_KERNELS, before);
+    dm_status rst = round(s->x.cap_stream, 1);
+    if (rst == DM_OK) k_round_continue<<<1, 32, 0, s->x.cap_stream>>>(d.ctrl, max_rounds, h);
+    cudaGraph_t body = nullptr;
+    e = cudaStreamEndCapture(s->x.cap_stream, &body);
+    for (int k = 0; k < DM_NUM_KERNELS; ++k) {
+      s->x.round_launches[k] = s->x.launches[k] - before[k];
+      s->x.launches[k] = before[k];
+    }
+    s->x.round_launches[K_BEGIN] += 1;  // k_round_continue
+    if (rst == DM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&s->x.round_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (rst != DM_OK) return rst;
+    if (e != cudaSuccess) {
+      s->x.round_graph = nullptr;
+      set_error(std::string("CUDA: round graph: ") + cudaGetErrorString(e));
+      return DM_ERR_CUDA;
+    }
+  }
   for (int step = 0; step < nsteps; ++step) {
-    int32_t init[4] = {0, 0, INT_MAX, 0};  // active, failed, first failed, queue
+    int32_t init[8] = {0, 0, INT_MAX, 0, 0, 0, 0, 0};  // active, failed, first failed, queue, rounds
     DM_CK(cudaMemcpyAsync(d.ctrl, init, sizeof(init), cudaMemcpyHostToDevice, st));
     {
       Timed t(s, K_BEGIN, st);
@@ -687,100 +863,23 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       DM_CK(cudaMemsetAsync(s->x.ls_nback, 0, S * sizeof(int32_t), st));
       if (ws_trial) DM_CK(cudaMemsetAsync(la.wstry, 0, S * sizeof(int32_t), st));
     }
-    for (int it = 0; it < max_rounds; ++it) {
-      DM_CK(cudaMemsetAsync(d.sys_res, 0, S * sizeof(unsigned long long), st));
-      DM_CK(cudaMemsetAsync(d.ctrl, 0, sizeof(int32_t), st));
-      DM_CK(cudaMemsetAsync(d.ctrl + 3, 0, sizeof(int32_t), st));
-      {
-        Timed t(s, K_EDGE, st);
-        k_edge<<<blocks(ne, 256), 256, 0, st>>>(ea);
-      }
-      if (T.ground) {
-        Timed t(s, K_NODES, st);
-        k_nodes<<<blocks(nn, 256), 256, 0, st>>>(na);
-      }
-      if (ns > 0) {
-        Timed t(s, K_STENCIL, st);
-        k_stencil<<<blocks(ns, 128), 128, 0, st>>>(ka);
-      }
-      if (contact_on) {
-        Timed t(s, K_CONTACT, st);
-        const auto &c = s->x.cc;
-        DM_CK(cudaMemsetAsync(c.fc, 0, nd * sizeof(double), st));
-        DM_CK(cudaMemsetAsync(c.npairs, 0, sizeof(int32_t), st));
-        DM_CK(cudaMemsetAsync(c.bucket_count, 0, c.table * sizeof(int32_t), st));
-        k_cc_clear<<<blocks(nd, 256), 256, 0, st>>>(ca);
-        k_cc_reset_bw<<<blocks(S, 256), 256, 0, st>>>(ca);
-        k_cc_cells<<<blocks(ne, 256), 256, 0, st>>>(ca);
-        k_cc_scan<<<1, 1024, 0, st>>>(ca);
-        k_cc_fill<<<blocks(ne, 256), 256, 0, st>>>(ca);
-        k_cc_pairs<<<blocks(ne, 128), 128, 0, st>>>(ca);
-        k_cc_terms<<<blocks(c.pair_cap, 64), 64, 0, st>>>(ca);
-      }
-      if (rod_on || contact_on) {
-        Timed t(s, K_ROWS, st);
-        k_rows_rod<<<blocks(nd, 256), 256, 0, st>>>(ra);
-      }
-      if (gen_on) {
-        Timed t(s, K_ROWS_GEN, st);
-        k_rows_gen<<<blocks(nd, 256), 256, 0, st>>>(rg);
-      }
-      if (ls_on) {
-        k_ls_merit<<<blocks((int64_t)S * 32, 128), 128, 0, st>>>(la);
-        k_ls_decide<<<blocks(S, 128), 128, 0, st>>>(la);
-        k_ls_apply<<<blocks(nd, 256), 256, 0, st>>>(la);
-        if (ws_trial && it == 0) DM_CK(ws_inject(s, st, s->x.ls_action, s->x.ls_trial));
-      }
-      if (rod_on) {
-        {
-          Timed t(s, K_SOLVE, st);
-          k_solve_rod<<<s->x.solve_blocks, 128, s->x.solve_smem, st>>>(va);
-        }
-      }
-      if (contact_on) {
-        Timed t(s, K_SOLVE_CONTACT, st);
-        k_cc_band<<<blocks(nd, 256), 256, 0, st>>>(ca);
-        const int nc = s->x.cc.n_contact;
-        k_cc_decide<<<blocks(nc, 128), 128, 0, st>>>(ca, va);
-        for (int c = 0; c < nc; ++c) {
-          const int n = T.sys_ndof[c];  // contact systems are systems 0..nc-1 in order
-          for (int k = 0; k < n; k += kNB) {
-            const int rest = n - k - std::min(kNB, n - k);
-            k_lu_diag<<<1, 256, 0, st>>>(ca, c, k);
-            if (rest > 0) {
-              k_lu_trsm<<<blocks(2 * rest, 128), 128, 0, st>>>(ca, c, k);
-              const int t = (rest + 63) / 64;
-              k_lu_gemm<<<dim3(t, t), 256, 0, st>>>(ca, c, k);
-            }
-          }
-        }
-        k_cc_subst<<<nc, 1024, 0, st>>>(ca, va);
-      }
-      if (gen_on) {
-        DM_CK(cudaMemsetAsync(d.gen, 0, T.gen_doubles * sizeof(double), st));
-        if (aa.ntarget > 0) {
-          Timed t(s, K_ASM_GEN, st);
-          k_assemble_gen<<<blocks(aa.ntarget, 256), 256, 0, st>>>(aa);
-        }
-        {
-          Timed t(s, K_SOLVE_GEN, st);
-          if (s->x.n_fast) {
-            const int wf = s->x.wpb_factor, wb = s->x.wpb_back;
-            if (ga.nlimb)
-              k_gen_limb_factor<<<(ga.nlimb + wf - 1) / wf, 32 * wf, s->x.smem_factor, st>>>(ga);
-            k_gen_border<<<ga.ngen, 32, s->x.border_smem, st>>>(ga);
-            if (ga.nlimb)
-              k_gen_limb_back<<<(ga.nlimb + wb - 1) / wb, 32 * wb, s->x.smem_back, st>>>(ga);
-          }
-          if (s->x.n_slow)
-            k_solve_gen<<<blocks((int64_t)ga.ngen * 32, 128), 128, 0, st>>>(ga);
-        }
-      }
-      DM_CK(cudaGetLastError());
-      DM_CK(cudaMemcpyAsync(s->h_ctrl, d.ctrl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (graph_mode) {
+      // an extra round after convergence (the graph body runs at least once)
+      // finds no active system and changes nothing
+      if (ws_trial) DM_TRY(round(st, 0));
+      DM_CK(cudaGraphLaunch(s->x.round_graph, st));
+      DM_CK(cudaMemcpyAsync(s->h_ctrl, d.ctrl, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
       DM_CK(cudaStreamSynchronize(st));
-      harvest(s);
-      if (s->h_ctrl[0] == 0) break;
+      for (int k = 0; k < DM_NUM_KERNELS; ++k)
+        s->x.launches[k] += (int64_t)s->h_ctrl[4] * s->x.round_launches[k];
+    } else {
+      for (int it = 0; it < max_rounds; ++it) {
+        DM_TRY(round(st, it));
+        DM_CK(cudaMemcpyAsync(s->h_ctrl, d.ctrl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        DM_CK(cudaStreamSynchronize(st));
+        harvest(s);
+        if (s->h_ctrl[0] == 0) break;
+      }
     }
     if (stats || s->h_ctrl[1] > 0) {
       iters.resize(S);
@@ -946,6 +1045,162 @@ dm_status dm_set_frames(dm_system *sys, const double *d1, const double *beta) {
   }
   if (beta)
     DM_CK(cudaMemcpy(sys->d.beta_n, beta, T.n_stencils * sizeof(double), cudaMemcpyHostToDevice));
+  return DM_OK;
+}
+
+dm_status dm_autotune(dm_system *sys, int32_t steps, dm_tuning *out) {
+  if (!sys || steps < 1) {
+    set_error("dm_autotune: bad arguments");
+    return DM_ERR_INVALID_ARG;
+  }
+  auto *s = static_cast<dm_system_ext *>(sys);
+  if (ws_active(s)) {
+    set_error("dm_autotune: detach the learned warm start first (it keeps a state history)");
+    return DM_ERR_INVALID_ARG;
+  }
+  const HostTopology &T = s->T;
+  DevArrays &d = s->d;
+  cudaStream_t st = s->stream;
+  const size_t nd = T.n_dofs, ne = T.n_edges, ns = T.n_stencils;
+  // the committed state, restored before every trial and at the end
+  double *save = nullptr;
+  const size_t nsave = 2 * nd + 6 * ne + ns;
+  DM_CK(cudaMalloc(&save, std::max<size_t>(nsave, 1) * sizeof(double)));
+  struct Part { double *p; size_t n; };
+  const Part parts[] = {{d.qn, nd}, {d.vn, nd}, {d.d1n, 3 * ne}, {d.tn, 3 * ne}, {d.beta_n, ns}};
+  auto copy_state = [&](bool to_save) -> cudaError_t {
+    size_t off = 0;
+    for (const Part &pt : parts) {
+      if (pt.n) {
+        cudaError_t e = to_save ? cudaMemcpyAsync(save + off, pt.p, pt.n * 8, cudaMemcpyDeviceToDevice, st)
+                                : cudaMemcpyAsync(pt.p, save + off, pt.n * 8, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+      }
+      off += pt.n;
+    }
+    return cudaSuccess;
+  };
+  const bool prof_was = s->x.prof;
+  dm_status result = DM_OK;
+  // per-launch time of kernel id over `steps` steps from the saved state
+  // (a failed trial, or a kernel that did not run, gives +inf)
+  auto trial = [&](int id) -> double {
+    if (copy_state(false) != cudaSuccess) return INFINITY;
+    s->x.prof = true;
+    for (int k = 0; k < DM_NUM_KERNELS; ++k) {
+      s->x.launches[k] = 0;
+      s->x.ms[k] = 0.0;
+      s->x.ev_used[k] = false;
+    }
+    if (dm_step(sys, steps, nullptr) != DM_OK) return INFINITY;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return INFINITY;
+    return s->x.launches[id] ? s->x.ms[id] / (double)s->x.launches[id] : INFINITY;
+  };
+  // coordinate search: the phases run one after another, so each kernel's
+  // shape is chosen on its own time, keeping the default unless another
+  // shape is faster by more than 2 %
+  auto pick = [&](int id, int ncand, auto apply) -> double {
+    apply(0);
+    double best = trial(id);
+    int arg = 0;
+    for (int c = 1; c < ncand; ++c) {
+      if (!apply(c)) continue;
+      const double t = trial(id);
+      if (t < 0.98 * best) {
+        best = t;
+        arg = c;
+      }
+    }
+    apply(arg);
+    return best;
+  };
+  double us[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (copy_state(true) != cudaSuccess) result = DM_ERR_CUDA;
+  if (result == DM_OK) trial(K_EDGE);  // warm-up
+  if (result == DM_OK) {
+    auto &tu = s->x.tune;
+    const int e_thr[] = {256, 128, 512};
+    us[0] = 1e3 * pick(K_EDGE, 3, [&](int c) { tu.edge_threads = e_thr[c]; return true; });
+    if (ns > 0) {
+      const int s_thr[] = {128, 64, 128, 64, 32};
+      const int s_per[] = {1, 1, 2, 2, 1};
+      us[1] = 1e3 * pick(K_STENCIL, 5, [&](int c) {
+        tu.stencil_threads = s_thr[c];
+        tu.stencil_per_thread = s_per[c];
+        return true;
+      });
+    }
+    if (s->x.n_rod_sys > 0 || s->x.cc.n_contact > 0) {
+      const int r_thr[] = {256, 128, 64};
+      us[2] = 1e3 * pick(K_ROWS, 3, [&](int c) { tu.rows_threads = r_thr[c]; return true; });
+    }
+    if (s->x.n_rod_sys > 0) {
+      const int w[] = {4, 2, 1, 4, 2, 4};
+      const int b[] = {1, 2, 4, 2, 1, 3};
+      us[3] = 1e3 * pick(K_SOLVE, 6, [&](int c) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_solve_rod, 32 * w[c], (size_t)w[c] * 4 * kSolveRodDoubles * 8) !=
+                cudaSuccess ||
+            per_sm < b[c])
+          return false;
+        set_solve_shape(s, w[c], b[c]);
+        return true;
+      });
+    }
+    if (s->x.n_fast > 0 && !T.lb_n.empty()) {
+      // the factor and back-substitution kernels are timed together
+      const int wf[] = {s->x.wpb_factor_max, 1, 2, 4};
+      us[4] = 1e3 * pick(K_SOLVE_GEN, 4, [&](int c) {
+        if (wf[c] > s->x.wpb_factor_max) return false;
+        s->x.wpb_factor = wf[c];
+        return true;
+      });
+      const int wb[] = {s->x.wpb_back_max, 1, 2, 4};
+      us[5] = 1e3 * pick(K_SOLVE_GEN, 4, [&](int c) {
+        if (wb[c] > s->x.wpb_back_max) return false;
+        s->x.wpb_back = wb[c];
+        return true;
+      });
+    }
+  }
+  // leave the state, the counters and the profiling switch as they were
+  if (copy_state(false) != cudaSuccess) result = DM_ERR_CUDA;
+  cudaStreamSynchronize(st);
+  cudaFree(save);
+  s->x.prof = prof_was;
+  for (int k = 0; k < DM_NUM_KERNELS; ++k) {
+    s->x.launches[k] = 0;
+    s->x.ms[k] = 0.0;
+    s->x.ev_used[k] = false;
+  }
+  cudaMemset(s->x.d_units, 0, DM_NUM_KERNELS * sizeof(unsigned long long));
+  if (s->x.round_graph) {  // launch shapes are baked into the graph
+    cudaGraphExecDestroy(s->x.round_graph);
+    s->x.round_graph = nullptr;
+  }
+  if (out) {
+    const auto &tu = s->x.tune;
+    out->edge_threads = tu.edge_threads;
+    out->stencil_threads = tu.stencil_threads;
+    out->stencil_per_thread = tu.stencil_per_thread;
+    out->rows_threads = tu.rows_threads;
+    out->solve_warps = tu.solve_warps;
+    out->solve_blocks_per_sm = tu.solve_bps;
+    out->limb_factor_warps = s->x.wpb_factor;
+    out->limb_back_warps = s->x.wpb_back;
+    for (int k = 0; k < 8; ++k) out->us_per_launch[k] = us[k];
+  }
+  if (result != DM_OK) set_error("dm_autotune: CUDA error while saving or restoring the state");
+  return result;
+}
+
+dm_status dm_set_graphs(dm_system *sys, int32_t enable) {
+  if (!sys) {
+    set_error("dm_set_graphs: NULL handle");
+    return DM_ERR_INVALID_ARG;
+  }
+  static_cast<dm_system_ext *>(sys)->x.graphs = enable != 0;
   return DM_OK;
 }
 

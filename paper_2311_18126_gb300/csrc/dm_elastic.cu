@@ -22,8 +22,8 @@
 
 namespace dm {
 
-__global__ void k_edge(EdgeArgs a) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+// One edge (the work of one thread); returns early when inactive.
+__device__ __forceinline__ void k_edge_one(EdgeArgs a, const int e) {
   const bool act = e < a.ne && a.sys_active[a.edge_sys[e]];
   count_units(a.units, act);
   if (!act) return;
@@ -85,6 +85,12 @@ __global__ void k_edge(EdgeArgs a) {
   w[8 * NE + e] = fma(be * tz, tz, al);
 }
 
+__global__ void k_edge(EdgeArgs a) {
+  // block-uniform grid-stride loop (count_units synchronises the block)
+  for (int b0 = blockIdx.x * blockDim.x; b0 < a.ne; b0 += gridDim.x * blockDim.x)
+    k_edge_one(a, b0 + threadIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // small vector helpers (FP64)
 // ---------------------------------------------------------------------------
@@ -132,8 +138,8 @@ __device__ __forceinline__ void load_edge(const double *ef, int NE, int e, int s
   m2 = mk(s * ef[10 * NE + e], s * ef[11 * NE + e], s * ef[12 * NE + e]);
 }
 
-__global__ void __launch_bounds__(128) k_stencil(StencilArgs a) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+// One bend-twist stencil (the work of one thread); returns early when inactive.
+__device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
   const bool act = k < a.ns && a.sys_active[a.st_sys[k]];
   count_units(a.units, act);
   if (!act) return;
@@ -443,6 +449,12 @@ __global__ void __launch_bounds__(128) k_stencil(StencilArgs a) {
         }
       Ho[up<11>(p, q) * NS + k] = v;
     }
+}
+
+__global__ void __launch_bounds__(128) k_stencil(StencilArgs a) {
+  // block-uniform grid-stride loop (count_units synchronises the block)
+  for (int b0 = blockIdx.x * blockDim.x; b0 < a.ns; b0 += gridDim.x * blockDim.x)
+    k_stencil_one(a, b0 + threadIdx.x);
 }
 
 }  // namespace dm

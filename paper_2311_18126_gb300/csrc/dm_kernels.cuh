@@ -217,6 +217,7 @@ struct StepArgs {
 __global__ void k_begin_step(StepArgs a);
 __global__ void k_commit(StepArgs a);
 __global__ void k_restore(StepArgs a);
+__global__ void k_round_continue(int32_t *ctrl, int max_rounds, cudaGraphConditionalHandle h);
 __global__ void k_tangents(int ne, const int32_t *edge_a, const int32_t *edge_b,
                            const double *q, double *tn, int32_t *bad);
 

@@ -26,8 +26,8 @@ __device__ __forceinline__ int ksym(int c, int cp) {  // packed 3x3 (xx,xy,xz,yy
   return 3 + (i == 0 ? j : (i == 1 ? 2 + j : 5));
 }
 
-__global__ void __launch_bounds__(256) k_rows_rod(RowArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// One DOF row (the work of one thread); returns early when inactive.
+__device__ __forceinline__ void k_rows_rod_one(RowArgs a, const int i) {
   const bool act = i < a.nd && a.sys_active[a.dof_sys[i]] &&
                    a.sys_kind[a.dof_sys[i]] != SOLVE_GENERAL;
   count_units(a.units, act);
@@ -103,6 +103,12 @@ __global__ void __launch_bounds__(256) k_rows_rod(RowArgs a) {
   // scaled residual, max-reduced per system (order independent)
   const double rr = fabs(f) * a.rscale[i];
   atomicMax(&a.sys_res[s], (unsigned long long)__double_as_longlong(rr));
+}
+
+__global__ void __launch_bounds__(256) k_rows_rod(RowArgs a) {
+  // block-uniform grid-stride loop (count_units synchronises the block)
+  for (int b0 = blockIdx.x * blockDim.x; b0 < a.nd; b0 += gridDim.x * blockDim.x)
+    k_rows_rod_one(a, b0 + threadIdx.x);
 }
 
 // Banded LDL^T solve of J dq = -f for single rods.

@@ -47,6 +47,16 @@ __global__ void k_restore(StepArgs a) {
   if (i < a.nd) a.q[i] = a.qn[i];
 }
 
+// End of one Newton round inside the round graph: counts the round and
+// keeps the graph's while loop going while some system is still active and
+// fewer than max_rounds rounds have run (ctrl[0] = systems still active,
+// ctrl[4] = rounds of this step), so the loop always ends.
+__global__ void k_round_continue(int32_t *ctrl, int max_rounds, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int r = ++ctrl[4];
+  cudaGraphSetConditional(h, (ctrl[0] > 0 && r < max_rounds) ? 1u : 0u);
+}
+
 // Committed tangents recomputed from q (after a state is set).
 __global__ void k_tangents(int ne, const int32_t *edge_a, const int32_t *edge_b,
                            const double *q, double *tn, int32_t *bad) {

@@ -55,6 +55,14 @@ class Profile(C.Structure):
                 ("ms", C.c_double * NUM_KERNELS)]
 
 
+TUNING_FIELDS = ("edge_threads", "stencil_threads", "stencil_per_thread", "rows_threads",
+                 "solve_warps", "solve_blocks_per_sm", "limb_factor_warps", "limb_back_warps")
+
+
+class Tuning(C.Structure):
+    _fields_ = [(f, C.c_int32) for f in TUNING_FIELDS] + [("us_per_launch", C.c_double * 8)]
+
+
 _lib = None
 
 
@@ -92,6 +100,10 @@ def load_library(path=LIB_PATH):
     lib.dm_num_stencils.restype = C.c_int64
     lib.dm_num_edges.argtypes = [H]
     lib.dm_num_edges.restype = C.c_int64
+    lib.dm_autotune.argtypes = [H, C.c_int32, C.POINTER(Tuning)]
+    lib.dm_autotune.restype = C.c_int
+    lib.dm_set_graphs.argtypes = [H, C.c_int32]
+    lib.dm_set_graphs.restype = C.c_int
     lib.dm_set_profiling.argtypes = [H, C.c_int32]
     lib.dm_set_profiling.restype = C.c_int
     lib.dm_get_profile.argtypes = [H, C.POINTER(Profile)]
@@ -317,6 +329,23 @@ class System:
         v = np.ascontiguousarray(np.asarray(qdot, np.float64))
         _check(self._lib.dm_set_state(self._h, q.ctypes.data_as(C.c_void_p),
                                       v.ctypes.data_as(C.c_void_p), len(q), 0))
+
+    def autotune(self, steps=2):
+        """Chooses the launch shapes of the edge, stencil, row, rod-solve
+        and limb-solve kernels by timing candidates on this system from its
+        current state (which is left unchanged); returns the choice and the
+        measured microseconds per launch of the chosen shapes."""
+        t = Tuning()
+        _check(self._lib.dm_autotune(self._h, int(steps), C.byref(t)))
+        out = {f: int(getattr(t, f)) for f in TUNING_FIELDS}
+        out["us_per_launch"] = dict(zip(("edge", "stencil", "rows", "rod_solve",
+                                         "limb_solve_factor", "limb_solve_back"),
+                                        [round(float(x), 2) for x in t.us_per_launch[:6]]))
+        return out
+
+    def set_graphs(self, enable=True):
+        """Newton rounds as one CUDA graph per step (default) or host-driven."""
+        _check(self._lib.dm_set_graphs(self._h, int(bool(enable))))
 
     def set_profiling(self, enable=True):
         _check(self._lib.dm_set_profiling(self._h, int(bool(enable))))
