@@ -380,8 +380,9 @@ typedef struct dm_tuning {
  * solver, limbs per block of the condensation kernels.  Every shape computes
  * the same arithmetic per system.  The committed state, the profiling
  * switch and the counters are restored before returning; `out` (optional,
- * caller-owned) receives the choice.  Rejects a system with a learned warm
- * start attached (DM_ERR_INVALID_ARG).  Synchronises the stream. */
+ * caller-owned) receives the choice.  Rejects a system on which the
+ * learned warm start is enabled (DM_ERR_INVALID_ARG: it keeps a history of
+ * the state).  Synchronises the stream. */
 dm_status dm_autotune(dm_system *sys, int32_t steps, dm_tuning *out);
 dm_status dm_get_profile(dm_system *sys, dm_profile *out);
 const char *dm_kernel_name(int32_t id); /* "" for unused ids */

@@ -152,6 +152,7 @@ struct Extra {
   bool graphs = true;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t round_graph = nullptr;
+  bool graph_ws = false;  // learned warm start on when the graph was captured
   int64_t round_launches[DM_NUM_KERNELS] = {};  // launches of one captured round
   std::vector<int32_t> slot2st;
   int32_t *d_slot2st = nullptr;
@@ -796,6 +797,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
           k_solve_gen<<<blocks((int64_t)ga.ngen * 32, 128), 128, 0, rs>>>(ga);
       }
     }
+    if (ws_on && !ws_trial) DM_CK(ws_fallback(s, rs, s->x.d_dof_sys));
     DM_CK(cudaGetLastError());
     return DM_OK;
   };
@@ -804,7 +806,12 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   // guess's trial round (the first, with the injection) runs before the
   // graph; per-kernel profiling uses the host-driven loop.
   const bool graph_mode = s->x.graphs && !s->x.prof;
+  if (s->x.round_graph && s->x.graph_ws != ws_on) {  // the round's kernels changed
+    cudaGraphExecDestroy(s->x.round_graph);
+    s->x.round_graph = nullptr;
+  }
   if (graph_mode && !s->x.round_graph) {
+    s->x.graph_ws = ws_on;
     if (!s->x.cap_stream) DM_CK(cudaStreamCreateWithFlags(&s->x.cap_stream, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     DM_CK(cudaGraphCreate(&g, 0));
@@ -856,7 +863,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     }
     if (ws_on) {
       Timed t(s, K_WARM, st);
-      DM_CK(ws_predict(s, st, ws_trial));
+      DM_CK(ws_predict(s, st, ws_trial, s->x.d_dof_sys));
     }
     if (ls_on) {
       DM_CK(cudaMemsetAsync(s->x.ls_trial, 0, S * sizeof(int32_t), st));
@@ -906,6 +913,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
                 " failed with status " + std::to_string(code));
       return (dm_status)code;
     }
+    DM_CK(ws_keep_velocity(s, st));
     {
       Timed t(s, K_COMMIT, st);
       k_commit<<<blocks(std::max({nd, ne, ns}), 256), 256, 0, st>>>(sa);
@@ -991,6 +999,7 @@ dm_status dm_set_state(dm_system *sys, const double *q, const double *qdot, size
     if (!is_device) DM_CK(cudaStreamSynchronize(st));
   }
   DM_CK(cudaMemcpyAsync(s->d.q, s->d.qn, s->T.n_dofs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  DM_CK(ws_keep_velocity(s, st));  // no velocity history for a state set from outside
   // committed tangents from the new positions
   DM_CK(cudaMemsetAsync(s->x.d_bad, 0, sizeof(int32_t), st));
   k_tangents<<<blocks(s->T.n_edges, 256), 256, 0, st>>>((int)s->T.n_edges, s->d.edge_a,
@@ -1054,8 +1063,8 @@ dm_status dm_autotune(dm_system *sys, int32_t steps, dm_tuning *out) {
     return DM_ERR_INVALID_ARG;
   }
   auto *s = static_cast<dm_system_ext *>(sys);
-  if (ws_active(s)) {
-    set_error("dm_autotune: detach the learned warm start first (it keeps a state history)");
+  if (s->ws) {
+    set_error("dm_autotune: run it before dm_ws_enable (the warm start keeps a state history)");
     return DM_ERR_INVALID_ARG;
   }
   const HostTopology &T = s->T;

@@ -182,12 +182,20 @@ dm_status run_band_solve(int32_t nsys, const int32_t *dof0, const int32_t *ndof,
 
 bool ws_active(const dm_system *s);  // a network is attached
 // Evaluates the network on the committed state.  defer = false: the guess
-// replaces the extrapolation in q; defer = true: it is kept for ws_inject.
-cudaError_t ws_predict(dm_system *s, cudaStream_t st, bool defer);
+// replaces the extrapolation in q (and the systems it reached are marked for
+// ws_fallback); defer = true: it is kept for ws_inject.
+cudaError_t ws_predict(dm_system *s, cudaStream_t st, bool defer, const int32_t *dof_sys);
+// After a round's solves (no line search): systems started from the learned
+// guess that have not converged in a few iterations restart from the
+// extrapolation.
+cudaError_t ws_fallback(dm_system *s, cudaStream_t st, const int32_t *dof_sys);
 // After the first line-search round: q <- learned guess for every active
 // system, marked as a trial (no solve this round).
 cudaError_t ws_inject(dm_system *s, cudaStream_t st, int32_t *ls_action, int32_t *ls_trial);
 int32_t *ws_trial_flags(dm_system *s);
+// qdot_{n-1} of the previous-correction features <- the current qdot_n
+// (before a commit overwrites it, and after a state is set).
+cudaError_t ws_keep_velocity(dm_system *s, cudaStream_t st);
 
 }  // namespace dm
 

@@ -16,7 +16,17 @@
 //   40..45 natural curvature (kappabar1, kappabar2) at nodes i-1, i, i+1
 //   46..48 gravity dt^2 / l (local);  49 (z_i - z_ground)/h;  50 mu (ground on)
 //   51..54 static: log10 E, log10(h/l), log10 rho, log10(dt^2 EA/(m l))
-// Targets: local (x_i^{n+1} - x_i^pred)/l and theta^{n+1} - theta^pred.
+//   55..58 the previous step's correction dt (qdot_n - qdot_{n-1}) of node i
+//          (local, / l: p) and of the twist of edge i-1 (p_theta), divided by
+//          the segment's scales sigma = max(|p|, |g| dt^2 / l) and
+//          sigma_theta = max(|p_theta|, 1e-9) (p = 0 after a state is set or
+//          when the warm start is enabled)
+//   59..60 log10 sigma, log10 sigma_theta
+// Targets: local (x_i^{n+1} - x_i^pred)/(l sigma) and
+// (theta^{n+1} - theta^pred)/sigma_theta, where x^{n+1} - x^pred =
+// dt (qdot_{n+1} - qdot_n): the correction relative to the last one, so
+// that the network's error is relative to each segment's own correction
+// (corrections differ by orders of magnitude between stiff and soft rods).
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -37,10 +47,12 @@ struct WarmStart {
   int64_t nseg = 0, mpad = 0;
   int32_t *seg_i = nullptr;  // [16][nseg]
   float *seg_f = nullptr;    // [6][nseg]
-  double *basis = nullptr;   // [10][nseg]: t, d1, d2, l
+  double *basis = nullptr;   // [12][nseg]: t, d1, d2, l, sigma, sigma_theta
   double *pred = nullptr;    // [4][nseg]
   uint16_t *X = nullptr;     // [mpad][64] bf16
   double *ql = nullptr;      // learned guess [n_dofs] (line-search trial)
+  double *vprev = nullptr;   // qdot_{n-1} [n_dofs]
+  int32_t *learned_sys = nullptr;  // [n_systems] 1: this step's guess came from the network
   int32_t *wstry = nullptr;  // [n_systems]
   float *norm = nullptr;     // in_mean[64], in_std[64], out_scale[4]
   int *err = nullptr;
@@ -56,7 +68,7 @@ struct FeatArgs {
   int ground;
   const int32_t *seg_i;
   const float *seg_f;
-  const double *qn, *vn, *tn, *d1n, *kbar, *node_h, *node_mu;
+  const double *qn, *vn, *vprev, *tn, *d1n, *kbar, *node_h, *node_mu;
   const int32_t *dof_node;
   double *basis, *pred;
   float *raw;          // mode 0: raw features [nseg][64]
@@ -125,6 +137,26 @@ __global__ void k_ws_features(FeatArgs a) {
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) f[51 + k] = a.seg_f[k * S + s];
+  {
+    double pc[3];
+    const double px = dt * (a.vn[nd] - a.vprev[nd]), py = dt * (a.vn[nd + 1] - a.vprev[nd + 1]),
+                 pz = dt * (a.vn[nd + 2] - a.vprev[nd + 2]);
+    pc[0] = il * (px * t[0] + py * t[1] + pz * t[2]);
+    pc[1] = il * (px * d1[0] + py * d1[1] + pz * d1[2]);
+    pc[2] = il * (px * d2[0] + py * d2[1] + pz * d2[2]);
+    const double gn = sqrt(a.g[0] * a.g[0] + a.g[1] * a.g[1] + a.g[2] * a.g[2]);
+    const double sig = fmax(sqrt(pc[0] * pc[0] + pc[1] * pc[1] + pc[2] * pc[2]),
+                            fmax(gn * dt * dt * il, 1e-30));
+    const double pth = dt * (a.vn[th] - a.vprev[th]);
+    const double sth = fmax(fabs(pth), 1e-9);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f[55 + c] = (float)(pc[c] / sig);
+    f[58] = (float)(pth / sth);
+    f[59] = (float)log10(sig);
+    f[60] = (float)log10(sth);
+    a.basis[10 * S + s] = sig;
+    a.basis[11 * S + s] = sth;
+  }
   // local basis and the extrapolation this segment corrects
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -147,20 +179,38 @@ __global__ void k_ws_features(FeatArgs a) {
 }
 
 __global__ void k_ws_apply(int64_t nseg, const int32_t *seg_i, const double *basis,
-                           const float *Y, const float *norm, double *q) {
+                           const float *Y, const float *norm, double *q,
+                           const int32_t *dof_sys, int32_t *learned_sys) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nseg) return;
   const int64_t S = nseg;
   const int nd = seg_i[s], th = seg_i[S + s], flags = seg_i[14 * S + s];
+  if (learned_sys && flags) learned_sys[dof_sys[nd]] = 1;
   const float *o = norm + 128;
   const double y0 = Y[s * 64] * o[0], y1 = Y[s * 64 + 1] * o[1], y2 = Y[s * 64 + 2] * o[2];
-  const double l = basis[9 * S + s];
+  const double l = basis[9 * S + s] * basis[10 * S + s];
   if (flags & 1)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       q[nd + c] += l * (y0 * basis[c * S + s] + y1 * basis[(3 + c) * S + s] +
                         y2 * basis[(6 + c) * S + s]);
-  if (flags & 2) q[th] += (double)Y[s * 64 + 3] * o[3];
+  if (flags & 2) q[th] += (double)Y[s * 64 + 3] * o[3] * basis[11 * S + s];
+}
+
+// Fallback to the extrapolation: a system whose Newton run from the learned
+// guess has taken kWsRestart iterations without converging starts over from
+// q_n + dt qdot_n (fixed DOFs keep q_n); the iteration count carries on, so
+// this happens once per step.
+constexpr int kWsRestart = 6;
+__global__ void k_ws_fallback(int32_t nd, double dt, const int32_t *dof_sys,
+                              const int32_t *learned_sys, const int32_t *sys_active,
+                              const int32_t *sys_iters, const uint8_t *fixed, const double *qn,
+                              const double *vn, double *q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  const int s = dof_sys[i];
+  if (!learned_sys[s] || !sys_active[s] || sys_iters[s] != kWsRestart) return;
+  q[i] = fixed[i] ? qn[i] : fma(dt, vn[i], qn[i]);
 }
 
 __global__ void k_ws_targets(int64_t nseg, const int32_t *seg_i, const double *basis,
@@ -172,7 +222,7 @@ __global__ void k_ws_targets(int64_t nseg, const int32_t *seg_i, const double *b
   double dx[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) dx[c] = qn[nd + c] - pred[c * S + s];
-  const double il = 1.0 / basis[9 * S + s];
+  const double il = 1.0 / (basis[9 * S + s] * basis[10 * S + s]);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     double v = 0.0;
@@ -180,7 +230,7 @@ __global__ void k_ws_targets(int64_t nseg, const int32_t *seg_i, const double *b
     for (int c = 0; c < 3; ++c) v += dx[c] * basis[(3 * k + c) * S + s];
     tgt[s * 4 + k] = (float)(v * il);
   }
-  tgt[s * 4 + 3] = (float)(qn[th] - pred[3 * S + s]);
+  tgt[s * 4 + 3] = (float)((qn[th] - pred[3 * S + s]) / basis[11 * S + s]);
 }
 
 __global__ void k_ws_gather(int32_t M, const float *feat, const float *tgt, const int64_t *idx,
@@ -295,15 +345,17 @@ dm_status ws_build(dm_system *s, WarmStart *w) {
     return true;
   };
   if (!dal((void **)&w->seg_i, ii.size() * 4) || !dal((void **)&w->seg_f, ff.size() * 4) ||
-      !dal((void **)&w->basis, 10 * S * 8) || !dal((void **)&w->pred, 4 * S * 8) ||
+      !dal((void **)&w->basis, 12 * S * 8) || !dal((void **)&w->pred, 4 * S * 8) ||
       !dal((void **)&w->X, w->mpad * 64 * 2) || !dal((void **)&w->norm, 132 * 4) ||
       !dal((void **)&w->err, 4) || !dal((void **)&w->ql, T.n_dofs * 8) ||
+      !dal((void **)&w->vprev, T.n_dofs * 8) || !dal((void **)&w->learned_sys, T.n_systems * 4) ||
       !dal((void **)&w->wstry, T.n_systems * 4)) {
     set_error("warm start: cudaMalloc failed");
     return DM_ERR_OOM;
   }
   cudaMemcpy(w->seg_i, ii.data(), ii.size() * 4, cudaMemcpyHostToDevice);
   cudaMemcpy(w->seg_f, ff.data(), ff.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(w->vprev, s->d.vn, T.n_dofs * 8, cudaMemcpyDeviceToDevice);
   return cudaDeviceSynchronize() == cudaSuccess ? DM_OK : DM_ERR_CUDA;
 }
 
@@ -323,6 +375,7 @@ static FeatArgs feat_args(dm_system *s, WarmStart *w) {
   a.seg_f = w->seg_f;
   a.qn = s->d.qn;
   a.vn = s->d.vn;
+  a.vprev = w->vprev;
   a.tn = s->d.tn;
   a.d1n = s->d.d1n;
   a.kbar = s->d.kbar;
@@ -336,11 +389,18 @@ static FeatArgs feat_args(dm_system *s, WarmStart *w) {
 
 bool ws_active(const dm_system *s) { return s->ws && s->ws->net && s->ws->nseg > 0; }
 
+cudaError_t ws_keep_velocity(dm_system *s, cudaStream_t st) {
+  if (!s->ws || !s->ws->vprev) return cudaSuccess;
+  return cudaMemcpyAsync(s->ws->vprev, s->d.vn, s->T.n_dofs * sizeof(double),
+                         cudaMemcpyDeviceToDevice, st);
+}
+
 int32_t *ws_trial_flags(dm_system *s) { return s->ws ? s->ws->wstry : nullptr; }
 
-cudaError_t ws_predict(dm_system *s, cudaStream_t st, bool defer) {
+cudaError_t ws_predict(dm_system *s, cudaStream_t st, bool defer, const int32_t *dof_sys) {
   WarmStart *w = s->ws;
   if (!ws_active(s)) return cudaSuccess;
+  if (!defer) cudaMemsetAsync(w->learned_sys, 0, s->T.n_systems * sizeof(int32_t), st);
   FeatArgs a = feat_args(s, w);
   a.X = w->X;
   a.norm = w->norm;
@@ -352,7 +412,18 @@ cudaError_t ws_predict(dm_system *s, cudaStream_t st, bool defer) {
     cudaMemcpyAsync(w->ql, s->d.q, s->T.n_dofs * sizeof(double), cudaMemcpyDeviceToDevice, st);
     dst = w->ql;
   }
-  k_ws_apply<<<nb(w->nseg, 128), 128, 0, st>>>(w->nseg, w->seg_i, w->basis, Y, w->norm, dst);
+  k_ws_apply<<<nb(w->nseg, 128), 128, 0, st>>>(w->nseg, w->seg_i, w->basis, Y, w->norm, dst,
+                                                dof_sys, defer ? nullptr : w->learned_sys);
+  return cudaGetLastError();
+}
+
+cudaError_t ws_fallback(dm_system *s, cudaStream_t st, const int32_t *dof_sys) {
+  WarmStart *w = s->ws;
+  if (!ws_active(s)) return cudaSuccess;
+  const int nd = (int)s->T.n_dofs;
+  k_ws_fallback<<<nb(nd, 256), 256, 0, st>>>(nd, s->p.dt, dof_sys, w->learned_sys,
+                                             s->d.sys_active, s->d.sys_iters, s->d.fixed,
+                                             s->d.qn, s->d.vn, s->d.q);
   return cudaGetLastError();
 }
 

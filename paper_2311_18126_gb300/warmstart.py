@@ -20,7 +20,7 @@ import torch
 
 from . import dismech as dmx
 
-N_FEAT = 55      # meaningful input columns of the 64-wide feature rows
+N_FEAT = 61      # meaningful input columns of the 64-wide feature rows
 N_OUT = 4        # position correction (3, local frame / edge length), twist
 
 

@@ -21,14 +21,14 @@ def _rod_offsets(npr):
     return off
 
 
-def _expected(desc, params, q, v, d1, kbar_slots, npr):
+def _expected(desc, params, q, v, d1, kbar_slots, npr, vprev):
     """Features [S, 64] and extrapolated guesses, from the documented
     definitions (segments: rods in order, nodes i = 1..N-1)."""
     dt = params["dt"]
     g = np.asarray(params["g"])
     off = _rod_offsets(npr)
     lbar = 0.1 / (npr[0] - 1)  # star robots: uniform spacing
-    feats, guess, basis = [], [], []
+    feats, guess, basis, sigmas = [], [], [], []
     e0 = 0
     k0 = 0
     for r, N in enumerate(npr):
@@ -64,13 +64,25 @@ def _expected(desc, params, q, v, d1, kbar_slots, npr):
             f[51] = np.log10(desc["E"][r])
             f[52] = np.log10(h / lbar)
             f[53] = np.log10(desc["rho"][r])
+            # the previous step's correction dt (qdot_n - qdot_{n-1}),
+            # relative to the segment's scales
+            VP = vprev[off[r]:off[r + 1]]
+            pc = B @ (dt * (XV(i) - VP[4 * i:4 * i + 3])) / lbar
+            pth = dt * (V[4 * (i - 1) + 3] - VP[4 * (i - 1) + 3])
+            sig = max(np.linalg.norm(pc), np.linalg.norm(g) * dt * dt / lbar)
+            sth = max(abs(pth), 1e-9)
+            f[55:58] = pc / sig
+            f[58] = pth / sth
+            f[59] = np.log10(sig)
+            f[60] = np.log10(sth)
+            sigmas.append((sig, sth))
             feats.append(f)
             guess.append(np.concatenate([X(i) + dt * XV(i),
                                          [Q[4 * (i - 1) + 3] + dt * V[4 * (i - 1) + 3]]]))
             basis.append(B)
         e0 += N - 1
         k0 += N - 2
-    return np.array(feats), np.array(guess), np.array(basis), lbar
+    return np.array(feats), np.array(guess), np.array(basis), lbar, np.array(sigmas)
 
 
 def test_features_and_targets_match_definitions():
@@ -79,13 +91,14 @@ def test_features_and_targets_match_definitions():
     sys = dmx.System(desc, params)
     npr = list(desc["nodes_per_rod"])
     dt = params["dt"]
+    S = sys.ws_enable()
+    assert S == sum(n - 1 for n in npr)
     for k in range(4):
         sys.set_natural_curvature(0, sys.n_rods, workloads.gait_kbar(gait, k * dt))
+        vprev = sys.get_state()[1]
         sys.step(1)
     kb = workloads.gait_kbar(gait, 4 * dt)
     sys.set_natural_curvature(0, sys.n_rods, kb)
-    S = sys.ws_enable()
-    assert S == sum(n - 1 for n in npr)
     q, v = sys.get_state()
     d1, _ = sys.get_frames()
     feat = torch.zeros((S, 64), dtype=torch.float32, device="cuda")
@@ -96,10 +109,12 @@ def test_features_and_targets_match_definitions():
     torch.cuda.synchronize()
     F = feat.cpu().numpy().astype(np.float64)
     T = tgt.cpu().numpy().astype(np.float64)
-    ef, guess, B, lbar = _expected(desc, params, q, v, d1, kb, npr)
+    ef, guess, B, lbar, sig = _expected(desc, params, q, v, d1, kb, npr, vprev)
     cols = list(range(0, 54))
     np.testing.assert_allclose(F[:, cols], ef[:, cols], rtol=2e-6, atol=2e-6)
-    assert np.all(F[:, 55:] == 0.0)
+    assert np.abs(ef[:, 55:59]).max() > 0.5
+    np.testing.assert_allclose(F[:, 55:61], ef[:, 55:61], rtol=1e-5, atol=1e-5)
+    assert np.all(F[:, 61:] == 0.0)
     # targets: local-frame correction of the guess, rebuilt from q_{n+1}
     q1, _ = sys.get_state()
     off = _rod_offsets(npr)
@@ -110,9 +125,10 @@ def test_features_and_targets_match_definitions():
             want.append(np.concatenate([Q[4 * i:4 * i + 3], [Q[4 * (i - 1) + 3]]]))
     want = np.array(want)
     dx = want[:, :3] - guess[:, :3]
-    loc = np.einsum("sij,sj->si", B, dx) / lbar
+    loc = np.einsum("sij,sj->si", B, dx) / lbar / sig[:, :1]
     np.testing.assert_allclose(T[:, :3], loc, rtol=1e-5, atol=1e-7 * np.abs(loc).max())
-    np.testing.assert_allclose(T[:, 3], want[:, 3] - guess[:, 3], rtol=1e-5, atol=1e-9)
+    tw = (want[:, 3] - guess[:, 3]) / sig[:, 1]
+    np.testing.assert_allclose(T[:, 3], tw, rtol=1e-5, atol=1e-7 * np.abs(tw).max())
     assert np.abs(loc).max() > 0.0
 
 
