@@ -229,7 +229,8 @@ dm_status dm_solve_band_noalloc(int32_t nsys, const int32_t *sys_dof0,
  * device arrays, bias [N] fp32 device array or NULL, C [M][N] row-major bf16
  * (out_f32 = 0) or fp32 (out_f32 != 0), act = ReLU when relu != 0.
  * Accumulation is fp32 in tensor memory (tcgen05).  Requires M % 128 == 0,
- * K % 64 == 0, 16 <= N <= 256, N % 16 == 0.  Synchronises `stream`. */
+ * K % 64 == 0, 16 <= N <= 256, N % 16 == 0 and 16-byte aligned A, B, C
+ * (DM_ERR_INVALID_ARG otherwise).  Synchronises `stream`. */
 dm_status dm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A, const void *B,
                        const float *bias, void *C, int32_t relu, int32_t out_f32,
                        void *stream);

@@ -12,7 +12,7 @@
 // the fp32 accumulator in tensor memory, tcgen05.commit signals an mbarrier,
 // and the four warps read their 32 accumulator lanes back with tcgen05.ld
 // for the epilogue (bias, ReLU, conversion).  Two shared-memory stages let
-// the next tile load while the tensor core works on the current one.
+// the next K block load (cp.async) while the tensor core works on the current one.
 // Every mbarrier wait is bounded: on timeout the kernel records an error
 // flag, skips the rest and frees its tensor memory.
 #include <cuda_bf16.h>
@@ -89,17 +89,26 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
       : "memory");
 }
 
-// Stores a rows x 64 bf16 tile (row-major source with leading dimension ld
+// Copies a rows x 64 bf16 tile (row-major source with leading dimension ld
 // elements) into the canonical no-swizzle K-major layout: core matrix
 // (r/8, k/8) at ((r/8) * 8 + k/8) * 128 bytes, row r%8 at 16-byte stride.
+// Asynchronous 16-byte copies (cp.async), so that every thread's loads are
+// in flight together; the caller commits the group and waits on it.
 __device__ __forceinline__ void stage_tile(char *dst, const uint16_t *src, int rows, int ld,
                                            int k0, int tid) {
   const int chunks = rows * (kBK / 8);  // 16-byte chunks
   for (int c = tid; c < chunks; c += kThreads) {
     const int r = c >> 3, kc = c & 7;
-    const uint4 v = *reinterpret_cast<const uint4 *>(src + (size_t)r * ld + k0 + kc * 8);
-    *reinterpret_cast<uint4 *>(dst + ((r >> 3) * 8 + kc) * 128 + (r & 7) * 16) = v;
+    const uint16_t *g = src + (size_t)r * ld + k0 + kc * 8;
+    const uint32_t d = smem_u32(dst + ((r >> 3) * 8 + kc) * 128 + (r & 7) * 16);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
   }
+}
+
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 }  // namespace
@@ -113,8 +122,9 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const uint16_t *__restri
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kBM;
   const int a_bytes = kBM * kBK * 2, b_bytes = N * kBK * 2;
-  char *sA[2] = {smem, smem + a_bytes + b_bytes};
-  char *sB[2] = {smem + a_bytes, smem + 2 * a_bytes + b_bytes};
+  // stage s: A tile at s * (a_bytes + b_bytes), B tile right after it
+  auto sA = [&](int st) { return smem + st * (a_bytes + b_bytes); };
+  auto sB = [&](int st) { return smem + a_bytes + st * (a_bytes + b_bytes); };
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * (a_bytes + b_bytes));
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2);
   uint32_t ncols = 32;
@@ -140,22 +150,33 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const uint16_t *__restri
   bool ok = true;
   uint32_t phase[2] = {0, 0};
 
+  // two-stage pipeline: the copies of block kb + 1 are in flight while the
+  // tensor core multiplies block kb
+  stage_tile(sA(0), A + (size_t)m0 * K, kBM, K, 0, tid);
+  stage_tile(sB(0), B, N, K, 0, tid);
+  cp_commit();
   for (int kb = 0; kb < nk && ok; ++kb) {
     const int s = kb & 1;
-    // the stage was last read by the MMAs of block kb - 2
-    if (kb >= 2) {
-      const bool w = mbar_wait(&bar[s], phase[s]);
-      phase[s] ^= 1u;
-      ok = __syncthreads_and(w) != 0;  // uniform decision: no thread is left behind
-      if (!ok) break;
+    if (kb + 1 < nk) {
+      // stage s^1 was last read by the MMAs of block kb - 1
+      if (kb >= 1) {
+        const bool w = mbar_wait(&bar[s ^ 1], phase[s ^ 1]);
+        phase[s ^ 1] ^= 1u;
+        ok = __syncthreads_and(w) != 0;  // uniform decision: no thread is left behind
+        if (!ok) break;
+      }
+      stage_tile(sA(s ^ 1), A + (size_t)m0 * K, kBM, K, (kb + 1) * kBK, tid);
+      stage_tile(sB(s ^ 1), B, N, K, (kb + 1) * kBK, tid);
+      cp_commit();
+      cp_wait<1>();  // block kb has landed (block kb + 1 may still be in flight)
+    } else {
+      cp_wait<0>();
     }
-    stage_tile(sA[s], A + (size_t)m0 * K, kBM, K, kb * kBK, tid);
-    stage_tile(sB[s], B, N, K, kb * kBK, tid);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(sA[s]), b0 = smem_u32(sB[s]);
+      const uint32_t a0 = smem_u32(sA(s)), b0 = smem_u32(sB(s));
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk) {
         // K = 16 per instruction = two 8-element core matrices (256 bytes)
@@ -173,39 +194,46 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const uint16_t *__restri
     const bool w = ok ? mbar_wait(&bar[sl], phase[sl]) : false;
     ok = __syncthreads_and(w) != 0;
   }
+  cp_wait<0>();  // nothing left in flight on an early exit
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (!ok) {
     if (lane == 0) atomicExch(err, 1);
   } else {
     // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
+    // (16 columns per tcgen05.ld: N is a multiple of 16)
     const int row = m0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < N; c0 += 8) {
-      uint32_t r[8];
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
       asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+          "%10, %11, %12, %13, %14, %15}, [%16];"
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-            "=r"(r[6]), "=r"(r[7])
+            "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+            "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      float v[8];
+      float v[16];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < 16; ++j) {
         v[j] = __uint_as_float(r[j]) + (bias ? bias[c0 + j] : 0.0f);
         if (relu) v[j] = fmaxf(v[j], 0.0f);
       }
       if (row < M) {
         if (out_f32) {
-          float *o = reinterpret_cast<float *>(C) + (size_t)row * N + c0;
+          float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(C) + (size_t)row * N + c0);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) o[j] = v[j];
+          for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         } else {
-          uint16_t *o = reinterpret_cast<uint16_t *>(C) + (size_t)row * N + c0;
+          uint32_t w[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const __nv_bfloat16 b = __float2bfloat16_rn(v[j]);
-            o[j] = *reinterpret_cast<const uint16_t *>(&b);
+            const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            w[j] = *reinterpret_cast<const uint32_t *>(&b);
           }
+          uint4 *o = reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(C) + (size_t)row * N + c0);
+          o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          o[1] = make_uint4(w[4], w[5], w[6], w[7]);
         }
       }
     }
@@ -244,8 +272,10 @@ extern "C" dm_status dm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A
                                   const float *bias, void *C, int32_t relu, int32_t out_f32,
                                   void *stream) {
   using namespace dm;
-  if (!A || !B || !C || !check_gemm_shape(M, N, K)) {
-    set_error("dm_gemm_bf16: need M % 128 == 0, K % 64 == 0, N in [16, 256] with N % 16 == 0");
+  if (!A || !B || !C || !check_gemm_shape(M, N, K) ||
+      (((uintptr_t)A | (uintptr_t)B | (uintptr_t)C) & 15)) {
+    set_error("dm_gemm_bf16: need M % 128 == 0, K % 64 == 0, N in [16, 256] with N % 16 == 0 "
+              "and 16-byte aligned A, B, C");
     return DM_ERR_INVALID_ARG;
   }
   int *err = nullptr;
