@@ -75,12 +75,17 @@ def parse():
     ap.add_argument("--rods", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="uneven_rods",
-                    choices=["uneven_rods", "star_robots", "coil", "warm_start", "calibration"],
+                    choices=["uneven_rods", "star_robots", "coil", "warm_start", "calibration",
+                             "mlp"],
                     help="uneven_rods: the headline batch (default); star_robots: limbed "
                          "robots on the ground with a gait; coil: edge-edge self-contact; "
                          "warm_start: learned vs extrapolated Newton guess on star robots; "
-                         "calibration: adjoint gradient of a 500-step star-robot rollout")
+                         "calibration: adjoint gradient of a 500-step star-robot rollout; "
+                         "mlp: the warm-start network's tensor-core inference and training "
+                         "at the headline batch's segment count")
     ap.add_argument("--robots", type=int, default=1024)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes (for profiler launch lists)")
     return ap.parse_args()
 
 
@@ -242,7 +247,7 @@ def run_ours(args):
             import torch.distributed as tdist
             tdist.barrier()
 
-    tuning = sysm.autotune(steps=2)
+    tuning = None if args.no_autotune else sysm.autotune(steps=2)
     for _ in range(args.warmup):
         sysm.step(1, stats=False)
     torch.cuda.synchronize()
@@ -505,7 +510,7 @@ def run_other(args):
         sysm = System(desc, params)
         if controls is not None:
             sysm.set_natural_curvature(0, R, controls(0))
-        tuning = sysm.autotune(steps=2)
+        tuning = None if args.no_autotune else sysm.autotune(steps=2)
         for k in range(warm):
             if controls is not None:
                 sysm.set_natural_curvature(0, R, controls(k))
@@ -655,12 +660,96 @@ def run_calibration(args):
         print(json.dumps(line))
 
 
+def run_mlp(args):
+    """The warm-start network (4 layers 64 -> 256 -> 256 -> 256 -> 64, BF16
+    operands, FP32 accumulation in tensor memory): inference over the
+    segments of the 4096-rod headline batch and Adam training steps at the
+    training batch size; the tensor-core roofline against the measured BF16
+    peak."""
+    import torch
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    from paper_2311_18126_gb300 import ensure_built, dismech as dmx
+    ensure_built()
+    M = 444544            # 444456 segments of the 4096-rod batch, padded to 128
+    B = 16384             # training batch
+    widths = [64, 256, 256, 256, 64]
+    fwd = 2 * sum(a * b for a, b in zip(widths[:-1], widths[1:]))  # flops per row
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1000 + rank)
+    X = torch.randn((M, 64), generator=g, device="cuda").to(torch.bfloat16)
+    out = torch.empty((M, 64), dtype=torch.float32, device="cuda")
+    Yt = torch.randn((B, 4), generator=g, device="cuda")
+    mlp = dmx.MLP(61, 4, seed=1)
+
+    def timed(fn, n):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    clk = Clocks(local)
+    clk.start()
+    ms_f = timed(lambda: mlp.forward(X, out), args.steps)
+    ms_t = timed(lambda: mlp.train_step(X[:B], Yt, 1e-4), args.steps)
+    clocks = clk.stop()
+    ms_f = max_over_ranks(ms_f, ws, "cuda")
+    peak = None
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peak = json.load(open(pk)).get("bf16_tflops")
+    src = "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)" if peak else "fallback 1900"
+    peak = peak or 1900.0
+    ach = fwd * M / (ms_f * 1e-3) / 1e12
+    ach_t = 3 * fwd * B / (ms_t * 1e-3) / 1e12
+    # end to end: features from pinned host memory in, outputs back
+    hX = torch.empty((M, 64), dtype=torch.bfloat16, pin_memory=True)
+    hY = torch.empty((M, 64), dtype=torch.float32, pin_memory=True)
+    hX.copy_(X)
+
+    def e2e():
+        X.copy_(hX, non_blocking=True)
+        mlp.forward(X, out)
+        hY.copy_(out, non_blocking=True)
+    ms_e = timed(e2e, max(3, args.steps // 2))
+    line = {"metric": "warm-start network inference, segments/s", "value": ws * M / (ms_f * 1e-3),
+            "unit": "segments/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_f, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": "mlp: 4 layers 64-256-256-256-64 over %d rows (the segments "
+                                   "of the 4096-rod batch); training batch %d" % (M, B),
+                       "l2": "inputs and activations (0.9 GB) exceed L2"},
+            "clocks": clocks,
+            "e2e": {"value": ws * M / (ms_e * 1e-3), "unit": "segments/s",
+                    "h2d_bytes_per_step": M * 64 * 2, "d2h_bytes_per_step": M * 64 * 4},
+            "gpu_launches": 4 * args.steps,
+            "roofline": {"bound": "tensor", "kernel": "k_gemm_bf16 (4 layers)",
+                         "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "peak_source": src, "flops_per_row": fwd, "rows_per_launch": M,
+                         "traffic": None},
+            "training": {"ms_per_step": ms_t, "samples_per_s": B / (ms_t * 1e-3),
+                         "tflops": ach_t, "frac": ach_t / peak,
+                         "note": "forward + backward (data and weight gradients) + Adam"}}
+    if rank == 0:
+        print(json.dumps(line))
+    mlp.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "calibration":
         run_calibration(args)
+    elif args.workload == "mlp":
+        run_mlp(args)
     elif args.workload != "uneven_rods":
         run_other(args)
     else:

@@ -113,14 +113,18 @@ __device__ __forceinline__ void cp_wait() {
 
 }  // namespace
 
+// Split K (gridDim.y > 1): CTA (x, z) reduces K columns [z kchunk, (z+1) kchunk)
+// and writes its fp32 partial tile to C + z M N (k_sum_splits adds them).
 __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const uint16_t *__restrict__ A,
                                                         const uint16_t *__restrict__ B,
                                                         const float *__restrict__ bias, void *C,
                                                         int M, int N, int K, int relu,
-                                                        int out_f32, int *err) {
+                                                        int out_f32, int *err, int kchunk) {
   extern __shared__ __align__(1024) char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kBM;
+  const int kz = blockIdx.y * kchunk;  // first K column of this CTA
+  if (gridDim.y > 1) C = reinterpret_cast<float *>(C) + (size_t)blockIdx.y * M * N;
   const int a_bytes = kBM * kBK * 2, b_bytes = N * kBK * 2;
   // stage s: A tile at s * (a_bytes + b_bytes), B tile right after it
   auto sA = [&](int st) { return smem + st * (a_bytes + b_bytes); };
@@ -146,14 +150,14 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const uint16_t *__restri
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = make_idesc(kBM, N);
-  const int nk = K / kBK;
+  const int nk = kchunk / kBK;
   bool ok = true;
   uint32_t phase[2] = {0, 0};
 
   // two-stage pipeline: the copies of block kb + 1 are in flight while the
   // tensor core multiplies block kb
-  stage_tile(sA(0), A + (size_t)m0 * K, kBM, K, 0, tid);
-  stage_tile(sB(0), B, N, K, 0, tid);
+  stage_tile(sA(0), A + (size_t)m0 * K, kBM, K, kz, tid);
+  stage_tile(sB(0), B, N, K, kz, tid);
   cp_commit();
   for (int kb = 0; kb < nk && ok; ++kb) {
     const int s = kb & 1;
@@ -165,8 +169,8 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const uint16_t *__restri
         ok = __syncthreads_and(w) != 0;  // uniform decision: no thread is left behind
         if (!ok) break;
       }
-      stage_tile(sA(s ^ 1), A + (size_t)m0 * K, kBM, K, (kb + 1) * kBK, tid);
-      stage_tile(sB(s ^ 1), B, N, K, (kb + 1) * kBK, tid);
+      stage_tile(sA(s ^ 1), A + (size_t)m0 * K, kBM, K, kz + (kb + 1) * kBK, tid);
+      stage_tile(sB(s ^ 1), B, N, K, kz + (kb + 1) * kBK, tid);
       cp_commit();
       cp_wait<1>();  // block kb has landed (block kb + 1 may still be in flight)
     } else {
@@ -244,11 +248,23 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const uint16_t *__restri
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
+// out[i] = sum over z < nsplit of part[z n + i] (fixed order: deterministic).
+__global__ void k_sum_splits(int64_t n, int nsplit, const float *part, float *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float acc = 0.0f;
+  for (int z = 0; z < nsplit; ++z) acc += part[(size_t)z * n + i];
+  out[i] = acc;
+}
+
 size_t gemm_smem_bytes(int N) { return 2 * (size_t)(kBM * kBK * 2 + N * kBK * 2) + 64; }
 
 // Launches k_gemm_bf16; err: device int (set to 1 on a barrier timeout).
+// ksplit > 1: fp32 output only, the partial tiles go to `work` (ksplit M N
+// floats) and are summed into C; K / ksplit must be a multiple of 64.
 cudaError_t launch_gemm_bf16(int M, int N, int K, const void *A, const void *B, const float *bias,
-                             void *C, int relu, int out_f32, int *err, cudaStream_t st) {
+                             void *C, int relu, int out_f32, int *err, cudaStream_t st,
+                             int ksplit, float *work) {
   static bool attr_set = false;
   const size_t smem = gemm_smem_bytes(256);
   if (!attr_set) {
@@ -257,8 +273,16 @@ cudaError_t launch_gemm_bf16(int M, int N, int K, const void *A, const void *B, 
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  if (ksplit > 1) {
+    if (!out_f32 || relu || bias || !work || K % (ksplit * kBK)) return cudaErrorInvalidValue;
+    k_gemm_bf16<<<dim3(M / kBM, ksplit), kThreads, gemm_smem_bytes(N), st>>>(
+        (const uint16_t *)A, (const uint16_t *)B, nullptr, work, M, N, K, 0, 1, err, K / ksplit);
+    const int64_t n = (int64_t)M * N;
+    k_sum_splits<<<(int)((n + 255) / 256), 256, 0, st>>>(n, ksplit, work, (float *)C);
+    return cudaGetLastError();
+  }
   k_gemm_bf16<<<M / kBM, kThreads, gemm_smem_bytes(N), st>>>(
-      (const uint16_t *)A, (const uint16_t *)B, bias, C, M, N, K, relu, out_f32, err);
+      (const uint16_t *)A, (const uint16_t *)B, bias, C, M, N, K, relu, out_f32, err, K);
   return cudaGetLastError();
 }
 
@@ -285,7 +309,7 @@ extern "C" dm_status dm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A
   }
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
-  if (e == cudaSuccess) e = launch_gemm_bf16(M, N, K, A, B, bias, C, relu, out_f32, err, st);
+  if (e == cudaSuccess) e = launch_gemm_bf16(M, N, K, A, B, bias, C, relu, out_f32, err, st, 1, nullptr);
   int h = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

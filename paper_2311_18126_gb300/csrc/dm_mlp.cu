@@ -20,7 +20,8 @@
 
 namespace dm {
 cudaError_t launch_gemm_bf16(int M, int N, int K, const void *A, const void *B, const float *bias,
-                             void *C, int relu, int out_f32, int *err, cudaStream_t st);
+                             void *C, int relu, int out_f32, int *err, cudaStream_t st,
+                             int ksplit = 1, float *work = nullptr);
 }
 
 using namespace dm;
@@ -99,11 +100,32 @@ __global__ void k_relu_back(int n, const uint16_t *H, uint16_t *dH, float *dH32)
 }
 // bias gradient: column sums of an M x N fp32 matrix (one thread per column,
 // fixed summation order)
-__global__ void k_colsum(int M, int N, const float *G, float *out) {
+// Column sums of G [M][N] in two passes with a fixed summation order:
+// k_colsum_part gives block (x, y) columns 32x.. and rows y, y + R, ...
+// (R = gridDim.y * 8), 8 row lanes per column, partials [gridDim.y][N];
+// k_colsum_final adds the partials.
+constexpr int kColChunks = 64;
+__global__ void k_colsum_part(int M, int N, const float *G, float *part) {
+  __shared__ float red[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int stride = gridDim.y * 8;
+  float s = 0.0f;
+  if (c < N)
+    for (int r = blockIdx.y * 8 + threadIdx.y; r < M; r += stride) s += G[(size_t)r * N + c];
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < N) {
+    float t = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+    part[(size_t)blockIdx.y * N + c] = t;
+  }
+}
+__global__ void k_colsum_final(int N, int chunks, const float *part, float *out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
   float s = 0.0f;
-  for (int r = 0; r < M; ++r) s += G[(size_t)r * N + c];
+  for (int z = 0; z < chunks; ++z) s += part[(size_t)z * N + c];
   out[c] = s;
 }
 // Adam on FP32 master parameters; mask zeroes the padded entries
@@ -137,6 +159,7 @@ struct dm_mlp {
   uint16_t *act[kLayers + 1] = {};  // act[0] = input X (not owned), act[l+1] layer l out
   uint16_t *actT = nullptr, *dA = nullptr, *dAT = nullptr, *dA2 = nullptr;
   float *out32 = nullptr, *dY32 = nullptr, *d32 = nullptr;
+  float *splitws = nullptr;  // split-K partial weight gradients [kMaxSplit][256][256]
   double *loss = nullptr;
   int *err = nullptr;
   int64_t step = 0;
@@ -158,7 +181,19 @@ dm_status mlp_alloc(dm_mlp *m, T **p, size_t n) {
   return DM_OK;
 }
 
+// K chunks of the weight-gradient GEMMs for a batch of M rows: up to
+// kMaxSplit chunks of at least two 64-column blocks, dividing M exactly.
+constexpr int kMaxSplit = 128;
+int split_for(int M) {
+  int ks = 1;
+  while (ks < kMaxSplit && M % (2 * ks * 128) == 0) ks *= 2;
+  return ks;
+}
+
 dm_status ensure_batch(dm_mlp *m, int M) {
+  if (!m->splitws &&
+      cudaMalloc(&m->splitws, (size_t)kMaxSplit * kHid * kHid * sizeof(float)) != cudaSuccess)
+    return DM_ERR_OOM;
   if (M <= m->cap) return DM_OK;
   for (int l = 1; l <= kLayers; ++l) {
     if (m->act[l]) {
@@ -281,7 +316,7 @@ void dm_mlp_destroy(dm_mlp *m) {
   for (int l = 1; l <= kLayers; ++l)
     if (m->act[l]) cudaFree(m->act[l]);
   for (void *p : {(void *)m->actT, (void *)m->dA, (void *)m->dAT, (void *)m->dA2,
-                  (void *)m->out32, (void *)m->dY32, (void *)m->d32})
+                  (void *)m->out32, (void *)m->dY32, (void *)m->d32, (void *)m->splitws})
     if (p) cudaFree(p);
   delete m;
 }
@@ -371,15 +406,23 @@ dm_status dm_mlp_train_step(dm_mlp *m, const void *X, const float *Y, int32_t M,
     dim3 blk(32, 8);
     k_transpose_bf16<<<dim3(nb(fi, 32), nb(M, 32)), blk, 0, st>>>(M, fi, m->act[l], m->actT);
     k_transpose_bf16<<<dim3(nb(fo, 32), nb(M, 32)), blk, 0, st>>>(M, fo, dcur, m->dAT);
+    // the batch reduction is split over K chunks so that the tiny M x N
+    // tile grid (two row tiles) still fills the GPU
+    const int ks = split_for(M);
     if (fo % 128 == 0) {
-      if (launch_gemm_bf16(fo, fi, M, m->dAT, m->actT, nullptr, m->gW[l], 0, 1, m->err, st))
+      if (launch_gemm_bf16(fo, fi, M, m->dAT, m->actT, nullptr, m->gW[l], 0, 1, m->err, st, ks,
+                           m->splitws))
         return DM_ERR_CUDA;
     } else {
-      if (launch_gemm_bf16(fi, fo, M, m->actT, m->dAT, nullptr, m->gWt[l], 0, 1, m->err, st))
+      if (launch_gemm_bf16(fi, fo, M, m->actT, m->dAT, nullptr, m->gWt[l], 0, 1, m->err, st, ks,
+                           m->splitws))
         return DM_ERR_CUDA;
       k_transpose_f32<<<nb(fi * fo, 256), 256, 0, st>>>(fi, fo, m->gWt[l], m->gW[l]);
     }
-    k_colsum<<<nb(fo, 128), 128, 0, st>>>(M, fo, dcur32, m->gb[l]);
+    // bias gradient (partials in the split-K workspace, free again here)
+    k_colsum_part<<<dim3(nb(fo, 32), kColChunks), dim3(32, 8), 0, st>>>(M, fo, dcur32,
+                                                                       m->splitws);
+    k_colsum_final<<<nb(fo, 128), 128, 0, st>>>(fo, kColChunks, m->splitws, m->gb[l]);
     if (l > 0) {
       // dA_in [M][fi] = dY [M][fo] * W^T: B = W^T as [fi][fo]
       uint16_t *dnext = (dcur == m->dA) ? m->dA2 : m->dA;
