@@ -75,11 +75,12 @@ def parse():
     ap.add_argument("--rods", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="uneven_rods",
-                    choices=["uneven_rods", "star_robots", "coil", "warm_start", "calibration",
-                             "mlp"],
+                    choices=["uneven_rods", "star_robots", "coil", "warm_start",
+                             "warm_start_rods", "calibration", "mlp"],
                     help="uneven_rods: the headline batch (default); star_robots: limbed "
                          "robots on the ground with a gait; coil: edge-edge self-contact; "
                          "warm_start: learned vs extrapolated Newton guess on star robots; "
+                         "warm_start_rods: the same on the headline batch of uneven rods; "
                          "calibration: adjoint gradient of a 500-step star-robot rollout; "
                          "mlp: the warm-start network's tensor-core inference and training "
                          "at the headline batch's segment count")
@@ -452,6 +453,12 @@ def run_other(args):
                           "ground, gait kappabar, dt=5e-3 s, line search" % args.robots,
                           "rods_per_gpu": len(desc["nodes_per_rod"]), "seed": seed,
                           "l2": "no flush: per-iteration working set exceeds L2 at 1024 robots"}
+    elif args.workload == "warm_start_rods":
+        # the headline batch (seed 2); training batches of seeds 1000+
+        desc, params, kbar = workloads.uneven_rods(n_rods=args.rods, seed=rank_seed(rank))
+        controls = lambda k: kbar
+        line["config"] = {"workload": WORKLOAD, "rods_per_gpu": args.rods,
+                          "l2": "no flush: per-iteration working set (~0.7 GB) exceeds L2"}
     else:
         desc, params, _ = workloads.coil(N=500)
         controls = None
@@ -461,19 +468,29 @@ def run_other(args):
     R = len(desc["nodes_per_rod"])
     warm = args.warmup if args.workload != "coil" else max(args.warmup, 400)
     line["warmup"] = warm
-    if args.workload == "warm_start":
+    if args.workload in ("warm_start", "warm_start_rods"):
         from paper_2311_18126_gb300 import warmstart as wsm
-        tdesc, tparams, tgait = workloads.star_robots(n_robots=max(args.robots // 4, 64),
-                                                      seed=1000 + rank)
+        if args.workload == "warm_start":
+            tdesc, tparams, tgait = workloads.star_robots(n_robots=max(args.robots // 4, 64),
+                                                          seed=1000 + rank)
+            tctl = lambda k: workloads.gait_kbar(tgait, k * dt)
+            tsteps, every = 400, 2
+            tnote = "%d robots x 400 steps (every 2nd step sampled)" % max(args.robots // 4, 64)
+        else:
+            tdesc, tparams, tkbar = workloads.uneven_rods(n_rods=1024, seed=1000 + rank)
+            tctl = lambda k: tkbar
+            tsteps, every = 160, 1
+            tnote = "1024 uneven rods of seed 1000 x 160 steps from rest"
         tsys = System(tdesc, tparams)
-        feats, tgts = wsm.collect(tsys, 400, controls=lambda k: workloads.gait_kbar(tgait, k * dt),
-                                  every=2)
+        feats, tgts = wsm.collect(tsys, tsteps, controls=tctl, every=every)
         tsys.close()
         mlp, norm, losses = wsm.train(feats, tgts, iters=4000, batch=16384, seed=1)
         del feats, tgts
         arms = {}
         for label, model in (("extrapolation", None), ("learned", mlp)):
             sysm = System(desc, params)
+            sysm.set_natural_curvature(0, R, controls(0))
+            tuning = None if args.no_autotune else sysm.autotune(steps=2)
             if model is not None:
                 sysm.ws_enable()
                 sysm.ws_set_model(model, norm)
@@ -491,10 +508,35 @@ def run_other(args):
             arms[label] = {"value": job_rate(ws, R, args.steps, ms * 1e-3),
                            "ms_per_step": ms / args.steps,
                            "iters_per_rod_step": float(its.mean()),
+                           "iters_histogram": np.bincount(its.ravel()).tolist(),
                            "slowest_per_step": float(its.max(1).mean()),
-                           "gpu_launches": int(n_launch),
+                           "gpu_launches": int(n_launch), "autotune": tuning,
                            "kernels": _kernel_table(sysm.get_profile()), "clocks": clocks}
             sysm.set_profiling(False)
+            if model is not None:
+                # end to end through the C ABI: pinned host state in and out
+                _restore(sysm, snap)
+                n = sysm.n_state
+                hq = torch.empty(n, dtype=torch.float64, pin_memory=True)
+                hv = torch.empty(n, dtype=torch.float64, pin_memory=True)
+                hq.numpy()[:], hv.numpy()[:] = snap[0], snap[1]
+                e2e_steps = max(3, args.steps // 2)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for i in range(e2e_steps):
+                    sysm.set_natural_curvature(0, R, controls(warm + i))
+                    sysm.set_state(hq.numpy(), hv.numpy())
+                    sysm.step(1, stats=False)
+                    qq, vv = sysm.get_state()
+                    hq.numpy()[:] = qq
+                    hv.numpy()[:] = vv
+                torch.cuda.synchronize()
+                te = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
+                arms[label]["e2e"] = {"value": job_rate(ws, R, e2e_steps, te), "unit": UNIT,
+                                      "h2d_bytes_per_step": 2 * n * 8,
+                                      "d2h_bytes_per_step": 2 * n * 8,
+                                      "note": "setting the state resets the velocity history "
+                                              "of the previous-correction features"}
             sysm.close()
         line.update({"value": arms["learned"]["value"],
                      "ms_per_step": arms["learned"]["ms_per_step"],
@@ -503,9 +545,12 @@ def run_other(args):
                                  "train_loss": [losses[0], losses[-1]], "arms": arms},
                      "clocks": arms["learned"]["clocks"],
                      "gpu_launches": arms["learned"]["gpu_launches"],
-                     "e2e": None, "roofline": None})
-        line["config"]["training"] = "%d robots x 400 steps (every 2nd step sampled), 4000 Adam " \
-                                     "steps of 16384 segments" % max(args.robots // 4, 64)
+                     "e2e": arms["learned"]["e2e"], "roofline": None,
+                     "roofline_note": "solver kernels as in the headline line; the network's "
+                                      "tensor-core roofline is the mlp workload's line"})
+        line["config"]["training"] = tnote + ", 4000 Adam steps of 16384 segments"
+        line["config"]["seed"] = rank_seed(rank) if args.workload == "warm_start_rods" \
+            else line["config"].get("seed")
     else:
         sysm = System(desc, params)
         if controls is not None:
