@@ -24,7 +24,9 @@ def step_adjoint(osys, q_next, gq, gv):
     with the kappabar slots in the set_natural_curvature layout.  A joint
     node appears once per rod in the layout: its loss gradients are summed
     over the copies and its output gradients go to its first copy (zeros in
-    the others)."""
+    the others).  Backward Euler only."""
+    if osys.midpoint:
+        raise NotImplementedError("the oracle's step adjoint covers backward Euler")
     dt = osys.dt
     maps = osys._rod_maps()
     n_slots = int(np.sum(osys.npr - 2))

@@ -31,7 +31,7 @@ def ground_terms(osys, s, x, xn, need_jac):
     """Per node: contact force along +z and friction in the ground plane.
     Yields (F [Nn,3], Jint [Nn,3,3]) pairs where Jint = -dF/dx."""
     p = osys.p
-    dt = osys.dt
+    dt = osys.dt_vel  # velocity interval (the step; half of it at the midpoint)
     delta = float(p["delta"])
     zg = float(p["ground_z"])
     kc = torch.as_tensor(s.gkc, dtype=DT)
@@ -175,7 +175,7 @@ def pair_terms(osys, s, q, q_n, need_jac):
     nu = float(p["nu_slip"])
     mm = torch.full_like(Ca, mu)
     nn = torch.full_like(Ca, nu)
-    dtt = torch.full_like(Ca, float(osys.dt))
+    dtt = torch.full_like(Ca, float(osys.dt_vel))
     sig = torch.linalg.vector_norm(vmap(_pair_slip)(xa, xn, dtt), dim=-1)
     moving = torch.nonzero(sig > 0).reshape(-1)
     still = torch.nonzero(sig == 0).reshape(-1)

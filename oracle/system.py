@@ -17,7 +17,13 @@ notes of the repository):
 * Sec. III-C      -- Eq. 14-15 backward-Euler residual with a diagonal mass
                      matrix, Newton's method with the Jacobian of Eq. 16
                      (taken in full: M/dt^2 - dF/dq, reading C10), velocity
-                     update q_dot = (q_{n+1} - q_n)/dt.
+                     update q_dot = (q_{n+1} - q_n)/dt.  The implicit
+                     midpoint scheme the section also offers (no formula in
+                     the paper; the textbook rule): q_{n+1} - q_n =
+                     dt (q_dot_n + q_dot_{n+1})/2 and M (q_dot_{n+1} -
+                     q_dot_n)/dt = F at the midpoint configuration
+                     (q_n + q_{n+1})/2, velocity-dependent forces taking the
+                     mid-step velocity (q_{n+1} - q_n)/dt.
 * Sec. III-D      -- elastic joints: bending and twisting for every pair of
                      edges meeting at a joint node.
 * Sec. III-E      -- natural curvatures as the control input.
@@ -51,7 +57,7 @@ DEFAULT_PARAMS = dict(dt=1e-3, tol=1e-10, max_iter=100,
                       g=(0.0, 0.0, -9.81), eta=0.0,
                       ground=False, ground_z=0.0, delta=5e-4, nu_slip=1e-3,
                       self_contact=False, pair_kc=0.0, pair_mu=0.0,
-                      line_search=False)
+                      line_search=False, integrator="be")
 
 
 class _Sys:
@@ -76,6 +82,14 @@ class OracleSystems:
             p.update(params)
         self.p = p
         self.dt = float(p["dt"])
+        if p["integrator"] not in ("be", "midpoint"):
+            raise ValueError("integrator must be 'be' or 'midpoint'")
+        self.midpoint = p["integrator"] == "midpoint"
+        # interval over which velocity-dependent forces (damping, friction)
+        # take the velocity of the point where forces are evaluated: the
+        # step for backward Euler, half of it at the midpoint, where
+        # (x_mid - x_n)/(dt/2) = (x_{n+1} - x_n)/dt
+        self.dt_vel = 0.5 * self.dt if self.midpoint else self.dt
         self._build(desc)
 
     # ------------------------------------------------------------------
@@ -320,7 +334,9 @@ class OracleSystems:
             s.fixed = torch.as_tensor(fixed)
             # residual scale (convergence reading C9'): a characteristic
             # stiffness per DOF from rest quantities, and a length per DOF
-            dscale = mass / self.dt ** 2
+            # (midpoint: the stiffness of the residual with respect to the
+            # midpoint configuration, inertia 4 M / dt^2)
+            dscale = mass / self.dt_vel ** 2
             for k, e in enumerate(s.edges):
                 i, j = s.edge_nl[k]
                 kst = EA[e] / lbar[e]
@@ -474,7 +490,7 @@ class OracleSystems:
         eta = float(self.p["eta"])
         if eta != 0.0:
             xn = q_n[nd]
-            cdamp = eta * _t(s.vor) / dt
+            cdamp = eta * _t(s.vor) / self.dt_vel
             Fd = -cdamp[:, None] * (x - xn)
             Jd = cdamp[:, None, None] * torch.eye(3, dtype=DT)[None]
             scatter(nd, Fd, Jd)
@@ -512,8 +528,27 @@ class OracleSystems:
     # ------------------------------------------------------------------
     def residual(self, s, q, q_n, v_n, need_jac=True):
         """Eq. 15: f = M/dt ((q - q_n)/dt - q_dot_n) - F_int - F_ext, with the
-        scale S of reading C9 and (optionally) J = M/dt^2 - dF/dq."""
+        scale S of reading C9 and (optionally) J = M/dt^2 - dF/dq.  Implicit
+        midpoint: f = 2 M/dt^2 (q - q_n - dt q_dot_n) - F(q_mid), q_mid =
+        (q + q_n)/2, J = 2 M/dt^2 - (1/2) dF/dx at q_mid."""
         dt = self.dt
+        if self.midpoint:
+            qm = 0.5 * (q + q_n)
+            F, Sabs, Jint = self.forces(s, qm, v_n, q_n, need_jac)
+            inert = 2.0 * s.mass / dt ** 2 * (q - q_n)
+            mom = 2.0 * s.mass / dt * v_n
+            f = inert - mom - F
+            S = inert.abs() + mom.abs() + Sabs
+            f = torch.where(s.fixed, torch.zeros_like(f), f)
+            S = torch.where(s.fixed, torch.zeros_like(S), S)
+            J = None
+            if need_jac:
+                J = 0.5 * Jint + torch.diag(2.0 * s.mass / dt ** 2)
+                fx = s.fixed
+                J[fx, :] = 0.0
+                J[:, fx] = 0.0
+                J[fx, fx] = 1.0
+            return f, S, J
         F, Sabs, Jint = self.forces(s, q, v_n, q_n, need_jac)
         inert = s.mass / dt ** 2 * (q - q_n)
         mom = s.mass / dt * v_n
@@ -550,7 +585,8 @@ class OracleSystems:
         return torch.as_tensor(np.linalg.solve(Jn, b))
 
     def step_system(self, s, record=None):
-        """One backward-Euler step of one system; all-or-nothing."""
+        """One implicit step (backward Euler or implicit midpoint) of one
+        system; all-or-nothing."""
         dt = self.dt
         tol = float(self.p["tol"])
         max_iter = int(self.p["max_iter"])
@@ -613,7 +649,11 @@ class OracleSystems:
             s.beta = der.reference_twist(ta, d1a, tb, d1b, s.beta)
         s.d1 = d1
         s.tn = t
-        s.v = (q - q_n) / self.dt
+        if self.midpoint:
+            v = 2.0 * (q - q_n) / self.dt - s.v
+            s.v = torch.where(s.fixed, torch.zeros_like(v), v)
+        else:
+            s.v = (q - q_n) / self.dt
         s.q = q
 
     def step(self, nsteps=1):

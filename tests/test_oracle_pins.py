@@ -606,3 +606,75 @@ def test_step_adjoint_matches_central_differences():
                 vp[j] += hh; vm[j] -= hh
             fd = (loss(kb0, qp, vp)[0] - loss(kb0, qm, vm)[0]) / (2 * hh)
             assert abs(fd - g[j]) <= 1e-4 * max(1.0, abs(fd)), (vec, j, fd, g[j])
+
+
+# ---------------------------------------------------------------------------
+# Implicit midpoint (Sec. III-C offers it beside backward Euler; the
+# textbook rule): exact on a linear oscillator, energy-conserving where
+# backward Euler dissipates
+# ---------------------------------------------------------------------------
+
+def test_midpoint_linear_oscillator_closed_form():
+    # one edge along x, node 0 and the twist clamped, node 1 moving axially:
+    # the stretch force -EA y / l is linear in the extension y, so the
+    # midpoint rule is the linear map y' = ((1 - a^2 w) y + 2 a v)/(1 + a^2 w),
+    # v' = v - a w (y + y') with a = dt/2, w = EA/(l m1), m1 = rho A l / 2,
+    # which keeps w y^2 + v^2 exactly
+    E, h, rho, l, dt, v0 = 1e7, 1e-3, 1000.0, 0.1, 2e-5, 0.3
+    x = np.array([[0.0, 0.0, 0.0], [l, 0.0, 0.0]])
+    fixed = np.zeros(7, np.uint8)
+    fixed[0:4] = 1
+    vel = np.zeros((2, 3))
+    vel[1, 0] = v0
+    o = OracleSystems(rod_desc(x, E=E, h=h, rho=rho, fixed=fixed, v0=vel),
+                      dict(g=(0, 0, 0), dt=dt, eta=0.0, integrator="midpoint"))
+    s = o.systems[0]
+    A = math.pi * h * h
+    w = E * A / (l * rho * A * l / 2)
+    a = dt / 2
+    y, v = 0.0, v0
+    amp = v0 / math.sqrt(w)
+    for _ in range(240):  # about one period (222 steps)
+        yn = ((1 - a * a * w) * y + 2 * a * v) / (1 + a * a * w)
+        v = v - a * w * (y + yn)
+        y = yn
+        st = o.step_system(s)
+        assert st[0] == 0
+        assert abs(float(s.q[4]) - l - y) <= 1e-9 * amp
+        assert abs(float(s.v[4]) - v) <= 1e-9 * v0
+    assert abs(w * y * y + v * v - v0 * v0) <= 1e-12 * v0 * v0
+
+
+def test_midpoint_momentum_and_energy():
+    # free rod with a natural curvature released straight, no gravity or
+    # damping: both schemes keep sum m v; the midpoint keeps the total
+    # energy (kinetic + elastic) to 0.1 % while backward Euler dissipates
+    # more than 10 % of it in the same 150 steps
+    N = 12
+    out = {}
+    for integ in ("midpoint", "be"):
+        rng = np.random.default_rng(3)
+        vel = 0.01 * rng.standard_normal((N, 3))
+        o = OracleSystems(rod_desc(straight(N, 0.2), E=1e6, h=2e-3, v0=vel),
+                          dict(g=(0, 0, 0), dt=1e-3, eta=0.0, integrator=integ))
+        s = o.systems[0]
+        s.kbar1 = torch.full((len(s.st),), 0.15, dtype=DT)
+        nd = torch.as_tensor(s.node_dof)[:, None] + torch.arange(3)
+
+        def energy():
+            return 0.5 * float((s.mass * s.v * s.v).sum()) + float(_total_energy(o, s, s.q))
+
+        def mom():
+            return (torch.as_tensor(s.mnode)[:, None] * s.v[nd]).sum(0).numpy()
+
+        E0, p0 = energy(), mom()
+        Es = []
+        for _ in range(150):
+            assert o.step_system(s)[0] == 0
+            Es.append(energy())
+        np.testing.assert_allclose(mom(), p0, atol=1e-12 * np.abs(p0).max())
+        out[integ] = (E0, np.array(Es))
+    E0, Es = out["midpoint"]
+    assert np.abs(Es - E0).max() <= 1e-3 * E0
+    E0, Es = out["be"]
+    assert Es[-1] < 0.9 * E0
