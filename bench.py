@@ -85,6 +85,8 @@ def parse():
                          "mlp: the warm-start network's tensor-core inference and training "
                          "at the headline batch's segment count")
     ap.add_argument("--robots", type=int, default=1024)
+    ap.add_argument("--integrator", default="be", choices=["be", "midpoint"],
+                    help="backward Euler (default) or implicit midpoint (Sec. III-C)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (for profiler launch lists)")
     return ap.parse_args()
@@ -199,6 +201,7 @@ def run_reference(args):
         return
     import workloads
     desc, params, kbar = workloads.uneven_rods(n_rods=args.rods, seed=2)
+    params = dict(params, integrator=args.integrator)
     rods = sample_rods(args.rods, 4)
     import torch
     from oracle import OracleSystems
@@ -216,7 +219,9 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rods_per_step": len(rods),
+            "config": {"workload": WORKLOAD if args.integrator == "be" else
+                       WORKLOAD.replace("backward Euler", "implicit midpoint"),
+                       "rods_per_step": len(rods),
                        "sample": "rods %s of the 4096 (seeded), consecutive steps" % rods.tolist()},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(),
                              "kind": "oracle",
@@ -238,6 +243,7 @@ def run_ours(args):
     ensure_built()
     _load_counts()
     desc, params, kbar = workloads.uneven_rods(n_rods=args.rods, seed=rank_seed(rank))
+    params = dict(params, integrator=args.integrator)
     R = args.rods
     sysm = System(desc, params)
     sysm.set_natural_curvature(0, R, kbar)
@@ -350,7 +356,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rods_per_gpu": R,
+            "config": {"workload": WORKLOAD if args.integrator == "be" else
+                       WORKLOAD.replace("backward Euler", "implicit midpoint"), "rods_per_gpu": R,
                        "nodes_per_gpu": int(np.sum(desc["nodes_per_rod"])),
                        "dofs_per_gpu": int(n), "dt": params["dt"], "newton_tol": params["tol"],
                        "parallelism": "independent rod batches per GPU (dp%d)" % ws,
@@ -465,6 +472,9 @@ def run_other(args):
         line["config"] = {"workload": "coil: one 500-node helix collapsing under gravity into "
                           "edge-edge self-contact, dt=2.5e-4 s, line search", "rods_per_gpu": 1,
                           "l2": "working set in L2 (one system)"}
+    if args.integrator != "be":
+        params = dict(params, integrator=args.integrator)
+        line["config"]["integrator"] = args.integrator
     R = len(desc["nodes_per_rod"])
     warm = args.warmup if args.workload != "coil" else max(args.warmup, 400)
     line["warmup"] = warm

@@ -108,6 +108,17 @@ typedef struct dm_params {
                            it is accepted (Sec. III-C notes a line search as an
                            optional safeguard)                                */
   void *stream;         /* cudaStream_t for all work, NULL = default stream    */
+  int32_t integrator;   /* 0: backward Euler (Eq. 15); 1: implicit midpoint
+                           (Sec. III-C offers both; the textbook rule:
+                           q_{n+1} - q_n = dt (qdot_n + qdot_{n+1})/2,
+                           M (qdot_{n+1} - qdot_n)/dt = F at (q_n + q_{n+1})/2,
+                           velocity-dependent forces at (x_{n+1} - x_n)/dt).
+                           Solved as backward Euler over dt/2 for the midpoint
+                           configuration y, whose residual is the same
+                           function, then q_{n+1} = 2y - q_n; newton_tol and
+                           line_search then act on that residual (D_i with
+                           M_i/(dt/2)^2).  Frames and reference twist are
+                           committed at q_{n+1}.  The step adjoint rejects it. */
 } dm_params;
 
 /* Optional per-call statistics (caller-owned arrays may be NULL). */

@@ -153,6 +153,7 @@ struct Extra {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t round_graph = nullptr;
   bool graph_ws = false;  // learned warm start on when the graph was captured
+  bool midpoint = false;  // implicit midpoint (p.dt holds dt/2)
   int64_t round_launches[DM_NUM_KERNELS] = {};  // launches of one captured round
   std::vector<int32_t> slot2st;
   int32_t *d_slot2st = nullptr;
@@ -183,6 +184,19 @@ static void set_solve_shape(dm_system_ext *s, int warps, int bps) {
 static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
                              dm_system_ext *s) {
   HostTopology &T = s->T;
+  // implicit midpoint: every step-size-dependent quantity (inertia M/dt^2,
+  // damping, friction velocity, residual scale, predictor) is built for the
+  // backward-Euler solve over dt/2 in the midpoint configuration
+  dm_params half;
+  if (prm->integrator == 1) {
+    half = *prm;
+    half.dt = 0.5 * prm->dt;
+    prm = &half;
+    s->x.midpoint = true;
+  } else if (prm->integrator != 0) {
+    set_error("integrator must be 0 (backward Euler) or 1 (implicit midpoint)");
+    return DM_ERR_INVALID_ARG;
+  }
   if (!build_topology(desc, prm, T)) return DM_ERR_INVALID_ARG;
   if (prm->self_contact) {
     // edge-edge contact within single rods (no joints, no ground)
@@ -888,6 +902,25 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
         if (s->h_ctrl[0] == 0) break;
       }
     }
+    if (s->x.midpoint && s->h_ctrl[1] == 0) {
+      // q_{n+1} = 2y - q_n, the staged velocity, and the frames and reference
+      // twist at q_{n+1}; a degenerate edge there fails the step
+      k_midpoint_finish<<<blocks(std::max(nd, S), 256), 256, 0, st>>>(sa, d.dq);
+      EdgeArgs ef_args = ea;
+      ef_args.units = nullptr;
+      k_edge<<<blocks(ne, 256), 256, 0, st>>>(ef_args);
+      if (ns > 0) {
+        StencilArgs kf = ka;
+        kf.units = nullptr;
+        kf.frames_only = 1;
+        k_stencil<<<blocks(ns, 128), 128, 0, st>>>(kf);
+      }
+      k_collect_failures<<<blocks(S, 256), 256, 0, st>>>(S, d.sys_status, d.ctrl);
+      DM_CK(cudaGetLastError());
+      DM_CK(cudaMemcpyAsync(s->h_ctrl, d.ctrl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      DM_CK(cudaStreamSynchronize(st));
+      sa.vnew = d.dq;
+    }
     if (stats || s->h_ctrl[1] > 0) {
       iters.resize(S);
       DM_CK(cudaMemcpyAsync(iters.data(), d.sys_iters, S * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -1285,6 +1318,10 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
   auto *s = static_cast<dm_system_ext *>(sys);
   if (!s || !q_next || !gq || !gv || !gkbar || !gq0 || !gv0) {
     set_error("dm_step_adjoint: NULL argument");
+    return DM_ERR_INVALID_ARG;
+  }
+  if (s->x.midpoint) {
+    set_error("dm_step_adjoint: backward Euler only (the system uses implicit midpoint)");
     return DM_ERR_INVALID_ARG;
   }
   const HostTopology &T = s->T;

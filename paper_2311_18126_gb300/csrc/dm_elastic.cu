@@ -173,6 +173,7 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
   dd -= 6.283185307179586 * rint(dd * 0.15915494309189535);
   const double beta = bn + dd;
   a.beta_it[k] = beta;
+  if (a.frames_only) return;
   const double tha = a.q[a.st_th[k]], thb = a.q[a.st_th[NS + k]];
   const double tau = sb * thb - sa * tha + beta;
   const double kbs = a.st_kb[k], kts = a.st_kt[k];

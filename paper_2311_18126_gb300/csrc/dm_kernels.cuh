@@ -25,6 +25,7 @@ struct StencilArgs {
   double *beta_it, *sg, *sh;
   unsigned long long *units;
   double *dk;  // NULL, or [22][Ns]: gradients of kappa1, kappa2 (11 stencil DOFs each)
+  int frames_only;  // 1: reference twist only (the commit of an implicit-midpoint step)
 };
 
 struct RowArgs {
@@ -213,11 +214,14 @@ struct StepArgs {
   const uint8_t *fixed;
   int32_t *sys_active, *sys_iters, *sys_status;
   unsigned long long *sys_res;
+  const double *vnew;  // NULL: qdot = (q - q_n)/dt; else the staged qdot_{n+1}
 };
 __global__ void k_begin_step(StepArgs a);
 __global__ void k_commit(StepArgs a);
 __global__ void k_restore(StepArgs a);
 __global__ void k_round_continue(int32_t *ctrl, int max_rounds, cudaGraphConditionalHandle h);
+__global__ void k_midpoint_finish(StepArgs a, double *vnew);
+__global__ void k_collect_failures(int nsys, const int32_t *sys_status, int32_t *ctrl);
 __global__ void k_tangents(int ne, const int32_t *edge_a, const int32_t *edge_b,
                            const double *q, double *tn, int32_t *bad);
 

@@ -27,7 +27,7 @@ __global__ void k_commit(StepArgs a) {
   const double idt = 1.0 / a.dt;
   if (i < a.nd) {
     const double q = a.q[i];
-    a.vn[i] = (q - a.qn[i]) * idt;
+    a.vn[i] = a.vnew ? a.vnew[i] : (q - a.qn[i]) * idt;
     a.qn[i] = q;
   }
   if (i < a.ne) {
@@ -39,6 +39,34 @@ __global__ void k_commit(StepArgs a) {
     }
   }
   if (i < a.ns) a.beta_n[i] = a.beta_it[i];
+}
+
+// Implicit midpoint, solved as backward Euler over dt/2 (a.dt) for the
+// midpoint configuration y (held in q): with y = (q_n + q_{n+1})/2 the
+// midpoint residual 2M/dt^2 (q_{n+1} - q_n - dt qdot_n) - F(y) is the
+// backward-Euler residual 4M/dt^2 (y - q_n - (dt/2) qdot_n) - F(y), and the
+// velocity of velocity-dependent forces (x_{n+1} - x_n)/dt = (y - x_n)/(dt/2).
+// Here: q <- q_{n+1} = 2y - q_n and the staged velocity qdot_{n+1} =
+// 2 (q_{n+1} - q_n)/dt - qdot_n = 2 (y - q_n)/(dt/2) - qdot_n (zero on fixed
+// DOFs); every system is marked active so that the frames and the reference
+// twist can be evaluated at q_{n+1} before the commit.
+__global__ void k_midpoint_finish(StepArgs a, double *vnew) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.nd) {
+    const double y = a.q[i], qn = a.qn[i];
+    vnew[i] = a.fixed[i] ? 0.0 : 2.0 * (y - qn) / a.dt - a.vn[i];
+    a.q[i] = a.fixed[i] ? qn : 2.0 * y - qn;
+  }
+  if (i < a.nsys) a.sys_active[i] = 1;
+}
+
+// Systems whose status was set outside the Newton bookkeeping (the frame
+// evaluation at q_{n+1} of an implicit-midpoint step) count as failed.
+__global__ void k_collect_failures(int nsys, const int32_t *sys_status, int32_t *ctrl) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys || sys_status[s] == 0) return;
+  atomicAdd(&ctrl[1], 1);
+  atomicMin(&ctrl[2], s);
 }
 
 // Failed step: drop the iterate, the committed state is untouched.

@@ -38,7 +38,9 @@ class Params(C.Structure):
                 ("gravity", C.c_double * 3), ("damping", C.c_double), ("ground", C.c_int32),
                 ("ground_z", C.c_double), ("delta", C.c_double), ("slip_nu", C.c_double),
                 ("self_contact", C.c_int32), ("pair_kc", C.c_double), ("pair_mu", C.c_double),
-                ("line_search", C.c_int32), ("stream", C.c_void_p)]
+                ("line_search", C.c_int32), ("stream", C.c_void_p), ("integrator", C.c_int32)]
+
+INTEGRATORS = {"be": 0, "midpoint": 1}
 
 
 class StepStats(C.Structure):
@@ -248,6 +250,10 @@ class System:
         p.pair_mu = params.get("pair_mu", 0.0)
         p.line_search = int(bool(params.get("line_search", False)))
         p.stream = params.get("stream", None)
+        integ = params.get("integrator", "be")
+        if integ not in INTEGRATORS:
+            raise ValueError("integrator must be one of %s" % sorted(INTEGRATORS))
+        p.integrator = INTEGRATORS[integ]
         h = C.c_void_p()
         _check(lib.dm_create_system(C.byref(d), C.byref(p), C.byref(h)))
         self._h = h
