@@ -202,6 +202,8 @@ def run_reference(args):
     import workloads
     desc, params, kbar = workloads.uneven_rods(n_rods=args.rods, seed=2)
     params = dict(params, integrator=args.integrator)
+    if args.integrator == "midpoint":
+        params["line_search"] = True
     rods = sample_rods(args.rods, 4)
     import torch
     from oracle import OracleSystems
@@ -244,6 +246,10 @@ def run_ours(args):
     _load_counts()
     desc, params, kbar = workloads.uneven_rods(n_rods=args.rods, seed=rank_seed(rank))
     params = dict(params, integrator=args.integrator)
+    if args.integrator == "midpoint":
+        # without numerical damping plain Newton diverges on stiff rods of
+        # this batch (the oracle likewise, e.g. rod 379 at its 5th step)
+        params["line_search"] = True
     R = args.rods
     sysm = System(desc, params)
     sysm.set_natural_curvature(0, R, kbar)
@@ -360,6 +366,7 @@ def run_ours(args):
                        WORKLOAD.replace("backward Euler", "implicit midpoint"), "rods_per_gpu": R,
                        "nodes_per_gpu": int(np.sum(desc["nodes_per_rod"])),
                        "dofs_per_gpu": int(n), "dt": params["dt"], "newton_tol": params["tol"],
+                       "line_search": bool(params.get("line_search", False)),
                        "parallelism": "independent rod batches per GPU (dp%d)" % ws,
                        "l2": "no flush: per-iteration working set (~0.7 GB) exceeds L2"},
             "newton": {"iters_mean": float(it.mean()), "iters_max": int(it.max()),

@@ -110,3 +110,34 @@ def test_midpoint_adjoint_rejected():
     gpu.set_state(q, v)
     with pytest.raises(DismechError):
         gpu.step_adjoint(q1, np.zeros_like(q), np.zeros_like(q))
+
+
+def test_midpoint_divergence_matches_oracle_and_line_search_recovers():
+    """Rod 379 of the headline batch (N = 151, E = 1.26e7): without the
+    numerical damping of backward Euler, plain Newton diverges at the 5th
+    midpoint step on both sides; the GPU reports DM_ERR_NOT_CONVERGED and
+    keeps the last good state, which equals the oracle's.  With the line
+    search both converge and agree."""
+    from paper_2311_18126_gb300 import DismechError
+    desc, params, kbar = workloads.uneven_rods(n_rods=4096, seed=2)
+    sub, kb = workloads.subset(desc, [379], kbar)
+    npr = sub["nodes_per_rod"]
+    L = max(1.0, float(np.max(np.abs(sub["x0"]))))
+    for ls in (False, True):
+        p = dict(params, integrator="midpoint", line_search=ls)
+        gpu = _gpu(sub, p)
+        ora = OracleSystems(sub, p)
+        gpu.set_natural_curvature(0, 1, kb)
+        ora.set_natural_curvature(0, 1, kb)
+        for k in range(6):
+            st = ora.step(1)
+            if st[0][0] != 0:
+                assert not ls and k == 4
+                with pytest.raises(DismechError) as ei:
+                    gpu.step(1)
+                assert ei.value.code == 2  # DM_ERR_NOT_CONVERGED
+                break
+            gpu.step(1)
+        qg, _ = gpu.get_state()
+        qo, _ = ora.get_state()
+        _assert_close(qg, qo, npr, L, 1e-8)
