@@ -81,6 +81,15 @@ typedef struct dm_system_desc {
    * joint node takes the values of its lowest-numbered rod), or NULL (0). */
   const double *ground_mu;      /* [n_rods]                                     */
   const double *ground_kc;      /* [n_rods] k_c multiplying Eq. 10, N/m         */
+  /* Contact groups (edge-edge contact between rods, params.self_contact):
+   * group g solves the rods contact_group_rods[k], k in
+   * [contact_group_offsets[g], contact_group_offsets[g+1]), consecutive in
+   * the descriptor and without joints, as one system, so that their edges
+   * can touch each other (reading C26: contact acts within a system).  0 /
+   * NULL: every rod is its own system. */
+  int32_t n_contact_groups;
+  const int32_t *contact_group_offsets; /* [n_contact_groups+1]                   */
+  const int32_t *contact_group_rods;    /* [contact_group_offsets[n]]              */
 } dm_system_desc;
 
 /* Step parameters (Sec. III-B, III-C). */

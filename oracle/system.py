@@ -245,6 +245,13 @@ class OracleSystems:
             ra, rb = cfind(ea[e]), cfind(eb[e])
             if ra != rb:
                 comp[max(ra, rb)] = min(ra, rb)
+        # contact groups: rods solved as one system so that their edges can
+        # touch each other (reading C26: contact acts within a system)
+        for grp in desc.get("contact_groups", []):
+            for r in grp[1:]:
+                ra, rb = cfind(gid[node_off[grp[0]]]), cfind(gid[node_off[r]])
+                if ra != rb:
+                    comp[max(ra, rb)] = min(ra, rb)
         ncomp = np.array([cfind(a) for a in range(Nn)])
         rod_comp = np.array([ncomp[gid[node_off[r]]] for r in range(R)])
         comps = []

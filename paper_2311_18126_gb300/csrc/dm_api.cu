@@ -158,6 +158,10 @@ struct Extra {
   std::vector<int32_t> slot2st;
   int32_t *d_slot2st = nullptr;
   int32_t *d_dof_sys = nullptr;
+  // rod tables of the row kernel: DOF -> rod (-1 on general systems), and
+  // per rod its first DOF, DOF count, first stencil and first edge
+  int32_t *d_dof_rod = nullptr, *d_rod_dof0 = nullptr, *d_rod_ndof = nullptr,
+          *d_rod_st0 = nullptr, *d_rod_edge0 = nullptr;
   double *d_damp = nullptr;
   double *d_scratch = nullptr;  // layout-sized staging for state copies
   size_t scratch_n = 0;
@@ -214,9 +218,9 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     }
     double dense = 0.0;
     for (int k = 0; k < T.n_systems; ++k) {
-      if (T.sys_kind[k] != SOLVE_ROD_BAND) {
-        set_error("edge-edge contact is supported on single rods only (system " +
-                  std::to_string(k) + " has joints)");
+      if (T.sys_kind[k] != SOLVE_ROD_BAND && T.sys_kind[k] != SOLVE_CONTACT) {
+        set_error("edge-edge contact is supported on single rods and contact groups of "
+                  "rods without joints (system " + std::to_string(k) + " has joints)");
         return DM_ERR_INVALID_ARG;
       }
       T.sys_kind[k] = SOLVE_CONTACT;
@@ -334,8 +338,11 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
   if (prm->self_contact) {
     auto &c = s->x.cc;
     std::vector<int32_t> eidx(ne), csys;
+    // edge index with a gap of three between rods, so that |eidx_e - eidx_f|
+    // <= 2 holds exactly for two edges of one rod at most two apart (the
+    // excluded pairs of reading C16); edges of different rods never match
     for (int r = 0; r < T.n_rods; ++r)
-      for (int64_t e = T.rod_edge0[r]; e < T.rod_edge0[r + 1]; ++e) eidx[e] = (int32_t)(e - T.rod_edge0[r]);
+      for (int64_t e = T.rod_edge0[r]; e < T.rod_edge0[r + 1]; ++e) eidx[e] = (int32_t)(e + 3 * r);
     std::vector<int64_t> dense0(S, 0);
     int64_t tot = 0;
     for (int k = 0; k < S; ++k) {
@@ -479,6 +486,28 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
   for (int64_t k = 0; k < ns; ++k)
     if (T.st_rod_slot[k] >= 0) s->x.slot2st[T.st_rod_slot[k]] = (int32_t)k;
   DM_TRY(upload(s, &s->x.d_slot2st, s->x.slot2st));
+  {
+    const int R = T.n_rods;
+    std::vector<int32_t> dof_rod(std::max<int64_t>(T.n_dofs, 1), -1), rd0(R), rnd(R), rst0(R),
+        re0(R);
+    int64_t k0 = 0;
+    for (int r = 0; r < R; ++r) {
+      const int N = T.npr[r];
+      rd0[r] = T.node_dof[T.flat2node[T.rod_node0[r]]];
+      rnd[r] = 4 * N - 1;
+      rst0[r] = N > 2 ? s->x.slot2st[k0] : 0;
+      re0[r] = (int32_t)T.rod_edge0[r];
+      k0 += N - 2;
+      const int sys = T.edge_sys[T.rod_edge0[r]];
+      if (T.sys_kind[sys] != SOLVE_GENERAL)
+        for (int k = 0; k < 4 * N - 1; ++k) dof_rod[rd0[r] + k] = r;
+    }
+    DM_TRY(upload(s, &s->x.d_dof_rod, dof_rod));
+    DM_TRY(upload(s, &s->x.d_rod_dof0, rd0));
+    DM_TRY(upload(s, &s->x.d_rod_ndof, rnd));
+    DM_TRY(upload(s, &s->x.d_rod_st0, rst0));
+    DM_TRY(upload(s, &s->x.d_rod_edge0, re0));
+  }
   s->x.scratch_n = std::max<size_t>({(size_t)T.layout2dof.size(), (size_t)(2 * nslots), (size_t)1});
   DM_TRY(dalloc(s, &s->x.d_scratch, s->x.scratch_n));
   DM_TRY(dalloc(s, &s->x.d_units, DM_NUM_KERNELS));
@@ -659,8 +688,9 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   ra.eta = s->p.eta;
   ra.q = d.q; ra.qn = d.qn; ra.vn = d.vn; ra.mass = d.mass; ra.rscale = d.rscale;
   ra.damp = s->x.d_damp; ra.fixed = d.fixed; ra.dof_sys = s->x.d_dof_sys;
-  ra.sys_dof0 = d.sys_dof0; ra.sys_ndof = d.sys_ndof; ra.sys_st0 = d.sys_st0;
-  ra.sys_edge0 = d.sys_edge0; ra.sys_active = d.sys_active; ra.sys_kind = s->x.d_sys_kind;
+  ra.dof_rod = s->x.d_dof_rod; ra.rod_dof0 = s->x.d_rod_dof0; ra.rod_ndof = s->x.d_rod_ndof;
+  ra.rod_st0 = s->x.d_rod_st0; ra.rod_edge0 = s->x.d_rod_edge0;
+  ra.sys_active = d.sys_active; ra.sys_kind = s->x.d_sys_kind;
   ra.sg = d.sg; ra.sh = d.sh; ra.es = d.es; ra.f = d.f; ra.band = d.band; ra.sys_res = d.sys_res;
   ra.units = s->x.prof ? s->x.d_units + K_ROWS : nullptr;
   SolveArgs va{s->x.n_rod_sys, nd, s->p.tol, s->p.max_iter, d.solve_order, d.sys_dof0, d.sys_ndof, d.fixed, d.f,
@@ -1443,8 +1473,9 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
     ra.eta = s->p.eta;
     ra.q = d.q; ra.qn = d.qn; ra.vn = d.vn; ra.mass = d.mass; ra.rscale = d.rscale;
     ra.damp = s->x.d_damp; ra.fixed = d.fixed; ra.dof_sys = s->x.d_dof_sys;
-    ra.sys_dof0 = d.sys_dof0; ra.sys_ndof = d.sys_ndof; ra.sys_st0 = d.sys_st0;
-    ra.sys_edge0 = d.sys_edge0; ra.sys_active = d.sys_active; ra.sys_kind = s->x.d_sys_kind;
+    ra.dof_rod = s->x.d_dof_rod; ra.rod_dof0 = s->x.d_rod_dof0; ra.rod_ndof = s->x.d_rod_ndof;
+    ra.rod_st0 = s->x.d_rod_st0; ra.rod_edge0 = s->x.d_rod_edge0;
+    ra.sys_active = d.sys_active; ra.sys_kind = s->x.d_sys_kind;
     ra.sg = d.sg; ra.sh = d.sh; ra.es = d.es; ra.f = d.f; ra.band = d.band; ra.sys_res = d.sys_res;
     k_rows_rod<<<blocks(nd, 256), 256, 0, st>>>(ra);
   }

@@ -35,7 +35,8 @@ struct RowArgs {
   const double *q, *qn, *vn, *mass, *rscale, *damp;
   const uint8_t *fixed;
   const int32_t *dof_sys;
-  const int32_t *sys_dof0, *sys_ndof, *sys_st0, *sys_edge0;
+  // per rod (rows are rod-local; a contact group holds several rods)
+  const int32_t *dof_rod, *rod_dof0, *rod_ndof, *rod_st0, *rod_edge0;
   const int32_t *sys_active, *sys_kind;
   const double *sg, *sh, *es;
   double *f, *band;

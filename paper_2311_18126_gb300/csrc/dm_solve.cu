@@ -33,12 +33,13 @@ __device__ __forceinline__ void k_rows_rod_one(RowArgs a, const int i) {
   count_units(a.units, act);
   if (!act) return;
   const int s = a.dof_sys[i];
-  const int base = a.sys_dof0[s];
+  const int rod = a.dof_rod[i];
+  const int base = a.rod_dof0[rod];
   const int r = i - base;
-  const int n = a.sys_ndof[s];
+  const int n = a.rod_ndof[rod];
   const int N = (n + 1) >> 2;
   const int node = r >> 2, c = r & 3;
-  const int st0 = a.sys_st0[s], e0 = a.sys_edge0[s];
+  const int st0 = a.rod_st0[rod], e0 = a.rod_edge0[rod];
   const int NS = a.ns, NE = a.ne;
   double F = 0.0;
   double brow[11];

@@ -260,6 +260,32 @@ bool build_topology(const dm_system_desc *D, const dm_params *P, HostTopology &T
       int64_t ra = cf(T.edge_a[e]), rb = cf(T.edge_b[e]);
       if (ra != rb) comp[std::max(ra, rb)] = std::min(ra, rb);
     }
+    // contact groups: their rods form one system (edge-edge contact between
+    // rods, reading C26)
+    if (D->n_contact_groups > 0) {
+      if (!P->self_contact || !D->contact_group_offsets || !D->contact_group_rods) {
+        set_error("contact groups need self_contact and the group arrays");
+        return false;
+      }
+      for (int g = 0; g < D->n_contact_groups; ++g) {
+        const int32_t b = D->contact_group_offsets[g], e = D->contact_group_offsets[g + 1];
+        if (b < 0 || e < b) {
+          set_error("contact groups: bad offsets");
+          return false;
+        }
+        for (int32_t k = b; k < e; ++k) {
+          const int32_t r = D->contact_group_rods[k];
+          if (r < 0 || r >= R || (k > b && r != D->contact_group_rods[k - 1] + 1)) {
+            set_error("contact group " + std::to_string(g) +
+                      ": rods must be valid and consecutive in the descriptor");
+            return false;
+          }
+          const int64_t ra = cf(T.flat2node[T.rod_node0[D->contact_group_rods[b]]]);
+          const int64_t rb = cf(T.flat2node[T.rod_node0[r]]);
+          if (ra != rb) comp[std::max(ra, rb)] = std::min(ra, rb);
+        }
+      }
+    }
     std::vector<int64_t> rootsys;
     for (int r = 0; r < R; ++r) {
       int64_t c = cf(T.flat2node[T.rod_node0[r]]);
@@ -320,14 +346,22 @@ bool build_topology(const dm_system_desc *D, const dm_params *P, HostTopology &T
   for (int s = 0; s < S; ++s) {
     T.sys_dof0[s] = ndof;
     const int r0 = T.sys_rod0[s], r1 = T.sys_rod0[s] + T.sys_nrods[s];
-    const bool general = T.sys_nrods[s] > 1 || T.ground;
-    T.sys_kind[s] = general ? SOLVE_GENERAL : SOLVE_ROD_BAND;
+    // a contact group: several rods without joints, each in Eq. 1 order,
+    // solved together on the contact path
+    bool jointless = true;
+    for (int r = r0; r < r1 && jointless; ++r)
+      for (int i = 0; i < T.npr[r]; ++i)
+        if (mult[T.flat2node[T.rod_node0[r] + i]] > 1) jointless = false;
+    const bool group = T.sys_nrods[s] > 1 && P->self_contact && jointless && !T.ground;
+    const bool general = (T.sys_nrods[s] > 1 || T.ground) && !group;
+    T.sys_kind[s] = group ? SOLVE_CONTACT : general ? SOLVE_GENERAL : SOLVE_ROD_BAND;
     if (!general) {
-      for (int i = 0; i < T.npr[r0]; ++i) {
-        T.node_dof[T.flat2node[T.rod_node0[r0] + i]] = ndof;
-        ndof += 3;
-        if (i + 1 < T.npr[r0]) T.edge_thdof[T.rod_edge0[r0] + i] = ndof++;
-      }
+      for (int r = r0; r < r1; ++r)
+        for (int i = 0; i < T.npr[r]; ++i) {
+          T.node_dof[T.flat2node[T.rod_node0[r] + i]] = ndof;
+          ndof += 3;
+          if (i + 1 < T.npr[r]) T.edge_thdof[T.rod_edge0[r] + i] = ndof++;
+        }
       T.sys_ndof[s] = ndof - T.sys_dof0[s];
       continue;
     }

@@ -30,7 +30,9 @@ class SystemDesc(C.Structure):
     _fields_ = [("n_rods", C.c_int32), ("nodes_per_rod", _ip), ("x0", _dp), ("v0", _dp),
                 ("theta0", _dp), ("theta_dot0", _dp), ("E", _dp), ("nu", _dp), ("rho", _dp),
                 ("radius", _dp), ("n_joints", C.c_int32), ("joint_offsets", _ip),
-                ("joint_members", _ip), ("fixed", _up), ("ground_mu", _dp), ("ground_kc", _dp)]
+                ("joint_members", _ip), ("fixed", _up), ("ground_mu", _dp), ("ground_kc", _dp),
+                ("n_contact_groups", C.c_int32), ("contact_group_offsets", _ip),
+                ("contact_group_rods", _ip)]
 
 
 class Params(C.Structure):
@@ -230,6 +232,16 @@ class System:
             d.n_joints = len(joints)
             d.joint_offsets = _ptr(off, C.c_int32)
             d.joint_members = _ptr(mem, C.c_int32)
+        groups = desc.get("contact_groups") or []
+        if groups:
+            goff = np.zeros(len(groups) + 1, np.int32)
+            goff[1:] = np.cumsum([len(g) for g in groups])
+            grods = np.ascontiguousarray(np.concatenate([np.asarray(g, np.int32) for g in groups]),
+                                         np.int32)
+            self._keep += [goff, grods]
+            d.n_contact_groups = len(groups)
+            d.contact_group_offsets = _ptr(goff, C.c_int32)
+            d.contact_group_rods = _ptr(grods, C.c_int32)
         d.fixed = _ptr(arr("fixed", np.uint8), C.c_uint8)
         d.ground_mu = _ptr(arr("ground_mu", np.float64), C.c_double)
         d.ground_kc = _ptr(arr("ground_kc", np.float64), C.c_double)

@@ -194,3 +194,40 @@ def coil(N=500, h=1e-3, radius=0.02, pitch_factor=2.2, E=1e7, rho=1000.0,
                   self_contact=True, delta=delta, pair_kc=kc, pair_mu=mu,
                   line_search=True)
     return desc, params, None
+
+
+def gripper(n_rods=5, N=60, L=0.3, h=2.5e-3, rho=1200.0, E=0.3e6, ring=0.03, mu=0.5,
+            delta=5e-4, nu_slip=1e-3, phi_max_deg=40.0, ramp=0.2, dt=1e-3, seed=11):
+    """Active entanglement gripper (Sec. IV): `n_rods` fingers hanging from a
+    ring of radius `ring`, clamped at the top, actuated by natural
+    curvatures 2 tan(phibar/2) per stencil with phibar ~ U[0, phi_max] (the
+    bending plane turns by a random angle per rod), ramped in over `ramp`
+    seconds; edge-edge contact with friction between all fingers (one
+    contact group).  The paper's radius is 5 mm; with N = 60 the edge length
+    then equals the radius and edges three apart along a finger would lie
+    within C + delta at rest, so h defaults to 2.5 mm.  Returns (desc,
+    params, kbar_fn) with kbar_fn(t) the (kappabar1, kappabar2) per interior
+    node of every finger."""
+    rng = np.random.default_rng(seed)
+    xs = []
+    for j in range(n_rods):
+        a = 2.0 * math.pi * j / n_rods
+        top = np.array([ring * math.cos(a), ring * math.sin(a), 0.0])
+        z = -np.linspace(0.0, L, N)
+        xs.append(top[None, :] + np.stack([np.zeros(N), np.zeros(N), z], 1))
+    mask = np.concatenate([_clamp_mask(N) for _ in range(n_rods)])
+    desc = _rod_desc([N] * n_rods, np.concatenate(xs), [E] * n_rods, [0.5] * n_rods,
+                     [rho] * n_rods, [h] * n_rods, mask,
+                     contact_groups=[list(range(n_rods))])
+    phi = np.deg2rad(rng.uniform(0.0, phi_max_deg, size=(n_rods, N - 2)))
+    psi = rng.uniform(0.0, 2.0 * math.pi, size=n_rods)
+    k = 2.0 * np.tan(0.5 * phi)
+    kb = np.stack([k * np.cos(psi)[:, None], k * np.sin(psi)[:, None]], -1).reshape(-1, 2)
+
+    def kbar_fn(t):
+        return min(max(t / ramp, 0.0), 1.0) * kb
+
+    params = dict(dt=dt, tol=1e-10, max_iter=100, g=(0.0, 0.0, -9.81), eta=0.1,
+                  self_contact=True, delta=delta, pair_kc=E * h, pair_mu=mu,
+                  nu_slip=nu_slip, line_search=True)
+    return desc, params, kbar_fn
