@@ -75,10 +75,12 @@ def parse():
     ap.add_argument("--rods", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="uneven_rods",
-                    choices=["uneven_rods", "star_robots", "coil", "warm_start",
+                    choices=["uneven_rods", "star_robots", "coil", "gripper", "warm_start",
                              "warm_start_rods", "calibration", "mlp"],
                     help="uneven_rods: the headline batch (default); star_robots: limbed "
                          "robots on the ground with a gait; coil: edge-edge self-contact; "
+                         "gripper: five 60-node fingers entangling with frictional contact "
+                         "between them; "
                          "warm_start: learned vs extrapolated Newton guess on star robots; "
                          "warm_start_rods: the same on the headline batch of uneven rods; "
                          "calibration: adjoint gradient of a 500-step star-robot rollout; "
@@ -473,6 +475,15 @@ def run_other(args):
         controls = lambda k: kbar
         line["config"] = {"workload": WORKLOAD, "rods_per_gpu": args.rods,
                           "l2": "no flush: per-iteration working set (~0.7 GB) exceeds L2"}
+    elif args.workload == "gripper":
+        desc, params, kfn = workloads.gripper()
+        dt = params["dt"]
+        controls = lambda k: kfn(k * dt)
+        line["config"] = {"workload": "gripper: 5 fingers of 60 nodes (L 0.3 m, h 2.5 mm, "
+                          "E 0.3 MPa) actuated by random natural curvatures (phibar up to 40 "
+                          "deg, ramped over 0.2 s), edge-edge contact with friction mu 0.5 "
+                          "between all fingers (one system), dt=1e-3 s, line search",
+                          "rods_per_gpu": 5, "l2": "working set in L2 (one system)"}
     else:
         desc, params, _ = workloads.coil(N=500)
         controls = None
@@ -483,7 +494,7 @@ def run_other(args):
         params = dict(params, integrator=args.integrator)
         line["config"]["integrator"] = args.integrator
     R = len(desc["nodes_per_rod"])
-    warm = args.warmup if args.workload != "coil" else max(args.warmup, 400)
+    warm = max(args.warmup, 400) if args.workload in ("coil", "gripper") else args.warmup
     line["warmup"] = warm
     if args.workload in ("warm_start", "warm_start_rods"):
         from paper_2311_18126_gb300 import warmstart as wsm
@@ -633,7 +644,7 @@ def run_other(args):
                                   "note": "no per-unit counts for this kernel: latency bound "
                                           "(few systems active in most Newton rounds)"},
                      "kernels": _kernel_table(prof)})
-        if args.workload == "coil":
+        if args.workload in ("coil", "gripper"):
             line["contact_pairs"] = sysm.contact_pairs()
         sysm.close()
     if rank == 0:
