@@ -346,7 +346,8 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
  * number of edge pairs closer than C + delta at the last evaluated Newton
  * iterate, summed over the systems (0 without edge-edge contact, -1 on a
  * CUDA error).  Synchronises the stream.  Contact acts within single rods
- * (no joints, no ground contact); friction at the closest points (Eq. 12-13)
+ * and within contact groups of rods (dm_system_desc.contact_groups; no
+ * joints, no ground contact); friction at the closest points (Eq. 12-13)
  * when pair_mu > 0, with the slip tolerance slip_nu.  dm_create_system
  * rejects other combinations with DM_ERR_INVALID_ARG. */
 int64_t dm_contact_pairs(dm_system *sys);
