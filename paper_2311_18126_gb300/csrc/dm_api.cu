@@ -811,7 +811,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
           const int rest = n - k - std::min(kNB, n - k);
           k_lu_diag<<<1, 256, 0, rs>>>(ca, c, k);
           if (rest > 0) {
-            k_lu_trsm<<<blocks(2 * rest, 128), 128, 0, rs>>>(ca, c, k);
+            k_lu_trsm<<<blocks(2 * rest, 32), 32, 0, rs>>>(ca, c, k);
             const int t = (rest + 63) / 64;
             k_lu_gemm<<<dim3(t, t), 256, 0, rs>>>(ca, c, k);
           }
@@ -1568,7 +1568,7 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
         const int rest = nc_n - k - std::min(kNB, nc_n - k);
         k_lu_diag<<<1, 256, 0, st>>>(ca, c, k);
         if (rest > 0) {
-          k_lu_trsm<<<blocks(2 * rest, 128), 128, 0, st>>>(ca, c, k);
+          k_lu_trsm<<<blocks(2 * rest, 32), 32, 0, st>>>(ca, c, k);
           const int t = (rest + 63) / 64;
           k_lu_gemm<<<dim3(t, t), 256, 0, st>>>(ca, c, k);
         }

@@ -604,6 +604,20 @@ __global__ void k_cc_decide(ContactArgs a, SolveArgs v) {
   a.cbad[c] = 0;
 }
 
+// 1/d from an FP32 seed and two FP64 Newton steps (relative error at the
+// FP64 rounding level) where |d| is well inside the FP32 range, else by
+// division: the panel kernels take many reciprocals, and an FP64 division
+// costs tens of FP64 instructions.
+__device__ __forceinline__ double lu_recip(double d) {
+  const double ad = fabs(d);
+  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+  double r = (double)__frcp_rn((float)d);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
 __global__ void __launch_bounds__(256) k_lu_diag(ContactArgs a, int c, int k) {
   if (!a.cgo[c] || a.cbad[c]) return;
   const int s = a.contact_sys[c];
@@ -622,7 +636,7 @@ __global__ void __launch_bounds__(256) k_lu_diag(ContactArgs a, int c, int k) {
       if (threadIdx.x == 0) a.cbad[c] = 1;
       return;  // uniform: every thread read the same pivot
     }
-    const double rp = 1.0 / piv;
+    const double rp = lu_recip(piv);
     for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) D[i][j] *= rp;
     __syncthreads();
     const int m = nb - 1 - j;
@@ -639,6 +653,10 @@ __global__ void __launch_bounds__(256) k_lu_diag(ContactArgs a, int c, int k) {
 }
 
 // Rows [k+nb, rend): L21 = A21 U11^{-1}; columns [k+nb, cend): U12 = L11^{-1} A12.
+// A thread per row or column, launched in small blocks so that the FP64 work
+// spreads over many SMs; the diagonal block and the reciprocals of its
+// pivots are staged in shared memory, the thread's row or column in
+// registers (loops fully unrolled, zero-padded past nb).
 __global__ void __launch_bounds__(128) k_lu_trsm(ContactArgs a, int c, int k) {
   if (!a.cgo[c] || a.cbad[c]) return;
   const int s = a.contact_sys[c];
@@ -647,38 +665,47 @@ __global__ void __launch_bounds__(128) k_lu_trsm(ContactArgs a, int c, int k) {
   const int bw = max(10, a.sys_bw[s]);
   const int lo = k + nb, hi = min(n, k + nb + bw);
   const int cnt = hi - lo;
-  if (cnt <= 0) return;
+  if (cnt <= 0 || blockIdx.x * blockDim.x >= 2 * cnt) return;
   double *A = a.dense + a.sys_dense0[s];
   __shared__ double D[kNB][kNB + 1];
-  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-    const int i = t / nb, j = t - i * nb;
-    D[i][j] = A[(size_t)(k + i) * n + k + j];
+  __shared__ double R[kNB];
+  for (int t = threadIdx.x; t < kNB * kNB; t += blockDim.x) {
+    const int i = t / kNB, j = t - i * kNB;
+    D[i][j] = (i < nb && j < nb) ? A[(size_t)(k + i) * n + k + j] : (i == j ? 1.0 : 0.0);
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kNB; j += blockDim.x) R[j] = lu_recip(D[j][j]);
   __syncthreads();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   double x[kNB];
   if (g < cnt) {  // a row of L21: x U11 = a
     double *row = A + (size_t)(lo + g) * n + k;
 #pragma unroll
+    for (int j = 0; j < kNB; ++j) x[j] = j < nb ? row[j] : 0.0;
+#pragma unroll
     for (int j = 0; j < kNB; ++j) {
-      if (j < nb) {
-        double v = row[j];
-        for (int m = 0; m < j; ++m) v = fma(-x[m], D[m][j], v);
-        x[j] = v / D[j][j];
-        row[j] = x[j];
-      }
+      double v = x[j];
+#pragma unroll
+      for (int m = 0; m < j; ++m) v = fma(-x[m], D[m][j], v);
+      x[j] = v * R[j];
     }
+#pragma unroll
+    for (int j = 0; j < kNB; ++j)
+      if (j < nb) row[j] = x[j];
   } else if (g < 2 * cnt) {  // a column of U12: L11 x = a (unit lower)
     const int col = lo + (g - cnt);
 #pragma unroll
+    for (int j = 0; j < kNB; ++j) x[j] = j < nb ? A[(size_t)(k + j) * n + col] : 0.0;
+#pragma unroll
     for (int j = 0; j < kNB; ++j) {
-      if (j < nb) {
-        double v = A[(size_t)(k + j) * n + col];
-        for (int m = 0; m < j; ++m) v = fma(-D[j][m], x[m], v);
-        x[j] = v;
-        A[(size_t)(k + j) * n + col] = v;
-      }
+      double v = x[j];
+#pragma unroll
+      for (int m = 0; m < j; ++m) v = fma(-D[j][m], x[m], v);
+      x[j] = v;
     }
+#pragma unroll
+    for (int j = 0; j < kNB; ++j)
+      if (j < nb) A[(size_t)(k + j) * n + col] = x[j];
   }
 }
 
@@ -794,9 +821,10 @@ __global__ void __launch_bounds__(1024) k_cc_subst(ContactArgs a, SolveArgs v) {
     const int nb = min(kNB, n - k);
     if (warp == 0) {
       double xv = lane < nb ? y[k + lane] : 0.0;
+      // the panel's pivot reciprocals, one per lane, off the sequential chain
+      const double rj = lane < nb ? lu_recip(A[(size_t)(k + lane) * n + k + lane]) : 1.0;
       for (int j = nb - 1; j >= 0; --j) {
-        double xj = __shfl_sync(0xffffffffu, xv, j);
-        xj = xj / A[(size_t)(k + j) * n + k + j];
+        double xj = __shfl_sync(0xffffffffu, xv, j) * __shfl_sync(0xffffffffu, rj, j);
         if (lane == j) xv = xj;
         if (lane < j) xv = fma(-A[(size_t)(k + lane) * n + k + j], xj, xv);
       }
