@@ -215,6 +215,23 @@ dm_status dm_solve_band(int32_t nsys, const int32_t *sys_dof0, const int32_t *sy
                         int64_t ntot, const double *band, const double *rhs, double *x,
                         void *stream);
 
+/* The same solve for long systems (scope NEXT f4: N >> 500 nodes), without
+ * the sequential chain over the whole system: each system is cut into
+ * interiors of part_rows - 10 rows separated by 10-row separators (interiors
+ * do not couple); a warp per interior factors it (band L D L^T) and forms
+ * its Schur contributions to the neighbouring separators (forward solves
+ * only, by symmetry), a warp per system solves the block-tridiagonal
+ * separator system (10 x 10 blocks, Gauss-Jordan with partial pivoting), and
+ * a warp per interior back-substitutes.  Arguments as dm_solve_band, plus
+ * part_rows (0 = 512; otherwise 21..1024).  Interiors are factored without
+ * pivoting, like the full band.  Allocates device scratch (about 170 bytes
+ * per DOF); returns after the solve has finished; DM_ERR_DEGENERATE on a
+ * zero or non-finite pivot. */
+dm_status dm_solve_band_partitioned(int32_t nsys, const int32_t *sys_dof0,
+                                    const int32_t *sys_ndof, int64_t ntot, const double *band,
+                                    const double *rhs, double *x, int32_t part_rows,
+                                    void *stream);
+
 /* dm_solve_band without any device allocation.
  *
  * Some callers cannot allocate device memory at the point where they need a

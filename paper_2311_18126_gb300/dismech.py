@@ -119,6 +119,9 @@ def load_library(path=LIB_PATH):
     lib.dm_solve_band.argtypes = [C.c_int32, _ip, _ip, C.c_int64, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]
     lib.dm_solve_band.restype = C.c_int
+    lib.dm_solve_band_partitioned.argtypes = lib.dm_solve_band.argtypes[:-1] + [C.c_int32,
+                                                                                C.c_void_p]
+    lib.dm_solve_band_partitioned.restype = C.c_int
     lib.dm_solve_band_noalloc.argtypes = lib.dm_solve_band.argtypes
     lib.dm_solve_band_noalloc.restype = C.c_int
     lib.dm_debug_copy.argtypes = [H, C.c_char_p, _dp, C.c_int64]
@@ -478,6 +481,19 @@ def solve_band(sys_dof0, sys_ndof, band, rhs, x, stream=None):
     nd = np.ascontiguousarray(np.asarray(sys_ndof, np.int32))
     _check(lib.dm_solve_band(len(d0), _ptr(d0, C.c_int32), _ptr(nd, C.c_int32), x.numel(),
                              _dev_ptr(band), _dev_ptr(rhs), _dev_ptr(x), stream))
+    return x
+
+
+def solve_band_partitioned(sys_dof0, sys_ndof, band, rhs, x, part_rows=0, stream=None):
+    """solve_band for long systems: interiors of part_rows - 10 rows factored
+    in parallel, a block-tridiagonal Schur system on the 10-row separators
+    (part_rows 0 = 512)."""
+    lib = load_library()
+    d0 = np.ascontiguousarray(np.asarray(sys_dof0, np.int32))
+    nd = np.ascontiguousarray(np.asarray(sys_ndof, np.int32))
+    _check(lib.dm_solve_band_partitioned(len(d0), _ptr(d0, C.c_int32), _ptr(nd, C.c_int32),
+                                         x.numel(), _dev_ptr(band), _dev_ptr(rhs), _dev_ptr(x),
+                                         int(part_rows), stream))
     return x
 
 
