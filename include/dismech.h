@@ -128,6 +128,11 @@ typedef struct dm_params {
                            line_search then act on that residual (D_i with
                            M_i/(dt/2)^2).  Frames and reference twist are
                            committed at q_{n+1}.  The step adjoint rejects it. */
+  int32_t long_rod_dofs; /* single rods with at least this many DOFs are solved
+                           by the partitioned band solve (dm_solve_band_
+                           partitioned, interiors of 502 rows) instead of the
+                           twisted LDL^T chain; 0 = 2048 (512 nodes),
+                           negative = never */
 } dm_params;
 
 /* Optional per-call statistics (caller-owned arrays may be NULL). */

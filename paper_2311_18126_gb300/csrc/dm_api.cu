@@ -154,6 +154,7 @@ struct Extra {
   cudaGraphExec_t round_graph = nullptr;
   bool graph_ws = false;  // learned warm start on when the graph was captured
   bool midpoint = false;  // implicit midpoint (p.dt holds dt/2)
+  LongRods *longr = nullptr;  // single rods on the partitioned solve
   int64_t round_launches[DM_NUM_KERNELS] = {};  // launches of one captured round
   std::vector<int32_t> slot2st;
   int32_t *d_slot2st = nullptr;
@@ -327,9 +328,14 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
   DM_TRY(dalloc(s, &d.ctrl, 8));  // [4] = Newton rounds of the step
   DM_TRY(dalloc(s, &d.band, 11 * nd));
   DM_TRY(dalloc(s, &d.dq, nd));
-  std::vector<int32_t> order;
+  std::vector<int32_t> order, longsys;
+  const int long_min = prm->long_rod_dofs == 0 ? 2048 : prm->long_rod_dofs;
   for (int k = 0; k < S; ++k)
-    if (T.sys_kind[k] == SOLVE_ROD_BAND) order.push_back(k);
+    if (T.sys_kind[k] == SOLVE_ROD_BAND) {
+      if (long_min > 0 && T.sys_ndof[k] >= long_min) longsys.push_back(k);
+      else order.push_back(k);
+    }
+  DM_TRY(long_rods_create(s, longsys, 512, &s->x.longr));
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return T.sys_ndof[a] > T.sys_ndof[b]; });
   s->x.n_rod_sys = (int)order.size();
@@ -608,6 +614,7 @@ void dm_destroy(dm_system *sys) {
     if (sx->x.ev[k]) cudaEventDestroy(sx->x.ev[k]);
   if (sys->h_ctrl) cudaFreeHost(sys->h_ctrl);
   if (sx->x.round_graph) cudaGraphExecDestroy(sx->x.round_graph);
+  long_rods_free(sx->x.longr);
   if (sx->x.cap_stream) cudaStreamDestroy(sx->x.cap_stream);
   dm::ws_free(sys->ws);
   delete static_cast<dm_system_ext *>(sys);
@@ -739,6 +746,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   if (ws_trial) la.wstry = ws_trial_flags(s);
   const int max_rounds = ls_on ? 13 * (s->p.max_iter + 1) : s->p.max_iter + 1;
   const bool gen_on = T.any_general, rod_on = s->x.n_rod_sys > 0;
+  const bool long_on = long_rods_count(s->x.longr) > 0;
   if (stats) {
     stats->first_failed = -1;
     stats->steps_done = 0;
@@ -779,7 +787,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       k_cc_pairs<<<blocks(ne, 128), 128, 0, rs>>>(ca);
       k_cc_terms<<<blocks(c.pair_cap, 64), 64, 0, rs>>>(ca);
     }
-    if (rod_on || contact_on) {
+    if (rod_on || contact_on || long_on) {
       Timed t(s, K_ROWS, rs);
       const int tb = s->x.tune.rows_threads;
       k_rows_rod<<<blocks(nd, tb), tb, 0, rs>>>(ra);
@@ -799,6 +807,10 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
         Timed t(s, K_SOLVE, rs);
         k_solve_rod<<<s->x.solve_blocks, 32 * s->x.tune.solve_warps, s->x.solve_smem, rs>>>(va);
       }
+    }
+    if (long_on) {
+      Timed t(s, K_SOLVE, rs);
+      DM_CK(long_rods_round(s->x.longr, va, rs));
     }
     if (contact_on) {
       Timed t(s, K_SOLVE_CONTACT, rs);

@@ -17,9 +17,11 @@
 // the sequential depth is m rows plus one 10 x 10 elimination per
 // separator instead of n rows.  One warp per interior or system; an
 // interior keeps its band and its top coupling solve in shared memory.
+#include <string>
 #include <vector>
 
 #include "dm_internal.h"
+#include "dm_kernels.cuh"
 
 namespace dm {
 
@@ -49,7 +51,9 @@ struct PartArgs {
   double *Zb;                  // [nparts][10][10]: L^{-1} C_bot in the last 10 rows
   double *ct, *cb, *co;        // [nparts][110]: top/bottom contributions (10x10 + 10), top x bottom (10x10)
   double *Xs;                  // [nsep][110]: T'^{-1} [To | g']
-  int *bad;
+  const int32_t *p_sys;        // interior -> system (index into go / bad)
+  const int32_t *go;           // per system: solve it (NULL: all)
+  int *bad;                    // per system: zero or non-finite pivot
 };
 
 // pair t in [0, 55) -> (u, v), 0 <= v <= u < 10
@@ -62,6 +66,8 @@ __device__ __forceinline__ void pair_uv(int t, int &u, int &v) {
 __global__ void __launch_bounds__(32) k_part_factor(PartArgs a) {
   extern __shared__ double sm[];
   const int p = blockIdx.x, lane = threadIdx.x;
+  const int sys = a.p_sys[p];
+  if (a.go && !a.go[sys]) return;
   const int r0 = a.p_a[p], mm = a.p_mm[p];
   const bool top = a.p_top[p] >= 0, bot = a.p_bot[p] >= 0;
   double *Bs = sm;                     // [mm][11]: band, then multipliers
@@ -76,7 +82,7 @@ __global__ void __launch_bounds__(32) k_part_factor(PartArgs a) {
   for (int j = 0; j < mm; ++j) {
     const double dj = Bs[j * 11];
     if (!(fabs(dj) > 0.0) || !isfinite(dj)) {
-      if (lane == 0) atomicExch(a.bad, 1);
+      if (lane == 0) atomicExch(a.bad + sys, 1);
       return;  // uniform: every lane read the same pivot
     }
     const double rj = pb_recip(dj);
@@ -210,7 +216,7 @@ __global__ void __launch_bounds__(32) k_part_separators(PartArgs a) {
   __shared__ double Tp[PW][PW + 1];  // To of the previous separator
   const int sys = blockIdx.x, lane = threadIdx.x;
   const int s0 = a.sys_sep0[sys], ns = a.sys_nsep[sys];
-  if (ns == 0) return;
+  if (ns == 0 || (a.go && !a.go[sys]) || a.bad[sys]) return;
   const int64_t N = a.ntot;
   // forward elimination: separator s couples to s+1 through interior s+1
   for (int s = 0; s < ns; ++s) {
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(32) k_part_separators(PartArgs a) {
     }
     __syncwarp();
     if (!gj10(M, lane, 2 * PW + 1)) {
-      if (lane == 0) atomicExch(a.bad, 1);
+      if (lane == 0) atomicExch(a.bad + sys, 1);
       return;
     }
     double *Xo = a.Xs + (size_t)gs * 110;
@@ -285,6 +291,7 @@ __global__ void __launch_bounds__(32) k_part_separators(PartArgs a) {
 
 __global__ void __launch_bounds__(32) k_part_back(PartArgs a) {
   const int p = blockIdx.x, lane = threadIdx.x;
+  if ((a.go && !a.go[a.p_sys[p]]) || a.bad[a.p_sys[p]]) return;
   const int r0 = a.p_a[p], mm = a.p_mm[p];
   const int st = a.p_top[p], sb = a.p_bot[p];
   const int lo = mm - PW;  // interiors have at least 11 rows
@@ -318,7 +325,280 @@ __global__ void __launch_bounds__(32) k_part_back(PartArgs a) {
   }
 }
 
+// Newton rounds of long rods (the partitioned path of dm_step): the
+// bookkeeping of the rod solver (converged, failed or solving this round),
+// the right-hand side -f, and after the solve q += dq.
+struct LongArgs {
+  int nlong;
+  const int32_t *sys;                 // long system -> system index
+  const int32_t *sys_dof0, *sys_ndof;  // per system
+  double tol;
+  int max_iter;
+  const double *f;
+  double *q, *dq, *rhs;
+  int32_t *sys_active, *sys_iters, *sys_status;
+  const unsigned long long *sys_res;
+  int32_t *ctrl;
+  const int32_t *ls_action;
+  int32_t *ls_trial;
+  int32_t *go;
+  int *bad;
+};
+
+__global__ void k_long_decide(LongArgs a) {
+  __shared__ int go_s;
+  const int k = blockIdx.x;
+  const int s = a.sys[k];
+  if (threadIdx.x == 0) {
+    int go = 0;
+    a.bad[k] = 0;
+    if (a.sys_active[s]) {
+      if (a.ls_action && a.ls_action[s] == 1) {  // backtracking: no solve this round
+        atomicAdd(&a.ctrl[0], 1);
+      } else {
+        const double res = __longlong_as_double((long long)a.sys_res[s]);
+        int st = a.sys_status[s];
+        if (st == 0 && isnan(res)) st = DM_ERR_NONFINITE;
+        if (st == 0 && res <= a.tol) {
+          a.sys_active[s] = 0;
+        } else {
+          if (st == 0 && a.sys_iters[s] >= a.max_iter) st = DM_ERR_NOT_CONVERGED;
+          if (st != 0) {
+            a.sys_status[s] = st;
+            a.sys_active[s] = 0;
+            atomicAdd(&a.ctrl[1], 1);
+            atomicMin(&a.ctrl[2], s);
+          } else {
+            go = 1;
+          }
+        }
+      }
+    }
+    a.go[k] = go;
+    go_s = go;
+  }
+  __syncthreads();
+  if (!go_s) return;
+  const int d0 = a.sys_dof0[s], n = a.sys_ndof[s];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a.rhs[d0 + i] = -a.f[d0 + i];
+}
+
+__global__ void k_long_finish(LongArgs a) {
+  const int k = blockIdx.x;
+  if (!a.go[k]) return;
+  const int s = a.sys[k];
+  if (a.bad[k]) {
+    if (threadIdx.x == 0) {
+      a.sys_status[s] = DM_ERR_DEGENERATE;
+      a.sys_active[s] = 0;
+      atomicAdd(&a.ctrl[1], 1);
+      atomicMin(&a.ctrl[2], s);
+    }
+    return;
+  }
+  const int d0 = a.sys_dof0[s], n = a.sys_ndof[s];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a.q[d0 + i] += a.dq[d0 + i];
+  if (threadIdx.x == 0) {
+    a.sys_iters[s] += 1;
+    if (a.ls_trial) a.ls_trial[s] = 1;
+    atomicAdd(&a.ctrl[0], 1);
+  }
+}
+
 }  // namespace
+
+// Host plan of a partitioned solve: interiors, separators and scratch for
+// a fixed set of systems.
+struct PartPlan {
+  int np = 0, nsep = 0, nsys = 0;
+  size_t smem = 0;
+  char *scr = nullptr;
+  PartArgs A{};
+};
+
+static void part_plan_free(PartPlan &P) {
+  if (P.scr) cudaFree(P.scr);
+  P.scr = nullptr;
+}
+
+// layout: interiors [k m, k m + m - 10), separators [k m + m - 10, (k+1) m),
+// the last interior [(P-1) m, n) with at least 11 rows
+static dm_status part_plan_build(int nsys, const int32_t *sys_dof0, const int32_t *sys_ndof,
+                                 int64_t ntot, int m, PartPlan &P, cudaStream_t st) {
+  std::vector<int32_t> pa, pmm, ptop, pbot, psys, sa, s0(nsys), nsp(nsys);
+  for (int k = 0; k < nsys; ++k) {
+    const int n = sys_ndof[k], d0 = sys_dof0[k];
+    if (n <= 0 || d0 < 0 || (int64_t)d0 + n > ntot) {
+      set_error("partitioned band solve: system outside the vectors");
+      return DM_ERR_INVALID_ARG;
+    }
+    int np = (n - 1) / m + 1;
+    while (np > 1 && n - (np - 1) * m < PW + 1) --np;
+    s0[k] = (int32_t)sa.size();
+    nsp[k] = np - 1;
+    for (int p = 0; p < np; ++p) {
+      const int a = p * m, b = p + 1 < np ? a + m - PW : n;
+      pa.push_back(d0 + a);
+      pmm.push_back(b - a);
+      psys.push_back(k);
+      // the top separator of interior p > 0 is the bottom one of p - 1
+      ptop.push_back(p > 0 ? pbot.back() : -1);
+      if (p + 1 < np) sa.push_back(d0 + b);
+      pbot.push_back(p + 1 < np ? (int32_t)sa.size() - 1 : -1);
+    }
+  }
+  const int np = (int)pa.size(), nsep = (int)sa.size();
+  P.np = np;
+  P.nsep = nsep;
+  P.nsys = nsys;
+  size_t bytes = 0;
+  auto take = [&](size_t n, size_t elt) {
+    const size_t o = bytes;
+    bytes += (n * elt + 255) / 256 * 256;
+    return o;
+  };
+  const size_t oL = take((size_t)ntot * PW, 8), oD = take(ntot, 8), oZ = take((size_t)ntot * PW, 8),
+               oz = take(ntot, 8), oZb = take((size_t)np * PW * PW, 8), oct = take((size_t)np * 110, 8),
+               ocb = take((size_t)np * 110, 8), oco = take((size_t)np * 110, 8),
+               oX = take((size_t)std::max(nsep, 1) * 110, 8),
+               oI = take(5 * (size_t)np + (size_t)nsep + 3 * (size_t)nsys + 1, 4);
+  if (cudaMalloc(&P.scr, bytes) != cudaSuccess) {
+    set_error("partitioned band solve: cudaMalloc");
+    return DM_ERR_OOM;
+  }
+  std::vector<int32_t> ints;
+  for (auto *v : {&pa, &pmm, &ptop, &pbot, &psys, &sa, &s0, &nsp}) ints.insert(ints.end(), v->begin(), v->end());
+  ints.resize(ints.size() + nsys, 0);  // bad flags
+  int32_t *ib = reinterpret_cast<int32_t *>(P.scr + oI);
+  PartArgs &A = P.A;
+  A.ntot = ntot;
+  A.nparts = np;
+  A.nsep = nsep;
+  A.p_a = ib;
+  A.p_mm = ib + np;
+  A.p_top = ib + 2 * np;
+  A.p_bot = ib + 3 * np;
+  A.p_sys = ib + 4 * np;
+  A.s_a = ib + 5 * np;
+  A.sys_sep0 = ib + 5 * np + nsep;
+  A.sys_nsep = ib + 5 * np + nsep + nsys;
+  A.bad = ib + 5 * np + nsep + 2 * nsys;
+  A.Lf = reinterpret_cast<double *>(P.scr + oL);
+  A.Df = reinterpret_cast<double *>(P.scr + oD);
+  A.Zt = reinterpret_cast<double *>(P.scr + oZ);
+  A.zf = reinterpret_cast<double *>(P.scr + oz);
+  A.Zb = reinterpret_cast<double *>(P.scr + oZb);
+  A.ct = reinterpret_cast<double *>(P.scr + oct);
+  A.cb = reinterpret_cast<double *>(P.scr + ocb);
+  A.co = reinterpret_cast<double *>(P.scr + oco);
+  A.Xs = reinterpret_cast<double *>(P.scr + oX);
+  cudaError_t e = cudaMemcpyAsync(ib, ints.data(), ints.size() * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.scr + oct, 0, oX - oct, st);
+  int mmax = 0;
+  for (int v : pmm) mmax = std::max(mmax, v);
+  P.smem = (size_t)mmax * (11 + PW) * sizeof(double);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_part_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)P.smem);
+  if (e != cudaSuccess) {
+    part_plan_free(P);
+    set_error(std::string("partitioned band solve: ") + cudaGetErrorString(e));
+    return DM_ERR_CUDA;
+  }
+  return DM_OK;
+}
+
+static cudaError_t part_launch(const PartPlan &P, const double *band, const double *rhs,
+                               double *x, const int32_t *go, cudaStream_t st) {
+  PartArgs A = P.A;
+  A.band = band;
+  A.rhs = rhs;
+  A.x = x;
+  A.go = go;
+  k_part_factor<<<P.np, 32, P.smem, st>>>(A);
+  if (P.nsep > 0) k_part_separators<<<P.nsys, 32, 0, st>>>(A);
+  k_part_back<<<P.np, 32, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+struct LongRods {
+  PartPlan plan;
+  LongArgs la{};
+  std::vector<void *> allocs;
+};
+
+dm_status long_rods_create(dm_system *s, const std::vector<int32_t> &sys, int part_rows,
+                           LongRods **out) {
+  *out = nullptr;
+  if (sys.empty()) return DM_OK;
+  const HostTopology &T = s->T;
+  auto *L = new LongRods();
+  const int nl = (int)sys.size();
+  std::vector<int32_t> d0(nl), nd(nl);
+  for (int k = 0; k < nl; ++k) {
+    d0[k] = T.sys_dof0[sys[k]];
+    nd[k] = T.sys_ndof[sys[k]];
+  }
+  dm_status r = part_plan_build(nl, d0.data(), nd.data(), T.n_dofs, part_rows, L->plan, s->stream);
+  auto dal = [&](void **p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+    L->allocs.push_back(*p);
+    return true;
+  };
+  int32_t *dsys = nullptr, *dgo = nullptr;
+  double *drhs = nullptr;
+  if (r == DM_OK && (!dal((void **)&dsys, nl * 4) || !dal((void **)&dgo, nl * 4) ||
+                     !dal((void **)&drhs, (size_t)T.n_dofs * 8))) {
+    set_error("long rods: cudaMalloc");
+    r = DM_ERR_OOM;
+  }
+  if (r == DM_OK && cudaMemcpy(dsys, sys.data(), nl * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    r = DM_ERR_CUDA;
+  if (r != DM_OK) {
+    long_rods_free(L);
+    return r;
+  }
+  L->la.nlong = nl;
+  L->la.sys = dsys;
+  L->la.go = dgo;
+  L->la.rhs = drhs;
+  L->la.bad = L->plan.A.bad;
+  *out = L;
+  return DM_OK;
+}
+
+void long_rods_free(LongRods *L) {
+  if (!L) return;
+  part_plan_free(L->plan);
+  for (void *p : L->allocs) cudaFree(p);
+  delete L;
+}
+
+int long_rods_count(const LongRods *L) { return L ? L->la.nlong : 0; }
+
+cudaError_t long_rods_round(LongRods *L, const SolveArgs &v, cudaStream_t st) {
+  LongArgs a = L->la;
+  a.sys_dof0 = v.sys_dof0;
+  a.sys_ndof = v.sys_ndof;
+  a.tol = v.tol;
+  a.max_iter = v.max_iter;
+  a.f = v.f;
+  a.q = v.q;
+  a.dq = v.dq;
+  a.sys_active = v.sys_active;
+  a.sys_iters = v.sys_iters;
+  a.sys_status = v.sys_status;
+  a.sys_res = v.sys_res;
+  a.ctrl = v.ctrl;
+  a.ls_action = v.ls_action;
+  a.ls_trial = v.ls_trial;
+  k_long_decide<<<a.nlong, 256, 0, st>>>(a);
+  cudaError_t e = part_launch(L->plan, v.band, a.rhs, a.dq, a.go, st);
+  if (e != cudaSuccess) return e;
+  k_long_finish<<<a.nlong, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
 
 }  // namespace dm
 
@@ -337,110 +617,26 @@ extern "C" dm_status dm_solve_band_partitioned(int32_t nsys, const int32_t *sys_
     set_error("dm_solve_band_partitioned: part_rows must be in [21, 1024]");
     return DM_ERR_INVALID_ARG;
   }
-  // layout: interiors [k m, k m + m - 10), separators [k m + m - 10, (k+1) m),
-  // the last interior [(P-1) m, n) with at least 11 rows
-  std::vector<int32_t> pa, pmm, ptop, pbot, sa, s0(nsys), nsp(nsys);
-  for (int k = 0; k < nsys; ++k) {
-    const int n = sys_ndof[k], d0 = sys_dof0[k];
-    if (n <= 0 || d0 < 0 || (int64_t)d0 + n > ntot) {
-      set_error("dm_solve_band_partitioned: system outside the vectors");
-      return DM_ERR_INVALID_ARG;
-    }
-    int P = (n - 1) / m + 1;
-    while (P > 1 && n - (P - 1) * m < PW + 1) --P;
-    s0[k] = (int32_t)sa.size();
-    nsp[k] = P - 1;
-    for (int p = 0; p < P; ++p) {
-      const int a = p * m, b = p + 1 < P ? a + m - PW : n;
-      pa.push_back(d0 + a);
-      pmm.push_back(b - a);
-      // the top separator of interior p > 0 is the bottom one of p - 1
-      ptop.push_back(p > 0 ? pbot.back() : -1);
-      if (p + 1 < P) sa.push_back(d0 + b);
-      pbot.push_back(p + 1 < P ? (int32_t)sa.size() - 1 : -1);
-    }
-  }
-  const int np = (int)pa.size(), nsep = (int)sa.size();
-  if (np == 0) return DM_OK;
+  if (nsys == 0) return DM_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  // scratch
-  size_t bytes = 0;
-  auto take = [&](size_t n) {
-    const size_t o = bytes;
-    bytes += (n * sizeof(double) + 255) / 256 * 256;
-    return o;
-  };
-  const size_t oL = take((size_t)ntot * PW), oD = take(ntot), oZ = take((size_t)ntot * PW),
-               oz = take(ntot), oZb = take((size_t)np * PW * PW), oct = take((size_t)np * 110),
-               ocb = take((size_t)np * 110), oco = take((size_t)np * 110),
-               oX = take((size_t)std::max(nsep, 1) * 110), oI = take((4 * (size_t)np + 3 * nsys +
-                                                                      (size_t)nsep + 8) / 2 + 1);
-  char *scr = nullptr;
-  if (cudaMalloc(&scr, bytes) != cudaSuccess) {
-    set_error("dm_solve_band_partitioned: cudaMalloc");
-    return DM_ERR_OOM;
-  }
-  int32_t *ib = reinterpret_cast<int32_t *>(scr + oI);
-  std::vector<int32_t> ints;
-  ints.insert(ints.end(), pa.begin(), pa.end());
-  ints.insert(ints.end(), pmm.begin(), pmm.end());
-  ints.insert(ints.end(), ptop.begin(), ptop.end());
-  ints.insert(ints.end(), pbot.begin(), pbot.end());
-  ints.insert(ints.end(), sa.begin(), sa.end());
-  ints.insert(ints.end(), s0.begin(), s0.end());
-  ints.insert(ints.end(), nsp.begin(), nsp.end());
-  ints.push_back(0);  // bad flag
-  PartArgs A{};
-  A.ntot = ntot;
-  A.nparts = np;
-  A.nsep = nsep;
-  A.p_a = ib;
-  A.p_mm = ib + np;
-  A.p_top = ib + 2 * np;
-  A.p_bot = ib + 3 * np;
-  A.s_a = ib + 4 * np;
-  A.sys_sep0 = ib + 4 * np + nsep;
-  A.sys_nsep = ib + 4 * np + nsep + nsys;
-  A.bad = ib + 4 * np + nsep + 2 * nsys;
-  A.band = band;
-  A.rhs = rhs;
-  A.x = x;
-  A.Lf = reinterpret_cast<double *>(scr + oL);
-  A.Df = reinterpret_cast<double *>(scr + oD);
-  A.Zt = reinterpret_cast<double *>(scr + oZ);
-  A.zf = reinterpret_cast<double *>(scr + oz);
-  A.Zb = reinterpret_cast<double *>(scr + oZb);
-  A.ct = reinterpret_cast<double *>(scr + oct);
-  A.cb = reinterpret_cast<double *>(scr + ocb);
-  A.co = reinterpret_cast<double *>(scr + oco);
-  A.Xs = reinterpret_cast<double *>(scr + oX);
-  cudaError_t e = cudaMemcpyAsync(ib, ints.data(), ints.size() * sizeof(int32_t),
-                                  cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(scr + oct, 0, oX - oct, st);
-  int mmax = 0;
-  for (int v : pmm) mmax = std::max(mmax, v);
-  const size_t smem = (size_t)mmax * (11 + PW) * sizeof(double);
+  PartPlan P;
+  dm_status r = part_plan_build(nsys, sys_dof0, sys_ndof, ntot, m, P, st);
+  if (r != DM_OK) return r;
+  cudaError_t e = part_launch(P, band, rhs, x, nullptr, st);
+  std::vector<int> bad(nsys, 0);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_part_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-  if (e == cudaSuccess) {
-    k_part_factor<<<np, 32, smem, st>>>(A);
-    if (nsep > 0) k_part_separators<<<nsys, 32, 0, st>>>(A);
-    k_part_back<<<np, 32, 0, st>>>(A);
-    e = cudaGetLastError();
-  }
-  int bad = 0;
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&bad, A.bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(bad.data(), P.A.bad, nsys * sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(scr);
+  part_plan_free(P);
   if (e != cudaSuccess) {
     set_error(std::string("dm_solve_band_partitioned: ") + cudaGetErrorString(e));
     return DM_ERR_CUDA;
   }
-  if (bad) {
-    set_error("dm_solve_band_partitioned: zero or non-finite pivot");
-    return DM_ERR_DEGENERATE;
-  }
+  for (int k = 0; k < nsys; ++k)
+    if (bad[k]) {
+      set_error("dm_solve_band_partitioned: zero or non-finite pivot in system " +
+                std::to_string(k));
+      return DM_ERR_DEGENERATE;
+    }
   return DM_OK;
 }

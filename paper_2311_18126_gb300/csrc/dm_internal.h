@@ -197,6 +197,15 @@ int32_t *ws_trial_flags(dm_system *s);
 // (before a commit overwrites it, and after a state is set).
 cudaError_t ws_keep_velocity(dm_system *s, cudaStream_t st);
 
+// Long rods (dm_band_partitioned.cu): the systems `sys` are solved in the
+// Newton rounds by the partitioned band solve (interiors of part_rows - 10
+// rows).  long_rods_round is declared with the kernel arguments.
+struct LongRods;
+dm_status long_rods_create(dm_system *s, const std::vector<int32_t> &sys, int part_rows,
+                           LongRods **out);
+void long_rods_free(LongRods *L);
+int long_rods_count(const LongRods *L);
+
 }  // namespace dm
 
 struct dm_system {

@@ -222,6 +222,8 @@ __global__ void k_commit(StepArgs a);
 __global__ void k_restore(StepArgs a);
 __global__ void k_round_continue(int32_t *ctrl, int max_rounds, cudaGraphConditionalHandle h);
 __global__ void k_midpoint_finish(StepArgs a, double *vnew);
+// Newton round of the long rods: bookkeeping, partitioned solve, q += dq.
+cudaError_t long_rods_round(LongRods *L, const SolveArgs &v, cudaStream_t st);
 __global__ void k_collect_failures(int nsys, const int32_t *sys_status, int32_t *ctrl);
 __global__ void k_tangents(int ne, const int32_t *edge_a, const int32_t *edge_b,
                            const double *q, double *tn, int32_t *bad);

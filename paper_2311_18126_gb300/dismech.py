@@ -40,7 +40,8 @@ class Params(C.Structure):
                 ("gravity", C.c_double * 3), ("damping", C.c_double), ("ground", C.c_int32),
                 ("ground_z", C.c_double), ("delta", C.c_double), ("slip_nu", C.c_double),
                 ("self_contact", C.c_int32), ("pair_kc", C.c_double), ("pair_mu", C.c_double),
-                ("line_search", C.c_int32), ("stream", C.c_void_p), ("integrator", C.c_int32)]
+                ("line_search", C.c_int32), ("stream", C.c_void_p), ("integrator", C.c_int32),
+                ("long_rod_dofs", C.c_int32)]
 
 INTEGRATORS = {"be": 0, "midpoint": 1}
 
@@ -269,6 +270,7 @@ class System:
         if integ not in INTEGRATORS:
             raise ValueError("integrator must be one of %s" % sorted(INTEGRATORS))
         p.integrator = INTEGRATORS[integ]
+        p.long_rod_dofs = int(params.get("long_rod_dofs", 0))
         h = C.c_void_p()
         _check(lib.dm_create_system(C.byref(d), C.byref(p), C.byref(h)))
         self._h = h
