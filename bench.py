@@ -75,10 +75,13 @@ def parse():
     ap.add_argument("--rods", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="uneven_rods",
-                    choices=["uneven_rods", "star_robots", "coil", "gripper", "warm_start",
+                    choices=["uneven_rods", "star_robots", "coil", "gripper", "long_rods",
+                             "warm_start",
                              "warm_start_rods", "calibration", "mlp"],
                     help="uneven_rods: the headline batch (default); star_robots: limbed "
                          "robots on the ground with a gait; coil: edge-edge self-contact; "
+                         "long_rods: 64 rods of 4000-6000 nodes, partitioned vs sequential "
+                         "band solve; "
                          "gripper: five 60-node fingers entangling with frictional contact "
                          "between them; "
                          "warm_start: learned vs extrapolated Newton guess on star robots; "
@@ -475,6 +478,14 @@ def run_other(args):
         controls = lambda k: kbar
         line["config"] = {"workload": WORKLOAD, "rods_per_gpu": args.rods,
                           "l2": "no flush: per-iteration working set (~0.7 GB) exceeds L2"}
+    elif args.workload == "long_rods":
+        desc, params, kbar = workloads.uneven_rods(n_rods=64, seed=rank_seed(rank),
+                                                   n_min=4000, n_max=6000)
+        controls = lambda k: kbar
+        line["config"] = {"workload": "long_rods: 64 clamped rods of 4000-6000 nodes "
+                          "(16k-24k DOFs each), uneven_rods recipe otherwise, dt=1e-3 s; "
+                          "rods of >= 2048 DOFs on the partitioned band solve",
+                          "rods_per_gpu": 64, "l2": "no flush: working set exceeds L2"}
     elif args.workload == "gripper":
         desc, params, kfn = workloads.gripper()
         dt = params["dt"]
@@ -604,6 +615,15 @@ def run_other(args):
         prof = sysm.get_profile()
         sysm.set_profiling(False)
         k1 = warm + args.steps
+        if args.workload == "long_rods":
+            # the same steps from the same state with every rod on the
+            # sequential twisted LDL^T
+            seq = System(desc, dict(params, long_rod_dofs=-1))
+            seq.set_natural_curvature(0, R, controls(0))
+            _restore(seq, snap)
+            seq_ms, _, _ = _timed_steps(seq, args.steps, controls, warm, local, clocks=False)
+            seq.close()
+            line["sequential_solve_ms_per_step"] = seq_ms / args.steps
         # end to end through the C ABI: pinned host state in and out every step
         n = sysm.n_state
         hq = torch.empty(n, dtype=torch.float64, pin_memory=True)
