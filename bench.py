@@ -145,10 +145,18 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        # nvidia-smi takes a moment to start: wait (at most 3 s) for its first
+        # sample so that the timed region that follows is sampled throughout
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -387,10 +395,10 @@ def run_ours(args):
                              "same kernels and launch shapes)",
             "roofline": roof, "kernels": kernels}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rods = sample_rods(R, 8)
-        v, dt, cores, nodes = oracle_rate(desc, params, kbar, rods, 2)
+        rods = sample_rods(R, 16)
+        v, dt, cores, nodes = oracle_rate(desc, params, kbar, rods, 5)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "8 seeded rods (%d nodes) of the batch, 2 steps "
+                                "sample": "16 seeded rods (%d nodes) of the batch, 5 steps "
                                           "from the initial state, %.1f s" % (nodes, dt)}
     if rank == 0:
         print(json.dumps(line))
