@@ -678,3 +678,29 @@ def test_midpoint_momentum_and_energy():
     assert np.abs(Es - E0).max() <= 1e-3 * E0
     E0, Es = out["be"]
     assert Es[-1] < 0.9 * E0
+
+
+def test_contact_group_pair_candidates_brute_force():
+    # two 6-node rods declared one contact group: one system, and the
+    # candidate edge pairs (reading C16) are every pair of edges of
+    # different rods plus the pairs of one rod at least three edges apart,
+    # enumerated here by brute force
+    from oracle.contact import pair_candidates_all
+    x0 = np.concatenate([straight(6, 0.05), straight(6, 0.05) + [0.0, 0.01, 0.0]])
+    desc = dict(nodes_per_rod=[6, 6], x0=x0, E=[1e6] * 2, nu=[0.5] * 2, rho=[1e3] * 2,
+                radius=[1e-3] * 2, contact_groups=[[0, 1]])
+    o = OracleSystems(desc, dict(self_contact=True, pair_kc=1.0, delta=1e-4))
+    assert len(o.systems) == 1
+    s = o.systems[0]
+    got = {tuple(p) for p in pair_candidates_all(o, s).tolist()}
+    want = set()
+    ne = len(s.edges)
+    for i in range(ne):
+        for j in range(i + 1, ne):
+            ri, rj = s.edge_rod[i], s.edge_rod[j]
+            if ri != rj or abs(i - j) >= 3:
+                want.add((i, j))
+    assert got == want and len(want) == 25 + 2 * 3
+    # without the group the rods are two systems
+    desc.pop("contact_groups")
+    assert len(OracleSystems(desc, dict(self_contact=True, pair_kc=1.0)).systems) == 2
