@@ -228,8 +228,9 @@ dm_status dm_solve_band(int32_t nsys, const int32_t *sys_dof0, const int32_t *sy
  * only, by symmetry), a warp per system solves the block-tridiagonal
  * separator system (10 x 10 blocks, Gauss-Jordan with partial pivoting), and
  * a warp per interior back-substitutes.  Arguments as dm_solve_band, plus
- * part_rows (0 = 512; otherwise 21..1024).  Interiors are factored without
- * pivoting, like the full band.  Allocates device scratch (about 170 bytes
+ * part_rows (0 = 512; otherwise 21..1024).  Interiors and separator blocks
+ * are eliminated without pivoting (the rod Jacobian, and with it every
+ * Schur complement, is symmetric positive definite), like the full band.  Allocates device scratch (about 170 bytes
  * per DOF); returns after the solve has finished; DM_ERR_DEGENERATE on a
  * zero or non-finite pivot. */
 dm_status dm_solve_band_partitioned(int32_t nsys, const int32_t *sys_dof0,

@@ -10,13 +10,13 @@
 //      Z_p^T D^{-1} Z_p and Z_p^T D^{-1} z_p (symmetry: only forward solves);
 //   2. per system: the separators' block-tridiagonal Schur system
 //      T x_S = g, T = A_SS - sum_p C_p^T B_p^{-1} C_p, eliminated block by
-//      block (10 x 10, Gauss-Jordan with partial pivoting);
+//      block (10 x 10 Gauss-Jordan, no pivoting: symmetric positive definite);
 //   3. per interior, in parallel: x_p = L^{-T} D^{-1} (z_p - Z_p x_S).
 //
 // The work per interior is a few times that of the plain band LDL^T, but
 // the sequential depth is m rows plus one 10 x 10 elimination per
 // separator instead of n rows.  One warp per interior or system; an
-// interior keeps its band and its top coupling solve in shared memory.
+// interior keeps its band in shared memory.
 #include <string>
 #include <vector>
 
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(32) k_part_factor(PartArgs a) {
   const int r0 = a.p_a[p], mm = a.p_mm[p];
   const bool top = a.p_top[p] >= 0, bot = a.p_bot[p] >= 0;
   double *Bs = sm;                     // [mm][11]: band, then multipliers
-  double *Zs = sm + (size_t)mm * 11;   // [mm][10]: L^{-1} C_top
+  double *Zs = a.Zt + (size_t)r0 * PW;  // [mm][10]: L^{-1} C_top (global, L2-resident)
   const int64_t N = a.ntot;
   for (int t = lane; t < mm * 11; t += 32) {
     const int i = t / 11, d = t - i * 11;
@@ -128,7 +128,6 @@ __global__ void __launch_bounds__(32) k_part_factor(PartArgs a) {
     win[0] = z;
     if (lane < PW) {
       Zs[i * PW + c] = z;
-      a.Zt[(size_t)(r0 + i) * PW + c] = z;
     } else if (lane == PW) {
       a.zf[r0 + i] = z;
     } else if (lane < 2 * PW + 1 && i >= mm - PW && mm >= PW) {
@@ -171,28 +170,12 @@ __global__ void __launch_bounds__(32) k_part_factor(PartArgs a) {
   }
 }
 
-// Gauss-Jordan with partial pivoting on M [10][21] in shared memory, lane j
-// owning column j: M <- [I | M_left^{-1} M_right].  Returns false on a zero
-// or non-finite pivot.
+// Gauss-Jordan on M [10][21] in shared memory, lane j owning column j:
+// M <- [I | M_left^{-1} M_right].  No pivoting: M_left is a Schur complement
+// of the symmetric positive definite rod Jacobian, itself symmetric positive
+// definite.  Returns false on a zero or non-finite pivot.
 __device__ bool gj10(double (*M)[22], int lane, int ncol) {
   for (int k = 0; k < PW; ++k) {
-    int piv = k;
-    if (lane == 0) {
-      double best = fabs(M[k][k]);
-      for (int i = k + 1; i < PW; ++i)
-        if (fabs(M[i][k]) > best) {
-          best = fabs(M[i][k]);
-          piv = i;
-        }
-    }
-    piv = __shfl_sync(0xffffffffu, piv, 0);
-    __syncwarp();
-    if (lane < ncol && piv != k) {
-      const double tmp = M[k][lane];
-      M[k][lane] = M[piv][lane];
-      M[piv][lane] = tmp;
-    }
-    __syncwarp();
     const double pk = M[k][k];
     if (!(fabs(pk) > 0.0) || !isfinite(pk)) return false;
     const double r = pb_recip(pk);
@@ -497,7 +480,7 @@ static dm_status part_plan_build(int nsys, const int32_t *sys_dof0, const int32_
   if (e == cudaSuccess) e = cudaMemsetAsync(P.scr + oct, 0, oX - oct, st);
   int mmax = 0;
   for (int v : pmm) mmax = std::max(mmax, v);
-  P.smem = (size_t)mmax * (11 + PW) * sizeof(double);
+  P.smem = (size_t)mmax * 11 * sizeof(double);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_part_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)P.smem);
