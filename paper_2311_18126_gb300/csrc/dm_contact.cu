@@ -636,8 +636,11 @@ __global__ void __launch_bounds__(256) k_lu_diag(ContactArgs a, int c, int k) {
       if (threadIdx.x == 0) a.cbad[c] = 1;
       return;  // uniform: every thread read the same pivot
     }
-    const double rp = lu_recip(piv);
-    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) D[i][j] *= rp;
+    // only the threads that scale the column take the reciprocal
+    if (j + 1 + (int)threadIdx.x < nb) {
+      const double rp = lu_recip(piv);
+      for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) D[i][j] *= rp;
+    }
     __syncthreads();
     const int m = nb - 1 - j;
     for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
