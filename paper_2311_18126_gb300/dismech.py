@@ -195,8 +195,12 @@ class System:
 
     ``desc``: dict with nodes_per_rod, x0, E, nu, rho, radius and optional
     v0, theta0, theta_dot0, joints (list of [(rod, node), ...]), fixed,
-    ground_mu, ground_kc.  ``params``: dt, tol, max_iter, g, eta, ground,
-    ground_z, delta, nu_slip, self_contact, pair_kc, pair_mu, stream.
+    ground_mu, ground_kc, contact_groups (list of lists of consecutive rods
+    solved as one system so that they can touch each other).  ``params``:
+    dt, tol, max_iter, g, eta, ground, ground_z, delta, nu_slip,
+    self_contact, pair_kc, pair_mu, line_search, integrator ("be" or
+    "midpoint"), long_rod_dofs (rods with at least this many DOFs use the
+    partitioned band solve; 0 = 2048, negative = never), stream.
     """
 
     def __init__(self, desc, params):
