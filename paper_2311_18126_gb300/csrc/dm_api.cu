@@ -779,7 +779,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       DM_CK(cudaMemsetAsync(c.fc, 0, nd * sizeof(double), rs));
       DM_CK(cudaMemsetAsync(c.npairs, 0, sizeof(int32_t), rs));
       DM_CK(cudaMemsetAsync(c.bucket_count, 0, c.table * sizeof(int32_t), rs));
-      k_cc_clear<<<blocks(nd, 256), 256, 0, rs>>>(ca);
+      k_cc_clear<<<blocks((int64_t)nd * 32, 256), 256, 0, rs>>>(ca);
       k_cc_reset_bw<<<blocks(S, 256), 256, 0, rs>>>(ca);
       k_cc_cells<<<blocks(ne, 256), 256, 0, rs>>>(ca);
       k_cc_scan<<<1, 1024, 0, rs>>>(ca);
@@ -1469,7 +1469,7 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
     DM_CK(cudaMemsetAsync(c.fc, 0, nd * sizeof(double), st));
     DM_CK(cudaMemsetAsync(c.npairs, 0, sizeof(int32_t), st));
     DM_CK(cudaMemsetAsync(c.bucket_count, 0, c.table * sizeof(int32_t), st));
-    k_cc_clear<<<blocks(nd, 256), 256, 0, st>>>(ca);
+    k_cc_clear<<<blocks((int64_t)nd * 32, 256), 256, 0, st>>>(ca);
     k_cc_reset_bw<<<blocks(S, 256), 256, 0, st>>>(ca);
     k_cc_cells<<<blocks(ne, 256), 256, 0, st>>>(ca);
     k_cc_scan<<<1, 1024, 0, st>>>(ca);

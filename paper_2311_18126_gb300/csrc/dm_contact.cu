@@ -546,15 +546,17 @@ __global__ void k_cc_band(ContactArgs a) {
 }
 
 // Clears the band (of the last bandwidth) of each active contact system.
+// A warp per matrix row, lanes striding along it (coalesced stores).
 __global__ void k_cc_clear(ContactArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(t >> 5), lane = (int)(t & 31);
   if (i >= a.nd) return;
   const int s = a.dof_sys[i];
   if (a.sys_kind[s] != SOLVE_CONTACT) return;
   const int d0 = a.sys_dof0[s], n = a.sys_ndof[s], r = i - d0;
   const int bw = max(10, a.sys_bw[s]);
   double *M = a.dense + a.sys_dense0[s] + (size_t)r * n;
-  for (int c = max(0, r - bw); c <= min(n - 1, r + bw); ++c) M[c] = 0.0;
+  for (int c = max(0, r - bw) + lane; c <= min(n - 1, r + bw); c += 32) M[c] = 0.0;
 }
 
 __global__ void k_cc_reset_bw(ContactArgs a) {
