@@ -756,7 +756,14 @@ def run_calibration(args):
                        "500 steps, per-step per-limb natural curvature, checkpoints every 50",
                        "rods": R, "params": int(np.prod(c_true.shape)), "seed": 4 + rank},
             "calibration": {"gradient_seconds": tg, "losses": losses}, "clocks": clocks,
-            "e2e": None, "roofline": None}
+            # the pass already runs through the public API with host arrays:
+            # per forward step the controls go in and the state comes out
+            "e2e": {"value": R * T / tg, "unit": "rod-steps/s (loss+gradient pass)",
+                    "h2d_bytes_per_step": int(R * nint * 2 * 8),
+                    "d2h_bytes_per_step": int(2 * len(q0) * 8),
+                    "note": "the loss+gradient pass itself (forward, re-simulation, adjoint), "
+                            "host buffers every step"},
+            "roofline": None}
     if rank == 0:
         print(json.dumps(line))
 
