@@ -704,3 +704,38 @@ def test_contact_group_pair_candidates_brute_force():
     # without the group the rods are two systems
     desc.pop("contact_groups")
     assert len(OracleSystems(desc, dict(self_contact=True, pair_kc=1.0)).systems) == 2
+
+
+@pytest.mark.parametrize("integ", ["be", "midpoint"])
+def test_damped_axial_oscillator_exact_step_map(integ):
+    # one edge along x, node 0 and the twist clamped: node 1 is a linear
+    # oscillator m y'' = -k y - c y' with k = EA/l, m = rho A l/2 and the
+    # viscous damping of reading C8, c = eta V = eta l/2, taken at the
+    # implicit (backward Euler) or mid-step (midpoint) velocity.  Each step
+    # of either scheme is a 2x2 linear map of (y, v), solved here directly.
+    E, h, rho, l, dt, v0, eta = 1e7, 1e-3, 1000.0, 0.1, 2e-5, 0.3, 0.05
+    x = np.array([[0.0, 0.0, 0.0], [l, 0.0, 0.0]])
+    fixed = np.zeros(7, np.uint8)
+    fixed[0:4] = 1
+    vel = np.zeros((2, 3))
+    vel[1, 0] = v0
+    o = OracleSystems(rod_desc(x, E=E, h=h, rho=rho, fixed=fixed, v0=vel),
+                      dict(g=(0, 0, 0), dt=dt, eta=eta, integrator=integ))
+    s = o.systems[0]
+    A = math.pi * h * h
+    m, k, c = rho * A * l / 2, E * A / l, eta * l / 2
+    if integ == "be":
+        # y' = y + dt v', m (v' - v) = dt (-k y' - c v')
+        Mx = np.array([[1.0, -dt], [dt * k, m + dt * c]])
+        rhs = lambda y, v: np.array([y, m * v])
+    else:
+        # y' = y + dt (v + v')/2, m (v' - v) = dt (-k (y + y')/2 - c (y' - y)/dt)
+        Mx = np.array([[1.0, -dt / 2], [dt * k / 2 + c, m]])
+        rhs = lambda y, v: np.array([y + dt * v / 2, m * v - dt * k * y / 2 + c * y])
+    y, v = 0.0, v0
+    amp = v0 * math.sqrt(m / k)
+    for _ in range(150):
+        y, v = np.linalg.solve(Mx, rhs(y, v))
+        assert o.step_system(s)[0] == 0
+        assert abs(float(s.q[4]) - l - y) <= 1e-9 * amp
+        assert abs(float(s.v[4]) - v) <= 1e-9 * v0
