@@ -113,3 +113,31 @@ def test_degenerate_sizes_and_free_rod():
         qg, vg = gpu.get_state()
         qo, vo = ora.get_state()
         _assert_close(qg, qo, npr, 0.3, 1e-10)
+
+
+def test_full_batch_sampled_rods_in_bench_configuration():
+    """The 4096-rod bench batch in the launch configuration bench.py times
+    (autotuned shapes, Newton rounds as one graph per step): six sampled
+    rods, the longest and the shortest among them, against the oracle run on
+    those rods alone (the rods are independent systems), 3 steps."""
+    desc, params, kbar = workloads.uneven_rods(n_rods=4096, seed=2)
+    gpu = _gpu(desc, params)
+    gpu.set_natural_curvature(0, 4096, kbar)
+    gpu.autotune(steps=2)
+    npr = np.asarray(desc["nodes_per_rod"])
+    rng = np.random.default_rng(123)
+    rods = sorted({int(np.argmax(npr)), int(np.argmin(npr))} |
+                  set(rng.choice(4096, 4, replace=False).tolist()))
+    sub, kb = workloads.subset(desc, rods, kbar)
+    ora = OracleSystems(sub, params)
+    ora.set_natural_curvature(0, len(rods), kb)
+    off = np.concatenate([[0], np.cumsum(4 * npr - 1)])
+    for _ in range(3):
+        gpu.step(1)
+        st = ora.step(1)
+        assert all(x[0] == 0 for x in st), st
+    qg, _ = gpu.get_state()
+    qo, _ = ora.get_state()
+    qs = np.concatenate([qg[off[r]:off[r + 1]] for r in rods])
+    L = max(1.0, float(np.max(np.abs(sub["x0"]))))
+    _assert_close(qs, qo, sub["nodes_per_rod"], L, 1e-9)
