@@ -114,3 +114,54 @@ def test_chain_with_two_jointed_ends_and_mixed_batch():
                 radius=[2e-3, 2.5e-3, 2e-3] * 2, joints=joints, fixed=fixed)
     params = dict(dt=2e-3, tol=1e-10, max_iter=60, g=(0, 0, -9.81), eta=0.05)
     _run(desc, params, 6, 1e-10)
+
+
+def _robot_subset(desc, robots, gait):
+    """Descriptor of whole robots (their limbs and joints) of a star-robot
+    batch, rods renumbered in order."""
+    owner = np.asarray(gait["robot"])
+    rods = [r for r in range(len(owner)) if owner[r] in set(robots)]
+    newid = {r: k for k, r in enumerate(rods)}
+    npr = np.asarray(desc["nodes_per_rod"])
+    noff = np.concatenate([[0], np.cumsum(npr)])
+    foff = np.concatenate([[0], np.cumsum(4 * npr - 1)])
+    out = dict(nodes_per_rod=npr[rods].astype(np.int32))
+    out["x0"] = np.concatenate([desc["x0"].reshape(-1, 3)[noff[r]:noff[r + 1]] for r in rods])
+    for k in ("E", "nu", "rho", "radius", "ground_mu", "ground_kc"):
+        out[k] = np.asarray(desc[k])[rods]
+    out["fixed"] = np.concatenate([desc["fixed"][foff[r]:foff[r + 1]] for r in rods])
+    out["joints"] = [[(newid[r], i) for (r, i) in grp] for grp in desc["joints"]
+                     if grp[0][0] in newid]
+    return out, rods
+
+
+def test_star_robots_full_batch_sampled_robots_in_bench_configuration():
+    """1024 star robots (the star_robots bench workload) autotuned with
+    graph rounds; three sampled robots against the oracle run on those
+    robots alone (robots are independent systems), 3 gait steps."""
+    desc, params, gait = workloads.star_robots(n_robots=1024, seed=3)
+    R = len(desc["nodes_per_rod"])
+    gpu = _gpu(desc, params)
+    dt = params["dt"]
+    gpu.set_natural_curvature(0, R, workloads.gait_kbar(gait, 0.0))
+    gpu.autotune(steps=2)
+    robots = [0, 517, 1023]
+    sub, rods = _robot_subset(desc, robots, gait)
+    ora = OracleSystems(sub, params)
+    npr = np.asarray(desc["nodes_per_rod"])
+    off = np.concatenate([[0], np.cumsum(4 * npr - 1)])
+    nint = gait["nodes_per_limb"] - 2
+    for k in range(3):
+        kb = workloads.gait_kbar(gait, k * dt)
+        gpu.set_natural_curvature(0, R, kb)
+        ora.set_natural_curvature(0, len(rods),
+                                  np.concatenate([kb[r * nint:(r + 1) * nint] for r in rods]))
+        gpu.step(1)
+        st = ora.step(1)
+        assert all(x[0] == 0 for x in st), st
+    qg, _ = gpu.get_state()
+    qo, _ = ora.get_state()
+    qs = np.concatenate([qg[off[r]:off[r + 1]] for r in rods])
+    # the first steps settle the robots onto the ground (many line-search
+    # iterations): Newton ends just under the tolerance on both sides
+    _assert_close(qs, qo, sub["nodes_per_rod"], 1.0, 1e-7)
