@@ -422,7 +422,7 @@ def test_cantilever_first_mode_frequency():
 # Ground contact with friction: the closed form of Sec. IV-C
 # ---------------------------------------------------------------------------
 
-def _sliding_energy(push, T):
+def _sliding_energy(push, T, integ="be"):
     gold = json.load(open(os.path.join(GOLD, "friction_validation.json")))
     h, rho, L, E, mu = gold["radius"], gold["rho"], gold["length"], gold["E"], gold["mu"]
     g = gold["g"]
@@ -436,7 +436,7 @@ def _sliding_energy(push, T):
     desc["ground_mu"] = [mu]
     desc["ground_kc"] = [kc]
     p = dict(dt=gold["dt"], g=(0.0, 0.0, -g), eta=0.0, ground=True, ground_z=0.0,
-             delta=gold["delta"], nu_slip=gold["slip_nu"])
+             delta=gold["delta"], nu_slip=gold["slip_nu"], integrator=integ)
     o = OracleSystems(desc, p)
     s = o.systems[0]
     for _ in range(40):                      # settle onto the floor at rest
@@ -452,10 +452,12 @@ def _sliding_energy(push, T):
     return Ek, m, mu, g
 
 
-@pytest.mark.parametrize("push", [10.5, 3.0])
-def test_friction_kinetic_energy_closed_form(push):
+@pytest.mark.parametrize("push,integ", [(10.5, "be"), (3.0, "be"), (10.5, "midpoint")])
+def test_friction_kinetic_energy_closed_form(push, integ):
+    # (the midpoint takes the friction at the mid-step velocity; under a
+    # constant net force both schemes follow the closed form)
     T = 0.5
-    Ek, m, mu, g = _sliding_energy(push, T)
+    Ek, m, mu, g = _sliding_energy(push, T, integ)
     if push <= mu * m * g:
         assert Ek < 1e-6
     else:
