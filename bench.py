@@ -452,8 +452,8 @@ def _kernel_table(prof):
 
 
 def run_other(args):
-    """Star robots (scope config 3), the self-contacting coil (config 4's
-    contact part) and the learned warm start (config 5): one JSON line each,
+    """Star robots on the ground, the self-contacting coil, the gripper,
+    long rods and the learned warm start: one JSON line each,
     same keys as the headline line; rod-steps/s counts every rod (limb) of
     the batch."""
     import torch
@@ -470,8 +470,8 @@ def run_other(args):
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic"}
     if args.workload in ("star_robots", "warm_start"):
-        # star robots: seed 3 (scope config 3); the warm start deploys on the
-        # unseen seed 5 and trains on seeds 1000+ (config 5)
+        # star robots: seed 3; the warm start deploys on the unseen seed 5
+        # and trains on seeds 1000+
         seed = (5 if args.workload == "warm_start" else 3) + rank
         desc, params, gait = workloads.star_robots(n_robots=args.robots, seed=seed)
         dt = params["dt"]
@@ -683,7 +683,7 @@ def run_other(args):
 
 
 def run_calibration(args):
-    """Scope config 4: 64 star robots of 4 limbs on the ground, per-step
+    """Calibration: 64 star robots of 4 limbs on the ground, per-step
     per-limb natural curvatures (kappabar1, kappabar2) as parameters, L2 loss
     on all node positions against a trajectory the solver makes from seeded
     sinusoids, 500 steps with checkpoints every 50.  Times one loss+gradient

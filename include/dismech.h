@@ -220,7 +220,7 @@ dm_status dm_solve_band(int32_t nsys, const int32_t *sys_dof0, const int32_t *sy
                         int64_t ntot, const double *band, const double *rhs, double *x,
                         void *stream);
 
-/* The same solve for long systems (scope NEXT f4: N >> 500 nodes), without
+/* The same solve for long systems (rods of thousands of nodes), without
  * the sequential chain over the whole system: each system is cut into
  * interiors of part_rows - 10 rows separated by 10-row separators (interiors
  * do not couple); a warp per interior factors it (band L D L^T) and forms

@@ -1,5 +1,5 @@
-"""Edge-edge contact with friction between rods (scope NEXT f3, the
-paper's active entanglement gripper): fingers of one contact group solved
+"""Edge-edge contact with friction between rods (the paper's active
+entanglement gripper, Sec. IV): fingers of one contact group solved
 as one system, per step from identical states against the oracle (1e-10
 relative) through contacts between different fingers."""
 import numpy as np

@@ -1,4 +1,4 @@
-"""Long rods in the Newton step (scope NEXT f4): single rods with at least
+"""Long rods in the Newton step: single rods with at least
 2048 DOFs are solved by the partitioned band solve inside dm_step.  Per
 step from identical states against the oracle (1e-10 relative) on a batch
 that mixes long and short rods, and the same trajectory with every rod on
