@@ -2,8 +2,8 @@
  * dismech.h -- C ABI of the GB300 implicit Discrete Elastic Rods step.
  *
  * The library advances batches of independent rod systems (single rods and
- * rods joined at elastic joints) by the fully implicit backward-Euler step of
- * the DisMech paper (arXiv 2311.18126):
+ * rods joined at elastic joints) by the fully implicit step of the DisMech
+ * paper (arXiv 2311.18126), backward Euler or implicit midpoint:
  *
  *   Sec. III, Eq. 1    DOF vector q = [q_0, theta^0, q_1, ..., q_{N-1}] per rod
  *                      (node positions, edge twist angles), 4N-1 entries.
@@ -51,7 +51,8 @@ typedef enum dm_status {
   DM_ERR_NONFINITE = 3,     /* NaN/Inf in the residual or the update         */
   DM_ERR_DEGENERATE = 4,    /* zero-length edge, antiparallel edges at a
                                stencil (kappa b singular, Eq. 4), an edge
-                               reversed within one step, or a zero pivot     */
+                               reversed within one step, or a pivot that is
+                               zero or tiny against its row's diagonal      */
   DM_ERR_PENETRATION = 5,   /* edge-edge distance D <= 0 (Eq. 10 undefined)  */
   DM_ERR_CUDA = 6,          /* a CUDA runtime call failed                    */
   DM_ERR_OOM = 7            /* device allocation failed                      */
@@ -171,10 +172,12 @@ dm_status dm_set_natural_curvature(dm_system *sys, int32_t rod_begin,
                                    int32_t rod_end, const double *kbar,
                                    int32_t is_device);
 
-/* Advances every system by `nsteps` backward-Euler steps (Eq. 15-16).
- * Each step is all-or-nothing: if any system fails (status != DM_OK) the
- * step is not committed, the state stays at the last completed step and the
- * call returns that status.  `stats` may be NULL. */
+/* Advances every system by `nsteps` implicit steps: backward Euler (Eq.
+ * 15-16) or implicit midpoint, as dm_params.integrator selects, each solved
+ * by Newton's method to newton_tol.  Each step is all-or-nothing: if any
+ * system fails (status != DM_OK) the step is not committed, the state stays
+ * at the last completed step and the call returns that status.  `stats` may
+ * be NULL. */
 dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats);
 
 /* Copies q and qdot out in the per-rod layout of Eq. 1, rods concatenated
@@ -208,14 +211,22 @@ int64_t dm_num_edges(const dm_system *sys);
  * Eq. 1 (Sec. III-C, Eq. 16 is solved with this kernel inside dm_step) --
  * with the library's twisted banded LDL^T kernel (no pivoting).
  *   nsys, sys_dof0[nsys], sys_ndof[nsys]: host arrays; system k occupies
- *     entries [sys_dof0[k], sys_dof0[k] + sys_ndof[k]) of the vectors.
+ *     entries [sys_dof0[k], sys_dof0[k] + sys_ndof[k]) of the vectors; the
+ *     systems may come in any order but may not share entries.
  *   ntot: length of the vectors.
  *   band: device, [11][ntot], band[d * ntot + i] = J[i][i - d] (the lower
  *     band; entries reaching outside a system are ignored).  Not modified.
- *   rhs: device [ntot]; x: device [ntot] output.  x may not alias band/rhs.
+ *   rhs: device [ntot]; x: device [ntot] output, overlapping neither band
+ *     nor rhs.
+ * Breaking these rules gives DM_ERR_INVALID_ARG before any device work.
  * Work is ordered on `stream` (NULL = default stream); the call allocates
- * device scratch and returns after the solve has finished.  Returns
- * DM_ERR_DEGENERATE if a pivot is zero or not finite. */
+ * device scratch and returns after the solve has finished.
+ * J need not be positive definite: the rod Jacobian M/dt^2 - dF/dq is
+ * indefinite for compressed or buckling rods and at large steps.  Without
+ * pivoting, the factorisation of such a matrix is accurate as long as no
+ * pivot D_i is small against its row; a pivot that is zero, not finite or
+ * below 1e-13 |J_ii| returns DM_ERR_DEGENERATE (the system is then
+ * numerically singular for this solver) instead of an inaccurate x. */
 dm_status dm_solve_band(int32_t nsys, const int32_t *sys_dof0, const int32_t *sys_ndof,
                         int64_t ntot, const double *band, const double *rhs, double *x,
                         void *stream);
@@ -226,13 +237,14 @@ dm_status dm_solve_band(int32_t nsys, const int32_t *sys_dof0, const int32_t *sy
  * do not couple); a warp per interior factors it (band L D L^T) and forms
  * its Schur contributions to the neighbouring separators (forward solves
  * only, by symmetry), a warp per system solves the block-tridiagonal
- * separator system (10 x 10 blocks, Gauss-Jordan with partial pivoting), and
- * a warp per interior back-substitutes.  Arguments as dm_solve_band, plus
- * part_rows (0 = 512; otherwise 21..1024).  Interiors and separator blocks
- * are eliminated without pivoting (the rod Jacobian, and with it every
- * Schur complement, is symmetric positive definite), like the full band.  Allocates device scratch (about 170 bytes
- * per DOF); returns after the solve has finished; DM_ERR_DEGENERATE on a
- * zero or non-finite pivot. */
+ * separator system (10 x 10 blocks, Gauss-Jordan), and a warp per interior
+ * back-substitutes.  Arguments and batch rules as dm_solve_band, plus
+ * part_rows (0 = 512; otherwise 21..1024).  Nothing is pivoted: interiors
+ * and separator blocks are eliminated in order, like the full band, and a
+ * pivot that is zero, not finite or below 1e-13 times its row's (or its
+ * Schur block's) starting diagonal entry returns DM_ERR_DEGENERATE.
+ * Allocates device scratch (about 170 bytes per DOF); returns after the
+ * solve has finished. */
 dm_status dm_solve_band_partitioned(int32_t nsys, const int32_t *sys_dof0,
                                     const int32_t *sys_ndof, int64_t ntot, const double *band,
                                     const double *rhs, double *x, int32_t part_rows,
@@ -248,12 +260,17 @@ dm_status dm_solve_band_partitioned(int32_t nsys, const int32_t *sys_dof0,
  * the same arguments and returns the same result as dm_solve_band, but keeps
  * all of its scratch in one fixed device array inside the library, sized for
  * DM_NOALLOC_MAX_SYSTEMS systems and DM_NOALLOC_MAX_DOFS DOFs in total
- * (about 3.3 MiB, held on every GPU that loads the library until the process
- * exits).  Larger batches are rejected with DM_ERR_INVALID_ARG and a message
- * naming the limit; it calls no allocating CUDA routine.
- *  - The first call on a device looks up the array's device address (once
- *    per device, with that device current); make that first call before any
- *    stream capture.
+ * (about 3.3 MiB).  Larger batches are rejected with DM_ERR_INVALID_ARG and
+ * a message naming the limit.  It calls no allocating CUDA routine itself.
+ *  - The array belongs to the library's module: the CUDA driver reserves it
+ *    on a device when it loads that module there, and keeps it until the
+ *    process exits.  Under CUDA's default lazy module loading that happens
+ *    inside the first call of this entry point on the device, which can
+ *    then fail with DM_ERR_CUDA if the device has no 3.3 MiB left; make one
+ *    call at set-up, while memory is still free and before any stream
+ *    capture, to take that reservation early.
+ *  - Each call looks the array's address up in the current context, with
+ *    that device current (no address is cached across calls).
  *  - Every call reuses the same array and leaves its contents behind; each
  *    call re-initialises what it reads.  Calls whose work overlaps on the
  *    GPU (other streams, other host threads) race on the array: serialise

@@ -756,7 +756,8 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   std::vector<int32_t> iters;
   // One Newton round: every phase's launches, in stream order on rs.
   auto round = [&](cudaStream_t rs, int it) -> dm_status {
-    DM_CK(cudaMemsetAsync(d.sys_res, 0, S * sizeof(unsigned long long), rs));
+    k_reset_res<<<blocks(S, 256), 256, 0, rs>>>(0, S, d.sys_active, d.sys_res);
+    s->x.launches[K_BEGIN]++;
     DM_CK(cudaMemsetAsync(d.ctrl, 0, sizeof(int32_t), rs));
     DM_CK(cudaMemsetAsync(d.ctrl + 3, 0, sizeof(int32_t), rs));
     {

@@ -10,7 +10,8 @@
 //      Z_p^T D^{-1} Z_p and Z_p^T D^{-1} z_p (symmetry: only forward solves);
 //   2. per system: the separators' block-tridiagonal Schur system
 //      T x_S = g, T = A_SS - sum_p C_p^T B_p^{-1} C_p, eliminated block by
-//      block (10 x 10 Gauss-Jordan, no pivoting: symmetric positive definite);
+//      block (10 x 10 Gauss-Jordan, no pivoting: T is symmetric, and
+//      positive definite whenever the rod Jacobian is);
 //   3. per interior, in parallel: x_p = L^{-T} D^{-1} (z_p - Z_p x_S).
 //
 // The work per interior is a few times that of the plain band LDL^T, but
@@ -28,6 +29,11 @@ namespace dm {
 namespace {
 
 constexpr int PW = 10;  // half bandwidth = separator width
+
+// Pivots smaller than this fraction of their row's original diagonal entry
+// are treated as zero (DM_ERR_DEGENERATE): without pivoting they would
+// amplify rounding errors without bound.
+constexpr double kTinyPivot = 1e-13;
 
 __device__ __forceinline__ double pb_recip(double d) {
   const double ad = fabs(d);
@@ -98,6 +104,16 @@ __global__ void __launch_bounds__(32) k_part_factor(PartArgs a) {
         Bs[ii * 11 + (ii - kk)] -= Bs[ii * 11 + (ii - j)] * dj * Bs[kk * 11 + (kk - j)];
     }
     __syncwarp();
+  }
+  // a pivot below kTinyPivot times its row's original diagonal entry counts
+  // as zero (the Jacobian need not be positive definite); checked here, in
+  // parallel, off the sequential chain
+  bool tiny = false;
+  for (int j = lane; j < mm; j += 32)
+    if (fabs(a.band[r0 + j]) * kTinyPivot * fabs(a.Df[r0 + j]) > 1.0) tiny = true;
+  if (__any_sync(0xffffffffu, tiny)) {
+    if (lane == 0) atomicExch(a.bad + sys, 1);
+    return;
   }
   for (int t = lane; t < mm * PW; t += 32) {
     const int i = t / PW, d = t - i * PW + 1;
@@ -172,12 +188,17 @@ __global__ void __launch_bounds__(32) k_part_factor(PartArgs a) {
 
 // Gauss-Jordan on M [10][21] in shared memory, lane j owning column j:
 // M <- [I | M_left^{-1} M_right].  No pivoting: M_left is a Schur complement
-// of the symmetric positive definite rod Jacobian, itself symmetric positive
-// definite.  Returns false on a zero or non-finite pivot.
+// of the symmetric rod Jacobian (positive definite at small steps, where
+// M/dt^2 dominates).  Returns false on a zero or non-finite pivot, or one
+// below kTinyPivot times the block's starting diagonal entry.
 __device__ bool gj10(double (*M)[22], int lane, int ncol) {
+  double d0[PW];
+#pragma unroll
+  for (int k = 0; k < PW; ++k) d0[k] = M[k][k];
+  __syncwarp();
   for (int k = 0; k < PW; ++k) {
     const double pk = M[k][k];
-    if (!(fabs(pk) > 0.0) || !isfinite(pk)) return false;
+    if (!(fabs(pk) > 0.0) || !isfinite(pk) || fabs(pk) < kTinyPivot * fabs(d0[k])) return false;
     const double r = pb_recip(pk);
     double colk[PW];
 #pragma unroll
@@ -585,16 +606,20 @@ cudaError_t long_rods_round(LongRods *L, const SolveArgs &v, cudaStream_t st) {
 
 }  // namespace dm
 
+namespace dm {
+bool check_band_batch(int32_t nsys, const int32_t *dof0, const int32_t *ndof, int64_t ntot,
+                      const double *band, const double *rhs, const double *x);
+}  // namespace dm
+
 using namespace dm;
 
 extern "C" dm_status dm_solve_band_partitioned(int32_t nsys, const int32_t *sys_dof0,
                                                const int32_t *sys_ndof, int64_t ntot,
                                                const double *band, const double *rhs, double *x,
                                                int32_t part_rows, void *stream) {
-  if (nsys < 0 || (nsys > 0 && (!sys_dof0 || !sys_ndof || !band || !rhs || !x)) || ntot < 0) {
-    set_error("dm_solve_band_partitioned: bad arguments");
-    return DM_ERR_INVALID_ARG;
-  }
+  // the same batch rules as dm_solve_band (systems in range, no shared
+  // rows, x apart from band and rhs)
+  if (!check_band_batch(nsys, sys_dof0, sys_ndof, ntot, band, rhs, x)) return DM_ERR_INVALID_ARG;
   const int m = part_rows > 0 ? part_rows : 512;
   if (m < 2 * PW + 1 || m > 1024) {
     set_error("dm_solve_band_partitioned: part_rows must be in [21, 1024]");

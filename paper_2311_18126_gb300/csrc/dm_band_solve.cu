@@ -1,7 +1,9 @@
 // Public batched banded solve (dm_solve_band): the twisted LDL^T kernel of
 // the Newton step (k_solve_rod) applied to caller-provided systems.
+#include <algorithm>
 #include <climits>
 #include <string>
+#include <vector>
 
 #include "dm_internal.h"
 #include "dm_kernels.cuh"
@@ -58,6 +60,30 @@ bool check_band_batch(int32_t nsys, const int32_t *dof0, const int32_t *ndof, in
       set_error("dm_solve_band: system " + std::to_string(k) + " outside [0, ntot)");
       return false;
     }
+  // the kernel updates each system's rows in place and accumulates into x:
+  // systems may not share rows
+  std::vector<int32_t> by_start(nsys);
+  for (int k = 0; k < nsys; ++k) by_start[k] = k;
+  std::sort(by_start.begin(), by_start.end(),
+            [&](int32_t u, int32_t v) { return dof0[u] < dof0[v]; });
+  for (int k = 1; k < nsys; ++k) {
+    const int32_t u = by_start[k - 1], v = by_start[k];
+    if ((int64_t)dof0[u] + ndof[u] > dof0[v]) {
+      set_error("dm_solve_band: systems " + std::to_string(u) + " and " + std::to_string(v) +
+                " overlap");
+      return false;
+    }
+  }
+  // x is written while band and rhs are still read
+  auto overlaps = [](const void *p, size_t pn, const void *q, size_t qn) {
+    const uintptr_t a = (uintptr_t)p, b = (uintptr_t)q;
+    return a < b + qn && b < a + pn;
+  };
+  const size_t vb = (size_t)ntot * sizeof(double);
+  if (nsys > 0 && ntot > 0 && (overlaps(x, vb, rhs, vb) || overlaps(x, vb, band, 11 * vb))) {
+    set_error("dm_solve_band: x overlaps band or rhs");
+    return false;
+  }
   return true;
 }
 

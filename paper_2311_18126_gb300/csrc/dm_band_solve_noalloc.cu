@@ -1,7 +1,6 @@
 // dm_solve_band_noalloc: the batched banded solve of dm_solve_band with all
 // of its device scratch in a fixed array of this file, for callers that may
 // not allocate device memory.  The kernels are the same as dm_solve_band's.
-#include <mutex>
 #include <string>
 
 #include "dm_internal.h"
@@ -19,8 +18,11 @@ namespace {
 
 // Scratch for DM_NOALLOC_MAX_SYSTEMS systems and DM_NOALLOC_MAX_DOFS DOFs:
 // band copy, right-hand side and substitution vectors (13 doubles per DOF),
-// six ints and one residual word per system, four counters.  About 3.3 MiB;
-// every GPU that loads the library keeps it until the process exits.
+// six ints and one residual word per system, four counters.  About 3.3 MiB.
+// The driver allocates it on a device when it loads this file's module
+// there: at the first call of this entry point on that device under CUDA's
+// default lazy module loading, at context creation under eager loading.
+// It is then held until the process exits.
 constexpr size_t kScratchBytes =
     13 * (size_t)DM_NOALLOC_MAX_DOFS * sizeof(double) +
     ((6 * (size_t)DM_NOALLOC_MAX_SYSTEMS * sizeof(int32_t) + 255) & ~(size_t)255) +
@@ -28,36 +30,20 @@ constexpr size_t kScratchBytes =
 
 static __device__ __align__(256) char g_noalloc_scratch[kScratchBytes];
 
-// Device address of g_noalloc_scratch, looked up once per device.  In host
-// code the symbol name only stands for the array; the kernels must be given
-// this address.
-constexpr int kMaxDevices = 64;
-char *g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
-
-dm_status scratch_for_current_device(char **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    dm::set_error(std::string("dm_solve_band_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+// Device address of g_noalloc_scratch in the current context.  In host code
+// the symbol name only stands for the array; the kernels must be given this
+// address.  It is looked up on every call (cudaGetSymbolAddress allocates
+// nothing once the module is loaded), so it is never stale after a device
+// reset or under another context of the same device.
+dm_status scratch_for_current_context(char **out) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    dm::set_error(std::string("dm_solve_band_noalloc: cudaGetSymbolAddress: ") +
+                  cudaGetErrorString(e));
     return DM_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) {
-    dm::set_error("dm_solve_band_noalloc: device index beyond 63");
-    return DM_ERR_INVALID_ARG;
-  }
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      dm::set_error(std::string("dm_solve_band_noalloc: cudaGetSymbolAddress: ") +
-                    cudaGetErrorString(e));
-      return DM_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = (char *)p;
-  }
-  *out = g_scratch_ptr[dev];
+  *out = (char *)p;
   return DM_OK;
 }
 
@@ -82,7 +68,7 @@ extern "C" dm_status dm_solve_band_noalloc(int32_t nsys, const int32_t *sys_dof0
   }
   if (nsys == 0 || ntot == 0) return DM_OK;
   char *scr = nullptr;
-  dm_status st = scratch_for_current_device(&scr);
+  dm_status st = scratch_for_current_context(&scr);
   if (st != DM_OK) return st;
   // run_band_solve clears every part of the scratch the kernel reads
   // before it reads it (band copy, right-hand side, counters, flags).

@@ -221,6 +221,9 @@ __global__ void k_begin_step(StepArgs a);
 __global__ void k_commit(StepArgs a);
 __global__ void k_restore(StepArgs a);
 __global__ void k_round_continue(int32_t *ctrl, int max_rounds, cudaGraphConditionalHandle h);
+__global__ void k_reset_res(int lo, int hi, const int32_t *sys_active,
+                            unsigned long long *sys_res);
+
 __global__ void k_midpoint_finish(StepArgs a, double *vnew);
 // Newton round of the long rods: bookkeeping, partitioned solve, q += dq.
 cudaError_t long_rods_round(LongRods *L, const SolveArgs &v, cudaStream_t st);

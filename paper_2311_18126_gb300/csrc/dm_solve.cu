@@ -203,8 +203,17 @@ struct Chain {
 // All eight chains of a warp run the same number of iterations (`nwarp`,
 // the warp's largest ncol); a chain past its own ncol changes nothing, so
 // every synchronisation is warp-wide and the warp never diverges.
+// A pivot smaller than kTinyPivot times the original diagonal entry of its
+// row counts as zero: J = M/dt^2 - dF/dq need not be positive definite
+// (large steps, compressed or buckling rods), and without pivoting such a
+// pivot would amplify rounding errors without bound.
+constexpr double kTinyPivot = 1e-13;
+
+// Dg (lane 0 of the chain only): an 11-slot ring of the original diagonal
+// entries of the rows in the window, filled from the loads that bring the
+// rows in.
 __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, double *W, int p,
-                                          int leader) {
+                                          int leader, double *Dg) {
   const int n = c.n;
   int rows[3];
   rows[0] = p == 0 ? 10 : (p == 1 ? 9 : (p == 2 ? 8 : 7));
@@ -229,11 +238,12 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, d
       double v = 0.0;
       if (r < n) v = d == 11 ? c.rhs(r) : (d <= r ? *c.entry(r, d) : 0.0);
       W[e] = v;
+      if (d == 0) Dg[r] = v;  // lane 0 holds every d == 0 entry
     }
   __syncwarp();
   double rj = ncol > 0 ? rcp64(W[0]) : 1.0;
   bool bad = false;
-  int b = 0;
+  int b = 0, jr = 0;  // jr = j mod 11, the ring slot of row j
   for (int j = 0; j < nwarp; ++j) {
     const bool act = j < ncol;
     // prefetch of row j + 11 (diagonals p, p+4, p+8; the right-hand side)
@@ -248,7 +258,10 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, d
     double *Wb = W + 12 * b;
     const double zj = Wb[11];
     if (act && p == 0) {
-      if (!isfinite(rj) || rj == 0.0) bad = true;
+      // |D_j| < kTinyPivot |J_jj| (1/rj infinite or not finite included)
+      if (!isfinite(rj) || rj == 0.0 || fabs(Dg[jr]) * kTinyPivot * fabs(rj) > 1.0) bad = true;
+      Dg[jr] = pre0;  // row j + 11 takes the slot (0 past the end)
+      jr = jr == 10 ? 0 : jr + 1;
       *c.zstore(j) = zj * rj;  // z_j = y_j / D_j for the backward pass
     }
     double l[4];
@@ -402,7 +415,7 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
   const int rid = (threadIdx.x >> 5) * SOLVE_RODS_PER_WARP + unit;
   double *Wt = smem + (size_t)rid * (2 * SOLVE_CHAIN_STRIDE + 32);
   double *Wb = Wt + SOLVE_CHAIN_STRIDE;
-  double *XS = Wb + SOLVE_CHAIN_STRIDE;  // separator solution (10) + scratch
+  double *XS = Wb + SOLVE_CHAIN_STRIDE;  // separator solution (10), diagonal rings (2 x 11)
   double *W = half ? Wb : Wt;
   const unsigned full = 0xffffffffu;
   const int leader = unit * 8 + half * 4;
@@ -451,7 +464,8 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
     const int m = twist ? (n - 10) / 2 : n;
     const int ncol = !go ? 0 : (half ? (twist ? n - m - 10 : 0) : m);
     const int nwarp = __reduce_max_sync(full, ncol);
-    bool bad = eliminate(c, ncol, nwarp, W, p, leader);
+    // the rod's scratch past the separator solution: one diagonal ring per chain
+    bool bad = eliminate(c, ncol, nwarp, W, p, leader, XS + 10 + 11 * half);
     // a rod is bad if either of its chains met a zero pivot
     const unsigned bm = __ballot_sync(full, bad);
     bad = ((bm >> (unit * 8)) & 0xFFu) != 0;

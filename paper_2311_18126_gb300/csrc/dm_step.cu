@@ -85,6 +85,15 @@ __global__ void k_round_continue(int32_t *ctrl, int max_rounds, cudaGraphConditi
   cudaGraphSetConditional(h, (ctrl[0] > 0 && r < max_rounds) ? 1u : 0u);
 }
 
+// Clears the residual slots of the systems [lo, hi) still iterating before a
+// round's row kernels max-reduce into them; a system that has stopped keeps
+// the residual of its last evaluated iterate (the value dm_step reports).
+__global__ void k_reset_res(int lo, int hi, const int32_t *sys_active,
+                            unsigned long long *sys_res) {
+  const int s = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < hi && sys_active[s]) sys_res[s] = 0ull;
+}
+
 // Committed tangents recomputed from q (after a state is set).
 __global__ void k_tangents(int ne, const int32_t *edge_a, const int32_t *edge_b,
                            const double *q, double *tn, int32_t *bad) {
