@@ -35,16 +35,19 @@ WORKLOAD = "uneven_rods: 4096 clamped rods, N~U{20..200}, dt=1e-3 s, backward Eu
 
 # FP64 flops executed per work unit of each kernel (DADD + DMUL + 2 DFMA,
 # predicated-on lanes), counted by ncu on the uneven-rods workload
-# (profiles/kernel_fp64_counts.md); the denominator is the measured FP64 FMA
-# throughput of the device.
+# (profiles/kernel_fp64_counts.json); the denominator is the measured FP64
+# FMA throughput of the device.
 FP64_FLOPS_PER_UNIT = {
-    "bend_twist_stencil": None,
+    "bend_twist_gradient": None,
+    "bend_twist_hessian": None,
     "edge_frames_stretch": None,
-    "residual_jacobian_rows": None,
+    "residual_rows": None,
+    "jacobian_band_rows": None,
     "band_ldlt_solve": None,
 }
-UNIT_NAME = {"bend_twist_stencil": "stencil", "edge_frames_stretch": "edge",
-             "residual_jacobian_rows": "DOF row", "band_ldlt_solve": "DOF",
+UNIT_NAME = {"bend_twist_gradient": "stencil", "bend_twist_hessian": "stencil",
+             "edge_frames_stretch": "edge", "residual_rows": "DOF row",
+             "jacobian_band_rows": "DOF row", "band_ldlt_solve": "DOF",
              "step_begin": "DOF", "step_commit": "DOF"}
 
 
@@ -104,9 +107,26 @@ def dist():
     return ws, rank, local
 
 
-def rank_seed(rank):
-    """Seed of a rank's own batch (weak scaling: independent rods per rank)."""
-    return 2 + rank
+def shard_of_batch(make, ws, rank):
+    """This rank's shard of one seeded batch: ``make(ws)`` builds the batch
+    for ws ranks (ws times the one-GPU size: weak scaling) as (desc, params,
+    per-rod controls); it is split into contiguous ranges of whole systems
+    balanced by DOF count, one per rank (no exchange inside a step).
+    Returns the rank's (desc, params, controls, rods of the whole batch).
+    ``controls`` is an array of rows per interior node, or a gait dict of
+    per-rod arrays, or None."""
+    from paper_2311_18126_gb300 import shard
+    desc, params, ctl = make(ws)
+    parts = shard.partition(desc, ws)
+    b, e = parts[rank]
+    sub = shard.sub_descriptor(desc, b, e)
+    if isinstance(ctl, dict):  # a gait: per-rod arrays, robot ids renumbered
+        ctl = {k: (np.asarray(v)[b:e] if np.ndim(v) == 1 and len(v) == len(desc["nodes_per_rod"])
+                   else v) for k, v in ctl.items()}
+    elif ctl is not None:
+        k0, k1 = shard.kbar_ranges(desc, parts)[rank]
+        ctl = ctl[k0:k1]
+    return sub, params, ctl, len(desc["nodes_per_rod"])
 
 
 def max_over_ranks(x, ws, device=None):
@@ -121,10 +141,10 @@ def max_over_ranks(x, ws, device=None):
     return float(t.item())
 
 
-def job_rate(ws, rods_per_rank, steps, seconds):
-    """Whole-job rod-steps per second: every rank's rods over the slowest
-    rank's time."""
-    return ws * rods_per_rank * steps / seconds
+def job_rate(total_rods, steps, seconds):
+    """Whole-job rod-steps per second: the rods of all ranks over the
+    slowest rank's time."""
+    return total_rods * steps / seconds
 
 
 class Clocks:
@@ -186,21 +206,43 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def oracle_rate(desc, params, kbar, rods, steps):
-    """Times the CPU oracle on `rods` of the workload for `steps` steps."""
+def _oracle_worker(job):
+    """One pool process: the oracle on its rods of the uneven-rods batch
+    (regenerated from its seed), one torch thread; returns the seconds of
+    the timed steps, the rods and their nodes."""
+    n_rods, params, rods, warmup, steps = job
     import torch
+    torch.set_num_threads(1)
     import workloads
     from oracle import OracleSystems
+    desc, _, kbar = workloads.uneven_rods(n_rods=n_rods, seed=2)
     sub, kb = workloads.subset(desc, rods, kbar)
     o = OracleSystems(sub, params)
     o.set_natural_curvature(0, len(rods), kb)
+    for _ in range(warmup):
+        o.step(1)
     t0 = time.perf_counter()
     for _ in range(steps):
         out = o.step(1)
         assert all(x[0] == 0 for x in out), out
-    dt = time.perf_counter() - t0
-    nodes = int(np.sum(np.asarray(sub["nodes_per_rod"])))
-    return len(rods) * steps / dt, dt, torch.get_num_threads(), nodes
+    return time.perf_counter() - t0, len(rods), int(np.sum(np.asarray(sub["nodes_per_rod"])))
+
+
+def oracle_pool_rate(n_rods, params, rods, warmup, steps, cores=None):
+    """The CPU oracle on the host cores: one process per core (spawned, one
+    torch thread each), the sampled rods dealt round-robin, every process
+    stepping its rods `warmup` untimed and `steps` timed steps.  Returns
+    (rod-steps/s = all timed rod-steps / the slowest process's time, that
+    time, processes, nodes)."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    cores = max(1, min(cores, len(rods)))
+    jobs = [(n_rods, params, [int(r) for r in rods[k::cores]], warmup, steps)
+            for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    tmax = max(r[0] for r in res)
+    return sum(r[1] for r in res) * steps / tmax, tmax, cores, sum(r[2] for r in res)
 
 
 def sample_rods(n_total, k, seed=12345):
@@ -217,19 +259,9 @@ def run_reference(args):
     params = dict(params, integrator=args.integrator)
     if args.integrator == "midpoint":
         params["line_search"] = True
-    rods = sample_rods(args.rods, 4)
-    import torch
-    from oracle import OracleSystems
-    sub, kb = workloads.subset(desc, rods, kbar)
-    o = OracleSystems(sub, params)
-    o.set_natural_curvature(0, len(rods), kb)
-    for _ in range(args.warmup):
-        o.step(1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        o.step(1)
-    dt = time.perf_counter() - t0
-    v = len(rods) * args.steps / dt
+    cores = os.cpu_count() or 1
+    rods = sample_rods(args.rods, 2 * cores)
+    v, dt, used, nodes = oracle_pool_rate(args.rods, params, rods, args.warmup, args.steps, cores)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
@@ -238,10 +270,11 @@ def run_reference(args):
                        WORKLOAD.replace("backward Euler", "implicit midpoint"),
                        "rods_per_step": len(rods),
                        "sample": "rods %s of the 4096 (seeded), consecutive steps" % rods.tolist()},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(),
-                             "kind": "oracle",
-                             "sample": "%d seeded rods of the 4096-rod batch, %d steps" %
-                                       (len(rods), args.steps)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
+                             "sample": "%d seeded rods (%d nodes) of the 4096-rod batch dealt "
+                                       "over %d single-threaded oracle processes, %d timed "
+                                       "steps after %d untimed" %
+                                       (len(rods), nodes, used, args.steps, args.warmup)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -257,13 +290,14 @@ def run_ours(args):
     from paper_2311_18126_gb300 import System, ensure_built, fp64_peak_gflops
     ensure_built()
     _load_counts()
-    desc, params, kbar = workloads.uneven_rods(n_rods=args.rods, seed=rank_seed(rank))
+    desc, params, kbar, R_all = shard_of_batch(
+        lambda n: workloads.uneven_rods(n_rods=args.rods * n, seed=2), ws, rank)
     params = dict(params, integrator=args.integrator)
     if args.integrator == "midpoint":
         # without numerical damping plain Newton diverges on stiff rods of
         # this batch (the oracle likewise, e.g. rod 379 at its 5th step)
         params["line_search"] = True
-    R = args.rods
+    R = len(desc["nodes_per_rod"])
     sysm = System(desc, params)
     sysm.set_natural_curvature(0, R, kbar)
     peak_fp64 = fp64_peak_gflops()
@@ -297,7 +331,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     n_launch = sum(v[0] for v in sysm.get_profile().values())
     tmax = max_over_ranks(ms, ws, "cuda")
-    value = job_rate(ws, R, args.steps, tmax * 1e-3)
+    value = job_rate(R_all, args.steps, tmax * 1e-3)
     # the same steps again from the same state with the host driving the
     # rounds, then a profiled pass (per-kernel CUDA events, host-driven) for
     # the kernel table
@@ -320,15 +354,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_steps = max(3, args.steps // 2)
     t0 = time.perf_counter()
+    nq, nv = hq.numpy(), hv.numpy()
     for _ in range(e2e_steps):
-        sysm.set_state(hq.numpy(), hv.numpy())
+        sysm.set_state(nq, nv)              # host -> device from pinned buffers
         sysm.step(1, stats=False)
-        qq, vv = sysm.get_state()
-        hq.numpy()[:] = qq
-        hv.numpy()[:] = vv
+        sysm.get_state(nq, nv)              # device -> host into the same buffers
     torch.cuda.synchronize()
     te = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
-    e2e = {"value": job_rate(ws, R, e2e_steps, te), "unit": UNIT,
+    e2e = {"value": job_rate(R_all, e2e_steps, te), "unit": UNIT,
            "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": 2 * n * 8}
 
     # dominant kernel and its FP64 roofline
@@ -380,7 +413,7 @@ def run_ours(args):
                        "nodes_per_gpu": int(np.sum(desc["nodes_per_rod"])),
                        "dofs_per_gpu": int(n), "dt": params["dt"], "newton_tol": params["tol"],
                        "line_search": bool(params.get("line_search", False)),
-                       "parallelism": "independent rod batches per GPU (dp%d)" % ws,
+                       "parallelism": "dp%d: each GPU steps a DOF-balanced shard of contiguous systems of one batch %d x the one-GPU size" % (ws, ws),
                        "l2": "no flush: per-iteration working set (~0.7 GB) exceeds L2"},
             "newton": {"iters_mean": float(it.mean()), "iters_max": int(it.max()),
                        "node_steps_per_s": value * float(np.mean(desc["nodes_per_rod"]))},
@@ -395,11 +428,14 @@ def run_ours(args):
                              "same kernels and launch shapes)",
             "roofline": roof, "kernels": kernels}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rods = sample_rods(R, 16)
-        v, dt, cores, nodes = oracle_rate(desc, params, kbar, rods, 5)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "16 seeded rods (%d nodes) of the batch, 5 steps "
-                                          "from the initial state, %.1f s" % (nodes, dt)}
+        cores = os.cpu_count() or 1
+        rods = sample_rods(R, 2 * cores)
+        v, dt, used, nodes = oracle_pool_rate(R, params, rods, 0, 5, cores)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
+                                "sample": "%d seeded rods (%d nodes) of the batch dealt over "
+                                          "%d single-threaded oracle processes, 5 steps from "
+                                          "the initial state, %.1f s" % (len(rods), nodes, used,
+                                                                         dt)}
     if rank == 0:
         print(json.dumps(line))
     sysm.close()
@@ -472,8 +508,9 @@ def run_other(args):
     if args.workload in ("star_robots", "warm_start"):
         # star robots: seed 3; the warm start deploys on the unseen seed 5
         # and trains on seeds 1000+
-        seed = (5 if args.workload == "warm_start" else 3) + rank
-        desc, params, gait = workloads.star_robots(n_robots=args.robots, seed=seed)
+        seed = 5 if args.workload == "warm_start" else 3
+        desc, params, gait, R_all = shard_of_batch(
+            lambda n: workloads.star_robots(n_robots=args.robots * n, seed=seed), ws, rank)
         dt = params["dt"]
         controls = lambda k: workloads.gait_kbar(gait, k * dt)
         line["config"] = {"workload": "star_robots: %d robots of 3-8 limbs x 30 nodes on the "
@@ -482,13 +519,15 @@ def run_other(args):
                           "l2": "no flush: per-iteration working set exceeds L2 at 1024 robots"}
     elif args.workload == "warm_start_rods":
         # the headline batch (seed 2); training batches of seeds 1000+
-        desc, params, kbar = workloads.uneven_rods(n_rods=args.rods, seed=rank_seed(rank))
+        desc, params, kbar, R_all = shard_of_batch(
+            lambda n: workloads.uneven_rods(n_rods=args.rods * n, seed=2), ws, rank)
         controls = lambda k: kbar
-        line["config"] = {"workload": WORKLOAD, "rods_per_gpu": args.rods,
+        line["config"] = {"workload": WORKLOAD, "rods_per_gpu": len(desc["nodes_per_rod"]),
                           "l2": "no flush: per-iteration working set (~0.7 GB) exceeds L2"}
     elif args.workload == "long_rods":
-        desc, params, kbar = workloads.uneven_rods(n_rods=64, seed=rank_seed(rank),
-                                                   n_min=4000, n_max=6000)
+        desc, params, kbar, R_all = shard_of_batch(
+            lambda n: workloads.uneven_rods(n_rods=64 * n, seed=2, n_min=4000, n_max=6000),
+            ws, rank)
         controls = lambda k: kbar
         line["config"] = {"workload": "long_rods: 64 clamped rods of 4000-6000 nodes "
                           "(16k-24k DOFs each), uneven_rods recipe otherwise, dt=1e-3 s; "
@@ -496,6 +535,7 @@ def run_other(args):
                           "rods_per_gpu": 64, "l2": "no flush: working set exceeds L2"}
     elif args.workload == "gripper":
         desc, params, kfn = workloads.gripper()
+        R_all = ws * len(desc["nodes_per_rod"])  # one gripper per rank
         dt = params["dt"]
         controls = lambda k: kfn(k * dt)
         line["config"] = {"workload": "gripper: 5 fingers of 60 nodes (L 0.3 m, h 2.5 mm, "
@@ -505,6 +545,7 @@ def run_other(args):
                           "rods_per_gpu": 5, "l2": "working set in L2 (one system)"}
     else:
         desc, params, _ = workloads.coil(N=500)
+        R_all = ws  # one coil per rank
         controls = None
         line["config"] = {"workload": "coil: one 500-node helix collapsing under gravity into "
                           "edge-edge self-contact, dt=2.5e-4 s, line search", "rods_per_gpu": 1,
@@ -552,7 +593,7 @@ def run_other(args):
             _restore(sysm, snap)
             sysm.set_profiling(True)
             _timed_steps(sysm, args.steps, controls, warm, local, clocks=False)
-            arms[label] = {"value": job_rate(ws, R, args.steps, ms * 1e-3),
+            arms[label] = {"value": job_rate(R_all, args.steps, ms * 1e-3),
                            "ms_per_step": ms / args.steps,
                            "iters_per_rod_step": float(its.mean()),
                            "iters_histogram": np.bincount(its.ravel()).tolist(),
@@ -574,12 +615,10 @@ def run_other(args):
                     sysm.set_natural_curvature(0, R, controls(warm + i))
                     sysm.set_state(hq.numpy(), hv.numpy())
                     sysm.step(1, stats=False)
-                    qq, vv = sysm.get_state()
-                    hq.numpy()[:] = qq
-                    hv.numpy()[:] = vv
+                    sysm.get_state(hq.numpy(), hv.numpy())
                 torch.cuda.synchronize()
                 te = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
-                arms[label]["e2e"] = {"value": job_rate(ws, R, e2e_steps, te), "unit": UNIT,
+                arms[label]["e2e"] = {"value": job_rate(R_all, e2e_steps, te), "unit": UNIT,
                                       "h2d_bytes_per_step": 2 * n * 8,
                                       "d2h_bytes_per_step": 2 * n * 8,
                                       "note": "setting the state resets the velocity history "
@@ -596,7 +635,7 @@ def run_other(args):
                      "roofline_note": "solver kernels as in the headline line; the network's "
                                       "tensor-core roofline is the mlp workload's line"})
         line["config"]["training"] = tnote + ", 4000 Adam steps of 16384 segments"
-        line["config"]["seed"] = rank_seed(rank) if args.workload == "warm_start_rods" \
+        line["config"]["seed"] = 2 if args.workload == "warm_start_rods" \
             else line["config"].get("seed")
     else:
         sysm = System(desc, params)
@@ -612,7 +651,7 @@ def run_other(args):
         ms, its, clocks = _timed_steps(sysm, args.steps, controls, warm, local)
         n_launch = sum(v[0] for v in sysm.get_profile().values())
         ms = max_over_ranks(ms, ws, "cuda")
-        value = job_rate(ws, R, args.steps, ms * 1e-3)
+        value = job_rate(R_all, args.steps, ms * 1e-3)
         # the same steps from the same state: host-driven rounds, then profiled
         _restore(sysm, snap)
         host_ms, _, _ = _timed_steps(sysm, args.steps, controls, warm, local, graphs=False,
@@ -647,9 +686,7 @@ def run_other(args):
                 sysm.set_natural_curvature(0, R, controls(k1 + i))
             sysm.set_state(hq.numpy(), hv.numpy())
             sysm.step(1, stats=False)
-            qq, vv = sysm.get_state()
-            hq.numpy()[:] = qq
-            hv.numpy()[:] = vv
+            sysm.get_state(hq.numpy(), hv.numpy())
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
         dom = max(prof, key=lambda k: prof[k][2])
@@ -657,7 +694,7 @@ def run_other(args):
                      "newton": {"iters_mean": float(its.mean()), "iters_max": int(its.max()),
                                 "slowest_per_step_mean": float(its.max(1).mean())},
                      "clocks": clocks,
-                     "e2e": {"value": job_rate(ws, R, e2e_steps, te), "unit": UNIT,
+                     "e2e": {"value": job_rate(R_all, e2e_steps, te), "unit": UNIT,
                              "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": 2 * n * 8},
                      "gpu_launches": int(n_launch),
                      "rounds": {"mode": "one CUDA graph per step (device-side while loop "

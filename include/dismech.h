@@ -425,7 +425,7 @@ typedef struct dm_tuning {
   int32_t stencil_threads;     /* threads per block, bend-twist stencils          */
   int32_t stencil_per_thread;  /* stencils per thread (stencils per warp / 32)    */
   int32_t rows_threads;        /* threads per block, residual/Jacobian rows       */
-  int32_t solve_warps;         /* rod solver: warps per block (4 rods per warp)   */
+  int32_t solve_warps;         /* rod solver: warps per block (2 rods per warp)   */
   int32_t solve_blocks_per_sm; /* rod solver: resident blocks per SM              */
   int32_t limb_factor_warps;   /* condensation: limbs (warps) per factor block    */
   int32_t limb_back_warps;     /* condensation: limbs (warps) per back-subst block */
@@ -438,7 +438,7 @@ typedef struct dm_tuning {
  * kernel, the fastest shape (the default unless another is faster by more
  * than 2 %): threads per block and stencils per thread of the stencil
  * kernel, threads per block of the edge and row kernels, warps per block
- * (systems per block = 4 x warps) and blocks per SM of the persistent rod
+ * (systems per block = 2 x warps) and blocks per SM of the persistent rod
  * solver, limbs per block of the condensation kernels.  Every shape computes
  * the same arithmetic per system.  The committed state, the profiling
  * switch and the counters are restored before returning; `out` (optional,

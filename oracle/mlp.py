@@ -74,3 +74,28 @@ def loss_and_grad(params, X, Y, n_out, rounding=False):
             g = np.where(acts[l] > 0, dA, 0.0)
     flat = np.concatenate([np.concatenate([gW.reshape(-1), gb]) for gW, gb in grads])
     return loss, flat
+
+
+def grad_abs_scale(params, X, Y, n_out):
+    """Per gradient entry, the sum of the absolute values of the terms that
+    make it up: the backward pass of ``loss_and_grad`` (with the bfloat16
+    rounding points) run on |W|, |activations| and |output gradient|, ReLU
+    masks of the rounded forward pass.  An element-wise error scale for a
+    kernel that rounds at the same points but sums in another order and
+    precision: moving one operand of a product to a neighbouring bfloat16
+    value changes the product by at most 2^-7 of its magnitude."""
+    layers = unpack(params)
+    acts = forward(params, X, rounding=True)
+    M = X.shape[0]
+    out = acts[-1]
+    d = np.zeros_like(out)
+    d[:, :n_out] = np.abs(2.0 * (out[:, :n_out] - Y[:, :n_out]) / (M * n_out))
+    grads = [None] * len(layers)
+    g = d
+    for l in range(len(layers) - 1, -1, -1):
+        W, _ = layers[l]
+        gW = g.T @ np.abs(acts[l])
+        grads[l] = (gW, g.sum(0))
+        if l > 0:
+            g = np.where(acts[l] > 0, g @ np.abs(bf16(W)), 0.0)
+    return np.concatenate([np.concatenate([gW.reshape(-1), gb]) for gW, gb in grads])

@@ -91,13 +91,13 @@ __global__ void k_scatter_kbar(int n, const int32_t *slot2st, int slot0, int ns,
 enum {
   K_EDGE = 0, K_STENCIL = 1, K_ROWS = 2, K_SOLVE = 3, K_BEGIN = 4, K_COMMIT = 5,
   K_NODES = 6, K_ROWS_GEN = 7, K_ASM_GEN = 8, K_SOLVE_GEN = 9, K_WARM = 10,
-  K_CONTACT = 11, K_SOLVE_CONTACT = 12
+  K_CONTACT = 11, K_SOLVE_CONTACT = 12, K_HESS = 13, K_BAND = 14
 };
 const char *kKernelNames[DM_NUM_KERNELS] = {
-    "edge_frames_stretch", "bend_twist_stencil", "residual_jacobian_rows", "band_ldlt_solve",
+    "edge_frames_stretch", "bend_twist_gradient", "residual_rows", "band_ldlt_solve",
     "step_begin",          "step_commit",        "ground_contact_friction", "residual_rows_general",
     "assemble_general",    "limb_schur_solve",   "learned_warm_start",
-    "edge_contact_pairs",  "contact_band_lu"};
+    "edge_contact_pairs",  "contact_band_lu",    "bend_twist_hessian", "jacobian_band_rows"};
 
 struct Extra {
   bool prof = false;
@@ -175,13 +175,13 @@ struct dm_system_ext : dm_system {
   Extra x;
 };
 
-// Persistent rod solver shape: `warps` warps of four rods each per block,
+// Persistent rod solver shape: `warps` warps of two rods each per block,
 // `bps` blocks per SM, no more blocks than the batch needs.
 static void set_solve_shape(dm_system_ext *s, int warps, int bps) {
   s->x.tune.solve_warps = warps;
   s->x.tune.solve_bps = bps;
-  s->x.solve_smem = (size_t)warps * 4 * kSolveRodDoubles * sizeof(double);
-  const int rods_per_block = 4 * warps;
+  s->x.solve_smem = (size_t)warps * kSolveRodsPerWarp * kSolveRodDoubles * sizeof(double);
+  const int rods_per_block = kSolveRodsPerWarp * warps;
   const int want = (s->x.n_rod_sys + rods_per_block - 1) / rods_per_block;
   s->x.solve_blocks = std::max(1, std::min(want, bps * s->x.sms));
 }
@@ -514,16 +514,17 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     DM_TRY(upload(s, &s->x.d_rod_st0, rst0));
     DM_TRY(upload(s, &s->x.d_rod_edge0, re0));
   }
-  s->x.scratch_n = std::max<size_t>({(size_t)T.layout2dof.size(), (size_t)(2 * nslots), (size_t)1});
+  // staging of q and qdot together (state copies), or of natural curvatures
+  s->x.scratch_n = std::max<size_t>({2 * (size_t)T.layout2dof.size(), (size_t)(2 * nslots), (size_t)1});
   DM_TRY(dalloc(s, &s->x.d_scratch, s->x.scratch_n));
   DM_TRY(dalloc(s, &s->x.d_units, DM_NUM_KERNELS));
   DM_CK(cudaMemset(s->x.d_units, 0, DM_NUM_KERNELS * sizeof(unsigned long long)));
   DM_TRY(dalloc(s, &s->x.d_bad, 1));
   for (int k = 0; k < 2 * DM_NUM_KERNELS; ++k) DM_CK(cudaEventCreate(&s->x.ev[k]));
   DM_CK(cudaMallocHost(&s->h_ctrl, 8 * sizeof(int32_t)));
-  // persistent banded solver: 32 rods per 128-thread block, enough blocks
+  // persistent banded solver: 8 rods per 128-thread block, enough blocks
   // to cover the batch but no more than fit at once
-  s->x.solve_smem = 16 * kSolveRodDoubles * sizeof(double);  // 16 rods per block
+  s->x.solve_smem = 4 * kSolveRodsPerWarp * kSolveRodDoubles * sizeof(double);  // 4 warps
   DM_CK(cudaFuncSetAttribute(k_solve_rod, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)s->x.solve_smem));
   {
@@ -533,7 +534,7 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     DM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_rod, 128,
                                                         s->x.solve_smem));
     // persistent: one block of four warps per SM, so that each SM partition
-    // runs one warp; the warps take rod quads from the size-sorted queue
+    // runs one warp; the warps take rod pairs from the size-sorted queue
     // (largest first), which balances the FP64 work across partitions
     s->x.sms = sms;
     set_solve_shape(s, 4, 1);
@@ -688,7 +689,15 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     ca.fc = c.fc; ca.dense = c.dense;
     ca.n_contact = c.n_contact; ca.cgo = c.cgo; ca.cbad = c.cbad;
   }
+  // the Jacobian passes test convergence as the solvers do
+  const int32_t *ls_act = s->prm.line_search ? s->x.ls_action : nullptr;
+  ka.sys_res = d.sys_res;
+  ka.tol = s->p.tol;
+  ka.ls_action = ls_act;
   RowArgs ra{};
+  ra.sys_status = d.sys_status;
+  ra.tol = s->p.tol;
+  ra.ls_action = ls_act;
   ra.fc = contact_on ? s->x.cc.fc : nullptr;
   ra.nd = nd; ra.ns = ns; ra.ne = ne; ra.dt = s->p.dt;
   for (int c = 0; c < 3; ++c) ra.g[c] = s->p.g[c];
@@ -769,10 +778,14 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       Timed t(s, K_NODES, rs);
       k_nodes<<<blocks(nn, 256), 256, 0, rs>>>(na);
     }
+    // residual pass: reference twist and gradients, then the residual rows;
+    // the Jacobian pass (stencil Hessians, band rows) below runs only for
+    // systems whose residual is still above the tolerance
+    const int st_tb = s->x.tune.stencil_threads;
+    const int st_grid = blocks(ns, (int64_t)st_tb * s->x.tune.stencil_per_thread);
     if (ns > 0) {
       Timed t(s, K_STENCIL, rs);
-      const int tb = s->x.tune.stencil_threads;
-      k_stencil<<<blocks(ns, (int64_t)tb * s->x.tune.stencil_per_thread), tb, 0, rs>>>(ka);
+      k_stencil_grad<<<st_grid, st_tb, 0, rs>>>(ka);
     }
     if (contact_on) {
       Timed t(s, K_CONTACT, rs);
@@ -788,10 +801,11 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       k_cc_pairs<<<blocks(ne, 128), 128, 0, rs>>>(ca);
       k_cc_terms<<<blocks(c.pair_cap, 64), 64, 0, rs>>>(ca);
     }
-    if (rod_on || contact_on || long_on) {
+    const bool rows_on = rod_on || contact_on || long_on;
+    if (rows_on) {
       Timed t(s, K_ROWS, rs);
       const int tb = s->x.tune.rows_threads;
-      k_rows_rod<<<blocks(nd, tb), tb, 0, rs>>>(ra);
+      k_rows_rod_res<<<blocks(nd, tb), tb, 0, rs>>>(ra);
     }
     if (gen_on) {
       Timed t(s, K_ROWS_GEN, rs);
@@ -802,6 +816,19 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       k_ls_decide<<<blocks(S, 128), 128, 0, rs>>>(la);
       k_ls_apply<<<blocks(nd, 256), 256, 0, rs>>>(la);
       if (ws_trial && it == 0) DM_CK(ws_inject(s, rs, s->x.ls_action, s->x.ls_trial));
+    }
+    if (ns > 0) {
+      Timed t(s, K_HESS, rs);
+      StencilArgs kh = ka;
+      kh.units = s->x.prof ? s->x.d_units + K_HESS : nullptr;
+      k_stencil_hess<<<st_grid, st_tb, 0, rs>>>(kh);
+    }
+    if (rows_on) {
+      Timed t(s, K_BAND, rs);
+      const int tb = s->x.tune.rows_threads;
+      RowArgs rb = ra;
+      rb.units = s->x.prof ? s->x.d_units + K_BAND : nullptr;
+      k_rows_rod_band<<<blocks(nd, tb), tb, 0, rs>>>(rb);
     }
     if (rod_on) {
       {
@@ -1033,18 +1060,18 @@ dm_status dm_get_state(dm_system *sys, double *q, double *qdot, size_t cap, int3
     return DM_ERR_INVALID_ARG;
   }
   cudaStream_t st = s->stream;
+  // both arrays staged side by side, copied, then one synchronisation
   for (int k = 0; k < 2; ++k) {
     double *dst = k == 0 ? q : qdot;
     if (!dst) continue;
-    double *stage = is_device ? dst : s->x.d_scratch;
+    double *stage = is_device ? dst : s->x.d_scratch + k * n;
     k_gather_layout<<<blocks(n, 256), 256, 0, st>>>((int)n, s->d.layout2dof,
                                                     k == 0 ? s->d.qn : s->d.vn, stage);
     DM_CK(cudaGetLastError());
-    if (!is_device) {
+    if (!is_device)
       DM_CK(cudaMemcpyAsync(dst, stage, n * sizeof(double), cudaMemcpyDeviceToHost, st));
-      DM_CK(cudaStreamSynchronize(st));
-    }
   }
+  if (!is_device) DM_CK(cudaStreamSynchronize(st));
   return DM_OK;
 }
 
@@ -1062,17 +1089,18 @@ dm_status dm_set_state(dm_system *sys, const double *q, const double *qdot, size
   }
   cudaStream_t st = s->stream;
   // scatter in reverse rod order so that the lowest rod's joint copy wins
+  // both arrays staged side by side: one synchronisation for the whole call
   for (int k = 0; k < 2; ++k) {
     const double *src = k == 0 ? q : qdot;
     const double *stage = src;
     if (!is_device) {
-      DM_CK(cudaMemcpyAsync(s->x.d_scratch, src, n * sizeof(double), cudaMemcpyHostToDevice, st));
-      stage = s->x.d_scratch;
+      DM_CK(cudaMemcpyAsync(s->x.d_scratch + k * n, src, n * sizeof(double),
+                            cudaMemcpyHostToDevice, st));
+      stage = s->x.d_scratch + k * n;
     }
     k_scatter_layout<<<blocks(n, 256), 256, 0, st>>>((int)n, s->d.layout2dof, stage,
                                                      k == 0 ? s->d.qn : s->d.vn);
     DM_CK(cudaGetLastError());
-    if (!is_device) DM_CK(cudaStreamSynchronize(st));
   }
   DM_CK(cudaMemcpyAsync(s->d.q, s->d.qn, s->T.n_dofs * sizeof(double), cudaMemcpyDeviceToDevice, st));
   DM_CK(ws_keep_velocity(s, st));  // no velocity history for a state set from outside
@@ -1179,7 +1207,13 @@ dm_status dm_autotune(dm_system *sys, int32_t steps, dm_tuning *out) {
     }
     if (dm_step(sys, steps, nullptr) != DM_OK) return INFINITY;
     if (cudaStreamSynchronize(st) != cudaSuccess) return INFINITY;
-    return s->x.launches[id] ? s->x.ms[id] / (double)s->x.launches[id] : INFINITY;
+    if (!s->x.launches[id]) return INFINITY;
+    // the residual and Jacobian passes of the stencils (of the rows) share
+    // one launch shape: both are timed
+    double ms = s->x.ms[id];
+    if (id == K_STENCIL) ms += s->x.ms[K_HESS];
+    if (id == K_ROWS) ms += s->x.ms[K_BAND];
+    return ms / (double)s->x.launches[id];
   };
   // coordinate search: the phases run one after another, so each kernel's
   // shape is chosen on its own time, keeping the default unless another
@@ -1225,7 +1259,8 @@ dm_status dm_autotune(dm_system *sys, int32_t steps, dm_tuning *out) {
       us[3] = 1e3 * pick(K_SOLVE, 6, [&](int c) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, k_solve_rod, 32 * w[c], (size_t)w[c] * 4 * kSolveRodDoubles * 8) !=
+                &per_sm, k_solve_rod, 32 * w[c],
+                (size_t)w[c] * kSolveRodsPerWarp * kSolveRodDoubles * 8) !=
                 cudaSuccess ||
             per_sm < b[c])
           return false;

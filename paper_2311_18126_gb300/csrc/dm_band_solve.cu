@@ -139,13 +139,14 @@ dm_status run_band_solve(int32_t nsys, const int32_t *dof0, const int32_t *ndof,
   va.sys_res = res;
   va.ctrl = ctrl;
   va.units = nullptr;
-  const size_t smem = 16 * kSolveRodDoubles * sizeof(double);  // 16 rods per block
+  const int rods_per_block = 4 * kSolveRodsPerWarp;  // four warps
+  const size_t smem = rods_per_block * kSolveRodDoubles * sizeof(double);
   int dev = 0, sms = 1, per_sm = 1;
   BS_CK(cudaGetDevice(&dev));
   BS_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   BS_CK(cudaFuncSetAttribute(k_solve_rod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   BS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_rod, 128, smem));
-  int nblk = (nsys + 15) / 16;
+  int nblk = (nsys + rods_per_block - 1) / rods_per_block;
   if (nblk > per_sm * sms) nblk = per_sm * sms;
   if (nblk > sms) nblk = sms;  // one block of four warps per SM, as in dm_step
   if (nblk < 1) nblk = 1;

@@ -138,9 +138,42 @@ __device__ __forceinline__ void load_edge(const double *ef, int NE, int e, int s
   m2 = mk(s * ef[10 * NE + e], s * ef[11 * NE + e], s * ef[12 * NE + e]);
 }
 
-// One bend-twist stencil (the work of one thread); returns early when inactive.
+// Gradient of one stencil in its 11 DOFs: (e_a, e_b, A, B) -> [x0, th_a,
+// x1, th_b, x2] with x0 = -e_a, x1 = e_a - e_b, x2 = e_b, A = sa th_a,
+// B = sb th_b.
+__device__ __forceinline__ void write_gradient(const StencilArgs &a, int k, const double *g8,
+                                               int sa, int sb) {
+  double *G = a.sg;
+  const int NS = a.ns;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    G[(0 + c) * NS + k] = -g8[c];
+    G[(4 + c) * NS + k] = g8[c] - g8[3 + c];
+    G[(8 + c) * NS + k] = g8[3 + c];
+  }
+  G[3 * NS + k] = sa * g8[6];
+  G[7 * NS + k] = sb * g8[7];
+}
+
+// The Hessian pass runs for a system only if the solver will factor its
+// Jacobian this round: it is still iterating, its residual is above the
+// tolerance (the solver's own convergence test on the same value), it has
+// not failed, and the line search is not backtracking it.
+__device__ __forceinline__ bool hess_due(const StencilArgs &a, int s) {
+  if (a.sys_status[s] != 0) return false;
+  if (a.ls_action && a.ls_action[s] == 1) return false;
+  return !(__longlong_as_double((long long)a.sys_res[s]) <= a.tol);
+}
+
+// One bend-twist stencil (the work of one thread); returns early when
+// inactive.  MODE 0: gradient and Hessian; 1: reference twist and gradient
+// (the residual pass of a round); 2: Hessian of the systems the solver will
+// factor, with the reference twist the gradient pass wrote (the Jacobian
+// pass of a round).
+template <int MODE>
 __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
-  const bool act = k < a.ns && a.sys_active[a.st_sys[k]];
+  bool act = k < a.ns && a.sys_active[a.st_sys[k]];
+  if (MODE == 2 && act) act = hess_due(a, a.st_sys[k]);
   count_units(a.units, act);
   if (!act) return;
   const int sys = a.st_sys[k];
@@ -155,7 +188,7 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
   // Eq. 4: curvature binormal
   const double chi = 1.0 + dot(ta, tb);
   if (!(chi > 1e-12)) {
-    atomicMax(&a.sys_status[sys], (int)DM_ERR_DEGENERATE);
+    if (MODE != 2) atomicMax(&a.sys_status[sys], (int)DM_ERR_DEGENERATE);
     return;
   }
   const double ichi = 1.0 / chi;
@@ -166,14 +199,19 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
   const double k2 = -0.5 * dot(kb, M1);
   // Eq. 7: reference twist, continued from the committed value
   const v3 s_ab = ta + tb;
-  const v3 u = axpy(-dot(d1a, tb) * ichi, s_ab, d1a);
-  const double ang = atan2(dot(tb, cross(u, d1b)), dot(u, d1b));
-  const double bn = a.beta_n[k];
-  double dd = ang - bn;
-  dd -= 6.283185307179586 * rint(dd * 0.15915494309189535);
-  const double beta = bn + dd;
-  a.beta_it[k] = beta;
-  if (a.frames_only) return;
+  double beta;
+  if (MODE == 2) {
+    beta = a.beta_it[k];
+  } else {
+    const v3 u = axpy(-dot(d1a, tb) * ichi, s_ab, d1a);
+    const double ang = atan2(dot(tb, cross(u, d1b)), dot(u, d1b));
+    const double bn = a.beta_n[k];
+    double dd = ang - bn;
+    dd -= 6.283185307179586 * rint(dd * 0.15915494309189535);
+    beta = bn + dd;
+    a.beta_it[k] = beta;
+    if (a.frames_only) return;
+  }
   const double tha = a.q[a.st_th[k]], thb = a.q[a.st_th[NS + k]];
   const double tau = sb * thb - sa * tha + beta;
   const double kbs = a.st_kb[k], kts = a.st_kt[k];
@@ -205,9 +243,24 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
   }
   // energy gradient (8-space) and its outer-product Hessian part
   double g8[8];
-  double h[36];
 #pragma unroll
   for (int i = 0; i < 8; ++i) g8[i] = fma(c1, g1[i], fma(c2, g2[i], c3 * g3[i]));
+  if (MODE == 1) {
+    // the holonomy correction of the gradient (see the Hessian block below)
+    const v3 tna = (double)sa * mk(a.tn[a.st_ed[k]], a.tn[NE + a.st_ed[k]], a.tn[2 * NE + a.st_ed[k]]);
+    const v3 tnb = (double)sb * mk(a.tn[a.st_ed[NS + k]], a.tn[NE + a.st_ed[NS + k]],
+                                   a.tn[2 * NE + a.st_ed[NS + k]]);
+    const v3 ga = ila * ((1.0 / (1.0 + dot(tna, ta))) * cross(tna, ta));
+    const v3 gb = ilb * ((1.0 / (1.0 + dot(tnb, tb))) * cross(tnb, tb));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      g8[i] -= g8[6] * cmp(ga, i);
+      g8[3 + i] -= g8[7] * cmp(gb, i);
+    }
+    write_gradient(a, k, g8, sa, sb);
+    return;
+  }
+  double h[36];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -407,17 +460,7 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
     }
   }
 
-  // map (e_a, e_b, A, B) -> 11 stencil DOFs [x0, th_a, x1, th_b, x2]:
-  // x0 = -e_a, x1 = e_a - e_b, x2 = e_b, A = sa th_a, B = sb th_b
-  double *G = a.sg;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    G[(0 + c) * NS + k] = -g8[c];
-    G[(4 + c) * NS + k] = g8[c] - g8[3 + c];
-    G[(8 + c) * NS + k] = g8[3 + c];
-  }
-  G[3 * NS + k] = sa * g8[6];
-  G[7 * NS + k] = sb * g8[7];
+  if (MODE == 0) write_gradient(a, k, g8, sa, sb);
 
   // H11 = T^T H8 T written as packed upper triangle
   auto H8 = [&](int i, int j) -> double { return i <= j ? h[up<8>(i, j)] : h[up<8>(j, i)]; };
@@ -452,10 +495,18 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
     }
 }
 
+// block-uniform grid-stride loops (count_units synchronises the block)
 __global__ void __launch_bounds__(128) k_stencil(StencilArgs a) {
-  // block-uniform grid-stride loop (count_units synchronises the block)
   for (int b0 = blockIdx.x * blockDim.x; b0 < a.ns; b0 += gridDim.x * blockDim.x)
-    k_stencil_one(a, b0 + threadIdx.x);
+    k_stencil_one<0>(a, b0 + threadIdx.x);
+}
+__global__ void __launch_bounds__(128) k_stencil_grad(StencilArgs a) {
+  for (int b0 = blockIdx.x * blockDim.x; b0 < a.ns; b0 += gridDim.x * blockDim.x)
+    k_stencil_one<1>(a, b0 + threadIdx.x);
+}
+__global__ void __launch_bounds__(128) k_stencil_hess(StencilArgs a) {
+  for (int b0 = blockIdx.x * blockDim.x; b0 < a.ns; b0 += gridDim.x * blockDim.x)
+    k_stencil_one<2>(a, b0 + threadIdx.x);
 }
 
 }  // namespace dm

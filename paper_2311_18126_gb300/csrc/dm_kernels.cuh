@@ -26,6 +26,10 @@ struct StencilArgs {
   unsigned long long *units;
   double *dk;  // NULL, or [22][Ns]: gradients of kappa1, kappa2 (11 stencil DOFs each)
   int frames_only;  // 1: reference twist only (the commit of an implicit-midpoint step)
+  // Hessian pass (k_stencil_hess): the solver's convergence test
+  const unsigned long long *sys_res;
+  double tol;
+  const int32_t *ls_action;  // NULL without line search
 };
 
 struct RowArgs {
@@ -42,6 +46,10 @@ struct RowArgs {
   double *f, *band;
   unsigned long long *sys_res;
   unsigned long long *units;
+  // band pass (k_rows_rod_band): the solver's convergence test
+  const int32_t *sys_status;
+  double tol;
+  const int32_t *ls_action;  // NULL without line search
 };
 
 struct SolveArgs {
@@ -64,6 +72,8 @@ struct SolveArgs {
 // shared memory (doubles) per rod of k_solve_rod: two chain windows and the
 // separator scratch
 constexpr int kSolveRodDoubles = 2 * (22 * 12 + 2) + 32;
+// rods per warp of k_solve_rod (two chains of eight lanes each per rod)
+constexpr int kSolveRodsPerWarp = 2;
 
 struct NodeArgs {
   int nn;
@@ -203,8 +213,12 @@ __global__ void k_gen_border(SolveGenArgs a);
 __global__ void k_gen_limb_back(SolveGenArgs a);
 
 __global__ void k_edge(EdgeArgs a);
-__global__ void k_stencil(StencilArgs a);
-__global__ void k_rows_rod(RowArgs a);
+__global__ void k_stencil(StencilArgs a);       // gradient and Hessian
+__global__ void k_stencil_grad(StencilArgs a);  // reference twist and gradient
+__global__ void k_stencil_hess(StencilArgs a);  // Hessian of systems still to be solved
+__global__ void k_rows_rod(RowArgs a);       // residual and band rows
+__global__ void k_rows_rod_res(RowArgs a);   // residual rows
+__global__ void k_rows_rod_band(RowArgs a);  // band rows of systems still to be solved
 __global__ void k_solve_rod(SolveArgs a);
 
 struct StepArgs {

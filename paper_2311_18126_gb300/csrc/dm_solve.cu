@@ -26,10 +26,23 @@ __device__ __forceinline__ int ksym(int c, int cp) {  // packed 3x3 (xx,xy,xz,yy
   return 3 + (i == 0 ? j : (i == 1 ? 2 + j : 5));
 }
 
+// The band pass runs for a system only if the solver will factor its
+// Jacobian this round (the test of the Hessian pass of the stencils).
+__device__ __forceinline__ bool band_due(const RowArgs &a, int s) {
+  if (a.sys_status[s] != 0) return false;
+  if (a.ls_action && a.ls_action[s] == 1) return false;
+  return !(__longlong_as_double((long long)a.sys_res[s]) <= a.tol);
+}
+
 // One DOF row (the work of one thread); returns early when inactive.
+// MODE 0: residual and band row; 1: residual only (the residual pass of a
+// round); 2: band row of the systems the solver will factor (the Jacobian
+// pass).
+template <int MODE>
 __device__ __forceinline__ void k_rows_rod_one(RowArgs a, const int i) {
-  const bool act = i < a.nd && a.sys_active[a.dof_sys[i]] &&
-                   a.sys_kind[a.dof_sys[i]] != SOLVE_GENERAL;
+  bool act = i < a.nd && a.sys_active[a.dof_sys[i]] &&
+             a.sys_kind[a.dof_sys[i]] != SOLVE_GENERAL;
+  if (MODE == 2 && act) act = band_due(a, a.dof_sys[i]);
   count_units(a.units, act);
   if (!act) return;
   const int s = a.dof_sys[i];
@@ -53,11 +66,13 @@ __device__ __forceinline__ void k_rows_rod_one(RowArgs a, const int i) {
   for (int m = mlo; m <= mhi; ++m) {
     const int lr = r - 4 * (m - 1);
     const int st = st0 + m - 1;
-    F -= a.sg[lr * NS + st];
+    if (MODE != 2) F -= a.sg[lr * NS + st];
+    if (MODE != 1) {
 #pragma unroll
-    for (int d = 0; d < 11; ++d) {
-      const int lc = lr - d;
-      if (lc >= 0) brow[d] += a.sh[upk<11>(lc, lr) * NS + st];
+      for (int d = 0; d < 11; ++d) {
+        const int lc = lr - d;
+        if (lc >= 0) brow[d] += a.sh[upk<11>(lc, lr) * NS + st];
+      }
     }
   }
   const double m_i = a.mass[i];
@@ -65,75 +80,99 @@ __device__ __forceinline__ void k_rows_rod_one(RowArgs a, const int i) {
   if (c < 3) {
     if (node <= N - 2) {  // edge `node` starts here
       const int e = e0 + node;
-      F += a.es[c * NE + e];
+      if (MODE != 2) F += a.es[c * NE + e];
+      if (MODE != 1) {
 #pragma unroll
-      for (int cp = 0; cp <= 2; ++cp)
-        if (cp <= c) brow[c - cp] += a.es[ksym(c, cp) * NE + e];
+        for (int cp = 0; cp <= 2; ++cp)
+          if (cp <= c) brow[c - cp] += a.es[ksym(c, cp) * NE + e];
+      }
     }
     if (node >= 1) {  // edge `node-1` ends here
       const int e = e0 + node - 1;
-      F -= a.es[c * NE + e];
+      if (MODE != 2) F -= a.es[c * NE + e];
+      if (MODE != 1) {
 #pragma unroll
-      for (int cp = 0; cp <= 2; ++cp) {
-        const double kv = a.es[ksym(c, cp) * NE + e];
-        if (cp <= c) brow[c - cp] += kv;
-        brow[4 + c - cp] -= kv;
+        for (int cp = 0; cp <= 2; ++cp) {
+          const double kv = a.es[ksym(c, cp) * NE + e];
+          if (cp <= c) brow[c - cp] += kv;
+          brow[4 + c - cp] -= kv;
+        }
       }
     }
-    F += m_i * a.g[c];
     const double cd = a.damp[i];
-    F -= cd * (a.q[i] - a.qn[i]);
+    if (MODE != 2) {
+      F += m_i * a.g[c];
+      F -= cd * (a.q[i] - a.qn[i]);
+    }
     brow[0] += cd;
   }
-  if (a.fc) F += a.fc[i];
-  brow[0] += m_i * idt * idt;
-  double f = m_i * idt * idt * (a.q[i] - a.qn[i]) - m_i * idt * a.vn[i] - F;
-  if (a.fixed[i]) {
-    f = 0.0;
-    brow[0] = 1.0;
+  if (MODE != 1) {
+    brow[0] += m_i * idt * idt;
+    if (a.fixed[i]) {
+      brow[0] = 1.0;
 #pragma unroll
-    for (int d = 1; d < 11; ++d) brow[d] = 0.0;
-  } else {
+      for (int d = 1; d < 11; ++d) brow[d] = 0.0;
+    } else {
 #pragma unroll
-    for (int d = 1; d < 11; ++d)
-      if (r - d < 0 || a.fixed[i - d]) brow[d] = 0.0;
+      for (int d = 1; d < 11; ++d)
+        if (r - d < 0 || a.fixed[i - d]) brow[d] = 0.0;
+    }
+#pragma unroll
+    for (int d = 0; d < 11; ++d) a.band[(size_t)d * a.nd + i] = brow[d];
   }
-  a.f[i] = f;
-#pragma unroll
-  for (int d = 0; d < 11; ++d) a.band[(size_t)d * a.nd + i] = brow[d];
-  // scaled residual, max-reduced per system (order independent)
-  const double rr = fabs(f) * a.rscale[i];
-  atomicMax(&a.sys_res[s], (unsigned long long)__double_as_longlong(rr));
+  if (MODE != 2) {
+    if (a.fc) F += a.fc[i];
+    double f = m_i * idt * idt * (a.q[i] - a.qn[i]) - m_i * idt * a.vn[i] - F;
+    if (a.fixed[i]) f = 0.0;
+    a.f[i] = f;
+    // scaled residual, max-reduced per system (order independent)
+    const double rr = fabs(f) * a.rscale[i];
+    atomicMax(&a.sys_res[s], (unsigned long long)__double_as_longlong(rr));
+  }
 }
 
+// block-uniform grid-stride loops (count_units synchronises the block)
 __global__ void __launch_bounds__(256) k_rows_rod(RowArgs a) {
-  // block-uniform grid-stride loop (count_units synchronises the block)
   for (int b0 = blockIdx.x * blockDim.x; b0 < a.nd; b0 += gridDim.x * blockDim.x)
-    k_rows_rod_one(a, b0 + threadIdx.x);
+    k_rows_rod_one<0>(a, b0 + threadIdx.x);
+}
+__global__ void __launch_bounds__(256) k_rows_rod_res(RowArgs a) {
+  for (int b0 = blockIdx.x * blockDim.x; b0 < a.nd; b0 += gridDim.x * blockDim.x)
+    k_rows_rod_one<1>(a, b0 + threadIdx.x);
+}
+__global__ void __launch_bounds__(256) k_rows_rod_band(RowArgs a) {
+  for (int b0 = blockIdx.x * blockDim.x; b0 < a.nd; b0 += gridDim.x * blockDim.x)
+    k_rows_rod_one<2>(a, b0 + threadIdx.x);
 }
 
 // Banded LDL^T solve of J dq = -f for single rods.
 //
 // The FP64 pipe of an SM partition retires one warp instruction about every
-// 80 cycles whatever the active mask, and a column of the band elimination
-// is a short dependency chain, so a 4096-rod batch is latency-bound unless
-// every partition holds several warps whose lanes all do useful FP64 work.
-// Each rod is therefore factored from both ends at once (a twisted
-// factorisation): a top chain eliminates columns 0..m-1 downwards, a bottom
-// chain eliminates columns n-1..m+10 upwards, and the 10-row separator left
-// in the middle is combined from both windows and solved densely.  Each
-// chain is run by four lanes with one uniform instruction stream; the 11x11
-// active window and the right-hand side live in shared memory.  Eliminating
-// a column costs 10 multipliers, 55 trailing updates and 10 right-hand-side
-// updates (forward substitution fused in); lane p owns whole window rows,
-// balanced by work (row i carries i + 1 FMAs):
-//   lane 0: rows 10, 3, 1   lane 1: rows 9, 5   lane 2: rows 8, 6
-//   lane 3: rows 7, 4, 2    -- at most 17 FMAs and 3 multipliers per lane.
-// The next pivot is updated first by lane 0, broadcast by a shuffle, and its
-// reciprocal (FP32 seed, two FP64 Newton steps) overlaps the other updates.
-// Rods are taken from a queue in order of decreasing size, four per warp.
+// 64 cycles whatever the active mask, and a column of the band elimination
+// is a short dependency chain, so the solve is bound by the chain of
+// dependent column steps of the largest rods unless every lane does useful
+// FP64 work and every column step is short.  Each rod is therefore factored
+// from both ends at once (a twisted factorisation): a top chain eliminates
+// columns 0..m-1 downwards, a bottom chain eliminates columns n-1..m+10
+// upwards, and the 10-row separator left in the middle is combined from both
+// windows and solved densely.  Each chain is run by eight lanes with one
+// uniform instruction stream; the 11x11 active window and the right-hand
+// side live in shared memory.  Eliminating a column costs 10 multipliers,
+// 55 trailing updates and 10 right-hand-side updates (forward substitution
+// fused in); the 65 update tasks are split over the eight lanes, rows 9 and
+// 10 across two lanes each (q = column in the window, r = right-hand side):
+//   lane 0: row 8            lane 1: row 7          lane 2: rows 6, 1
+//   lane 3: rows 5, 2        lane 4: rows 4, 3      lane 5: row 10 q1-7
+//   lane 6: row 10 q8-10,r; row 9 q1-3              lane 7: row 9 q4-9,r
+// -- at most 9 FMAs and 2 multipliers per lane.  Lane 2 updates the next
+// pivot (row 1) first and broadcasts it by a shuffle; its reciprocal (FP32
+// seed, two FP64 Newton steps) overlaps the other updates.  A warp holds two
+// rods (four chains); rods are taken from a queue in order of decreasing
+// size, two per warp.
 #define SOLVE_WARPS 4
-#define SOLVE_RODS_PER_WARP 4
+#define SOLVE_RODS_PER_WARP kSolveRodsPerWarp
+#define SOLVE_LANES 8  // lanes per chain
+static_assert(SOLVE_RODS_PER_WARP * 2 * SOLVE_LANES == 32, "two chains per rod fill a warp");
 // Window of a chain in shared memory: matrix rows in order, 12 doubles per
 // row (the 11 lower-band diagonals J[r][r-d], d = 0..10, then the
 // right-hand side), SOLVE_WROWS rows; the pivot row walks down the buffer
@@ -152,15 +191,19 @@ __device__ __forceinline__ double rcp64(double d) {
 }
 
 // Task k of lane p: window row i (bits 0-3) and u index q (bits 4-7,
-// 0 = right-hand side, 15 = padding); row slot r (bits 8-9) in rows[].
+// 0 = right-hand side, 15 = padding); row slot (bits 8-9) among the lane's
+// two multipliers.
 __host__ __device__ constexpr int task_code(int p, int k) {
-  // lane rows in order; each row i contributes q = 1..i then q = 0
-  int rows[4][3] = {{10, 3, 1}, {9, 5, 0}, {8, 6, 0}, {7, 4, 2}};
+  // (row, first q, last q) segments of each lane; q = i + 1 stands for the
+  // right-hand side
+  const int seg[8][2][3] = {{{8, 1, 9}, {0, 0, -1}},  {{7, 1, 8}, {0, 0, -1}},
+                            {{6, 1, 7}, {1, 1, 2}},   {{5, 1, 6}, {2, 1, 3}},
+                            {{4, 1, 5}, {3, 1, 4}},   {{10, 1, 7}, {0, 0, -1}},
+                            {{10, 8, 11}, {9, 1, 3}}, {{9, 4, 10}, {0, 0, -1}}};
   int t = 0;
-  for (int r = 0; r < 3; ++r) {
-    const int i = rows[p][r];
-    if (i == 0) continue;
-    for (int q = 1; q <= i + 1; ++q) {
+  for (int r = 0; r < 2; ++r) {
+    const int i = seg[p][r][0];
+    for (int q = seg[p][r][1]; q <= seg[p][r][2]; ++q) {
       const int qq = (q == i + 1) ? 0 : q;
       if (t == k) return i | (qq << 4) | (r << 8);
       ++t;
@@ -168,6 +211,18 @@ __host__ __device__ constexpr int task_code(int p, int k) {
   }
   return 15 << 4;  // padding
 }
+// window row of the lane's multiplier slot r (0 = none)
+__host__ __device__ constexpr int lane_row(int p, int r) {
+  return r == 0 ? (p == 0 ? 8 : p == 1 ? 7 : p == 2 ? 6 : p == 3 ? 5 : p == 4 ? 4 : p == 5 ? 10
+                                                                       : p == 6 ? 10 : 9)
+                : (p == 2 ? 1 : p == 3 ? 2 : p == 4 ? 3 : p == 6 ? 9 : 0);
+}
+// the lane that stores the multiplier of slot r (rows 9 and 10 live on two lanes)
+__host__ __device__ constexpr bool lane_stores(int p, int r) {
+  return lane_row(p, r) > 0 && !(p == 6 && r == 0) && !(p == 7 && r == 0);
+}
+#define SOLVE_TASKS 9
+#define SOLVE_PIVOT_LANE 2  // owns row 1: the next pivot
 
 struct Chain {
   // address maps of one elimination direction
@@ -189,6 +244,12 @@ struct Chain {
   __device__ __forceinline__ double *zstore(int idx) const { return dq + base + orig(idx); }
 };
 
+// A pivot smaller than kTinyPivot times the original diagonal entry of its
+// row counts as zero: J = M/dt^2 - dF/dq need not be positive definite
+// (large steps, compressed or buckling rods), and without pivoting such a
+// pivot would amplify rounding errors without bound.
+constexpr double kTinyPivot = 1e-13;
+
 // Eliminates `ncol` columns of a chain.  On return the window rows
 // W[(b + i) * 12 + .] (b = the final base, also stored at W[SOLVE_WROWS * 12])
 // hold rows ncol..ncol+10 of the partially reduced matrix and right-hand side.
@@ -197,121 +258,123 @@ struct Chain {
 // column j to j+1 moves no data: the update of window entry (i, q) (row
 // j+i, column j+q) is always at offset 12 i + (i - q) from the pivot row,
 // its column entry a_q at 13 q, the multiplier source at 13 i, and the
-// right-hand side at 12 i + 11; every lane holds its 17 offsets in
+// right-hand side at 12 i + 11; every lane holds its 9 offsets in
 // registers.  Rows beyond the end are zero, so no update needs a bound test.
 //
-// All eight chains of a warp run the same number of iterations (`nwarp`,
+// All four chains of a warp run the same number of iterations (`nwarp`,
 // the warp's largest ncol); a chain past its own ncol changes nothing, so
 // every synchronisation is warp-wide and the warp never diverges.
-// A pivot smaller than kTinyPivot times the original diagonal entry of its
-// row counts as zero: J = M/dt^2 - dF/dq need not be positive definite
-// (large steps, compressed or buckling rods), and without pivoting such a
-// pivot would amplify rounding errors without bound.
-constexpr double kTinyPivot = 1e-13;
-
+//
 // Dg (lane 0 of the chain only): an 11-slot ring of the original diagonal
 // entries of the rows in the window, filled from the loads that bring the
 // rows in.
 __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, double *W, int p,
-                                          int leader, double *Dg) {
+                                          int pivot_lane, double *Dg) {
   const int n = c.n;
-  int rows[3];
-  rows[0] = p == 0 ? 10 : (p == 1 ? 9 : (p == 2 ? 8 : 7));
-  rows[1] = p == 0 ? 3 : (p == 1 ? 5 : (p == 2 ? 6 : 4));
-  rows[2] = p == 0 ? 1 : (p == 3 ? 2 : 0);
-  int toff[17], uoff[17], rsel[17];
+  int toff[SOLVE_TASKS], uoff[SOLVE_TASKS], rsel[SOLVE_TASKS];
 #pragma unroll
-  for (int k = 0; k < 17; ++k) {
-    const int code = p == 0 ? task_code(0, k) : (p == 1 ? task_code(1, k) : (p == 2 ? task_code(2, k) : task_code(3, k)));
+  for (int k = 0; k < SOLVE_TASKS; ++k) {
+    int code = 0;
+#pragma unroll
+    for (int pp = 0; pp < SOLVE_LANES; ++pp)
+      if (p == pp) code = task_code(pp, k);
     const int i = code & 15, q = (code >> 4) & 15;
-    rsel[k] = q == 15 ? 3 : (code >> 8);
+    rsel[k] = q == 15 ? 2 : (code >> 8);
     toff[k] = q == 15 ? 0 : (q == 0 ? 12 * i + 11 : 12 * i + (i - q));
     uoff[k] = q == 15 ? 0 : (q == 0 ? 11 : 13 * q);
   }
-  int loff[3];
+  int row0 = 0, row1 = 0;
+  bool st0 = false, st1 = false;
 #pragma unroll
-  for (int r = 0; r < 3; ++r) loff[r] = 13 * rows[r];
+  for (int pp = 0; pp < SOLVE_LANES; ++pp)
+    if (p == pp) {
+      row0 = lane_row(pp, 0);
+      row1 = lane_row(pp, 1);
+      st0 = lane_stores(pp, 0);
+      st1 = lane_stores(pp, 1);
+    }
+  const int loff0 = 13 * row0, loff1 = 13 * row1;
   // rows 0..10 of the chain; diagonals reaching before row 0 are zero
   if (ncol > 0)
-    for (int e = p; e < 11 * 12; e += 4) {
+    for (int e = p; e < 11 * 12; e += SOLVE_LANES) {
       const int r = e / 12, d = e - 12 * r;
       double v = 0.0;
       if (r < n) v = d == 11 ? c.rhs(r) : (d <= r ? *c.entry(r, d) : 0.0);
       W[e] = v;
-      if (d == 0) Dg[r] = v;  // lane 0 holds every d == 0 entry
     }
   __syncwarp();
+  if (ncol > 0 && p == 0)
+    for (int r = 0; r < 11; ++r) Dg[r] = W[12 * r];
   double rj = ncol > 0 ? rcp64(W[0]) : 1.0;
   bool bad = false;
   int b = 0, jr = 0;  // jr = j mod 11, the ring slot of row j
   for (int j = 0; j < nwarp; ++j) {
     const bool act = j < ncol;
-    // prefetch of row j + 11 (diagonals p, p+4, p+8; the right-hand side)
+    // prefetch of row j + 11 (diagonals p and p + 8; the right-hand side)
     const bool more = act && j + 11 < n;
-    double pre0 = 0.0, pre1 = 0.0, pre2 = 0.0, prz = 0.0;
+    double pre0 = 0.0, pre1 = 0.0, prz = 0.0;
     if (more) {
       pre0 = *c.entry(j + 11, p);
-      pre1 = *c.entry(j + 11, p + 4);
-      if (p + 8 < 11) pre2 = *c.entry(j + 11, p + 8);
+      if (p + 8 < 11) pre1 = *c.entry(j + 11, p + 8);
       if (p == 3) prz = c.rhs(j + 11);
     }
     double *Wb = W + 12 * b;
     const double zj = Wb[11];
     if (act && p == 0) {
       // |D_j| < kTinyPivot |J_jj| (1/rj infinite or not finite included)
-      if (!isfinite(rj) || rj == 0.0 || fabs(Dg[jr]) * kTinyPivot * fabs(rj) > 1.0) bad = true;
+      if (!isfinite(rj) || rj == 0.0 ||
+          fabsf((float)Dg[jr]) * (float)kTinyPivot * fabsf((float)rj) > 1.0f)  // in FP32: off the FP64 pipe
+        bad = true;
       Dg[jr] = pre0;  // row j + 11 takes the slot (0 past the end)
       jr = jr == 10 ? 0 : jr + 1;
       *c.zstore(j) = zj * rj;  // z_j = y_j / D_j for the backward pass
     }
-    double l[4];
+    const double l0 = row0 > 0 ? Wb[loff0] * rj : 0.0;
+    const double l1 = row1 > 0 ? Wb[loff1] * rj : 0.0;
+    double uq[SOLVE_TASKS], dv[SOLVE_TASKS];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) l[r] = rows[r] > 0 ? Wb[loff[r]] * rj : 0.0;
-    l[3] = 0.0;
-    double uq[17], dv[17];
-#pragma unroll
-    for (int k = 0; k < 17; ++k) {
+    for (int k = 0; k < SOLVE_TASKS; ++k) {
       uq[k] = Wb[uoff[k]];
       dv[k] = Wb[toff[k]];
     }
-    // next pivot first (lane 0 owns window row 1), broadcast, reciprocal
+    // next pivot first (the pivot lane owns window row 1), broadcast, reciprocal
     double piv = 1.0;
-    if (p == 0 && act && j + 1 < n) piv = fma(-l[2], Wb[13], Wb[12]);
-    piv = __shfl_sync(0xffffffffu, piv, leader);
+    if (p == SOLVE_PIVOT_LANE && act && j + 1 < n) piv = fma(-l1, Wb[13], Wb[12]);
+    piv = __shfl_sync(0xffffffffu, piv, pivot_lane);
+    // no barrier here: every update target is read only by its own lane
     const double rnext = act ? rcp64(piv) : rj;
-    __syncwarp();
     if (act) {
+      if (st0 && j + row0 < n) *c.lstore(j, row0) = l0;
+      if (st1 && j + row1 < n) *c.lstore(j, row1) = l1;
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const int i = rows[r];
-        if (i > 0 && j + i < n) *c.lstore(j, i) = l[r];
-      }
-#pragma unroll
-      for (int k = 0; k < 17; ++k) {
-        const double lk = rsel[k] == 0 ? l[0] : (rsel[k] == 1 ? l[1] : (rsel[k] == 2 ? l[2] : l[3]));
-        if (rsel[k] < 3) Wb[toff[k]] = fma(-lk, uq[k], dv[k]);
-      }
+      for (int k = 0; k < SOLVE_TASKS; ++k)
+        if (rsel[k] < 2) Wb[toff[k]] = fma(-(rsel[k] == 0 ? l0 : l1), uq[k], dv[k]);
       // the new row j + 11 (zeros past the end)
       double *Wn = Wb + 12 * 11;
       Wn[p] = pre0;
-      Wn[p + 4] = pre1;
-      if (p + 8 < 11) Wn[p + 8] = pre2;
+      if (p + 8 < 11) Wn[p + 8] = pre1;
       if (p == 3) Wn[11] = prz;
     }
-    __syncwarp();
     const bool wrap = act && b + 1 == SOLVE_WROWS - 11;
-    // move rows b+1..b+11 (the next window) to the top of the buffer
-    double t[33];
-    if (wrap) {
+    // move rows b+1..b+11 (the next window) to the top of the buffer; the
+    // extra barriers only in the columns where some chain of the warp wraps
+    if (__any_sync(0xffffffffu, wrap)) {
+      double t[17];
+      if (wrap) {
 #pragma unroll
-      for (int u = 0; u < 33; ++u) t[u] = Wb[12 + p + 4 * u];
-    }
-    __syncwarp();
-    if (wrap) {
+        for (int u = 0; u < 17; ++u)
+          if (p + SOLVE_LANES * u < 132) t[u] = Wb[12 + p + SOLVE_LANES * u];
+      }
+      __syncwarp();
+      if (wrap) {
 #pragma unroll
-      for (int u = 0; u < 33; ++u) W[p + 4 * u] = t[u];
+        for (int u = 0; u < 17; ++u)
+          if (p + SOLVE_LANES * u < 132) W[p + SOLVE_LANES * u] = t[u];
+      }
+      __syncwarp();
+    } else {
+      __syncwarp();
     }
-    __syncwarp();
     if (act) {
       b = wrap ? 0 : b + 1;
       rj = rnext;
@@ -335,7 +398,7 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 // exist are zero.
 __device__ __forceinline__ void stage_rows(const Chain &c, bool on, int k0, int kstart,
                                            double *buf, int p) {
-  for (int e = p; e < 121; e += 4) {
+  for (int e = p; e < 121; e += SOLVE_LANES) {
     const int u = e / 11, d = e - 11 * u;
     const int kk = k0 - u;
     bool ok = on && kk >= 0 && kk < c.n && kk <= kstart + 9;
@@ -360,12 +423,13 @@ __device__ __forceinline__ void stage_rows(const Chain &c, bool on, int k0, int 
 // 11 rows (W[0..120], W[121..241]), filled by asynchronous copies one block
 // of rows ahead, and the running z values in an 11-slot ring (W[242..252]).
 // `on` = this chain solves; `ktop` = the warp's largest kstart + 9 (uniform
-// trip count, warp-wide synchronisation).
+// trip count, warp-wide synchronisation).  Lane p applies diagonals p + 1
+// and p + 9.
 __device__ __forceinline__ void back_substitute(const Chain &c, bool on, int kstart, int ktop,
                                                 const double *xs, double *W, double *q, int p) {
   double *Z = W + 242;
   if (on)
-    for (int m = kstart - 1 - p; m >= 0 && m >= kstart - 11; m -= 4) Z[m % 11] = *c.zstore(m);
+    for (int m = kstart - 1 - p; m >= 0 && m >= kstart - 11; m -= SOLVE_LANES) Z[m % 11] = *c.zstore(m);
   stage_rows(c, on, ktop, kstart, W, p);
   cp_async_commit();
   for (int g = 0; ktop - 11 * g >= 0; ++g) {
@@ -390,8 +454,8 @@ __device__ __forceinline__ void back_substitute(const Chain &c, bool on, int kst
       __syncwarp();
       if (act) {
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          const int d = 1 + p + 4 * t;
+        for (int t = 0; t < 2; ++t) {
+          const int d = 1 + p + SOLVE_LANES * t;
           if (d <= 10 && k - d >= 0 && k - d < kstart) {
             const int slot = (k - d) % 11;
             Z[slot] = fma(-cur[u * 11 + d], xk, Z[slot]);
@@ -409,19 +473,20 @@ __device__ __forceinline__ void back_substitute(const Chain &c, bool on, int kst
 __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
-  const int unit = lane >> 3;          // rod slot in the warp
-  const int half = (lane >> 2) & 1;    // 0 = top chain, 1 = bottom chain
-  const int p = lane & 3;
+  const int unit = lane >> 4;                      // rod slot in the warp
+  const int half = (lane >> 3) & 1;                // 0 = top chain, 1 = bottom chain
+  const int p = lane & (SOLVE_LANES - 1);
   const int rid = (threadIdx.x >> 5) * SOLVE_RODS_PER_WARP + unit;
   double *Wt = smem + (size_t)rid * (2 * SOLVE_CHAIN_STRIDE + 32);
   double *Wb = Wt + SOLVE_CHAIN_STRIDE;
   double *XS = Wb + SOLVE_CHAIN_STRIDE;  // separator solution (10), diagonal rings (2 x 11)
   double *W = half ? Wb : Wt;
   const unsigned full = 0xffffffffu;
-  const int leader = unit * 8 + half * 4;
-  const bool head = (lane & 7) == 0;     // bookkeeping lane of the rod
+  const int pivot_lane = unit * 16 + half * SOLVE_LANES + SOLVE_PIVOT_LANE;
+  const bool head = (lane & 15) == 0;     // bookkeeping lane of the rod
+  const unsigned rod_mask = 0xFFFFu << (unit * 16);
 
-  // The warp takes four consecutive rods of the size-sorted queue at a time
+  // The warp takes two consecutive rods of the size-sorted queue at a time
   // and factors them in lockstep.
   while (true) {
     int t = 0;
@@ -465,10 +530,9 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
     const int ncol = !go ? 0 : (half ? (twist ? n - m - 10 : 0) : m);
     const int nwarp = __reduce_max_sync(full, ncol);
     // the rod's scratch past the separator solution: one diagonal ring per chain
-    bool bad = eliminate(c, ncol, nwarp, W, p, leader, XS + 10 + 11 * half);
+    bool bad = eliminate(c, ncol, nwarp, W, p, pivot_lane, XS + 10 + 11 * half);
     // a rod is bad if either of its chains met a zero pivot
-    const unsigned bm = __ballot_sync(full, bad);
-    bad = ((bm >> (unit * 8)) & 0xFFu) != 0;
+    bad = (__ballot_sync(full, bad) & rod_mask) != 0;
     if (bad && go) {
       if (head) {
         a.sys_status[s] = DM_ERR_DEGENERATE;
@@ -479,11 +543,11 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
       go = false;
     }
     // separator: S = top window + bottom window - original (10 x 10, lower),
-    // right-hand side likewise; dense LDL^T by the rod's 8 lanes (one row of
-    // the trailing update each, rows 8 and 9 by lanes 0 and 1), staged in the
-    // top window after it has been read
-    const bool sep = go && twist;
-    const int r8 = lane & 7;
+    // right-hand side likewise; dense LDL^T by the rod's top-chain lanes (one
+    // row of the trailing update each, rows 8 and 9 by lanes 0 and 1), staged
+    // in the top window after it has been read
+    const bool sep = go && twist && half == 0;
+    const int r8 = p;
     double sv[14];
     if (sep) {
       const int bt = (int)Wt[SOLVE_WROWS * 12], bb = (int)Wb[SOLVE_WROWS * 12];
@@ -564,8 +628,7 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
         atomicAdd(a.q + c.base + m + i, x);
       }
     }
-    const unsigned sm = __ballot_sync(full, sbad);
-    if (((sm >> (unit * 8)) & 0xFFu) != 0 && go) {
+    if ((__ballot_sync(full, sbad) & rod_mask) != 0 && go) {
       if (head) {
         a.sys_status[s] = DM_ERR_DEGENERATE;
         a.sys_active[s] = 0;

@@ -335,16 +335,23 @@ class System:
                                                       k.ctypes.data_as(C.c_void_p), 0))
 
     def get_state(self, q=None, qdot=None):
-        """Host copy (numpy) unless torch CUDA tensors are given."""
+        """(q, qdot) in the per-rod layout of Eq. 1.  Into torch CUDA tensors
+        when given; into caller-owned host arrays (numpy float64, e.g. views
+        of pinned memory, which copy fastest) when given; otherwise into new
+        numpy arrays."""
         if q is not None and hasattr(q, "data_ptr"):
             _check(self._lib.dm_get_state(self._h, _dev_ptr(q),
                                           _dev_ptr(qdot) if qdot is not None else None,
                                           self.n_state, 1))
             return q, qdot
-        q = np.zeros(self.n_state)
-        v = np.zeros(self.n_state)
+        q = np.zeros(self.n_state) if q is None else q
+        v = np.zeros(self.n_state) if qdot is None else qdot
+        for a in (q, v):
+            if (a.dtype != np.float64 or not a.flags.c_contiguous or a.size < self.n_state):
+                raise ValueError("host state buffers must be contiguous float64 arrays of "
+                                 "at least %d entries" % self.n_state)
         _check(self._lib.dm_get_state(self._h, q.ctypes.data_as(C.c_void_p),
-                                      v.ctypes.data_as(C.c_void_p), self.n_state, 0))
+                                      v.ctypes.data_as(C.c_void_p), q.size, 0))
         return q, v
 
     def set_state(self, q, qdot):

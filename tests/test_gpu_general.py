@@ -165,3 +165,18 @@ def test_star_robots_full_batch_sampled_robots_in_bench_configuration():
     # the first steps settle the robots onto the ground (many line-search
     # iterations): Newton ends just under the tolerance on both sides
     _assert_close(qs, qo, sub["nodes_per_rod"], 1.0, 1e-7)
+
+
+def test_star_robots_30_node_limbs_per_step_tight_newton():
+    """The star-robot configuration of the bench (limbs of 30 nodes, 0.1 m,
+    on the ground, line search, gait), backward Euler per step from identical
+    states at 1e-10, with Newton run to 1e-13 on both sides.  On the step in
+    which the robots settle onto the ground the twist angles of the
+    converged state move about 400 times the scaled residual at which
+    Newton stops (the oracle alone: stopping at 5e-12 instead of 2e-15
+    moves them by 2e-9), so two correct solvers that stop at different
+    points under a 1e-10 or 1e-12 tolerance can differ by more than 1e-10;
+    under 1e-13 that term stays below 4e-11."""
+    desc, params, gait = workloads.star_robots(n_robots=2, seed=3)
+    R = len(desc["nodes_per_rod"])
+    _run(desc, dict(params, tol=1e-13), 4, 1e-10, lambda t: workloads.gait_kbar(gait, t), R)

@@ -741,3 +741,26 @@ def test_damped_axial_oscillator_exact_step_map(integ):
         assert o.step_system(s)[0] == 0
         assert abs(float(s.q[4]) - l - y) <= 1e-9 * amp
         assert abs(float(s.v[4]) - v) <= 1e-9 * v0
+
+
+def test_mlp_gradient_error_scale_bounds_and_matches_positive_terms():
+    # the element-wise error scale of the network gradients (sum of the
+    # absolute values of the terms) is at least |gradient| everywhere, and
+    # equals the gradient where every term is non-negative: positive inputs
+    # and weights, outputs above their targets
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    n = sum(fo * fi + fo for fi, fo in zip(mlp.DIN, mlp.DOUT))
+    X = mlp.bf16(rng.standard_normal((64, 64)))
+    Y = rng.standard_normal((64, 64))
+    p = 0.05 * rng.standard_normal(n)
+    _, g = mlp.loss_and_grad(p, X, Y, 4, rounding=True)
+    S = mlp.grad_abs_scale(p, X, Y, 4)
+    assert np.all(S >= np.abs(g) * (1 - 2.0 ** -6) - 1e-30)
+    assert np.max(S) > 0
+    Xp = mlp.bf16(np.abs(X))
+    pp = np.abs(p)
+    Yp = np.full_like(Y, -10.0)
+    _, gp = mlp.loss_and_grad(pp, Xp, Yp, 4, rounding=True)
+    Sp = mlp.grad_abs_scale(pp, Xp, Yp, 4)
+    np.testing.assert_allclose(gp, Sp, rtol=2.0 ** -6, atol=1e-30)

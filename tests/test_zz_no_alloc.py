@@ -49,3 +49,28 @@ def test_noalloc_rejects_oversized_batch():
     with pytest.raises(DismechError) as ei:
         solve_band_noalloc([0], [n], tb, tr, torch.empty_like(tr))
     assert ei.value.code == 1 and "limit" in str(ei.value)
+
+
+def test_noalloc_full_scratch_on_a_side_stream_then_a_smaller_batch():
+    # exactly the fixed limit (2048 systems, 32768 DOFs, short and twisted
+    # systems mixed), ordered on a non-default stream, then a much smaller
+    # batch whose scratch regions still hold the first call's data
+    import torch
+    from paper_2311_18126_gb300 import ensure_built, solve_band, solve_band_noalloc
+    from paper_2311_18126_gb300.dismech import NOALLOC_MAX_DOFS, NOALLOC_MAX_SYSTEMS
+    ensure_built()
+    big = [4] * 1536 + [40] * 256 + [64] * 256
+    assert len(big) == NOALLOC_MAX_SYSTEMS and sum(big) == NOALLOC_MAX_DOFS
+    side = torch.cuda.Stream()
+    for sizes, seed in ((big, 3), ([799, 197, 33, 32, 31, 11, 7], 4)):
+        band, rhs, _ = random_band_batch(sizes, seed)
+        d0 = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+        tb = torch.tensor(band, device="cuda")
+        tr = torch.tensor(rhs, device="cuda")
+        ref = torch.empty_like(tr)
+        solve_band(d0, sizes, tb, tr, ref)
+        out = torch.full_like(tr, float("nan"))
+        side.wait_stream(torch.cuda.current_stream())
+        solve_band_noalloc(d0, sizes, tb, tr, out, stream=side.cuda_stream)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(out.cpu().numpy(), ref.cpu().numpy(), rtol=1e-12, atol=1e-14)

@@ -18,7 +18,12 @@ Workloads (all SI units, FP64):
   curvature A sin(2 pi t / T + 2 pi j / k), A ~ U[0, 20] 1/m,
   T ~ U[0.5, 2] s, mu ~ U[0.3, 0.8], dt = 5e-3.
 * ``coil``        -- one 500-node helical rod, h = 1e-3 m, helix radius
-  0.02 m, pitch 2.2 h, natural curvature 1.5x the helix's, self-contact on.
+  0.02 m, pitch 2.2 h, stress-free at rest (natural strains = initial),
+  clamped at its lower end and collapsing under gravity until its turns
+  touch, edge-edge self-contact on, dt = 2.5e-4.
+* ``gripper``     -- five 60-node fingers hanging from a 3 cm ring, actuated
+  by random natural curvatures, edge-edge contact with friction between all
+  fingers (one contact group), dt = 1e-3.
 
 Integrated natural curvature (the library's input) is the physical curvature
 times the rest Voronoi length; for a uniformly spaced rod that length is the
