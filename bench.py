@@ -93,6 +93,9 @@ def parse():
                          "mlp: the warm-start network's tensor-core inference and training "
                          "at the headline batch's segment count")
     ap.add_argument("--robots", type=int, default=1024)
+    ap.add_argument("--predictor", default="projected", choices=["extrapolate", "projected"],
+                    help="Newton's starting guess on single rods: q_n + dt qdot_n, or that "
+                         "guess with every edge rescaled to its committed length")
     ap.add_argument("--integrator", default="be", choices=["be", "midpoint"],
                     help="backward Euler (default) or implicit midpoint (Sec. III-C)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -297,6 +300,8 @@ def run_ours(args):
         # without numerical damping plain Newton diverges on stiff rods of
         # this batch (the oracle likewise, e.g. rod 379 at its 5th step)
         params["line_search"] = True
+    else:
+        params["predictor"] = args.predictor
     R = len(desc["nodes_per_rod"])
     sysm = System(desc, params)
     sysm.set_natural_curvature(0, R, kbar)
@@ -413,6 +418,7 @@ def run_ours(args):
                        "nodes_per_gpu": int(np.sum(desc["nodes_per_rod"])),
                        "dofs_per_gpu": int(n), "dt": params["dt"], "newton_tol": params["tol"],
                        "line_search": bool(params.get("line_search", False)),
+                       "predictor": params.get("predictor", "extrapolate"),
                        "parallelism": "dp%d: each GPU steps a DOF-balanced shard of contiguous systems of one batch %d x the one-GPU size" % (ws, ws),
                        "l2": "no flush: per-iteration working set (~0.7 GB) exceeds L2"},
             "newton": {"iters_mean": float(it.mean()), "iters_max": int(it.max()),
@@ -553,6 +559,9 @@ def run_other(args):
     if args.integrator != "be":
         params = dict(params, integrator=args.integrator)
         line["config"]["integrator"] = args.integrator
+    elif args.workload == "long_rods":
+        params = dict(params, predictor=args.predictor)
+        line["config"]["predictor"] = args.predictor
     R = len(desc["nodes_per_rod"])
     warm = max(args.warmup, 400) if args.workload in ("coil", "gripper") else args.warmup
     line["warmup"] = warm
@@ -575,8 +584,12 @@ def run_other(args):
         mlp, norm, losses = wsm.train(feats, tgts, iters=4000, batch=16384, seed=1)
         del feats, tgts
         arms = {}
-        for label, model in (("extrapolation", None), ("learned", mlp)):
-            sysm = System(desc, params)
+        variants = [("extrapolation", None, "extrapolate"), ("learned", mlp, "extrapolate")]
+        if args.workload == "warm_start_rods":
+            # single rods: the length-projected guess, with and without the network
+            variants += [("projected", None, "projected"), ("learned_projected", mlp, "projected")]
+        for label, model, pred in variants:
+            sysm = System(desc, dict(params, predictor=pred))
             sysm.set_natural_curvature(0, R, controls(0))
             tuning = None if args.no_autotune else sysm.autotune(steps=2)
             if model is not None:
@@ -624,14 +637,17 @@ def run_other(args):
                                       "note": "setting the state resets the velocity history "
                                               "of the previous-correction features"}
             sysm.close()
-        line.update({"value": arms["learned"]["value"],
-                     "ms_per_step": arms["learned"]["ms_per_step"],
-                     "learned": {"speedup_vs_extrapolation":
-                                 arms["learned"]["value"] / arms["extrapolation"]["value"],
-                                 "train_loss": [losses[0], losses[-1]], "arms": arms},
-                     "clocks": arms["learned"]["clocks"],
-                     "gpu_launches": arms["learned"]["gpu_launches"],
-                     "e2e": arms["learned"]["e2e"], "roofline": None,
+        head = "learned_projected" if "learned_projected" in arms else "learned"
+        learned = {"speedup_vs_extrapolation": arms[head]["value"] / arms["extrapolation"]["value"],
+                   "arm": head, "train_loss": [losses[0], losses[-1]], "arms": arms}
+        if "projected" in arms:
+            learned["speedup_vs_projected"] = arms[head]["value"] / arms["projected"]["value"]
+        line.update({"value": arms[head]["value"],
+                     "ms_per_step": arms[head]["ms_per_step"],
+                     "learned": learned,
+                     "clocks": arms[head]["clocks"],
+                     "gpu_launches": arms[head]["gpu_launches"],
+                     "e2e": arms[head]["e2e"], "roofline": None,
                      "roofline_note": "solver kernels as in the headline line; the network's "
                                       "tensor-core roofline is the mlp workload's line"})
         line["config"]["training"] = tnote + ", 4000 Adam steps of 16384 segments"
@@ -749,14 +765,16 @@ def run_calibration(args):
                                      gait["phase"][None, :])
     c_true = np.stack([c1, np.zeros_like(c1)], axis=-1)
     expand = lambda c: (c[:, :, None, :] * spacing).expand(-1, -1, nint, -1).reshape(T, R * nint, 2)
+    # every tensor of the pass on the GPU: controls, states, target, loss
+    cuda = lambda a: torch.as_tensor(a, dtype=torch.float64).cuda()
+    q0t, v0t = cuda(q0), cuda(v0)
     with torch.no_grad():
-        target = rollout(sysm, expand(torch.from_numpy(c_true)), torch.from_numpy(q0),
-                         torch.from_numpy(v0), frames, K)
-    pos = torch.from_numpy(_layout_positions(np.asarray(desc["nodes_per_rod"])).astype(np.float64))
-    c = torch.zeros_like(torch.from_numpy(c_true), requires_grad=True)
+        target = rollout(sysm, expand(cuda(c_true)), q0t, v0t, frames, K)
+    pos = cuda(_layout_positions(np.asarray(desc["nodes_per_rod"])).astype(np.float64))
+    c = torch.zeros_like(cuda(c_true), requires_grad=True)
 
     def loss_grad(cc):
-        x = rollout(sysm, expand(cc), torch.from_numpy(q0), torch.from_numpy(v0), frames, K)
+        x = rollout(sysm, expand(cc), q0t, v0t, frames, K)
         loss = (((x - target) ** 2) * pos).sum()
         g, = torch.autograd.grad(loss, [cc])
         return float(loss.detach()), g
@@ -785,6 +803,14 @@ def run_calibration(args):
                 step *= 1.5
                 break
             step *= 0.5
+    # end to end: the same pass with the controls and their gradient in host
+    # memory (the controls go to the device, the gradient comes back)
+    c_host = c.detach().cpu().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, g_host = loss_grad(c_host)
+    g_host = g_host.numpy()
+    te = time.perf_counter() - t0
     line = {"metric": METRIC, "value": R * T / tg, "unit": "rod-steps/s (loss+gradient pass)",
             "n_gpus": ws, "steps": T, "warmup": 0, "ms_per_step": 1e3 * tg / T,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -793,13 +819,12 @@ def run_calibration(args):
                        "500 steps, per-step per-limb natural curvature, checkpoints every 50",
                        "rods": R, "params": int(np.prod(c_true.shape)), "seed": 4 + rank},
             "calibration": {"gradient_seconds": tg, "losses": losses}, "clocks": clocks,
-            # the pass already runs through the public API with host arrays:
-            # per forward step the controls go in and the state comes out
-            "e2e": {"value": R * T / tg, "unit": "rod-steps/s (loss+gradient pass)",
+            "e2e": {"value": R * T / te, "unit": "rod-steps/s (loss+gradient pass)",
                     "h2d_bytes_per_step": int(R * nint * 2 * 8),
-                    "d2h_bytes_per_step": int(2 * len(q0) * 8),
-                    "note": "the loss+gradient pass itself (forward, re-simulation, adjoint), "
-                            "host buffers every step"},
+                    "d2h_bytes_per_step": int(c_true.shape[1] * 2 * 8),
+                    "note": "the loss+gradient pass with the per-step controls in host memory "
+                            "(copied in) and their gradient returned to host memory; the timed "
+                            "pass above keeps controls, states, target and gradient on the GPU"},
             "roofline": None}
     if rank == 0:
         print(json.dumps(line))

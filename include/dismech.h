@@ -134,6 +134,15 @@ typedef struct dm_params {
                            partitioned, interiors of 502 rows) instead of the
                            twisted LDL^T chain; 0 = 2048 (512 nodes),
                            negative = never */
+  int32_t predictor;    /* Newton's starting guess (the paper leaves it open;
+                           Newton runs to the same tolerance from any guess):
+                           0: q_n + dt qdot_n, fixed DOFs at q_n; 1: the same,
+                           then for every system of a single rod each edge
+                           rescaled to its committed length, node positions
+                           rebuilt outward from the rod's first node along
+                           the guess's edge directions (nodes with a fixed
+                           position DOF keep theirs), also applied to a
+                           learned guess.  Backward Euler only.             */
 } dm_params;
 
 /* Optional per-call statistics (caller-owned arrays may be NULL). */
@@ -196,9 +205,12 @@ dm_status dm_set_state(dm_system *sys, const double *q, const double *qdot,
 
 /* History a bitwise resume needs: reference director d1 per edge
  * ([sum (N_r-1)][3], descriptor edge order) and reference twist beta per
- * bend-twist stencil ([dm_num_stencils]).  Host buffers.  Either may be NULL. */
-dm_status dm_get_frames(dm_system *sys, double *d1, double *beta);
-dm_status dm_set_frames(dm_system *sys, const double *d1, const double *beta);
+ * bend-twist stencil ([dm_num_stencils]).  Host buffers (the calls
+ * synchronise the stream), or device buffers when is_device != 0 (ordered
+ * on the system's stream, no synchronisation).  Either may be NULL. */
+dm_status dm_get_frames(dm_system *sys, double *d1, double *beta, int32_t is_device);
+dm_status dm_set_frames(dm_system *sys, const double *d1, const double *beta,
+                        int32_t is_device);
 
 /* Sizes. */
 int64_t dm_state_size(const dm_system *sys);  /* sum (4 N_r - 1) */
@@ -381,6 +393,30 @@ dm_status dm_ws_column_stats(const float *data, int64_t rows, int32_t cols, floa
 dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq,
                           const double *gv, double *gkbar, double *gq0, double *gv0,
                           int32_t is_device);
+
+/* Frame chain of the adjoint of a rollout (no counterpart in the paper,
+ * whose calibration uses finite differences).  dm_step_adjoint holds the
+ * committed reference frames of its step fixed; over a rollout they come
+ * from the earlier tangents by time-parallel transport (Sec. III), which
+ * this call adds, one step at a time, going backwards:
+ *   sigma_e = -((gq + gv/dt) - gv0/dt) at edge e's twist angle (0 if fixed)
+ *             -- the adjoint of a rotation of e's committed director;
+ *   phibar_e <- phibar_e + sigma_e;
+ *   gq0 += the node-position gradient of -phibar_e [w(t_e, t_e') + w(t_e'', t_e)]
+ *          through t = e/|e|, with w(a, b) = (a x b)/(1 + a . b) the
+ *          holonomy of the transport, t_e, t_e', t_e'' the tangents in q,
+ *          q_next and q_prev.
+ * q_prev (the state before q, or NULL at the start of the rollout), q and
+ * q_next (the step's states), gq, gv (the loss gradients given to
+ * dm_step_adjoint for this step) and gv0 (its dL/dqdot_n output) are in the
+ * dm_get_state layout; phibar is [sum (N_r-1)] (descriptor edge order, in:
+ * the value carried from the later steps, zeros at the end of the rollout;
+ * out: the value to carry to the earlier ones); gq0 (dm_step_adjoint's
+ * dL/dq_n output) is updated in place.  All device pointers; ordered on the
+ * system's stream without synchronisation.  Backward Euler only. */
+dm_status dm_adjoint_frame_chain(dm_system *sys, const double *q_prev, const double *q,
+                                 const double *q_next, const double *gq, const double *gv,
+                                 const double *gv0, double *phibar, double *gq0);
 
 /* Edge-edge contact (Sec. III-B, Eq. 10-11; params.self_contact != 0):
  * number of edge pairs closer than C + delta at the last evaluated Newton

@@ -57,7 +57,7 @@ DEFAULT_PARAMS = dict(dt=1e-3, tol=1e-10, max_iter=100,
                       g=(0.0, 0.0, -9.81), eta=0.0,
                       ground=False, ground_z=0.0, delta=5e-4, nu_slip=1e-3,
                       self_contact=False, pair_kc=0.0, pair_mu=0.0,
-                      line_search=False, integrator="be")
+                      line_search=False, integrator="be", predictor="extrapolate")
 
 
 class _Sys:
@@ -600,6 +600,8 @@ class OracleSystems:
         q_n, v_n = s.q.clone(), s.v.clone()
         q = q_n + dt * v_n                                 # reading C23
         q = torch.where(s.fixed, q_n, q)
+        if self.p.get("predictor", "extrapolate") == "projected":
+            q = self._project_lengths(s, q, q_n)
         status, it = ERR_NOT_CONVERGED, 0
         res = scale = float("nan")
         ls = bool(self.p["line_search"])
@@ -645,6 +647,25 @@ class OracleSystems:
         if status == OK:
             self._commit(s, q, q_n)
         return status, it, res, scale
+
+    def _project_lengths(self, s, q, q_n):
+        """The length-projected starting guess (an option; Newton's root does
+        not depend on it): on a system of one rod, each edge of the guess q
+        takes its length in q_n, node positions rebuilt from the first node
+        along the guess's edge directions; nodes with a fixed position DOF
+        keep their value.  Other systems keep q."""
+        if len(s.rods) != 1 or self.p["self_contact"]:
+            return q
+        out = q.clone()
+        nd = s.node_dof
+        for k in range(1, len(nd)):
+            a, b = nd[k - 1], nd[k]
+            if bool(s.fixed[b:b + 3].any()):
+                continue
+            e = q[b:b + 3] - q[a:a + 3]
+            l_n = torch.linalg.vector_norm(q_n[b:b + 3] - q_n[a:a + 3])
+            out[b:b + 3] = out[a:a + 3] + l_n * e / torch.linalg.vector_norm(e)
+        return out
 
     def _commit(self, s, q, q_n):
         """Velocity update (Sec. III-C) and commit of the reference frames

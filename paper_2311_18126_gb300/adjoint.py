@@ -29,53 +29,6 @@ import torch
 from . import dismech as dmx
 
 
-def _edge_tangents(q, npr):
-    """Unit tangents [E, 3] and inverse lengths [E] of every edge, from a
-    state in the dm_get_state layout."""
-    ts, ils = [], []
-    off = 0
-    for N in npr:
-        x = q[off:off + 4 * N - 1]
-        X = np.stack([x[4 * i:4 * i + 3] for i in range(N)])
-        e = X[1:] - X[:-1]
-        l = np.linalg.norm(e, axis=1)
-        ts.append(e / l[:, None])
-        ils.append(1.0 / l)
-        off += 4 * N - 1
-    return np.concatenate(ts), np.concatenate(ils)
-
-
-def _hol(a, b):
-    """w(a, b) = (a x b) / (1 + a . b) per edge."""
-    return np.cross(a, b) / (1.0 + np.sum(a * b, axis=1))[:, None]
-
-
-def _theta_index(npr):
-    """Layout index of every edge's twist angle."""
-    idx = []
-    off = 0
-    for N in npr:
-        idx.append(off + 4 * np.arange(N - 1) + 3)
-        off += 4 * N - 1
-    return np.concatenate(idx)
-
-
-def _tangent_to_positions(gt, il, t, npr, n):
-    """dL/dt per edge -> dL/dq on the node positions (t = e/|e|)."""
-    g = gt - np.sum(gt * t, axis=1)[:, None] * t
-    g = g * il[:, None]
-    out = np.zeros(n)
-    off = 0
-    e0 = 0
-    for N in npr:
-        for i in range(N - 1):
-            out[off + 4 * (i + 1):off + 4 * (i + 1) + 3] += g[e0 + i]
-            out[off + 4 * i:off + 4 * i + 3] -= g[e0 + i]
-        e0 += N - 1
-        off += 4 * N - 1
-    return out
-
-
 def _layout_positions(npr):
     """Boolean mask of the position entries in the dm_get_state layout."""
     mask = []
@@ -91,67 +44,72 @@ class Rollout(torch.autograd.Function):
 
     kbar_seq: [T, slots, 2] float64 (natural curvature applied before each
     step), q0, v0: [n] float64 (dm_get_state layout), frames0: (d1, beta) of
-    the initial state.  Returns the states q_1..q_T as [T, n] float64; the
-    gradient flows to kbar_seq, q0 and v0."""
+    the initial state.  Returns the states q_1..q_T as [T, n] float64 on the
+    device of q0; the gradient flows to kbar_seq, q0 and v0.  Every state,
+    checkpoint and gradient of the forward and backward passes stays in GPU
+    memory; the frame chain runs in the library (dm_adjoint_frame_chain)."""
 
     @staticmethod
     def forward(ctx, kbar_seq, q0, v0, system, frames0, checkpoint_every):
+        dev = torch.device("cuda")
+        f64 = dict(device=dev, dtype=torch.float64)
         T = kbar_seq.shape[0]
         R = system.n_rods
-        kb = kbar_seq.detach().cpu().numpy()
-        q = q0.detach().cpu().numpy().copy()
-        v = v0.detach().cpu().numpy().copy()
+        kb = kbar_seq.detach().to(**f64).contiguous()
+        q = q0.detach().to(**f64).clone()
+        v = v0.detach().to(**f64).clone()
+        d1 = torch.as_tensor(np.asarray(frames0[0]), **f64).contiguous()
+        beta = torch.as_tensor(np.asarray(frames0[1]), **f64).contiguous()
         system.set_state(q, v)
-        system.set_frames(*frames0)
+        system.set_frames(d1, beta)
         ckpt = {}
-        out = np.zeros((T, len(q)))
+        out = torch.empty((T, q.numel()), **f64)
         qprev = None
         for t in range(T):
             if t % checkpoint_every == 0:
-                ckpt[t] = (q.copy(), v.copy()) + tuple(a.copy() for a in system.get_frames()) \
-                    + (None if qprev is None else qprev.copy(),)
+                fr = system.get_frames(torch.empty_like(d1), torch.empty_like(beta))
+                ckpt[t] = (q, v) + fr + (qprev,)
             system.set_natural_curvature(0, R, kb[t])
             system.step(1, stats=False)
             qprev = q
-            q, v = system.get_state()
+            q, v = system.get_state(torch.empty_like(q), torch.empty_like(v))
             out[t] = q
         ctx.system = system
         ctx.kb = kb
         ctx.ckpt = ckpt
         ctx.every = checkpoint_every
         ctx.T = T
-        return torch.from_numpy(out)
+        ctx.devices = (kbar_seq.device, q0.device, v0.device)
+        ctx.frame_shapes = (d1.shape, beta.shape)
+        return out.to(q0.device)
 
     @staticmethod
     def backward(ctx, gx):
         system, kb, T, every = ctx.system, ctx.kb, ctx.T, ctx.every
         R = system.n_rods
-        gx = gx.detach().cpu().numpy()
+        gx = gx.detach().to(device="cuda", dtype=torch.float64)
         n = gx.shape[1]
-        npr = np.asarray(system._npr)
-        dt = system.dt
-        th = _theta_index(npr)
-        thfree = ~system.fixed_mask()[th]
-        gk = np.zeros_like(kb)
-        carry_q = np.zeros(n)
-        carry_v = np.zeros(n)
-        carry_phi = np.zeros(len(th))
-        starts = sorted(ctx.ckpt)
-        for s0 in reversed(starts):
+        gk = torch.zeros_like(kb)
+        carry_q = torch.zeros(n, dtype=torch.float64, device="cuda")
+        carry_v = torch.zeros_like(carry_q)
+        carry_phi = torch.zeros(system.n_edges, dtype=torch.float64, device="cuda")
+        d1_shape, beta_shape = ctx.frame_shapes
+        for s0 in reversed(sorted(ctx.ckpt)):
             s1 = min(s0 + every, T)
             q, v, d1, beta, qprev = ctx.ckpt[s0]
-            # re-simulate the segment, keeping its per-step states
+            # re-simulate the segment, keeping its per-step states and frames
             seg = []
             system.set_state(q, v)
             system.set_frames(d1, beta)
             for t in range(s0, s1):
-                frames = system.get_frames()
-                qs, vs = system.get_state()
+                fr = system.get_frames(torch.empty(d1_shape, dtype=torch.float64, device="cuda"),
+                                       torch.empty(beta_shape, dtype=torch.float64,
+                                                   device="cuda"))
                 system.set_natural_curvature(0, R, kb[t])
                 system.step(1, stats=False)
-                qn, _ = system.get_state()
-                seg.append((qs, vs, frames, qn, qprev))
-                qprev = qs
+                qn, vn = system.get_state(torch.empty_like(q), torch.empty_like(v))
+                seg.append((q, v, fr, qn, qprev))
+                qprev, q, v = q, qn, vn
             for t in range(s1 - 1, s0 - 1, -1):
                 qs, vs, frames, qn, qp = seg[t - s0]
                 system.set_state(qs, vs)
@@ -161,18 +119,11 @@ class Rollout(torch.autograd.Function):
                 gv = carry_v
                 gkt, gq0, gv0 = system.step_adjoint(qn, gq, gv)
                 gk[t] = gkt
-                # frame chain (module docstring)
-                sigma = np.where(thfree, -((gq[th] + gv[th] / dt) - gv0[th] / dt), 0.0)
-                phibar = carry_phi + sigma
-                tt, il = _edge_tangents(qs, npr)
-                t1, _ = _edge_tangents(qn, npr)
-                w = _hol(tt, t1)
-                if qp is not None:
-                    w = w + _hol(_edge_tangents(qp, npr)[0], tt)
-                gq0 = gq0 + _tangent_to_positions(-phibar[:, None] * w, il, tt, npr, n)
-                carry_q, carry_v, carry_phi = gq0, gv0, phibar
-        return torch.from_numpy(gk), torch.from_numpy(carry_q), torch.from_numpy(carry_v), \
-            None, None, None
+                # frame chain (module docstring): carry_phi and gq0 in place
+                system.adjoint_frame_chain(qp, qs, qn, gq, gv, gv0, carry_phi, gq0)
+                carry_q, carry_v = gq0, gv0
+        dk, dq, dv = ctx.devices
+        return gk.to(dk), carry_q.to(dq), carry_v.to(dv), None, None, None
 
 
 def rollout(system, kbar_seq, q0, v0, frames0, checkpoint_every=50):

@@ -101,4 +101,86 @@ __global__ void k_adj_kbar(AdjArgs a) {
   }
 }
 
+
+
+// ---------------------------------------------------------------------------
+// Frame chain of a rollout adjoint (the step adjoint holds the committed
+// frames fixed; each step's frames come from the earlier tangents by
+// time-parallel transport, Sec. III).  A rotation of edge e's committed
+// director acts on the energy like a shift of its twist angle, so its
+// adjoint is sigma_e = -(gbar_theta - M_theta/dt^2 lambda_theta), which in
+// the step adjoint's own quantities is -((gq + gv/dt) - gv0/dt) at theta_e;
+// moving a tangent rotates the directors transported from or to it by
+// -w . dt with w(a, b) = (a x b)/(1 + a . b), the holonomy of the geodesic
+// triangle.  Carried backwards: Phibar_n = Phibar_{n+1} + sigma and
+// dL/dt_n = -Phibar_n [w(t_n, t_{n+1}) + w(t_{n-1}, t_n)], taken to the
+// node positions through t = e/|e|.  All vectors in the state layout.
+
+__device__ __forceinline__ void unit_edge(const double *q, int a, double t[3], double &il) {
+  const double ex = q[a + 4] - q[a], ey = q[a + 5] - q[a + 1], ez = q[a + 6] - q[a + 2];
+  il = 1.0 / sqrt(ex * ex + ey * ey + ez * ez);
+  t[0] = ex * il;
+  t[1] = ey * il;
+  t[2] = ez * il;
+}
+
+__device__ __forceinline__ void add_holonomy(const double a[3], const double b[3], double w[3]) {
+  const double c = 1.0 / (1.0 + a[0] * b[0] + a[1] * b[1] + a[2] * b[2]);
+  w[0] += (a[1] * b[2] - a[2] * b[1]) * c;
+  w[1] += (a[2] * b[0] - a[0] * b[2]) * c;
+  w[2] += (a[0] * b[1] - a[1] * b[0]) * c;
+}
+
+// per edge: sigma, Phibar, and the tangent term g_e (3 doubles) to add at
+// its end node and subtract at its start node
+__global__ void k_frame_chain_edges(FrameChainArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.ne) return;
+  const int x0 = a.edge_lay[e], th = x0 + 3;
+  const double sigma =
+      a.fixed[a.layout2dof[th]] ? 0.0 : -((a.gq[th] + a.gv[th] / a.dt) - a.gv0[th] / a.dt);
+  const double phi = a.phibar[e] + sigma;
+  a.phibar[e] = phi;
+  double t[3], t1[3], il, il1, w[3] = {0.0, 0.0, 0.0};
+  unit_edge(a.q, x0, t, il);
+  unit_edge(a.q_next, x0, t1, il1);
+  add_holonomy(t, t1, w);
+  if (a.q_prev) {
+    double tp[3], ilp;
+    unit_edge(a.q_prev, x0, tp, ilp);
+    add_holonomy(tp, t, w);
+  }
+  const double gt[3] = {-phi * w[0], -phi * w[1], -phi * w[2]};
+  const double tg = gt[0] * t[0] + gt[1] * t[1] + gt[2] * t[2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) a.g[3 * e + c] = (gt[c] - tg * t[c]) * il;
+}
+
+// per layout node: + the term of the edge ending there - that of the edge
+// starting there (a fixed order: deterministic)
+__global__ void k_frame_chain_nodes(FrameChainArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.nlnode) return;
+  const int x = a.lnode_lay[k], ein = a.lnode_ein[k], eout = a.lnode_eout[k];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double v = 0.0;
+    if (ein >= 0) v += a.g[3 * ein + c];
+    if (eout >= 0) v -= a.g[3 * eout + c];
+    a.gq0[x + c] += v;
+  }
+}
+
+// committed directors SoA [3][Ne] <-> caller layout [Ne][3]
+__global__ void k_frames_out(int ne, const double *soa, double *aos) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  for (int c = 0; c < 3; ++c) aos[3 * e + c] = soa[c * ne + e];
+}
+__global__ void k_frames_in(int ne, const double *aos, double *soa) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  for (int c = 0; c < 3; ++c) soa[c * ne + e] = aos[3 * e + c];
+}
+
 }  // namespace dm

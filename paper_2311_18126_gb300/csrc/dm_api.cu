@@ -133,6 +133,12 @@ struct Extra {
     int32_t *ints = nullptr; // bookkeeping of the transposed solve
     unsigned long long *res = nullptr;
   } adj;  // step adjoint (allocated on first use)
+  struct {
+    int nlnode = 0;
+    int32_t *edge_lay = nullptr, *lnode_lay = nullptr, *lnode_ein = nullptr,
+            *lnode_eout = nullptr, *layout2dof = nullptr;
+    double *g = nullptr;
+  } fchain;  // frame chain of rollout adjoints (allocated on first use)
   int n_fast = 0, n_slow = 0;   // general systems on the condensation / Schur path
   size_t border_smem = 0;
   int limb_nmax = 0, wpb_factor = 1, wpb_back = 1;  // limb kernels: rows, warps per block
@@ -200,6 +206,10 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     s->x.midpoint = true;
   } else if (prm->integrator != 0) {
     set_error("integrator must be 0 (backward Euler) or 1 (implicit midpoint)");
+    return DM_ERR_INVALID_ARG;
+  }
+  if (prm->predictor != 0 && (prm->predictor != 1 || prm->integrator != 0)) {
+    set_error("predictor must be 0, or 1 (length-projected) with backward Euler");
     return DM_ERR_INVALID_ARG;
   }
   if (!build_topology(desc, prm, T)) return DM_ERR_INVALID_ARG;
@@ -763,6 +773,8 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     stats->max_iterations = 0;
   }
   std::vector<int32_t> iters;
+  // residual and Jacobian passes apart, except with rod networks
+  const bool split = !gen_on;
   // One Newton round: every phase's launches, in stream order on rs.
   auto round = [&](cudaStream_t rs, int it) -> dm_status {
     k_reset_res<<<blocks(S, 256), 256, 0, rs>>>(0, S, d.sys_active, d.sys_res);
@@ -780,12 +792,15 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     }
     // residual pass: reference twist and gradients, then the residual rows;
     // the Jacobian pass (stencil Hessians, band rows) below runs only for
-    // systems whose residual is still above the tolerance
+    // systems whose residual is still above the tolerance.  Batches with rod
+    // networks keep one fused pass: most of their many rounds carry systems
+    // that iterate on, for which the split would only add work.
     const int st_tb = s->x.tune.stencil_threads;
     const int st_grid = blocks(ns, (int64_t)st_tb * s->x.tune.stencil_per_thread);
     if (ns > 0) {
       Timed t(s, K_STENCIL, rs);
-      k_stencil_grad<<<st_grid, st_tb, 0, rs>>>(ka);
+      if (split) k_stencil_grad<<<st_grid, st_tb, 0, rs>>>(ka);
+      else k_stencil<<<st_grid, st_tb, 0, rs>>>(ka);
     }
     if (contact_on) {
       Timed t(s, K_CONTACT, rs);
@@ -805,7 +820,8 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     if (rows_on) {
       Timed t(s, K_ROWS, rs);
       const int tb = s->x.tune.rows_threads;
-      k_rows_rod_res<<<blocks(nd, tb), tb, 0, rs>>>(ra);
+      if (split) k_rows_rod_res<<<blocks(nd, tb), tb, 0, rs>>>(ra);
+      else k_rows_rod<<<blocks(nd, tb), tb, 0, rs>>>(ra);
     }
     if (gen_on) {
       Timed t(s, K_ROWS_GEN, rs);
@@ -817,13 +833,13 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       k_ls_apply<<<blocks(nd, 256), 256, 0, rs>>>(la);
       if (ws_trial && it == 0) DM_CK(ws_inject(s, rs, s->x.ls_action, s->x.ls_trial));
     }
-    if (ns > 0) {
+    if (split && ns > 0) {
       Timed t(s, K_HESS, rs);
       StencilArgs kh = ka;
       kh.units = s->x.prof ? s->x.d_units + K_HESS : nullptr;
       k_stencil_hess<<<st_grid, st_tb, 0, rs>>>(kh);
     }
-    if (rows_on) {
+    if (split && rows_on) {
       Timed t(s, K_BAND, rs);
       const int tb = s->x.tune.rows_threads;
       RowArgs rb = ra;
@@ -948,6 +964,11 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     if (ws_on) {
       Timed t(s, K_WARM, st);
       DM_CK(ws_predict(s, st, ws_trial, s->x.d_dof_sys));
+    }
+    if (s->prm.predictor == 1) {
+      k_project_lengths<<<blocks((int64_t)S * 32, 128), 128, 0, st>>>(
+          S, s->x.d_sys_kind, d.sys_dof0, d.sys_ndof, d.fixed, d.qn, d.q);
+      s->x.launches[K_BEGIN]++;
     }
     if (ls_on) {
       DM_CK(cudaMemsetAsync(s->x.ls_trial, 0, S * sizeof(int32_t), st));
@@ -1119,13 +1140,24 @@ dm_status dm_set_state(dm_system *sys, const double *q, const double *qdot, size
   return DM_OK;
 }
 
-dm_status dm_get_frames(dm_system *sys, double *d1, double *beta) {
+dm_status dm_get_frames(dm_system *sys, double *d1, double *beta, int32_t is_device) {
   if (!sys) {
     set_error("dm_get_frames: NULL handle");
     return DM_ERR_INVALID_ARG;
   }
   const HostTopology &T = sys->T;
   cudaStream_t st = sys->stream;
+  const int ne = (int)T.n_edges;
+  if (is_device) {
+    if (d1 && ne > 0) {
+      k_frames_out<<<blocks(ne, 256), 256, 0, st>>>(ne, sys->d.d1n, d1);
+      DM_CK(cudaGetLastError());
+    }
+    if (beta && T.n_stencils > 0)
+      DM_CK(cudaMemcpyAsync(beta, sys->d.beta_n, T.n_stencils * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st));
+    return DM_OK;
+  }
   if (d1) {
     std::vector<double> soa(3 * T.n_edges);
     DM_CK(cudaMemcpyAsync(soa.data(), sys->d.d1n, soa.size() * sizeof(double),
@@ -1142,13 +1174,25 @@ dm_status dm_get_frames(dm_system *sys, double *d1, double *beta) {
   return DM_OK;
 }
 
-dm_status dm_set_frames(dm_system *sys, const double *d1, const double *beta) {
+dm_status dm_set_frames(dm_system *sys, const double *d1, const double *beta,
+                        int32_t is_device) {
   if (!sys) {
     set_error("dm_set_frames: NULL handle");
     return DM_ERR_INVALID_ARG;
   }
   const HostTopology &T = sys->T;
   cudaStream_t st = sys->stream;
+  const int ne = (int)T.n_edges;
+  if (is_device) {
+    if (d1 && ne > 0) {
+      k_frames_in<<<blocks(ne, 256), 256, 0, st>>>(ne, d1, sys->d.d1n);
+      DM_CK(cudaGetLastError());
+    }
+    if (beta && T.n_stencils > 0)
+      DM_CK(cudaMemcpyAsync(sys->d.beta_n, beta, T.n_stencils * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st));
+    return DM_OK;
+  }
   DM_CK(cudaStreamSynchronize(st));
   if (d1) {
     std::vector<double> soa(3 * T.n_edges);
@@ -1158,6 +1202,55 @@ dm_status dm_set_frames(dm_system *sys, const double *d1, const double *beta) {
   }
   if (beta)
     DM_CK(cudaMemcpy(sys->d.beta_n, beta, T.n_stencils * sizeof(double), cudaMemcpyHostToDevice));
+  return DM_OK;
+}
+
+dm_status dm_adjoint_frame_chain(dm_system *sys, const double *q_prev, const double *q,
+                                 const double *q_next, const double *gq, const double *gv,
+                                 const double *gv0, double *phibar, double *gq0) {
+  auto *s = static_cast<dm_system_ext *>(sys);
+  if (!s || !q || !q_next || !gq || !gv || !gv0 || !phibar || !gq0) {
+    set_error("dm_adjoint_frame_chain: NULL argument");
+    return DM_ERR_INVALID_ARG;
+  }
+  if (s->x.midpoint) {
+    set_error("dm_adjoint_frame_chain: backward Euler only");
+    return DM_ERR_INVALID_ARG;
+  }
+  const HostTopology &T = s->T;
+  auto &F = s->x.fchain;
+  if (!F.g) {
+    // layout tables: each edge's start node, each layout node's incident edges
+    std::vector<int32_t> edge_lay(T.n_edges), lay, ein, eout;
+    for (int r = 0; r < T.n_rods; ++r) {
+      const int N = T.npr[r];
+      for (int i = 0; i < N; ++i) {
+        const int64_t x = T.rod_layout0[r] + 4 * (int64_t)i;
+        const int64_t e = T.rod_edge0[r] + i;
+        lay.push_back((int32_t)x);
+        ein.push_back(i > 0 ? (int32_t)(e - 1) : -1);
+        eout.push_back(i + 1 < N ? (int32_t)e : -1);
+        if (i + 1 < N) edge_lay[e] = (int32_t)x;
+      }
+    }
+    F.nlnode = (int)lay.size();
+    DM_TRY(upload(s, &F.edge_lay, edge_lay));
+    DM_TRY(upload(s, &F.lnode_lay, lay));
+    DM_TRY(upload(s, &F.lnode_ein, ein));
+    DM_TRY(upload(s, &F.lnode_eout, eout));
+    DM_TRY(upload(s, &F.layout2dof, T.layout2dof));
+    DM_TRY(dalloc(s, &F.g, 3 * std::max<size_t>(1, (size_t)T.n_edges)));
+  }
+  FrameChainArgs fa{(int)T.n_edges, F.nlnode, s->p.dt, F.edge_lay, F.lnode_lay, F.lnode_ein,
+                    F.lnode_eout, F.layout2dof, s->d.fixed, q_prev, q, q_next, gq, gv, gv0,
+                    phibar, gq0, F.g};
+  cudaStream_t st = s->stream;
+  if (fa.ne > 0) {
+    k_frame_chain_edges<<<blocks(fa.ne, 128), 128, 0, st>>>(fa);
+    DM_CK(cudaGetLastError());
+    k_frame_chain_nodes<<<blocks(fa.nlnode, 128), 128, 0, st>>>(fa);
+    DM_CK(cudaGetLastError());
+  }
   return DM_OK;
 }
 

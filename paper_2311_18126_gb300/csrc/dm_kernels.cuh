@@ -231,7 +231,26 @@ struct StepArgs {
   unsigned long long *sys_res;
   const double *vnew;  // NULL: qdot = (q - q_n)/dt; else the staged qdot_{n+1}
 };
+// Frame chain of a rollout adjoint (dm_adjoint_frame_chain).
+struct FrameChainArgs {
+  int ne, nlnode;
+  double dt;
+  const int32_t *edge_lay;     // [Ne] layout index of each edge's start node x
+  const int32_t *lnode_lay, *lnode_ein, *lnode_eout;  // per layout node
+  const int32_t *layout2dof;
+  const uint8_t *fixed;        // DOF order
+  const double *q_prev, *q, *q_next, *gq, *gv, *gv0;
+  double *phibar, *gq0;
+  double *g;                   // [Ne][3] scratch
+};
+__global__ void k_frame_chain_edges(FrameChainArgs a);
+__global__ void k_frame_chain_nodes(FrameChainArgs a);
+__global__ void k_frames_out(int ne, const double *soa, double *aos);
+__global__ void k_frames_in(int ne, const double *aos, double *soa);
 __global__ void k_begin_step(StepArgs a);
+__global__ void k_project_lengths(int nsys, const int32_t *sys_kind, const int32_t *sys_dof0,
+                                  const int32_t *sys_ndof, const uint8_t *fixed,
+                                  const double *qn, double *q);
 __global__ void k_commit(StepArgs a);
 __global__ void k_restore(StepArgs a);
 __global__ void k_round_continue(int32_t *ctrl, int max_rounds, cudaGraphConditionalHandle h);

@@ -19,6 +19,96 @@ __global__ void k_begin_step(StepArgs a) {
   if (i < a.nd) a.q[i] = a.fixed[i] ? a.qn[i] : fma(a.dt, a.vn[i], a.qn[i]);
 }
 
+// Length-projected Newton guess (an option of the predictor): for each
+// single-rod system, every edge of the guess in q is rescaled to its length
+// in the committed state q_n, node positions rebuilt outward from the rod's
+// first node along the guess's edge directions; a node with a fixed position
+// DOF keeps its value.  The stiff stretching part of the guess's error goes,
+// the soft bending part stays.  The rebuilt positions are a prefix sum of
+// the rescaled edge vectors that restarts at node 0 and at every fixed node
+// (a segmented scan): one warp per system, 32 nodes per pass, the running
+// position carried from pass to pass (Eq. 1 layout: node k at DOFs 4k..4k+2).
+__global__ void k_project_lengths(int nsys, const int32_t *sys_kind, const int32_t *sys_dof0,
+                                  const int32_t *sys_ndof, const uint8_t *fixed,
+                                  const double *qn, double *q) {
+  const int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= nsys || sys_kind[s] != SOLVE_ROD_BAND) return;  // warp-uniform
+  const unsigned full = 0xffffffffu;
+  const int d0 = sys_dof0[s], N = (sys_ndof[s] + 1) / 4;
+  // the previous pass's last node: rebuilt position (c) and guess (p)
+  double cx = 0.0, cy = 0.0, cz = 0.0, px = 0.0, py = 0.0, pz = 0.0;
+  for (int base = 0; base < N; base += 32) {
+    const int k = base + lane;
+    const bool on = k < N;
+    const int o = d0 + 4 * k;
+    // guess of node k, and of node k - 1 from the lane before (or the carry)
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    if (on) {
+      gx = q[o];
+      gy = q[o + 1];
+      gz = q[o + 2];
+    }
+    double hx = __shfl_up_sync(full, gx, 1), hy = __shfl_up_sync(full, gy, 1),
+           hz = __shfl_up_sync(full, gz, 1);
+    if (lane == 0) {
+      hx = px;
+      hy = py;
+      hz = pz;
+    }
+    // a head restarts the sum at its own (guessed) position; any other node
+    // adds its rescaled edge vector from node k - 1
+    bool head = true, keep = true;
+    double vx = gx, vy = gy, vz = gz;
+    if (on) {
+      keep = k == 0 || fixed[o] || fixed[o + 1] || fixed[o + 2];
+      head = keep;
+      if (!keep) {
+        const double ex = gx - hx, ey = gy - hy, ez = gz - hz;
+        const double lx = qn[o] - qn[o - 4], ly = qn[o + 1] - qn[o - 3], lz = qn[o + 2] - qn[o - 2];
+        const double l2 = ex * ex + ey * ey + ez * ez;
+        const double sc = l2 > 0.0 ? sqrt((lx * lx + ly * ly + lz * lz) / l2) : 1.0;
+        vx = sc * ex;
+        vy = sc * ey;
+        vz = sc * ez;
+      }
+    }
+    // inclusive segmented scan over the pass
+    bool h = head;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const double ux = __shfl_up_sync(full, vx, d), uy = __shfl_up_sync(full, vy, d),
+                   uz = __shfl_up_sync(full, vz, d);
+      const bool uh = __shfl_up_sync(full, (int)h, d) != 0;
+      if (lane >= d) {
+        if (!h) {
+          vx += ux;
+          vy += uy;
+          vz += uz;
+        }
+        h = h || uh;
+      }
+    }
+    if (!h) {  // no restart in this pass up to here: continue from the carry
+      vx += cx;
+      vy += cy;
+      vz += cz;
+    }
+    if (on && !keep) {  // only this lane reads its node's q
+      q[o] = vx;
+      q[o + 1] = vy;
+      q[o + 2] = vz;
+    }
+    const int last = min(31, N - 1 - base);
+    cx = __shfl_sync(full, vx, last);
+    cy = __shfl_sync(full, vy, last);
+    cz = __shfl_sync(full, vz, last);
+    px = __shfl_sync(full, gx, last);
+    py = __shfl_sync(full, gy, last);
+    pz = __shfl_sync(full, gz, last);
+  }
+}
+
 // Commit the converged step: velocities, then q_n, the transported reference
 // directors and tangents of every edge, and the reference twist of every
 // stencil (all computed at the converged iterate).

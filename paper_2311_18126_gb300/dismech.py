@@ -41,9 +41,10 @@ class Params(C.Structure):
                 ("ground_z", C.c_double), ("delta", C.c_double), ("slip_nu", C.c_double),
                 ("self_contact", C.c_int32), ("pair_kc", C.c_double), ("pair_mu", C.c_double),
                 ("line_search", C.c_int32), ("stream", C.c_void_p), ("integrator", C.c_int32),
-                ("long_rod_dofs", C.c_int32)]
+                ("long_rod_dofs", C.c_int32), ("predictor", C.c_int32)]
 
 INTEGRATORS = {"be": 0, "midpoint": 1}
+PREDICTORS = {"extrapolate": 0, "projected": 1}
 
 
 class StepStats(C.Structure):
@@ -93,10 +94,12 @@ def load_library(path=LIB_PATH):
     lib.dm_get_state.restype = C.c_int
     lib.dm_set_state.argtypes = [H, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32]
     lib.dm_set_state.restype = C.c_int
-    lib.dm_get_frames.argtypes = [H, _dp, _dp]
+    lib.dm_get_frames.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int32]
     lib.dm_get_frames.restype = C.c_int
-    lib.dm_set_frames.argtypes = [H, _dp, _dp]
+    lib.dm_set_frames.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int32]
     lib.dm_set_frames.restype = C.c_int
+    lib.dm_adjoint_frame_chain.argtypes = [H] + [C.c_void_p] * 8
+    lib.dm_adjoint_frame_chain.restype = C.c_int
     lib.dm_state_size.argtypes = [H]
     lib.dm_state_size.restype = C.c_int64
     lib.dm_num_systems.argtypes = [H]
@@ -200,7 +203,9 @@ class System:
     dt, tol, max_iter, g, eta, ground, ground_z, delta, nu_slip,
     self_contact, pair_kc, pair_mu, line_search, integrator ("be" or
     "midpoint"), long_rod_dofs (rods with at least this many DOFs use the
-    partitioned band solve; 0 = 2048, negative = never), stream.
+    partitioned band solve; 0 = 2048, negative = never), predictor
+    ("extrapolate" or "projected": the guess rescaled to the committed edge
+    lengths on single rods), stream.
     """
 
     def __init__(self, desc, params):
@@ -275,6 +280,10 @@ class System:
             raise ValueError("integrator must be one of %s" % sorted(INTEGRATORS))
         p.integrator = INTEGRATORS[integ]
         p.long_rod_dofs = int(params.get("long_rod_dofs", 0))
+        pred = params.get("predictor", "extrapolate")
+        if pred not in PREDICTORS:
+            raise ValueError("predictor must be one of %s" % sorted(PREDICTORS))
+        p.predictor = PREDICTORS[pred]
         h = C.c_void_p()
         _check(lib.dm_create_system(C.byref(d), C.byref(p), C.byref(h)))
         self._h = h
@@ -400,22 +409,50 @@ class System:
         _check(self._lib.dm_debug_copy(self._h, name.encode(), _ptr(out, C.c_double), len(out)))
         return out
 
-    def get_frames(self):
+    def get_frames(self, d1=None, beta=None):
+        """(d1 [edges, 3], beta [stencils]): into torch CUDA tensors when
+        given (no synchronisation), else new numpy arrays."""
+        if d1 is not None and hasattr(d1, "data_ptr"):
+            _check(self._lib.dm_get_frames(self._h, _dev_ptr(d1), _dev_ptr(beta), 1))
+            return d1, beta
         d1 = np.zeros((self.n_edges, 3))
         beta = np.zeros(self.n_stencils)
-        _check(self._lib.dm_get_frames(self._h, _ptr(d1, C.c_double), _ptr(beta, C.c_double)))
+        _check(self._lib.dm_get_frames(self._h, d1.ctypes.data_as(C.c_void_p),
+                                       beta.ctypes.data_as(C.c_void_p), 0))
         return d1, beta
 
     def set_frames(self, d1, beta):
+        if hasattr(d1, "data_ptr"):
+            _check(self._lib.dm_set_frames(self._h, _dev_ptr(d1), _dev_ptr(beta), 1))
+            return
         d1 = np.ascontiguousarray(np.asarray(d1, np.float64))
         beta = np.ascontiguousarray(np.asarray(beta, np.float64))
-        _check(self._lib.dm_set_frames(self._h, _ptr(d1, C.c_double), _ptr(beta, C.c_double)))
+        _check(self._lib.dm_set_frames(self._h, d1.ctypes.data_as(C.c_void_p),
+                                       beta.ctypes.data_as(C.c_void_p), 0))
+
+    def adjoint_frame_chain(self, q_prev, q, q_next, gq, gv, gv0, phibar, gq0):
+        """One step of the rollout adjoint's frame chain (torch CUDA
+        float64 tensors; phibar and gq0 updated in place)."""
+        p = lambda t: _dev_ptr(t) if t is not None else None
+        _check(self._lib.dm_adjoint_frame_chain(self._h, p(q_prev), p(q), p(q_next), p(gq),
+                                                p(gv), p(gv0), p(phibar), p(gq0)))
 
 
     def step_adjoint(self, q_next, gq, gv):
         """Adjoint of the step from the current state (step n) to q_next:
         returns (dL/dkappabar [slots, 2], dL/dq_n, dL/dqdot_n) for the loss
-        gradients gq = dL/dq_{n+1}, gv = dL/dqdot_{n+1} (host numpy)."""
+        gradients gq = dL/dq_{n+1}, gv = dL/dqdot_{n+1} (host numpy, or
+        torch CUDA float64 tensors, returned as such)."""
+        if hasattr(q_next, "data_ptr"):
+            import torch
+            nslots = int(np.sum(self._npr - 2))
+            gk = torch.zeros((max(nslots, 1), 2), dtype=torch.float64, device=q_next.device)
+            gq0 = torch.empty_like(q_next)
+            gv0 = torch.empty_like(q_next)
+            _check(self._lib.dm_step_adjoint(self._h, _dev_ptr(q_next), _dev_ptr(gq),
+                                             _dev_ptr(gv), _dev_ptr(gk), _dev_ptr(gq0),
+                                             _dev_ptr(gv0), 1))
+            return gk[:nslots], gq0, gv0
         f = lambda a: np.ascontiguousarray(np.asarray(a, np.float64))
         q_next, gq, gv = f(q_next), f(gq), f(gv)
         nslots = int(np.sum(self._npr - 2))

@@ -252,3 +252,67 @@ def test_step_adjoint_coil_with_contact_matches_oracle_adjoint():
     for a, b in ((gk, ok), (gq, oq), (gv, ov)):
         scale = max(1.0, float(np.abs(b).max()))
         assert np.abs(a - b).max() <= 1e-8 * scale, np.abs(a - b).max() / scale
+
+
+def test_frame_chain_kernel_matches_a_numpy_restatement():
+    """dm_adjoint_frame_chain (the rollout adjoint's frame chain on the GPU)
+    against the same chain written out in NumPy: sigma at every free twist
+    angle, the carried frame adjoint, and the tangent term on the node
+    positions, on random states of three rods (one with fixed DOFs)."""
+    import torch
+    desc, params, _ = workloads.uneven_rods(n_rods=3, seed=9, n_min=6, n_max=9)
+    gpu = _gpu(desc, params)
+    npr = np.asarray(desc["nodes_per_rod"])
+    fixed = gpu.fixed_mask()
+    n = gpu.n_state
+    rng = np.random.default_rng(3)
+    q = gpu.get_state()[0]
+    pos = np.ones(n, bool)
+    off = 0
+    for N in npr:
+        pos[off + 4 * np.arange(N - 1) + 3] = False
+        off += 4 * N - 1
+    jitter = lambda s: q + s * rng.standard_normal(n) * pos
+    q_prev, q_next = jitter(0.01), jitter(0.01)
+    gq, gv, gv0 = rng.standard_normal((3, n))
+    phi0 = rng.standard_normal(int(np.sum(npr - 1)))
+    gq0 = rng.standard_normal(n)
+    dt = params["dt"]
+
+    # NumPy restatement
+    def tangents(x):
+        ts, ils, off = [], [], 0
+        for N in npr:
+            X = np.stack([x[off + 4 * i:off + 4 * i + 3] for i in range(N)])
+            e = X[1:] - X[:-1]
+            l = np.linalg.norm(e, axis=1)
+            ts.append(e / l[:, None])
+            ils.append(1.0 / l)
+            off += 4 * N - 1
+        return np.concatenate(ts), np.concatenate(ils)
+
+    hol = lambda a, b: np.cross(a, b) / (1.0 + np.sum(a * b, axis=1))[:, None]
+    th = np.concatenate([o + 4 * np.arange(N - 1) + 3
+                         for o, N in zip(np.concatenate([[0], np.cumsum(4 * npr - 1)])[:-1], npr)])
+    sigma = np.where(~fixed[th], -((gq[th] + gv[th] / dt) - gv0[th] / dt), 0.0)
+    phi = phi0 + sigma
+    t, il = tangents(q)
+    w = hol(t, tangents(q_next)[0]) + hol(tangents(q_prev)[0], t)
+    gt = -phi[:, None] * w
+    g = (gt - np.sum(gt * t, axis=1)[:, None] * t) * il[:, None]
+    want = gq0.copy()
+    off, e0 = 0, 0
+    for N in npr:
+        for i in range(N - 1):
+            want[off + 4 * (i + 1):off + 4 * (i + 1) + 3] += g[e0 + i]
+            want[off + 4 * i:off + 4 * i + 3] -= g[e0 + i]
+        e0 += N - 1
+        off += 4 * N - 1
+
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    tphi, tgq0 = T(phi0), T(gq0)
+    gpu.adjoint_frame_chain(T(q_prev), T(q), T(q_next), T(gq), T(gv), T(gv0), tphi, tgq0)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(tphi.cpu().numpy(), phi, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(tgq0.cpu().numpy(), want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+    assert np.any(fixed[th])  # the clamped first twist angles are exercised

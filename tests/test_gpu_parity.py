@@ -141,3 +141,34 @@ def test_full_batch_sampled_rods_in_bench_configuration():
     qs = np.concatenate([qg[off[r]:off[r + 1]] for r in rods])
     L = max(1.0, float(np.max(np.abs(sub["x0"]))))
     _assert_close(qs, qo, sub["nodes_per_rod"], L, 1e-9)
+
+
+@pytest.mark.parametrize("n_rods,seed", [(24, 2), (7, 5)])
+def test_uneven_rods_projected_predictor_per_step(n_rods, seed):
+    """The length-projected Newton guess on both sides: per step from
+    identical states at 1e-10, and no more Newton iterations than the
+    extrapolated guess takes from the same states."""
+    desc, params, kbar = workloads.uneven_rods(n_rods=n_rods, seed=seed)
+    pp = dict(params, predictor="projected")
+    gpu = _gpu(desc, pp)
+    ref = _gpu(desc, params)
+    ora = OracleSystems(desc, pp)
+    for s in (gpu, ref, ora):
+        s.set_natural_curvature(0, n_rods, kbar)
+    L = max(1.0, float(np.max(np.abs(desc["x0"]))))
+    its_p, its_e = 0, 0
+    for _ in range(4):
+        gpu.step(1)
+        ref.step(1)
+        st = ora.step(1)
+        assert all(x[0] == 0 for x in st), st
+        its_p += int(gpu.iterations.sum())
+        its_e += int(ref.iterations.sum())
+        qg, _ = gpu.get_state()
+        qo, vo = ora.get_state()
+        _assert_close(qg, qo, desc["nodes_per_rod"], L, 1e-10)
+        d1, beta = ora.get_frames()
+        for s in (gpu, ref):
+            s.set_state(qo, vo)
+            s.set_frames(d1, beta)
+    assert its_p <= its_e, (its_p, its_e)

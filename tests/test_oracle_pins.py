@@ -764,3 +764,43 @@ def test_mlp_gradient_error_scale_bounds_and_matches_positive_terms():
     _, gp = mlp.loss_and_grad(pp, Xp, Yp, 4, rounding=True)
     Sp = mlp.grad_abs_scale(pp, Xp, Yp, 4)
     np.testing.assert_allclose(gp, Sp, rtol=2.0 ** -6, atol=1e-30)
+
+
+def test_length_projected_guess_keeps_committed_lengths_and_the_root():
+    # the optional length-projected starting guess: every free edge takes
+    # its committed length along the extrapolated direction, fixed nodes
+    # stay, and Newton from it reaches the root Newton reaches from the
+    # extrapolation (within what the 1e-10 tolerance allows)
+    import workloads
+    desc, params, kbar = workloads.uneven_rods(n_rods=3, seed=4)
+    outs = []
+    for pred in ("extrapolate", "projected"):
+        o = OracleSystems(desc, dict(params, predictor=pred))
+        o.set_natural_curvature(0, 3, kbar)
+        for _ in range(3):
+            o.step(1)
+        outs.append(o)
+    o = outs[1]
+    for s in o.systems:
+        q_n = s.q
+        rng = np.random.default_rng(0)
+        guess = q_n + torch.as_tensor(0.01 * rng.standard_normal(s.n))
+        guess = torch.where(s.fixed, q_n, guess)
+        p = o._project_lengths(s, guess, q_n)
+        nd = s.node_dof
+        for k in range(1, len(nd)):
+            a, b = nd[k - 1], nd[k]
+            if bool(s.fixed[b:b + 3].any()):
+                assert torch.equal(p[b:b + 3], q_n[b:b + 3])
+                continue
+            ln = torch.linalg.vector_norm(q_n[b:b + 3] - q_n[a:a + 3])
+            e = p[b:b + 3] - p[a:a + 3]
+            assert float(torch.linalg.vector_norm(e)) == pytest.approx(float(ln), rel=1e-14)
+            g = guess[b:b + 3] - guess[a:a + 3]
+            cosang = float(der.dot(e, g) / (torch.linalg.vector_norm(e) * torch.linalg.vector_norm(g)))
+            assert cosang == pytest.approx(1.0, abs=1e-14)
+        # twist angles are left as guessed
+        assert torch.equal(p[torch.as_tensor(s.edge_dof)], guess[torch.as_tensor(s.edge_dof)])
+    qa, _ = outs[0].get_state()
+    qb, _ = outs[1].get_state()
+    assert np.max(np.abs(qa - qb)) <= 1e-8 * max(1.0, np.max(np.abs(qa)))
