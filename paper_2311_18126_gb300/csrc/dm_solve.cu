@@ -308,16 +308,27 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, d
   double rj = ncol > 0 ? rcp64(W[0]) : 1.0;
   bool bad = false;
   int b = 0, jr = 0;  // jr = j mod 11, the ring slot of row j
+  // running addresses (one element per column in the chain's direction) of
+  // row j + 11's diagonals p and p + 8 and right-hand side, of z_j, and of
+  // the lane's multipliers L[j + row][j]
+  const ptrdiff_t step = c.dir;
+  const double *pe0 = c.entry(11, p), *pe1 = c.entry(11, p + 8 < 11 ? p + 8 : p);
+  const double *pfz = c.f + c.base + c.orig(11);
+  double *pz = c.dq + c.base + c.orig(0);
+  double *pl0 = c.lstore(0, row0), *pl1 = c.lstore(0, row1);
   for (int j = 0; j < nwarp; ++j) {
     const bool act = j < ncol;
     // prefetch of row j + 11 (diagonals p and p + 8; the right-hand side)
     const bool more = act && j + 11 < n;
     double pre0 = 0.0, pre1 = 0.0, prz = 0.0;
     if (more) {
-      pre0 = *c.entry(j + 11, p);
-      if (p + 8 < 11) pre1 = *c.entry(j + 11, p + 8);
-      if (p == 3) prz = c.rhs(j + 11);
+      pre0 = *pe0;
+      if (p + 8 < 11) pre1 = *pe1;
+      if (p == 3) prz = -*pfz;
     }
+    pe0 += step;
+    pe1 += step;
+    pfz += step;
     double *Wb = W + 12 * b;
     const double zj = Wb[11];
     if (act && p == 0) {
@@ -327,8 +338,9 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, d
         bad = true;
       Dg[jr] = pre0;  // row j + 11 takes the slot (0 past the end)
       jr = jr == 10 ? 0 : jr + 1;
-      *c.zstore(j) = zj * rj;  // z_j = y_j / D_j for the backward pass
+      *pz = zj * rj;  // z_j = y_j / D_j for the backward pass
     }
+    pz += step;
     const double l0 = row0 > 0 ? Wb[loff0] * rj : 0.0;
     const double l1 = row1 > 0 ? Wb[loff1] * rj : 0.0;
     double uq[SOLVE_TASKS], dv[SOLVE_TASKS];
@@ -344,8 +356,8 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, d
     // no barrier here: every update target is read only by its own lane
     const double rnext = act ? rcp64(piv) : rj;
     if (act) {
-      if (st0 && j + row0 < n) *c.lstore(j, row0) = l0;
-      if (st1 && j + row1 < n) *c.lstore(j, row1) = l1;
+      if (st0 && j + row0 < n) *pl0 = l0;
+      if (st1 && j + row1 < n) *pl1 = l1;
 #pragma unroll
       for (int k = 0; k < SOLVE_TASKS; ++k)
         if (rsel[k] < 2) Wb[toff[k]] = fma(-(rsel[k] == 0 ? l0 : l1), uq[k], dv[k]);
@@ -375,6 +387,8 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, d
     } else {
       __syncwarp();
     }
+    pl0 += step;
+    pl1 += step;
     if (act) {
       b = wrap ? 0 : b + 1;
       rj = rnext;
