@@ -11,6 +11,11 @@ reference frames are held fixed.  J is the oracle's autograd Jacobian;
 lambda . df/dp is a vector-Jacobian product of the oracle's residual.
 Fixed DOFs keep q_{n+1} = q_n: they pass dL/dq_{n+1} through and get no
 velocity gradient.
+
+Implicit midpoint (the textbook rule, f = 2M/dt^2 (q_{n+1} - q_n - dt qdot_n)
+- F((q_n + q_{n+1})/2), qdot_{n+1} = 2 (q_{n+1} - q_n)/dt - qdot_n): the same
+with dL/dqdot_{n+1} entering as 2/dt, and the velocity update adding
+-2/dt dL/dqdot_{n+1} on q_n and -dL/dqdot_{n+1} on qdot_n.
 """
 import numpy as np
 import torch
@@ -24,10 +29,9 @@ def step_adjoint(osys, q_next, gq, gv):
     with the kappabar slots in the set_natural_curvature layout.  A joint
     node appears once per rod in the layout: its loss gradients are summed
     over the copies and its output gradients go to its first copy (zeros in
-    the others).  Backward Euler only."""
-    if osys.midpoint:
-        raise NotImplementedError("the oracle's step adjoint covers backward Euler")
+    the others).  Backward Euler or implicit midpoint."""
     dt = osys.dt
+    cv = 2.0 / dt if osys.midpoint else 1.0 / dt  # dqdot_{n+1} / dq_{n+1}
     maps = osys._rod_maps()
     n_slots = int(np.sum(osys.npr - 2))
     gk = np.zeros((n_slots, 2))
@@ -56,7 +60,7 @@ def step_adjoint(osys, q_next, gq, gv):
             g_v.index_add_(0, torch.as_tensor(idx), torch.as_tensor(gv[o:o + k], dtype=DT))
             seen[idx] = True
         _, _, J = osys.residual(s, q, s.q, s.v, need_jac=True)
-        gbar = torch.where(s.fixed, torch.zeros_like(g_q), g_q + g_v / dt)
+        gbar = torch.where(s.fixed, torch.zeros_like(g_q), g_q + cv * g_v)
         lam = torch.as_tensor(np.linalg.solve(J.numpy().T, gbar.numpy()))
         keep = (s.kbar1, s.kbar2)
         kb1 = s.kbar1.clone().requires_grad_(True)
@@ -73,8 +77,9 @@ def step_adjoint(osys, q_next, gq, gv):
         z = torch.zeros(s.n, dtype=DT)
         dqn = z if dqn is None else dqn
         dvn = z if dvn is None else dvn
-        a_q0 = torch.where(s.fixed, g_q, -dqn - g_v / dt)
-        a_v0 = torch.where(s.fixed, torch.zeros_like(g_v), -dvn)
+        a_q0 = torch.where(s.fixed, g_q, -dqn - cv * g_v)
+        a_v0 = torch.where(s.fixed, torch.zeros_like(g_v),
+                           -dvn - g_v if osys.midpoint else -dvn)
         done = np.zeros(s.n, bool)
         for (o, idx) in parts:
             k = len(idx)

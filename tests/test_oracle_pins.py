@@ -553,17 +553,18 @@ def test_edge_pair_friction_closed_form():
     assert float(torch.abs(F0).max()) < 1e-20
 
 
-def test_step_adjoint_matches_central_differences():
+@pytest.mark.parametrize("integ", ["be", "midpoint"])
+def test_step_adjoint_matches_central_differences(integ):
     """The oracle's one-step adjoint (implicit function theorem) against
     central differences of the oracle's own step, for natural curvatures and
     the initial state, the committed frames (directors, reference twist and
     tangents) held fixed: every evaluation restarts from the same step-n
-    frames."""
+    frames.  Backward Euler and implicit midpoint."""
     import workloads
     from oracle import OracleSystems
     from oracle.adjoint import step_adjoint
     desc, params = workloads.cantilever(N=10)
-    o = OracleSystems(desc, params)
+    o = OracleSystems(desc, dict(params, integrator=integ))
     rng = np.random.default_rng(4)
     kb0 = rng.uniform(-0.02, 0.02, size=(8, 2))
     o.set_natural_curvature(0, 1, kb0)
