@@ -44,10 +44,13 @@ FP64_FLOPS_PER_UNIT = {
     "residual_rows": None,
     "jacobian_band_rows": None,
     "band_ldlt_solve": None,
+    "bend_twist_fused": None,
+    "residual_jacobian_rows": None,
 }
 UNIT_NAME = {"bend_twist_gradient": "stencil", "bend_twist_hessian": "stencil",
              "edge_frames_stretch": "edge", "residual_rows": "DOF row",
              "jacobian_band_rows": "DOF row", "band_ldlt_solve": "DOF",
+             "bend_twist_fused": "stencil", "residual_jacobian_rows": "DOF row",
              "step_begin": "DOF", "step_commit": "DOF"}
 
 
@@ -300,8 +303,7 @@ def run_ours(args):
         # without numerical damping plain Newton diverges on stiff rods of
         # this batch (the oracle likewise, e.g. rod 379 at its 5th step)
         params["line_search"] = True
-    else:
-        params["predictor"] = args.predictor
+    params["predictor"] = args.predictor
     R = len(desc["nodes_per_rod"])
     sysm = System(desc, params)
     sysm.set_natural_curvature(0, R, kbar)

@@ -142,7 +142,9 @@ typedef struct dm_params {
                            rebuilt outward from the rod's first node along
                            the guess's edge directions (nodes with a fixed
                            position DOF keep theirs), also applied to a
-                           learned guess.  Backward Euler only.             */
+                           learned guess.  Implicit midpoint: applied to
+                           the step's end guess 2y - q_n, the midpoint guess
+                           y rebuilt as its mean with q_n.                  */
 } dm_params;
 
 /* Optional per-call statistics (caller-owned arrays may be NULL). */
@@ -388,7 +390,11 @@ dm_status dm_ws_column_stats(const float *data, int64_t rows, int32_t cols, floa
  * both ends, are rejected (DM_ERR_INVALID_ARG); the ground friction
  * force's dependence on x_n enters
  * dL/dq_n; fixed DOFs pass dL/dq_{n+1} through and get no velocity
- * gradient.  Synchronises the stream; the state of step n is left in
+ * gradient.  Implicit midpoint (solved as backward Euler over h = dt/2 in
+ * y = (q_n + q_{n+1})/2): the same adjoint over h at y with the loss
+ * gradients doubled (q_{n+1} = 2y - q_n, qdot_{n+1} = 2 (y - q_n)/h -
+ * qdot_n), then dL/dq_n -= dL/dq_{n+1} and, on free DOFs, dL/dqdot_n -=
+ * dL/dqdot_{n+1}.  Synchronises the stream; the state of step n is left in
  * place. */
 dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq,
                           const double *gv, double *gkbar, double *gq0, double *gv0,
@@ -412,8 +418,12 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
  * dm_get_state layout; phibar is [sum (N_r-1)] (descriptor edge order, in:
  * the value carried from the later steps, zeros at the end of the rollout;
  * out: the value to carry to the earlier ones); gq0 (dm_step_adjoint's
- * dL/dq_n output) is updated in place.  All device pointers; ordered on the
- * system's stream without synchronisation.  Backward Euler only. */
+ * dL/dq_n output) is updated in place.  Implicit midpoint, whose step energy
+ * sees step n's frames transported to the tangents t_y of y = (q + q_next)/2:
+ * sigma_e = -(2 gq + (gv - gv0)/h) with h = dt/2, and the source term of the
+ * transport out of t_e splits into phibar_e(in) w(t_e, t_e') +
+ * sigma_e w(t_e, t_y).  All device pointers; ordered on the system's stream
+ * without synchronisation. */
 dm_status dm_adjoint_frame_chain(dm_system *sys, const double *q_prev, const double *q,
                                  const double *q_next, const double *gq, const double *gv,
                                  const double *gv0, double *phibar, double *gq0);
@@ -423,9 +433,9 @@ dm_status dm_adjoint_frame_chain(dm_system *sys, const double *q_prev, const dou
  * iterate, summed over the systems (0 without edge-edge contact, -1 on a
  * CUDA error).  Synchronises the stream.  Contact acts within single rods
  * and within contact groups of rods (dm_system_desc.contact_groups; no
- * joints, no ground contact); friction at the closest points (Eq. 12-13)
+ * joints), on the ground or not; friction at the closest points (Eq. 12-13)
  * when pair_mu > 0, with the slip tolerance slip_nu.  dm_create_system
- * rejects other combinations with DM_ERR_INVALID_ARG. */
+ * rejects rods with joints under edge-edge contact (DM_ERR_INVALID_ARG). */
 int64_t dm_contact_pairs(dm_system *sys);
 
 /* Per-kernel profile of dm_step calls made while profiling is on: CUDA-event
@@ -435,9 +445,14 @@ int64_t dm_contact_pairs(dm_system *sys);
  * 3 banded solve, 4 step begin, 5 step commit, 6 ground contact/friction,
  * 7 general residual rows, 8 general assembly, 9 limb/Schur solve,
  * 10 learned warm start (features + network + apply), 11 edge-edge contact
- * (broadphase, pairs, derivatives), 12 contact-system LU.  Profiling adds two event
- * records per launch; it is off by default. */
-#define DM_NUM_KERNELS 16
+ * (broadphase, pairs, derivatives), 12 contact-system LU, 13 bend-twist
+ * Hessians (the Jacobian pass of a round), 14 Jacobian band rows, 15
+ * bend-twist gradients and Hessians in one pass (the first round of a step;
+ * every round of batches with rod networks), 16 residual and band rows in
+ * one pass.  Ids 1 and 2 are then the residual pass (reference twist and
+ * gradients; residual rows).  Profiling adds two event records per launch;
+ * it is off by default. */
+#define DM_NUM_KERNELS 17
 typedef struct dm_profile {
   int64_t launches[DM_NUM_KERNELS];
   int64_t units[DM_NUM_KERNELS];

@@ -21,7 +21,10 @@ for the source and the target of a transport).  With Phi_n the committed
 frame angles of step n:  Phibar_n = Phibar_{n+1} + sigma_{n+1} and
 dL/dt_n = -Phibar_n [w(t_n, t_{n+1}) + w(t_{n-1}, t_n)], carried to the
 node positions through t = e/|e|.  The directors of the initial state are
-taken as transported along with its tangents.
+taken as transported along with its tangents.  Implicit midpoint takes each
+step's energy at (q_n + q_{n+1})/2, with the frames transported to its
+tangents; the library's frame chain splits the transport out of t_n
+accordingly (dm_adjoint_frame_chain).
 """
 import numpy as np
 import torch

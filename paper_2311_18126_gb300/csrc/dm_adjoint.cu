@@ -45,6 +45,25 @@ __global__ void k_adj_state(AdjArgs a) {
   a.gv0[i] = a.lam[i] * m * idt;
 }
 
+__global__ void k_adj_midpoint_in(int nd, const uint8_t *fixed, const double *qn, double *q,
+                                  double *gq, double *gv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  q[i] = fixed[i] ? qn[i] : 0.5 * (qn[i] + q[i]);
+  gq[i] *= 2.0;
+  gv[i] *= 2.0;
+}
+
+// gq2, gv2: the doubled loss gradients.  Fixed DOFs: the core passed 2 gq
+// through, the step keeps them (gq0 = gq) and gives them no velocity.
+__global__ void k_adj_midpoint_out(int nd, const uint8_t *fixed, const double *gq2,
+                                   const double *gv2, double *gq0, double *gv0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  gq0[i] -= 0.5 * gq2[i];
+  if (!fixed[i]) gv0[i] -= 0.5 * gv2[i];
+}
+
 // dst = transposed condensation-path storage: per limb the band
 // B'[p][k + 10] = B[p + k][10 - k], C' = R^T, R' = C^T (one thread per entry)
 __global__ void k_gen_transpose(SolveGenArgs a, const double *src, double *dst) {
@@ -115,6 +134,14 @@ __global__ void k_adj_kbar(AdjArgs a) {
 // triangle.  Carried backwards: Phibar_n = Phibar_{n+1} + sigma and
 // dL/dt_n = -Phibar_n [w(t_n, t_{n+1}) + w(t_{n-1}, t_n)], taken to the
 // node positions through t = e/|e|.  All vectors in the state layout.
+//
+// Implicit midpoint: the step's energy is taken at y = (q_n + q_{n+1})/2,
+// its frames transported from step n's to the tangents t_y of y, while the
+// committed frames of step n+1 are transported to t_{n+1}.  In the outputs
+// of the midpoint step adjoint (core over h = dt/2 with doubled gradients)
+// sigma = -(2 gq + (gv - gv0)/h), and the transport out of t_n splits:
+// dL/dt_n = -[Phibar_{n+1} w(t_n, t_{n+1}) + sigma w(t_n, t_y)
+//             + Phibar_n w(t_{n-1}, t_n)].
 
 __device__ __forceinline__ void unit_edge(const double *q, int a, double t[3], double &il) {
   const double ex = q[a + 4] - q[a], ey = q[a + 5] - q[a + 1], ez = q[a + 6] - q[a + 2];
@@ -137,20 +164,41 @@ __global__ void k_frame_chain_edges(FrameChainArgs a) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.ne) return;
   const int x0 = a.edge_lay[e], th = x0 + 3;
-  const double sigma =
-      a.fixed[a.layout2dof[th]] ? 0.0 : -((a.gq[th] + a.gv[th] / a.dt) - a.gv0[th] / a.dt);
-  const double phi = a.phibar[e] + sigma;
+  double sigma = 0.0;
+  if (!a.fixed[a.layout2dof[th]])
+    sigma = a.midpoint ? -(2.0 * a.gq[th] + (a.gv[th] - a.gv0[th]) / a.dt)
+                       : -((a.gq[th] + a.gv[th] / a.dt) - a.gv0[th] / a.dt);
+  const double phi1 = a.phibar[e], phi = phi1 + sigma;
   a.phibar[e] = phi;
   double t[3], t1[3], il, il1, w[3] = {0.0, 0.0, 0.0};
   unit_edge(a.q, x0, t, il);
   unit_edge(a.q_next, x0, t1, il1);
-  add_holonomy(t, t1, w);
   if (a.q_prev) {
     double tp[3], ilp;
     unit_edge(a.q_prev, x0, tp, ilp);
     add_holonomy(tp, t, w);
   }
-  const double gt[3] = {-phi * w[0], -phi * w[1], -phi * w[2]};
+  double gt[3];
+  if (a.midpoint) {
+    double w1[3] = {0.0, 0.0, 0.0}, wy[3] = {0.0, 0.0, 0.0}, ty[3];
+    add_holonomy(t, t1, w1);
+    double ey[3], ly = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ey[c] = 0.5 * ((a.q[x0 + 4 + c] + a.q_next[x0 + 4 + c]) - (a.q[x0 + c] + a.q_next[x0 + c]));
+      ly += ey[c] * ey[c];
+    }
+    ly = 1.0 / sqrt(ly);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ty[c] = ey[c] * ly;
+    add_holonomy(t, ty, wy);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gt[c] = -(phi * w[c] + phi1 * w1[c] + sigma * wy[c]);
+  } else {
+    add_holonomy(t, t1, w);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gt[c] = -phi * w[c];
+  }
   const double tg = gt[0] * t[0] + gt[1] * t[1] + gt[2] * t[2];
 #pragma unroll
   for (int c = 0; c < 3; ++c) a.g[3 * e + c] = (gt[c] - tg * t[c]) * il;

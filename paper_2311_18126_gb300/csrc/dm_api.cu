@@ -91,13 +91,15 @@ __global__ void k_scatter_kbar(int n, const int32_t *slot2st, int slot0, int ns,
 enum {
   K_EDGE = 0, K_STENCIL = 1, K_ROWS = 2, K_SOLVE = 3, K_BEGIN = 4, K_COMMIT = 5,
   K_NODES = 6, K_ROWS_GEN = 7, K_ASM_GEN = 8, K_SOLVE_GEN = 9, K_WARM = 10,
-  K_CONTACT = 11, K_SOLVE_CONTACT = 12, K_HESS = 13, K_BAND = 14
+  K_CONTACT = 11, K_SOLVE_CONTACT = 12, K_HESS = 13, K_BAND = 14, K_FUSED = 15,
+  K_ROWS_FUSED = 16
 };
 const char *kKernelNames[DM_NUM_KERNELS] = {
     "edge_frames_stretch", "bend_twist_gradient", "residual_rows", "band_ldlt_solve",
     "step_begin",          "step_commit",        "ground_contact_friction", "residual_rows_general",
     "assemble_general",    "limb_schur_solve",   "learned_warm_start",
-    "edge_contact_pairs",  "contact_band_lu",    "bend_twist_hessian", "jacobian_band_rows"};
+    "edge_contact_pairs",  "contact_band_lu",    "bend_twist_hessian", "jacobian_band_rows",
+    "bend_twist_fused",    "residual_jacobian_rows"};
 
 struct Extra {
   bool prof = false;
@@ -142,6 +144,7 @@ struct Extra {
   int n_fast = 0, n_slow = 0;   // general systems on the condensation / Schur path
   size_t border_smem = 0;
   int limb_nmax = 0, wpb_factor = 1, wpb_back = 1;  // limb kernels: rows, warps per block
+  int asm_chunks = 0;  // assembly blocks per system (the largest system's targets)
   size_t smem_factor = 0, smem_back = 0;
   int solve_blocks = 1;
   size_t solve_smem = 0;
@@ -158,6 +161,8 @@ struct Extra {
   bool graphs = true;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t round_graph = nullptr;
+  cudaGraphExec_t first_graph = nullptr;            // the fused first round of a step
+  int64_t first_launches[DM_NUM_KERNELS] = {};
   bool graph_ws = false;  // learned warm start on when the graph was captured
   bool midpoint = false;  // implicit midpoint (p.dt holds dt/2)
   LongRods *longr = nullptr;  // single rods on the partitioned solve
@@ -208,17 +213,14 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     set_error("integrator must be 0 (backward Euler) or 1 (implicit midpoint)");
     return DM_ERR_INVALID_ARG;
   }
-  if (prm->predictor != 0 && (prm->predictor != 1 || prm->integrator != 0)) {
-    set_error("predictor must be 0, or 1 (length-projected) with backward Euler");
+  if (prm->predictor != 0 && prm->predictor != 1) {
+    set_error("predictor must be 0 (extrapolated) or 1 (length-projected)");
     return DM_ERR_INVALID_ARG;
   }
   if (!build_topology(desc, prm, T)) return DM_ERR_INVALID_ARG;
   if (prm->self_contact) {
-    // edge-edge contact within single rods (no joints, no ground)
-    if (prm->ground) {
-      set_error("edge-edge contact together with ground contact is not supported");
-      return DM_ERR_INVALID_ARG;
-    }
+    // edge-edge contact within single rods and contact groups (no joints),
+    // on the ground or not
     if (prm->pair_mu < 0.0 || (prm->pair_mu > 0.0 && !(prm->slip_nu > 0.0))) {
       set_error("edge-edge friction needs pair_mu >= 0 and slip_nu > 0");
       return DM_ERR_INVALID_ARG;
@@ -416,7 +418,8 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
       dc[i] = T.dof_fixed[i] ? 1.0 : T.dof_mass[i] / (prm->dt * prm->dt) + damp[i];
     DM_TRY(upload(s, &d.dconst, dc));
   }
-  if (T.any_general) {
+  if (T.any_general || T.ground) {
+    // node tables and node terms (ground contact and friction, k_nodes)
     std::vector<int32_t> ndof_arr(T.n_nodes);
     for (int64_t v = 0; v < T.n_nodes; ++v) ndof_arr[v] = T.node_dof[v];
     DM_TRY(upload(s, &d.node_dof_arr, ndof_arr));
@@ -426,7 +429,12 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     DM_TRY(upload(s, &d.node_kc, T.node_kc));
     DM_TRY(dalloc(s, &d.nt, 12 * T.n_nodes));
     DM_CK(cudaMemset(d.nt, 0, 12 * T.n_nodes * sizeof(double)));
+  }
+  if (T.any_general) {
     DM_TRY(dalloc(s, &d.gen, T.gen_doubles));
+    // entries no assembly targets stay zero: the condensation path factors
+    // out of place (the other path's systems are cleared every round)
+    DM_CK(cudaMemset(d.gen, 0, std::max<int64_t>(T.gen_doubles, 1) * sizeof(double)));
     DM_TRY(upload(s, &d.gen_sys, T.gen_sys));
     DM_TRY(upload(s, &d.gs_limb0, T.gs_limb0));
     DM_TRY(upload(s, &d.gs_nlimb, T.gs_nlimb));
@@ -436,6 +444,8 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     DM_TRY(upload(s, &d.gs_rB, T.gs_rB));
     DM_TRY(upload(s, &d.gs_S, T.gs_S));
     DM_TRY(upload(s, &d.gs_xB, T.gs_xB));
+    DM_TRY(upload(s, &d.gs_mat0, T.gs_mat0));
+    DM_TRY(upload(s, &d.gs_mat1, T.gs_mat1));
     DM_TRY(upload(s, &d.lb_dof0, T.lb_dof0));
     DM_TRY(upload(s, &d.lb_n, T.lb_n));
     DM_TRY(upload(s, &d.lb_ncr, T.lb_ncr));
@@ -462,7 +472,7 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
       if (T.gs_fast[w]) {
         s->x.n_fast++;
         s->x.border_smem = std::max<size_t>(
-            s->x.border_smem, (size_t)(T.gs_nB[w] * T.gs_nB[w] + T.gs_nB[w]) * sizeof(double));
+            s->x.border_smem, (size_t)(T.gs_nB[w] * (T.gs_nB[w] + 3)) * sizeof(double));
       } else {
         s->x.n_slow++;
       }
@@ -489,6 +499,10 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
     }
     DM_TRY(upload(s, &d.asm_target, T.asm_target));
     DM_TRY(upload(s, &d.asm_sys, T.asm_sys));
+    DM_TRY(upload(s, &d.asm_t0, T.asm_t0));
+    for (size_t w = 0; w + 1 < T.asm_t0.size(); ++w)
+      s->x.asm_chunks = std::max(s->x.asm_chunks, (T.asm_t0[w + 1] - T.asm_t0[w] + kAsmPerBlock - 1) /
+                                                      kAsmPerBlock);
     DM_TRY(upload(s, &d.asm_ptr, T.asm_ptr));
     DM_TRY(upload(s, &d.asm_src, T.asm_src));
     DM_TRY(upload(s, &d.gat_ptr, T.gat_ptr));
@@ -625,6 +639,7 @@ void dm_destroy(dm_system *sys) {
     if (sx->x.ev[k]) cudaEventDestroy(sx->x.ev[k]);
   if (sys->h_ctrl) cudaFreeHost(sys->h_ctrl);
   if (sx->x.round_graph) cudaGraphExecDestroy(sx->x.round_graph);
+  if (sx->x.first_graph) cudaGraphExecDestroy(sx->x.first_graph);
   long_rods_free(sx->x.longr);
   if (sx->x.cap_stream) cudaStreamDestroy(sx->x.cap_stream);
   dm::ws_free(sys->ws);
@@ -698,6 +713,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     ca.bucket_edges = c.bucket_edges; ca.pairs = c.pairs; ca.npairs = c.npairs;
     ca.fc = c.fc; ca.dense = c.dense;
     ca.n_contact = c.n_contact; ca.cgo = c.cgo; ca.cbad = c.cbad;
+    ca.nn = (int)T.n_nodes;
   }
   // the Jacobian passes test convergence as the solvers do
   const int32_t *ls_act = s->prm.line_search ? s->x.ls_action : nullptr;
@@ -735,7 +751,8 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   rg.nt = T.ground ? d.nt : nullptr; rg.f = d.f; rg.sys_res = d.sys_res;
   const bool ls_on = s->prm.line_search != 0;
   AsmArgs aa{(int)T.asm_target.size(), d.asm_target, d.asm_ptr, d.asm_src, d.sh, d.es, d.nt,
-             d.dconst, d.gen, d.asm_sys, d.sys_active, ls_on ? s->x.ls_action : nullptr};
+             d.dconst, d.gen, d.asm_sys, d.sys_active, ls_on ? s->x.ls_action : nullptr,
+             (int)T.gen_sys.size(), d.gen_sys, d.asm_t0, d.gs_mat0, d.gs_mat1};
   SolveGenArgs ga{};
   ga.ngen = (int)T.gen_sys.size(); ga.max_iter = s->p.max_iter; ga.tol = s->p.tol;
   ga.gen_sys = d.gen_sys; ga.gs_limb0 = d.gs_limb0; ga.gs_nlimb = d.gs_nlimb; ga.gs_nB = d.gs_nB;
@@ -773,10 +790,15 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     stats->max_iterations = 0;
   }
   std::vector<int32_t> iters;
-  // residual and Jacobian passes apart, except with rod networks
+  // residual and Jacobian passes apart, except with rod networks; the first
+  // round of a step, whose guess essentially never meets the tolerance, runs
+  // the fused passes (without a learned guess, whose trial round may be
+  // rejected)
   const bool split = !gen_on;
+  const bool fuse_first = split && !ws_on;
   // One Newton round: every phase's launches, in stream order on rs.
-  auto round = [&](cudaStream_t rs, int it) -> dm_status {
+  auto round = [&](cudaStream_t rs, int it, bool first) -> dm_status {
+    const bool sp = split && !first;
     k_reset_res<<<blocks(S, 256), 256, 0, rs>>>(0, S, d.sys_active, d.sys_res);
     s->x.launches[K_BEGIN]++;
     DM_CK(cudaMemsetAsync(d.ctrl, 0, sizeof(int32_t), rs));
@@ -797,10 +819,14 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     // that iterate on, for which the split would only add work.
     const int st_tb = s->x.tune.stencil_threads;
     const int st_grid = blocks(ns, (int64_t)st_tb * s->x.tune.stencil_per_thread);
-    if (ns > 0) {
+    if (ns > 0 && sp) {
       Timed t(s, K_STENCIL, rs);
-      if (split) k_stencil_grad<<<st_grid, st_tb, 0, rs>>>(ka);
-      else k_stencil<<<st_grid, st_tb, 0, rs>>>(ka);
+      k_stencil_grad<<<st_grid, st_tb, 0, rs>>>(ka);
+    } else if (ns > 0) {
+      Timed t(s, K_FUSED, rs);
+      StencilArgs kf = ka;
+      kf.units = s->x.prof ? s->x.d_units + K_FUSED : nullptr;
+      k_stencil<<<st_grid, st_tb, 0, rs>>>(kf);
     }
     if (contact_on) {
       Timed t(s, K_CONTACT, rs);
@@ -815,13 +841,19 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       k_cc_fill<<<blocks(ne, 256), 256, 0, rs>>>(ca);
       k_cc_pairs<<<blocks(ne, 128), 128, 0, rs>>>(ca);
       k_cc_terms<<<blocks(c.pair_cap, 64), 64, 0, rs>>>(ca);
+      if (T.ground) k_cc_ground<<<blocks(nn, 128), 128, 0, rs>>>(ca, na.node_dof, d.node_sys, d.nt);
     }
     const bool rows_on = rod_on || contact_on || long_on;
-    if (rows_on) {
+    if (rows_on && sp) {
       Timed t(s, K_ROWS, rs);
       const int tb = s->x.tune.rows_threads;
-      if (split) k_rows_rod_res<<<blocks(nd, tb), tb, 0, rs>>>(ra);
-      else k_rows_rod<<<blocks(nd, tb), tb, 0, rs>>>(ra);
+      k_rows_rod_res<<<blocks(nd, tb), tb, 0, rs>>>(ra);
+    } else if (rows_on) {
+      Timed t(s, K_ROWS_FUSED, rs);
+      const int tb = s->x.tune.rows_threads;
+      RowArgs rf = ra;
+      rf.units = s->x.prof ? s->x.d_units + K_ROWS_FUSED : nullptr;
+      k_rows_rod<<<blocks(nd, tb), tb, 0, rs>>>(rf);
     }
     if (gen_on) {
       Timed t(s, K_ROWS_GEN, rs);
@@ -833,13 +865,13 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       k_ls_apply<<<blocks(nd, 256), 256, 0, rs>>>(la);
       if (ws_trial && it == 0) DM_CK(ws_inject(s, rs, s->x.ls_action, s->x.ls_trial));
     }
-    if (split && ns > 0) {
+    if (sp && ns > 0) {
       Timed t(s, K_HESS, rs);
       StencilArgs kh = ka;
       kh.units = s->x.prof ? s->x.d_units + K_HESS : nullptr;
       k_stencil_hess<<<st_grid, st_tb, 0, rs>>>(kh);
     }
-    if (split && rows_on) {
+    if (sp && rows_on) {
       Timed t(s, K_BAND, rs);
       const int tb = s->x.tune.rows_threads;
       RowArgs rb = ra;
@@ -876,10 +908,11 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       k_cc_subst<<<nc, 1024, 0, rs>>>(ca, va);
     }
     if (gen_on) {
-      DM_CK(cudaMemsetAsync(d.gen, 0, T.gen_doubles * sizeof(double), rs));
-      if (aa.ntarget > 0) {
+      {
         Timed t(s, K_ASM_GEN, rs);
-        k_assemble_gen<<<blocks(aa.ntarget, 256), 256, 0, rs>>>(aa);
+        if (s->x.n_slow) k_gen_clear_slow<<<aa.ngen, 256, 0, rs>>>(aa, d.gs_fast);
+        if (s->x.asm_chunks > 0)
+          k_assemble_gen<<<dim3(aa.ngen, s->x.asm_chunks), 256, 0, rs>>>(aa);
       }
       {
         Timed t(s, K_SOLVE_GEN, rs);
@@ -889,7 +922,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
           const size_t sb = s->x.smem_back / s->x.wpb_back_max * wb;
           if (ga.nlimb)
             k_gen_limb_factor<<<(ga.nlimb + wf - 1) / wf, 32 * wf, sf, rs>>>(ga);
-          k_gen_border<<<ga.ngen, 32, s->x.border_smem, rs>>>(ga);
+          k_gen_border<<<ga.ngen, kGenBorderThreads, s->x.border_smem, rs>>>(ga);
           if (ga.nlimb)
             k_gen_limb_back<<<(ga.nlimb + wb - 1) / wb, 32 * wb, sb, rs>>>(ga);
         }
@@ -909,6 +942,8 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   if (s->x.round_graph && s->x.graph_ws != ws_on) {  // the round's kernels changed
     cudaGraphExecDestroy(s->x.round_graph);
     s->x.round_graph = nullptr;
+    if (s->x.first_graph) cudaGraphExecDestroy(s->x.first_graph);
+    s->x.first_graph = nullptr;
   }
   if (graph_mode && !s->x.round_graph) {
     s->x.graph_ws = ws_on;
@@ -936,7 +971,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     }
     int64_t before[DM_NUM_KERNELS];
     std::copy(s->x.launches, s->x.launches + DM_NUM_KERNELS, before);
-    dm_status rst = round(s->x.cap_stream, 1);
+    dm_status rst = round(s->x.cap_stream, 1, false);
     if (rst == DM_OK) k_round_continue<<<1, 32, 0, s->x.cap_stream>>>(d.ctrl, max_rounds, h);
     cudaGraph_t body = nullptr;
     e = cudaStreamEndCapture(s->x.cap_stream, &body);
@@ -954,6 +989,33 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       return DM_ERR_CUDA;
     }
   }
+  if (graph_mode && fuse_first && !s->x.first_graph) {
+    // the first round (fused passes), counted as a round of the step
+    cudaError_t e = cudaStreamBeginCapture(s->x.cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      set_error(std::string("CUDA: first-round graph: ") + cudaGetErrorString(e));
+      return DM_ERR_CUDA;
+    }
+    int64_t before[DM_NUM_KERNELS];
+    std::copy(s->x.launches, s->x.launches + DM_NUM_KERNELS, before);
+    dm_status rst = round(s->x.cap_stream, 0, true);
+    if (rst == DM_OK) k_round_count<<<1, 32, 0, s->x.cap_stream>>>(d.ctrl);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s->x.cap_stream, &g);
+    for (int k = 0; k < DM_NUM_KERNELS; ++k) {
+      s->x.first_launches[k] = s->x.launches[k] - before[k];
+      s->x.launches[k] = before[k];
+    }
+    s->x.first_launches[K_BEGIN] += 1;  // k_round_count
+    if (rst == DM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&s->x.first_graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (rst != DM_OK) return rst;
+    if (e != cudaSuccess) {
+      s->x.first_graph = nullptr;
+      set_error(std::string("CUDA: first-round graph: ") + cudaGetErrorString(e));
+      return DM_ERR_CUDA;
+    }
+  }
   for (int step = 0; step < nsteps; ++step) {
     int32_t init[8] = {0, 0, INT_MAX, 0, 0, 0, 0, 0};  // active, failed, first failed, queue, rounds
     DM_CK(cudaMemcpyAsync(d.ctrl, init, sizeof(init), cudaMemcpyHostToDevice, st));
@@ -967,7 +1029,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     }
     if (s->prm.predictor == 1) {
       k_project_lengths<<<blocks((int64_t)S * 32, 128), 128, 0, st>>>(
-          S, s->x.d_sys_kind, d.sys_dof0, d.sys_ndof, d.fixed, d.qn, d.q);
+          S, s->x.d_sys_kind, d.sys_dof0, d.sys_ndof, d.fixed, d.qn, d.q, s->x.midpoint ? 1 : 0);
       s->x.launches[K_BEGIN]++;
     }
     if (ls_on) {
@@ -978,15 +1040,18 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     if (graph_mode) {
       // an extra round after convergence (the graph body runs at least once)
       // finds no active system and changes nothing
-      if (ws_trial) DM_TRY(round(st, 0));
+      if (ws_trial) DM_TRY(round(st, 0, false));
+      if (fuse_first) DM_CK(cudaGraphLaunch(s->x.first_graph, st));
       DM_CK(cudaGraphLaunch(s->x.round_graph, st));
       DM_CK(cudaMemcpyAsync(s->h_ctrl, d.ctrl, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
       DM_CK(cudaStreamSynchronize(st));
+      const int64_t loop_rounds = s->h_ctrl[4] - (fuse_first ? 1 : 0);
       for (int k = 0; k < DM_NUM_KERNELS; ++k)
-        s->x.launches[k] += (int64_t)s->h_ctrl[4] * s->x.round_launches[k];
+        s->x.launches[k] += loop_rounds * s->x.round_launches[k] +
+                            (fuse_first ? s->x.first_launches[k] : 0);
     } else {
       for (int it = 0; it < max_rounds; ++it) {
-        DM_TRY(round(st, it));
+        DM_TRY(round(st, it, fuse_first && it == 0));
         DM_CK(cudaMemcpyAsync(s->h_ctrl, d.ctrl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         DM_CK(cudaStreamSynchronize(st));
         harvest(s);
@@ -1213,10 +1278,6 @@ dm_status dm_adjoint_frame_chain(dm_system *sys, const double *q_prev, const dou
     set_error("dm_adjoint_frame_chain: NULL argument");
     return DM_ERR_INVALID_ARG;
   }
-  if (s->x.midpoint) {
-    set_error("dm_adjoint_frame_chain: backward Euler only");
-    return DM_ERR_INVALID_ARG;
-  }
   const HostTopology &T = s->T;
   auto &F = s->x.fchain;
   if (!F.g) {
@@ -1241,7 +1302,7 @@ dm_status dm_adjoint_frame_chain(dm_system *sys, const double *q_prev, const dou
     DM_TRY(upload(s, &F.layout2dof, T.layout2dof));
     DM_TRY(dalloc(s, &F.g, 3 * std::max<size_t>(1, (size_t)T.n_edges)));
   }
-  FrameChainArgs fa{(int)T.n_edges, F.nlnode, s->p.dt, F.edge_lay, F.lnode_lay, F.lnode_ein,
+  FrameChainArgs fa{(int)T.n_edges, F.nlnode, s->p.dt, s->x.midpoint ? 1 : 0, F.edge_lay, F.lnode_lay, F.lnode_ein,
                     F.lnode_eout, F.layout2dof, s->d.fixed, q_prev, q, q_next, gq, gv, gv0,
                     phibar, gq0, F.g};
   cudaStream_t st = s->stream;
@@ -1300,13 +1361,20 @@ dm_status dm_autotune(dm_system *sys, int32_t steps, dm_tuning *out) {
     }
     if (dm_step(sys, steps, nullptr) != DM_OK) return INFINITY;
     if (cudaStreamSynchronize(st) != cudaSuccess) return INFINITY;
-    if (!s->x.launches[id]) return INFINITY;
-    // the residual and Jacobian passes of the stencils (of the rows) share
-    // one launch shape: both are timed
+    // the residual, Jacobian and fused passes of the stencils (of the rows)
+    // share one launch shape: all are timed
     double ms = s->x.ms[id];
-    if (id == K_STENCIL) ms += s->x.ms[K_HESS];
-    if (id == K_ROWS) ms += s->x.ms[K_BAND];
-    return ms / (double)s->x.launches[id];
+    int64_t nl = s->x.launches[id];
+    if (id == K_STENCIL) {
+      ms += s->x.ms[K_HESS] + s->x.ms[K_FUSED];
+      nl += s->x.launches[K_FUSED];
+    }
+    if (id == K_ROWS) {
+      ms += s->x.ms[K_BAND] + s->x.ms[K_ROWS_FUSED];
+      nl += s->x.launches[K_ROWS_FUSED];
+    }
+    if (!nl) return INFINITY;
+    return ms / (double)nl;
   };
   // coordinate search: the phases run one after another, so each kernel's
   // shape is chosen on its own time, keeping the default unless another
@@ -1388,7 +1456,11 @@ dm_status dm_autotune(dm_system *sys, int32_t steps, dm_tuning *out) {
     s->x.ev_used[k] = false;
   }
   cudaMemset(s->x.d_units, 0, DM_NUM_KERNELS * sizeof(unsigned long long));
-  if (s->x.round_graph) {  // launch shapes are baked into the graph
+  if (s->x.first_graph) {  // launch shapes are baked into the graphs
+    cudaGraphExecDestroy(s->x.first_graph);
+    s->x.first_graph = nullptr;
+  }
+  if (s->x.round_graph) {
     cudaGraphExecDestroy(s->x.round_graph);
     s->x.round_graph = nullptr;
   }
@@ -1491,10 +1563,6 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
     set_error("dm_step_adjoint: NULL argument");
     return DM_ERR_INVALID_ARG;
   }
-  if (s->x.midpoint) {
-    set_error("dm_step_adjoint: backward Euler only (the system uses implicit midpoint)");
-    return DM_ERR_INVALID_ARG;
-  }
   const HostTopology &T = s->T;
   std::vector<int32_t> rod_d0, rod_n;
   for (int k = 0; k < T.n_systems; ++k) {
@@ -1562,7 +1630,12 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
     else
       k_scatter_add_layout<<<blocks(n, 256), 256, 0, st>>>(n, d.layout2dof, in, dst[k]);
   }
-  // every system active; J and the curvature gradients at q_next
+  // implicit midpoint: the backward-Euler adjoint over dt/2 at the midpoint
+  // configuration, with the loss gradients doubled
+  if (s->x.midpoint)
+    k_adj_midpoint_in<<<blocks(nd, 256), 256, 0, st>>>(nd, d.fixed, d.qn, d.q, bgq, bgv);
+  // every system active; J and the curvature gradients at q_next (at the
+  // midpoint configuration for implicit midpoint)
   std::vector<int32_t> ones(S, 1);
   DM_CK(cudaMemcpyAsync(d.sys_active, ones.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   DM_CK(cudaMemsetAsync(d.sys_status, 0, S * sizeof(int32_t), st));
@@ -1595,6 +1668,7 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
     ca.bucket_fill = c.bucket_fill; ca.bucket_edges = c.bucket_edges; ca.pairs = c.pairs;
     ca.npairs = c.npairs; ca.fc = c.fc; ca.dense = c.dense;
     ca.n_contact = c.n_contact; ca.cgo = c.cgo; ca.cbad = c.cbad;
+    ca.nn = (int)T.n_nodes;
     DM_CK(cudaMemsetAsync(c.fc, 0, nd * sizeof(double), st));
     DM_CK(cudaMemsetAsync(c.npairs, 0, sizeof(int32_t), st));
     DM_CK(cudaMemsetAsync(c.bucket_count, 0, c.table * sizeof(int32_t), st));
@@ -1605,6 +1679,7 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
     k_cc_fill<<<blocks(ne, 256), 256, 0, st>>>(ca);
     k_cc_pairs<<<blocks(ne, 128), 128, 0, st>>>(ca);
     k_cc_terms<<<blocks(c.pair_cap, 64), 64, 0, st>>>(ca);
+    if (T.ground) k_cc_ground<<<blocks(nn, 128), 128, 0, st>>>(ca, d.node_dof_arr, d.node_sys, d.nt);
   }
   if (!rod_d0.empty() || contact_on) {
     RowArgs ra{};
@@ -1621,10 +1696,11 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
     k_rows_rod<<<blocks(nd, 256), 256, 0, st>>>(ra);
   }
   if (ngen > 0) {
-    DM_CK(cudaMemsetAsync(d.gen, 0, T.gen_doubles * sizeof(double), st));
     AsmArgs aa{(int)T.asm_target.size(), d.asm_target, d.asm_ptr, d.asm_src, d.sh, d.es, d.nt,
-               d.dconst, d.gen, d.asm_sys, d.sys_active, nullptr};
-    if (aa.ntarget > 0) k_assemble_gen<<<blocks(aa.ntarget, 256), 256, 0, st>>>(aa);
+               d.dconst, d.gen, d.asm_sys, d.sys_active, nullptr,
+               (int)T.gen_sys.size(), d.gen_sys, d.asm_t0, d.gs_mat0, d.gs_mat1};
+    if (s->x.n_slow) k_gen_clear_slow<<<aa.ngen, 256, 0, st>>>(aa, d.gs_fast);
+    if (s->x.asm_chunks > 0) k_assemble_gen<<<dim3(aa.ngen, s->x.asm_chunks), 256, 0, st>>>(aa);
   }
   AdjArgs aa{nd, ns, nslots, s->p.dt, lam, bgq, bgv, d.mass, s->x.d_damp, A.dk, d.st_kb,
              d.fixed, d.st_nd, d.st_th, s->x.d_slot2st, rhs, bgq0, bgv0, A.gk,
@@ -1677,7 +1753,7 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
     const int wf = s->x.wpb_factor, wb = s->x.wpb_back;
     if (ga.nlimb)
       k_gen_limb_factor<<<(ga.nlimb + wf - 1) / wf, 32 * wf, s->x.smem_factor, st>>>(ga);
-    k_gen_border<<<ngen, 32, s->x.border_smem, st>>>(ga);
+    k_gen_border<<<ngen, kGenBorderThreads, s->x.border_smem, st>>>(ga);
     if (ga.nlimb)
       k_gen_limb_back<<<(ga.nlimb + wb - 1) / wb, 32 * wb, s->x.smem_back, st>>>(ga);
     DM_CK(cudaGetLastError());
@@ -1738,6 +1814,8 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
   DM_CK(cudaMemcpyAsync(d.q, d.qn, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (bs != DM_OK) return bs;
   k_adj_state<<<blocks(nd, 256), 256, 0, st>>>(aa);
+  if (s->x.midpoint)
+    k_adj_midpoint_out<<<blocks(nd, 256), 256, 0, st>>>(nd, d.fixed, bgq, bgv, bgq0, bgv0);
   if (nslots > 0) k_adj_kbar<<<blocks(nslots, 128), 128, 0, st>>>(aa);
   // outputs: state gradients in layout order, curvature gradients by slot
   double *outs[2] = {gq0, gv0};

@@ -528,6 +528,30 @@ __global__ void __launch_bounds__(64) k_cc_terms(ContactArgs a) {
     }
 }
 
+// Ground contact and friction of the nodes of contact systems (Eq. 10-13,
+// the node terms of k_nodes: force F and -dF/dx, nonsymmetric with friction)
+// into their contact force and dense matrix, one thread per node; after
+// k_cc_terms in stream order (no concurrent writer to these entries).
+__global__ void k_cc_ground(ContactArgs a, const int32_t *node_dof, const int32_t *node_sys,
+                            const double *nt) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= a.nn) return;
+  const int s = node_sys[v];
+  // residual phase of the round: the line search has not decided yet (an
+  // earlier round's backtracking decision must not drop the force)
+  if (!a.sys_active[s] || a.sys_kind[s] != SOLVE_CONTACT) return;
+  const int d = node_dof[v], d0 = a.sys_dof0[s], n = a.sys_ndof[s], NN = a.nn;
+  double *M = a.dense + a.sys_dense0[s];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    if (a.fixed[d + r]) continue;
+    a.fc[d + r] += nt[r * NN + v];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (!a.fixed[d + c]) M[(size_t)(d + r - d0) * n + (d + c - d0)] += nt[(3 + 3 * r + c) * NN + v];
+  }
+}
+
 // The rod's band (lower, symmetric) into the dense matrix of each contact
 // system, one thread per DOF row.
 __global__ void k_cc_band(ContactArgs a) {

@@ -10,8 +10,9 @@
 //  k_rows_gen      -- one thread per DOF: residual of Eq. 15 from the force
 //                     gather lists and its scaled size.
 //  k_assemble_gen  -- one thread per matrix entry of the limb bands, the
-//                     limb/border coupling blocks and the border block:
-//                     the sum of its element contributions in a fixed order.
+//                     limb/border coupling blocks and the border block of
+//                     the systems that solve this round: the sum of its
+//                     element contributions in a fixed order.
 //  k_solve_gen     -- one warp per system: banded LU with partial pivoting of
 //                     every limb interior (one lane per limb), the Schur complement
 //                     on the border DOFs (joint nodes, their neighbours and
@@ -114,23 +115,42 @@ __global__ void __launch_bounds__(256) k_rows_gen(RowGenArgs a) {
   atomicMax(&a.sys_res[s], (unsigned long long)__double_as_longlong(rr));
 }
 
+// Grid (system, chunk of kAsmPerBlock targets): blocks of systems that do
+// not solve this round (inactive or backtracking) leave at once; every
+// target entry gets the sum of its element contributions in a fixed order.
 __global__ void k_assemble_gen(AsmArgs a) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.ntarget) return;
-  const int sy = a.tsys[t];
+  const int w = blockIdx.x;
+  const int sy = a.gen_sys[w];
   if (!a.sys_active[sy] || (a.ls_action && a.ls_action[sy] == 1)) return;  // no solve
-  double v = 0.0;
-  for (int k = a.ptr[t]; k < a.ptr[t + 1]; ++k) {
-    const uint32_t code = a.src[k];
-    const uint32_t type = (code >> 29) & 3u, idx = code & 0x1FFFFFFFu;
-    double x;
-    if (type == SRC_STENCIL) x = a.sh[idx];
-    else if (type == SRC_EDGE) x = a.es[idx];
-    else if (type == SRC_NODE) x = a.nt[idx];
-    else x = a.dconst[idx];
-    v += (code & 0x80000000u) ? -x : x;
+  const int t1 = a.t0[w + 1];
+#pragma unroll
+  for (int u = 0; u < kAsmPerBlock / 256; ++u) {
+    const int t = a.t0[w] + (int)blockIdx.y * kAsmPerBlock + u * 256 + (int)threadIdx.x;
+    if (t >= t1) break;
+    double v = 0.0;
+    for (int k = a.ptr[t]; k < a.ptr[t + 1]; ++k) {
+      const uint32_t code = a.src[k];
+      const uint32_t type = (code >> 29) & 3u, idx = code & 0x1FFFFFFFu;
+      double x;
+      if (type == SRC_STENCIL) x = a.sh[idx];
+      else if (type == SRC_EDGE) x = a.es[idx];
+      else if (type == SRC_NODE) x = a.nt[idx];
+      else x = a.dconst[idx];
+      v += (code & 0x80000000u) ? -x : x;
+    }
+    a.gen[a.target[t]] = v;
   }
-  a.gen[a.target[t]] = v;
+}
+
+// Storage of the systems on the pivoting path that solve this round: it
+// holds the last factorisation (in place, with fill), cleared before the
+// assembly; one block per system.
+__global__ void k_gen_clear_slow(AsmArgs a, const int32_t *gs_fast) {
+  const int w = blockIdx.x;
+  if (gs_fast[w]) return;
+  const int sy = a.gen_sys[w];
+  if (!a.sys_active[sy] || (a.ls_action && a.ls_action[sy] == 1)) return;
+  for (int64_t i = a.mat0[w] + threadIdx.x; i < a.mat1[w]; i += blockDim.x) a.gen[i] = 0.0;
 }
 
 __global__ void k_solve_gen(SolveGenArgs a) {

@@ -13,6 +13,16 @@
 //   3. k_gen_limb_back (one warp per limb): the m condensed rows from the
 //      border values, then back substitution towards the free end; q += dq.
 //
+// Late Newton rounds carry few systems, so a round costs the length of one
+// limb's elimination chain; both limb kernels keep that chain short.  Per
+// column the factor takes the 10 multipliers in one instruction (a lane
+// each, broadcast by shuffles), the 110 updates in four, and the next
+// pivot's reciprocal (FP32 seed, two FP64 Newton steps) right after the
+// update that produces it, overlapping the others.  The back substitution
+// is column oriented: lanes 1..10 hold the partial right-hand sides of the
+// ten rows above the current one in registers, so a row costs one multiply,
+// one update and two shuffles.
+//
 // The Jacobian is that of Sec. III-C (M/dt^2 - dF/dq, with the contact and
 // friction terms of Sec. III-B), not symmetric when friction acts, hence LU.
 // Band storage of a limb (row-major in elimination order p): entry (p, p+k)
@@ -26,6 +36,18 @@ namespace {
 constexpr int kRow = 22;        // 21 band entries and the right-hand side
 constexpr int kSmall = kFastMaxM * (kFastMaxM + kFastMaxBC + 1);  // condensed block
 constexpr unsigned kFull = 0xffffffffu;
+
+// 1/d from an FP32 seed and two Newton steps in FP64; a division outside
+// the seed's range.
+__device__ __forceinline__ double limb_recip(double d) {
+  const double ad = fabs(d);
+  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+  double r = (double)__frcp_rn((float)d);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
 
 // The border kernel's decision for system s, without its side effects.
 __device__ __forceinline__ bool wants_solve(const SolveGenArgs &a, int s) {
@@ -128,9 +150,8 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
   const int n = a.lb_n[L], m = a.lb_m[L], nbc = a.lb_nbc[L], dir = a.lb_dir[L];
   const int d0 = a.lb_dof0[L];
   double *G = a.gen;
-  double *band = G + a.lb_band[L];
-  double *rpv = G + a.lb_piv[L];
-  double *y = G + a.lb_y[L];
+  const double *band = G + a.lb_band[L];
+  double *U = G + a.lb_y[L];  // [ne][12] out: U row, right-hand side, 1/pivot
   // coalesced staging of the contiguous band
   for (int e = lane; e < n * 21; e += 32) {
     const int p = e / 21;
@@ -140,58 +161,59 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
   __syncwarp();
   bool bad = false;
   const int ne = n - m;  // rows eliminated inside the limb
-  for (int j = 0; j < ne; ++j) {
+  // update slots of this lane, the same for every column: row j + si
+  // (si = 1..10; 0 = no slot) and entry sk (0 = right-hand side, 1..10 =
+  // the band entry under column j + sk); the slot (1, 1), which yields the
+  // next pivot, is lane 1's first
+  int si[4], sk[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int t = lane + 32 * u;
+    si[u] = t < 110 ? t / 11 + 1 : 0;
+    sk[u] = t < 110 ? t - (si[u] - 1) * 11 : 0;
+  }
+  double rp = 1.0;
+  if (ne > 0) {
+    const double piv = Bs[10];
+    if (!(fabs(piv) > 0.0) || !isfinite(piv)) bad = true;
+    else rp = limb_recip(piv);
+  }
+  for (int j = 0; j < ne && !bad; ++j) {
     const double *pr = Bs + j * kRow;
-    const double piv = pr[10];
-    if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
-      bad = true;
-      break;
+    // multiplier of row j + 1 + lane, stored in place by the lane that reads it
+    double l = 0.0;
+    if (lane < 10 && j + lane + 1 < n) {
+      double *mp = Bs + (j + lane + 1) * kRow + 9 - lane;
+      l = *mp * rp;
+      *mp = l;
     }
-    const double rp = 1.0 / piv;
-    // updates of rows j+i (i = 1..10): k = 0 the multiplier and the
-    // right-hand side, k = 1..10 the band entry under column j + k
-    double val[4], mul[4];
-    int tgt[4];
+    if (lane == 0) Bs[j * kRow + 10] = rp;  // the pivot is read no more
+    double v0 = 0.0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      tgt[u] = -1;
-      const int t = lane + 32 * u;
-      if (t < 110) {
-        const int i = t / 11 + 1, k = t - (i - 1) * 11;
-        if (j + i < n) {
-          const double *ri = Bs + (j + i) * kRow;
-          const double l = ri[10 - i] * rp;
-          mul[u] = l;
-          if (k == 0) {
-            val[u] = fma(-l, pr[21], ri[21]);
-            tgt[u] = (j + i) * kRow + 21;
-          } else {
-            val[u] = fma(-l, pr[10 + k], ri[10 - i + k]);
-            tgt[u] = (j + i) * kRow + 10 - i + k;
-          }
-        }
+      const double lu = __shfl_sync(kFull, l, si[u] > 0 ? si[u] - 1 : 0);
+      if (si[u] > 0 && j + si[u] < n) {
+        double *dst = Bs + (j + si[u]) * kRow + (sk[u] ? 10 - si[u] + sk[u] : 21);
+        const double v = fma(-lu, pr[sk[u] ? 10 + sk[u] : 21], *dst);
+        *dst = v;
+        if (u == 0) v0 = v;
+      }
+      if (u == 0 && j + 1 < ne) {
+        // the next pivot (lane 1's first slot), its reciprocal off the chain
+        const double pn = __shfl_sync(kFull, v0, 1);
+        if (!(fabs(pn) > 0.0) || !isfinite(pn)) bad = true;
+        else rp = limb_recip(pn);
       }
     }
-    if (lane == 0) rpv[j] = rp;
-    __syncwarp();
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (tgt[u] >= 0) {
-        Bs[tgt[u]] = val[u];
-        const int t = lane + 32 * u, i = t / 11 + 1;
-        if (t - (i - 1) * 11 == 0) Bs[(j + i) * kRow + 10 - i] = mul[u];
-      }
     __syncwarp();
   }
-  // factors of the eliminated rows (L multipliers, U rows) and their
-  // eliminated right-hand side, for the back substitution
-  if (!bad) {
-    for (int e = lane; e < ne * 21; e += 32) {
-      const int p = e / 21;
-      band[e] = Bs[p * kRow + (e - p * 21)];
+  // U rows, eliminated right-hand sides and reciprocal pivots of the
+  // eliminated rows, for the back substitution
+  if (!bad)
+    for (int e = lane; e < ne * 12; e += 32) {
+      const int p = e / 12, c = e - p * 12;
+      U[e] = Bs[p * kRow + (c < 10 ? 11 + c : (c == 10 ? 21 : 10))];
     }
-    for (int p = lane; p < ne; p += 32) y[p] = Bs[p * kRow + 21];
-  }
   if (!bad && m > 0) {
     // condensed block A_m and right-hand sides [C_m | y_m]
     double *A = small;
@@ -230,13 +252,21 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
   if (bad && lane == 0) atomicOr(a.gen_bad + w, 1);
 }
 
-__global__ void k_gen_border(SolveGenArgs a) {
+// The border system [S | r] (row-major, leading dimension nB + 1, right-hand
+// side in the last column) solved by a block of kGenBorderThreads: Gaussian
+// elimination with partial pivoting (the pivot search by warp 0, the
+// trailing update spread over all threads, one matrix entry per thread and
+// step), then a column-oriented back substitution by warp 0 with the
+// right-hand sides in registers (rows lane, lane + 32, lane + 64).
+__global__ void __launch_bounds__(kGenBorderThreads) k_gen_border(SolveGenArgs a) {
   extern __shared__ double sm[];
-  const int w = blockIdx.x, lane = threadIdx.x;
-  if (w >= a.ngen || !a.gs_fast[w]) return;
+  __shared__ int flag[4];  // go, bad, pivot row, pivot ok
+  const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nt = blockDim.x;
+  if (w >= a.ngen || !a.gs_fast[w]) return;  // block-uniform
   const int s = a.gen_sys[w];
-  int go = 0, bad = 0;
-  if (lane == 0) {
+  if (tid == 0) {
+    int go = 0, bad = 0;
     if (a.sys_active[s] && a.ls_action && a.ls_action[s] == 1) {
       atomicAdd(&a.ctrl[0], 1);  // backtracking: no solve this round
     } else if (a.sys_active[s]) {
@@ -261,38 +291,118 @@ __global__ void k_gen_border(SolveGenArgs a) {
       bad = a.gen_bad[w];
       a.gen_bad[w] = 0;
     }
+    flag[0] = go;
+    flag[1] = bad;
   }
-  go = __shfl_sync(kFull, go, 0);
-  bad = __shfl_sync(kFull, bad, 0);
+  __syncthreads();
+  const int go = flag[0];
+  bool bad = flag[1] != 0;
   const int nB = a.gs_nB[w];
+  const int ld = nB + 1;
+  double *S = sm, *rinv = sm + (size_t)nB * ld, *lm = rinv + nB;
+  const int32_t *bd = a.border_dof + a.gs_border0[w];
+  if (go && nB > 0) {
+    // the border block and the limbs' Schur sums, left zero for the next
+    // round's assembly and atomics (the limb factors ran: go)
+    double *J = a.gen + a.gs_JBB[w];
+    double *acc = a.gen + a.gs_rB[w];
+    for (int e = tid; e < nB * nB; e += nt) {
+      const int r = e / nB;
+      S[r * ld + e - r * nB] = J[e];
+      J[e] = 0.0;
+    }
+    for (int b = tid; b < nB; b += nt) {
+      S[b * ld + nB] = acc[b] - a.f[bd[b]];
+      acc[b] = 0.0;
+    }
+    __syncthreads();
+  }
   if (go && !bad && nB > 0) {
-    double *S = sm, *x = sm + nB * nB;
-    const double *J = a.gen + a.gs_JBB[w];
-    const double *acc = a.gen + a.gs_rB[w];
-    const int32_t *bd = a.border_dof + a.gs_border0[w];
-    for (int e = lane; e < nB * nB; e += 32) S[e] = J[e];
-    for (int b = lane; b < nB; b += 32) x[b] = acc[b] - a.f[bd[b]];
-    __syncwarp();
-    if (!warp_lu_solve(S, nB, nB, x, 1, 1, lane)) {
-      bad = 1;
-    } else {
+    for (int j = 0; j < nB; ++j) {
+      if (warp == 0) {
+        double best = -1.0;
+        int bi = j;
+        for (int i = j + lane; i < nB; i += 32) {
+          const double v = fabs(S[i * ld + j]);
+          if (v > best) {
+            best = v;
+            bi = i;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          const double ob = __shfl_xor_sync(kFull, best, o);
+          const int oi = __shfl_xor_sync(kFull, bi, o);
+          if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+          }
+        }
+        if (lane == 0) {
+          flag[2] = bi;
+          flag[3] = (best > 0.0) && isfinite(best);
+        }
+      }
+      __syncthreads();
+      const int pr = flag[2];
+      if (!flag[3]) {
+        bad = true;
+        break;  // uniform
+      }
+      if (pr != j)
+        for (int c = j + tid; c <= nB; c += nt) {
+          const double t = S[j * ld + c];
+          S[j * ld + c] = S[pr * ld + c];
+          S[pr * ld + c] = t;
+        }
+      __syncthreads();
+      const double rp = limb_recip(S[j * ld + j]);
+      if (tid == 0) rinv[j] = rp;
+      for (int i = j + 1 + tid; i < nB; i += nt) lm[i] = S[i * ld + j] * rp;
+      __syncthreads();
+      // rows j+1.., columns j+1..nB (the right-hand side included)
+      const int nc = nB - j;
+      for (int e = tid; e < (nB - j - 1) * nc; e += nt) {
+        const int r = e / nc;
+        const int i = j + 1 + r, c = j + 1 + e - r * nc;
+        S[i * ld + c] = fma(-lm[i], S[j * ld + c], S[i * ld + c]);
+      }
+      __syncthreads();
+    }
+    if (!bad && warp == 0) {
+      double b0 = lane < nB ? S[lane * ld + nB] : 0.0;
+      double b1 = lane + 32 < nB ? S[(lane + 32) * ld + nB] : 0.0;
+      double b2 = lane + 64 < nB ? S[(lane + 64) * ld + nB] : 0.0;
+      for (int i = nB - 1; i >= 0; --i) {
+        const int hi = i >> 5;
+        const double src = hi == 0 ? b0 : (hi == 1 ? b1 : b2);
+        const double xi = __shfl_sync(kFull, src, i & 31) * rinv[i];
+        if (lane == 0) lm[i] = xi;
+        if (lane < i) b0 = fma(-S[lane * ld + i], xi, b0);
+        if (lane + 32 < i) b1 = fma(-S[(lane + 32) * ld + i], xi, b1);
+        if (lane + 64 < i) b2 = fma(-S[(lane + 64) * ld + i], xi, b2);
+      }
+    }
+    __syncthreads();
+    if (!bad) {
       double *xB = a.gen + a.gs_xB[w];
-      for (int b = lane; b < nB; b += 32) {
-        xB[b] = x[b];
-        a.q[bd[b]] += x[b];
+      for (int b = tid; b < nB; b += nt) {
+        xB[b] = lm[b];
+        a.q[bd[b]] += lm[b];
       }
     }
   }
-  if (lane == 0) {
-    if (go && bad) {
+  if (tid == 0) {
+    int g = go;
+    if (g && bad) {
       a.sys_status[s] = DM_ERR_DEGENERATE;
       a.sys_active[s] = 0;
       atomicAdd(&a.ctrl[1], 1);
       atomicMin(&a.ctrl[2], s);
-      go = 0;
+      g = 0;
     }
-    a.gen_go[w] = go;
-    if (go) {
+    a.gen_go[w] = g;
+    if (g) {
       a.sys_iters[s] += 1;
       if (a.ls_trial) a.ls_trial[s] = 1;
       atomicAdd(&a.ctrl[0], 1);
@@ -307,7 +417,7 @@ __global__ void k_gen_border(SolveGenArgs a) {
 
 __global__ void __launch_bounds__(128) k_gen_limb_back(SolveGenArgs a) {
   // per warp: U rows (10 off-diagonal entries), eliminated right-hand side
-  // and reciprocal pivot [n][12], then a ring of 16 solution values
+  // and reciprocal pivot [n][12], then the m condensed rows' values
   extern __shared__ double dyn[];
   const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int L = blockIdx.x * (blockDim.x >> 5) + wi;
@@ -315,43 +425,43 @@ __global__ void __launch_bounds__(128) k_gen_limb_back(SolveGenArgs a) {
   const int w = a.lb_gsys[L];
   if (!a.gs_fast[w] || !a.gen_go[w]) return;
   double *Us = dyn + (size_t)wi * (a.limb_nmax * 12 + 16);
-  double *xr = Us + (size_t)a.limb_nmax * 12;  // x of rows p .. p + 10 at [p & 15]
+  double *xr = Us + (size_t)a.limb_nmax * 12;  // x of rows ne .. n - 1
   const int n = a.lb_n[L], m = a.lb_m[L], nbc = a.lb_nbc[L], dir = a.lb_dir[L];
   const int d0 = a.lb_dof0[L], ne = n - m;
   const double *G = a.gen;
-  const double *band = G + a.lb_band[L];
-  const double *rpv = G + a.lb_piv[L];
-  const double *y = G + a.lb_y[L];
+  const double *Ug = G + a.lb_y[L];
   auto dof = [&](int p) { return d0 + (dir ? n - 1 - p : p); };
-  for (int e = lane; e < ne * 21; e += 32) {
-    const int p = e / 21, c = e - p * 21;
-    if (c > 10) Us[p * 12 + c - 11] = band[e];
-  }
-  for (int p = lane; p < ne; p += 32) {
-    Us[p * 12 + 10] = y[p];
-    Us[p * 12 + 11] = rpv[p];
-  }
+  for (int e = lane; e < ne * 12; e += 32) Us[e] = Ug[e];
+  // the condensed rows ne..n-1 from the border values
   if (lane < m) {
     const double *Z = G + a.lb_Y[L] + lane * (nbc + 1);
     const double *xB = G + a.gs_xB[w];
     const int32_t *bc = a.lb_bcols + a.lb_bc0[L];
     double v = Z[nbc];
     for (int b = 0; b < nbc; ++b) v = fma(-Z[b], xB[bc[b]], v);
-    xr[(ne + lane) & 15] = v;
+    xr[lane] = v;
     atomicAdd(a.q + dof(ne + lane), v);
   }
   __syncwarp();
-  for (int p = ne - 1; p >= 0; --p) {
-    const double *u = Us + p * 12;
-    double t = (lane >= 1 && lane <= 10 && p + lane < n) ? u[lane - 1] * xr[(p + lane) & 15] : 0.0;
-#pragma unroll
-    for (int o = 8; o; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-    if (lane == 0) {
-      const double x = (u[10] - t) * u[11];
-      xr[p & 15] = x;
-      atomicAdd(a.q + dof(p), x);  // a reduction: no load on the recurrence
+  // lane i (0..10) holds the right-hand side of row p - i less the terms of
+  // the solved rows; lane 11 brings in row p - 11 untouched
+  auto U = [&](int r, int k) { return Us[r * 12 + k - 1]; };  // entry (r, r + k)
+  double acc = 0.0;
+  {
+    const int r = ne - 1 - lane;
+    if (lane <= 11 && r >= 0) {
+      acc = Us[r * 12 + 10];
+      if (lane <= 10)
+        for (int c = ne; c < n && c <= r + 10; ++c) acc = fma(-U(r, c - r), xr[c - ne], acc);
     }
-    __syncwarp();
+  }
+  for (int p = ne - 1; p >= 0; --p) {
+    const double x = __shfl_sync(kFull, acc * Us[p * 12 + 11], 0);
+    if (lane == 0) atomicAdd(a.q + dof(p), x);  // a reduction: no load on the recurrence
+    if (lane >= 1 && lane <= 10 && p - lane >= 0) acc = fma(-U(p - lane, lane), x, acc);
+    // row p - 1 - i to lane i; lane 11 takes row p - 12
+    acc = __shfl_down_sync(kFull, acc, 1);
+    if (lane == 11) acc = p - 12 >= 0 ? Us[(p - 12) * 12 + 10] : 0.0;
   }
 }
 

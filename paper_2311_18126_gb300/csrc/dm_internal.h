@@ -30,6 +30,7 @@ enum SolverKind : int32_t {
 constexpr int kFastMaxM = 10;        // coupled rows at one limb end
 constexpr int kFastMaxBC = 16;       // border columns one limb couples to
 constexpr int kFastMaxBorder = 96;   // border DOFs of one system
+constexpr int kGenBorderThreads = 128;  // block of the border solve
 constexpr int kFastMaxRows = 1200;   // rows of one limb (shared-memory staging)
 
 enum SrcType : uint32_t { SRC_STENCIL = 0, SRC_EDGE = 1, SRC_NODE = 2, SRC_DIAG = 3 };
@@ -87,6 +88,7 @@ struct HostTopology {
   // scratch) <- sum of sources
   std::vector<int64_t> asm_target;
   std::vector<int32_t> asm_sys;            // system of each target
+  std::vector<int32_t> asm_t0;             // first target of each general system
   std::vector<int32_t> asm_ptr;
   std::vector<uint32_t> asm_src;
   bool any_general = false, ground = false;
@@ -151,6 +153,7 @@ struct DevArrays {
   int32_t *gen_sys = nullptr, *gs_limb0 = nullptr, *gs_nlimb = nullptr, *gs_nB = nullptr,
           *gs_border0 = nullptr;
   int64_t *gs_JBB = nullptr, *gs_rB = nullptr, *gs_S = nullptr, *gs_xB = nullptr;
+  int64_t *gs_mat0 = nullptr, *gs_mat1 = nullptr;  // each system's storage range
   int32_t *lb_dof0 = nullptr, *lb_n = nullptr, *lb_ncr = nullptr, *lb_cr0 = nullptr;
   int64_t *lb_band = nullptr, *lb_piv = nullptr, *lb_C = nullptr, *lb_R = nullptr, *lb_Y = nullptr, *lb_y = nullptr;
   int32_t *border_dof = nullptr, *coupled_rows = nullptr;
@@ -158,7 +161,7 @@ struct DevArrays {
           *lb_nbc = nullptr, *lb_bc0 = nullptr, *lb_bcols = nullptr;
   int32_t *gen_go = nullptr, *gen_bad = nullptr;  // per general system
   int64_t *asm_target = nullptr;
-  int32_t *asm_sys = nullptr;
+  int32_t *asm_sys = nullptr, *asm_t0 = nullptr;
   int32_t *asm_ptr = nullptr;
   uint32_t *asm_src = nullptr;
 };

@@ -106,6 +106,10 @@ struct AsmArgs {
   double *gen;
   const int32_t *tsys;       // system of each target
   const int32_t *sys_active, *ls_action;
+  // per general system: its system index, first target, storage range
+  int ngen;
+  const int32_t *gen_sys, *t0;
+  const int64_t *mat0, *mat1;
 };
 
 struct SolveGenArgs {
@@ -160,6 +164,7 @@ struct ContactArgs {
   double *fc, *dense;
   int n_contact;
   int32_t *cgo, *cbad;  // per contact system: solve this round, zero pivot met
+  int nn;  // nodes (ground terms of contact systems)
 };
 constexpr int kNB = 32;  // panel width of the contact-system LU
 __global__ void k_cc_cells(ContactArgs a);
@@ -168,6 +173,8 @@ __global__ void k_cc_fill(ContactArgs a);
 __global__ void k_cc_pairs(ContactArgs a);
 __global__ void k_cc_terms(ContactArgs a);
 __global__ void k_cc_band(ContactArgs a);
+__global__ void k_cc_ground(ContactArgs a, const int32_t *node_dof, const int32_t *node_sys,
+                            const double *nt);
 __global__ void k_cc_clear(ContactArgs a);
 __global__ void k_cc_reset_bw(ContactArgs a);
 __global__ void k_cc_decide(ContactArgs a, SolveArgs v);
@@ -199,6 +206,14 @@ __global__ void k_gen_transpose_border(SolveGenArgs a, const double *src, double
 __global__ void k_adj_rhs(AdjArgs a);
 __global__ void k_adj_state(AdjArgs a);
 __global__ void k_adj_kbar(AdjArgs a);
+// Implicit midpoint as the backward-Euler adjoint over h = dt/2 at the
+// midpoint configuration y: in, y = (q_n + q_{n+1})/2 and the loss
+// gradients doubled; out, the terms of q_{n+1} = 2y - q_n and
+// qdot_{n+1} = 2 (y - q_n)/h - qdot_n taken explicitly.
+__global__ void k_adj_midpoint_in(int nd, const uint8_t *fixed, const double *qn, double *q,
+                                  double *gq, double *gv);
+__global__ void k_adj_midpoint_out(int nd, const uint8_t *fixed, const double *gq2,
+                                   const double *gv2, double *gq0, double *gv0);
 
 __global__ void k_ls_merit(LineSearchArgs a);
 __global__ void k_ls_decide(LineSearchArgs a);
@@ -206,7 +221,9 @@ __global__ void k_ls_apply(LineSearchArgs a);
 
 __global__ void k_nodes(NodeArgs a);
 __global__ void k_rows_gen(RowGenArgs a);
-__global__ void k_assemble_gen(AsmArgs a);
+constexpr int kAsmPerBlock = 1024;  // assembly targets per block (256 threads)
+__global__ void k_assemble_gen(AsmArgs a);  // grid (systems, chunks), 256 threads
+__global__ void k_gen_clear_slow(AsmArgs a, const int32_t *gs_fast);
 __global__ void k_solve_gen(SolveGenArgs a);
 __global__ void k_gen_limb_factor(SolveGenArgs a);
 __global__ void k_gen_border(SolveGenArgs a);
@@ -234,7 +251,8 @@ struct StepArgs {
 // Frame chain of a rollout adjoint (dm_adjoint_frame_chain).
 struct FrameChainArgs {
   int ne, nlnode;
-  double dt;
+  double dt;                   // the backward-Euler step (dt/2 for implicit midpoint)
+  int midpoint;                // the energy of a step is taken at (q + q_next)/2
   const int32_t *edge_lay;     // [Ne] layout index of each edge's start node x
   const int32_t *lnode_lay, *lnode_ein, *lnode_eout;  // per layout node
   const int32_t *layout2dof;
@@ -250,10 +268,11 @@ __global__ void k_frames_in(int ne, const double *aos, double *soa);
 __global__ void k_begin_step(StepArgs a);
 __global__ void k_project_lengths(int nsys, const int32_t *sys_kind, const int32_t *sys_dof0,
                                   const int32_t *sys_ndof, const uint8_t *fixed,
-                                  const double *qn, double *q);
+                                  const double *qn, double *q, int midpoint);
 __global__ void k_commit(StepArgs a);
 __global__ void k_restore(StepArgs a);
 __global__ void k_round_continue(int32_t *ctrl, int max_rounds, cudaGraphConditionalHandle h);
+__global__ void k_round_count(int32_t *ctrl);
 __global__ void k_reset_res(int lo, int hi, const int32_t *sys_active,
                             unsigned long long *sys_res);
 

@@ -28,9 +28,11 @@ __global__ void k_begin_step(StepArgs a) {
 // the rescaled edge vectors that restarts at node 0 and at every fixed node
 // (a segmented scan): one warp per system, 32 nodes per pass, the running
 // position carried from pass to pass (Eq. 1 layout: node k at DOFs 4k..4k+2).
+// Implicit midpoint (q holds the midpoint guess y): the projection acts on
+// the step's end guess 2y - q_n and y is rebuilt as its mean with q_n.
 __global__ void k_project_lengths(int nsys, const int32_t *sys_kind, const int32_t *sys_dof0,
                                   const int32_t *sys_ndof, const uint8_t *fixed,
-                                  const double *qn, double *q) {
+                                  const double *qn, double *q, int midpoint) {
   const int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (s >= nsys || sys_kind[s] != SOLVE_ROD_BAND) return;  // warp-uniform
@@ -48,6 +50,11 @@ __global__ void k_project_lengths(int nsys, const int32_t *sys_kind, const int32
       gx = q[o];
       gy = q[o + 1];
       gz = q[o + 2];
+      if (midpoint) {
+        gx = 2.0 * gx - qn[o];
+        gy = 2.0 * gy - qn[o + 1];
+        gz = 2.0 * gz - qn[o + 2];
+      }
     }
     double hx = __shfl_up_sync(full, gx, 1), hy = __shfl_up_sync(full, gy, 1),
            hz = __shfl_up_sync(full, gz, 1);
@@ -95,9 +102,15 @@ __global__ void k_project_lengths(int nsys, const int32_t *sys_kind, const int32
       vz += cz;
     }
     if (on && !keep) {  // only this lane reads its node's q
-      q[o] = vx;
-      q[o + 1] = vy;
-      q[o + 2] = vz;
+      if (midpoint) {
+        q[o] = 0.5 * (qn[o] + vx);
+        q[o + 1] = 0.5 * (qn[o + 1] + vy);
+        q[o + 2] = 0.5 * (qn[o + 2] + vz);
+      } else {
+        q[o] = vx;
+        q[o + 1] = vy;
+        q[o + 2] = vz;
+      }
     }
     const int last = min(31, N - 1 - base);
     cx = __shfl_sync(full, vx, last);
@@ -173,6 +186,11 @@ __global__ void k_round_continue(int32_t *ctrl, int max_rounds, cudaGraphConditi
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int r = ++ctrl[4];
   cudaGraphSetConditional(h, (ctrl[0] > 0 && r < max_rounds) ? 1u : 0u);
+}
+
+// Counts a round run before the graph's while node (the fused first round).
+__global__ void k_round_count(int32_t *ctrl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ++ctrl[4];
 }
 
 // Clears the residual slots of the systems [lo, hi) still iterating before a

@@ -352,8 +352,11 @@ bool build_topology(const dm_system_desc *D, const dm_params *P, HostTopology &T
     for (int r = r0; r < r1 && jointless; ++r)
       for (int i = 0; i < T.npr[r]; ++i)
         if (mult[T.flat2node[T.rod_node0[r] + i]] > 1) jointless = false;
-    const bool group = T.sys_nrods[s] > 1 && P->self_contact && jointless && !T.ground;
-    const bool general = (T.sys_nrods[s] > 1 || T.ground) && !group;
+    // (with edge-edge contact, jointless systems stay on the contact path
+    // also on the ground: the ground terms join their dense matrix)
+    const bool group = T.sys_nrods[s] > 1 && P->self_contact && jointless;
+    const bool general = (T.sys_nrods[s] > 1 || T.ground) && !group &&
+                         !(P->self_contact && jointless);
     T.sys_kind[s] = group ? SOLVE_CONTACT : general ? SOLVE_GENERAL : SOLVE_ROD_BAND;
     if (!general) {
       for (int r = r0; r < r1; ++r)
@@ -737,7 +740,9 @@ bool build_topology(const dm_system_desc *D, const dm_params *P, HostTopology &T
         T.lb_C.push_back(off); off += m * nbc;
         T.lb_R.push_back(off); off += nbc * m;
         T.lb_Y.push_back(off); off += m * (nbc + 1);
-        T.lb_y.push_back(off); off += n;
+        // [n][12]: U row (10 entries), eliminated right-hand side and
+        // reciprocal pivot of each eliminated row (the band stays assembled)
+        T.lb_y.push_back(off); off += 12 * n;
       } else {
         T.lb_band.push_back(off); off += 31 * n;   // kl = 10, ku + fill = 20
         T.lb_piv.push_back(off); off += n;
@@ -813,6 +818,12 @@ bool build_topology(const dm_system_desc *D, const dm_params *P, HostTopology &T
     const size_t w = std::upper_bound(T.gs_mat0.begin(), T.gs_mat0.end(), o) - T.gs_mat0.begin() - 1;
     T.asm_sys[k] = T.gen_sys[w];
   }
+  // first target of each system's storage region
+  T.asm_t0.resize(T.gen_sys.size() + 1);
+  for (size_t w = 0; w < T.gen_sys.size(); ++w)
+    T.asm_t0[w] = (int32_t)(std::lower_bound(T.asm_target.begin(), T.asm_target.end(),
+                                             T.gs_mat0[w]) - T.asm_target.begin());
+  T.asm_t0[T.gen_sys.size()] = (int32_t)T.asm_target.size();
   return true;
 }
 

@@ -53,7 +53,7 @@ class StepStats(C.Structure):
                 ("sum_iterations", C.c_int64), ("max_iterations", C.c_int32)]
 
 
-NUM_KERNELS = 16
+NUM_KERNELS = 17
 
 
 class Profile(C.Structure):

@@ -12,14 +12,17 @@ from test_gpu_parity import _gpu
 pytestmark = pytest.mark.gpu
 
 
-def _batch():
+def _batch(integrator="be"):
     desc, params, kbar = workloads.uneven_rods(n_rods=64, seed=2)
     sub, kb = workloads.subset(desc, [3, 17, 40], kbar)
-    return sub, params, kb
+    return sub, dict(params, integrator=integrator), kb
 
 
-def test_step_adjoint_matches_oracle_adjoint():
-    desc, params, kb = _batch()
+@pytest.mark.parametrize("integrator", ["be", "midpoint"])
+def test_step_adjoint_matches_oracle_adjoint(integrator):
+    """The GPU adjoint (for implicit midpoint: over dt/2 at the midpoint
+    configuration) against the oracle's (for implicit midpoint: in q_{n+1})."""
+    desc, params, kb = _batch(integrator)
     gpu = _gpu(desc, params)
     ora = OracleSystems(desc, params)
     R = len(desc["nodes_per_rod"])
@@ -79,9 +82,9 @@ def test_step_adjoint_kappabar_matches_central_differences():
             assert abs(fd - gk[i, c]) <= 1e-5 * max(1.0, abs(fd)), (i, c, fd, gk[i, c])
 
 
-def _rollout_case(T=8):
+def _rollout_case(T=8, integrator="be"):
     from paper_2311_18126_gb300 import dismech as dmx
-    desc, params, kb = _batch()
+    desc, params, kb = _batch(integrator)
     gpu = dmx.System(desc, params)
     R = len(desc["nodes_per_rod"])
     gpu.set_natural_curvature(0, R, kb)
@@ -94,13 +97,14 @@ def _rollout_case(T=8):
     return gpu, q0, v0, frames, kseq
 
 
-def test_rollout_gradient_against_central_differences():
+@pytest.mark.parametrize("integrator", ["be", "midpoint"])
+def test_rollout_gradient_against_central_differences(integrator):
     """Gradient of a trajectory loss through 8 steps (checkpoints every 3
     steps, the frame chain included) against central differences of the GPU
     rollout.  Without the frame chain the errors were 18-26 %."""
     import torch
     from paper_2311_18126_gb300.adjoint import rollout
-    gpu, q0, v0, frames, kseq = _rollout_case()
+    gpu, q0, v0, frames, kseq = _rollout_case(integrator=integrator)
     rng = np.random.default_rng(3)
     w = rng.normal(size=(kseq.shape[0], len(q0)))
 
@@ -122,7 +126,16 @@ def test_rollout_gradient_against_central_differences():
         km[t, i, c] -= h
         fd = (loss_np(kp, q0, v0) - loss_np(km, q0, v0)) / (2 * h)
         errs.append(abs(fd - gk[t, i, c]) / max(abs(fd), 1e-3 * np.abs(gk).max()))
-    print("rollout kappabar gradient relative errors vs central differences:",
+    # initial velocities of free DOFs (the frames of the initial state stay
+    # as given: positions would move its tangents under fixed directors)
+    gv0 = vt.grad.numpy()
+    for i in rng.choice(np.flatnonzero(~gpu.fixed_mask()), size=4, replace=False):
+        vp, vm = v0.copy(), v0.copy()
+        vp[i] += 1e-5
+        vm[i] -= 1e-5
+        fd = (loss_np(kseq, q0, vp) - loss_np(kseq, q0, vm)) / 2e-5
+        errs.append(abs(fd - gv0[i]) / max(abs(fd), 1e-3 * np.abs(gv0).max()))
+    print("rollout gradient relative errors vs central differences (%s):" % integrator,
           ["%.2e" % e for e in errs])
     assert max(errs) < 2e-4
 
@@ -153,10 +166,12 @@ def _stars():
     return desc, params, gait
 
 
-def test_step_adjoint_star_robots_matches_oracle_adjoint():
+@pytest.mark.parametrize("integrator", ["be", "midpoint"])
+def test_step_adjoint_star_robots_matches_oracle_adjoint(integrator):
     """Limbed robots on the ground (joints, contact, friction: J not
     symmetric, solved transposed by the condensation kernels)."""
     desc, params, gait = _stars()
+    params = dict(params, integrator=integrator)
     R = len(desc["nodes_per_rod"])
     gpu = _gpu(desc, params)
     ora = OracleSystems(desc, params)
@@ -226,12 +241,14 @@ def test_star_robot_rollout_gradient_against_central_differences():
     assert max(errs) < 1e-3
 
 
-def test_step_adjoint_coil_with_contact_matches_oracle_adjoint():
+@pytest.mark.parametrize("integrator", ["be", "midpoint"])
+def test_step_adjoint_coil_with_contact_matches_oracle_adjoint(integrator):
     """A self-contacting coil (edge-edge IMC contact, no friction): the
     transposed dense-band LU on the GPU against the oracle's adjoint, at a
     step where turns touch."""
     from test_gpu_contact import _short_coil, _oracle_active_pairs
     desc, params = _short_coil()
+    params = dict(params, integrator=integrator)
     gpu = _gpu(desc, params)
     ora = OracleSystems(desc, params)
     for _ in range(36):
@@ -254,13 +271,17 @@ def test_step_adjoint_coil_with_contact_matches_oracle_adjoint():
         assert np.abs(a - b).max() <= 1e-8 * scale, np.abs(a - b).max() / scale
 
 
-def test_frame_chain_kernel_matches_a_numpy_restatement():
+@pytest.mark.parametrize("integrator", ["be", "midpoint"])
+def test_frame_chain_kernel_matches_a_numpy_restatement(integrator):
     """dm_adjoint_frame_chain (the rollout adjoint's frame chain on the GPU)
     against the same chain written out in NumPy: sigma at every free twist
     angle, the carried frame adjoint, and the tangent term on the node
-    positions, on random states of three rods (one with fixed DOFs)."""
+    positions, on random states of three rods (one with fixed DOFs).  For
+    implicit midpoint the step energy sees the frames transported to the
+    tangents of (q + q_next)/2."""
     import torch
     desc, params, _ = workloads.uneven_rods(n_rods=3, seed=9, n_min=6, n_max=9)
+    params = dict(params, integrator=integrator)
     gpu = _gpu(desc, params)
     npr = np.asarray(desc["nodes_per_rod"])
     fixed = gpu.fixed_mask()
@@ -277,7 +298,8 @@ def test_frame_chain_kernel_matches_a_numpy_restatement():
     gq, gv, gv0 = rng.standard_normal((3, n))
     phi0 = rng.standard_normal(int(np.sum(npr - 1)))
     gq0 = rng.standard_normal(n)
-    dt = params["dt"]
+    mid = integrator == "midpoint"
+    dt = params["dt"] / 2 if mid else params["dt"]
 
     # NumPy restatement
     def tangents(x):
@@ -294,11 +316,21 @@ def test_frame_chain_kernel_matches_a_numpy_restatement():
     hol = lambda a, b: np.cross(a, b) / (1.0 + np.sum(a * b, axis=1))[:, None]
     th = np.concatenate([o + 4 * np.arange(N - 1) + 3
                          for o, N in zip(np.concatenate([[0], np.cumsum(4 * npr - 1)])[:-1], npr)])
-    sigma = np.where(~fixed[th], -((gq[th] + gv[th] / dt) - gv0[th] / dt), 0.0)
+    if mid:
+        sigma = np.where(~fixed[th], -(2 * gq[th] + (gv[th] - gv0[th]) / dt), 0.0)
+    else:
+        sigma = np.where(~fixed[th], -((gq[th] + gv[th] / dt) - gv0[th] / dt), 0.0)
     phi = phi0 + sigma
     t, il = tangents(q)
-    w = hol(t, tangents(q_next)[0]) + hol(tangents(q_prev)[0], t)
-    gt = -phi[:, None] * w
+    if mid:
+        # phi0 on the committed transport t -> t(q_next), sigma on the
+        # transport t -> t((q + q_next)/2) the step energy sees
+        gt = -(phi0[:, None] * hol(t, tangents(q_next)[0])
+               + sigma[:, None] * hol(t, tangents(0.5 * (q + q_next))[0])
+               + phi[:, None] * hol(tangents(q_prev)[0], t))
+    else:
+        w = hol(t, tangents(q_next)[0]) + hol(tangents(q_prev)[0], t)
+        gt = -phi[:, None] * w
     g = (gt - np.sum(gt * t, axis=1)[:, None] * t) * il[:, None]
     want = gq0.copy()
     off, e0 = 0, 0
@@ -316,3 +348,33 @@ def test_frame_chain_kernel_matches_a_numpy_restatement():
     np.testing.assert_allclose(tphi.cpu().numpy(), phi, rtol=1e-13, atol=1e-13)
     np.testing.assert_allclose(tgq0.cpu().numpy(), want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
     assert np.any(fixed[th])  # the clamped first twist angles are exercised
+
+
+def test_step_adjoint_rods_in_contact_on_the_ground_matches_oracle_adjoint():
+    """Two rods of one contact group lying across each other on the ground
+    (edge-edge contact without pair friction, ground contact with friction):
+    the transposed contact LU with the ground terms, and the ground
+    friction's dependence on x_n, against the oracle's adjoint."""
+    from test_gpu_contact import _crossing_rods_on_ground, _oracle_active_pairs
+    desc, params = _crossing_rods_on_ground()
+    params = dict(params, pair_mu=0.0)
+    gpu = _gpu(desc, params)
+    ora = OracleSystems(desc, params)
+    for _ in range(5):
+        ora.step(1)
+    q0, v0 = ora.get_state()
+    d1, beta = ora.get_frames()
+    ora.step(1)
+    assert _oracle_active_pairs(ora, params) > 0
+    q1, _ = ora.get_state()
+    rng = np.random.default_rng(11)
+    wq, wv = rng.normal(size=len(q0)), rng.normal(size=len(q0))
+    ora.set_state(q0, v0)
+    ora.set_frames(d1, beta)
+    ok, oq, ov = step_adjoint(ora, q1, wq, wv)
+    gpu.set_state(q0, v0)
+    gpu.set_frames(d1, beta)
+    gk, gq, gv = gpu.step_adjoint(q1, wq, wv)
+    for a, b in ((gk, ok), (gq, oq), (gv, ov)):
+        scale = max(1.0, float(np.abs(b).max()))
+        assert np.abs(a - b).max() <= 1e-8 * scale, np.abs(a - b).max() / scale

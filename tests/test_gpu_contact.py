@@ -76,8 +76,6 @@ def test_contact_options_rejected():
     desc, params, _ = workloads.coil(N=20)
     with pytest.raises(DismechError):
         System(desc, dict(params, pair_mu=-0.3))
-    with pytest.raises(DismechError):
-        System(desc, dict(params, ground=True))
 
 
 def test_coil_contact_with_friction_per_step():
@@ -101,3 +99,48 @@ def test_coil_contact_with_friction_per_step():
         gpu.set_state(qo, vo)
         gpu.set_frames(d1, beta)
     assert touched >= 5
+
+
+def _crossing_rods_on_ground(N=12, h=1e-3, delta=5e-4):
+    # two free rods of one contact group dropped on the ground, the upper one
+    # crossing the lower one and sliding along it: ground contact with
+    # friction and edge-edge contact with friction act together
+    import math
+    L = 0.1
+    s = np.linspace(-L / 2, L / 2, N)
+    xa = np.stack([s, np.zeros(N), np.full(N, h + 1e-4)], 1)
+    xb = np.stack([np.full(N, 0.01), s, np.full(N, 3 * h + 2e-4)], 1)
+    v0 = np.zeros((2 * N, 3))
+    v0[N:, 0] = 0.05
+    rho, E = 1000.0, 1e6
+    kc = 50.0 * rho * math.pi * h * h * (L / (N - 1)) * 9.81 / delta  # reading C11
+    desc = dict(nodes_per_rod=[N, N], x0=np.concatenate([xa, xb]), v0=v0, E=[E, E],
+                nu=[0.5, 0.5], rho=[rho, rho], radius=[h, h],
+                fixed=np.zeros(2 * (4 * N - 1), np.uint8), ground_mu=[0.5, 0.5],
+                ground_kc=[kc, kc], contact_groups=[[0, 1]])
+    params = dict(dt=1e-3, tol=1e-10, max_iter=100, g=(0.0, 0.0, -9.81), eta=0.05,
+                  ground=True, ground_z=0.0, delta=delta, nu_slip=1e-3, self_contact=True,
+                  pair_kc=E * h, pair_mu=0.4, line_search=True)
+    return desc, params
+
+
+def test_edge_contact_together_with_ground_contact_per_step():
+    desc, params = _crossing_rods_on_ground()
+    gpu = _gpu(desc, params)
+    ora = OracleSystems(desc, params)
+    npr = desc["nodes_per_rod"]
+    touching = 0
+    for k in range(20):
+        gpu.step(1)
+        st = ora.step(1)
+        assert all(x[0] == 0 for x in st), st
+        qg, _ = gpu.get_state()
+        qo, vo = ora.get_state()
+        _assert_close(qg, qo, npr, 1.0, 1e-10)
+        ng, no = gpu.contact_pairs(), _oracle_active_pairs(ora, params)
+        assert ng == no, (k, ng, no)
+        touching += no > 0
+        d1, beta = ora.get_frames()
+        gpu.set_state(qo, vo)
+        gpu.set_frames(d1, beta)
+    assert touching >= 10

@@ -78,10 +78,11 @@ def test_midpoint_contact_coil_per_step():
     assert touched >= 3
 
 
-def test_midpoint_uneven_rods_trajectory():
+@pytest.mark.parametrize("predictor", ["extrapolate", "projected"])
+def test_midpoint_uneven_rods_trajectory(predictor):
     desc, params, kbar = workloads.uneven_rods(n_rods=4096, seed=2)
     sub, kb = workloads.subset(desc, [5, 77, 1031, 2500, 4000], kbar)
-    params = dict(params, integrator="midpoint")
+    params = dict(params, integrator="midpoint", predictor=predictor)
     gpu = _gpu(sub, params)
     ora = OracleSystems(sub, params)
     R = len(sub["nodes_per_rod"])
@@ -98,18 +99,6 @@ def test_midpoint_uneven_rods_trajectory():
     # velocities: qdot_{n+1} = 2 (q_{n+1} - q_n)/dt - qdot_n on both sides
     scale = max(1.0, float(np.abs(vo).max()))
     assert np.abs(vg - vo).max() <= 1e-6 * scale
-
-
-def test_midpoint_adjoint_rejected():
-    from paper_2311_18126_gb300 import DismechError
-    desc, params = workloads.cantilever(N=10)
-    gpu = _gpu(desc, dict(params, integrator="midpoint"))
-    q, v = gpu.get_state()
-    gpu.step(1)
-    q1, _ = gpu.get_state()
-    gpu.set_state(q, v)
-    with pytest.raises(DismechError):
-        gpu.step_adjoint(q1, np.zeros_like(q), np.zeros_like(q))
 
 
 def test_midpoint_divergence_matches_oracle_and_line_search_recovers():
