@@ -160,6 +160,10 @@ struct Extra {
   // Newton rounds as one CUDA graph: a device-side while loop over rounds
   bool graphs = true;
   cudaStream_t cap_stream = nullptr;
+  // a side branch of a round (the ground-contact node terms, independent of
+  // the edge and stencil kernels), forked and joined by events
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t round_graph = nullptr;
   cudaGraphExec_t first_graph = nullptr;            // the fused first round of a step
   int64_t first_launches[DM_NUM_KERNELS] = {};
@@ -642,6 +646,9 @@ void dm_destroy(dm_system *sys) {
   if (sx->x.first_graph) cudaGraphExecDestroy(sx->x.first_graph);
   long_rods_free(sx->x.longr);
   if (sx->x.cap_stream) cudaStreamDestroy(sx->x.cap_stream);
+  if (sx->x.side_stream) cudaStreamDestroy(sx->x.side_stream);
+  if (sx->x.ev_fork) cudaEventDestroy(sx->x.ev_fork);
+  if (sx->x.ev_join) cudaEventDestroy(sx->x.ev_join);
   dm::ws_free(sys->ws);
   delete static_cast<dm_system_ext *>(sys);
 }
@@ -796,6 +803,14 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   // rejected)
   const bool split = !gen_on;
   const bool fuse_first = split && !ws_on;
+  // the node terms run beside the edge and stencil kernels (not while
+  // profiling, whose events time each kernel alone)
+  const bool fork_nodes = T.ground && !s->x.prof;
+  if (fork_nodes && !s->x.side_stream) {
+    DM_CK(cudaStreamCreateWithFlags(&s->x.side_stream, cudaStreamNonBlocking));
+    DM_CK(cudaEventCreateWithFlags(&s->x.ev_fork, cudaEventDisableTiming));
+    DM_CK(cudaEventCreateWithFlags(&s->x.ev_join, cudaEventDisableTiming));
+  }
   // One Newton round: every phase's launches, in stream order on rs.
   auto round = [&](cudaStream_t rs, int it, bool first) -> dm_status {
     const bool sp = split && !first;
@@ -803,12 +818,19 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     s->x.launches[K_BEGIN]++;
     DM_CK(cudaMemsetAsync(d.ctrl, 0, sizeof(int32_t), rs));
     DM_CK(cudaMemsetAsync(d.ctrl + 3, 0, sizeof(int32_t), rs));
+    if (fork_nodes) {
+      DM_CK(cudaEventRecord(s->x.ev_fork, rs));
+      DM_CK(cudaStreamWaitEvent(s->x.side_stream, s->x.ev_fork, 0));
+      k_nodes<<<blocks(nn, 256), 256, 0, s->x.side_stream>>>(na);
+      s->x.launches[K_NODES]++;
+      DM_CK(cudaEventRecord(s->x.ev_join, s->x.side_stream));
+    }
     {
       Timed t(s, K_EDGE, rs);
       const int tb = s->x.tune.edge_threads;
       k_edge<<<blocks(ne, tb), tb, 0, rs>>>(ea);
     }
-    if (T.ground) {
+    if (T.ground && !fork_nodes) {
       Timed t(s, K_NODES, rs);
       k_nodes<<<blocks(nn, 256), 256, 0, rs>>>(na);
     }
@@ -828,6 +850,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       kf.units = s->x.prof ? s->x.d_units + K_FUSED : nullptr;
       k_stencil<<<st_grid, st_tb, 0, rs>>>(kf);
     }
+    if (fork_nodes) DM_CK(cudaStreamWaitEvent(rs, s->x.ev_join, 0));  // the node terms are in
     if (contact_on) {
       Timed t(s, K_CONTACT, rs);
       const auto &c = s->x.cc;
@@ -860,9 +883,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       k_rows_gen<<<blocks(nd, 256), 256, 0, rs>>>(rg);
     }
     if (ls_on) {
-      k_ls_merit<<<blocks((int64_t)S * 32, 128), 128, 0, rs>>>(la);
-      k_ls_decide<<<blocks(S, 128), 128, 0, rs>>>(la);
-      k_ls_apply<<<blocks(nd, 256), 256, 0, rs>>>(la);
+      k_line_search<<<blocks((int64_t)S * 32, 128), 128, 0, rs>>>(la);
       if (ws_trial && it == 0) DM_CK(ws_inject(s, rs, s->x.ls_action, s->x.ls_trial));
     }
     if (sp && ns > 0) {

@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
 // right-hand sides in registers (rows lane, lane + 32, lane + 64).
 __global__ void __launch_bounds__(kGenBorderThreads) k_gen_border(SolveGenArgs a) {
   extern __shared__ double sm[];
-  __shared__ int flag[4];  // go, bad, pivot row, pivot ok
+  __shared__ int flag[4];  // go, bad, -, pivot ok
   const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = blockDim.x;
   if (w >= a.ngen || !a.gs_fast[w]) return;  // block-uniform
@@ -319,6 +319,7 @@ __global__ void __launch_bounds__(kGenBorderThreads) k_gen_border(SolveGenArgs a
   }
   if (go && !bad && nB > 0) {
     for (int j = 0; j < nB; ++j) {
+      // warp 0: pivot search, row swap, reciprocal and multipliers
       if (warp == 0) {
         double best = -1.0;
         int bi = j;
@@ -338,32 +339,33 @@ __global__ void __launch_bounds__(kGenBorderThreads) k_gen_border(SolveGenArgs a
             bi = oi;
           }
         }
-        if (lane == 0) {
-          flag[2] = bi;
-          flag[3] = (best > 0.0) && isfinite(best);
+        const bool ok = (best > 0.0) && isfinite(best);
+        if (ok) {
+          if (bi != j)
+            for (int c = j + lane; c <= nB; c += 32) {
+              const double t = S[j * ld + c];
+              S[j * ld + c] = S[bi * ld + c];
+              S[bi * ld + c] = t;
+            }
+          __syncwarp();
+          const double rp = limb_recip(S[j * ld + j]);
+          if (lane == 0) rinv[j] = rp;
+          for (int i = j + 1 + lane; i < nB; i += 32) lm[i] = S[i * ld + j] * rp;
         }
+        if (lane == 0) flag[3] = ok;
       }
       __syncthreads();
-      const int pr = flag[2];
       if (!flag[3]) {
         bad = true;
         break;  // uniform
       }
-      if (pr != j)
-        for (int c = j + tid; c <= nB; c += nt) {
-          const double t = S[j * ld + c];
-          S[j * ld + c] = S[pr * ld + c];
-          S[pr * ld + c] = t;
-        }
-      __syncthreads();
-      const double rp = limb_recip(S[j * ld + j]);
-      if (tid == 0) rinv[j] = rp;
-      for (int i = j + 1 + tid; i < nB; i += nt) lm[i] = S[i * ld + j] * rp;
-      __syncthreads();
-      // rows j+1.., columns j+1..nB (the right-hand side included)
+      // rows j+1.., columns j+1..nB (the right-hand side included); the row
+      // of entry e by a float reciprocal: the quotient is below 96 and at
+      // least 0.5/96 from an integer, its float error below 2e-5
       const int nc = nB - j;
+      const float inv = 1.0f / (float)nc;
       for (int e = tid; e < (nB - j - 1) * nc; e += nt) {
-        const int r = e / nc;
+        const int r = (int)(((float)e + 0.5f) * inv);
         const int i = j + 1 + r, c = j + 1 + e - r * nc;
         S[i * ld + c] = fma(-lm[i], S[j * ld + c], S[i * ld + c]);
       }

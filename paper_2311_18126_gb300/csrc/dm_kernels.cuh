@@ -215,9 +215,7 @@ __global__ void k_adj_midpoint_in(int nd, const uint8_t *fixed, const double *qn
 __global__ void k_adj_midpoint_out(int nd, const uint8_t *fixed, const double *gq2,
                                    const double *gv2, double *gq0, double *gv0);
 
-__global__ void k_ls_merit(LineSearchArgs a);
-__global__ void k_ls_decide(LineSearchArgs a);
-__global__ void k_ls_apply(LineSearchArgs a);
+__global__ void k_line_search(LineSearchArgs a);  // one warp per system
 
 __global__ void k_nodes(NodeArgs a);
 __global__ void k_rows_gen(RowGenArgs a);

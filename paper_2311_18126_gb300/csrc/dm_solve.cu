@@ -674,13 +674,14 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
 // Line search (optional): Armijo test on the 2-norm of the scaled residual
 // |f_i| / (D_i l_i) of each system (the Newton direction is a descent
 // direction for it); a trial point without sufficient decrease is pulled
-// halfway back to the last accepted iterate, at most 12 times.
-// k_ls_merit: one warp per system, fixed summation order (deterministic).
-__global__ void k_ls_merit(LineSearchArgs a) {
-  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// halfway back to the last accepted iterate, at most 12 times.  One warp per
+// system: the merit in a fixed summation order (deterministic), the
+// decision by lane 0, then the move (or the new accepted iterate) over the
+// system's DOFs.
+__global__ void k_line_search(LineSearchArgs a) {
+  const int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (s >= a.nsys) return;
-  if (!a.sys_active[s]) return;
+  if (s >= a.nsys || !a.sys_active[s]) return;  // warp-uniform
   const int d0 = a.sys_dof0[s], n = a.sys_ndof[s];
   double acc = 0.0;
   for (int i = lane; i < n; i += 32) {
@@ -689,45 +690,44 @@ __global__ void k_ls_merit(LineSearchArgs a) {
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) a.merit[s] = sqrt(acc);
-}
-
-__global__ void k_ls_decide(LineSearchArgs a) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= a.nsys || !a.sys_active[s]) return;
-  const double m = a.merit[s];
-  if (a.wstry && a.wstry[s]) {
-    // the learned guess is kept only if it lowers the merit below that of
-    // the extrapolation; otherwise the iterate returns to the extrapolation
-    a.wstry[s] = 0;
-    if (!(m <= (1.0 - 1e-4) * a.racc[s])) {
-      a.action[s] = 1;
-      a.alpha[s] = 0.0;
-      a.trial[s] = 0;
-      a.nback[s] = 0;
-      return;
+  int action = 0;
+  double alpha = 1.0;
+  if (lane == 0) {
+    const double m = sqrt(acc);
+    a.merit[s] = m;
+    bool done = false;
+    if (a.wstry && a.wstry[s]) {
+      // the learned guess is kept only if it lowers the merit below that of
+      // the extrapolation; otherwise the iterate returns to the extrapolation
+      a.wstry[s] = 0;
+      if (!(m <= (1.0 - 1e-4) * a.racc[s])) {
+        action = 1;
+        alpha = 0.0;
+        a.trial[s] = 0;
+        a.nback[s] = 0;
+        done = true;
+      }
     }
+    if (!done) {
+      if (a.trial[s] && a.nback[s] < 12 && !(m <= (1.0 - 1e-4 * a.alpha[s]) * a.racc[s])) {
+        action = 1;
+        alpha = 0.5 * a.alpha[s];
+        a.nback[s] += 1;
+      } else {
+        a.trial[s] = 0;
+        a.nback[s] = 0;
+        a.racc[s] = m;
+      }
+    }
+    a.action[s] = action;
+    a.alpha[s] = alpha;
   }
-  if (a.trial[s] && a.nback[s] < 12 && !(m <= (1.0 - 1e-4 * a.alpha[s]) * a.racc[s])) {
-    a.action[s] = 1;
-    a.alpha[s] *= 0.5;
-    a.nback[s] += 1;
-  } else {
-    a.action[s] = 0;
-    a.trial[s] = 0;
-    a.nback[s] = 0;
-    a.alpha[s] = 1.0;
-    a.racc[s] = m;
+  action = __shfl_sync(0xffffffffu, action, 0);
+  alpha = __shfl_sync(0xffffffffu, alpha, 0);
+  for (int i = d0 + lane; i < d0 + n; i += 32) {
+    if (action == 1) a.q[i] = alpha == 0.0 ? a.qacc[i] : 0.5 * (a.q[i] + a.qacc[i]);
+    else a.qacc[i] = a.q[i];
   }
-}
-
-__global__ void k_ls_apply(LineSearchArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.nd) return;
-  const int s = a.dof_sys[i];
-  if (!a.sys_active[s]) return;
-  if (a.action[s] == 1) a.q[i] = a.alpha[s] == 0.0 ? a.qacc[i] : 0.5 * (a.q[i] + a.qacc[i]);
-  else a.qacc[i] = a.q[i];
 }
 
 }  // namespace dm
