@@ -48,6 +48,7 @@ FP64_FLOPS_PER_UNIT = {
     "residual_jacobian_rows": None,
 }
 UNIT_NAME = {"bend_twist_gradient": "stencil", "bend_twist_hessian": "stencil",
+             "limb_schur_solve": "DOF",
              "edge_frames_stretch": "edge", "residual_rows": "DOF row",
              "jacobian_band_rows": "DOF row", "band_ldlt_solve": "DOF",
              "bend_twist_fused": "stencil", "residual_jacobian_rows": "DOF row",
@@ -70,6 +71,16 @@ def _load_counts():
         d = json.load(open(p))
         for k, v in d.get("flops_per_unit", {}).items():
             FP64_FLOPS_PER_UNIT[k] = v
+
+
+def launch_shapes(sysm, args):
+    """Launch shapes: given (--tuning, a dict of autotune's fields), the
+    defaults (--no-autotune), or measured by the autotuner."""
+    if args.tuning:
+        t = json.loads(args.tuning)
+        sysm.set_tuning(t)
+        return dict(t, source="given")
+    return None if args.no_autotune else sysm.autotune(steps=2)
 
 
 def parse():
@@ -102,7 +113,11 @@ def parse():
     ap.add_argument("--integrator", default="be", choices=["be", "midpoint"],
                     help="backward Euler (default) or implicit midpoint (Sec. III-C)")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the default launch shapes (for profiler launch lists)")
+                    help="keep the default launch shapes")
+    ap.add_argument("--tuning", default=None,
+                    help="launch shapes to apply instead of autotuning (JSON object with the "
+                         "fields of the 'autotune' key of an earlier line), e.g. for profiler "
+                         "launch lists in the bench's own launch configuration")
     return ap.parse_args()
 
 
@@ -314,7 +329,7 @@ def run_ours(args):
             import torch.distributed as tdist
             tdist.barrier()
 
-    tuning = None if args.no_autotune else sysm.autotune(steps=2)
+    tuning = launch_shapes(sysm, args)
     for _ in range(args.warmup):
         sysm.step(1, stats=False)
     torch.cuda.synchronize()
@@ -489,10 +504,57 @@ def _timed_steps(sysm, steps, controls, k0, local, graphs=True, clocks=True):
     return e0.elapsed_time(e1), np.array(its), clk.stop() if clk else None
 
 
-def _kernel_table(prof):
+def _counts(workload):
+    """Per-unit FP64 flops and DRAM bytes by kernel name, counted by ncu on
+    this workload: the file's top level for the uneven-rods batch, its
+    "workloads" section for the others (none: no counts)."""
+    p = os.path.join(ROOT, "profiles", "kernel_fp64_counts.json")
+    if not os.path.exists(p):
+        return {}, {}
+    d = json.load(open(p))
+    if workload != "uneven_rods":
+        d = d.get("workloads", {}).get(workload, {})
+    return dict(d.get("flops_per_unit", {})), dict(d.get("dram_bytes_per_unit", {}))
+
+
+def _kernel_table(prof, fpu=None, bpu=None, peak_fp64=None):
+    """Per kernel: launches, units, time and share; with per-unit counts,
+    the achieved FP64 rate against the measured FP64 peak and the DRAM rate
+    from the counted bytes."""
     tot = sum(x[2] for x in prof.values()) or 1.0
-    return {k: {"launches": v[0], "units": v[1], "ms_total": round(v[2], 3),
-                "share": round(v[2] / tot, 4)} for k, v in prof.items()}
+    out = {k: {"launches": v[0], "units": v[1], "ms_total": round(v[2], 3),
+               "share": round(v[2] / tot, 4)} for k, v in prof.items()}
+    for k, v in prof.items():
+        f = (fpu or {}).get(k)
+        if f and v[1] and v[2] > 0 and peak_fp64:
+            rate = f * v[1] / (v[2] * 1e-3) / 1e12
+            out[k]["fp64_tflops"] = round(rate, 4)
+            out[k]["fp64_frac"] = round(rate / (peak_fp64 / 1e3), 4)
+        b = (bpu or {}).get(k)
+        if b and v[1] and v[2] > 0:
+            gbs = b * v[1] / (v[2] * 1e-3) / 1e9
+            out[k]["dram_gbs"] = round(gbs, 1)
+            out[k]["hbm_frac"] = round(gbs / HBM_PEAK, 4) if HBM_PEAK else None
+    return out
+
+
+def _roofline_fp64(prof, dom, fpu, bpu, peak_fp64):
+    """FP64 roofline object of kernel `dom` (achieved = counted flops per
+    unit x units / event time), or the latency-bound note without counts."""
+    launches, units, kms = prof[dom]
+    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": peak_fp64 / 1e3,
+            "peak_source": "measured FP64 FMA throughput (dm_fp64_peak_gflops, this run)",
+            "achieved": None, "frac": None, "traffic": None}
+    f, b = fpu.get(dom), bpu.get(dom)
+    if f and units and kms > 0:
+        ach = f * units / launches / (kms / launches * 1e-3) / 1e12
+        roof.update({"achieved": ach, "frac": ach / (peak_fp64 / 1e3), "flops_per_unit": f,
+                     "unit_name": UNIT_NAME.get(dom), "units_per_launch": units / launches})
+        if b:
+            roof["traffic"] = b * units / launches
+    else:
+        roof["note"] = "no per-unit counts for this kernel"
+    return roof
 
 
 def run_other(args):
@@ -593,7 +655,7 @@ def run_other(args):
         for label, model, pred in variants:
             sysm = System(desc, dict(params, predictor=pred))
             sysm.set_natural_curvature(0, R, controls(0))
-            tuning = None if args.no_autotune else sysm.autotune(steps=2)
+            tuning = launch_shapes(sysm, args)
             if model is not None:
                 sysm.ws_enable()
                 sysm.ws_set_model(model, norm)
@@ -659,7 +721,7 @@ def run_other(args):
         sysm = System(desc, params)
         if controls is not None:
             sysm.set_natural_curvature(0, R, controls(0))
-        tuning = None if args.no_autotune else sysm.autotune(steps=2)
+        tuning = launch_shapes(sysm, args)
         for k in range(warm):
             if controls is not None:
                 sysm.set_natural_curvature(0, R, controls(k))
@@ -708,6 +770,7 @@ def run_other(args):
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
         dom = max(prof, key=lambda k: prof[k][2])
+        fpu, bpu = _counts(args.workload)
         line.update({"value": value, "ms_per_step": ms / args.steps,
                      "newton": {"iters_mean": float(its.mean()), "iters_max": int(its.max()),
                                 "slowest_per_step_mean": float(its.max(1).mean())},
@@ -721,12 +784,8 @@ def run_other(args):
                                 "note": "host loop timed on the same steps from the same "
                                         "state"},
                      "autotune": tuning,
-                     "roofline": {"bound": "alu", "kernel": dom, "unit": "TFLOP/s",
-                                  "peak": peak_fp64 / 1e3, "achieved": None, "frac": None,
-                                  "traffic": None,
-                                  "note": "no per-unit counts for this kernel: latency bound "
-                                          "(few systems active in most Newton rounds)"},
-                     "kernels": _kernel_table(prof)})
+                     "roofline": _roofline_fp64(prof, dom, fpu, bpu, peak_fp64),
+                     "kernels": _kernel_table(prof, fpu, bpu, peak_fp64)})
         if args.workload in ("coil", "gripper"):
             line["contact_pairs"] = sysm.contact_pairs()
         sysm.close()
@@ -870,6 +929,9 @@ def run_mlp(args):
     clk = Clocks(local)
     clk.start()
     ms_f = timed(lambda: mlp.forward(X, out), args.steps)
+    mlp.set_fused(False)
+    ms_layers = timed(lambda: mlp.forward(X, out), args.steps)
+    mlp.set_fused(True)
     ms_t = timed(lambda: mlp.train_step(X[:B], Yt, 1e-4), args.steps)
     clocks = clk.stop()
     ms_f = max_over_ranks(ms_f, ws, "cuda")
@@ -901,11 +963,17 @@ def run_mlp(args):
             "clocks": clocks,
             "e2e": {"value": ws * M / (ms_e * 1e-3), "unit": "segments/s",
                     "h2d_bytes_per_step": M * 64 * 2, "d2h_bytes_per_step": M * 64 * 4},
-            "gpu_launches": 4 * args.steps,
-            "roofline": {"bound": "tensor", "kernel": "k_gemm_bf16 (4 layers)",
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "tensor", "kernel": "k_mlp_fused (4 layers, one launch)",
                          "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                          "peak_source": src, "flops_per_row": fwd, "rows_per_launch": M,
-                         "traffic": None},
+                         "traffic": None,
+                         "timing": "CUDA events around dm_mlp_forward calls (each also "
+                                   "reads its error word back)"},
+            "per_layer_gemms": {"ms": ms_layers,
+                                "tflops": fwd * M / (ms_layers * 1e-3) / 1e12,
+                                "note": "the same inference as four k_gemm_bf16 launches "
+                                        "through global memory"},
             "training": {"ms_per_step": ms_t, "samples_per_s": B / (ms_t * 1e-3),
                          "tflops": ach_t, "frac": ach_t / peak,
                          "note": "forward + backward (data and weight gradients) + Adam"}}

@@ -324,8 +324,13 @@ void dm_mlp_destroy(dm_mlp *m);
 int64_t dm_mlp_num_params(void);
 dm_status dm_mlp_get_params(dm_mlp *m, float *host);
 dm_status dm_mlp_set_params(dm_mlp *m, const float *host);
-/* Y [M][64] = network(X) (fp32, columns >= out_dim are zero). */
+/* Y [M][64] = network(X) (fp32, columns >= out_dim are zero).  By default
+ * one persistent kernel runs the four layers per 128-row tile on chip (TMA
+ * loads with 128-byte swizzle, the hidden activations in shared memory);
+ * dm_mlp_set_fused(m, 0) switches inference (and the warm start's) to one
+ * GEMM launch per layer through global memory, with the same arithmetic. */
 dm_status dm_mlp_forward(dm_mlp *m, const void *X, float *Y, int32_t M);
+dm_status dm_mlp_set_fused(dm_mlp *m, int32_t enable);
 /* One Adam step (learning rate lr; lr = 0 computes gradients only) on the
  * mean squared error against Y [M][out_dim]; grads (device, optional) gets
  * the gradient in the parameter layout, loss the loss before the update. */
@@ -497,6 +502,16 @@ typedef struct dm_tuning {
  * learned warm start is enabled (DM_ERR_INVALID_ARG: it keeps a history of
  * the state).  Synchronises the stream. */
 dm_status dm_autotune(dm_system *sys, int32_t steps, dm_tuning *out);
+/* Applies launch shapes found by an earlier dm_autotune (for instance on
+ * another system of the same workload) without timing anything:
+ * edge_threads in {128, 256, 512}, stencil_threads in {32, 64, 128} with
+ * stencil_per_thread in {1, 2}, rows_threads in {64, 128, 256},
+ * solve_warps in {1, 2, 4} with solve_blocks_per_sm >= 1 within the rod
+ * solver's occupancy, limb_factor_warps and limb_back_warps in {1, 2, 4}
+ * within the shared memory of a block; us_per_launch is ignored.  Any other
+ * value: DM_ERR_INVALID_ARG, nothing changed.  The shapes of kernels the
+ * system does not launch are accepted and kept. */
+dm_status dm_set_tuning(dm_system *sys, const dm_tuning *t);
 dm_status dm_get_profile(dm_system *sys, dm_profile *out);
 const char *dm_kernel_name(int32_t id); /* "" for unused ids */
 

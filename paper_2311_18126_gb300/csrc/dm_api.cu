@@ -1336,6 +1336,56 @@ dm_status dm_adjoint_frame_chain(dm_system *sys, const double *q_prev, const dou
   return DM_OK;
 }
 
+dm_status dm_set_tuning(dm_system *sys, const dm_tuning *t) {
+  auto *s = static_cast<dm_system_ext *>(sys);
+  if (!s || !t) {
+    set_error("dm_set_tuning: NULL argument");
+    return DM_ERR_INVALID_ARG;
+  }
+  auto in = [](int v, std::initializer_list<int> set) {
+    for (int x : set)
+      if (v == x) return true;
+    return false;
+  };
+  int per_sm = 0;
+  const bool solve_ok =
+      in(t->solve_warps, {1, 2, 4}) && t->solve_blocks_per_sm >= 1 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, k_solve_rod, 32 * t->solve_warps,
+          (size_t)t->solve_warps * kSolveRodsPerWarp * kSolveRodDoubles * 8) == cudaSuccess &&
+      per_sm >= t->solve_blocks_per_sm;
+  // limb shapes beyond this system's shared-memory limit matter only if it
+  // has condensation-path limbs
+  const bool limb_ok = in(t->limb_factor_warps, {1, 2, 4}) && in(t->limb_back_warps, {1, 2, 4}) &&
+                       (s->x.n_fast == 0 || (t->limb_factor_warps <= s->x.wpb_factor_max &&
+                                             t->limb_back_warps <= s->x.wpb_back_max));
+  if (!in(t->edge_threads, {128, 256, 512}) || !in(t->stencil_threads, {32, 64, 128}) ||
+      !in(t->stencil_per_thread, {1, 2}) || !in(t->rows_threads, {64, 128, 256}) || !solve_ok ||
+      !limb_ok) {
+    set_error("dm_set_tuning: launch shape outside the autotuner's candidates");
+    return DM_ERR_INVALID_ARG;
+  }
+  auto &tu = s->x.tune;
+  tu.edge_threads = t->edge_threads;
+  tu.stencil_threads = t->stencil_threads;
+  tu.stencil_per_thread = t->stencil_per_thread;
+  tu.rows_threads = t->rows_threads;
+  set_solve_shape(s, t->solve_warps, t->solve_blocks_per_sm);
+  if (s->x.n_fast) {
+    s->x.wpb_factor = t->limb_factor_warps;
+    s->x.wpb_back = t->limb_back_warps;
+  }
+  if (s->x.first_graph) {  // launch shapes are baked into the graphs
+    cudaGraphExecDestroy(s->x.first_graph);
+    s->x.first_graph = nullptr;
+  }
+  if (s->x.round_graph) {
+    cudaGraphExecDestroy(s->x.round_graph);
+    s->x.round_graph = nullptr;
+  }
+  return DM_OK;
+}
+
 dm_status dm_autotune(dm_system *sys, int32_t steps, dm_tuning *out) {
   if (!sys || steps < 1) {
     set_error("dm_autotune: bad arguments");

@@ -19,6 +19,8 @@
 #include "dm_internal.h"
 
 namespace dm {
+cudaError_t launch_mlp_fused(int M, const void *X, const void *const W[4], const float *const b[4],
+                             float *Y, int *err, cudaStream_t st);
 cudaError_t launch_gemm_bf16(int M, int N, int K, const void *A, const void *B, const float *bias,
                              void *C, int relu, int out_f32, int *err, cudaStream_t st,
                              int ksplit = 1, float *work = nullptr);
@@ -161,6 +163,7 @@ struct dm_mlp {
   float *out32 = nullptr, *dY32 = nullptr, *d32 = nullptr;
   float *splitws = nullptr;  // split-K partial weight gradients [kMaxSplit][256][256]
   double *loss = nullptr;
+  bool fused = true;  // inference: the fused 4-layer kernel (else a GEMM per layer)
   int *err = nullptr;
   int64_t step = 0;
   std::vector<void *> allocs;
@@ -222,6 +225,10 @@ void refresh_bf16(dm_mlp *m) {
   }
 }
 
+// Inference into Y (NULL: the network's own output buffer): the fused
+// kernel, or the per-layer GEMMs followed by a copy to Y.
+cudaError_t infer(dm_mlp *m, const uint16_t *X, int M, float *Y = nullptr);
+
 cudaError_t forward(dm_mlp *m, const uint16_t *X, int M) {
   m->act[0] = const_cast<uint16_t *>(X);
   cudaError_t e = cudaSuccess;
@@ -232,6 +239,18 @@ cudaError_t forward(dm_mlp *m, const uint16_t *X, int M) {
                          last ? 1 : 0, m->err, m->stream);
   }
   return e;
+}
+
+cudaError_t infer(dm_mlp *m, const uint16_t *X, int M, float *Y) {
+  if (!m->fused) {
+    cudaError_t e = forward(m, X, M);
+    if (e == cudaSuccess && Y)
+      e = cudaMemcpyAsync(Y, m->out32, (size_t)M * kOut * 4, cudaMemcpyDeviceToDevice, m->stream);
+    return e;
+  }
+  const void *W[kLayers] = {m->Wh[0], m->Wh[1], m->Wh[2], m->Wh[3]};
+  const float *b[kLayers] = {m->b[0], m->b[1], m->b[2], m->b[3]};
+  return launch_mlp_fused(M, X, W, b, Y ? Y : m->out32, m->err, m->stream);
 }
 
 }  // namespace
@@ -246,7 +265,7 @@ float *mlp_forward_async(dm_mlp *m, const void *X, int M, cudaStream_t st, int *
   int *keep_err = m->err;
   m->stream = st;
   m->err = err;
-  const cudaError_t e = forward(m, (const uint16_t *)X, M);
+  const cudaError_t e = infer(m, (const uint16_t *)X, M);
   m->stream = keep;
   m->err = keep_err;
   return e == cudaSuccess ? m->out32 : nullptr;
@@ -356,6 +375,15 @@ dm_status dm_mlp_set_params(dm_mlp *m, const float *host) {
   return cudaStreamSynchronize(m->stream) == cudaSuccess ? DM_OK : DM_ERR_CUDA;
 }
 
+dm_status dm_mlp_set_fused(dm_mlp *m, int32_t enable) {
+  if (!m) {
+    set_error("dm_mlp_set_fused: NULL network");
+    return DM_ERR_INVALID_ARG;
+  }
+  m->fused = enable != 0;
+  return DM_OK;
+}
+
 // Forward pass: X [M][64] bf16 (device) -> Y [M][64] fp32 (device).
 dm_status dm_mlp_forward(dm_mlp *m, const void *X, float *Y, int32_t M) {
   if (!m || !X || !Y || M <= 0 || M % 128) {
@@ -364,8 +392,7 @@ dm_status dm_mlp_forward(dm_mlp *m, const void *X, float *Y, int32_t M) {
   }
   if (ensure_batch(m, M) != DM_OK) return DM_ERR_OOM;
   cudaMemsetAsync(m->err, 0, 4, m->stream);
-  if (forward(m, (const uint16_t *)X, M) != cudaSuccess) return DM_ERR_CUDA;
-  cudaMemcpyAsync(Y, m->out32, (size_t)M * kOut * 4, cudaMemcpyDeviceToDevice, m->stream);
+  if (infer(m, (const uint16_t *)X, M, Y) != cudaSuccess) return DM_ERR_CUDA;
   int h = 0;
   cudaMemcpyAsync(&h, m->err, 4, cudaMemcpyDeviceToHost, m->stream);
   if (cudaStreamSynchronize(m->stream) != cudaSuccess || h) {

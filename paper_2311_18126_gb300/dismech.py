@@ -110,6 +110,8 @@ def load_library(path=LIB_PATH):
     lib.dm_num_edges.restype = C.c_int64
     lib.dm_autotune.argtypes = [H, C.c_int32, C.POINTER(Tuning)]
     lib.dm_autotune.restype = C.c_int
+    lib.dm_set_tuning.argtypes = [H, C.POINTER(Tuning)]
+    lib.dm_set_tuning.restype = C.c_int
     lib.dm_set_graphs.argtypes = [H, C.c_int32]
     lib.dm_set_graphs.restype = C.c_int
     lib.dm_set_profiling.argtypes = [H, C.c_int32]
@@ -146,6 +148,8 @@ def load_library(path=LIB_PATH):
     lib.dm_mlp_set_params.restype = C.c_int
     lib.dm_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
     lib.dm_mlp_forward.restype = C.c_int
+    lib.dm_mlp_set_fused.argtypes = [C.c_void_p, C.c_int32]
+    lib.dm_mlp_set_fused.restype = C.c_int
     lib.dm_mlp_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
                                       C.c_void_p, C.POINTER(C.c_double)]
     lib.dm_mlp_train_step.restype = C.c_int
@@ -386,6 +390,14 @@ class System:
                                         [round(float(x), 2) for x in t.us_per_launch[:6]]))
         return out
 
+    def set_tuning(self, tuning):
+        """Applies launch shapes returned by autotune() (a dict with the
+        Tuning fields; us_per_launch is ignored) without timing anything."""
+        t = Tuning()
+        for f in TUNING_FIELDS:
+            setattr(t, f, int(tuning[f]))
+        _check(self._lib.dm_set_tuning(self._h, C.byref(t)))
+
     def set_graphs(self, enable=True):
         """Newton rounds as one CUDA graph per step (default) or host-driven."""
         _check(self._lib.dm_set_graphs(self._h, int(bool(enable))))
@@ -615,6 +627,10 @@ class MLP:
 
     def forward(self, X, Y):
         _check(self._lib.dm_mlp_forward(self._h, _dev_ptr(X), _dev_ptr(Y), X.shape[0]))
+
+    def set_fused(self, enable=True):
+        """Inference by the fused 4-layer kernel (default) or a GEMM per layer."""
+        _check(self._lib.dm_mlp_set_fused(self._h, int(bool(enable))))
         return Y
 
     def train_step(self, X, Y, lr, grads=None):

@@ -133,3 +133,26 @@ def test_autotune_keeps_state_and_results(kind):
             assert np.abs(qa - qb).max() <= 1e-12 * max(1.0, np.abs(qb).max())
     a.close()
     b.close()
+
+
+def test_set_tuning_applies_shapes_and_rejects_others():
+    """dm_set_tuning: an autotuned shape applied to a second system of the
+    same workload steps it bit for bit like the tuned one; a shape outside
+    the candidate sets is rejected and changes nothing."""
+    from paper_2311_18126_gb300 import DismechError
+    desc, params, kbar = workloads.uneven_rods(n_rods=512, seed=2)
+    a, b = _gpu(desc, params), _gpu(desc, params)
+    for s in (a, b):
+        s.set_natural_curvature(0, s.n_rods, kbar)
+        s.step(1)
+    tune = a.autotune(steps=2)
+    b.set_tuning(tune)
+    bad = dict(tune, stencil_threads=96)
+    with pytest.raises(DismechError):
+        b.set_tuning(bad)
+    for k in range(3):
+        a.step(1)
+        b.step(1)
+        assert np.array_equal(a.get_state()[0], b.get_state()[0])
+    a.close()
+    b.close()
