@@ -328,8 +328,15 @@ dm_status dm_mlp_set_params(dm_mlp *m, const float *host);
  * one persistent kernel runs the four layers per 128-row tile on chip (TMA
  * loads with 128-byte swizzle, the hidden activations in shared memory);
  * dm_mlp_set_fused(m, 0) switches inference (and the warm start's) to one
- * GEMM launch per layer through global memory, with the same arithmetic. */
+ * GEMM launch per layer through global memory, with the same arithmetic.
+ * dm_mlp_forward synchronises the network's stream and reports a
+ * tensor-core barrier timeout (DM_ERR_CUDA); dm_mlp_forward_async only
+ * enqueues the work (X and Y must stay valid until it has run), and
+ * dm_mlp_check synchronises and reports (and clears) a timeout of any
+ * earlier asynchronous call. */
 dm_status dm_mlp_forward(dm_mlp *m, const void *X, float *Y, int32_t M);
+dm_status dm_mlp_forward_async(dm_mlp *m, const void *X, float *Y, int32_t M);
+dm_status dm_mlp_check(dm_mlp *m);
 dm_status dm_mlp_set_fused(dm_mlp *m, int32_t enable);
 /* One Adam step (learning rate lr; lr = 0 computes gradients only) on the
  * mean squared error against Y [M][out_dim]; grads (device, optional) gets

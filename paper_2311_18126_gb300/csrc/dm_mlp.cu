@@ -385,21 +385,40 @@ dm_status dm_mlp_set_fused(dm_mlp *m, int32_t enable) {
 }
 
 // Forward pass: X [M][64] bf16 (device) -> Y [M][64] fp32 (device).
-dm_status dm_mlp_forward(dm_mlp *m, const void *X, float *Y, int32_t M) {
+dm_status dm_mlp_forward_async(dm_mlp *m, const void *X, float *Y, int32_t M) {
   if (!m || !X || !Y || M <= 0 || M % 128) {
     set_error("dm_mlp_forward: M must be a positive multiple of 128");
     return DM_ERR_INVALID_ARG;
   }
-  if (ensure_batch(m, M) != DM_OK) return DM_ERR_OOM;
-  cudaMemsetAsync(m->err, 0, 4, m->stream);
-  if (infer(m, (const uint16_t *)X, M, Y) != cudaSuccess) return DM_ERR_CUDA;
-  int h = 0;
-  cudaMemcpyAsync(&h, m->err, 4, cudaMemcpyDeviceToHost, m->stream);
-  if (cudaStreamSynchronize(m->stream) != cudaSuccess || h) {
-    set_error("dm_mlp_forward: CUDA error or tensor-core barrier timeout");
+  // the per-layer path keeps every layer's activations
+  if (!m->fused && ensure_batch(m, M) != DM_OK) return DM_ERR_OOM;
+  if (infer(m, (const uint16_t *)X, M, Y) != cudaSuccess) {
+    set_error("dm_mlp_forward: launch failed");
     return DM_ERR_CUDA;
   }
   return DM_OK;
+}
+
+dm_status dm_mlp_check(dm_mlp *m) {
+  if (!m) {
+    set_error("dm_mlp_check: NULL network");
+    return DM_ERR_INVALID_ARG;
+  }
+  int h = 0;
+  cudaMemcpyAsync(&h, m->err, 4, cudaMemcpyDeviceToHost, m->stream);
+  const bool ok = cudaStreamSynchronize(m->stream) == cudaSuccess && !h;
+  cudaMemsetAsync(m->err, 0, 4, m->stream);
+  if (!ok) {
+    set_error("dm_mlp: CUDA error or tensor-core barrier timeout");
+    return DM_ERR_CUDA;
+  }
+  return DM_OK;
+}
+
+dm_status dm_mlp_forward(dm_mlp *m, const void *X, float *Y, int32_t M) {
+  dm_status st = dm_mlp_forward_async(m, X, Y, M);
+  if (st != DM_OK) return st;
+  return dm_mlp_check(m);
 }
 
 // One training step on a minibatch: forward, MSE loss on the first out_dim

@@ -8,18 +8,22 @@
 //     loads (cp.async.bulk.tensor, tensor maps with SWIZZLE_128B) for the
 //     input and the weights, and by the epilogue's swizzled stores for the
 //     activations;
-//   * layer 1's weights (256 x 64) stay resident; the 12 weight blocks of
-//     layers 2-4 per tile (4 x [256 x 64] of each hidden layer, 4 x [64 x 64]
-//     of the output layer) stream through a 3-stage ring from L2, loaded two
-//     blocks ahead of the tensor core;
-//   * one elected thread issues TMA and tcgen05.mma (M = 128, K = 16 per
-//     instruction, the accumulator of up to 256 fp32 columns in tensor
-//     memory); tcgen05.commit signals the ring's free slots and the end of a
-//     layer; the four warps read their 32 accumulator lanes back
-//     (tcgen05.ld), add the bias, apply ReLU, round to BF16 and store the
-//     next layer's operand, or write the FP32 output;
+//   * the output layer's weights (64 x 256) stay resident; the 9 weight
+//     blocks of layers 1-3 per tile ([256 x 64] each: layer 1's, then four
+//     K-blocks of each hidden layer) stream through a 3-stage ring from L2,
+//     loaded two blocks ahead of the tensor core;
+//   * warp 0 issues TMA and tcgen05.mma (M = 128, K = 16 per instruction;
+//     lane 0 issues, the whole warp takes the waits, so no lane of it spins
+//     while lane 0 has work); the hidden layers accumulate into 256 fp32
+//     columns of tensor memory, the output layer into 64 others;
+//     tcgen05.commit signals the ring's free slots and the end of a layer;
+//   * eight warps read the accumulator back (tcgen05.ld; warp w the lanes
+//     32 (w % 4).. and half w / 4 of the columns, all loads before one
+//     wait), add the bias, apply ReLU, round to BF16 and store the next
+//     layer's operand with the swizzle, or write the FP32 output;
 //   * the next tile's input is loaded as soon as layer 1 has consumed the
-//     current one.
+//     current one, and its layer 1 runs while the output of the current one
+//     is written.
 // Every mbarrier wait is bounded: on timeout the kernel records an error,
 // waits (bounded) for its copies in flight, frees its tensor memory and
 // returns.
@@ -38,17 +42,21 @@ namespace dm {
 namespace {
 
 constexpr int kTM = 128;  // rows per tile
-constexpr int kThreadsF = 128;
+constexpr int kThreadsF = 256;  // 8 warps: warp w reads lanes 32 (w % 4).., columns half w / 4
 constexpr int kStages = 3;
-constexpr int kBlocksPerTile = 12;  // weight blocks streamed per tile
+constexpr int kBlocksPerTile = 9;  // streamed weight blocks per tile: W1, 4 of W2, 4 of W3
 // shared memory map (bytes from a 1024-aligned base)
-constexpr int kOffW1 = 0;                       // [256][64] bf16: 32 KB
-constexpr int kOffH = kOffW1 + 256 * 128;       // 4 K-blocks of [128][64]: 64 KB
+constexpr int kOffW4 = 0;                       // 4 K-blocks of [64][64] bf16: 32 KB
+constexpr int kOffH = kOffW4 + 4 * 64 * 128;    // 4 K-blocks of [128][64]: 64 KB
 constexpr int kOffX = kOffH + 4 * kTM * 128;    // [128][64]: 16 KB
 constexpr int kOffRing = kOffX + kTM * 128;     // 3 x [256][64]: 96 KB
 constexpr int kStageBytes = 256 * 128;
-constexpr int kOffBar = kOffRing + kStages * kStageBytes;
+constexpr int kOffBias = kOffRing + kStages * kStageBytes;  // fp32 biases: 3 x 256 + 64
+constexpr int kOffBar = kOffBias + (3 * 256 + 64) * 4;
 constexpr int kSmemFused = kOffBar + 128 + 1024;  // barriers, TMEM slot, alignment slack
+constexpr uint32_t kTmemCols = 512;  // hidden accumulator at 0, output accumulator at 256
+
+constexpr unsigned kFullMask = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -67,9 +75,10 @@ __global__ void __launch_bounds__(kThreadsF, 1)
   extern __shared__ char smem_raw[];
   char *smem = reinterpret_cast<char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  char *W1s = smem + kOffW1, *Hs = smem + kOffH, *Xs = smem + kOffX, *Ring = smem + kOffRing;
+  char *W4s = smem + kOffW4, *Hs = smem + kOffH, *Xs = smem + kOffX, *Ring = smem + kOffRing;
+  float *sbias = reinterpret_cast<float *>(smem + kOffBias);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kOffBar);
-  uint64_t *bar_w1 = bar, *bar_x = bar + 1, *bar_mma = bar + 2;
+  uint64_t *bar_w4 = bar, *bar_x = bar + 1, *bar_mma = bar + 2;
   uint64_t *bar_full = bar + 3, *bar_free = bar + 3 + kStages;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 3 + 2 * kStages);
   volatile int *fail = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -80,7 +89,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(256));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -88,43 +97,90 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     *fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
+  for (int i = tid; i < 3 * 256 + 64; i += kThreadsF)
+    sbias[i] = i < 256 ? b1[i] : (i < 512 ? b2[i - 256] : (i < 768 ? b3[i - 512] : b4[i - 768]));
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = *tmem_slot, tmem_out = tmem + 256;
 
-  // weight block g of this CTA's stream: layer 2, 3 (blocks of [256][64]) or
-  // 4 ([64][64]), K-block g % 4
-  auto block_bytes = [](int b) { return b < 8 ? kStageBytes : 64 * 128; };
-  int issued = 0;      // weight blocks whose load was issued (thread 0)
-  int x_loads = 0;     // input tiles whose load was issued (thread 0)
+  // Warp 0 issues the copies and the MMAs: it runs the issue path as a
+  // whole (every lane takes the same waits, lane 0 issues), so that no lane
+  // of it spins on a barrier while lane 0 has work to do.
+  int issued = 0;      // weight blocks whose load was issued (warp 0)
+  int x_loads = 0;     // input tiles whose load was issued (warp 0)
   bool x_pending = false;
-  auto load_block = [&](int g) -> bool {  // thread 0
+  // weight block g of this CTA's stream: W1 (g % 9 == 0), else K-block
+  // (g % 9 - 1) % 4 of W2 (g % 9 <= 4) or W3
+  auto load_block = [&](int g) -> bool {  // warp 0
     const int s = g % kStages, b = g % kBlocksPerTile;
-    if (g >= kStages && !mbar_wait(&bar_free[s], (uint32_t)((g / kStages - 1) & 1))) return false;
-    mbar_expect_tx(&bar_full[s], (uint32_t)block_bytes(b));
-    const void *map = b < 4 ? (const void *)&tm_w2 : (b < 8 ? (const void *)&tm_w3 : (const void *)&tm_w4);
-    tma_load_2d(Ring + s * kStageBytes, map, 64 * (b % 4), 0, &bar_full[s]);
+    bool w = true;
+    if (g >= kStages) w = mbar_wait(&bar_free[s], (uint32_t)((g / kStages - 1) & 1));
+    if (!__all_sync(kFullMask, w)) return false;
+    if (lane == 0) {
+      mbar_expect_tx(&bar_full[s], (uint32_t)kStageBytes);
+      const void *map = b == 0 ? (const void *)&tm_w1 : (b <= 4 ? (const void *)&tm_w2 : (const void *)&tm_w3);
+      tma_load_2d(Ring + s * kStageBytes, map, b == 0 ? 0 : 64 * ((b - 1) % 4), 0, &bar_full[s]);
+    }
+    __syncwarp();
     issued = g + 1;
     return true;
   };
+  // warp 0: the MMAs of weight blocks g0 .. g0 + nb - 1 from the ring into
+  // the hidden accumulator, A = the input tile (layer 1) or the activations
+  // in H; the next loads two blocks ahead; then the layer's commit
+  auto ring_layer = [&](int g0, int nb, bool from_x) -> bool {
+    for (int b = 0; b < nb; ++b) {
+      const int g = g0 + b, s = g % kStages;
+      if (!__all_sync(kFullMask, mbar_wait(&bar_full[s], (uint32_t)((g / kStages) & 1))))
+        return false;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (lane == 0) {
+        const uint32_t a0 = smem_u32(from_x ? Xs : Hs + b * (kTM * 128));
+        const uint32_t w0 = smem_u32(Ring + s * kStageBytes);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma_bf16(tmem, make_desc(a0 + 32 * kk, 16, 1024, kSwizzle128B),
+                   make_desc(w0 + 32 * kk, 16, 1024, kSwizzle128B), make_idesc(kTM, 256),
+                   (b | kk) ? 1u : 0u);
+        mma_commit(&bar_free[s]);
+      }
+      __syncwarp();
+      if (g + 2 < total_blocks && !load_block(g + 2)) return false;
+    }
+    if (lane == 0) mma_commit(bar_mma);
+    __syncwarp();
+    return true;
+  };
+  // warp 0: layer 1 of local tile i (its input and W1 block must land)
+  auto issue_layer1 = [&](int i) -> bool {
+    if (!__all_sync(kFullMask, mbar_wait(bar_x, (uint32_t)(i & 1)))) return false;
+    x_pending = false;
+    return ring_layer(i * kBlocksPerTile, 1, true);
+  };
 
-  bool ok = true;
-  if (tid == 0 && my_tiles > 0) {
-    mbar_expect_tx(bar_w1, 256 * 128);
-    tma_load_2d(W1s, &tm_w1, 0, 0, bar_w1);
-    mbar_expect_tx(bar_x, kTM * 128);
-    tma_load_2d(Xs, &tm_x, 0, (int)blockIdx.x * kTM, bar_x);
+  if (warp == 0 && my_tiles > 0) {
+    if (lane == 0) {
+      mbar_expect_tx(bar_w4, 4 * 64 * 128);
+      for (int kb = 0; kb < 4; ++kb) tma_load_2d(W4s + kb * 64 * 128, &tm_w4, 64 * kb, 0, bar_w4);
+      mbar_expect_tx(bar_x, kTM * 128);
+      tma_load_2d(Xs, &tm_x, 0, (int)blockIdx.x * kTM, bar_x);
+    }
+    __syncwarp();
     x_pending = true;
     x_loads = 1;
-    for (int g = 0; g < 2 && g < total_blocks; ++g) ok = ok && load_block(g);
-    ok = ok && mbar_wait(bar_w1, 0);
-    if (!ok) *fail = 1;
+    bool w = true;
+    for (int g = 0; g < 2 && g < total_blocks; ++g) w = w && load_block(g);
+    w = w && __all_sync(kFullMask, mbar_wait(bar_w4, 0));
+    w = w && issue_layer1(0);
+    if (!w && lane == 0) *fail = 1;
   }
-  const uint32_t id256 = make_idesc(kTM, 256), id64 = make_idesc(kTM, 64);
+  __syncthreads();
+  bool ok = !*fail;
   uint32_t mma_phase = 0;
-  const int row = warp * 32 + lane;  // this thread's accumulator lane / tile row
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = quarter * 32 + lane;  // this thread's accumulator lane / tile row
+  const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
 
   // all threads: the end of a layer's MMAs (bounded), agreed by the block
   auto layer_done = [&]() -> bool {
@@ -134,101 +190,98 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     return w;
   };
-  // epilogue of a hidden layer: accumulator + bias, ReLU, BF16 into H
+  // epilogue of a hidden layer: accumulator + bias, ReLU, BF16 into H; the
+  // thread's row, columns [128 half, 128 half + 128) (eight loads from
+  // tensor memory, one wait)
   auto hidden_epilogue = [&](const float *bias) {
-#pragma unroll 1
-    for (int c0 = 0; c0 < 256; c0 += 16) {
-      uint32_t r[16];
-      tmem_ld16(trow + (uint32_t)c0, r);
-      uint32_t p[8];
+    const int cb = 128 * half;
+    uint32_t r[128];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float v0 = fmaxf(__uint_as_float(r[2 * j]) + __ldg(bias + c0 + 2 * j), 0.0f);
-        const float v1 = fmaxf(__uint_as_float(r[2 * j + 1]) + __ldg(bias + c0 + 2 * j + 1), 0.0f);
-        p[j] = pack_bf16(v0, v1);
+    for (int q = 0; q < 8; ++q) tmem_ld16_nowait(tmem + lane_off + (uint32_t)(cb + 16 * q), r + 16 * q);
+    tmem_wait();
+#pragma unroll
+    for (int kb = 0; kb < 2; ++kb) {
+      // K-block (cb + 64 kb) / 64 of H, this row's eight 16-byte chunks, swizzled
+      char *rowp = Hs + ((cb >> 6) + kb) * (kTM * 128) + row * 128;
+#pragma unroll
+      for (int ch = 0; ch < 8; ++ch) {
+        const int c = 64 * kb + 8 * ch;
+        const float4 bl = *reinterpret_cast<const float4 *>(bias + cb + c);
+        const float4 bh = *reinterpret_cast<const float4 *>(bias + cb + c + 4);
+        const float *a = reinterpret_cast<const float *>(r + c);
+        const uint32_t p0 = pack_bf16(fmaxf(a[0] + bl.x, 0.0f), fmaxf(a[1] + bl.y, 0.0f));
+        const uint32_t p1 = pack_bf16(fmaxf(a[2] + bl.z, 0.0f), fmaxf(a[3] + bl.w, 0.0f));
+        const uint32_t p2 = pack_bf16(fmaxf(a[4] + bh.x, 0.0f), fmaxf(a[5] + bh.y, 0.0f));
+        const uint32_t p3 = pack_bf16(fmaxf(a[6] + bh.z, 0.0f), fmaxf(a[7] + bh.w, 0.0f));
+        *reinterpret_cast<uint4 *>(rowp + ((ch ^ (row & 7)) << 4)) = make_uint4(p0, p1, p2, p3);
       }
-      // K-block c0 / 64, 16-byte chunks (c0 % 64) / 8 and the next, swizzled
-      char *rowp = Hs + (c0 >> 6) * (kTM * 128) + row * 128;
-      const int ch = (c0 & 63) >> 3;
-      *reinterpret_cast<uint4 *>(rowp + ((ch ^ (row & 7)) << 4)) = make_uint4(p[0], p[1], p[2], p[3]);
-      *reinterpret_cast<uint4 *>(rowp + (((ch + 1) ^ (row & 7)) << 4)) =
-          make_uint4(p[4], p[5], p[6], p[7]);
     }
     // the generic-proxy stores become visible to the tensor core's reads
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
   };
-  // thread 0: the MMAs of a streamed layer (4 weight blocks from g0 on), A
-  // the activations in H; the next loads two blocks ahead
-  auto streamed_layer = [&](int g0, uint32_t idesc) -> bool {
-    for (int b = 0; b < 4; ++b) {
-      const int g = g0 + b, s = g % kStages;
-      if (!mbar_wait(&bar_full[s], (uint32_t)((g / kStages) & 1))) return false;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(Hs + b * (kTM * 128)), w0 = smem_u32(Ring + s * kStageBytes);
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        mma_bf16(tmem, make_desc(a0 + 32 * kk, 16, 1024, kSwizzle128B),
-                 make_desc(w0 + 32 * kk, 16, 1024, kSwizzle128B), idesc, (b | kk) ? 1u : 0u);
-      mma_commit(&bar_free[s]);
-      if (g + 2 < total_blocks && !load_block(g + 2)) return false;
-    }
-    mma_commit(bar_mma);
-    return true;
-  };
 
   for (int i = 0; i < my_tiles && ok; ++i) {
     const int tile = (int)blockIdx.x + i * (int)gridDim.x;
     const int g0 = i * kBlocksPerTile;
-    // layer 1: A = the input tile, B = the resident weights
-    if (tid == 0 && !*fail) {
-      if (mbar_wait(bar_x, (uint32_t)(i & 1))) {
-        x_pending = false;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t a0 = smem_u32(Xs), w0 = smem_u32(W1s);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma_bf16(tmem, make_desc(a0 + 32 * kk, 16, 1024, kSwizzle128B),
-                   make_desc(w0 + 32 * kk, 16, 1024, kSwizzle128B), id256, kk ? 1u : 0u);
-        mma_commit(bar_mma);
-      } else {
-        *fail = 1;
-      }
-    }
+    // layer 1 was issued before (the prologue, or the previous tile)
     if (!(ok = layer_done())) break;
-    if (tid == 0 && i + 1 < my_tiles) {  // the input buffer is free: next tile's input
-      mbar_expect_tx(bar_x, kTM * 128);
-      tma_load_2d(Xs, &tm_x, 0, (tile + (int)gridDim.x) * kTM, bar_x);
+    if (warp == 0 && i + 1 < my_tiles) {  // the input buffer is free: next tile's input
+      if (lane == 0) {
+        mbar_expect_tx(bar_x, kTM * 128);
+        tma_load_2d(Xs, &tm_x, 0, (tile + (int)gridDim.x) * kTM, bar_x);
+      }
+      __syncwarp();
       x_pending = true;
       ++x_loads;
     }
-    hidden_epilogue(b1);
+    hidden_epilogue(sbias);
     // layers 2 and 3: A = H, B = streamed blocks
     for (int l = 0; l < 2 && ok; ++l) {
-      if (tid == 0 && !*fail && !streamed_layer(g0 + 4 * l, id256)) *fail = 1;
+      if (warp == 0 && !*fail && !ring_layer(g0 + 1 + 4 * l, 4, false) && lane == 0) *fail = 1;
       if (!(ok = layer_done())) break;
-      hidden_epilogue(l == 0 ? b2 : b3);
+      hidden_epilogue(sbias + 256 * (l + 1));
     }
     if (!ok) break;
-    // layer 4 (N = 64): FP32 output rows
-    if (tid == 0 && !*fail && !streamed_layer(g0 + 8, id64)) *fail = 1;
-    if (!(ok = layer_done())) break;
-    float *yrow = Y + ((size_t)tile * kTM + row) * 64;
-#pragma unroll 1
-    for (int c0 = 0; c0 < 64; c0 += 16) {
-      uint32_t r[16];
-      tmem_ld16(trow + (uint32_t)c0, r);
-      float4 *o = reinterpret_cast<float4 *>(yrow + c0);
+    // layer 4 (N = 64, resident weights) into the output accumulator
+    if (warp == 0 && !*fail) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (lane == 0) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        o[j] = make_float4(__uint_as_float(r[4 * j]) + __ldg(b4 + c0 + 4 * j),
-                           __uint_as_float(r[4 * j + 1]) + __ldg(b4 + c0 + 4 * j + 1),
-                           __uint_as_float(r[4 * j + 2]) + __ldg(b4 + c0 + 4 * j + 2),
-                           __uint_as_float(r[4 * j + 3]) + __ldg(b4 + c0 + 4 * j + 3));
+        for (int kb = 0; kb < 4; ++kb) {
+          const uint32_t a0 = smem_u32(Hs + kb * (kTM * 128)), w0 = smem_u32(W4s + kb * 64 * 128);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            mma_bf16(tmem_out, make_desc(a0 + 32 * kk, 16, 1024, kSwizzle128B),
+                     make_desc(w0 + 32 * kk, 16, 1024, kSwizzle128B), make_idesc(kTM, 64),
+                     (kb | kk) ? 1u : 0u);
+        }
+        mma_commit(bar_mma);
+      }
+      __syncwarp();
+    }
+    if (!(ok = layer_done())) break;
+    // the next tile's layer 1 (hidden accumulator) runs under this epilogue
+    if (warp == 0 && i + 1 < my_tiles && !issue_layer1(i + 1) && lane == 0) *fail = 1;
+    {
+      // the thread's row, columns [32 half, 32 half + 32) of the output
+      float *yrow = Y + ((size_t)tile * kTM + row) * 64 + 32 * half;
+      const float *bo = sbias + 768 + 32 * half;
+      uint32_t r[32];
+      tmem_ld16_nowait(tmem_out + lane_off + (uint32_t)(32 * half), r);
+      tmem_ld16_nowait(tmem_out + lane_off + (uint32_t)(32 * half + 16), r + 16);
+      tmem_wait();
+      float4 *o = reinterpret_cast<float4 *>(yrow);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float4 bb = *reinterpret_cast<const float4 *>(bo + 4 * j);
+        o[j] = make_float4(__uint_as_float(r[4 * j]) + bb.x, __uint_as_float(r[4 * j + 1]) + bb.y,
+                           __uint_as_float(r[4 * j + 2]) + bb.z, __uint_as_float(r[4 * j + 3]) + bb.w);
+      }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // the accumulator is read before the next tile's layer 1
+    __syncthreads();  // the output accumulator is read before the next tile's layer 4
   }
   if (!ok || *fail) {
     if (tid == 0) {
@@ -245,7 +298,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 namespace {

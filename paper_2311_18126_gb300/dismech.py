@@ -148,6 +148,10 @@ def load_library(path=LIB_PATH):
     lib.dm_mlp_set_params.restype = C.c_int
     lib.dm_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
     lib.dm_mlp_forward.restype = C.c_int
+    lib.dm_mlp_forward_async.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+    lib.dm_mlp_forward_async.restype = C.c_int
+    lib.dm_mlp_check.argtypes = [C.c_void_p]
+    lib.dm_mlp_check.restype = C.c_int
     lib.dm_mlp_set_fused.argtypes = [C.c_void_p, C.c_int32]
     lib.dm_mlp_set_fused.restype = C.c_int
     lib.dm_mlp_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
@@ -627,11 +631,20 @@ class MLP:
 
     def forward(self, X, Y):
         _check(self._lib.dm_mlp_forward(self._h, _dev_ptr(X), _dev_ptr(Y), X.shape[0]))
+        return Y
+
+    def forward_async(self, X, Y):
+        """Enqueues inference on the network's stream without synchronising;
+        check() reports a failure of it."""
+        _check(self._lib.dm_mlp_forward_async(self._h, _dev_ptr(X), _dev_ptr(Y), X.shape[0]))
+        return Y
+
+    def check(self):
+        _check(self._lib.dm_mlp_check(self._h))
 
     def set_fused(self, enable=True):
         """Inference by the fused 4-layer kernel (default) or a GEMM per layer."""
         _check(self._lib.dm_mlp_set_fused(self._h, int(bool(enable))))
-        return Y
 
     def train_step(self, X, Y, lr, grads=None):
         loss = C.c_double()

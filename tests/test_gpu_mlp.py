@@ -95,3 +95,14 @@ def test_fused_inference_equals_per_layer_gemms(M):
     net.set_fused(True)
     torch.cuda.synchronize()
     assert torch.equal(a, b), float((a - b).abs().max())
+
+
+def test_async_inference_matches_synchronous():
+    import torch
+    net, Xb, Y, tX, tY = _setup(M=512, seed=4)
+    a = torch.empty(512, 64, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    net.forward(tX, a)
+    net.forward_async(tX, b)
+    net.check()
+    assert torch.equal(a, b)
