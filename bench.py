@@ -114,6 +114,9 @@ def parse():
                     help="backward Euler (default) or implicit midpoint (Sec. III-C)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="mlp workload: rows of the inference batch (a multiple of 128; "
+                         "default the 444544 segments of the 4096-rod batch)")
     ap.add_argument("--tuning", default=None,
                     help="launch shapes to apply instead of autotuning (JSON object with the "
                          "fields of the 'autotune' key of an earlier line), e.g. for profiler "
@@ -902,7 +905,7 @@ def run_mlp(args):
     torch.cuda.set_device(local)
     from paper_2311_18126_gb300 import ensure_built, dismech as dmx
     ensure_built()
-    M = 444544            # 444456 segments of the 4096-rod batch, padded to 128
+    M = args.rows or 444544   # 444456 segments of the 4096-rod batch, padded to 128
     B = 16384             # training batch
     widths = [64, 256, 256, 256, 64]
     fwd = 2 * sum(a * b for a, b in zip(widths[:-1], widths[1:]))  # flops per row
