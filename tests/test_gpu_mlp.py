@@ -78,13 +78,13 @@ def test_training_reduces_loss():
     assert last < 0.1 * l0
 
 
-@pytest.mark.parametrize("M", [128, 256 * 152 + 384])
+@pytest.mark.parametrize("M", [128, 256 * 152 + 384, 444544])
 def test_fused_inference_equals_per_layer_gemms(M):
     """The fused 4-layer kernel (TMA, swizzled operands, activations in
     shared memory) against one GEMM launch per layer: the same BF16 rounding
     points, K blocks and tensor-core instruction shapes, so the outputs
-    agree bit for bit; M spans one tile and several tiles per CTA with a
-    ragged last round of tiles."""
+    agree bit for bit; M spans one tile, several tiles per CTA with a
+    ragged last round of tiles, and the bench's 444544 rows."""
     import torch
     net, Xb, Y, tX, tY = _setup(M=M, seed=3)
     a = torch.empty(M, 64, dtype=torch.float32, device="cuda")
