@@ -476,7 +476,7 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
       if (T.gs_fast[w]) {
         s->x.n_fast++;
         s->x.border_smem = std::max<size_t>(
-            s->x.border_smem, (size_t)(T.gs_nB[w] * (T.gs_nB[w] + 3)) * sizeof(double));
+            s->x.border_smem, (size_t)(T.gs_nB[w] * (T.gs_nB[w] + 4)) * sizeof(double));
       } else {
         s->x.n_slow++;
       }

@@ -8,8 +8,9 @@
 //      block A_m of the rows next to the border; with it the limb's Schur
 //      complement R_m A_m^{-1} C_m and right-hand side R_m A_m^{-1} y_m are
 //      subtracted from the border system (atomics on the system's matrix).
-//   2. k_gen_border (one warp per system): Newton bookkeeping for the system
-//      and the dense LU with partial pivoting of the border system.
+//   2. k_gen_border (a block per system): Newton bookkeeping for the system
+//      and the dense LU of the border system (in order, partial pivoting
+//      where a pivot is tiny).
 //   3. k_gen_limb_back (one warp per limb): the m condensed rows from the
 //      border values, then back substitution towards the free end; q += dq.
 //
@@ -36,6 +37,10 @@ namespace {
 constexpr int kRow = 22;        // 21 band entries and the right-hand side
 constexpr int kSmall = kFastMaxM * (kFastMaxM + kFastMaxBC + 1);  // condensed block
 constexpr unsigned kFull = 0xffffffffu;
+
+// Pivots of the border system's elimination in order smaller than this
+// fraction of their original diagonal entry send it to partial pivoting.
+constexpr double kTinyPivotB = 1e-13;
 
 // 1/d from an FP32 seed and two Newton steps in FP64; a division outside
 // the seed's range.
@@ -254,10 +259,13 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
 
 // The border system [S | r] (row-major, leading dimension nB + 1, right-hand
 // side in the last column) solved by a block of kGenBorderThreads: Gaussian
-// elimination with partial pivoting (the pivot search by warp 0, the
-// trailing update spread over all threads, one matrix entry per thread and
-// step), then a column-oriented back substitution by warp 0 with the
-// right-hand sides in registers (rows lane, lane + 32, lane + 64).
+// elimination in order, the trailing update spread over all threads (one
+// matrix entry per thread and step) and the next pivot's reciprocal taken by
+// the thread that updates it, so one barrier per column; a pivot below
+// kTinyPivotB of its original diagonal entry restarts the elimination with
+// partial pivoting (the pivot search, row swap and multipliers by warp 0).
+// Then a column-oriented back substitution by warp 0 with the right-hand
+// sides in registers (rows lane, lane + 32, lane + 64).
 __global__ void __launch_bounds__(kGenBorderThreads) k_gen_border(SolveGenArgs a) {
   extern __shared__ double sm[];
   __shared__ int flag[4];  // go, bad, -, pivot ok
@@ -299,77 +307,107 @@ __global__ void __launch_bounds__(kGenBorderThreads) k_gen_border(SolveGenArgs a
   bool bad = flag[1] != 0;
   const int nB = a.gs_nB[w];
   const int ld = nB + 1;
-  double *S = sm, *rinv = sm + (size_t)nB * ld, *lm = rinv + nB;
+  double *S = sm, *rinv = sm + (size_t)nB * ld, *lm = rinv + nB, *dorig = lm + nB;
   const int32_t *bd = a.border_dof + a.gs_border0[w];
-  if (go && nB > 0) {
-    // the border block and the limbs' Schur sums, left zero for the next
-    // round's assembly and atomics (the limb factors ran: go)
-    double *J = a.gen + a.gs_JBB[w];
-    double *acc = a.gen + a.gs_rB[w];
+  double *J = a.gen + a.gs_JBB[w];
+  double *acc = a.gen + a.gs_rB[w];
+  // the border block [S | r] from the assembled block and the limbs' Schur sums
+  auto load = [&]() {
     for (int e = tid; e < nB * nB; e += nt) {
       const int r = e / nB;
       S[r * ld + e - r * nB] = J[e];
-      J[e] = 0.0;
     }
-    for (int b = tid; b < nB; b += nt) {
-      S[b * ld + nB] = acc[b] - a.f[bd[b]];
-      acc[b] = 0.0;
+    for (int b = tid; b < nB; b += nt) S[b * ld + nB] = acc[b] - a.f[bd[b]];
+  };
+  if (go && !bad && nB > 0) {
+    load();
+    for (int b = tid; b < nB; b += nt) dorig[b] = fabs(J[b * nB + b]);
+    if (tid == 0) flag[3] = 1;
+    __syncthreads();
+    // first attempt: elimination in order, without pivoting; the thread that
+    // updates the next pivot takes its reciprocal (one barrier per column).
+    // A pivot below kTinyPivotB of its original diagonal entry, or not
+    // finite, abandons it for partial pivoting.
+    if (tid == 0) {
+      const double v = S[0];
+      if (!(fabs(v) > kTinyPivotB * dorig[0]) || !isfinite(v)) flag[3] = 0;
+      else rinv[0] = limb_recip(v);
     }
     __syncthreads();
-  }
-  if (go && !bad && nB > 0) {
-    for (int j = 0; j < nB; ++j) {
-      // warp 0: pivot search, row swap, reciprocal and multipliers
-      if (warp == 0) {
-        double best = -1.0;
-        int bi = j;
-        for (int i = j + lane; i < nB; i += 32) {
-          const double v = fabs(S[i * ld + j]);
-          if (v > best) {
-            best = v;
-            bi = i;
-          }
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-          const double ob = __shfl_xor_sync(kFull, best, o);
-          const int oi = __shfl_xor_sync(kFull, bi, o);
-          if (ob > best || (ob == best && oi < bi)) {
-            best = ob;
-            bi = oi;
-          }
-        }
-        const bool ok = (best > 0.0) && isfinite(best);
-        if (ok) {
-          if (bi != j)
-            for (int c = j + lane; c <= nB; c += 32) {
-              const double t = S[j * ld + c];
-              S[j * ld + c] = S[bi * ld + c];
-              S[bi * ld + c] = t;
-            }
-          __syncwarp();
-          const double rp = limb_recip(S[j * ld + j]);
-          if (lane == 0) rinv[j] = rp;
-          for (int i = j + 1 + lane; i < nB; i += 32) lm[i] = S[i * ld + j] * rp;
-        }
-        if (lane == 0) flag[3] = ok;
-      }
-      __syncthreads();
-      if (!flag[3]) {
-        bad = true;
-        break;  // uniform
-      }
-      // rows j+1.., columns j+1..nB (the right-hand side included); the row
-      // of entry e by a float reciprocal: the quotient is below 96 and at
-      // least 0.5/96 from an integer, its float error below 2e-5
+    for (int j = 0; j < nB && flag[3]; ++j) {
+      const double rp = rinv[j];
       const int nc = nB - j;
       const float inv = 1.0f / (float)nc;
       for (int e = tid; e < (nB - j - 1) * nc; e += nt) {
         const int r = (int)(((float)e + 0.5f) * inv);
         const int i = j + 1 + r, c = j + 1 + e - r * nc;
-        S[i * ld + c] = fma(-lm[i], S[j * ld + c], S[i * ld + c]);
+        const double v = fma(-(S[i * ld + j] * rp), S[j * ld + c], S[i * ld + c]);
+        S[i * ld + c] = v;
+        if (r == 0 && c == j + 1) {
+          if (!(fabs(v) > kTinyPivotB * dorig[j + 1]) || !isfinite(v)) flag[3] = 0;
+          else rinv[j + 1] = limb_recip(v);
+        }
       }
       __syncthreads();
+    }
+    if (!flag[3]) {
+      // partial pivoting on a fresh copy
+      __syncthreads();
+      load();
+      __syncthreads();
+      for (int j = 0; j < nB; ++j) {
+        // warp 0: pivot search, row swap, reciprocal and multipliers
+        if (warp == 0) {
+          double best = -1.0;
+          int bi = j;
+          for (int i = j + lane; i < nB; i += 32) {
+            const double v = fabs(S[i * ld + j]);
+            if (v > best) {
+              best = v;
+              bi = i;
+            }
+          }
+#pragma unroll
+          for (int o = 16; o; o >>= 1) {
+            const double ob = __shfl_xor_sync(kFull, best, o);
+            const int oi = __shfl_xor_sync(kFull, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+              best = ob;
+              bi = oi;
+            }
+          }
+          const bool ok = (best > 0.0) && isfinite(best);
+          if (ok) {
+            if (bi != j)
+              for (int c = j + lane; c <= nB; c += 32) {
+                const double t = S[j * ld + c];
+                S[j * ld + c] = S[bi * ld + c];
+                S[bi * ld + c] = t;
+              }
+            __syncwarp();
+            const double rp = limb_recip(S[j * ld + j]);
+            if (lane == 0) rinv[j] = rp;
+            for (int i = j + 1 + lane; i < nB; i += 32) lm[i] = S[i * ld + j] * rp;
+          }
+          if (lane == 0) flag[3] = ok;
+        }
+        __syncthreads();
+        if (!flag[3]) {
+          bad = true;
+          break;  // uniform
+        }
+        // rows j+1.., columns j+1..nB (the right-hand side included); the row
+        // of entry e by a float reciprocal: the quotient is below 96 and at
+        // least 0.5/96 from an integer, its float error below 2e-5
+        const int nc = nB - j;
+        const float inv = 1.0f / (float)nc;
+        for (int e = tid; e < (nB - j - 1) * nc; e += nt) {
+          const int r = (int)(((float)e + 0.5f) * inv);
+          const int i = j + 1 + r, c = j + 1 + e - r * nc;
+          S[i * ld + c] = fma(-lm[i], S[j * ld + c], S[i * ld + c]);
+        }
+        __syncthreads();
+      }
     }
     if (!bad && warp == 0) {
       double b0 = lane < nB ? S[lane * ld + nB] : 0.0;
@@ -393,6 +431,12 @@ __global__ void __launch_bounds__(kGenBorderThreads) k_gen_border(SolveGenArgs a
         a.q[bd[b]] += lm[b];
       }
     }
+  }
+  if (go && nB > 0) {
+    // the border block and the limbs' Schur sums, left zero for the next
+    // round's assembly and atomics (the limb factors ran: go)
+    for (int e = tid; e < nB * nB; e += nt) J[e] = 0.0;
+    for (int b = tid; b < nB; b += nt) acc[b] = 0.0;
   }
   if (tid == 0) {
     int g = go;
