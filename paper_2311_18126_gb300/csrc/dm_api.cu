@@ -883,7 +883,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
       k_rows_gen<<<blocks(nd, 256), 256, 0, rs>>>(rg);
     }
     if (ls_on) {
-      k_line_search<<<blocks((int64_t)S * 32, 128), 128, 0, rs>>>(la);
+      k_line_search<<<S, kLineSearchThreads, 0, rs>>>(la);
       if (ws_trial && it == 0) DM_CK(ws_inject(s, rs, s->x.ls_action, s->x.ls_trial));
     }
     if (sp && ns > 0) {

@@ -215,7 +215,8 @@ __global__ void k_adj_midpoint_in(int nd, const uint8_t *fixed, const double *qn
 __global__ void k_adj_midpoint_out(int nd, const uint8_t *fixed, const double *gq2,
                                    const double *gv2, double *gq0, double *gv0);
 
-__global__ void k_line_search(LineSearchArgs a);  // one warp per system
+constexpr int kLineSearchThreads = 128;
+__global__ void k_line_search(LineSearchArgs a);  // one block per system
 
 __global__ void k_nodes(NodeArgs a);
 __global__ void k_rows_gen(RowGenArgs a);

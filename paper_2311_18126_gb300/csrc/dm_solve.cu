@@ -674,27 +674,35 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
 // Line search (optional): Armijo test on the 2-norm of the scaled residual
 // |f_i| / (D_i l_i) of each system (the Newton direction is a descent
 // direction for it); a trial point without sufficient decrease is pulled
-// halfway back to the last accepted iterate, at most 12 times.  One warp per
-// system: the merit in a fixed summation order (deterministic), the
-// decision by lane 0, then the move (or the new accepted iterate) over the
+// halfway back to the last accepted iterate, at most 12 times.  One block
+// of kLineSearchThreads per system: the merit in a fixed summation order
+// (per-thread strided sums, then a fixed tree: deterministic), the decision
+// by thread 0, then the move (or the new accepted iterate) over the
 // system's DOFs.
-__global__ void k_line_search(LineSearchArgs a) {
-  const int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (s >= a.nsys || !a.sys_active[s]) return;  // warp-uniform
+__global__ void __launch_bounds__(kLineSearchThreads) k_line_search(LineSearchArgs a) {
+  __shared__ double part[kLineSearchThreads / 32];
+  __shared__ int s_action;
+  __shared__ double s_alpha;
+  const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (s >= a.nsys || !a.sys_active[s]) return;  // block-uniform
   const int d0 = a.sys_dof0[s], n = a.sys_ndof[s];
   double acc = 0.0;
-  for (int i = lane; i < n; i += 32) {
+  for (int i = tid; i < n; i += kLineSearchThreads) {
     const double v = a.f[d0 + i] * a.rscale[d0 + i];
     acc = fma(v, v, acc);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  int action = 0;
-  double alpha = 1.0;
-  if (lane == 0) {
-    const double m = sqrt(acc);
+  if (lane == 0) part[warp] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0;
+#pragma unroll
+    for (int w = 0; w < kLineSearchThreads / 32; ++w) tot += part[w];
+    const double m = sqrt(tot);
     a.merit[s] = m;
+    int action = 0;
+    double alpha = 1.0;
     bool done = false;
     if (a.wstry && a.wstry[s]) {
       // the learned guess is kept only if it lowers the merit below that of
@@ -721,10 +729,13 @@ __global__ void k_line_search(LineSearchArgs a) {
     }
     a.action[s] = action;
     a.alpha[s] = alpha;
+    s_action = action;
+    s_alpha = alpha;
   }
-  action = __shfl_sync(0xffffffffu, action, 0);
-  alpha = __shfl_sync(0xffffffffu, alpha, 0);
-  for (int i = d0 + lane; i < d0 + n; i += 32) {
+  __syncthreads();
+  const int action = s_action;
+  const double alpha = s_alpha;
+  for (int i = d0 + tid; i < d0 + n; i += kLineSearchThreads) {
     if (action == 1) a.q[i] = alpha == 0.0 ? a.qacc[i] : 0.5 * (a.q[i] + a.qacc[i]);
     else a.qacc[i] = a.q[i];
   }
