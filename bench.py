@@ -48,7 +48,9 @@ FP64_FLOPS_PER_UNIT = {
     "residual_jacobian_rows": None,
 }
 UNIT_NAME = {"bend_twist_gradient": "stencil", "bend_twist_hessian": "stencil",
-             "limb_schur_solve": "DOF",
+             "limb_schur_solve": "DOF", "ground_contact_friction": "node",
+             "contact_band_lu": "flop of the trailing updates",
+             "residual_rows_general": "DOF row", "assemble_general": "DOF",
              "edge_frames_stretch": "edge", "residual_rows": "DOF row",
              "jacobian_band_rows": "DOF row", "band_ldlt_solve": "DOF",
              "bend_twist_fused": "stencil", "residual_jacobian_rows": "DOF row",

@@ -721,6 +721,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
     ca.fc = c.fc; ca.dense = c.dense;
     ca.n_contact = c.n_contact; ca.cgo = c.cgo; ca.cbad = c.cbad;
     ca.nn = (int)T.n_nodes;
+    ca.lu_flops = s->x.prof ? s->x.d_units + K_SOLVE_CONTACT : nullptr;
   }
   // the Jacobian passes test convergence as the solvers do
   const int32_t *ls_act = s->prm.line_search ? s->x.ls_action : nullptr;
@@ -747,8 +748,10 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
                s->x.prof ? s->x.d_units + K_SOLVE : nullptr, s->x.ls_action, s->x.ls_trial};
   const int nn = (int)T.n_nodes;
   NodeArgs na{nn, s->p.dt, s->prm.ground_z, s->prm.delta, s->prm.slip_nu, d.q, d.qn,
-              d.node_dof_arr, d.node_sys, d.node_h, d.node_mu, d.node_kc, d.sys_active, d.nt};
+              d.node_dof_arr, d.node_sys, d.node_h, d.node_mu, d.node_kc, d.sys_active, d.nt,
+              s->x.prof ? s->x.d_units + K_NODES : nullptr};
   RowGenArgs rg{};
+  rg.units = s->x.prof ? s->x.d_units + K_ROWS_GEN : nullptr;
   rg.nd = nd; rg.ns = ns; rg.ne = ne; rg.nn = nn; rg.dt = s->p.dt;
   for (int c = 0; c < 3; ++c) rg.g[c] = s->p.g[c];
   rg.q = d.q; rg.qn = d.qn; rg.vn = d.vn; rg.mass = d.mass; rg.rscale = d.rscale;
@@ -759,7 +762,8 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   const bool ls_on = s->prm.line_search != 0;
   AsmArgs aa{(int)T.asm_target.size(), d.asm_target, d.asm_ptr, d.asm_src, d.sh, d.es, d.nt,
              d.dconst, d.gen, d.asm_sys, d.sys_active, ls_on ? s->x.ls_action : nullptr,
-             (int)T.gen_sys.size(), d.gen_sys, d.asm_t0, d.gs_mat0, d.gs_mat1};
+             (int)T.gen_sys.size(), d.gen_sys, d.asm_t0, d.gs_mat0, d.gs_mat1, d.sys_ndof,
+             s->x.prof ? s->x.d_units + K_ASM_GEN : nullptr};
   SolveGenArgs ga{};
   ga.ngen = (int)T.gen_sys.size(); ga.max_iter = s->p.max_iter; ga.tol = s->p.tol;
   ga.gen_sys = d.gen_sys; ga.gs_limb0 = d.gs_limb0; ga.gs_nlimb = d.gs_nlimb; ga.gs_nB = d.gs_nB;
@@ -1769,7 +1773,8 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
   if (ngen > 0) {
     AsmArgs aa{(int)T.asm_target.size(), d.asm_target, d.asm_ptr, d.asm_src, d.sh, d.es, d.nt,
                d.dconst, d.gen, d.asm_sys, d.sys_active, nullptr,
-               (int)T.gen_sys.size(), d.gen_sys, d.asm_t0, d.gs_mat0, d.gs_mat1};
+               (int)T.gen_sys.size(), d.gen_sys, d.asm_t0, d.gs_mat0, d.gs_mat1, d.sys_ndof,
+               nullptr};
     if (s->x.n_slow) k_gen_clear_slow<<<aa.ngen, 256, 0, st>>>(aa, d.gs_fast);
     if (s->x.asm_chunks > 0) k_assemble_gen<<<dim3(aa.ngen, s->x.asm_chunks), 256, 0, st>>>(aa);
   }

@@ -748,6 +748,8 @@ __global__ void __launch_bounds__(256) k_lu_gemm(ContactArgs a, int c, int k) {
   const int lo = k + nb, hi = min(n, k + nb + bw);
   const int r0 = lo + blockIdx.y * 64, c0 = lo + blockIdx.x * 64;
   if (r0 >= hi || c0 >= hi) return;
+  if (a.lu_flops && threadIdx.x == 0)
+    atomicAdd(a.lu_flops, 2ull * (unsigned long long)(min(64, hi - r0) * min(64, hi - c0) * nb));
   double *A = a.dense + a.sys_dense0[s];
   __shared__ double Ls[64][kNB + 1];
   __shared__ double Us[kNB][64 + 1];

@@ -31,6 +31,7 @@ __global__ void k_nodes(NodeArgs a) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= a.nn) return;
   if (!a.sys_active[a.node_sys[v]]) return;
+  count_active(a.units);
   const int NN = a.nn;
   const int d = a.node_dof[v];
   const double z = a.q[d + 2] - a.ground_z;
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(256) k_rows_gen(RowGenArgs a) {
   if (i >= a.nd) return;
   const int s = a.dof_sys[i];
   if (a.sys_kind[s] != SOLVE_GENERAL || !a.sys_active[s]) return;
+  count_active(a.units);
   double F = 0.0;
   for (int k = a.gat_ptr[i]; k < a.gat_ptr[i + 1]; ++k) {
     const int code = a.gat_ent[k];
@@ -122,6 +124,8 @@ __global__ void k_assemble_gen(AsmArgs a) {
   const int w = blockIdx.x;
   const int sy = a.gen_sys[w];
   if (!a.sys_active[sy] || (a.ls_action && a.ls_action[sy] == 1)) return;  // no solve
+  if (a.units && blockIdx.y == 0 && threadIdx.x == 0)
+    atomicAdd(a.units, (unsigned long long)a.sys_ndof[sy]);
   const int t1 = a.t0[w + 1];
 #pragma unroll
   for (int u = 0; u < kAsmPerBlock / 256; ++u) {

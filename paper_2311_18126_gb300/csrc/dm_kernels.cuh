@@ -83,6 +83,7 @@ struct NodeArgs {
   const double *node_h, *node_mu, *node_kc;
   const int32_t *sys_active;
   double *nt;
+  unsigned long long *units;  // profiling: nodes evaluated (or NULL)
 };
 
 struct RowGenArgs {
@@ -95,6 +96,7 @@ struct RowGenArgs {
   const double *sg, *es, *nt;
   double *f;
   unsigned long long *sys_res;
+  unsigned long long *units;  // profiling: DOF rows evaluated (or NULL)
 };
 
 struct AsmArgs {
@@ -110,7 +112,16 @@ struct AsmArgs {
   int ngen;
   const int32_t *gen_sys, *t0;
   const int64_t *mat0, *mat1;
+  const int32_t *sys_ndof;
+  unsigned long long *units;  // profiling: DOFs of the systems assembled (or NULL)
 };
+// Profiling: counts the calling warp's active threads into *units (one
+// atomic per warp).
+__device__ __forceinline__ void count_active(unsigned long long *units) {
+  if (units == nullptr) return;
+  const unsigned m = __activemask();
+  if ((threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(units, (unsigned long long)__popc(m));
+}
 
 struct SolveGenArgs {
   int ngen, max_iter;
@@ -165,6 +176,7 @@ struct ContactArgs {
   int n_contact;
   int32_t *cgo, *cbad;  // per contact system: solve this round, zero pivot met
   int nn;  // nodes (ground terms of contact systems)
+  unsigned long long *lu_flops;  // profiling: FP64 flops of the LU's trailing updates (or NULL)
 };
 constexpr int kNB = 32;  // panel width of the contact-system LU
 __global__ void k_cc_cells(ContactArgs a);
