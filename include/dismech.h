@@ -462,8 +462,9 @@ int64_t dm_contact_pairs(dm_system *sys);
  * bend-twist gradients and Hessians in one pass (the first round of a step;
  * every round of batches with rod networks), 16 residual and band rows in
  * one pass.  Ids 1 and 2 are then the residual pass (reference twist and
- * gradients; residual rows).  Profiling adds two event records per launch;
- * it is off by default. */
+ * gradients; residual rows).  launches[k] counts the launches of id k's
+ * phase, which for ids 8, 9, 11 and 12 is a short sequence of kernels.
+ * Profiling adds two event records per launch; it is off by default. */
 #define DM_NUM_KERNELS 17
 typedef struct dm_profile {
   int64_t launches[DM_NUM_KERNELS];
