@@ -161,14 +161,17 @@ __global__ void __launch_bounds__(256) k_rows_rod_band(RowArgs a) {
 // 55 trailing updates and 10 right-hand-side updates (forward substitution
 // fused in); the 65 update tasks are split over the eight lanes, rows 9 and
 // 10 across two lanes each (q = column in the window, r = right-hand side):
-//   lane 0: row 8            lane 1: row 7          lane 2: rows 6, 1
+//   lane 0: row 8            lane 1: row 7          lane 2: rows 1, 6
 //   lane 3: rows 5, 2        lane 4: rows 4, 3      lane 5: row 10 q1-7
 //   lane 6: row 10 q8-10,r; row 9 q1-3              lane 7: row 9 q4-9,r
-// -- at most 9 FMAs and 2 multipliers per lane.  Lane 2 updates the next
-// pivot (row 1) first and broadcasts it by a shuffle; its reciprocal (FP32
-// seed, two FP64 Newton steps) overlaps the other updates.  A warp holds two
-// rods (four chains); rods are taken from a queue in order of decreasing
-// size, two per warp.
+// -- at most 9 FMAs and 2 multipliers per lane.  Lane 2's first update is
+// the next pivot (row 1), broadcast by a shuffle; its reciprocal overlaps
+// the other updates.  Lane 0 computes z_j = y_j / D_j in the instruction of
+// the second multipliers, which it does not use, and the tiny-pivot test
+// runs on the integer pipe, so that a column costs 14 FP64 warp
+// instructions (2 multiplier products, 9 update FMAs, 3 for the reciprocal).
+// A warp holds two rods (four chains); rods are taken from a queue in order
+// of decreasing size, two per warp.
 #define SOLVE_WARPS 4
 #define SOLVE_RODS_PER_WARP kSolveRodsPerWarp
 #define SOLVE_LANES 8  // lanes per chain
@@ -181,13 +184,24 @@ static_assert(SOLVE_RODS_PER_WARP * 2 * SOLVE_LANES == 32, "two chains per rod f
 #define SOLVE_CHAIN_STRIDE (SOLVE_WROWS * 12 + 2)  // window + final base + spare
 static_assert(SOLVE_CHAIN_STRIDE * 2 + 32 == kSolveRodDoubles, "rod smem layout");
 
-// 1/d from an FP32 seed and two Newton steps in FP64 (|d| within FP32 range).
+// 1/d for 2^-126 <= |d| < 2^126 (the pivot test rejects the rest).  The
+// leading 23 bits of d become an FP32 number by integer operations (the
+// exponent field rebiased by 1023 - 127 = 896: 0x38000000 in the upper word),
+// its approximate FP32 reciprocal (relative error ~2^-22) returns the same
+// way, and one third-order step of the iteration for 1/d,
+// r <- r (1 + e + e^2) with e = 1 - d r (the truncated series of
+// r / (1 - e)), leaves a relative error of about e^3 ~ 2^-66, below FP64
+// rounding: three FP64 instructions, no FP32/FP64 conversions.
 __device__ __forceinline__ double rcp64(double d) {
-  double r = (double)__frcp_rn((float)d);
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned fb = (hi & 0x80000000u) | (((hi & 0x7FFFFFFFu) - 0x38000000u) << 3) | (lo >> 29);
+  float sf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(sf) : "f"(__uint_as_float(fb)));
+  const unsigned sb = __float_as_uint(sf);
+  const double r = __hiloint2double(
+      (int)((sb & 0x80000000u) | (((sb & 0x7FFFFFFFu) >> 3) + 0x38000000u)), (int)(sb << 29));
+  const double e = fma(-d, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 
 // Task k of lane p: window row i (bits 0-3) and u index q (bits 4-7,
@@ -197,7 +211,7 @@ __host__ __device__ constexpr int task_code(int p, int k) {
   // (row, first q, last q) segments of each lane; q = i + 1 stands for the
   // right-hand side
   const int seg[8][2][3] = {{{8, 1, 9}, {0, 0, -1}},  {{7, 1, 8}, {0, 0, -1}},
-                            {{6, 1, 7}, {1, 1, 2}},   {{5, 1, 6}, {2, 1, 3}},
+                            {{1, 1, 2}, {6, 1, 7}},   {{5, 1, 6}, {2, 1, 3}},
                             {{4, 1, 5}, {3, 1, 4}},   {{10, 1, 7}, {0, 0, -1}},
                             {{10, 8, 11}, {9, 1, 3}}, {{9, 4, 10}, {0, 0, -1}}};
   int t = 0;
@@ -213,16 +227,17 @@ __host__ __device__ constexpr int task_code(int p, int k) {
 }
 // window row of the lane's multiplier slot r (0 = none)
 __host__ __device__ constexpr int lane_row(int p, int r) {
-  return r == 0 ? (p == 0 ? 8 : p == 1 ? 7 : p == 2 ? 6 : p == 3 ? 5 : p == 4 ? 4 : p == 5 ? 10
+  return r == 0 ? (p == 0 ? 8 : p == 1 ? 7 : p == 2 ? 1 : p == 3 ? 5 : p == 4 ? 4 : p == 5 ? 10
                                                                        : p == 6 ? 10 : 9)
-                : (p == 2 ? 1 : p == 3 ? 2 : p == 4 ? 3 : p == 6 ? 9 : 0);
+                : (p == 2 ? 6 : p == 3 ? 2 : p == 4 ? 3 : p == 6 ? 9 : 0);
 }
 // the lane that stores the multiplier of slot r (rows 9 and 10 live on two lanes)
 __host__ __device__ constexpr bool lane_stores(int p, int r) {
   return lane_row(p, r) > 0 && !(p == 6 && r == 0) && !(p == 7 && r == 0);
 }
 #define SOLVE_TASKS 9
-#define SOLVE_PIVOT_LANE 2  // owns row 1: the next pivot
+#define SOLVE_PIVOT_LANE 2  // owns row 1, its first task: the next pivot
+static_assert(task_code(SOLVE_PIVOT_LANE, 0) == (1 | (1 << 4)), "the pivot lane's first task");
 
 struct Chain {
   // address maps of one elimination direction
@@ -244,11 +259,26 @@ struct Chain {
   __device__ __forceinline__ double *zstore(int idx) const { return dq + base + orig(idx); }
 };
 
-// A pivot smaller than kTinyPivot times the original diagonal entry of its
-// row counts as zero: J = M/dt^2 - dF/dq need not be positive definite
+// A pivot smaller than 2^-43 (1.1e-13) times the original diagonal entry of
+// its row counts as zero: J = M/dt^2 - dF/dq need not be positive definite
 // (large steps, compressed or buckling rods), and without pivoting such a
-// pivot would amplify rounding errors without bound.
-constexpr double kTinyPivot = 1e-13;
+// pivot would amplify rounding errors without bound.  So do pivots outside
+// [2^-126, 2^126) (the reciprocal's range; physical Jacobians stay many
+// decades inside), infinite or NaN ones.  The test compares the upper 32
+// bits of |D| (exponent and 20 leading mantissa bits, whose integer order is
+// the order of the magnitudes) with a per-row threshold: the upper word of
+// |J_jj| with 43 subtracted from its exponent field, at least that of
+// 2^-126.  Exact but for ties in those 32 bits.
+constexpr int kTinyPivotExp = 43;
+constexpr int kPivotFloorHi = (1023 - 126) << 20;  // upper word of 2^-126
+constexpr int kPivotCeilHi = (1023 + 126) << 20;   // upper word of 2^126
+__device__ __forceinline__ int pivot_threshold(double jjj) {
+  return max((__double2hiint(jjj) & 0x7FFFFFFF) - (kTinyPivotExp << 20), kPivotFloorHi);
+}
+__device__ __forceinline__ bool pivot_bad(int dhi, int thr) {
+  const int h = dhi & 0x7FFFFFFF;
+  return h < thr || h >= kPivotCeilHi;
+}
 
 // Eliminates `ncol` columns of a chain.  On return the window rows
 // W[(b + i) * 12 + .] (b = the final base, also stored at W[SOLVE_WROWS * 12])
@@ -265,11 +295,11 @@ constexpr double kTinyPivot = 1e-13;
 // the warp's largest ncol); a chain past its own ncol changes nothing, so
 // every synchronisation is warp-wide and the warp never diverges.
 //
-// Dg (lane 0 of the chain only): an 11-slot ring of the original diagonal
-// entries of the rows in the window, filled from the loads that bring the
-// rows in.
+// Dg (lane 0 of the chain only): an 11-slot ring of the pivot-test
+// thresholds of the rows in the window, from the original diagonal entries
+// that the loads bringing the rows in deliver.
 __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, double *W, int p,
-                                          int pivot_lane, double *Dg) {
+                                          int pivot_lane, int *Dg) {
   const int n = c.n;
   int toff[SOLVE_TASKS], uoff[SOLVE_TASKS], rsel[SOLVE_TASKS];
 #pragma unroll
@@ -293,7 +323,9 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, d
       st0 = lane_stores(pp, 0);
       st1 = lane_stores(pp, 1);
     }
-  const int loff0 = 13 * row0, loff1 = 13 * row1;
+  // the second multiplier's source; lane 0 (one row) takes the pivot row's
+  // right-hand side there, which makes its product z_j = y_j / D_j
+  const int loff0 = 13 * row0, loff1 = row1 > 0 ? 13 * row1 : 11;
   // rows 0..10 of the chain; diagonals reaching before row 0 are zero
   if (ncol > 0)
     for (int e = p; e < 11 * 12; e += SOLVE_LANES) {
@@ -304,8 +336,9 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, d
     }
   __syncwarp();
   if (ncol > 0 && p == 0)
-    for (int r = 0; r < 11; ++r) Dg[r] = W[12 * r];
+    for (int r = 0; r < 11; ++r) Dg[r] = pivot_threshold(W[12 * r]);
   double rj = ncol > 0 ? rcp64(W[0]) : 1.0;
+  int dhi = __double2hiint(W[0]);  // upper word of the pivot D_j
   bool bad = false;
   int b = 0, jr = 0;  // jr = j mod 11, the ring slot of row j
   // running addresses (one element per column in the chain's direction) of
@@ -330,29 +363,28 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, d
     pe1 += step;
     pfz += step;
     double *Wb = W + 12 * b;
-    const double zj = Wb[11];
     if (act && p == 0) {
-      // |D_j| < kTinyPivot |J_jj| (1/rj infinite or not finite included)
-      if (!isfinite(rj) || rj == 0.0 ||
-          fabsf((float)Dg[jr]) * (float)kTinyPivot * fabsf((float)rj) > 1.0f)  // in FP32: off the FP64 pipe
-        bad = true;
-      Dg[jr] = pre0;  // row j + 11 takes the slot (0 past the end)
+      if (pivot_bad(dhi, Dg[jr])) bad = true;
+      Dg[jr] = pivot_threshold(pre0);  // row j + 11 takes the slot (0 past the end)
       jr = jr == 10 ? 0 : jr + 1;
-      *pz = zj * rj;  // z_j = y_j / D_j for the backward pass
     }
+    const double l0 = Wb[loff0] * rj;
+    const double l1 = Wb[loff1] * rj;  // lane 0: z_j for the backward pass
+    if (act && p == 0) *pz = l1;
     pz += step;
-    const double l0 = row0 > 0 ? Wb[loff0] * rj : 0.0;
-    const double l1 = row1 > 0 ? Wb[loff1] * rj : 0.0;
     double uq[SOLVE_TASKS], dv[SOLVE_TASKS];
 #pragma unroll
     for (int k = 0; k < SOLVE_TASKS; ++k) {
       uq[k] = Wb[uoff[k]];
       dv[k] = Wb[toff[k]];
     }
-    // next pivot first (the pivot lane owns window row 1), broadcast, reciprocal
-    double piv = 1.0;
-    if (p == SOLVE_PIVOT_LANE && act && j + 1 < n) piv = fma(-l1, Wb[13], Wb[12]);
-    piv = __shfl_sync(0xffffffffu, piv, pivot_lane);
+    // the updates; the pivot lane's first one is the next pivot D_{j+1}
+    // (row 1; zero, and unused, past a short rod's last column), broadcast
+    // for the reciprocal, which overlaps the other updates
+    double v[SOLVE_TASKS];
+#pragma unroll
+    for (int k = 0; k < SOLVE_TASKS; ++k) v[k] = fma(-(rsel[k] == 1 ? l1 : l0), uq[k], dv[k]);
+    const double piv = __shfl_sync(0xffffffffu, v[0], pivot_lane);
     // no barrier here: every update target is read only by its own lane
     const double rnext = act ? rcp64(piv) : rj;
     if (act) {
@@ -360,7 +392,7 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, d
       if (st1 && j + row1 < n) *pl1 = l1;
 #pragma unroll
       for (int k = 0; k < SOLVE_TASKS; ++k)
-        if (rsel[k] < 2) Wb[toff[k]] = fma(-(rsel[k] == 0 ? l0 : l1), uq[k], dv[k]);
+        if (rsel[k] < 2) Wb[toff[k]] = v[k];
       // the new row j + 11 (zeros past the end)
       double *Wn = Wb + 12 * 11;
       Wn[p] = pre0;
@@ -392,6 +424,7 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, d
     if (act) {
       b = wrap ? 0 : b + 1;
       rj = rnext;
+      dhi = __double2hiint(piv);
     }
   }
   if (p == 0) W[SOLVE_WROWS * 12] = (double)b;
@@ -544,7 +577,8 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
     const int ncol = !go ? 0 : (half ? (twist ? n - m - 10 : 0) : m);
     const int nwarp = __reduce_max_sync(full, ncol);
     // the rod's scratch past the separator solution: one diagonal ring per chain
-    bool bad = eliminate(c, ncol, nwarp, W, p, pivot_lane, XS + 10 + 11 * half);
+    bool bad = eliminate(c, ncol, nwarp, W, p, pivot_lane,
+                         reinterpret_cast<int *>(XS + 10 + 11 * half));
     // a rod is bad if either of its chains met a zero pivot
     bad = (__ballot_sync(full, bad) & rod_mask) != 0;
     if (bad && go) {
