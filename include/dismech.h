@@ -238,9 +238,10 @@ int64_t dm_num_edges(const dm_system *sys);
  * J need not be positive definite: the rod Jacobian M/dt^2 - dF/dq is
  * indefinite for compressed or buckling rods and at large steps.  Without
  * pivoting, the factorisation of such a matrix is accurate as long as no
- * pivot D_i is small against its row; a pivot that is zero, not finite or
- * below 1e-13 |J_ii| returns DM_ERR_DEGENERATE (the system is then
- * numerically singular for this solver) instead of an inaccurate x. */
+ * pivot D_i is small against its row; a pivot that is zero, not finite,
+ * below 2^-43 |J_ii| (1.1e-13) or outside [2^-126, 2^126) returns
+ * DM_ERR_DEGENERATE (the system is then numerically singular for this
+ * solver) instead of an inaccurate x. */
 dm_status dm_solve_band(int32_t nsys, const int32_t *sys_dof0, const int32_t *sys_ndof,
                         int64_t ntot, const double *band, const double *rhs, double *x,
                         void *stream);
