@@ -297,9 +297,24 @@ __device__ __forceinline__ bool pivot_bad(int dhi, int thr) {
 //
 // Dg (lane 0 of the chain only): an 11-slot ring of the pivot-test
 // thresholds of the rows in the window, from the original diagonal entries
-// that the loads bringing the rows in deliver.
-__device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, double *W, int p,
-                                          int pivot_lane, int *Dg) {
+// that the loads bringing the rows in deliver; Dg[11..21] is scratch.
+//
+// The first `nfast` columns (a multiple of 11 that every chain of the warp
+// eliminates with rows j + 11 in its rod: no tests of the rod's end) run an
+// unrolled loop over the window's 11-column period: every shared-memory
+// address is a per-lane constant plus an immediate, and the lanes without a
+// task (pads, the second row load of lanes 4-7, the ring writes of lanes
+// 1-7) store into scratch instead of branching -- the window row two below
+// the new one, which the next column's row load overwrites, or the word
+// after the last row.
+__device__ __forceinline__ double pick(double a, double b, unsigned m) {  // m ? b : a, m = 0 or ~0
+  const unsigned alo = (unsigned)__double2loint(a), ahi = (unsigned)__double2hiint(a);
+  const unsigned blo = (unsigned)__double2loint(b), bhi = (unsigned)__double2hiint(b);
+  return __hiloint2double((int)((ahi & ~m) | (bhi & m)), (int)((alo & ~m) | (blo & m)));
+}
+
+__device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, int nfast, double *W,
+                                          int p, int pivot_lane, int *Dg) {
   const int n = c.n;
   int toff[SOLVE_TASKS], uoff[SOLVE_TASKS], rsel[SOLVE_TASKS];
 #pragma unroll
@@ -341,15 +356,78 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, d
   int dhi = __double2hiint(W[0]);  // upper word of the pivot D_j
   bool bad = false;
   int b = 0, jr = 0;  // jr = j mod 11, the ring slot of row j
+  const ptrdiff_t step = c.dir;
+  if (nfast > 0) {
+    __syncwarp();  // the ring, read by every lane below
+    double *tg[SOLVE_TASKS];
+    const double *sr[SOLVE_TASKS];
+    unsigned sm[SOLVE_TASKS];
+#pragma unroll
+    for (int k = 0; k < SOLVE_TASKS; ++k) {
+      tg[k] = W + (rsel[k] == 2 ? 144 : toff[k]);  // pads: scratch row
+      sr[k] = W + uoff[k];
+      sm[k] = rsel[k] == 1 ? ~0u : 0u;
+    }
+    const double *ls0 = W + loff0, *ls1 = W + loff1;
+    // the new row: diagonal p by every lane, then diagonals 8-10 (lanes
+    // 0-2), the right-hand side -f (lane 3, sign flipped on the upper word)
+    // or scratch (lanes 4-7)
+    double *nw1 = W + (p < 3 ? 140 + p : p == 3 ? 143 : 144);
+    const unsigned neg = p == 3 ? 0x80000000u : 0u;
+    const double *qe0 = c.entry(11, p);
+    const double *qe1 = p < 3 ? c.entry(11, p + 8) : p == 3 ? c.f + c.base + c.orig(11) : qe0;
+    int *ringw = Dg + (p == 0 ? 0 : 11);
+    // lane 0 stores z_j through its second multiplier slot
+    double *ql0 = c.lstore(0, row0);
+    double *ql1 = p == 0 ? c.dq + c.base + c.orig(0) : c.lstore(0, row1);
+    const bool w1 = st1 || p == 0;
+    for (int j0 = 0; j0 < nfast; j0 += 11) {
+#pragma unroll
+      for (int u = 0; u < 11; ++u) {
+        const double pre0 = *qe0;
+        const double pre1 = *qe1;
+        qe0 += step;
+        qe1 += step;
+        if (pivot_bad(dhi, Dg[u])) bad = true;
+        ringw[u] = pivot_threshold(pre0);
+        const double l0 = ls0[12 * u] * rj;
+        const double l1 = ls1[12 * u] * rj;
+        double uq[SOLVE_TASKS], dv[SOLVE_TASKS], v[SOLVE_TASKS];
+#pragma unroll
+        for (int k = 0; k < SOLVE_TASKS; ++k) {
+          uq[k] = sr[k][12 * u];
+          dv[k] = tg[k][12 * u];
+        }
+#pragma unroll
+        for (int k = 0; k < SOLVE_TASKS; ++k) v[k] = fma(-pick(l0, l1, sm[k]), uq[k], dv[k]);
+        const double piv = __shfl_sync(0xffffffffu, v[0], pivot_lane);
+        rj = rcp64(piv);
+        dhi = __double2hiint(piv);
+        if (st0) *ql0 = l0;
+        if (w1) *ql1 = l1;
+        ql0 += step;
+        ql1 += step;
+#pragma unroll
+        for (int k = 0; k < SOLVE_TASKS; ++k) tg[k][12 * u] = v[k];
+        W[12 * u + 132 + p] = pre0;
+        nw1[12 * u] = __hiloint2double(__double2hiint(pre1) ^ (int)neg, __double2loint(pre1));
+        __syncwarp();
+      }
+      // rows 11..21 (the next window) to the top of the buffer
+#pragma unroll
+      for (int e = 0; e < 132; e += SOLVE_LANES)
+        if (e + p < 132) W[e + p] = W[132 + e + p];
+      __syncwarp();
+    }
+  }
   // running addresses (one element per column in the chain's direction) of
   // row j + 11's diagonals p and p + 8 and right-hand side, of z_j, and of
   // the lane's multipliers L[j + row][j]
-  const ptrdiff_t step = c.dir;
-  const double *pe0 = c.entry(11, p), *pe1 = c.entry(11, p + 8 < 11 ? p + 8 : p);
-  const double *pfz = c.f + c.base + c.orig(11);
-  double *pz = c.dq + c.base + c.orig(0);
-  double *pl0 = c.lstore(0, row0), *pl1 = c.lstore(0, row1);
-  for (int j = 0; j < nwarp; ++j) {
+  const double *pe0 = c.entry(nfast + 11, p), *pe1 = c.entry(nfast + 11, p + 8 < 11 ? p + 8 : p);
+  const double *pfz = c.f + c.base + c.orig(nfast + 11);
+  double *pz = c.dq + c.base + c.orig(nfast);
+  double *pl0 = c.lstore(nfast, row0), *pl1 = c.lstore(nfast, row1);
+  for (int j = nfast; j < nwarp; ++j) {
     const bool act = j < ncol;
     // prefetch of row j + 11 (diagonals p and p + 8; the right-hand side)
     const bool more = act && j + 11 < n;
@@ -576,8 +654,11 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
     const int m = twist ? (n - 10) / 2 : n;
     const int ncol = !go ? 0 : (half ? (twist ? n - m - 10 : 0) : m);
     const int nwarp = __reduce_max_sync(full, ncol);
+    // the unrolled columns: whole 11-column blocks that every chain of the
+    // warp eliminates, none if a chain is idle or its rod too short to twist
+    const int nfast = 11 * ((int)__reduce_min_sync(full, (unsigned)(go && twist ? ncol : 0)) / 11);
     // the rod's scratch past the separator solution: one diagonal ring per chain
-    bool bad = eliminate(c, ncol, nwarp, W, p, pivot_lane,
+    bool bad = eliminate(c, ncol, nwarp, nfast, W, p, pivot_lane,
                          reinterpret_cast<int *>(XS + 10 + 11 * half));
     // a rod is bad if either of its chains met a zero pivot
     bad = (__ballot_sync(full, bad) & rod_mask) != 0;
