@@ -299,14 +299,17 @@ __device__ __forceinline__ bool pivot_bad(int dhi, int thr) {
 // thresholds of the rows in the window, from the original diagonal entries
 // that the loads bringing the rows in deliver; Dg[11..21] is scratch.
 //
-// The first `nfast` columns (a multiple of 11 that every chain of the warp
-// eliminates with rows j + 11 in its rod: no tests of the rod's end) run an
-// unrolled loop over the window's 11-column period: every shared-memory
-// address is a per-lane constant plus an immediate, and the lanes without a
-// task (pads, the second row load of lanes 4-7, the ring writes of lanes
-// 1-7) store into scratch instead of branching -- the window row two below
-// the new one, which the next column's row load overwrites, or the word
-// after the last row.
+// The first `nfast` columns (a multiple of 11 that every solving chain of
+// the warp eliminates with rows j + 11 in its rod: no tests of the rod's
+// end) run an unrolled loop over the window's 11-column period: every
+// shared-memory address is a per-lane constant plus an immediate, and the
+// lanes without a task (pads, the second row load of lanes 4-7, the ring
+// writes of lanes 1-7) store into scratch instead of branching -- the
+// window row two below the new one, which the next column's row load
+// overwrites, or the word after the last row.  A chain without columns
+// (its rod does not solve this round) runs along on rows 0..nfast + 10 of
+// the batch's arrays (which exist: a solving rod of the warp has that many
+// rows) with its global stores off; its window is not used afterwards.
 __device__ __forceinline__ double pick(double a, double b, unsigned m) {  // m ? b : a, m = 0 or ~0
   const unsigned alo = (unsigned)__double2loint(a), ahi = (unsigned)__double2hiint(a);
   const unsigned blo = (unsigned)__double2loint(b), bhi = (unsigned)__double2hiint(b);
@@ -374,20 +377,24 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, i
     // or scratch (lanes 4-7)
     double *nw1 = W + (p < 3 ? 140 + p : p == 3 ? 143 : 144);
     const unsigned neg = p == 3 ? 0x80000000u : 0u;
-    const double *qe0 = c.entry(11, p);
-    const double *qe1 = p < 3 ? c.entry(11, p + 8) : p == 3 ? c.f + c.base + c.orig(11) : qe0;
+    const bool live = ncol > 0;
+    Chain cf = c;
+    if (!live) cf.base = 0, cf.dir = 1;
+    const ptrdiff_t fstep = cf.dir;
+    const double *qe0 = cf.entry(11, p);
+    const double *qe1 = p < 3 ? cf.entry(11, p + 8) : p == 3 ? cf.f + cf.base + cf.orig(11) : qe0;
     int *ringw = Dg + (p == 0 ? 0 : 11);
     // lane 0 stores z_j through its second multiplier slot
-    double *ql0 = c.lstore(0, row0);
-    double *ql1 = p == 0 ? c.dq + c.base + c.orig(0) : c.lstore(0, row1);
-    const bool w1 = st1 || p == 0;
+    double *ql0 = cf.lstore(0, row0);
+    double *ql1 = p == 0 ? cf.dq + cf.base + cf.orig(0) : cf.lstore(0, row1);
+    const bool w0 = st0 && live, w1 = (st1 || p == 0) && live;
     for (int j0 = 0; j0 < nfast; j0 += 11) {
 #pragma unroll
       for (int u = 0; u < 11; ++u) {
         const double pre0 = *qe0;
         const double pre1 = *qe1;
-        qe0 += step;
-        qe1 += step;
+        qe0 += fstep;
+        qe1 += fstep;
         if (pivot_bad(dhi, Dg[u])) bad = true;
         ringw[u] = pivot_threshold(pre0);
         const double l0 = ls0[12 * u] * rj;
@@ -403,10 +410,10 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, i
         const double piv = __shfl_sync(0xffffffffu, v[0], pivot_lane);
         rj = rcp64(piv);
         dhi = __double2hiint(piv);
-        if (st0) *ql0 = l0;
+        if (w0) *ql0 = l0;
         if (w1) *ql1 = l1;
-        ql0 += step;
-        ql1 += step;
+        ql0 += fstep;
+        ql1 += fstep;
 #pragma unroll
         for (int k = 0; k < SOLVE_TASKS; ++k) tg[k][12 * u] = v[k];
         W[12 * u + 132 + p] = pre0;
@@ -517,23 +524,36 @@ __device__ __forceinline__ void cp_async8(double *dst, const double *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// Copies, for rows k0, k0-1, .., k0-10 of a chain, the multipliers
-// L(k, d) (d = 1..10) and the z value of row k - 11 (slot d = 0) into
-// buf[u * 11 + d] (u = k0 - k) with asynchronous copies; entries that do not
-// exist are zero.
-__device__ __forceinline__ void stage_rows(const Chain &c, bool on, int k0, int kstart,
-                                           double *buf, int p) {
+// Back substitution x_i = z_i - sum_d L[i+d][i] x_{i+d} of a chain, rows
+// kstart + 9 .. 0 (the separator rows kstart..kstart+9, whose x is known,
+// only contribute), in blocks of 11 rows from k0 = kstart + 9 - 11 g down.
+// Z = W + 242 holds the running values in a sliding linear buffer: at the
+// start of a block, Z[i] is row k0 - i (i = 0..10); the step of row
+// k = k0 - u takes x_k = Z[u], subtracts L[k][k-d] x_k from Z[u + d]
+// (d = 1..10) and brings z_{k-11} into Z[u + 11]; at the end of the block
+// Z[11..21] moves to Z[0..10].  So each row step has one warp barrier.  The
+// block's multipliers L(k, d) (d = 1..10) and z_{k-11} (d = 0) for
+// k = k0 - u sit in cur[11 u + d], staged one block ahead by asynchronous
+// copies into two buffers (W[0..120], W[121..241]).
+
+// Stages block k0 of a chain with the tests of the rod's ends: entries that
+// do not exist or are not used are zero.  (The z of row kk - 11 is staged
+// for rows kk past the rod's end too: a rod too short to twist has
+// kstart = n, and its first block's steps beyond the end bring in its last
+// rows.)
+__device__ __forceinline__ void stage_block(const Chain &c, bool on, int k0, int kstart,
+                                            double *buf, int p) {
   for (int e = p; e < 121; e += SOLVE_LANES) {
     const int u = e / 11, d = e - 11 * u;
     const int kk = k0 - u;
-    bool ok = on && kk >= 0 && kk < c.n && kk <= kstart + 9;
+    bool ok = on && kk >= 0;
     const double *src = nullptr;
     if (ok) {
       if (d == 0) {
-        ok = kk < kstart && kk - 11 >= 0;
+        ok = kk - 11 >= 0 && kk - 11 < kstart;
         if (ok) src = c.zstore(kk - 11);
       } else {
-        ok = kk - d >= 0 && kk - d < kstart;
+        ok = kk < c.n && kk - d >= 0 && kk - d < kstart;
         if (ok) src = c.entry(kk, d);
       }
     }
@@ -542,54 +562,89 @@ __device__ __forceinline__ void stage_rows(const Chain &c, bool on, int k0, int 
   }
 }
 
-// Right-looking backward substitution x_i = z_i - sum_d L[i+d][i] x_{i+d}
-// for chain rows kstart-1 .. 0, given x of rows kstart..kstart+9 in xs[].
-// The chain's window buffer W (free by now) holds two staging buffers of
-// 11 rows (W[0..120], W[121..241]), filled by asynchronous copies one block
-// of rows ahead, and the running z values in an 11-slot ring (W[242..252]).
-// `on` = this chain solves; `ktop` = the warp's largest kstart + 9 (uniform
-// trip count, warp-wide synchronisation).  Lane p applies diagonals p + 1
-// and p + 9.
-__device__ __forceinline__ void back_substitute(const Chain &c, bool on, int kstart, int ktop,
-                                                const double *xs, double *W, double *q, int p) {
+// Stages a block whose rows k0 - 10 .. k0 all lie in [11, kstart): every
+// entry exists.  Lane p copies diagonal 1 + p of the 11 rows, lanes 0-1
+// diagonals 9-10, lane 2 the z values.
+__device__ __forceinline__ void stage_block_full(const Chain &c, int k0, double *buf, int p) {
+  const ptrdiff_t dn = -(ptrdiff_t)c.dir;  // address step from row k to row k - 1
+  const double *s1 = c.entry(k0, 1 + p);
+#pragma unroll
+  for (int u = 0; u < 11; ++u) cp_async8(buf + 11 * u + 1 + p, s1 + dn * u);
+  if (p < 3) {
+    const double *s2 = p < 2 ? c.entry(k0, 9 + p) : c.zstore(k0 - 11);
+    double *b2 = buf + (p < 2 ? 9 + p : 0);
+#pragma unroll
+    for (int u = 0; u < 11; ++u) cp_async8(b2 + 11 * u, s2 + dn * u);
+  }
+}
+
+// xs = x of the separator rows kstart..kstart+9 (zero for a rod without
+// one); `nblk` = the warp's largest block count, blocks [1, gfast) run the
+// unrolled step (every row of them in [11, kstart) for every chain of the
+// warp that solves; the others run along on their own scratch).
+__device__ __forceinline__ void back_substitute(const Chain &c, bool on, int kstart, int nblk,
+                                                int gfast, const double *xs, double *W, double *q,
+                                                int p) {
   double *Z = W + 242;
-  if (on)
-    for (int m = kstart - 1 - p; m >= 0 && m >= kstart - 11; m -= SOLVE_LANES) Z[m % 11] = *c.zstore(m);
-  stage_rows(c, on, ktop, kstart, W, p);
+  // block 0: the separator's x at Z[0..9] (rows kstart+9..kstart), z of row
+  // kstart - 1 at Z[10]
+  if (p == 0) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) Z[i] = xs[9 - i];
+    Z[10] = (on && kstart - 1 >= 0) ? *c.zstore(kstart - 1) : 0.0;
+  }
+  stage_block(c, on, kstart + 9, kstart, W, p);
   cp_async_commit();
-  for (int g = 0; ktop - 11 * g >= 0; ++g) {
-    const int k0 = ktop - 11 * g;
+  // lane 0 adds x_k into q (rows below the separator), running address
+  double *qk = q + c.base + c.orig(kstart + 9);
+  const ptrdiff_t dn = -(ptrdiff_t)c.dir;
+  for (int g = 0; g < nblk; ++g) {
+    const int k0 = kstart + 9 - 11 * g;
     double *cur = W + 121 * (g & 1);
-    if (k0 - 11 >= 0) stage_rows(c, on, k0 - 11, kstart, W + 121 * ((g + 1) & 1), p);
+    double *nxt = W + 121 * ((g + 1) & 1);
+    if (g + 1 < nblk) {
+      if (g + 1 < gfast) stage_block_full(c, k0 - 11, nxt, p);
+      else stage_block(c, on, k0 - 11, kstart, nxt, p);
+    }
     cp_async_commit();
     cp_async_wait1();
     __syncwarp();
-    for (int u = 0; u < 11; ++u) {
-      const int k = k0 - u;
-      const bool act = on && k >= 0 && k <= kstart + 9 && k < c.n;
-      double xk = 0.0;
-      if (act) {
-        if (k >= kstart) {
-          xk = xs[k - kstart];
-        } else {
-          xk = Z[k % 11];
-          if (p == 0) atomicAdd(q + c.base + c.orig(k), xk);  // no read on the chain
-        }
-      }
-      __syncwarp();
-      if (act) {
+    if (g >= 1 && g < gfast) {
+      // every row of the block is below the separator and at least 11
+      double *z1 = Z + 1 + p, *z2 = Z + 9 + (p & 1);
+      const double *c1 = cur + 1 + p, *c2 = cur + 9 + (p & 1);
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const int d = 1 + p + SOLVE_LANES * t;
-          if (d <= 10 && k - d >= 0 && k - d < kstart) {
-            const int slot = (k - d) % 11;
-            Z[slot] = fma(-cur[u * 11 + d], xk, Z[slot]);
+      for (int u = 0; u < 11; ++u) {
+        const double xk = Z[u];
+        if (p == 0 && on) atomicAdd(qk, xk);
+        qk += dn;
+        z1[u] = fma(-c1[11 * u], xk, z1[u]);
+        if (p < 2) z2[u] = fma(-c2[11 * u], xk, z2[u]);
+        if (p == 2) Z[u + 11] = cur[11 * u];
+        __syncwarp();
+      }
+    } else {
+      for (int u = 0; u < 11; ++u) {
+        const int k = k0 - u;
+        const bool act = on && k >= 0 && k < c.n;
+        const double xk = Z[u];
+        if (act && p == 0 && k < kstart) atomicAdd(qk, xk);
+        qk += dn;
+        if (act) {
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const int d = 1 + p + SOLVE_LANES * t;
+            if (d <= 10 && k - d >= 0 && k - d < kstart) Z[u + d] = fma(-cur[11 * u + d], xk, Z[u + d]);
           }
         }
-        if (p == 1 && k < kstart && k - 11 >= 0) Z[k % 11] = cur[u * 11];
+        if (on && p == 2 && k - 11 >= 0 && k - 11 < kstart) Z[u + 11] = cur[11 * u];
+        __syncwarp();
       }
-      __syncwarp();
     }
+    // rows k0 - 11 .. k0 - 21 to the top of the buffer
+    Z[p] = Z[11 + p];
+    if (p < 3) Z[8 + p] = Z[19 + p];
+    __syncwarp();
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncwarp();
@@ -654,9 +709,10 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
     const int m = twist ? (n - 10) / 2 : n;
     const int ncol = !go ? 0 : (half ? (twist ? n - m - 10 : 0) : m);
     const int nwarp = __reduce_max_sync(full, ncol);
-    // the unrolled columns: whole 11-column blocks that every chain of the
-    // warp eliminates, none if a chain is idle or its rod too short to twist
-    const int nfast = 11 * ((int)__reduce_min_sync(full, (unsigned)(go && twist ? ncol : 0)) / 11);
+    // the unrolled columns: whole 11-column blocks that every solving chain
+    // of the warp eliminates, none if a solving rod is too short to twist
+    const unsigned fmin = __reduce_min_sync(full, go ? (twist ? (unsigned)ncol : 0u) : ~0u);
+    const int nfast = nwarp > 0 ? 11 * (int)(fmin / 11) : 0;
     // the rod's scratch past the separator solution: one diagonal ring per chain
     bool bad = eliminate(c, ncol, nwarp, nfast, W, p, pivot_lane,
                          reinterpret_cast<int *>(XS + 10 + 11 * half));
@@ -774,8 +830,18 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve_rod(SolveArgs a) {
     for (int i = 0; i < 10; ++i) xs[i] = (go && twist) ? (half ? XS[9 - i] : XS[i]) : 0.0;
     const bool on = go && (twist || !half);
     const int kstart = !on ? 0 : (twist ? (half ? n - m - 10 : m) : n);
-    const int ktop = __reduce_max_sync(full, on ? kstart + 9 : -1);
-    back_substitute(c, on, kstart, ktop, xs, W, a.q, p);
+    // blocks of 11 rows from kstart + 9 down to row 0; the unrolled ones have
+    // all rows in [11, kstart) for every chain that solves; a chain that does
+    // not runs along on rows of the batch's arrays (the largest kstart's)
+    const int nblk = (int)__reduce_max_sync(full, on ? (unsigned)((kstart + 20) / 11) : 0u);
+    const unsigned gf = __reduce_min_sync(
+        full, on ? (kstart >= 12 ? (unsigned)((kstart - 12) / 11 + 1) : 1u) : ~0u);
+    const int gfast = nblk > 0 ? (int)min(gf, (unsigned)nblk) : 0;
+    const int kmax = (int)__reduce_max_sync(full, on ? (unsigned)kstart : 0u);
+    Chain cb = c;
+    int kb = kstart;
+    if (!on) cb.base = 0, cb.dir = 1, cb.n = a.nd, kb = kmax;
+    back_substitute(cb, on, kb, nblk, gfast, xs, W, a.q, p);
     if (go && head) {
       a.sys_iters[s] += 1;
       if (a.ls_trial) a.ls_trial[s] = 1;
