@@ -42,16 +42,9 @@ constexpr unsigned kFull = 0xffffffffu;
 // fraction of their original diagonal entry send it to partial pivoting.
 constexpr double kTinyPivotB = 1e-13;
 
-// 1/d from an FP32 seed and two Newton steps in FP64; a division outside
-// the seed's range.
+// 1/d by rcp64 (three FP64 instructions); a division outside its range.
 __device__ __forceinline__ double limb_recip(double d) {
-  const double ad = fabs(d);
-  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
-  double r = (double)__frcp_rn((float)d);
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
+  return rcp64_in_range(d) ? rcp64(d) : 1.0 / d;
 }
 
 // The border kernel's decision for system s, without its side effects.
@@ -180,10 +173,42 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
   double rp = 1.0;
   if (ne > 0) {
     const double piv = Bs[10];
-    if (!(fabs(piv) > 0.0) || !isfinite(piv)) bad = true;
+    if (zero_or_nonfinite(piv)) bad = true;
     else rp = limb_recip(piv);
   }
-  for (int j = 0; j < ne && !bad; ++j) {
+  // columns whose ten rows below lie inside the limb: no tests of its end,
+  // per-lane offsets from the pivot row, the next pivot's update first
+  const int jf = min(ne, n - 10);
+  {
+    const int mo = lane < 10 ? (lane + 1) * kRow + 9 - lane : kRow + 9;
+    int dof[4], sof[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      dof[u] = si[u] > 0 ? si[u] * kRow + (sk[u] ? 10 - si[u] + sk[u] : 21) : 0;
+      sof[u] = sk[u] ? 10 + sk[u] : 21;
+    }
+    const bool s3 = si[3] > 0;
+    double *pr = Bs;
+    for (int j = 0; j < jf && !bad; ++j, pr += kRow) {
+      const double l = pr[mo] * rp;
+      if (lane < 10) pr[mo] = l;
+      if (lane == 0) pr[10] = rp;  // the pivot is read no more
+      const double v0 = fma(-__shfl_sync(kFull, l, si[0] - 1), pr[sof[0]], pr[dof[0]]);
+      pr[dof[0]] = v0;
+      if (j + 1 < ne) {
+        const double pn = __shfl_sync(kFull, v0, 1);
+        if (zero_or_nonfinite(pn)) bad = true;
+        else rp = limb_recip(pn);
+      }
+#pragma unroll
+      for (int u = 1; u < 3; ++u)
+        pr[dof[u]] = fma(-__shfl_sync(kFull, l, si[u] - 1), pr[sof[u]], pr[dof[u]]);
+      const double l3 = __shfl_sync(kFull, l, s3 ? si[3] - 1 : 0);
+      if (s3) pr[dof[3]] = fma(-l3, pr[sof[3]], pr[dof[3]]);
+      __syncwarp();
+    }
+  }
+  for (int j = max(jf, 0); j < ne && !bad; ++j) {
     const double *pr = Bs + j * kRow;
     // multiplier of row j + 1 + lane, stored in place by the lane that reads it
     double l = 0.0;
@@ -206,7 +231,7 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
       if (u == 0 && j + 1 < ne) {
         // the next pivot (lane 1's first slot), its reciprocal off the chain
         const double pn = __shfl_sync(kFull, v0, 1);
-        if (!(fabs(pn) > 0.0) || !isfinite(pn)) bad = true;
+        if (zero_or_nonfinite(pn)) bad = true;
         else rp = limb_recip(pn);
       }
     }

@@ -117,6 +117,38 @@ struct AsmArgs {
 };
 // Profiling: counts the calling warp's active threads into *units (one
 // atomic per warp).
+// 1/d for 2^-126 <= |d| < 2^126 (callers test the range first).  The
+// leading 23 bits of d become an FP32 number by integer operations (the
+// exponent field rebiased by 1023 - 127 = 896: 0x38000000 in the upper word),
+// its approximate FP32 reciprocal (relative error ~2^-22) returns the same
+// way, and one third-order step of the iteration for 1/d,
+// r <- r (1 + e + e^2) with e = 1 - d r (the truncated series of
+// r / (1 - e)), leaves a relative error of about e^3 ~ 2^-66, below FP64
+// rounding: three FP64 instructions, no FP32/FP64 conversions.
+__device__ __forceinline__ double rcp64(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned fb = (hi & 0x80000000u) | (((hi & 0x7FFFFFFFu) - 0x38000000u) << 3) | (lo >> 29);
+  float sf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(sf) : "f"(__uint_as_float(fb)));
+  const unsigned sb = __float_as_uint(sf);
+  const double r = __hiloint2double(
+      (int)((sb & 0x80000000u) | (((sb & 0x7FFFFFFFu) >> 3) + 0x38000000u)), (int)(sb << 29));
+  const double e = fma(-d, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+
+// Upper word of |d| against the range of rcp64: true for 2^-126 <= |d| < 2^126.
+__device__ __forceinline__ bool rcp64_in_range(double d) {
+  const unsigned h = (unsigned)__double2hiint(d) & 0x7FFFFFFFu;
+  return h >= ((1023u - 126u) << 20) && h < ((1023u + 126u) << 20);
+}
+
+// d == 0 or not finite, by integer tests on its words (off the FP64 pipe).
+__device__ __forceinline__ bool zero_or_nonfinite(double d) {
+  const unsigned h = (unsigned)__double2hiint(d) & 0x7FFFFFFFu;
+  return (h | (unsigned)__double2loint(d)) == 0u || h >= 0x7FF00000u;
+}
+
 __device__ __forceinline__ void count_active(unsigned long long *units) {
   if (units == nullptr) return;
   const unsigned m = __activemask();

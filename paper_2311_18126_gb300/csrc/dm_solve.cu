@@ -184,25 +184,6 @@ static_assert(SOLVE_RODS_PER_WARP * 2 * SOLVE_LANES == 32, "two chains per rod f
 #define SOLVE_CHAIN_STRIDE (SOLVE_WROWS * 12 + 2)  // window + final base + spare
 static_assert(SOLVE_CHAIN_STRIDE * 2 + 32 == kSolveRodDoubles, "rod smem layout");
 
-// 1/d for 2^-126 <= |d| < 2^126 (the pivot test rejects the rest).  The
-// leading 23 bits of d become an FP32 number by integer operations (the
-// exponent field rebiased by 1023 - 127 = 896: 0x38000000 in the upper word),
-// its approximate FP32 reciprocal (relative error ~2^-22) returns the same
-// way, and one third-order step of the iteration for 1/d,
-// r <- r (1 + e + e^2) with e = 1 - d r (the truncated series of
-// r / (1 - e)), leaves a relative error of about e^3 ~ 2^-66, below FP64
-// rounding: three FP64 instructions, no FP32/FP64 conversions.
-__device__ __forceinline__ double rcp64(double d) {
-  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-  const unsigned fb = (hi & 0x80000000u) | (((hi & 0x7FFFFFFFu) - 0x38000000u) << 3) | (lo >> 29);
-  float sf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(sf) : "f"(__uint_as_float(fb)));
-  const unsigned sb = __float_as_uint(sf);
-  const double r = __hiloint2double(
-      (int)((sb & 0x80000000u) | (((sb & 0x7FFFFFFFu) >> 3) + 0x38000000u)), (int)(sb << 29));
-  const double e = fma(-d, r, 1.0);
-  return fma(r, fma(e, e, e), r);
-}
 
 // Task k of lane p: window row i (bits 0-3) and u index q (bits 4-7,
 // 0 = right-hand side, 15 = padding); row slot (bits 8-9) among the lane's
