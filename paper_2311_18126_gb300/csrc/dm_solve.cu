@@ -218,6 +218,32 @@ __host__ __device__ constexpr bool lane_stores(int p, int r) {
 }
 #define SOLVE_TASKS 9
 #define SOLVE_PIVOT_LANE 2  // owns row 1, its first task: the next pivot
+// Every update task (row i = 1..10, column q = 1..i or the right-hand side)
+// appears exactly once over the lanes' task lists; every task's row is its
+// lane's multiplier row of the slot it names; the multipliers of rows
+// 1..10 are stored by exactly one lane each.
+__host__ __device__ constexpr bool solve_tasks_cover() {
+  int seen[11][12] = {};
+  for (int p = 0; p < SOLVE_LANES; ++p)
+    for (int k = 0; k < SOLVE_TASKS; ++k) {
+      const int code = task_code(p, k);
+      const int i = code & 15, q = (code >> 4) & 15, r = code >> 8;
+      if (q == 15) continue;
+      if (i < 1 || i > 10 || q > i || lane_row(p, r) != i) return false;
+      ++seen[i][q];
+    }
+  for (int i = 1; i <= 10; ++i)
+    for (int q = 0; q <= i; ++q)
+      if (seen[i][q] != 1) return false;
+  int stored[11] = {};
+  for (int p = 0; p < SOLVE_LANES; ++p)
+    for (int r = 0; r < 2; ++r)
+      if (lane_stores(p, r)) ++stored[lane_row(p, r)];
+  for (int i = 1; i <= 10; ++i)
+    if (stored[i] != 1) return false;
+  return true;
+}
+static_assert(solve_tasks_cover(), "rod solver task tables");
 static_assert(task_code(SOLVE_PIVOT_LANE, 0) == (1 | (1 << 4)), "the pivot lane's first task");
 
 struct Chain {
