@@ -35,7 +35,9 @@ namespace dm {
 
 namespace {
 constexpr int kRow = 22;        // 21 band entries and the right-hand side
-constexpr int kSmall = kFastMaxM * (kFastMaxM + kFastMaxBC + 1);  // condensed block
+// condensed block [A_m | C_m | y_m] (leading dimension m + nbc + 1), the
+// coupling rows R_m (nbc x m), then the small LU's scratch
+constexpr int kSmall = kFastMaxM * (kFastMaxM + kFastMaxBC + 1) + kFastMaxBC * kFastMaxM + 2 * kFastMaxM;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Pivots of the border system's elimination in order smaller than this
@@ -57,18 +59,21 @@ __device__ __forceinline__ bool wants_solve(const SolveGenArgs &a, int s) {
   return a.sys_iters[s] < a.max_iter;
 }
 
-// B <- A^{-1} B for a dense n x n matrix A (row-major, leading dimension
-// lda) and n x nrhs right-hand sides B (leading dimension ldb), both in
-// shared memory, by one warp: Gaussian elimination with partial pivoting,
-// then back substitution.  A is destroyed.  Returns false (uniformly) on a
-// zero or non-finite pivot.
-__device__ bool warp_lu_solve(double *A, int n, int lda, double *B, int nrhs, int ldb,
+// [A | B] <- [U | A^{-1} B] for a dense n x n matrix A with nrhs
+// right-hand sides B beside it (row-major, leading dimension ld >= n + nrhs)
+// in shared memory, by one warp: Gaussian elimination with partial
+// pivoting, reciprocal pivots, the multipliers of a column by one lane per
+// row, the trailing update and the back substitution spread over (row,
+// column) pairs -- no lane works through a whole row.  lm and dinv: n
+// doubles of scratch each.  Returns false (uniformly) on a zero or
+// non-finite pivot.
+__device__ bool warp_lu_solve(double *M, int n, int ld, int nrhs, double *lm, double *dinv,
                               int lane) {
   for (int j = 0; j < n; ++j) {
     double best = -1.0;
     int bi = j;
     for (int i = j + lane; i < n; i += 32) {
-      const double v = fabs(A[i * lda + j]);
+      const double v = fabs(M[i * ld + j]);
       if (v > best) {
         best = v;
         bi = i;
@@ -84,47 +89,38 @@ __device__ bool warp_lu_solve(double *A, int n, int lda, double *B, int nrhs, in
       }
     }
     if (!(best > 0.0) || !isfinite(best)) return false;
-    if (bi != j) {
-      for (int c = lane; c < n; c += 32) {
-        const double t = A[j * lda + c];
-        A[j * lda + c] = A[bi * lda + c];
-        A[bi * lda + c] = t;
+    if (bi != j)
+      for (int c = j + lane; c < n + nrhs; c += 32) {
+        const double t = M[j * ld + c];
+        M[j * ld + c] = M[bi * ld + c];
+        M[bi * ld + c] = t;
       }
-      for (int c = lane; c < nrhs; c += 32) {
-        const double t = B[j * ldb + c];
-        B[j * ldb + c] = B[bi * ldb + c];
-        B[bi * ldb + c] = t;
-      }
-    }
     __syncwarp();
-    const double rp = 1.0 / A[j * lda + j];
-    // each lane updates whole rows: row i reads column j and row j, which no
-    // update of this step writes
-    for (int i = j + 1 + lane; i < n; i += 32) {
-      const double l = A[i * lda + j] * rp;
-      double *Ai = A + i * lda;
-      const double *Aj = A + j * lda;
-      for (int c = j + 1; c < n; ++c) Ai[c] = fma(-l, Aj[c], Ai[c]);
-      for (int c = 0; c < nrhs; ++c) B[i * ldb + c] = fma(-l, B[j * ldb + c], B[i * ldb + c]);
+    const double rp = limb_recip(M[j * ld + j]);
+    if (lane == 0) dinv[j] = rp;
+    for (int i = j + 1 + lane; i < n; i += 32) lm[i] = M[i * ld + j] * rp;
+    __syncwarp();
+    // rows j+1.., columns j+1 .. n+nrhs-1; the row of pair e by a float
+    // reciprocal (e < 2^10, so the quotient is exact after rounding down)
+    const int wdt = n + nrhs - j - 1, cnt = (n - j - 1) * wdt;
+    const float iw = 1.0f / (float)wdt;
+    for (int e = lane; e < cnt; e += 32) {
+      const int r = (int)(((float)e + 0.5f) * iw);
+      const int i = j + 1 + r, c = j + 1 + e - r * wdt;
+      M[i * ld + c] = fma(-lm[i], M[j * ld + c], M[i * ld + c]);
     }
     __syncwarp();
   }
-  if (nrhs == 1) {
-    for (int i = n - 1; i >= 0; --i) {
-      double part = 0.0;
-      for (int k = i + 1 + lane; k < n; k += 32) part = fma(A[i * lda + k], B[k * ldb], part);
-#pragma unroll
-      for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
-      if (lane == 0) B[i * ldb] = (B[i * ldb] - part) / A[i * lda + i];
-      __syncwarp();
+  // back substitution, column by column of U: x_i = y_i / u_ii, then
+  // y_k -= u_ki x_i for the rows above
+  const float ir = 1.0f / (float)nrhs;
+  for (int i = n - 1; i >= 0; --i) {
+    for (int c = lane; c < nrhs; c += 32) M[i * ld + n + c] *= dinv[i];
+    __syncwarp();
+    for (int e = lane; e < i * nrhs; e += 32) {
+      const int k = (int)(((float)e + 0.5f) * ir), c = e - k * nrhs;
+      M[k * ld + n + c] = fma(-M[k * ld + i], M[i * ld + n + c], M[k * ld + n + c]);
     }
-  } else {
-    for (int c = lane; c < nrhs; c += 32)
-      for (int i = n - 1; i >= 0; --i) {
-        double v = B[i * ldb + c];
-        for (int k = i + 1; k < n; ++k) v = fma(-A[i * lda + k], B[k * ldb + c], v);
-        B[i * ldb + c] = v / A[i * lda + i];
-      }
     __syncwarp();
   }
   return true;
@@ -150,12 +146,16 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
   double *G = a.gen;
   const double *band = G + a.lb_band[L];
   double *U = G + a.lb_y[L];  // [ne][12] out: U row, right-hand side, 1/pivot
-  // coalesced staging of the contiguous band
+  // staging of the contiguous band by asynchronous copies (all in flight
+  // at once), the right-hand side alongside
   for (int e = lane; e < n * 21; e += 32) {
     const int p = e / 21;
-    Bs[p * kRow + (e - p * 21)] = band[e];
+    cp_async8(Bs + p * kRow + (e - p * 21), band + e);
   }
+  cp_async_commit();
+#pragma unroll 4
   for (int p = lane; p < n; p += 32) Bs[p * kRow + 21] = -a.f[d0 + (dir ? n - 1 - p : p)];
+  cp_async_wait_all();
   __syncwarp();
   bool bad = false;
   const int ne = n - m;  // rows eliminated inside the limb
@@ -245,27 +245,37 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
       U[e] = Bs[p * kRow + (c < 10 ? 11 + c : (c == 10 ? 21 : 10))];
     }
   if (!bad && m > 0) {
-    // condensed block A_m and right-hand sides [C_m | y_m]
-    double *A = small;
-    double *B = A + m * m;
-    const int ldb = nbc + 1;
+    // condensed block [A_m | C_m | y_m] (leading dimension ld), C_m and the
+    // coupling rows R_m by asynchronous copies
+    const int ldb = nbc + 1, ld = m + ldb;
+    double *M = small;
+    double *Rs = small + kFastMaxM * (kFastMaxM + kFastMaxBC + 1);
+    double *lm = Rs + kFastMaxBC * kFastMaxM, *dinv = lm + kFastMaxM;
     const double *C = G + a.lb_C[L];
+    const double *R = G + a.lb_R[L];
+    for (int e = lane; e < m * nbc; e += 32) {
+      const int r = e / nbc;
+      cp_async8(M + r * ld + m + e - r * nbc, C + e);
+    }
+    for (int e = lane; e < nbc * m; e += 32) cp_async8(Rs + e, R + e);
+    cp_async_commit();
     for (int e = lane; e < m * m; e += 32) {
       const int r = e / m, c = e - r * m;
-      A[e] = Bs[(ne + r) * kRow + 10 + c - r];
+      M[r * ld + c] = Bs[(ne + r) * kRow + 10 + c - r];
     }
-    for (int e = lane; e < m * ldb; e += 32) {
-      const int r = e / ldb, c = e - r * ldb;
-      B[e] = c < nbc ? C[r * nbc + c] : Bs[(ne + r) * kRow + 21];
-    }
+    for (int r = lane; r < m; r += 32) M[r * ld + m + nbc] = Bs[(ne + r) * kRow + 21];
+    cp_async_wait_all();
     __syncwarp();
-    if (!warp_lu_solve(A, m, m, B, ldb, ldb, lane)) {
+    if (!warp_lu_solve(M, m, ld, ldb, lm, dinv, lane)) {
       bad = true;
     } else {
+      // Z = A_m^{-1} [C_m | y_m] for the back substitution
       double *Z = G + a.lb_Y[L];
-      for (int e = lane; e < m * ldb; e += 32) Z[e] = B[e];
+      for (int e = lane; e < m * ldb; e += 32) {
+        const int r = e / ldb;
+        Z[e] = M[r * ld + m + e - r * ldb];
+      }
       // Schur complement and right-hand side of the border system
-      const double *R = G + a.lb_R[L];
       const int32_t *bc = a.lb_bcols + a.lb_bc0[L];
       const int nB = a.gs_nB[w];
       double *S = G + a.gs_JBB[w];
@@ -273,7 +283,7 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
       for (int e = lane; e < nbc * ldb; e += 32) {
         const int b1 = e / ldb, b2 = e - b1 * ldb;
         double v = 0.0;
-        for (int r = 0; r < m; ++r) v = fma(R[b1 * m + r], B[r * ldb + b2], v);
+        for (int r = 0; r < m; ++r) v = fma(Rs[b1 * m + r], M[r * ld + m + b2], v);
         if (b2 < nbc) atomicAdd(S + (int64_t)bc[b1] * nB + bc[b2], -v);
         else atomicAdd(rB + bc[b1], -v);
       }

@@ -137,6 +137,15 @@ __device__ __forceinline__ double rcp64(double d) {
   return fma(r, fma(e, e, e), r);
 }
 
+// Asynchronous 8-byte copy global -> shared (both 8-byte aligned), and the
+// group commit / wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Upper word of |d| against the range of rcp64: true for 2^-126 <= |d| < 2^126.
 __device__ __forceinline__ bool rcp64_in_range(double d) {
   const unsigned h = (unsigned)__double2hiint(d) & 0x7FFFFFFFu;
@@ -177,9 +186,12 @@ struct SolveGenArgs {
   int32_t *gen_go, *gen_bad;
 };
 
-// shared memory (doubles) per warp of the condensation-path limb kernels
+// shared memory (doubles) per warp of the condensation-path limb kernels:
+// the factor's limb band, its condensed block [A_m | C_m | y_m], the
+// coupling rows R_m and the small LU's scratch
 __host__ __device__ constexpr size_t gen_factor_smem(int nmax) {
-  return (size_t)nmax * 22 + kFastMaxM * (kFastMaxM + kFastMaxBC + 1);
+  return (size_t)nmax * 22 + kFastMaxM * (kFastMaxM + kFastMaxBC + 1) + kFastMaxBC * kFastMaxM +
+         2 * kFastMaxM;
 }
 __host__ __device__ constexpr size_t gen_back_smem(int nmax) { return (size_t)nmax * 12 + 16; }
 

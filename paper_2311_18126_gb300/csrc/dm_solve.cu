@@ -524,11 +524,6 @@ __device__ __forceinline__ bool eliminate(const Chain &c, int ncol, int nwarp, i
   return bad;
 }
 
-__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Back substitution x_i = z_i - sum_d L[i+d][i] x_{i+d} of a chain, rows
