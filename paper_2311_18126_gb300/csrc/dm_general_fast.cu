@@ -18,8 +18,12 @@
 // limb's elimination chain; both limb kernels keep that chain short.  Per
 // column the factor takes the 10 multipliers in one instruction (a lane
 // each, broadcast by shuffles), the 110 updates in four, and the next
-// pivot's reciprocal (FP32 seed, two FP64 Newton steps) right after the
-// update that produces it, overlapping the others.  The back substitution
+// pivot's reciprocal (an FP32 seed and one third-order step, three FP64
+// instructions) interleaved with the updates after the one that produces
+// it; a pivot outside [2^-126, 2^126) (zero and non-finite included) fails
+// the system.  The band, C_m and R_m are staged by asynchronous copies, and
+// the condensed block's small LU spreads its work over (row, column)
+// pairs.  The back substitution
 // is column oriented: lanes 1..10 hold the partial right-hand sides of the
 // ten rows above the current one in registers, so a row costs one multiply,
 // one update and two shuffles.
@@ -173,8 +177,8 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
   double rp = 1.0;
   if (ne > 0) {
     const double piv = Bs[10];
-    if (zero_or_nonfinite(piv)) bad = true;
-    else rp = limb_recip(piv);
+    if (!rcp64_in_range(piv)) bad = true;
+    else rp = rcp64(piv);
   }
   // columns whose ten rows below lie inside the limb: no tests of its end,
   // per-lane offsets from the pivot row, the next pivot's update first
@@ -195,16 +199,27 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
       if (lane == 0) pr[10] = rp;  // the pivot is read no more
       const double v0 = fma(-__shfl_sync(kFull, l, si[0] - 1), pr[sof[0]], pr[dof[0]]);
       pr[dof[0]] = v0;
-      if (j + 1 < ne) {
-        const double pn = __shfl_sync(kFull, v0, 1);
-        if (zero_or_nonfinite(pn)) bad = true;
-        else rp = limb_recip(pn);
-      }
-#pragma unroll
-      for (int u = 1; u < 3; ++u)
-        pr[dof[u]] = fma(-__shfl_sync(kFull, l, si[u] - 1), pr[sof[u]], pr[dof[u]]);
+      // the next pivot's reciprocal (seed, e = 1 - d r0, t = e + e^2,
+      // r0 + r0 t) interleaved with the other updates, without branches; a
+      // pivot outside [2^-126, 2^126) (zero and non-finite included) fails
+      const double pn = __shfl_sync(kFull, v0, 1);
+      const double r0 = rcp64_seed(pn);
+      const double l1 = __shfl_sync(kFull, l, si[1] - 1);
+      const double l2 = __shfl_sync(kFull, l, si[2] - 1);
       const double l3 = __shfl_sync(kFull, l, s3 ? si[3] - 1 : 0);
-      if (s3) pr[dof[3]] = fma(-l3, pr[sof[3]], pr[dof[3]]);
+      const double v1 = fma(-l1, pr[sof[1]], pr[dof[1]]);
+      const double e = fma(-pn, r0, 1.0);
+      const double v2 = fma(-l2, pr[sof[2]], pr[dof[2]]);
+      const double t = fma(e, e, e);
+      const double v3 = fma(-l3, pr[sof[3]], pr[dof[3]]);
+      const double rn = fma(r0, t, r0);
+      pr[dof[1]] = v1;
+      pr[dof[2]] = v2;
+      if (s3) pr[dof[3]] = v3;
+      if (j + 1 < ne) {
+        if (!rcp64_in_range(pn)) bad = true;
+        rp = rn;
+      }
       __syncwarp();
     }
   }
@@ -231,8 +246,8 @@ __global__ void __launch_bounds__(128) k_gen_limb_factor(SolveGenArgs a) {
       if (u == 0 && j + 1 < ne) {
         // the next pivot (lane 1's first slot), its reciprocal off the chain
         const double pn = __shfl_sync(kFull, v0, 1);
-        if (zero_or_nonfinite(pn)) bad = true;
-        else rp = limb_recip(pn);
+        if (!rcp64_in_range(pn)) bad = true;
+        else rp = rcp64(pn);
       }
     }
     __syncwarp();

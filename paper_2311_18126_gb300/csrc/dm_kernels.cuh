@@ -125,14 +125,17 @@ struct AsmArgs {
 // r <- r (1 + e + e^2) with e = 1 - d r (the truncated series of
 // r / (1 - e)), leaves a relative error of about e^3 ~ 2^-66, below FP64
 // rounding: three FP64 instructions, no FP32/FP64 conversions.
-__device__ __forceinline__ double rcp64(double d) {
+__device__ __forceinline__ double rcp64_seed(double d) {  // the FP32 seed, as FP64
   const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
   const unsigned fb = (hi & 0x80000000u) | (((hi & 0x7FFFFFFFu) - 0x38000000u) << 3) | (lo >> 29);
   float sf;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(sf) : "f"(__uint_as_float(fb)));
   const unsigned sb = __float_as_uint(sf);
-  const double r = __hiloint2double(
-      (int)((sb & 0x80000000u) | (((sb & 0x7FFFFFFFu) >> 3) + 0x38000000u)), (int)(sb << 29));
+  return __hiloint2double((int)((sb & 0x80000000u) | (((sb & 0x7FFFFFFFu) >> 3) + 0x38000000u)),
+                          (int)(sb << 29));
+}
+__device__ __forceinline__ double rcp64(double d) {
+  const double r = rcp64_seed(d);
   const double e = fma(-d, r, 1.0);
   return fma(r, fma(e, e, e), r);
 }
