@@ -404,6 +404,18 @@ def run_ours(args):
         roof.update({"achieved": ach, "frac": ach / (peak_fp64 / 1e3),
                      "flops_per_unit": fpu, "unit_name": UNIT_NAME.get(dom),
                      "units_per_launch": units / launches})
+        if dom == "band_ldlt_solve":
+            # the executed count includes the lanes' redundant work (the
+            # reciprocal by all eight lanes of a chain, idle multiplier
+            # lanes); the LDL^T's own arithmetic per eliminated column and
+            # its back-substitution row is 10 multipliers, 55 symmetric
+            # updates, 10 right-hand-side updates, the reciprocal and z_j,
+            # and 10 updates: 162 flops, plus about 730 per rod for the
+            # 10 x 10 separator
+            n = 4 * np.asarray(desc["nodes_per_rod"], dtype=np.float64) - 1
+            own = float((162.0 * (n - 10) + 730.0).sum() / n.sum())
+            roof.update({"own_flops_per_unit": round(own, 1),
+                         "frac_own_flops": ach * own / fpu / (peak_fp64 / 1e3)})
     else:
         roof.update({"achieved": None, "frac": None})
     counts = os.path.join(ROOT, "profiles", "kernel_fp64_counts.json")
