@@ -412,8 +412,8 @@ def run_ours(args):
             # updates, 10 right-hand-side updates, the reciprocal and z_j,
             # and 10 updates: 162 flops, plus about 730 per rod for the
             # 10 x 10 separator
-            n = 4 * np.asarray(desc["nodes_per_rod"], dtype=np.float64) - 1
-            own = float((162.0 * (n - 10) + 730.0).sum() / n.sum())
+            nr = 4 * np.asarray(desc["nodes_per_rod"], dtype=np.float64) - 1
+            own = float((162.0 * (nr - 10) + 730.0).sum() / nr.sum())
             roof.update({"own_flops_per_unit": round(own, 1),
                          "frac_own_flops": ach * own / fpu / (peak_fp64 / 1e3)})
     else:
