@@ -261,11 +261,20 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
     return;
   }
   double h[36];
+  {
+    // gradients pre-scaled by the stiffnesses: three FP64 instructions an entry
+    double a1[8], a2[8], a3[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i) {
+      a1[i] = kbs * g1[i];
+      a2[i] = kbs * g2[i];
+      a3[i] = kts * g3[i];
+    }
 #pragma unroll
-    for (int j = i; j < 8; ++j)
-      h[up<8>(i, j)] = kbs * fma(g1[i], g1[j], g2[i] * g2[j]) + kts * g3[i] * g3[j];
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = i; j < 8; ++j) h[up<8>(i, j)] = fma(a1[i], g1[j], fma(a2[i], g2[j], a3[i] * g3[j]));
+  }
 
   // second-derivative part, first in tangent space then projected
   const v3 w = c1 * M2 - c2 * M1;
@@ -419,18 +428,25 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
       g8[i] -= EA * cmp(ga, i);
       g8[3 + i] -= EB * cmp(gb, i);
     }
+    // grad chi_A lives on entries 0-2, grad chi_B on 3-5: only the terms
+    // whose factors are not structurally zero are formed (a product with a
+    // literal zero is not dropped by an IEEE-conforming compiler)
+    v3 hga_a = HAA * ga, hab_a = HAB * ga, hgb_b = HBB * gb;
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
       for (int j = i; j < 8; ++j) {
-        const double Gai = i < 3 ? cmp(ga, i) : 0.0, Gaj = j < 3 ? cmp(ga, j) : 0.0;
-        const double Gbi = (i >= 3 && i < 6) ? cmp(gb, i - 3) : 0.0;
-        const double Gbj = (j >= 3 && j < 6) ? cmp(gb, j - 3) : 0.0;
-        double v = -(colA[i] * Gaj + Gai * colA[j]) - (colB[i] * Gbj + Gbi * colB[j]);
-        v += HAA * Gai * Gaj + HBB * Gbi * Gbj + HAB * (Gai * Gbj + Gbi * Gaj);
-        if (i < 3 && j < 3) v -= EA * Ha[up<3>(i, j)];
-        if (i >= 3 && i < 6 && j >= 3 && j < 6) v -= EB * Hb[up<3>(i - 3, j - 3)];
-        h[up<8>(i, j)] += v;
+        const bool ai = i < 3, aj = j < 3, bi = i >= 3 && i < 6, bj = j >= 3 && j < 6;
+        if (!ai && !bi) continue;  // i, j >= 6: no correction
+        double v = h[up<8>(i, j)];
+        if (aj) v = fma(-colA[i], cmp(ga, j), v);
+        if (ai) v = fma(-cmp(ga, i), colA[j], v);
+        if (bj) v = fma(-colB[i], cmp(gb, j - 3), v);
+        if (bi) v = fma(-cmp(gb, i - 3), colB[j], v);
+        if (ai && aj) v = fma(cmp(hga_a, i), cmp(ga, j), fma(-EA, Ha[up<3>(i, j)], v));
+        if (ai && bj) v = fma(cmp(hab_a, i), cmp(gb, j - 3), v);
+        if (bi && bj) v = fma(cmp(hgb_b, i - 3), cmp(gb, j - 3), fma(-EB, Hb[up<3>(i - 3, j - 3)], v));
+        h[up<8>(i, j)] = v;
       }
     if (a.dk) {
       // gradients of kappa1 and kappa2 as functions of the 11 DOFs (the
