@@ -116,6 +116,9 @@ def parse():
                     help="backward Euler (default) or implicit midpoint (Sec. III-C)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes")
+    ap.add_argument("--split-first", action="store_true",
+                    help="run a step's first Newton round with the split passes (for "
+                         "counting the split kernels with every unit active)")
     ap.add_argument("--rows", type=int, default=0,
                     help="mlp workload: rows of the inference batch (a multiple of 128; "
                          "default the 444544 segments of the 4096-rod batch)")
@@ -326,6 +329,8 @@ def run_ours(args):
     params["predictor"] = args.predictor
     R = len(desc["nodes_per_rod"])
     sysm = System(desc, params)
+    if args.split_first:
+        sysm.set_fused_first(False)
     sysm.set_natural_curvature(0, R, kbar)
     peak_fp64 = fp64_peak_gflops()
 
@@ -453,6 +458,7 @@ def run_ours(args):
                        "dofs_per_gpu": int(n), "dt": params["dt"], "newton_tol": params["tol"],
                        "line_search": bool(params.get("line_search", False)),
                        "predictor": params.get("predictor", "extrapolate"),
+                       "first_round": "split" if args.split_first else "fused",
                        "parallelism": "dp%d: each GPU steps a DOF-balanced shard of contiguous systems of one batch %d x the one-GPU size" % (ws, ws),
                        "l2": "no flush: per-iteration working set (~0.7 GB) exceeds L2"},
             "newton": {"iters_mean": float(it.mean()), "iters_max": int(it.max()),

@@ -484,6 +484,15 @@ dm_status dm_set_profiling(dm_system *sys, int32_t enable); /* also resets */
  * (per-launch events). */
 dm_status dm_set_graphs(dm_system *sys, int32_t enable);
 
+/* The first Newton round of a step (whose guess essentially never meets the
+ * tolerance) runs the fused passes: one kernel for the bend-twist
+ * gradients and Hessians, one for the residual and band rows (default, 1).
+ * Off (0): it runs the split passes of the later rounds (residual pass,
+ * then the Jacobian pass for the systems above the tolerance), the same
+ * arithmetic per entry in a different kernel grouping: results equal to
+ * rounding.  Batches with rod networks always run the fused passes. */
+dm_status dm_set_fused_first(dm_system *sys, int32_t enable);
+
 /* Launch shapes chosen by dm_autotune. */
 typedef struct dm_tuning {
   int32_t edge_threads;        /* threads per block, edge frames + stretch        */

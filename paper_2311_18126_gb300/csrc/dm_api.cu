@@ -159,6 +159,7 @@ struct Extra {
   } tune;
   // Newton rounds as one CUDA graph: a device-side while loop over rounds
   bool graphs = true;
+  bool fused_first = true;  // first round of a step: fused gradient+Hessian passes
   cudaStream_t cap_stream = nullptr;
   // a side branch of a round (the ground-contact node terms, independent of
   // the edge and stencil kernels), forked and joined by events
@@ -806,7 +807,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   // the fused passes (without a learned guess, whose trial round may be
   // rejected)
   const bool split = !gen_on;
-  const bool fuse_first = split && !ws_on;
+  const bool fuse_first = split && !ws_on && s->x.fused_first;
   // the node terms run beside the edge and stencil kernels (not while
   // profiling, whose events time each kernel alone)
   const bool fork_nodes = T.ground && !s->x.prof;
@@ -1561,6 +1562,15 @@ dm_status dm_set_graphs(dm_system *sys, int32_t enable) {
     return DM_ERR_INVALID_ARG;
   }
   static_cast<dm_system_ext *>(sys)->x.graphs = enable != 0;
+  return DM_OK;
+}
+
+dm_status dm_set_fused_first(dm_system *sys, int32_t enable) {
+  if (!sys) {
+    set_error("dm_set_fused_first: NULL handle");
+    return DM_ERR_INVALID_ARG;
+  }
+  static_cast<dm_system_ext *>(sys)->x.fused_first = enable != 0;
   return DM_OK;
 }
 

@@ -121,21 +121,49 @@ __host__ __device__ constexpr int up(int i, int j) {
 
 // H8[blk] += s * (x y^T + y x^T) on a 3x3 diagonal block starting at o
 __device__ __forceinline__ void add_sym(double *h, int o, double s, v3 x, v3 y) {
+  const v3 sx = s * x;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = i; j < 3; ++j)
-      h[up<8>(o + i, o + j)] += s * fma(cmp(x, i), cmp(y, j), cmp(y, i) * cmp(x, j));
+      h[up<8>(o + i, o + j)] = fma(cmp(sx, i), cmp(y, j), fma(cmp(y, i), cmp(sx, j), h[up<8>(o + i, o + j)]));
+}
+
+// s x for s = +-1 given as a sign word (0 or 0x80000000): the sign bit
+// flipped on the integer pipe, the same value as the FP64 product
+__device__ __forceinline__ double sgnmul(unsigned sw, double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)sw, __double2loint(x));
+}
+__device__ __forceinline__ unsigned sign_word(int s) { return s < 0 ? 0x80000000u : 0u; }
+__device__ __forceinline__ v3 sgn3(int s, v3 v) {
+  const unsigned sw = sign_word(s);
+  return mk(sgnmul(sw, v.x), sgnmul(sw, v.y), sgnmul(sw, v.z));
 }
 
 __device__ __forceinline__ void load_edge(const double *ef, int NE, int e, int sgn,
                                           v3 &t, double &il, v3 &d1, v3 &m1, v3 &m2) {
-  const double s = (double)sgn;
-  t = mk(s * ef[e], s * ef[NE + e], s * ef[2 * NE + e]);
+  const unsigned sw = sign_word(sgn);
+  t = mk(sgnmul(sw, ef[e]), sgnmul(sw, ef[NE + e]), sgnmul(sw, ef[2 * NE + e]));
   il = ef[3 * NE + e];
   d1 = mk(ef[4 * NE + e], ef[5 * NE + e], ef[6 * NE + e]);
   m1 = mk(ef[7 * NE + e], ef[8 * NE + e], ef[9 * NE + e]);
-  m2 = mk(s * ef[10 * NE + e], s * ef[11 * NE + e], s * ef[12 * NE + e]);
+  m2 = mk(sgnmul(sw, ef[10 * NE + e]), sgnmul(sw, ef[11 * NE + e]), sgnmul(sw, ef[12 * NE + e]));
+}
+
+// Slot p of the 11 DOFs [x0 (0-2), th_a (3), x1 (4-6), th_b (7), x2 (8-10)]
+// as a combination of the 8-space (e_a 0-2, e_b 3-5, A 6, B 7): x0 = -e_a,
+// x1 = e_a - e_b, x2 = e_b, th_a = sa A, th_b = sb B.  Term t (0, 1) of
+// slot p: its 8-space index (-1: none) and weight (1: +1, -1: -1, 2: sa,
+// 3: sb).
+__host__ __device__ constexpr int slot_index(int p, int t) {
+  return p == 3 ? (t == 0 ? 6 : -1)
+       : p == 7 ? (t == 0 ? 7 : -1)
+       : p < 3  ? (t == 0 ? p : -1)
+       : p < 7  ? (t == 0 ? p - 4 : p - 1)
+                : (t == 0 ? p - 5 : -1);
+}
+__host__ __device__ constexpr int slot_weight(int p, int t) {
+  return p == 3 ? 2 : p == 7 ? 3 : p < 3 ? -1 : p < 7 ? (t == 0 ? 1 : -1) : 1;
 }
 
 // Gradient of one stencil in its 11 DOFs: (e_a, e_b, A, B) -> [x0, th_a,
@@ -151,8 +179,8 @@ __device__ __forceinline__ void write_gradient(const StencilArgs &a, int k, cons
     G[(4 + c) * NS + k] = g8[c] - g8[3 + c];
     G[(8 + c) * NS + k] = g8[3 + c];
   }
-  G[3 * NS + k] = sa * g8[6];
-  G[7 * NS + k] = sb * g8[7];
+  G[3 * NS + k] = sgnmul(sign_word(sa), g8[6]);
+  G[7 * NS + k] = sgnmul(sign_word(sb), g8[7]);
 }
 
 // The Hessian pass runs for a system only if the solver will factor its
@@ -213,7 +241,7 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
     if (a.frames_only) return;
   }
   const double tha = a.q[a.st_th[k]], thb = a.q[a.st_th[NS + k]];
-  const double tau = sb * thb - sa * tha + beta;
+  const double tau = sgnmul(sign_word(sb), thb) - sgnmul(sign_word(sa), tha) + beta;
   const double kbs = a.st_kb[k], kts = a.st_kt[k];
   const double c1 = kbs * (k1 - a.kbar[k]);
   const double c2 = kbs * (k2 - a.kbar[NS + k]);
@@ -247,9 +275,9 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
   for (int i = 0; i < 8; ++i) g8[i] = fma(c1, g1[i], fma(c2, g2[i], c3 * g3[i]));
   if (MODE == 1) {
     // the holonomy correction of the gradient (see the Hessian block below)
-    const v3 tna = (double)sa * mk(a.tn[a.st_ed[k]], a.tn[NE + a.st_ed[k]], a.tn[2 * NE + a.st_ed[k]]);
-    const v3 tnb = (double)sb * mk(a.tn[a.st_ed[NS + k]], a.tn[NE + a.st_ed[NS + k]],
-                                   a.tn[2 * NE + a.st_ed[NS + k]]);
+    const v3 tna = sgn3(sa, mk(a.tn[a.st_ed[k]], a.tn[NE + a.st_ed[k]], a.tn[2 * NE + a.st_ed[k]]));
+    const v3 tnb = sgn3(sb, mk(a.tn[a.st_ed[NS + k]], a.tn[NE + a.st_ed[NS + k]],
+                                   a.tn[2 * NE + a.st_ed[NS + k]]));
     const v3 ga = ila * ((1.0 / (1.0 + dot(tna, ta))) * cross(tna, ta));
     const v3 gb = ilb * ((1.0 / (1.0 + dot(tnb, tb))) * cross(tnb, tb));
 #pragma unroll
@@ -297,11 +325,16 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
     add_sym(h, 0, s2, Xa, pb);
     add_sym(h, 0, 0.25 * s2, perp(ta, Pa), kb);
     add_sym(h, 0, -s2, ta, hga);
+    {
+      // - s2 tga (I - t_a t_a^T)
+      const double c = s2 * tga;
+      const v3 ct = c * ta;
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+      for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = i; j < 3; ++j)
-        h[up<8>(i, j)] -= s2 * tga * ((i == j ? 1.0 : 0.0) - cmp(ta, i) * cmp(ta, j));
+        for (int j = i; j < 3; ++j)
+          h[up<8>(i, j)] = fma(cmp(ct, i), cmp(ta, j), i == j ? h[up<8>(i, j)] - c : h[up<8>(i, j)]);
+    }
   }
   // bb block
   {
@@ -310,11 +343,16 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
     add_sym(h, 3, s2, Xb, pa);
     add_sym(h, 3, 0.25 * s2, perp(tb, Pb), kb);
     add_sym(h, 3, -s2, tb, hgb);
+    {
+      const double c = s2 * tga;
+      const v3 ct = c * tb;
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+      for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = i; j < 3; ++j)
-        h[up<8>(3 + i, 3 + j)] -= s2 * tga * ((i == j ? 1.0 : 0.0) - cmp(tb, i) * cmp(tb, j));
+        for (int j = i; j < 3; ++j)
+          h[up<8>(3 + i, 3 + j)] =
+              fma(cmp(ct, i), cmp(tb, j), i == j ? h[up<8>(3 + i, 3 + j)] - c : h[up<8>(3 + i, 3 + j)]);
+    }
   }
   // ab block: M = -ichi [w]x - ichi^2 (alpha_a t_a^T + t_b alpha_b^T)
   //               + (kw ichi^2) t_b t_a^T - kw ichi/2 I
@@ -382,9 +420,9 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
   // hess_e chi = -[ (n s^T + s n^T) / (2 c^2) + w t^T + t w^T ] / l^2,
   // n = t_n x t, c = 1 + t_n.t, s = t_n - (t_n.t) t.
   {
-    const v3 tna = (double)sa * mk(a.tn[a.st_ed[k]], a.tn[NE + a.st_ed[k]], a.tn[2 * NE + a.st_ed[k]]);
-    const v3 tnb = (double)sb * mk(a.tn[a.st_ed[NS + k]], a.tn[NE + a.st_ed[NS + k]],
-                                   a.tn[2 * NE + a.st_ed[NS + k]]);
+    const v3 tna = sgn3(sa, mk(a.tn[a.st_ed[k]], a.tn[NE + a.st_ed[k]], a.tn[2 * NE + a.st_ed[k]]));
+    const v3 tnb = sgn3(sb, mk(a.tn[a.st_ed[NS + k]], a.tn[NE + a.st_ed[NS + k]],
+                                   a.tn[2 * NE + a.st_ed[NS + k]]));
     v3 ga, gb;
     double Ha[6], Hb[6];
     {
@@ -470,8 +508,8 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
           o[(size_t)(4 + i) * NS] = e8[i] - e8[3 + i];
           o[(size_t)(8 + i) * NS] = e8[3 + i];
         }
-        o[(size_t)3 * NS] = sa * e8[6];
-        o[(size_t)7 * NS] = sb * e8[7];
+        o[(size_t)3 * NS] = sgnmul(sign_word(sa), e8[6]);
+        o[(size_t)7 * NS] = sgnmul(sign_word(sb), e8[7]);
       }
     }
   }
@@ -480,32 +518,32 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
 
   // H11 = T^T H8 T written as packed upper triangle
   auto H8 = [&](int i, int j) -> double { return i <= j ? h[up<8>(i, j)] : h[up<8>(j, i)]; };
-  // coefficient rows: slot -> list of (8-space index, weight)
+  // each entry a signed sum of H8 entries, from its first term (no add of
+  // a zero), the signs sa, sb applied on the integer pipe
   double *Ho = a.sh;
+  const unsigned swa = sign_word(sa), swb = sign_word(sb);
 #pragma unroll
   for (int p = 0; p < 11; ++p)
 #pragma unroll
     for (int q = p; q < 11; ++q) {
-      // slot p combination
       double v = 0.0;
+      bool first = true;
 #pragma unroll
       for (int tp = 0; tp < 2; ++tp)
 #pragma unroll
         for (int tq = 0; tq < 2; ++tq) {
-          int ip, iq;
-          double wp, wq;
-          // decode slot -> (index, weight) pairs
-          if (p == 3) { ip = (tp == 0) ? 6 : -1; wp = sa; }
-          else if (p == 7) { ip = (tp == 0) ? 7 : -1; wp = sb; }
-          else if (p < 3) { ip = (tp == 0) ? p : -1; wp = -1.0; }
-          else if (p < 7) { ip = (tp == 0) ? (p - 4) : (p - 4 + 3); wp = (tp == 0) ? 1.0 : -1.0; }
-          else { ip = (tp == 0) ? (p - 8 + 3) : -1; wp = 1.0; }
-          if (q == 3) { iq = (tq == 0) ? 6 : -1; wq = sa; }
-          else if (q == 7) { iq = (tq == 0) ? 7 : -1; wq = sb; }
-          else if (q < 3) { iq = (tq == 0) ? q : -1; wq = -1.0; }
-          else if (q < 7) { iq = (tq == 0) ? (q - 4) : (q - 4 + 3); wq = (tq == 0) ? 1.0 : -1.0; }
-          else { iq = (tq == 0) ? (q - 8 + 3) : -1; wq = 1.0; }
-          if (ip >= 0 && iq >= 0) v += wp * wq * H8(ip, iq);
+          const int ip = slot_index(p, tp), iq = slot_index(q, tq);
+          if (ip < 0 || iq < 0) continue;
+          const int wp = slot_weight(p, tp), wq = slot_weight(q, tq);
+          const bool neg = (wp == -1) != (wq == -1);
+          const unsigned sw = (wp == 2 ? swa : wp == 3 ? swb : 0u) ^ (wq == 2 ? swa : wq == 3 ? swb : 0u);
+          if (first) {
+            v = sgnmul(sw ^ (neg ? 0x80000000u : 0u), H8(ip, iq));
+            first = false;
+          } else {
+            const double x = sgnmul(sw, H8(ip, iq));
+            v = neg ? v - x : v + x;
+          }
         }
       Ho[up<11>(p, q) * NS + k] = v;
     }

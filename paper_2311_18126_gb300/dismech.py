@@ -114,6 +114,8 @@ def load_library(path=LIB_PATH):
     lib.dm_set_tuning.restype = C.c_int
     lib.dm_set_graphs.argtypes = [H, C.c_int32]
     lib.dm_set_graphs.restype = C.c_int
+    lib.dm_set_fused_first.argtypes = [H, C.c_int32]
+    lib.dm_set_fused_first.restype = C.c_int
     lib.dm_set_profiling.argtypes = [H, C.c_int32]
     lib.dm_set_profiling.restype = C.c_int
     lib.dm_get_profile.argtypes = [H, C.POINTER(Profile)]
@@ -405,6 +407,10 @@ class System:
     def set_graphs(self, enable=True):
         """Newton rounds as one CUDA graph per step (default) or host-driven."""
         _check(self._lib.dm_set_graphs(self._h, int(bool(enable))))
+
+    def set_fused_first(self, enable=True):
+        """First round of a step by the fused passes (default) or the split ones."""
+        _check(self._lib.dm_set_fused_first(self._h, int(bool(enable))))
 
     def set_profiling(self, enable=True):
         _check(self._lib.dm_set_profiling(self._h, int(bool(enable))))

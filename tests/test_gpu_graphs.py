@@ -156,3 +156,29 @@ def test_set_tuning_applies_shapes_and_rejects_others():
         assert np.array_equal(a.get_state()[0], b.get_state()[0])
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_split_first_round_matches_fused(graphs):
+    """The first Newton round by the split passes (gradient pass, then the
+    Hessian pass) against the fused passes: the same arithmetic per entry in
+    another kernel grouping, so the same iteration counts and states to
+    rounding."""
+    desc, params, kbar = workloads.uneven_rods(n_rods=48, seed=6, n_min=20, n_max=90)
+    runs = []
+    for fused in (True, False):
+        s = _gpu(desc, params)
+        s.set_graphs(graphs)
+        s.set_fused_first(fused)
+        s.set_natural_curvature(0, s.n_rods, kbar)
+        its, qs = [], []
+        for _ in range(4):
+            s.step(1)
+            its.append(s.iterations)
+            qs.append(np.concatenate(s.get_state()))
+        runs.append((np.array(its), np.array(qs)))
+        s.close()
+    (ia, qa), (ib, qb) = runs
+    assert ia.sum() > 0 and np.array_equal(ia, ib)
+    scale = np.maximum(1.0, np.abs(qb).max(axis=1, keepdims=True))
+    assert np.max(np.abs(qa - qb) / scale) < 1e-12
