@@ -360,15 +360,15 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
   {
     double Mab[3][3];
     const double ca = -0.5 * kw * ichi;
+    // the rank-one parts as Ev t_a^T + Bv wxta^T
+    const v3 Ev = axpy(-ichi2, tbxw, axpy(kw * ichi2, tb, (-0.5 * c3 * ichi) * kb));
+    const v3 Bv = (-ichi2) * tb;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        double v = -ichi2 * fma(cmp(tbxw, i), cmp(ta, j), cmp(tb, i) * cmp(wxta, j));
-        v = fma(kw * ichi2, cmp(tb, i) * cmp(ta, j), v);
-        v = fma(-0.5 * c3 * ichi, cmp(kb, i) * cmp(ta, j), v);
-        if (i == j) v += ca;
-        Mab[i][j] = v;
+        const double v = fma(cmp(Ev, i), cmp(ta, j), cmp(Bv, i) * cmp(wxta, j));
+        Mab[i][j] = i == j ? v + ca : v;
       }
     // skew parts: -ichi [w]x + c3 ichi [t_a]x = [z]x with z = ichi (c3 t_a - w)
     const v3 z = ichi * axpy(c3, ta, (-1.0) * w);
@@ -383,12 +383,15 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
     for (int i = 0; i < 3; ++i) cc[i] = Mab[i][0] * tb.x + Mab[i][1] * tb.y + Mab[i][2] * tb.z;
     const double sc = r[0] * tb.x + r[1] * tb.y + r[2] * tb.z;
     const double s2 = ila * ilb;
+    // M - t_a r^T - cc t_b^T + sc t_a t_b^T = M - t_a (r - sc t_b)^T - cc t_b^T
+#pragma unroll
+    for (int j = 0; j < 3; ++j) r[j] = fma(-sc, cmp(tb, j), r[j]);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        double v = Mab[i][j] - cmp(ta, i) * r[j] - cc[i] * cmp(tb, j) + sc * cmp(ta, i) * cmp(tb, j);
-        h[up<8>(i, 3 + j)] += s2 * v;
+        const double v = fma(-cmp(ta, i), r[j], fma(-cc[i], cmp(tb, j), Mab[i][j]));
+        h[up<8>(i, 3 + j)] = fma(s2, v, h[up<8>(i, 3 + j)]);
       }
   }
   // theta cross blocks: -1/2 P ga(R), ga(v) = 2 ichi (t_b x v) - (kb.v) ichi t_b,
@@ -431,13 +434,14 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
       const v3 sp = axpy(-dot(tna, ta), ta, tna);
       ga = ila * w;
       const double f1 = -0.5 * ic * ic * ila * ila, f2 = -ila * ila;
+      const v3 fn = f1 * n, fw = f2 * w;
       int e = 0;
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j, ++e)
-          Ha[e] = f1 * fma(cmp(n, i), cmp(sp, j), cmp(sp, i) * cmp(n, j)) +
-                  f2 * fma(cmp(w, i), cmp(ta, j), cmp(ta, i) * cmp(w, j));
+          Ha[e] = fma(cmp(fn, i), cmp(sp, j),
+                      fma(cmp(sp, i), cmp(fn, j), fma(cmp(fw, i), cmp(ta, j), cmp(ta, i) * cmp(fw, j))));
     }
     {
       const double c = 1.0 + dot(tnb, tb), ic = 1.0 / c;
@@ -445,13 +449,14 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
       const v3 sp = axpy(-dot(tnb, tb), tb, tnb);
       gb = ilb * w;
       const double f1 = -0.5 * ic * ic * ilb * ilb, f2 = -ilb * ilb;
+      const v3 fn = f1 * n, fw = f2 * w;
       int e = 0;
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j, ++e)
-          Hb[e] = f1 * fma(cmp(n, i), cmp(sp, j), cmp(sp, i) * cmp(n, j)) +
-                  f2 * fma(cmp(w, i), cmp(tb, j), cmp(tb, i) * cmp(w, j));
+          Hb[e] = fma(cmp(fn, i), cmp(sp, j),
+                      fma(cmp(sp, i), cmp(fn, j), fma(cmp(fw, i), cmp(tb, j), cmp(tb, i) * cmp(fw, j))));
     }
     double colA[8], colB[8];
 #pragma unroll
