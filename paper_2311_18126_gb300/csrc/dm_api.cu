@@ -290,7 +290,11 @@ static dm_status create_impl(const dm_system_desc *desc, const dm_params *prm,
   DM_TRY(upload(s, &d.edge_b, eb));
   DM_TRY(upload(s, &d.edge_th, T.edge_thdof));
   DM_TRY(upload(s, &d.edge_sys, T.edge_sys));
-  DM_TRY(upload(s, &d.edge_lbar, T.edge_lbar));
+  {
+    std::vector<double> il(T.edge_lbar.size());
+    for (size_t e = 0; e < il.size(); ++e) il[e] = 1.0 / T.edge_lbar[e];
+    DM_TRY(upload(s, &d.edge_ilbar, il));
+  }
   DM_TRY(upload(s, &d.edge_EA, T.edge_EA));
   std::vector<double> soa(3 * ne);
   for (int64_t e = 0; e < ne; ++e)
@@ -696,7 +700,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   const int nd = (int)T.n_dofs, ne = (int)T.n_edges, ns = (int)T.n_stencils, S = T.n_systems;
   StepArgs sa{nd, ne, ns, S, s->p.dt, d.q, d.qn, d.vn, d.d1n, d.tn, d.beta_n, d.ef, d.beta_it,
               d.fixed, d.sys_active, d.sys_iters, d.sys_status, d.sys_res};
-  EdgeArgs ea{ne, d.q, d.edge_a, d.edge_b, d.edge_th, d.edge_sys, d.edge_EA, d.edge_lbar,
+  EdgeArgs ea{ne, d.q, d.edge_a, d.edge_b, d.edge_th, d.edge_sys, d.edge_EA, d.edge_ilbar,
               d.tn, d.d1n, d.sys_active, d.sys_status, d.ef, d.es,
               s->x.prof ? s->x.d_units + K_EDGE : nullptr};
   StencilArgs ka{ns, ne, d.q, d.ef, d.tn, d.st_ed, d.st_th, d.st_sg, d.st_sys, d.st_kb, d.st_kt,
@@ -734,7 +738,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
   ra.tol = s->p.tol;
   ra.ls_action = ls_act;
   ra.fc = contact_on ? s->x.cc.fc : nullptr;
-  ra.nd = nd; ra.ns = ns; ra.ne = ne; ra.dt = s->p.dt;
+  ra.nd = nd; ra.ns = ns; ra.ne = ne; ra.dt = s->p.dt; ra.idt = 1.0 / s->p.dt;
   for (int c = 0; c < 3; ++c) ra.g[c] = s->p.g[c];
   ra.eta = s->p.eta;
   ra.q = d.q; ra.qn = d.qn; ra.vn = d.vn; ra.mass = d.mass; ra.rscale = d.rscale;
@@ -753,7 +757,7 @@ dm_status dm_step(dm_system *sys, int32_t nsteps, dm_step_stats *stats) {
               s->x.prof ? s->x.d_units + K_NODES : nullptr};
   RowGenArgs rg{};
   rg.units = s->x.prof ? s->x.d_units + K_ROWS_GEN : nullptr;
-  rg.nd = nd; rg.ns = ns; rg.ne = ne; rg.nn = nn; rg.dt = s->p.dt;
+  rg.nd = nd; rg.ns = ns; rg.ne = ne; rg.nn = nn; rg.dt = s->p.dt; rg.idt = 1.0 / s->p.dt;
   for (int c = 0; c < 3; ++c) rg.g[c] = s->p.g[c];
   rg.q = d.q; rg.qn = d.qn; rg.vn = d.vn; rg.mass = d.mass; rg.rscale = d.rscale;
   rg.damp = s->x.d_damp; rg.fixed = d.fixed; rg.dof_sys = s->x.d_dof_sys; rg.dof_node = d.dof_node;
@@ -1725,7 +1729,7 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
   DM_CK(cudaMemcpyAsync(d.sys_active, ones.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   DM_CK(cudaMemsetAsync(d.sys_status, 0, S * sizeof(int32_t), st));
   DM_CK(cudaMemsetAsync(d.sys_res, 0, S * sizeof(unsigned long long), st));
-  EdgeArgs ea{ne, d.q, d.edge_a, d.edge_b, d.edge_th, d.edge_sys, d.edge_EA, d.edge_lbar,
+  EdgeArgs ea{ne, d.q, d.edge_a, d.edge_b, d.edge_th, d.edge_sys, d.edge_EA, d.edge_ilbar,
               d.tn, d.d1n, d.sys_active, d.sys_status, d.ef, d.es, nullptr};
   StencilArgs ka{ns, ne, d.q, d.ef, d.tn, d.st_ed, d.st_th, d.st_sg, d.st_sys, d.st_kb, d.st_kt,
                  d.kbar, d.taubar, d.beta_n, d.sys_active, d.sys_status, d.beta_it, d.sg, d.sh,
@@ -1769,7 +1773,7 @@ dm_status dm_step_adjoint(dm_system *sys, const double *q_next, const double *gq
   if (!rod_d0.empty() || contact_on) {
     RowArgs ra{};
     ra.fc = contact_on ? s->x.cc.fc : nullptr;
-    ra.nd = nd; ra.ns = ns; ra.ne = ne; ra.dt = s->p.dt;
+    ra.nd = nd; ra.ns = ns; ra.ne = ne; ra.dt = s->p.dt; ra.idt = 1.0 / s->p.dt;
     for (int c = 0; c < 3; ++c) ra.g[c] = s->p.g[c];
     ra.eta = s->p.eta;
     ra.q = d.q; ra.qn = d.qn; ra.vn = d.vn; ra.mass = d.mass; ra.rscale = d.rscale;

@@ -49,7 +49,7 @@ __device__ __forceinline__ void k_edge_one(EdgeArgs a, const int e) {
   }
   // time-parallel transport of d1 from t_n to t (d1 normal to t_n)
   const double px = a.d1n[e], py = a.d1n[NE + e], pz = a.d1n[2 * NE + e];
-  const double k = (px * tx + py * ty + pz * tz) / c;
+  const double k = (px * tx + py * ty + pz * tz) * rcp64(c);  // c in (1e-12, 2]
   const double d1x = px - k * (nx + tx), d1y = py - k * (ny + ty), d1z = pz - k * (nz + tz);
   const double d2x = ty * d1z - tz * d1y, d2y = tz * d1x - tx * d1z, d2z = tx * d1y - ty * d1x;
   double sn, cs;
@@ -70,7 +70,7 @@ __device__ __forceinline__ void k_edge_one(EdgeArgs a, const int e) {
   o[12 * NE + e] = -sn * d1z + cs * d2z;
   // stretching: dE/dx_b = EA (l/lbar - 1) t,
   // Hessian block K = EA/l t t^T + EA (1/lbar - 1/l) I
-  const double EA = a.edge_EA[e], ilb = 1.0 / a.edge_lbar[e];
+  const double EA = a.edge_EA[e], ilb = a.edge_ilbar[e];
   const double fm = EA * (l * ilb - 1.0);
   const double al = EA * (ilb - il), be = EA * il;
   double *w = a.es;
@@ -219,7 +219,7 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
     if (MODE != 2) atomicMax(&a.sys_status[sys], (int)DM_ERR_DEGENERATE);
     return;
   }
-  const double ichi = 1.0 / chi;
+  const double ichi = rcp64(chi);  // chi in (1e-12, 2]
   const v3 kb = (2.0 * ichi) * cross(ta, tb);
   const v3 M1 = m1a + m1b, M2 = m2a + m2b;
   // Eq. 5: material curvatures
@@ -278,8 +278,8 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
     const v3 tna = sgn3(sa, mk(a.tn[a.st_ed[k]], a.tn[NE + a.st_ed[k]], a.tn[2 * NE + a.st_ed[k]]));
     const v3 tnb = sgn3(sb, mk(a.tn[a.st_ed[NS + k]], a.tn[NE + a.st_ed[NS + k]],
                                    a.tn[2 * NE + a.st_ed[NS + k]]));
-    const v3 ga = ila * ((1.0 / (1.0 + dot(tna, ta))) * cross(tna, ta));
-    const v3 gb = ilb * ((1.0 / (1.0 + dot(tnb, tb))) * cross(tnb, tb));
+    const v3 ga = ila * (rcp64(1.0 + dot(tna, ta)) * cross(tna, ta));
+    const v3 gb = ilb * (rcp64(1.0 + dot(tnb, tb)) * cross(tnb, tb));
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       g8[i] -= g8[6] * cmp(ga, i);
@@ -429,7 +429,7 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
     v3 ga, gb;
     double Ha[6], Hb[6];
     {
-      const double c = 1.0 + dot(tna, ta), ic = 1.0 / c;
+      const double c = 1.0 + dot(tna, ta), ic = rcp64(c);
       const v3 n = cross(tna, ta), w = ic * n;
       const v3 sp = axpy(-dot(tna, ta), ta, tna);
       ga = ila * w;
@@ -444,7 +444,7 @@ __device__ __forceinline__ void k_stencil_one(StencilArgs a, const int k) {
                       fma(cmp(sp, i), cmp(fn, j), fma(cmp(fw, i), cmp(ta, j), cmp(ta, i) * cmp(fw, j))));
     }
     {
-      const double c = 1.0 + dot(tnb, tb), ic = 1.0 / c;
+      const double c = 1.0 + dot(tnb, tb), ic = rcp64(c);
       const v3 n = cross(tnb, tb), w = ic * n;
       const v3 sp = axpy(-dot(tnb, tb), tb, tnb);
       gb = ilb * w;

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) k_rows_gen(RowGenArgs a) {
     }
   }
   const int c = a.dof_comp[i];
-  const double m = a.mass[i], idt = 1.0 / a.dt;
+  const double m = a.mass[i], idt = a.idt;
   if (c < 3) {
     F += m * a.g[c];
     F -= a.damp[i] * (a.q[i] - a.qn[i]);

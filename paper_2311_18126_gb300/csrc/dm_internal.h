@@ -112,7 +112,7 @@ struct DevArrays {
   // edges
   int32_t *edge_a = nullptr, *edge_b = nullptr, *edge_th = nullptr,
           *edge_sys = nullptr;
-  double *edge_lbar = nullptr, *edge_EA = nullptr;
+  double *edge_ilbar = nullptr, *edge_EA = nullptr;  // 1 / rest length, EA
   double *d1n = nullptr, *tn = nullptr;  // committed frames, SoA [3][Ne]
   // per-iteration edge outputs (SoA): t[3], len, d1[3], m1[3], m2[3]
   double *ef = nullptr;                  // [13][Ne]

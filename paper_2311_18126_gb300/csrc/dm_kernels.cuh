@@ -8,7 +8,7 @@ struct EdgeArgs {
   int ne;
   const double *q;
   const int32_t *edge_a, *edge_b, *edge_th, *edge_sys;
-  const double *edge_EA, *edge_lbar, *tn, *d1n;
+  const double *edge_EA, *edge_ilbar, *tn, *d1n;  // edge_ilbar: 1 / rest length
   const int32_t *sys_active;
   int32_t *sys_status;
   double *ef, *es;
@@ -36,6 +36,7 @@ struct RowArgs {
   const double *fc;  // edge-edge contact force per DOF (NULL without contact)
   int nd, ns, ne;
   double dt, g[3], eta;
+  double idt;  // 1 / dt
   const double *q, *qn, *vn, *mass, *rscale, *damp;
   const uint8_t *fixed;
   const int32_t *dof_sys;
@@ -89,6 +90,7 @@ struct NodeArgs {
 struct RowGenArgs {
   int nd, ns, ne, nn;
   double dt, g[3];
+  double idt;  // 1 / dt
   const double *q, *qn, *vn, *mass, *rscale, *damp;
   const uint8_t *fixed;
   const int32_t *dof_sys, *dof_node, *dof_comp, *sys_kind, *sys_active;

@@ -54,19 +54,30 @@ __device__ __forceinline__ void k_rows_rod_one(RowArgs a, const int i) {
   const int node = r >> 2, c = r & 3;
   const int st0 = a.rod_st0[rod], e0 = a.rod_edge0[rod];
   const int NS = a.ns, NE = a.ne;
-  double F = 0.0;
+  // G = minus the sum of the forces on DOF i (the residual adds it), so
+  // that the sums start from their first term, not from an add to zero
+  double G = 0.0;
   double brow[11];
-#pragma unroll
-  for (int d = 0; d < 11; ++d) brow[d] = 0.0;
   // stencils m (interior nodes 1..N-2) with 4m-4 <= r <= 4m+6
   int mlo = (r - 6 + 3) >= 0 ? (r - 6 + 3) / 4 : 0;
   if (mlo < 1) mlo = 1;
   int mhi = (r + 4) / 4;
   if (mhi > N - 2) mhi = N - 2;
-  for (int m = mlo; m <= mhi; ++m) {
+  {
+    const bool any = mlo <= mhi;
+    const int lr = r - 4 * (mlo - 1);
+    const int st = st0 + mlo - 1;
+    if (MODE != 2 && any) G = a.sg[lr * NS + st];
+#pragma unroll
+    for (int d = 0; d < 11; ++d) {
+      const int lc = lr - d;
+      brow[d] = (MODE != 1 && any && lc >= 0) ? a.sh[upk<11>(lc, lr) * NS + st] : 0.0;
+    }
+  }
+  for (int m = mlo + 1; m <= mhi; ++m) {
     const int lr = r - 4 * (m - 1);
     const int st = st0 + m - 1;
-    if (MODE != 2) F -= a.sg[lr * NS + st];
+    if (MODE != 2) G += a.sg[lr * NS + st];
     if (MODE != 1) {
 #pragma unroll
       for (int d = 0; d < 11; ++d) {
@@ -76,33 +87,38 @@ __device__ __forceinline__ void k_rows_rod_one(RowArgs a, const int i) {
     }
   }
   const double m_i = a.mass[i];
-  const double idt = 1.0 / a.dt;
+  const double idt = a.idt;
   if (c < 3) {
-    if (node <= N - 2) {  // edge `node` starts here
-      const int e = e0 + node;
-      if (MODE != 2) F += a.es[c * NE + e];
-      if (MODE != 1) {
+    // one copy per component, so that every index of brow is a constant
+    // (brow stays in registers)
 #pragma unroll
-        for (int cp = 0; cp <= 2; ++cp)
-          if (cp <= c) brow[c - cp] += a.es[ksym(c, cp) * NE + e];
+    for (int cc = 0; cc < 3; ++cc) {
+      if (cc != c) continue;
+      if (node <= N - 2) {  // edge `node` starts here
+        const int e = e0 + node;
+        if (MODE != 2) G -= a.es[cc * NE + e];
+        if (MODE != 1) {
+#pragma unroll
+          for (int cp = 0; cp <= cc; ++cp) brow[cc - cp] += a.es[ksym(cc, cp) * NE + e];
+        }
       }
-    }
-    if (node >= 1) {  // edge `node-1` ends here
-      const int e = e0 + node - 1;
-      if (MODE != 2) F -= a.es[c * NE + e];
-      if (MODE != 1) {
+      if (node >= 1) {  // edge `node-1` ends here
+        const int e = e0 + node - 1;
+        if (MODE != 2) G += a.es[cc * NE + e];
+        if (MODE != 1) {
 #pragma unroll
-        for (int cp = 0; cp <= 2; ++cp) {
-          const double kv = a.es[ksym(c, cp) * NE + e];
-          if (cp <= c) brow[c - cp] += kv;
-          brow[4 + c - cp] -= kv;
+          for (int cp = 0; cp <= 2; ++cp) {
+            const double kv = a.es[ksym(cc, cp) * NE + e];
+            if (cp <= cc) brow[cc - cp] += kv;
+            brow[4 + cc - cp] -= kv;
+          }
         }
       }
     }
     const double cd = a.damp[i];
     if (MODE != 2) {
-      F += m_i * a.g[c];
-      F -= cd * (a.q[i] - a.qn[i]);
+      G = fma(-m_i, a.g[c], G);
+      G = fma(cd, a.q[i] - a.qn[i], G);
     }
     brow[0] += cd;
   }
@@ -121,8 +137,8 @@ __device__ __forceinline__ void k_rows_rod_one(RowArgs a, const int i) {
     for (int d = 0; d < 11; ++d) a.band[(size_t)d * a.nd + i] = brow[d];
   }
   if (MODE != 2) {
-    if (a.fc) F += a.fc[i];
-    double f = m_i * idt * idt * (a.q[i] - a.qn[i]) - m_i * idt * a.vn[i] - F;
+    if (a.fc) G -= a.fc[i];
+    double f = m_i * idt * idt * (a.q[i] - a.qn[i]) - m_i * idt * a.vn[i] + G;
     if (a.fixed[i]) f = 0.0;
     a.f[i] = f;
     // scaled residual, max-reduced per system (order independent)
