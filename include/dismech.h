@@ -52,7 +52,9 @@ typedef enum dm_status {
   DM_ERR_DEGENERATE = 4,    /* zero-length edge, antiparallel edges at a
                                stencil (kappa b singular, Eq. 4), an edge
                                reversed within one step, or a pivot that is
-                               zero or tiny against its row's diagonal      */
+                               zero or tiny against its row's diagonal (or,
+                               in the rod and limb eliminations, outside
+                               [2^-126, 2^126), the reciprocal's range)     */
   DM_ERR_PENETRATION = 5,   /* edge-edge distance D <= 0 (Eq. 10 undefined)  */
   DM_ERR_CUDA = 6,          /* a CUDA runtime call failed                    */
   DM_ERR_OOM = 7            /* device allocation failed                      */
