@@ -362,16 +362,20 @@ __global__ void __launch_bounds__(kGenBorderThreads) k_gen_border(SolveGenArgs a
   double *J = a.gen + a.gs_JBB[w];
   double *acc = a.gen + a.gs_rB[w];
   // the border block [S | r] from the assembled block and the limbs' Schur sums
+  // (asynchronous copies for the matrix, all in flight at once)
   auto load = [&]() {
     for (int e = tid; e < nB * nB; e += nt) {
       const int r = e / nB;
-      S[r * ld + e - r * nB] = J[e];
+      cp_async8(S + r * ld + e - r * nB, J + e);
     }
+    cp_async_commit();
     for (int b = tid; b < nB; b += nt) S[b * ld + nB] = acc[b] - a.f[bd[b]];
+    cp_async_wait_all();
   };
   if (go && !bad && nB > 0) {
     load();
-    for (int b = tid; b < nB; b += nt) dorig[b] = fabs(J[b * nB + b]);
+    __syncthreads();
+    for (int b = tid; b < nB; b += nt) dorig[b] = fabs(S[b * ld + b]);
     if (tid == 0) flag[3] = 1;
     __syncthreads();
     // first attempt: elimination in order, without pivoting; the thread that
@@ -527,17 +531,29 @@ __global__ void __launch_bounds__(128) k_gen_limb_back(SolveGenArgs a) {
   const double *G = a.gen;
   const double *Ug = G + a.lb_y[L];
   auto dof = [&](int p) { return d0 + (dir ? n - 1 - p : p); };
-  for (int e = lane; e < ne * 12; e += 32) Us[e] = Ug[e];
-  // the condensed rows ne..n-1 from the border values
-  if (lane < m) {
-    const double *Z = G + a.lb_Y[L] + lane * (nbc + 1);
+  // the U rows by asynchronous copies, in flight while the condensed rows
+  // are formed
+  for (int e = lane; e < ne * 12; e += 32) cp_async8(Us + e, Ug + e);
+  cp_async_commit();
+  // the condensed rows ne..n-1 from the border values: the nbc values this
+  // limb couples to fetched one per lane (one round trip), then broadcast
+  {
     const double *xB = G + a.gs_xB[w];
     const int32_t *bc = a.lb_bcols + a.lb_bc0[L];
-    double v = Z[nbc];
-    for (int b = 0; b < nbc; ++b) v = fma(-Z[b], xB[bc[b]], v);
-    xr[lane] = v;
-    atomicAdd(a.q + dof(ne + lane), v);
+    const double xbv = lane < nbc ? xB[bc[lane]] : 0.0;
+    const double *Z = G + a.lb_Y[L] + (lane < m ? lane : 0) * (nbc + 1);
+    double v = lane < m ? Z[nbc] : 0.0;
+#pragma unroll
+    for (int b = 0; b < kFastMaxBC; ++b) {
+      const double xb = __shfl_sync(kFull, xbv, b);
+      if (lane < m && b < nbc) v = fma(-Z[b], xb, v);
+    }
+    if (lane < m) {
+      xr[lane] = v;
+      atomicAdd(a.q + dof(ne + lane), v);
+    }
   }
+  cp_async_wait_all();
   __syncwarp();
   // lane i (0..10) holds the right-hand side of row p - i less the terms of
   // the solved rows; lane 11 brings in row p - 11 untouched
