@@ -1,5 +1,5 @@
-"""Host emulations (numpy, CPU) of arithmetic the rod solver's kernels do
-with integer tricks or blocked indexing, checked against plain definitions:
+"""Host emulations (numpy, CPU) of arithmetic the solver kernels do with
+integer tricks or blocked indexing, checked against plain definitions:
 
 * the FP64 reciprocal: an FP32 seed built from the upper bits of d by
   integer operations (exponent rebiased by 1023 - 127), its FP32 reciprocal,
@@ -11,7 +11,10 @@ with integer tricks or blocked indexing, checked against plain definitions:
 * the blocked back substitution of a chain (blocks of 11 rows from the
   separator down, a sliding 22-slot buffer of running values, the z of row
   k - 11 brought in at row k, the unrolled step for blocks whose rows are
-  all in [11, kstart)) against x_i = z_i - sum_d L[i+d][i] x_{i+d}.
+  all in [11, kstart)) against x_i = z_i - sum_d L[i+d][i] x_{i+d};
+* the limb factor's small LU of the condensed block on the augmented
+  matrix (the trailing update and the back substitution over (row, column)
+  pairs, rows from a float reciprocal) against a dense LAPACK solve.
 """
 import numpy as np
 
@@ -163,3 +166,45 @@ def test_blocked_back_substitution_matches_direct():
             for gfast in (None, 1):  # with and without the unrolled blocks
                 got = _back_blocked(L, z, xs, kstart, rows, gfast)
                 np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()))
+
+
+def _small_lu_solve(M, n, nrhs):
+    """The condensed block's LU as the warp runs it on the augmented matrix
+    [A | B] (n x (n + nrhs)): partial pivoting, reciprocal pivots, the
+    trailing update over (row, column) pairs whose row comes from a float
+    reciprocal, the back substitution column by column of U over (row,
+    right-hand side) pairs."""
+    M = M.copy()
+    dinv = np.zeros(n)
+    for j in range(n):
+        bi = j + int(np.argmax(np.abs(M[j:, j])))
+        M[[j, bi]] = M[[bi, j]]
+        rp = 1.0 / M[j, j]
+        dinv[j] = rp
+        lm = M[:, j] * rp
+        wdt = n + nrhs - j - 1
+        iw = np.float32(1.0) / np.float32(wdt)
+        for e in range((n - j - 1) * wdt):
+            r = int((np.float32(e) + np.float32(0.5)) * iw)
+            assert r == e // wdt  # the float row is exact here
+            i, c = j + 1 + r, j + 1 + e - r * wdt
+            M[i, c] = -lm[i] * M[j, c] + M[i, c]
+    ir = np.float32(1.0) / np.float32(nrhs)
+    for i in range(n - 1, -1, -1):
+        M[i, n:] *= dinv[i]
+        for e in range(i * nrhs):
+            k = int((np.float32(e) + np.float32(0.5)) * ir)
+            assert k == e // nrhs
+            c = e - k * nrhs
+            M[k, n + c] = -M[k, i] * M[i, n + c] + M[k, n + c]
+    return M[:, n:]
+
+
+def test_small_lu_pairs_match_dense_solve():
+    rng = np.random.default_rng(3)
+    for n in range(1, 11):
+        for nrhs in (1, 2, 9, 17):
+            A = rng.standard_normal((n, n)) + 0.1 * np.eye(n)
+            B = rng.standard_normal((n, nrhs))
+            got = _small_lu_solve(np.hstack([A, B]), n, nrhs)
+            np.testing.assert_allclose(got, np.linalg.solve(A, B), rtol=1e-9, atol=1e-9)
